@@ -1,0 +1,223 @@
+"""FP64 CPU oracle for the Q1 phase-field method -- TEST INFRASTRUCTURE.
+
+Only the tests, ``__graft_entry__.smoke()`` and the bench's CPU-baseline leg
+may import this package.  The library path of the product never does, and
+this package never imports the product.
+
+The arithmetic lives in ``pf_oracle.c`` (plain element loops in FP64, built by
+``oracle.build``); this module only marshals numpy arrays.  Each wrapper names
+the equation of the paper (JAX-PF, Hu et al.) that it computes.
+
+Parity pins (tests/test_oracle_*.py check them without a GPU):
+  lumped_mass          closed form h^d {1, 1/2, 1/4, 1/8}; sum = domain volume
+  residual             = gradient of energy (central FD); independent dense
+                         NumPy assembler on 4x4 / 5x7 meshes; the Q1 stiffness
+                         stencil closed form (8/3, -1/3); K 1 = 0; uniform
+                         fixed points 0, 1/2, 1
+  ac_explicit          cosine-mode growth factor (exact eigenvector of the
+                         Neumann Q1 operators); 1-D tanh equilibrium profile,
+                         width and interfacial energy; monotone energy decrease
+  ch_explicit          cosine-mode growth factor; exact mass conservation;
+                         monotone energy decrease
+  hessian / jvp        central FD of the residual; symmetry u.Jv = v.Ju
+  newton / gmres       FP64 re-evaluation of the root's residual; GMRES on a
+                         problem with known solution
+  ch_adjoint           central FD of the loss (scalars, a smooth direction of
+                         the mobility field, single nodes); per-step
+                         dot-product test against the linearised forward map
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = None
+
+OR_DOUBLE_WELL = 0
+OR_FAN_CHEN = 1
+
+
+class Mesh(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int64 * 3), ("h", C.c_double * 3)]
+
+
+class Params(C.Structure):
+    _fields_ = [("energy", C.c_int), ("nf", C.c_int), ("W", C.c_double),
+                ("kappa", C.c_double), ("mob", C.c_double), ("alpha", C.c_double),
+                ("beta", C.c_double), ("gamma", C.c_double),
+                ("mob_field", C.POINTER(C.c_double))]
+
+
+def lib():
+    global _LIB
+    if _LIB is None:
+        from . import build as _b
+        path = _b.build()
+        L = C.CDLL(path)
+        P = C.POINTER(C.c_double)
+        M = C.POINTER(Mesh)
+        Pp = C.POINTER(Params)
+        L.or_nnodes.restype = C.c_int64
+        L.or_nnodes.argtypes = [M]
+        L.or_lumped_mass.argtypes = [M, P]
+        L.or_energy.restype = C.c_double
+        L.or_energy.argtypes = [M, Pp, P]
+        L.or_residual.argtypes = [M, Pp, P, P]
+        L.or_hessian_apply.argtypes = [M, Pp, P, P, P]
+        L.or_mobility_stiffness_apply.argtypes = [M, Pp, P, P]
+        L.or_ac_explicit.argtypes = [M, Pp, C.c_double, C.c_int64, P]
+        L.or_ch_chemical_potential.argtypes = [M, Pp, P, P]
+        L.or_ch_explicit.argtypes = [M, Pp, C.c_double, C.c_int64, P]
+        L.or_mass_integral.restype = C.c_double
+        L.or_mass_integral.argtypes = [M, P]
+        L.or_implicit_residual.argtypes = [M, Pp, C.c_double, P, P, P]
+        L.or_implicit_jvp.argtypes = [M, Pp, C.c_double, P, P, P]
+        L.or_gmres.restype = C.c_int
+        L.or_gmres.argtypes = [M, Pp, C.c_double, P, P, P, C.c_int, C.c_int, C.c_double,
+                               C.POINTER(C.c_int)]
+        L.or_newton.restype = C.c_int
+        L.or_newton.argtypes = [M, Pp, C.c_double, P, P, C.c_double, C.c_int, C.c_int,
+                                C.c_double, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                C.POINTER(C.c_double)]
+        L.or_ch_adjoint.restype = C.c_double
+        L.or_ch_adjoint.argtypes = [M, Pp, C.c_double, C.c_int64, P, P, C.c_int, P, P, P]
+        _LIB = L
+    return _LIB
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def mesh(shape, h=1.0):
+    """Mesh for a node array of `shape` = (ny, nx) or (nz, ny, nx)."""
+    dim = len(shape)
+    hs = (h,) * dim if np.isscalar(h) else tuple(h)
+    n = list(reversed(shape)) + [1] * (3 - dim)
+    hh = list(hs) + [1.0] * (3 - dim)
+    return Mesh(dim, (C.c_int64 * 3)(*n), (C.c_double * 3)(*hh))
+
+
+class Problem:
+    """A mesh plus the material parameters of one phase-field model.
+
+    energy: 'double_well' (f = W c^2 (1-c)^2, Eq. 5-6 with the Supp. 3
+    polynomial) or 'fan_chen' (grain growth); nf fields; kappa; mob = L (AC) or
+    M (CH); mob_field = per-node mobility multiplier (CH only).
+    """
+
+    def __init__(self, shape, h=1.0, energy="double_well", nf=1, W=1.0, kappa=1.0, mob=1.0,
+                 alpha=1.0, beta=1.0, gamma=1.5, mob_field=None):
+        self.shape = tuple(shape)
+        self.nf = nf
+        self.m = mesh(self.shape, h)
+        self._mf = None if mob_field is None else _f64(mob_field).ravel()
+        self.p = Params(OR_DOUBLE_WELL if energy == "double_well" else OR_FAN_CHEN, nf, W, kappa,
+                        mob, alpha, beta, gamma,
+                        None if self._mf is None else _ptr(self._mf))
+        self.nnodes = int(np.prod(self.shape))
+
+    def _fshape(self):
+        return self.shape if self.nf == 1 else (self.nf,) + self.shape
+
+    def _out(self, nf=None):
+        nf = self.nf if nf is None else nf
+        return np.zeros((nf,) + self.shape if nf > 1 else self.shape, dtype=np.float64)
+
+    # -- operators --
+    def lumped_mass(self):
+        out = np.zeros(self.shape)
+        lib().or_lumped_mass(C.byref(self.m), _ptr(out))
+        return out
+
+    def energy(self, U):
+        U = _f64(U)
+        return lib().or_energy(C.byref(self.m), C.byref(self.p), _ptr(U))
+
+    def residual(self, U):
+        """r = dE_h/dU (Eq. 11's r without the mobility factor)."""
+        U = _f64(U)
+        out = self._out()
+        lib().or_residual(C.byref(self.m), C.byref(self.p), _ptr(U), _ptr(out))
+        return out
+
+    def hessian_apply(self, U, v):
+        U, v = _f64(U), _f64(v)
+        out = self._out()
+        lib().or_hessian_apply(C.byref(self.m), C.byref(self.p), _ptr(U), _ptr(v), _ptr(out))
+        return out
+
+    def mobility_stiffness_apply(self, mu):
+        mu = _f64(mu)
+        out = self._out(1)
+        lib().or_mobility_stiffness_apply(C.byref(self.m), C.byref(self.p), _ptr(mu), _ptr(out))
+        return out
+
+    def chemical_potential(self, c):
+        c = _f64(c)
+        out = self._out(1)
+        lib().or_ch_chemical_potential(C.byref(self.m), C.byref(self.p), _ptr(c), _ptr(out))
+        return out
+
+    def mass_integral(self, c):
+        c = _f64(c)
+        return lib().or_mass_integral(C.byref(self.m), _ptr(c))
+
+    # -- time stepping --
+    def ac_explicit(self, U, dt, nsteps):
+        U = _f64(U).copy()
+        lib().or_ac_explicit(C.byref(self.m), C.byref(self.p), dt, nsteps, _ptr(U))
+        return U
+
+    def ch_explicit(self, c, dt, nsteps):
+        c = _f64(c).copy()
+        lib().or_ch_explicit(C.byref(self.m), C.byref(self.p), dt, nsteps, _ptr(c))
+        return c
+
+    def implicit_residual(self, dt, Un, U):
+        Un, U = _f64(Un), _f64(U)
+        out = self._out()
+        lib().or_implicit_residual(C.byref(self.m), C.byref(self.p), dt, _ptr(Un), _ptr(U),
+                                   _ptr(out))
+        return out
+
+    def implicit_jvp(self, dt, U, v):
+        U, v = _f64(U), _f64(v)
+        out = self._out()
+        lib().or_implicit_jvp(C.byref(self.m), C.byref(self.p), dt, _ptr(U), _ptr(v), _ptr(out))
+        return out
+
+    def gmres(self, dt, U, b, restart=30, maxit=1000, rtol=1e-10):
+        U, b = _f64(U), _f64(b)
+        x = np.zeros_like(b)
+        it = C.c_int(0)
+        ok = lib().or_gmres(C.byref(self.m), C.byref(self.p), dt, _ptr(U), _ptr(b), _ptr(x),
+                            restart, maxit, rtol, C.byref(it))
+        return x, bool(ok), it.value
+
+    def newton(self, dt, Un, U0=None, abs_tol=1e-10, max_newton=30, restart=30, gmres_rtol=1e-10):
+        Un = _f64(Un)
+        U = Un.copy() if U0 is None else _f64(U0).copy()
+        ni, gi, fn = C.c_int(0), C.c_int(0), C.c_double(0)
+        ok = lib().or_newton(C.byref(self.m), C.byref(self.p), dt, _ptr(Un), _ptr(U), abs_tol,
+                             max_newton, restart, gmres_rtol, C.byref(ni), C.byref(gi),
+                             C.byref(fn))
+        return U, dict(ok=bool(ok), newton_iters=ni.value, gmres_iters=gi.value,
+                       final_norm=fn.value)
+
+    def ch_adjoint(self, c0, target, dt, nsteps, nodal_loss=False, want_field=True):
+        c0, target = _f64(c0), _f64(target)
+        gs = np.zeros(3)
+        gmf = np.zeros(self.shape) if want_field else None
+        lam0 = np.zeros(self.shape)
+        loss = lib().or_ch_adjoint(C.byref(self.m), C.byref(self.p), dt, nsteps, _ptr(c0),
+                                   _ptr(target), int(nodal_loss), _ptr(gs),
+                                   _ptr(gmf) if want_field else None, _ptr(lam0))
+        return loss, dict(kappa=gs[0], W=gs[1], M=gs[2], mob_field=gmf, c0=lam0)
