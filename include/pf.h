@@ -1,0 +1,116 @@
+/*
+ * libpf -- GB300 (sm_103a) matrix-free phase-field solver, C ABI.
+ *
+ * Method (JAX-PF, Hu et al.): Q1 finite elements on a uniform grid, 2x2
+ * (2x2x2) Gauss quadrature, lumped mass, zero-flux boundaries.  The
+ * semi-discrete system is M dU/dt + r(U, theta) = 0 (Eq. 11) with
+ *   r_i = sum_e sum_q w_q |J| [ f'(U_q) N_i(q) + kappa grad U_q . grad N_i(q) ]
+ * (the gradient of the discrete free energy of Eq. 5-6).  Allen-Cahn
+ * (Eq. 1) advances U <- U - dt L M^-1 r(U) (Eq. 12).  Cahn-Hilliard uses the
+ * split form of Eq. 9-10, read as mu = f'(c) - kappa lap c:
+ *   M mu = r(c),   c <- c - dt M^-1 K_M mu,
+ * where K_M is the mobility-weighted stiffness matrix.  The implicit step
+ * solves R(U) = M (U - U^n)/dt + L r(U) = 0 (Eq. 13-14) by Newton with a
+ * matrix-free Jacobian-vector product inside GMRES.
+ *
+ * Conventions for every entry point:
+ *   - Array arguments are DEVICE pointers to caller-owned memory unless the
+ *     comment says "host".  Fields are FP32, structure-of-arrays: field f of
+ *     a mesh with N nodes occupies state[f*N .. f*N+N-1]; node
+ *     (i, j, k) sits at (k*ny + j)*nx + i (x fastest).
+ *   - The library never allocates device memory.  pf_create_mesh reports the
+ *     workspace size; the caller allocates it and binds it with
+ *     pf_bind_workspace before any compute call.
+ *   - Work is enqueued on the stream given at creation, in order, without a
+ *     device synchronisation.  Calls that return host scalars (pf_energy,
+ *     pf_step_implicit statistics, pf_adjoint) synchronise that stream.
+ *   - Every call returns a pf_status; on failure pf_last_error(ctx) gives a
+ *     message.  No C++ exception crosses the ABI.  After PF_ERR_CUDA the
+ *     context should be destroyed.
+ *   - A context is not thread-safe; use one per host thread.
+ */
+#ifndef PF_H
+#define PF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pf_ctx pf_ctx; /* opaque, owned by the library */
+
+typedef enum {
+  PF_OK = 0,
+  PF_ERR_ARG = -1,            /* invalid argument (null pointer, size, model mismatch) */
+  PF_ERR_CUDA = -2,           /* a CUDA runtime call or kernel launch failed */
+  PF_ERR_NOT_CONVERGED = -3,  /* Newton / GMRES hit their iteration limits */
+  PF_ERR_NONFINITE = -4,      /* a NaN or Inf was produced (e.g. dt above the stability bound) */
+  PF_ERR_TIMEOUT = -5,        /* a bounded device-side wait expired */
+  PF_ERR_STATE = -6           /* call order violated (no workspace bound, no params set) */
+} pf_status;
+
+typedef enum {
+  PF_MODEL_AC = 0,      /* Allen-Cahn, double well f = W u^2 (1-u)^2 (Eq. 1, 5; Supp. 3) */
+  PF_MODEL_CH = 1,      /* Cahn-Hilliard split form, same f (Eq. 2, 6, 9, 10) */
+  PF_MODEL_FANCHEN = 2  /* n_fields Allen-Cahn order parameters, Fan-Chen grain-growth energy */
+} pf_model;
+
+typedef struct {
+  double W;           /* double-well height (AC, CH) */
+  double kappa;       /* gradient-energy coefficient (Eq. 5-6) */
+  double mobility;    /* L (AC, Fan-Chen; Eq. 1 M_eta) or M (CH; Eq. 2 M_c) */
+  double dt;          /* time step */
+  double fc_alpha;    /* Fan-Chen f = sum_i(-a/2 e_i^2 + b/4 e_i^4) + g sum_{i<j} e_i^2 e_j^2 */
+  double fc_beta;
+  double fc_gamma;
+  double shift;       /* the FP32 working state is stored as U - shift (exact change of
+                         variable that keeps rounding relative to the deviation); 0.5 suits
+                         the double well, 0 the Fan-Chen model */
+  const float* mobility_field; /* CH only: device, one multiplier per node, M(x) = M m(x)
+                                  interpolated by Q1 at Gauss points; NULL = uniform.
+                                  Must stay valid while the context uses it. */
+} pf_params;
+
+/* Create a solver context for a uniform Q1 mesh.
+ *   dim              2 (AC, CH) or 3 (FANCHEN)
+ *   nodes[3]         nodes per axis (x, y, z); nodes[2] ignored in 2-D; each >= 2
+ *                    (>= 3 along every axis for CH)
+ *   h[3]             node spacing per axis (> 0)
+ *   model, n_fields  n_fields must be 1 for AC/CH, 1..8 for FANCHEN
+ *   stream           cudaStream_t (NULL = legacy default stream) on which all work runs
+ *   workspace_bytes  out (host): device workspace the caller must bind
+ * Defines the discretisation of Sec. 2.2 / Eq. 11.  Host only; no CUDA call. */
+pf_status pf_create_mesh(pf_ctx** out, int dim, const int64_t nodes[3], const double h[3],
+                         pf_model model, int n_fields, void* stream, size_t* workspace_bytes);
+
+/* Bind caller-owned device memory (>= workspace_bytes, 256-byte aligned) as the
+ * context's scratch space.  The memory must outlive the context's use of it. */
+pf_status pf_bind_workspace(pf_ctx* ctx, void* dev_ptr, size_t bytes);
+
+/* Set the material and time-step parameters theta (Eq. 11, 15).  Host pointer p
+ * is copied; p->mobility_field (device) is referenced, not copied. */
+pf_status pf_set_params(pf_ctx* ctx, const pf_params* p);
+
+/* Advance `state` (device, n_fields * N FP32, in/out) by n_steps >= 0 explicit
+ * Euler steps with the lumped mass, Eq. 12: AC U <- U - dt L r(U)/m;
+ * CH c <- c - dt K_M mu / m with m mu = r(c).  Enqueues only. */
+pf_status pf_step_explicit(pf_ctx* ctx, float* state, int64_t n_steps);
+
+/* Discrete free energy E_h = sum_e sum_q w_q |J| [f(U_q) + kappa/2 |grad U_q|^2]
+ * (Eq. 5-6) and, per field, the mass integral sum_i m_i U_i, accumulated in FP64.
+ * energy: host, 1 double; mass: host, n_fields doubles (either may be NULL).
+ * Synchronises the stream. */
+pf_status pf_energy(pf_ctx* ctx, const float* state, double* energy, double* mass);
+
+/* Human-readable description of the last failure on this context. */
+const char* pf_last_error(const pf_ctx* ctx);
+
+/* Release the context (not the caller's workspace or arrays). NULL is a no-op. */
+void pf_destroy(pf_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PF_H */

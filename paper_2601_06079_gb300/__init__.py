@@ -1,0 +1,102 @@
+"""GB300-native matrix-free phase-field solver (JAX-PF method, Q1 FEM).
+
+Python face of libpf (include/pf.h).  PyTorch provides device memory and
+streams only; every step of the method runs in the library's CUDA kernels.
+
+    from paper_2601_06079_gb300 import Solver
+    s = Solver((2048, 2048), h=1.0, model="ch")
+    s.set_params(W=1.0, kappa=0.5, mobility=1.0, dt=1e-3, shift=0.5)
+    s.step_explicit(c, 10_000)          # c: torch.float32 CUDA tensor (ny, nx)
+    E, mass = s.energy(c)
+"""
+from __future__ import annotations
+
+import torch
+
+from . import _lib
+from ._lib import (PF_MODEL_AC, PF_MODEL_CH, PF_MODEL_FANCHEN, pf_bind_workspace,  # noqa: F401
+                   pf_create_mesh, pf_destroy, pf_energy, pf_last_error, pf_set_params,
+                   pf_step_explicit)
+
+_MODELS = {"ac": PF_MODEL_AC, "ch": PF_MODEL_CH, "fanchen": PF_MODEL_FANCHEN}
+
+
+class PFError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_lib.STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Solver:
+    """One mesh + model + parameter set on one CUDA device and stream.
+
+    shape: node counts (ny, nx) or (nz, ny, nx); h: spacing (scalar or per
+    axis, x first); model: 'ac' | 'ch' | 'fanchen'.  The workspace is a torch
+    uint8 tensor owned by this object and bound to the library context.
+    """
+
+    def __init__(self, shape, h=1.0, model="ac", n_fields=1, device="cuda", stream=None):
+        self.shape = tuple(int(s) for s in shape)
+        self.dim = len(self.shape)
+        self.device = torch.device(device)
+        if self.device.type != "cuda":
+            raise ValueError("libpf runs on CUDA devices only")
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        hs = [float(h)] * self.dim if isinstance(h, (int, float)) else [float(v) for v in h]
+        nodes = list(reversed(self.shape))
+        self.n_fields = n_fields
+        self.model = model
+        st, self._ctx, ws = pf_create_mesh(self.dim, nodes, hs, _MODELS[model], n_fields,
+                                           self.stream.cuda_stream)
+        if st != 0:
+            raise PFError(st, "pf_create_mesh rejected the mesh/model")
+        self._ws = torch.empty(max(ws, 256), dtype=torch.uint8, device=self.device)
+        self._check(pf_bind_workspace(self._ctx, self._ws.data_ptr(), self._ws.numel()))
+        self._params = None
+        self._keep = None
+
+    def _check(self, st):
+        if st != 0:
+            raise PFError(st, pf_last_error(self._ctx))
+
+    def set_params(self, W=1.0, kappa=1.0, mobility=1.0, dt=0.01, shift=None,
+                   alpha=1.0, beta=1.0, gamma=1.5, mobility_field=None):
+        if shift is None:
+            shift = 0.5 if self.model in ("ac", "ch") else 0.0
+        mf = None
+        if mobility_field is not None:
+            mf = mobility_field.to(self.device, torch.float32).contiguous()
+        p = _lib.pf_params(W, kappa, mobility, dt, alpha, beta, gamma, shift,
+                           None if mf is None else mf.data_ptr())
+        self._check(pf_set_params(self._ctx, p))
+        self._params, self._keep = p, mf
+
+    def _state(self, t):
+        if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+            raise ValueError("state must be a contiguous float32 CUDA tensor")
+        want = self.n_fields * int(torch.tensor(self.shape).prod())
+        if t.numel() != want:
+            raise ValueError(f"state has {t.numel()} values, mesh needs {want}")
+        return t.data_ptr()
+
+    def step_explicit(self, state, n_steps):
+        """Advance `state` in place by n_steps explicit Euler steps (Eq. 12)."""
+        self._check(pf_step_explicit(self._ctx, self._state(state), n_steps))
+        return state
+
+    def energy(self, state):
+        """(E_h, mass integral) in FP64 (Eq. 5-6); synchronises the stream."""
+        st, e, m = pf_energy(self._ctx, self._state(state))
+        self._check(st)
+        return e, m
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            pf_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,118 @@
+"""ctypes binding of libpf (include/pf.h): argument marshalling only.
+
+Every function here keeps the C name and forwards to the shared library;
+all arithmetic runs in the CUDA kernels behind it.  The library must be built
+(``paper_2601_06079_gb300.build``); loading fails loudly otherwise -- there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from . import build as _build
+
+PF_OK = 0
+PF_ERR_ARG = -1
+PF_ERR_CUDA = -2
+PF_ERR_NOT_CONVERGED = -3
+PF_ERR_NONFINITE = -4
+PF_ERR_TIMEOUT = -5
+PF_ERR_STATE = -6
+
+PF_MODEL_AC = 0
+PF_MODEL_CH = 1
+PF_MODEL_FANCHEN = 2
+
+STATUS_NAMES = {0: "PF_OK", -1: "PF_ERR_ARG", -2: "PF_ERR_CUDA", -3: "PF_ERR_NOT_CONVERGED",
+                -4: "PF_ERR_NONFINITE", -5: "PF_ERR_TIMEOUT", -6: "PF_ERR_STATE"}
+
+
+class pf_params(C.Structure):
+    _fields_ = [("W", C.c_double), ("kappa", C.c_double), ("mobility", C.c_double),
+                ("dt", C.c_double), ("fc_alpha", C.c_double), ("fc_beta", C.c_double),
+                ("fc_gamma", C.c_double), ("shift", C.c_double),
+                ("mobility_field", C.c_void_p)]
+
+
+_LIB = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libpf.so from the package's _build directory (never rebuilt here)."""
+    global _LIB
+    if _LIB is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(
+                f"libpf is not built ({path} missing); run paper_2601_06079_gb300.build.build()")
+        L = C.CDLL(path)
+        ctx = C.c_void_p
+        st = C.c_int
+        L.pf_create_mesh.restype = st
+        L.pf_create_mesh.argtypes = [C.POINTER(ctx), C.c_int, C.POINTER(C.c_int64),
+                                     C.POINTER(C.c_double), C.c_int, C.c_int, C.c_void_p,
+                                     C.POINTER(C.c_size_t)]
+        L.pf_bind_workspace.restype = st
+        L.pf_bind_workspace.argtypes = [ctx, C.c_void_p, C.c_size_t]
+        L.pf_set_params.restype = st
+        L.pf_set_params.argtypes = [ctx, C.POINTER(pf_params)]
+        L.pf_step_explicit.restype = st
+        L.pf_step_explicit.argtypes = [ctx, C.c_void_p, C.c_int64]
+        L.pf_energy.restype = st
+        L.pf_energy.argtypes = [ctx, C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        L.pf_last_error.restype = C.c_char_p
+        L.pf_last_error.argtypes = [ctx]
+        L.pf_destroy.restype = None
+        L.pf_destroy.argtypes = [ctx]
+        _LIB = L
+    return _LIB
+
+
+def exported_symbols():
+    """Names declared in include/pf.h (checked against the .so by the tests)."""
+    return ["pf_create_mesh", "pf_bind_workspace", "pf_set_params", "pf_step_explicit",
+            "pf_energy", "pf_last_error", "pf_destroy"]
+
+
+# --- thin same-name wrappers -------------------------------------------------
+
+def pf_create_mesh(dim, nodes, h, model, n_fields, stream):
+    ctx = C.c_void_p()
+    ws = C.c_size_t(0)
+    n = (C.c_int64 * 3)(*(list(nodes) + [1] * (3 - len(nodes))))
+    hh = (C.c_double * 3)(*(list(h) + [1.0] * (3 - len(h))))
+    s = lib().pf_create_mesh(C.byref(ctx), dim, n, hh, model, n_fields, C.c_void_p(stream),
+                             C.byref(ws))
+    return s, ctx, ws.value
+
+
+def pf_bind_workspace(ctx, ptr, nbytes):
+    return lib().pf_bind_workspace(ctx, C.c_void_p(ptr), nbytes)
+
+
+def pf_set_params(ctx, params: pf_params):
+    return lib().pf_set_params(ctx, C.byref(params))
+
+
+def pf_step_explicit(ctx, state_ptr, n_steps):
+    return lib().pf_step_explicit(ctx, C.c_void_p(state_ptr), int(n_steps))
+
+
+def pf_energy(ctx, state_ptr):
+    e, m = C.c_double(0), C.c_double(0)
+    s = lib().pf_energy(ctx, C.c_void_p(state_ptr), C.byref(e), C.byref(m))
+    return s, e.value, m.value
+
+
+def pf_last_error(ctx) -> str:
+    r = lib().pf_last_error(ctx)
+    return r.decode() if r else ""
+
+
+def pf_destroy(ctx):
+    lib().pf_destroy(ctx)

@@ -1,0 +1,56 @@
+// Internal declarations shared by the libpf translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/pf.h"
+
+namespace pf {
+
+// Gauss points of the 2-point rule on the unit interval, (1 -+ 1/sqrt 3)/2.
+// g_lo = N_0 at the upper point = N_1 at the lower point, and vice versa.
+constexpr float kGHi = 0.78867513459481288225f;
+constexpr float kGLo = 0.21132486540518711775f;
+
+// Assembled 9-point Q1 stiffness stencil on a uniform 2-D grid, pre-scaled:
+// (K v)_i = c0 v_i + cx (v_W + v_E) + cy (v_S + v_N) + cd (v_SW + v_SE + v_NW + v_NE).
+struct Stencil2D {
+  float c0, cx, cy, cd;
+};
+
+// Arguments of one fused explicit step on a 2-D mesh.  The state is the
+// shifted FP32 variable d = u - shift; the mirror extension about boundary
+// nodes reproduces the zero-flux Q1 operators divided by the lumped mass, so
+// every node uses the interior stencil and the interior mass.
+struct Explicit2DArgs {
+  const float* in;
+  float* out;
+  int nx, ny;
+  // f'(shift + d) / 4 as p0 + d (p1 + d (p2 + d p3)), times the stage factor
+  float p0, p1, p2, p3;
+  Stencil2D k1;  // AC: -dt L kappa / m * K;   CH: kappa / m * K  (mu stage)
+  Stencil2D k2;  // CH: -dt M / m * K          (c stage)
+  int vec_ok;    // rows 16-byte aligned: nx % 4 == 0 and 16-byte aligned base pointers
+};
+
+cudaError_t launch_ac2d(const Explicit2DArgs& a, cudaStream_t s);
+cudaError_t launch_ch2d(const Explicit2DArgs& a, cudaStream_t s);
+cudaError_t launch_shift(const float* in, float* out, int64_t n, float add, cudaStream_t s);
+
+// Energy / mass diagnostics (Eq. 5-6), FP64 accumulation, deterministic.
+struct Energy2DArgs {
+  const float* d;  // shifted state (one field)
+  int nx, ny;
+  double hx, hy;
+  float shift;
+  float q0, q1, q2, q3, q4;  // f(shift + d) = q0 + d (q1 + d (q2 + d (q3 + d q4)))
+  float kappa;
+};
+int energy2d_blocks(int nx, int ny);
+cudaError_t launch_energy2d(const Energy2DArgs& a, double* partials, double* result,
+                            cudaStream_t s);
+
+}  // namespace pf

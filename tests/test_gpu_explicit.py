@@ -1,0 +1,204 @@
+"""GPU parity: fused explicit AC / CH step kernels vs the FP64 oracle.
+
+Bar (the benchmark spec): relative L2 error <= 1e-5 against the FP64 oracle after the
+stated steps, element by element on the same seeded FP32 inputs.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import pf_inputs as G
+
+pytestmark = pytest.mark.gpu
+
+REL_L2 = 1e-5
+
+
+def _pf():
+    import paper_2601_06079_gb300 as pf
+    return pf
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def gpu_run(model, u0, h, n_steps, **par):
+    pf = _pf()
+    s = pf.Solver(u0.shape, h=h, model=model)
+    s.set_params(**par)
+    t = torch.from_numpy(np.ascontiguousarray(u0, dtype=np.float32)).cuda()
+    s.step_explicit(t, n_steps)
+    torch.cuda.synchronize()
+    out = t.cpu().numpy()
+    return out, s, t
+
+
+# ---------------------------------------------------------------- Allen-Cahn
+
+@pytest.mark.parametrize("shape", [(2, 2), (4, 4), (5, 7), (17, 13), (64, 64), (131, 250), (300, 128)])
+def test_ac_matches_oracle_small_and_ragged(shape):
+    u0 = G.ac_initial(3, shape)
+    par = dict(W=1.0, kappa=1.0, mobility=1.0, dt=0.01)
+    steps = 50
+    out, _, _ = gpu_run("ac", u0, 1.0, steps, **par)
+    ref = O.Problem(shape, W=1.0, kappa=1.0, mob=1.0).ac_explicit(u0, 0.01, steps)
+    assert rel_l2(out, ref) <= REL_L2
+    assert np.abs(out - ref).max() <= 1e-5
+
+
+def test_ac_config_64x64_200_steps():
+    # 64x64 nodes, domain 64x64 -> h = 64/63; W = kappa = L = 1; dt = 0.01; 200 steps
+    for seed in (1, 2, 3, 4, 5):
+        u0 = G.ac_initial(seed, (64, 64))
+        h = 64.0 / 63.0
+        out, _, _ = gpu_run("ac", u0, h, 200, W=1.0, kappa=1.0, mobility=1.0, dt=0.01)
+        ref = O.Problem((64, 64), h=h, W=1.0, kappa=1.0, mob=1.0).ac_explicit(u0, 0.01, 200)
+        assert rel_l2(out, ref) <= REL_L2, seed
+
+
+def test_ac_anisotropic_spacing_and_params():
+    shape = (37, 45)
+    u0 = G.ac_initial(9, shape, 0.2, 0.8)
+    out, _, _ = gpu_run("ac", u0, (0.8, 1.25), 40, W=1.7, kappa=0.6, mobility=1.3, dt=0.01)
+    ref = O.Problem(shape, h=(0.8, 1.25), W=1.7, kappa=0.6, mob=1.3).ac_explicit(u0, 0.01, 40)
+    assert rel_l2(out, ref) <= REL_L2
+
+
+# ---------------------------------------------------------------- Cahn-Hilliard
+
+@pytest.mark.parametrize("shape", [(3, 3), (4, 4), (5, 7), (17, 13), (130, 67), (256, 256), (129, 515)])
+def test_ch_matches_oracle_small_and_ragged(shape):
+    c0 = G.ch_initial(4, shape)
+    steps = 100
+    out, _, _ = gpu_run("ch", c0, 1.0, steps, W=1.0, kappa=0.5, mobility=1.0, dt=1e-3)
+    ref = O.Problem(shape, W=1.0, kappa=0.5, mob=1.0).ch_explicit(c0, 1e-3, steps)
+    assert rel_l2(out, ref) <= REL_L2
+    assert rel_l2(out - ref.mean(), ref - ref.mean()) <= 1e-4
+
+
+def test_ch_full_trajectory_length_on_128x128():
+    # the stated trajectory (dt = 1e-3, 10,000 steps, t = 10) through spinodal
+    # growth and phase separation, on a domain the oracle finishes in seconds
+    c0 = G.ch_initial(1, (128, 128))
+    out, _, _ = gpu_run("ch", c0, 1.0, 10_000, W=1.0, kappa=0.5, mobility=1.0, dt=1e-3)
+    ref = O.Problem((128, 128), W=1.0, kappa=0.5, mob=1.0).ch_explicit(c0, 1e-3, 10_000)
+    assert ref.max() - ref.min() > 0.5  # phase separated
+    assert rel_l2(out, ref) <= REL_L2
+
+
+def test_ch_full_size_2048_elementwise():
+    n = 2048
+    c0 = G.ch_initial(2, (n, n))
+    steps = 12
+    out, _, _ = gpu_run("ch", c0, 1.0, steps, W=1.0, kappa=0.5, mobility=1.0, dt=1e-3)
+    ref = O.Problem((n, n), W=1.0, kappa=0.5, mob=1.0).ch_explicit(c0, 1e-3, steps)
+    assert rel_l2(out, ref) <= REL_L2
+    assert np.abs(out - ref).max() <= 2e-6
+
+
+def test_ch_full_size_2048_sampled_windows():
+    # after k steps a node depends only on initial data within 2k nodes, so
+    # the oracle reproduces sampled nodes from windows of radius 2k + margin;
+    # windows at corners / edges keep the true zero-flux boundary.
+    n, k = 2048, 100
+    c0 = G.ch_initial(3, (n, n))
+    out, _, _ = gpu_run("ch", c0, 1.0, k, W=1.0, kappa=0.5, mobility=1.0, dt=1e-3)
+    R = 2 * k + 4
+    for cy, cx in [(0, 0), (n - 1, n - 1), (0, 1000), (1023, 1024), (n - 1, 5), (700, n - 1)]:
+        y0, y1 = max(0, cy - R), min(n, cy + R + 1)
+        x0, x1 = max(0, cx - R), min(n, cx + R + 1)
+        win = c0[y0:y1, x0:x1]
+        ref = O.Problem(win.shape, W=1.0, kappa=0.5, mob=1.0).ch_explicit(win, 1e-3, k)
+        # nodes at distance > 2k from every artificial window edge are exact
+        sy = slice(0 if y0 == 0 else 2 * k + 1, win.shape[0] if y1 == n else win.shape[0] - 2 * k - 1)
+        sx = slice(0 if x0 == 0 else 2 * k + 1, win.shape[1] if x1 == n else win.shape[1] - 2 * k - 1)
+        g = out[y0:y1, x0:x1][sy, sx]
+        r = ref[sy, sx]
+        assert g.size > 0
+        assert rel_l2(g, r) <= REL_L2, (cy, cx)
+
+
+# ---------------------------------------------------------------- diagnostics
+
+@pytest.mark.parametrize("model", ["ac", "ch"])
+def test_energy_and_mass_match_oracle(model):
+    shape = (130, 257)
+    u0 = G.ch_initial(6, shape) if model == "ch" else G.ac_initial(6, shape)
+    pf = _pf()
+    s = pf.Solver(shape, h=(0.9, 1.1), model=model)
+    s.set_params(W=1.3, kappa=0.7, mobility=1.0, dt=1e-3)
+    t = torch.from_numpy(u0).cuda()
+    E, M = s.energy(t)
+    P = O.Problem(shape, h=(0.9, 1.1), W=1.3, kappa=0.7)
+    assert abs(E - P.energy(u0)) <= 1e-6 * abs(P.energy(u0))
+    assert abs(M - P.mass_integral(u0)) <= 1e-12 * abs(P.mass_integral(u0))
+
+
+def test_ch_mass_conservation_and_energy_decrease_gpu():
+    shape = (512, 512)
+    c0 = G.ch_initial(7, shape)
+    pf = _pf()
+    s = pf.Solver(shape, h=1.0, model="ch")
+    s.set_params(W=1.0, kappa=0.5, mobility=1.0, dt=1e-3)
+    t = torch.from_numpy(c0).cuda()
+    E0, M0 = s.energy(t)
+    Es = [E0]
+    for _ in range(10):
+        s.step_explicit(t, 1000)
+        E, M = s.energy(t)
+        Es.append(E)
+        assert abs(M - M0) <= 1e-6 * abs(M0)
+    assert all(b <= a + 1e-7 * abs(a) for a, b in zip(Es, Es[1:]))
+    assert Es[-1] < 0.9 * Es[0]
+
+
+def test_deterministic_bitwise():
+    shape = (300, 260)
+    c0 = G.ch_initial(8, shape)
+    a, _, _ = gpu_run("ch", c0, 1.0, 333, W=1.0, kappa=0.5, mobility=1.0, dt=1e-3)
+    b, _, _ = gpu_run("ch", c0, 1.0, 333, W=1.0, kappa=0.5, mobility=1.0, dt=1e-3)
+    assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+
+
+# ---------------------------------------------------------------- edge cases and errors
+
+def test_zero_steps_is_identity_and_uniform_states_fixed():
+    pf = _pf()
+    s = pf.Solver((64, 68), model="ch")
+    s.set_params(W=1.0, kappa=0.5, mobility=1.0, dt=1e-3)
+    c0 = G.ch_initial(1, (64, 68))
+    t = torch.from_numpy(c0).cuda()
+    s.step_explicit(t, 0)
+    assert np.array_equal(t.cpu().numpy(), c0)
+    for a in (0.0, 0.5, 1.0):
+        for model in ("ac", "ch"):
+            s2 = pf.Solver((33, 35), model=model)
+            s2.set_params(W=1.0, kappa=1.0, mobility=1.0, dt=1e-3)
+            u = torch.full((33, 35), a, device="cuda")
+            s2.step_explicit(u, 25)
+            assert torch.equal(u, torch.full_like(u, a))
+
+
+def test_errors_are_reported():
+    pf = _pf()
+    with pytest.raises(pf.PFError):
+        pf.Solver((1, 5), model="ac")            # fewer than 2 nodes
+    with pytest.raises(pf.PFError):
+        pf.Solver((2, 5), model="ch")            # CH needs >= 3 nodes per axis
+    s = pf.Solver((16, 16), model="ac")
+    u = torch.zeros(16, 16, device="cuda")
+    with pytest.raises(pf.PFError) as e:
+        s.step_explicit(u, 1)                    # params not set
+    assert e.value.status == pf._lib.PF_ERR_STATE
+    with pytest.raises(pf.PFError):
+        s.set_params(dt=-1.0)
+    s.set_params(W=1.0, kappa=1.0, mobility=1.0, dt=10.0)  # far above the stability bound
+    u = torch.from_numpy(G.ac_initial(1, (16, 16))).cuda()
+    s.step_explicit(u, 200)
+    with pytest.raises(pf.PFError) as e:
+        s.energy(u)
+    assert e.value.status == pf._lib.PF_ERR_NONFINITE
