@@ -104,6 +104,31 @@ pf_status pf_step_explicit(pf_ctx* ctx, float* state, int64_t n_steps);
  * Synchronises the stream. */
 pf_status pf_energy(pf_ctx* ctx, const float* state, double* energy, double* mass);
 
+/* Energy and mass of a 2-D single-field double-well state (AC or CH) without a
+ * context or workspace, for callers that cannot allocate device memory: a
+ * host that owns all device memory through its own allocator, a process held
+ * to a fixed device-memory budget, or a latency-critical path where
+ * cudaMalloc / cudaFree would synchronise the device.  The paper has no
+ * counterpart; it computes the same E_h and sum_i m_i u_i as pf_energy.
+ *   state         device, nx * ny FP32 values u (unshifted), node (i, j) at j*nx + i
+ *   nx, ny        nodes per axis, >= 2, nx * ny <= 2^31 - 1 (else PF_ERR_ARG)
+ *   hx, hy        node spacing (> 0);  W, kappa: f = W u^2 (1-u)^2, gradient coefficient
+ *   out           device, 2 doubles: out[0] = E_h, out[1] = mass (written on `stream`)
+ *   stream        cudaStream_t to enqueue on (NULL = legacy default stream)
+ *   err           host, may be NULL: set to a static message ("" on success)
+ * Allocates nothing: the reduction's scratch is a static device array of
+ * 2 x 1024 doubles (16 KiB) inside libpf that every GPU loading the library
+ * holds until exit.  The first call on each device looks up that array's
+ * address on the current device; make it before any stream capture.  All
+ * calls share the array and it keeps the last call's partial sums; nothing in
+ * it needs to start at zero (each call overwrites every slot it reads), but
+ * calls that overlap on the GPU (other streams, other threads) race on it and
+ * must be serialised by the caller.  Does not synchronise; returns PF_ERR_CUDA
+ * if a launch fails. */
+pf_status pf_energy2d_static(const float* state, int64_t nx, int64_t ny, double hx, double hy,
+                             double W, double kappa, double* out, void* stream,
+                             const char** err);
+
 /* Human-readable description of the last failure on this context. */
 const char* pf_last_error(const pf_ctx* ctx);
 

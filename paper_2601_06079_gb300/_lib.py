@@ -65,6 +65,10 @@ def lib():
         L.pf_step_explicit.argtypes = [ctx, C.c_void_p, C.c_int64]
         L.pf_energy.restype = st
         L.pf_energy.argtypes = [ctx, C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        L.pf_energy2d_static.restype = st
+        L.pf_energy2d_static.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_double,
+                                         C.c_double, C.c_double, C.c_double, C.c_void_p,
+                                         C.c_void_p, C.POINTER(C.c_char_p)]
         L.pf_last_error.restype = C.c_char_p
         L.pf_last_error.argtypes = [ctx]
         L.pf_destroy.restype = None
@@ -76,7 +80,7 @@ def lib():
 def exported_symbols():
     """Names declared in include/pf.h (checked against the .so by the tests)."""
     return ["pf_create_mesh", "pf_bind_workspace", "pf_set_params", "pf_step_explicit",
-            "pf_energy", "pf_last_error", "pf_destroy"]
+            "pf_energy", "pf_energy2d_static", "pf_last_error", "pf_destroy"]
 
 
 # --- thin same-name wrappers -------------------------------------------------
@@ -107,6 +111,15 @@ def pf_energy(ctx, state_ptr):
     e, m = C.c_double(0), C.c_double(0)
     s = lib().pf_energy(ctx, C.c_void_p(state_ptr), C.byref(e), C.byref(m))
     return s, e.value, m.value
+
+
+def pf_energy2d_static(state_ptr, nx, ny, hx, hy, W, kappa, out_ptr, stream):
+    """Context-free energy/mass into a caller-owned device buffer of 2 doubles;
+    returns (status, message)."""
+    msg = C.c_char_p()
+    s = lib().pf_energy2d_static(C.c_void_p(state_ptr), nx, ny, hx, hy, W, kappa,
+                                 C.c_void_p(out_ptr), C.c_void_p(stream), C.byref(msg))
+    return s, (msg.value.decode() if msg.value else "")
 
 
 def pf_last_error(ctx) -> str:

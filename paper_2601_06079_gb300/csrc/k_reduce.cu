@@ -4,6 +4,8 @@
 // in FP64: warp shuffles, then shared memory, one partial per block, then a
 // single-block pass over the partials in a fixed order, so the result does
 // not depend on scheduling (no atomics).
+#include <math.h>
+
 #include "pf_internal.h"
 
 namespace pf {
@@ -107,3 +109,87 @@ cudaError_t launch_energy2d(const Energy2DArgs& a, double* partials, double* res
 }
 
 }  // namespace pf
+
+// ---------------------------------------------------------------------------
+// Energy / mass without a context or a workspace (pf_energy2d_static).
+//
+// Some callers cannot allocate device memory: a host that owns all device
+// memory through its own allocator and forbids foreign allocations, a process
+// that runs under a fixed device-memory budget, or a latency-critical path
+// where cudaMalloc / cudaFree would synchronise the whole device.  For them
+// the reduction's scratch -- one FP64 (energy, mass) pair per block of the
+// first pass -- sits in the static array below instead of a caller-bound
+// workspace.  Its size is fixed: kMaxBlocks pairs (16 KiB), which is every
+// block the first pass ever launches, so any mesh the kernel accepts fits.
+// Every GPU that loads libpf holds this array until the process exits.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace pf {
+namespace {
+
+static __device__ __align__(256) double g_static_partials[2 * kMaxBlocks];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mutex;
+double* g_static_ptr[kMaxDevices] = {};
+
+// Device address of g_static_partials for the current device, looked up once
+// per device (host code only knows the symbol as a host-side stand-in).
+cudaError_t static_partials(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_static_mutex);
+  if (!g_static_ptr[dev]) {
+    double* p = nullptr;
+    e = cudaGetSymbolAddress((void**)&p, g_static_partials);
+    if (e != cudaSuccess) return e;
+    g_static_ptr[dev] = p;
+  }
+  *out = g_static_ptr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace pf
+
+extern "C" pf_status pf_energy2d_static(const float* state, int64_t nx, int64_t ny, double hx,
+                                        double hy, double W, double kappa, double* out,
+                                        void* stream, const char** err) {
+  const char* msg = nullptr;
+  if (!state || !out) msg = "state and out must be non-null device pointers";
+  else if (nx < 2 || ny < 2) msg = "nx and ny must be >= 2";
+  else if (nx > INT32_MAX || ny > INT32_MAX || nx * ny > (int64_t)INT32_MAX)
+    msg = "mesh too large: nx * ny must be <= 2^31 - 1 nodes";
+  else if (!(hx > 0.0) || !(hy > 0.0) || !isfinite(hx) || !isfinite(hy))
+    msg = "hx and hy must be finite and > 0";
+  else if (!isfinite(W) || !isfinite(kappa)) msg = "W and kappa must be finite";
+  if (msg) {
+    if (err) *err = msg;
+    return PF_ERR_ARG;
+  }
+  double* partials = nullptr;
+  cudaError_t e = pf::static_partials(&partials);
+  if (e == cudaSuccess) {
+    pf::Energy2DArgs a{};
+    a.d = state;
+    a.nx = (int)nx;
+    a.ny = (int)ny;
+    a.hx = hx;
+    a.hy = hy;
+    a.shift = 0.0f;
+    a.q2 = (float)W;
+    a.q3 = (float)(-2 * W);
+    a.q4 = (float)W;
+    a.kappa = (float)kappa;
+    e = pf::launch_energy2d(a, partials, out, (cudaStream_t)stream);
+  }
+  if (e != cudaSuccess) {
+    if (err) *err = cudaGetErrorString(e);
+    return PF_ERR_CUDA;
+  }
+  if (err) *err = "";
+  return PF_OK;
+}
