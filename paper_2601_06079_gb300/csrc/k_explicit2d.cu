@@ -3,232 +3,410 @@
 // stencil -> lumped-mass Euler update (JAX-PF Eq. 11-12; Cahn-Hilliard via the
 // split form of Eq. 9-10).  One pass reads the state once and writes it once.
 //
-// Layout and work split.  A warp owns 128 consecutive columns (4 per lane,
-// one float4 per row) and sweeps down a band of rows, keeping a sliding
-// window of rows in registers.  Neighbouring columns come from the adjacent
-// lane by warp shuffle, so no shared memory and no block barrier is used and
-// every element is evaluated exactly once per warp.  Lanes 0 and 31 are halo
-// lanes (their outer columns lack a neighbour), so warps overlap by 8
-// columns and each writes the 120 columns of lanes 1..30.
+// Work split.  A warp owns 64 consecutive columns (a pair per lane) and
+// sweeps down a band of rows with a sliding window in registers; the
+// neighbouring columns come from the adjacent lanes by warp shuffle, so there
+// is no shared memory and no block barrier, and every element is evaluated
+// once per warp.  Lanes 0 and 31 are halo lanes (their outer column lacks a
+// neighbour), so warps overlap by 4 columns and each writes the 60 columns of
+// lanes 1..30.  All arithmetic is on packed FP32 pairs (one lane's two
+// columns) with the f32x2 instructions of sm_100+, which halve the issue slots
+// of the FP32 work.
 //
 // Quadrature is sum-factorised: per row, two x-interpolated values per
 // segment; per element, the four Gauss values from the segment values of its
 // two rows; the weights N_a(q) are applied back the same way (y first into
-// per-segment sums S, then x into the nodes).  The linear gradient term is
-// the exact assembled 9-point stencil of the Q1 stiffness (2x2 Gauss
-// integrates it exactly).  Zero-flux boundaries are the mirror extension
-// about the boundary nodes, which equals the partial element sets divided by
-// the partial lumped masses (both double when mirrored), so every node uses
-// the interior formula.
+// per-segment sums, then x into the nodes).  Interpolation uses
+// g_hi = 1 - g_lo, e.g. g_hi a + g_lo b = a + g_lo (b - a).  The linear
+// gradient term is the exact assembled 9-point Q1 stencil (2x2 Gauss
+// integrates it exactly); on square cells it is a v + b (sum of the 3x3 block).
+// Zero-flux boundaries are the mirror extension about the boundary nodes,
+// which equals the partial element sets divided by the partial lumped masses
+// (both double when mirrored), so every node uses the interior formula.  The
+// working planes carry that extension explicitly: a frame of 2 ghost rows and
+// columns that every step rewrites from the nodes it mirrors, so all warps run
+// the same branch-free sweep with no index reflection.
+#include <string.h>
+
 #include "pf_internal.h"
 
 namespace pf {
 namespace {
 
-constexpr int kCols = 4;                      // columns per lane
-constexpr int kOutCols = 32 * kCols - 2 * kCols;  // 120 output columns per warp
-constexpr int kWarps = 4;                     // warps per block, stacked in y
+typedef unsigned long long u64;  // packed FP32 pair: low half = lower column
+
+constexpr int kPair = 2;                          // columns per lane
+constexpr int kOutCols = 32 * kPair - 2 * kPair;  // 60 output columns per warp
+#ifndef PF_WARPS
+#define PF_WARPS 1
+#endif
+constexpr int kWarps = PF_WARPS;                  // warps per block, stacked in y
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kGhost = 2;  // mirror frame around the working planes
+#ifndef PF_ROWS_AHEAD
+#define PF_ROWS_AHEAD 3
+#endif
+constexpr int kAhead = PF_ROWS_AHEAD;  // rows loaded ahead of use (divides the unroll of 6)
 
-__device__ __forceinline__ int reflect(int k, int n) {
+__device__ __forceinline__ u64 pk(float lo, float hi) {
+  u64 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float plo(u64 v) {
+  float l, h;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(l), "=f"(h) : "l"(v));
+  return l;
+}
+__device__ __forceinline__ float phi(u64 v) {
+  float l, h;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(l), "=f"(h) : "l"(v));
+  return h;
+}
+__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
+  u64 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ u64 add2(u64 a, u64 b) {
+  u64 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ u64 sub2(u64 a, u64 b) {
+  u64 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ u64 mul2(u64 a, u64 b) {
+  u64 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ u64 bc(float v) { return pk(v, v); }
+
+__device__ __forceinline__ int reflect_row(int k, int n) {
+  k = k < 0 ? -k : k;
+  k = k >= n ? 2 * (n - 1) - k : k;
+  return k < 0 ? 0 : (k >= n ? n - 1 : k);  // rows this far out are never stored
+}
+
+__device__ __forceinline__ int reflect_col(int x, int n) {
   const int p = 2 * (n - 1);
-  k %= p;
-  if (k < 0) k += p;
-  return k < n ? k : p - k;
+  x %= p;
+  if (x < 0) x += p;
+  return x < n ? x : p - x;
 }
 
-__device__ __forceinline__ void load_row(const float* __restrict__ row, int x, int nx, bool vec,
-                                         float* v) {
-  if (vec && x >= 0 && x + 3 < nx) {
-    const float4 t = __ldg(reinterpret_cast<const float4*>(row + x));
-    v[0] = t.x;
-    v[1] = t.y;
-    v[2] = t.z;
-    v[3] = t.w;
+// f'(shift + d) / 4 (times the stage factor) as a cubic in d
+__device__ __forceinline__ u64 cubic2(u64 d, u64 p0, u64 p1, u64 p2, u64 p3) {
+  return fma2(fma2(fma2(p3, d, p2), d, p1), d, p0);
+}
+
+// Packed constants, read straight from the kernel parameter space.
+struct Coef {
+  const unsigned long long* c;
+  __device__ __forceinline__ u64 glo() const { return c[0]; }
+  __device__ __forceinline__ u64 ghi() const { return c[1]; }
+  __device__ __forceinline__ u64 nglo() const { return c[2]; }
+  __device__ __forceinline__ u64 p(int i) const { return c[3 + i]; }
+  __device__ __forceinline__ u64 k(int stage, int i) const { return c[7 + 6 * stage + i]; }
+};
+
+// Per-row stencil helper value: iso -> v + (v_W + v_E) (3-sum of the row);
+// general -> v_W + v_E.
+template <bool kIso>
+__device__ __forceinline__ u64 row_aux(u64 v, u64 hs) {
+  return kIso ? add2(v, hs) : hs;
+}
+
+// init + K v at the centre row (own values s/c/n, row helpers aux_s/aux_c/aux_n)
+template <bool kIso>
+__device__ __forceinline__ u64 stencil2(u64 init, u64 s, u64 c, u64 n, u64 aux_s, u64 aux_c,
+                                        u64 aux_n, u64 ka, u64 kb, u64 c0, u64 cx, u64 cy,
+                                        u64 cd) {
+  if (kIso) {
+    const u64 s9 = add2(add2(aux_s, aux_c), aux_n);
+    return fma2(kb, s9, fma2(ka, c, init));
   } else {
-#pragma unroll
-    for (int c = 0; c < 4; ++c) v[c] = __ldg(row + reflect(x + c, nx));
+    return fma2(cd, add2(aux_s, aux_n), fma2(cy, add2(s, n), fma2(cx, aux_c, fma2(c0, c, init))));
   }
 }
 
-__device__ __forceinline__ void store_row(float* __restrict__ row, int x, int nx, bool vec,
-                                          const float* v) {
-  if (vec && x + 3 < nx) {
-    *reinterpret_cast<float4*>(row + x) = make_float4(v[0], v[1], v[2], v[3]);
+// Sliding-window state of one lane (rows k-1, k-2, ...).
+struct Window {
+  u64 c1 = 0, c2 = 0, x1 = 0, x2 = 0;      // own values and row helpers, rows k-1, k-2
+  u64 am1 = 0, ap1 = 0;                    // x-interpolants of row k-1
+  u64 tl1 = 0, th1 = 0;                    // element row k-2 -> node row k-1
+  u64 mua = 0, mub = 0, mxa = 0, mxb = 0;  // CH: mu and helpers, rows k-3, k-2
+};
+
+// One row of the sweep: consume row k (P), advance the window, return the
+// finished output row (k-1 for AC, k-2 for CH).
+template <bool kCH, bool kIso>
+__device__ __forceinline__ u64 sweep_row(const u64 P, Window& w, const Coef& K) {
+  const float c0 = plo(P), c1v = phi(P);
+  const float cl = __shfl_up_sync(kFull, c1v, 1);   // column x-1
+  const float cr = __shfl_down_sync(kFull, c0, 1);  // column x+2
+  // horizontal neighbour sums and segment differences, formed as scalars so
+  // that no pair has to be re-packed from halves of other pairs
+  const u64 hs = pk(cl + c1v, c0 + cr);
+  const u64 dc = pk(c1v - c0, cr - c1v);
+  const u64 xr = row_aux<kIso>(P, hs);
+
+  // x-interpolation of row k on segments x, x+1 at xi = g_lo (am) and g_hi (ap)
+  const u64 am = fma2(K.glo(), dc, P);
+  const u64 ap = fma2(K.ghi(), dc, P);
+
+  // element row k-1: four Gauss values, f', weights back in y
+  const u64 dm = sub2(am, w.am1);
+  const u64 dp = sub2(ap, w.ap1);
+  const u64 fll = cubic2(fma2(K.glo(), dm, w.am1), K.p(0), K.p(1), K.p(2), K.p(3));
+  const u64 flh = cubic2(fma2(K.ghi(), dm, w.am1), K.p(0), K.p(1), K.p(2), K.p(3));
+  const u64 fhl = cubic2(fma2(K.glo(), dp, w.ap1), K.p(0), K.p(1), K.p(2), K.p(3));
+  const u64 fhh = cubic2(fma2(K.ghi(), dp, w.ap1), K.p(0), K.p(1), K.p(2), K.p(3));
+  const u64 dl = sub2(flh, fll);
+  const u64 dh = sub2(fhh, fhl);
+  const u64 sl = add2(fma2(K.glo(), dl, fll), w.tl1);  // node row k-1, xi = g_lo
+  const u64 sh = add2(fma2(K.glo(), dh, fhl), w.th1);  // node row k-1, xi = g_hi
+  const u64 tl = fma2(K.nglo(), dl, flh);              // node row k (next row)
+  const u64 th = fma2(K.nglo(), dh, fhh);
+  // weights back in x: segment s gives A to node s and B to node s+1
+  const u64 ds = sub2(sh, sl);
+  const u64 A = fma2(K.glo(), ds, sl);
+  const u64 B = fma2(K.nglo(), ds, sh);
+  const float bl = __shfl_up_sync(kFull, phi(B), 1);
+  const u64 F = pk(plo(A) + bl, phi(A) + plo(B));
+
+  u64 o;
+  if constexpr (!kCH) {
+    // u(k-1) <- u + F + K1 u   (coefficients carry -dt L / m)
+    o = stencil2<kIso>(add2(w.c1, F), w.c2, w.c1, P, w.x2, w.x1, xr, K.k(0, 0), K.k(0, 1), K.k(0, 2),
+                       K.k(0, 3), K.k(0, 4), K.k(0, 5));
   } else {
+    // mu(k-1) = F + K1 c ; then c(k-2) <- c + K2 mu   (K2 carries -dt M / m)
+    const u64 mu = stencil2<kIso>(F, w.c2, w.c1, P, w.x2, w.x1, xr, K.k(0, 0), K.k(0, 1), K.k(0, 2),
+                                  K.k(0, 3), K.k(0, 4), K.k(0, 5));
+    const float m0 = plo(mu), m1 = phi(mu);
+    const float ml = __shfl_up_sync(kFull, m1, 1);
+    const float mr = __shfl_down_sync(kFull, m0, 1);
+    const u64 mx = row_aux<kIso>(mu, pk(ml + m1, m0 + mr));
+    o = stencil2<kIso>(w.c2, w.mua, w.mub, mu, w.mxa, w.mxb, mx, K.k(1, 0), K.k(1, 1), K.k(1, 2), K.k(1, 3),
+                       K.k(1, 4), K.k(1, 5));
+    w.mua = w.mub;
+    w.mxa = w.mxb;
+    w.mub = mu;
+    w.mxb = mx;
+  }
+  w.c2 = w.c1;
+  w.x2 = w.x1;
+  w.c1 = P;
+  w.x1 = xr;
+  w.am1 = am;
+  w.ap1 = ap;
+  w.tl1 = tl;
+  w.th1 = th;
+  return o;
+}
+
+// Output of one finished pair: real row y, real columns x (lo) and x+1 (hi),
+// plus every ghost cell that mirrors it (rows -1, -2 <- 1, 2 and
+// ny, ny+1 <- ny-2, ny-3; the same for columns), so the next step reads the
+// mirror extension without any index reflection.
+__device__ __forceinline__ void store_cols(float* __restrict__ row, int x, int nx, u64 v) {
+  const float lo = plo(v), hi = phi(v);
+  if (x + 1 < nx) {
+    *reinterpret_cast<u64*>(row + x) = v;
+  } else {
+    row[x] = lo;
+  }
 #pragma unroll
-    for (int c = 0; c < 4; ++c)
-      if (x + c < nx) row[x + c] = v[c];
+  for (int h = 0; h < 2; ++h) {
+    const int xc = x + h;
+    const float val = h ? hi : lo;
+    if (xc >= nx) break;
+    if (xc == 1 || xc == 2) row[-xc] = val;
+    if (xc == nx - 2 || xc == nx - 3) row[2 * (nx - 1) - xc] = val;
   }
 }
 
-__device__ __forceinline__ float cubic(float d, float p0, float p1, float p2, float p3) {
-  return fmaf(fmaf(fmaf(p3, d, p2), d, p1), d, p0);
+__device__ __forceinline__ void store_out(float* __restrict__ base0, int64_t pitch, int y, int ny,
+                                          int x, int nx, u64 v) {
+  store_cols(base0 + (int64_t)y * pitch, x, nx, v);
+  if (y == 1 || y == 2) store_cols(base0 - (int64_t)y * pitch, x, nx, v);
+  if ((y == ny - 2 || y == ny - 3) && y >= 0)
+    store_cols(base0 + (int64_t)(2 * (ny - 1) - y) * pitch, x, nx, v);
 }
 
-// Stencil at one column from three rows (own values and horizontal-neighbour sums).
-__device__ __forceinline__ float stencil(const Stencil2D& k, float s_own, float s_hs, float c_own,
-                                         float c_hs, float n_own, float n_hs) {
-  return fmaf(k.cd, s_hs + n_hs, fmaf(k.cy, s_own + n_own, fmaf(k.cx, c_hs, k.c0 * c_own)));
-}
-
-// Horizontal neighbour sums of a row segment (own 4 values + lane neighbours).
-__device__ __forceinline__ void hsum(const float* v, float left, float right, float* hs) {
-  hs[0] = left + v[1];
-  hs[1] = v[0] + v[2];
-  hs[2] = v[1] + v[3];
-  hs[3] = v[2] + right;
-}
-
-template <bool kCH, int kTY>
-__global__ void __launch_bounds__(kWarps * 32) k_explicit2d(const Explicit2DArgs a) {
-  const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
-  const int x = blockIdx.x * kOutCols - kCols + kCols * lane;
-  const int y0 = (blockIdx.y * kWarps + warp) * kTY;
-  if (y0 >= a.ny) return;  // warp-uniform
-  const bool vec = a.vec_ok != 0;
-  const int nx = a.nx, ny = a.ny;
+// One warp task: the band of kTY output rows starting at y0, columns of
+// warp column bx.
+template <bool kCH, bool kIso, int kTY>
+__device__ __forceinline__ void sweep_task(const Explicit2DArgs& a, int bx, int y0) {
   constexpr int kLag = kCH ? 2 : 1;
-  constexpr int kIters = kTY + 2 * kLag;
-
-  // sliding window (row k-1 = "1", row k-2 = "2")
-  float c1[4] = {0, 0, 0, 0}, h1[4] = {0, 0, 0, 0};
-  float c2[4] = {0, 0, 0, 0}, h2[4] = {0, 0, 0, 0};
-  float am1[4] = {0, 0, 0, 0}, ap1[4] = {0, 0, 0, 0};  // x-interp of row k-1
-  float tl1[4] = {0, 0, 0, 0}, th1[4] = {0, 0, 0, 0};  // element row k-2 -> node row k-1
-  float mua[4] = {0, 0, 0, 0}, mha[4] = {0, 0, 0, 0};  // CH: mu row k-3
-  float mub[4] = {0, 0, 0, 0}, mhb[4] = {0, 0, 0, 0};  // CH: mu row k-2
-
-  float nxt[4];
-  load_row(a.in + (int64_t)reflect(y0 - kLag, ny) * nx, x, nx, vec, nxt);
-
-#pragma unroll 1
-  for (int it = 0; it < kIters; ++it) {
-    const int k = y0 - kLag + it;
-    float c[4];
+  constexpr int kWarm = 2 * kLag;  // rows consumed before the first finished row
+  const int lane = threadIdx.x & 31;
+  const int nx = a.nx, ny = a.ny;
+  const int64_t pitch = a.pitch;
+  const int x = bx * kOutCols - kPair + kPair * lane;  // real column of lo
+  const bool writer = lane >= 1 && lane <= 30 && x < nx;
+  // plain vector store unless this lane / band also owns mirror-frame cells
+  const bool ghost_cols = x <= 2 || x + 1 >= nx - 3;
+  const bool ghost_rows = y0 <= 2 || y0 + kTY + 3 >= ny;
+  const bool plain = writer && !ghost_cols && !ghost_rows;
+  // origin of the real mesh inside the ghost-padded planes
+  const float* __restrict__ in0 = a.in + kGhost * pitch + kGhost;
+  float* __restrict__ out0 = a.out + kGhost * pitch + kGhost;
+  const float* src = in0 + (int64_t)(y0 - kLag) * pitch + x;
+  const Coef K{a.pair};
+  Window w;
+  u64 ahead[kAhead];  // rows k .. k+kAhead-1 in flight
 #pragma unroll
-    for (int v = 0; v < 4; ++v) c[v] = nxt[v];
-    load_row(a.in + (int64_t)reflect(k + 1, ny) * nx, x, nx, vec, nxt);  // prefetch row k+1
-
-    const float cl = __shfl_up_sync(kFull, c[3], 1);
-    const float cr = __shfl_down_sync(kFull, c[0], 1);
-    float hs[4];
-    hsum(c, cl, cr, hs);
-
-    // x-interpolation of row k on segments x+s .. x+s+1 at xi = g_lo (am), g_hi (ap)
-    float am[4], ap[4];
+  for (int j = 0; j < kAhead; ++j) {
+    ahead[j] = __ldg(reinterpret_cast<const u64*>(src));
+    src += pitch;
+  }
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      const float right = (s < 3) ? c[s + 1] : cr;
-      am[s] = fmaf(kGHi, c[s], kGLo * right);
-      ap[s] = fmaf(kGLo, c[s], kGHi * right);
-    }
-
-    // element row k-1 (node rows k-1 .. k): Gauss values, f', weights back in y
-    float sl[4], sh[4], tl[4], th[4];
+  for (int it = 0; it < kWarm; ++it) {  // fill the window, nothing to store yet
+    const u64 P = ahead[0];
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      const float qll = fmaf(kGHi, am1[s], kGLo * am[s]);
-      const float qlh = fmaf(kGLo, am1[s], kGHi * am[s]);
-      const float qhl = fmaf(kGHi, ap1[s], kGLo * ap[s]);
-      const float qhh = fmaf(kGLo, ap1[s], kGHi * ap[s]);
-      const float fll = cubic(qll, a.p0, a.p1, a.p2, a.p3);
-      const float flh = cubic(qlh, a.p0, a.p1, a.p2, a.p3);
-      const float fhl = cubic(qhl, a.p0, a.p1, a.p2, a.p3);
-      const float fhh = cubic(qhh, a.p0, a.p1, a.p2, a.p3);
-      sl[s] = fmaf(kGHi, fll, fmaf(kGLo, flh, tl1[s]));  // + element row k-2's top share
-      sh[s] = fmaf(kGHi, fhl, fmaf(kGLo, fhh, th1[s]));
-      tl[s] = fmaf(kGLo, fll, kGHi * flh);
-      th[s] = fmaf(kGLo, fhl, kGHi * fhh);
-    }
-    // weights back in x: node x+v gets segment x+v (left end) and x+v-1 (right end)
-    const float sl_l = __shfl_up_sync(kFull, sl[3], 1);
-    const float sh_l = __shfl_up_sync(kFull, sh[3], 1);
-    float F[4];
+    for (int j = 0; j + 1 < kAhead; ++j) ahead[j] = ahead[j + 1];
+    ahead[kAhead - 1] = __ldg(reinterpret_cast<const u64*>(src));
+    src += pitch;
+    sweep_row<kCH, kIso>(P, w, K);
+  }
+#pragma unroll 6
+  for (int it = 0; it < kTY; ++it) {
+    const u64 P = ahead[0];
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const float pl = (v == 0) ? sl_l : sl[v - 1];
-      const float ph = (v == 0) ? sh_l : sh[v - 1];
-      F[v] = fmaf(kGHi, sl[v], fmaf(kGLo, sh[v], fmaf(kGLo, pl, kGHi * ph)));
-    }
-
-    if constexpr (!kCH) {
-      // u(k-1) <- u + F + K1 u   (coefficients carry -dt L / m)
-      float o[4];
-#pragma unroll
-      for (int v = 0; v < 4; ++v)
-        o[v] = c1[v] + F[v] + stencil(a.k1, c2[v], h2[v], c1[v], h1[v], c[v], hs[v]);
-      const int row = k - 1;
-      if (row >= y0 && row < y0 + kTY && row < ny && lane >= 1 && lane <= 30)
-        store_row(a.out + (int64_t)row * nx, x, nx, vec, o);
-    } else {
-      // mu(k-1) = F + K1 c ; then c(k-2) <- c + K2 mu  (K2 carries -dt M / m)
-      float mu[4], mh[4];
-#pragma unroll
-      for (int v = 0; v < 4; ++v)
-        mu[v] = F[v] + stencil(a.k1, c2[v], h2[v], c1[v], h1[v], c[v], hs[v]);
-      const float ml = __shfl_up_sync(kFull, mu[3], 1);
-      const float mr = __shfl_down_sync(kFull, mu[0], 1);
-      hsum(mu, ml, mr, mh);
-      float o[4];
-#pragma unroll
-      for (int v = 0; v < 4; ++v)
-        o[v] = c2[v] + stencil(a.k2, mua[v], mha[v], mub[v], mhb[v], mu[v], mh[v]);
-      const int row = k - 2;
-      if (row >= y0 && row < y0 + kTY && row < ny && lane >= 1 && lane <= 30)
-        store_row(a.out + (int64_t)row * nx, x, nx, vec, o);
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        mua[v] = mub[v];
-        mha[v] = mhb[v];
-        mub[v] = mu[v];
-        mhb[v] = mh[v];
-      }
-    }
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      c2[v] = c1[v];
-      h2[v] = h1[v];
-      c1[v] = c[v];
-      h1[v] = hs[v];
-      am1[v] = am[v];
-      ap1[v] = ap[v];
-      tl1[v] = tl[v];
-      th1[v] = th[v];
-    }
+    for (int j = 0; j + 1 < kAhead; ++j) ahead[j] = ahead[j + 1];
+    ahead[kAhead - 1] = __ldg(reinterpret_cast<const u64*>(src));
+    src += pitch;
+    const u64 o = sweep_row<kCH, kIso>(P, w, K);
+    const int y = y0 + it;
+    if (plain)
+      *reinterpret_cast<u64*>(out0 + (int64_t)y * pitch + x) = o;
+    else if (writer && y < ny)
+      store_out(out0, pitch, y, ny, x, nx, o);
   }
 }
 
-__global__ void k_shift(const float* __restrict__ in, float* __restrict__ out, int64_t n,
-                        float add) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-    out[i] = in[i] + add;
+// One warp per block and one (column, band) task per warp: many small blocks
+// spread evenly over the SMs and keep each scheduler fed from several warps.
+template <bool kCH, bool kIso, int kTY>
+__global__ void __launch_bounds__(kWarps * 32) k_explicit2d(const Explicit2DArgs a) {
+  const int warp = threadIdx.x >> 5;
+  const int y0 = (blockIdx.y * kWarps + warp) * kTY;
+  if (y0 < a.ny) sweep_task<kCH, kIso, kTY>(a, blockIdx.x, y0);
 }
 
-constexpr int kTYAc = 32;
-constexpr int kTYCh = 32;
+// Plain <-> padded working layout.  Working cell (u, v) holds real node
+// (reflect(u - kGhost), reflect(v - kGhost)) minus/plus the shift; padding
+// beyond the ghost frame is zero.
+__global__ void k_to_work(const float* __restrict__ in, float* __restrict__ work, int nx, int ny,
+                          int64_t pitch, int rows, float sub) {
+  const int64_t n = pitch * rows;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int u = (int)(i % pitch), v = (int)(i / pitch);
+    const int x = u - kGhost, y = v - kGhost;
+    float val = 0.0f;
+    if (x >= -kGhost && x < nx + kGhost && y >= -kGhost && y < ny + kGhost)
+      val = in[(int64_t)reflect_row(y, ny) * nx + reflect_col(x, nx)] - sub;
+    work[i] = val;
+  }
+}
+
+__global__ void k_from_work(const float* __restrict__ work, float* __restrict__ out, int nx,
+                            int ny, int64_t pitch, float add) {
+  const int64_t n = (int64_t)nx * ny;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int x = (int)(i % nx), y = (int)(i / nx);
+    out[i] = work[(int64_t)(y + kGhost) * pitch + x + kGhost] + add;
+  }
+}
+
+#ifndef PF_TY_CH
+#define PF_TY_CH 12
+#endif
+#ifndef PF_TY_AC
+#define PF_TY_AC 12
+#endif
+constexpr int kTYAc = PF_TY_AC;  // output rows per warp band (a multiple of the unroll of 6)
+constexpr int kTYCh = PF_TY_CH;
+
+template <bool kCH, bool kIso, int kTY>
+cudaError_t launch(const Explicit2DArgs& a, cudaStream_t s) {
+  const dim3 grid((a.nx + kOutCols - 1) / kOutCols, (a.ny + kWarps * kTY - 1) / (kWarps * kTY));
+  k_explicit2d<kCH, kIso, kTY><<<grid, kWarps * 32, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+bool is_iso(const Stencil2D& k) { return k.cx == k.cd && k.cy == k.cd; }
 
 }  // namespace
 
 cudaError_t launch_ac2d(const Explicit2DArgs& a, cudaStream_t s) {
-  const dim3 grid((a.nx + kOutCols - 1) / kOutCols, (a.ny + kWarps * kTYAc - 1) / (kWarps * kTYAc));
-  k_explicit2d<false, kTYAc><<<grid, kWarps * 32, 0, s>>>(a);
-  return cudaGetLastError();
+  return is_iso(a.k1) ? launch<false, true, kTYAc>(a, s) : launch<false, false, kTYAc>(a, s);
 }
 
 cudaError_t launch_ch2d(const Explicit2DArgs& a, cudaStream_t s) {
-  const dim3 grid((a.nx + kOutCols - 1) / kOutCols, (a.ny + kWarps * kTYCh - 1) / (kWarps * kTYCh));
-  k_explicit2d<true, kTYCh><<<grid, kWarps * 32, 0, s>>>(a);
+  return (is_iso(a.k1) && is_iso(a.k2)) ? launch<true, true, kTYCh>(a, s)
+                                        : launch<true, false, kTYCh>(a, s);
+}
+
+void pack_explicit2d(Explicit2DArgs& a) {
+  auto pk_host = [](float v) {
+    unsigned int b;
+    memcpy(&b, &v, 4);
+    return (unsigned long long)b | ((unsigned long long)b << 32);
+  };
+  a.pair[0] = pk_host(kGLo);
+  a.pair[1] = pk_host(kGHi);
+  a.pair[2] = pk_host(-kGLo);
+  a.pair[3] = pk_host(a.p0);
+  a.pair[4] = pk_host(a.p1);
+  a.pair[5] = pk_host(a.p2);
+  a.pair[6] = pk_host(a.p3);
+  const Stencil2D* st[2] = {&a.k1, &a.k2};
+  for (int s = 0; s < 2; ++s) {
+    a.pair[7 + 6 * s + 0] = pk_host(st[s]->c0 - st[s]->cd);
+    a.pair[7 + 6 * s + 1] = pk_host(st[s]->cd);
+    a.pair[7 + 6 * s + 2] = pk_host(st[s]->c0);
+    a.pair[7 + 6 * s + 3] = pk_host(st[s]->cx);
+    a.pair[7 + 6 * s + 4] = pk_host(st[s]->cy);
+    a.pair[7 + 6 * s + 5] = pk_host(st[s]->cd);
+  }
+}
+
+int work_pitch(int nx) {
+  const int gx = (nx + kOutCols - 1) / kOutCols;
+  const int p = gx * kOutCols + 2 * kGhost + 2 * kPair;
+  return (p + 3) / 4 * 4;
+}
+
+int work_rows(int ny) {
+  // the last band reads up to kTY + kLag + kAhead rows past its first row
+  const int ty = kTYAc > kTYCh ? kTYAc : kTYCh;
+  return ny + ty + kAhead + 2 * kGhost + 4;
+}
+
+cudaError_t launch_to_work(const float* in, float* work, int nx, int ny, float shift,
+                           cudaStream_t s) {
+  const int64_t n = (int64_t)work_pitch(nx) * work_rows(ny);
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_to_work<<<(unsigned)blocks, 256, 0, s>>>(in, work, nx, ny, work_pitch(nx), work_rows(ny),
+                                             shift);
   return cudaGetLastError();
 }
 
-cudaError_t launch_shift(const float* in, float* out, int64_t n, float add, cudaStream_t s) {
-  if (n == 0) return cudaSuccess;
+cudaError_t launch_from_work(const float* work, float* out, int nx, int ny, float shift,
+                             cudaStream_t s) {
+  const int64_t n = (int64_t)nx * ny;
   int64_t blocks = (n + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  k_shift<<<(unsigned)blocks, 256, 0, s>>>(in, out, n, add);
+  k_from_work<<<(unsigned)blocks, 256, 0, s>>>(work, out, nx, ny, work_pitch(nx), shift);
   return cudaGetLastError();
 }
 

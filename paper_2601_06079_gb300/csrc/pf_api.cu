@@ -76,7 +76,8 @@ struct Layout {
 
 Layout layout(const pf_ctx* c) {
   Layout L{};
-  const size_t field = align_up(sizeof(float) * (size_t)nnodes(c) * c->nf, 256);
+  const size_t field =
+      align_up(sizeof(float) * (size_t)pf::work_pitch((int)c->n[0]) * pf::work_rows((int)c->n[1]), 256);
   size_t off = 0;
   L.a = off;
   off += field;
@@ -110,7 +111,7 @@ cudaError_t launch_step(pf_ctx* c, const float* in, float* out, cudaStream_t s) 
   pf::Explicit2DArgs a = c->ex;
   a.in = in;
   a.out = out;
-  a.vec_ok = (c->n[0] % 4 == 0) && ((uintptr_t)in % 16 == 0) && ((uintptr_t)out % 16 == 0);
+  a.pitch = pf::work_pitch((int)c->n[0]);
   return c->model == PF_MODEL_CH ? pf::launch_ch2d(a, s) : pf::launch_ac2d(a, s);
 }
 
@@ -223,6 +224,7 @@ pf_status pf_set_params(pf_ctx* c, const pf_params* p) {
     a.k1 = stiffness2d(hx, hy, p->kappa / m);
     a.k2 = stiffness2d(hx, hy, -p->dt * p->mobility / m);
   }
+  pf::pack_explicit2d(a);
   destroy_graph(c);
   return PF_OK;
 }
@@ -234,9 +236,11 @@ pf_status pf_step_explicit(pf_ctx* c, float* state, int64_t n_steps) {
   if (!state) return fail(c, PF_ERR_ARG, "state is NULL");
   if (n_steps < 0) return fail(c, PF_ERR_ARG, "n_steps < 0");
   if (n_steps == 0) return PF_OK;
-  const int64_t N = nnodes(c) * c->nf;
   const float shift = (float)c->par.shift;
-  PF_CUDA(pf::launch_shift(state, c->buf_a, N, -shift, c->stream));
+  const int nx = (int)c->n[0], ny = (int)c->n[1];
+  // working copies with the mirror frame: d = u - shift (both planes fully defined)
+  PF_CUDA(pf::launch_to_work(state, c->buf_a, nx, ny, shift, c->stream));
+  PF_CUDA(pf::launch_to_work(state, c->buf_b, nx, ny, shift, c->stream));
   int64_t left = n_steps;
   if (left >= kGraphSteps) {
     pf_status st = ensure_graph(c);
@@ -251,7 +255,7 @@ pf_status pf_step_explicit(pf_ctx* c, float* state, int64_t n_steps) {
     cur = oth;
     oth = t;
   }
-  PF_CUDA(pf::launch_shift(cur, state, N, shift, c->stream));
+  PF_CUDA(pf::launch_from_work(cur, state, nx, ny, shift, c->stream));
   return PF_OK;
 }
 

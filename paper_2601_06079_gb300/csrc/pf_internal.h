@@ -29,16 +29,27 @@ struct Explicit2DArgs {
   const float* in;
   float* out;
   int nx, ny;
+  int64_t pitch;  // row pitch of the ghost-padded working planes (floats)
   // f'(shift + d) / 4 as p0 + d (p1 + d (p2 + d p3)), times the stage factor
   float p0, p1, p2, p3;
   Stencil2D k1;  // AC: -dt L kappa / m * K;   CH: kappa / m * K  (mu stage)
   Stencil2D k2;  // CH: -dt M / m * K          (c stage)
-  int vec_ok;    // rows 16-byte aligned: nx % 4 == 0 and 16-byte aligned base pointers
+  // the same constants duplicated into FP32 pairs for the packed f32x2 path
+  // (filled by pack_explicit2d): g_lo, g_hi, -g_lo, p0..p3, then per stencil
+  // a = c0 - cd, b = cd, c0, cx, cy, cd
+  unsigned long long pair[7 + 12];
 };
+void pack_explicit2d(Explicit2DArgs& a);
 
 cudaError_t launch_ac2d(const Explicit2DArgs& a, cudaStream_t s);
 cudaError_t launch_ch2d(const Explicit2DArgs& a, cudaStream_t s);
-cudaError_t launch_shift(const float* in, float* out, int64_t n, float add, cudaStream_t s);
+// Ghost-padded working planes: work_pitch(nx) x work_rows(ny) floats each.
+int work_pitch(int nx);
+int work_rows(int ny);
+cudaError_t launch_to_work(const float* in, float* work, int nx, int ny, float shift,
+                           cudaStream_t s);
+cudaError_t launch_from_work(const float* work, float* out, int nx, int ny, float shift,
+                             cudaStream_t s);
 
 // Energy / mass diagnostics (Eq. 5-6), FP64 accumulation, deterministic.
 struct Energy2DArgs {
