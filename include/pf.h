@@ -73,8 +73,26 @@ typedef struct {
                                   Must stay valid while the context uses it. */
 } pf_params;
 
+/* Newton-Krylov controls for the implicit step (Eq. 13-14).  NULL = defaults. */
+typedef struct {
+  int max_newton;       /* Newton corrections per time step (default 20) */
+  int gmres_restart;    /* GMRES restart length m, 1..31 (default 30) */
+  int gmres_max_iters;  /* GMRES iterations per Newton correction (default 300) */
+  double newton_rtol;   /* stop when ||R||_2 <= newton_rtol * ||M U^n / dt||_2 (default 1e-5) */
+  double gmres_rtol;    /* inexact-Newton forcing: ||r_gmres|| <= gmres_rtol ||G|| (default 1e-3) */
+} pf_newton_opts;
+
+typedef struct {
+  int newton_iters;         /* Newton corrections, summed over the call's steps */
+  int gmres_iters;          /* GMRES iterations, summed */
+  int converged;            /* 1 if every step met the Newton tolerance */
+  double initial_residual;  /* ||R(U_0)||_2 of the first step's initial guess */
+  double final_residual;    /* ||R||_2 at the end of the last step */
+} pf_newton_stats;
+
 /* Create a solver context for a uniform Q1 mesh.
- *   dim              2 (AC, CH) or 3 (FANCHEN)
+ *   dim              2 (AC, CH: explicit steps, energy) or 3 (AC with one field or
+ *                    FANCHEN: explicit and implicit steps, JVP, residual)
  *   nodes[3]         nodes per axis (x, y, z); nodes[2] ignored in 2-D; each >= 2
  *                    (>= 3 along every axis for CH)
  *   h[3]             node spacing per axis (> 0)
@@ -95,13 +113,35 @@ pf_status pf_set_params(pf_ctx* ctx, const pf_params* p);
 
 /* Advance `state` (device, n_fields * N FP32, in/out) by n_steps >= 0 explicit
  * Euler steps with the lumped mass, Eq. 12: AC U <- U - dt L r(U)/m;
- * CH c <- c - dt K_M mu / m with m mu = r(c).  Enqueues only. */
+ * CH c <- c - dt K_M mu / m with m mu = r(c).  2-D: one fused kernel per step;
+ * 3-D: residual kernel then update.  Enqueues only. */
 pf_status pf_step_explicit(pf_ctx* ctx, float* state, int64_t n_steps);
+
+/* Advance `state` (device, 3-D, in/out) by n_steps backward-Euler steps, Eq. 13:
+ * each step solves R(U) = M (U - U^n)/dt + L r(U) = 0 (Eq. 14) by Newton, each
+ * correction by restarted GMRES(m) on the Jacobian-vector product (matrix-free;
+ * Krylov vectors FP32, inner products FP64, CGS2 orthogonalisation).
+ * guess: device initial Newton iterate for the FIRST step (NULL = U^n); later
+ * steps start from their U^n.  opts may be NULL (defaults); stats (host) may be
+ * NULL.  Synchronises the stream.  PF_ERR_NOT_CONVERGED: state holds the last
+ * iterate and stats the counts so far. */
+pf_status pf_step_implicit(pf_ctx* ctx, float* state, int64_t n_steps, const float* guess,
+                           const pf_newton_opts* opts, pf_newton_stats* stats);
+
+/* Jacobian-vector product of Eq. 14 (3-D): Jv = M v / dt + L (F''(U) v + kappa K v),
+ * with F''(U) v = sum_e sum_q w|J| H_f(U_q) v_q N_i (the Hessian of the local
+ * energy) and K the Q1 stiffness.  U, v, Jv: device, n_fields * N FP32.
+ * Enqueues only. */
+pf_status pf_jvp(pf_ctx* ctx, const float* U, const float* v, float* Jv);
+
+/* Implicit residual of Eq. 14 (3-D): R = M (U - Un) / dt + L r(U).  Device arrays,
+ * n_fields * N FP32.  Enqueues only. */
+pf_status pf_implicit_residual(pf_ctx* ctx, const float* Un, const float* U, float* R);
 
 /* Discrete free energy E_h = sum_e sum_q w_q |J| [f(U_q) + kappa/2 |grad U_q|^2]
  * (Eq. 5-6) and, per field, the mass integral sum_i m_i U_i, accumulated in FP64.
  * energy: host, 1 double; mass: host, n_fields doubles (either may be NULL).
- * Synchronises the stream. */
+ * 2-D meshes.  Synchronises the stream. */
 pf_status pf_energy(pf_ctx* ctx, const float* state, double* energy, double* mass);
 
 /* Energy and mass of a 2-D single-field double-well state (AC or CH) without a

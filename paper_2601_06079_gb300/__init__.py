@@ -15,8 +15,9 @@ import torch
 
 from . import _lib
 from ._lib import (PF_MODEL_AC, PF_MODEL_CH, PF_MODEL_FANCHEN, pf_bind_workspace,  # noqa: F401
-                   pf_create_mesh, pf_destroy, pf_energy, pf_last_error, pf_set_params,
-                   pf_step_explicit)
+                   pf_create_mesh, pf_destroy, pf_energy, pf_energy2d_static,
+                   pf_implicit_residual, pf_jvp, pf_last_error, pf_set_params, pf_step_explicit,
+                   pf_step_implicit)
 
 _MODELS = {"ac": PF_MODEL_AC, "ch": PF_MODEL_CH, "fanchen": PF_MODEL_FANCHEN}
 
@@ -83,6 +84,33 @@ class Solver:
         """Advance `state` in place by n_steps explicit Euler steps (Eq. 12)."""
         self._check(pf_step_explicit(self._ctx, self._state(state), n_steps))
         return state
+
+    def step_implicit(self, state, n_steps=1, guess=None, max_newton=20, gmres_restart=30,
+                      gmres_max_iters=300, newton_rtol=1e-5, gmres_rtol=1e-3, check=True):
+        """Backward-Euler steps (Eq. 13-14) by Newton-GMRES; returns the stats dict."""
+        opts = _lib.pf_newton_opts(max_newton, gmres_restart, gmres_max_iters, newton_rtol,
+                                   gmres_rtol)
+        stats = _lib.pf_newton_stats()
+        gp = self._state(guess) if guess is not None else 0
+        st = pf_step_implicit(self._ctx, self._state(state), n_steps, gp, opts, stats)
+        out = {k: getattr(stats, k) for k, _ in _lib.pf_newton_stats._fields_}
+        if check:
+            self._check(st)
+        out["status"] = st
+        return out
+
+    def jvp(self, U, v, out=None):
+        """J v of Eq. 14 (unscaled: includes the lumped mass)."""
+        out = torch.empty_like(v) if out is None else out
+        self._check(pf_jvp(self._ctx, self._state(U), self._state(v), self._state(out)))
+        return out
+
+    def implicit_residual(self, Un, U, out=None):
+        """R = M (U - Un)/dt + L r(U) of Eq. 14."""
+        out = torch.empty_like(U) if out is None else out
+        self._check(pf_implicit_residual(self._ctx, self._state(Un), self._state(U),
+                                         self._state(out)))
+        return out
 
     def energy(self, state):
         """(E_h, mass integral) in FP64 (Eq. 5-6); synchronises the stream."""

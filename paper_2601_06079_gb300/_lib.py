@@ -35,6 +35,16 @@ class pf_params(C.Structure):
                 ("mobility_field", C.c_void_p)]
 
 
+class pf_newton_opts(C.Structure):
+    _fields_ = [("max_newton", C.c_int), ("gmres_restart", C.c_int), ("gmres_max_iters", C.c_int),
+                ("newton_rtol", C.c_double), ("gmres_rtol", C.c_double)]
+
+
+class pf_newton_stats(C.Structure):
+    _fields_ = [("newton_iters", C.c_int), ("gmres_iters", C.c_int), ("converged", C.c_int),
+                ("initial_residual", C.c_double), ("final_residual", C.c_double)]
+
+
 _LIB = None
 
 
@@ -63,6 +73,13 @@ def lib():
         L.pf_set_params.argtypes = [ctx, C.POINTER(pf_params)]
         L.pf_step_explicit.restype = st
         L.pf_step_explicit.argtypes = [ctx, C.c_void_p, C.c_int64]
+        L.pf_step_implicit.restype = st
+        L.pf_step_implicit.argtypes = [ctx, C.c_void_p, C.c_int64, C.c_void_p,
+                                       C.POINTER(pf_newton_opts), C.POINTER(pf_newton_stats)]
+        L.pf_jvp.restype = st
+        L.pf_jvp.argtypes = [ctx, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.pf_implicit_residual.restype = st
+        L.pf_implicit_residual.argtypes = [ctx, C.c_void_p, C.c_void_p, C.c_void_p]
         L.pf_energy.restype = st
         L.pf_energy.argtypes = [ctx, C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.pf_energy2d_static.restype = st
@@ -80,7 +97,8 @@ def lib():
 def exported_symbols():
     """Names declared in include/pf.h (checked against the .so by the tests)."""
     return ["pf_create_mesh", "pf_bind_workspace", "pf_set_params", "pf_step_explicit",
-            "pf_energy", "pf_energy2d_static", "pf_last_error", "pf_destroy"]
+            "pf_step_implicit", "pf_jvp", "pf_implicit_residual", "pf_energy",
+            "pf_energy2d_static", "pf_last_error", "pf_destroy"]
 
 
 # --- thin same-name wrappers -------------------------------------------------
@@ -105,6 +123,22 @@ def pf_set_params(ctx, params: pf_params):
 
 def pf_step_explicit(ctx, state_ptr, n_steps):
     return lib().pf_step_explicit(ctx, C.c_void_p(state_ptr), int(n_steps))
+
+
+def pf_step_implicit(ctx, state_ptr, n_steps, guess_ptr, opts, stats):
+    return lib().pf_step_implicit(ctx, C.c_void_p(state_ptr), int(n_steps),
+                                  C.c_void_p(guess_ptr) if guess_ptr else None,
+                                  C.byref(opts) if opts is not None else None,
+                                  C.byref(stats) if stats is not None else None)
+
+
+def pf_jvp(ctx, U_ptr, v_ptr, out_ptr):
+    return lib().pf_jvp(ctx, C.c_void_p(U_ptr), C.c_void_p(v_ptr), C.c_void_p(out_ptr))
+
+
+def pf_implicit_residual(ctx, Un_ptr, U_ptr, out_ptr):
+    return lib().pf_implicit_residual(ctx, C.c_void_p(Un_ptr), C.c_void_p(U_ptr),
+                                      C.c_void_p(out_ptr))
 
 
 def pf_energy(ctx, state_ptr):

@@ -6,7 +6,10 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
+#include <cmath>
 #include <new>
+#include <vector>
 #include <string>
 
 #include "pf_internal.h"
@@ -32,6 +35,16 @@ struct pf_ctx {
 
   // derived coefficients
   pf::Explicit2DArgs ex{};
+  pf::Implicit3DArgs im{};
+
+  // 3-D workspace segments (each n_fields * N floats)
+  float* u = nullptr;   // current iterate / state
+  float* un = nullptr;  // U^n
+  float* g = nullptr;   // scaled residual M^-1 R
+  float* d = nullptr;   // Newton correction
+  float* basis = nullptr;  // kMaxBasis Krylov vectors
+  int64_t ldv = 0;         // floats between consecutive Krylov vectors
+  double* small = nullptr; // h1[32], h2[32], scalars
 
   // CUDA graph of kGraphSteps explicit steps buf_a -> ... -> buf_a
   cudaStream_t cap_stream = nullptr;
@@ -71,22 +84,33 @@ pf_status cuda_fail(pf_ctx* c, cudaError_t e, const char* where) {
   } while (0)
 
 struct Layout {
-  size_t a, b, partials, result, total;
+  size_t a, b, partials, result, vec, vecs, small, total;
 };
+
+constexpr int kVec3d = 4;  // U, U^n, G, D before the Krylov basis
 
 Layout layout(const pf_ctx* c) {
   Layout L{};
-  const size_t field =
-      align_up(sizeof(float) * (size_t)pf::work_pitch((int)c->n[0]) * pf::work_rows((int)c->n[1]), 256);
   size_t off = 0;
-  L.a = off;
-  off += field;
-  L.b = off;
-  off += field;
+  if (c->dim == 2) {
+    const size_t field = align_up(
+        sizeof(float) * (size_t)pf::work_pitch((int)c->n[0]) * pf::work_rows((int)c->n[1]), 256);
+    L.a = off;
+    off += field;
+    L.b = off;
+    off += field;
+  } else {
+    L.vec = align_up(sizeof(float) * (size_t)nnodes(c) * c->nf, 256);
+    L.vecs = off;
+    off += L.vec * (kVec3d + pf::kMaxBasis);
+  }
   L.partials = off;
-  off += align_up(sizeof(double) * 2 * 1024, 256);
+  const size_t np = (size_t)std::max(2 * 1024, pf::krylov_partial_blocks() * pf::kMaxBasis);
+  off += align_up(sizeof(double) * np, 256);
   L.result = off;
   off += 256;
+  L.small = off;
+  off += align_up(sizeof(double) * 4 * pf::kMaxBasis, 256);
   L.total = off;
   return L;
 }
@@ -100,6 +124,45 @@ pf::Stencil2D stiffness2d(double hx, double hy, double scale) {
   s.cy = (float)(scale * ((1.0 / 3.0) * rx - (2.0 / 3.0) * ry));
   s.cd = (float)(scale * (-(1.0 / 6.0) * (rx + ry)));
   return s;
+}
+
+// 27-point Q1 stiffness stencil of a uniform 3-D grid by offset class
+// (x!=0) + 2 (y!=0) + 4 (z!=0): sum over axes d of S_d * prod_{e != d} M_e with
+// the 1-D stiffness S(0) = 2/h, S(1) = -1/h and mass M(0) = 4h/6, M(1) = h/6
+// (2x2x2 Gauss integrates it exactly), times `scale`.
+void stiffness3d(const double h[3], double scale, float kc[8]) {
+  for (int cls = 0; cls < 8; ++cls) {
+    double s = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      const bool off_d = (cls >> d) & 1;
+      double t = off_d ? -1.0 / h[d] : 2.0 / h[d];
+      for (int e = 0; e < 3; ++e)
+        if (e != d) t *= ((cls >> e) & 1) ? h[e] / 6.0 : 4.0 * h[e] / 6.0;
+      s += t;
+    }
+    kc[cls] = (float)(scale * s);
+  }
+}
+
+void set_params3d(pf_ctx* c, const pf_params* p) {
+  pf::Implicit3DArgs& a = c->im;
+  a.nx = (int)c->n[0];
+  a.ny = (int)c->n[1];
+  a.nz = (int)c->n[2];
+  a.nf = c->nf;
+  a.double_well = (c->model == PF_MODEL_AC);
+  a.dw2 = (float)(2.0 * p->W);
+  a.alpha = (float)p->fc_alpha;
+  a.two_gamma = (float)(2.0 * p->fc_gamma);
+  a.four_gamma = (float)(4.0 * p->fc_gamma);
+  a.cb2g = (float)(p->fc_beta - 2.0 * p->fc_gamma);
+  a.c3b6g = (float)(3.0 * p->fc_beta - 6.0 * p->fc_gamma);
+  const double cell = c->h[0] * c->h[1] * c->h[2];
+  stiffness3d(c->h, p->kappa / cell, a.kc);
+  a.inv_dt = (float)(1.0 / p->dt);
+  a.mob = (float)p->mobility;
+  a.cell = (float)cell;
+  a.unscaled = 0;
 }
 
 void destroy_graph(pf_ctx* c) {
@@ -139,6 +202,149 @@ pf_status ensure_graph(pf_ctx* c) {
   return PF_OK;
 }
 
+// ---- 3-D: residual / JVP launches, explicit steps, Newton-GMRES -----------
+
+pf_status check_ready(pf_ctx* c) {
+  if (!c->ws) return fail(c, PF_ERR_STATE, "no workspace bound");
+  if (!c->par_set) return fail(c, PF_ERR_STATE, "parameters not set");
+  return PF_OK;
+}
+
+cudaError_t residual3d(pf_ctx* c, const float* U, const float* Un, float* out, int unscaled) {
+  pf::Implicit3DArgs a = c->im;
+  a.U = U;
+  a.W = Un;
+  a.out = out;
+  a.unscaled = unscaled;
+  return pf::launch_residual3d(a, c->stream);
+}
+
+cudaError_t jvp3d(pf_ctx* c, const float* U, const float* v, float* out, int unscaled) {
+  pf::Implicit3DArgs a = c->im;
+  a.U = U;
+  a.W = v;
+  a.out = out;
+  a.unscaled = unscaled;
+  return pf::launch_jvp3d(a, c->stream);
+}
+
+int64_t vec_len(const pf_ctx* c) { return nnodes(c) * c->nf; }
+
+// U <- U - dt G with G = L M^-1 r(U) (the residual with U^n = U)
+pf_status step_explicit3d(pf_ctx* c, float* state, int64_t n_steps) {
+  const int64_t n = vec_len(c);
+  const float dt = (float)c->par.dt;
+  for (int64_t s = 0; s < n_steps; ++s) {
+    PF_CUDA(residual3d(c, state, state, c->g, 0));
+    PF_CUDA(pf::launch_axpby(-dt, c->g, 1.0f, state, n, c->stream));
+  }
+  return PF_OK;
+}
+
+// ||M g||_2 in FP64 (weights = lumped mass), returned on the host
+pf_status mass_norm(pf_ctx* c, const float* g, double* out) {
+  PF_CUDA(pf::launch_mass_norm(g, (int)c->n[0], (int)c->n[1], (int)c->n[2], c->nf,
+                               c->h[0] * c->h[1] * c->h[2], c->partials, c->result, c->stream));
+  double h;
+  PF_CUDA(cudaMemcpyAsync(&h, c->result, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  PF_CUDA(cudaStreamSynchronize(c->stream));
+  *out = std::sqrt(h);
+  return PF_OK;
+}
+
+// Restarted GMRES(m) for (M^-1 J) x = -G at the linearisation point c->u, x in
+// c->d (zero start).  Arnoldi with classical Gram-Schmidt applied twice (CGS2);
+// inner products in FP64 on the device, Hessenberg and Givens rotations in
+// FP64 on the host (Saad & Schultz 1986).
+pf_status gmres3d(pf_ctx* c, int m, int maxit, double rtol, int* iters, double* rel_out) {
+  const int64_t n = vec_len(c);
+  const int64_t ldv = c->ldv;
+  float* V = c->basis;
+  double* dh1 = c->small;
+  double* dh2 = c->small + pf::kMaxBasis;
+  double* dnrm = c->small + 2 * pf::kMaxBasis;
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), y(m);
+  double host[2 * pf::kMaxBasis + 1];
+  PF_CUDA(cudaMemsetAsync(c->d, 0, sizeof(float) * n, c->stream));
+  int total = 0;
+  double beta0 = -1.0, rel = 1.0;
+  for (;;) {
+    // r = -G - J x  (x = 0 on the first cycle)
+    if (total == 0) {
+      PF_CUDA(pf::launch_axpby(-1.0f, c->g, 0.0f, V, n, c->stream));
+    } else {
+      PF_CUDA(jvp3d(c, c->u, c->d, V, 0));
+      PF_CUDA(pf::launch_axpby(-1.0f, c->g, -1.0f, V, n, c->stream));
+    }
+    PF_CUDA(pf::launch_dots(V, ldv, 1, nullptr, n, c->partials, dnrm, c->stream));
+    PF_CUDA(cudaMemcpyAsync(host, dnrm, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    PF_CUDA(cudaStreamSynchronize(c->stream));
+    const double beta = std::sqrt(host[0]);
+    if (beta0 < 0) beta0 = beta;
+    if (beta0 == 0.0) {
+      rel = 0.0;
+      break;
+    }
+    rel = beta / beta0;
+    if (rel <= rtol || total >= maxit) break;
+    PF_CUDA(pf::launch_axpby((float)(1.0 / beta), V, 0.0f, V, n, c->stream));
+    std::fill(gv.begin(), gv.end(), 0.0);
+    gv[0] = beta;
+    int k = 0;
+    bool done = false;
+    for (; k < m && total < maxit; ++k) {
+      float* vk1 = V + (int64_t)(k + 1) * ldv;
+      PF_CUDA(jvp3d(c, c->u, V + (int64_t)k * ldv, vk1, 0));
+      PF_CUDA(pf::launch_dots(V, ldv, k + 1, vk1, n, c->partials, dh1, c->stream));
+      PF_CUDA(pf::launch_update(V, ldv, k + 1, dh1, vk1, n, c->partials, nullptr, c->stream));
+      PF_CUDA(pf::launch_dots(V, ldv, k + 1, vk1, n, c->partials, dh2, c->stream));
+      PF_CUDA(pf::launch_update(V, ldv, k + 1, dh2, vk1, n, c->partials, dnrm, c->stream));
+      PF_CUDA(cudaMemcpyAsync(host, c->small, sizeof(double) * (2 * pf::kMaxBasis + 1),
+                              cudaMemcpyDeviceToHost, c->stream));
+      PF_CUDA(cudaStreamSynchronize(c->stream));
+      ++total;
+      for (int j = 0; j <= k; ++j) H[(size_t)j * m + k] = host[j] + host[pf::kMaxBasis + j];
+      const double hk1 = std::sqrt(std::max(host[2 * pf::kMaxBasis], 0.0));
+      H[(size_t)(k + 1) * m + k] = hk1;
+      if (hk1 > 0.0)
+        PF_CUDA(pf::launch_axpby((float)(1.0 / hk1), vk1, 0.0f, vk1, n, c->stream));
+      for (int j = 0; j < k; ++j) {
+        const double t = cs[j] * H[(size_t)j * m + k] + sn[j] * H[(size_t)(j + 1) * m + k];
+        H[(size_t)(j + 1) * m + k] = -sn[j] * H[(size_t)j * m + k] + cs[j] * H[(size_t)(j + 1) * m + k];
+        H[(size_t)j * m + k] = t;
+      }
+      const double den = std::hypot(H[(size_t)k * m + k], hk1);
+      cs[k] = den > 0 ? H[(size_t)k * m + k] / den : 1.0;
+      sn[k] = den > 0 ? hk1 / den : 0.0;
+      H[(size_t)k * m + k] = den;
+      H[(size_t)(k + 1) * m + k] = 0.0;
+      gv[k + 1] = -sn[k] * gv[k];
+      gv[k] = cs[k] * gv[k];
+      if (std::fabs(gv[k + 1]) <= rtol * beta0 || hk1 == 0.0) {
+        ++k;
+        done = true;
+        break;
+      }
+    }
+    // y = H^-1 g (upper triangular), x += V y
+    for (int i = k - 1; i >= 0; --i) {
+      double s = gv[i];
+      for (int j = i + 1; j < k; ++j) s -= H[(size_t)i * m + j] * y[j];
+      y[i] = s / H[(size_t)i * m + i];
+    }
+    pf::LinComb lc{};
+    for (int j = 0; j < k; ++j) lc.c[j] = (float)y[j];
+    PF_CUDA(pf::launch_lincomb(V, ldv, k, lc, c->d, n, c->stream));
+    if (done || total >= maxit) {
+      rel = (k > 0) ? std::fabs(gv[k]) / beta0 : rel;
+      break;
+    }
+  }
+  *iters = total;
+  *rel_out = rel;
+  return PF_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -147,15 +353,28 @@ pf_status pf_create_mesh(pf_ctx** out, int dim, const int64_t nodes[3], const do
                          pf_model model, int n_fields, void* stream, size_t* workspace_bytes) {
   if (!out || !nodes || !h || !workspace_bytes) return PF_ERR_ARG;
   *out = nullptr;
-  if (dim != 2) return PF_ERR_ARG;  // 2-D explicit AC / CH
-  if (model != PF_MODEL_AC && model != PF_MODEL_CH) return PF_ERR_ARG;
-  if (n_fields != 1) return PF_ERR_ARG;
+  if (dim == 2) {  // explicit AC / CH
+    if (model != PF_MODEL_AC && model != PF_MODEL_CH) return PF_ERR_ARG;
+    if (n_fields != 1) return PF_ERR_ARG;
+  } else if (dim == 3) {  // AC (double well, one field) or Fan-Chen (1..8 fields)
+    if (model == PF_MODEL_AC) {
+      if (n_fields != 1) return PF_ERR_ARG;
+    } else if (model == PF_MODEL_FANCHEN) {
+      if (n_fields < 1 || n_fields > 8) return PF_ERR_ARG;
+    } else {
+      return PF_ERR_ARG;
+    }
+  } else {
+    return PF_ERR_ARG;
+  }
   const int64_t minn = (model == PF_MODEL_CH) ? 3 : 2;
+  int64_t total = 1;
   for (int k = 0; k < dim; ++k) {
     if (nodes[k] < minn || nodes[k] > (int64_t)1 << 20) return PF_ERR_ARG;
     if (!(h[k] > 0.0) || !isfinite(h[k])) return PF_ERR_ARG;
+    total *= nodes[k];
+    if (total > ((int64_t)1 << 31) - 1) return PF_ERR_ARG;
   }
-  if (nodes[0] * nodes[1] > ((int64_t)1 << 31) - 1) return PF_ERR_ARG;
   pf_ctx* c = new (std::nothrow) pf_ctx();
   if (!c) return PF_ERR_ARG;
   c->dim = dim;
@@ -180,10 +399,21 @@ pf_status pf_bind_workspace(pf_ctx* c, void* dev_ptr, size_t bytes) {
     return fail(c, PF_ERR_ARG, "workspace too small: %zu < %zu bytes", bytes, c->ws_bytes);
   const Layout L = layout(c);
   c->ws = (char*)dev_ptr;
-  c->buf_a = (float*)(c->ws + L.a);
-  c->buf_b = (float*)(c->ws + L.b);
   c->partials = (double*)(c->ws + L.partials);
   c->result = (double*)(c->ws + L.result);
+  c->small = (double*)(c->ws + L.small);
+  if (c->dim == 2) {
+    c->buf_a = (float*)(c->ws + L.a);
+    c->buf_b = (float*)(c->ws + L.b);
+  } else {
+    char* v = c->ws + L.vecs;
+    c->u = (float*)v;
+    c->un = (float*)(v + L.vec);
+    c->g = (float*)(v + 2 * L.vec);
+    c->d = (float*)(v + 3 * L.vec);
+    c->basis = (float*)(v + kVec3d * L.vec);
+    c->ldv = (int64_t)(L.vec / sizeof(float));
+  }
   destroy_graph(c);
   return PF_OK;
 }
@@ -199,6 +429,11 @@ pf_status pf_set_params(pf_ctx* c, const pf_params* p) {
     return fail(c, PF_ERR_ARG, "per-node mobility field is not supported by pf_step_explicit yet");
   c->par = *p;
   c->par_set = true;
+  destroy_graph(c);
+  if (c->dim == 3) {
+    set_params3d(c, p);
+    return PF_OK;
+  }
 
   const double s = p->shift, W = p->W;
   // f'(s + d) = f'(s) + f''(s) d + f'''(s)/2 d^2 + f''''(s)/6 d^3 for f = W u^2 (1-u)^2
@@ -236,6 +471,7 @@ pf_status pf_step_explicit(pf_ctx* c, float* state, int64_t n_steps) {
   if (!state) return fail(c, PF_ERR_ARG, "state is NULL");
   if (n_steps < 0) return fail(c, PF_ERR_ARG, "n_steps < 0");
   if (n_steps == 0) return PF_OK;
+  if (c->dim == 3) return step_explicit3d(c, state, n_steps);
   const float shift = (float)c->par.shift;
   const int nx = (int)c->n[0], ny = (int)c->n[1];
   // working copies with the mirror frame: d = u - shift (both planes fully defined)
@@ -264,6 +500,7 @@ pf_status pf_energy(pf_ctx* c, const float* state, double* energy, double* mass)
   if (!c->ws) return fail(c, PF_ERR_STATE, "no workspace bound");
   if (!c->par_set) return fail(c, PF_ERR_STATE, "parameters not set");
   if (!state) return fail(c, PF_ERR_ARG, "state is NULL");
+  if (c->dim != 2) return fail(c, PF_ERR_ARG, "pf_energy supports 2-D meshes");
   const double W = c->par.W;
   pf::Energy2DArgs a{};
   a.d = state;  // unshifted: f(u) = W (u^2 - 2 u^3 + u^4)
@@ -286,6 +523,87 @@ pf_status pf_energy(pf_ctx* c, const float* state, double* energy, double* mass)
   if (mass) *mass = host[1];
   if (!isfinite(host[0]) || !isfinite(host[1]))
     return fail(c, PF_ERR_NONFINITE, "non-finite energy or mass (unstable time step?)");
+  return PF_OK;
+}
+
+pf_status pf_step_implicit(pf_ctx* c, float* state, int64_t n_steps, const float* guess,
+                           const pf_newton_opts* opts, pf_newton_stats* stats) {
+  if (!c) return PF_ERR_ARG;
+  pf_status st = check_ready(c);
+  if (st != PF_OK) return st;
+  if (c->dim != 3) return fail(c, PF_ERR_ARG, "pf_step_implicit supports 3-D meshes");
+  if (!state) return fail(c, PF_ERR_ARG, "state is NULL");
+  if (n_steps < 0) return fail(c, PF_ERR_ARG, "n_steps < 0");
+  pf_newton_opts o{20, 30, 300, 1e-5, 1e-3};
+  if (opts) o = *opts;
+  if (o.gmres_restart < 1 || o.gmres_restart > pf::kMaxBasis - 1 || o.max_newton < 0 ||
+      o.gmres_max_iters < 1 || !(o.newton_rtol > 0) || !(o.gmres_rtol > 0))
+    return fail(c, PF_ERR_ARG, "invalid Newton/GMRES options (restart must be 1..%d)",
+                pf::kMaxBasis - 1);
+  pf_newton_stats s{0, 0, 1, 0.0, 0.0};
+  const int64_t n = vec_len(c);
+  const double inv_dt = 1.0 / c->par.dt;
+  for (int64_t step = 0; step < n_steps; ++step) {
+    PF_CUDA(cudaMemcpyAsync(c->un, state, sizeof(float) * n, cudaMemcpyDeviceToDevice, c->stream));
+    const float* start = (step == 0 && guess) ? guess : state;
+    PF_CUDA(cudaMemcpyAsync(c->u, start, sizeof(float) * n, cudaMemcpyDeviceToDevice, c->stream));
+    double ref;
+    st = mass_norm(c, c->un, &ref);  // ||M U^n||; the target is rtol ||M U^n / dt||
+    if (st != PF_OK) return st;
+    const double tol = o.newton_rtol * ref * inv_dt;
+    bool ok = false;
+    double rn = 0.0;
+    for (int it = 0;; ++it) {
+      PF_CUDA(residual3d(c, c->u, c->un, c->g, 0));
+      st = mass_norm(c, c->g, &rn);
+      if (st != PF_OK) return st;
+      if (!std::isfinite(rn)) return fail(c, PF_ERR_NONFINITE, "non-finite Newton residual");
+      if (step == 0 && it == 0) s.initial_residual = rn;
+      if (rn <= tol) {
+        ok = true;
+        break;
+      }
+      if (it >= o.max_newton) break;
+      int gi = 0;
+      double rel = 0.0;
+      st = gmres3d(c, o.gmres_restart, o.gmres_max_iters, o.gmres_rtol, &gi, &rel);
+      if (st != PF_OK) return st;
+      s.gmres_iters += gi;
+      s.newton_iters += 1;
+      PF_CUDA(pf::launch_axpby(1.0f, c->d, 1.0f, c->u, n, c->stream));
+    }
+    s.final_residual = rn;
+    if (!ok) s.converged = 0;
+    PF_CUDA(cudaMemcpyAsync(state, c->u, sizeof(float) * n, cudaMemcpyDeviceToDevice, c->stream));
+    if (!ok) {
+      PF_CUDA(cudaStreamSynchronize(c->stream));
+      if (stats) *stats = s;
+      return fail(c, PF_ERR_NOT_CONVERGED, "Newton did not reach ||R|| <= %g (got %g) in step %lld",
+                  tol, rn, (long long)step);
+    }
+  }
+  PF_CUDA(cudaStreamSynchronize(c->stream));
+  if (stats) *stats = s;
+  return PF_OK;
+}
+
+pf_status pf_jvp(pf_ctx* c, const float* U, const float* v, float* Jv) {
+  if (!c) return PF_ERR_ARG;
+  pf_status st = check_ready(c);
+  if (st != PF_OK) return st;
+  if (c->dim != 3) return fail(c, PF_ERR_ARG, "pf_jvp supports 3-D meshes");
+  if (!U || !v || !Jv) return fail(c, PF_ERR_ARG, "null array");
+  PF_CUDA(jvp3d(c, U, v, Jv, 1));
+  return PF_OK;
+}
+
+pf_status pf_implicit_residual(pf_ctx* c, const float* Un, const float* U, float* R) {
+  if (!c) return PF_ERR_ARG;
+  pf_status st = check_ready(c);
+  if (st != PF_OK) return st;
+  if (c->dim != 3) return fail(c, PF_ERR_ARG, "pf_implicit_residual supports 3-D meshes");
+  if (!U || !Un || !R) return fail(c, PF_ERR_ARG, "null array");
+  PF_CUDA(residual3d(c, U, Un, R, 1));
   return PF_OK;
 }
 

@@ -64,4 +64,37 @@ int energy2d_blocks(int nx, int ny);
 cudaError_t launch_energy2d(const Energy2DArgs& a, double* partials, double* result,
                             cudaStream_t s);
 
+// 3-D implicit operators (Eq. 13-14), scaled by the lumped mass unless unscaled.
+struct Implicit3DArgs {
+  const float* U;  // state at which r / H is evaluated (nf planes)
+  const float* W;  // JVP: direction v; residual: U^n
+  float* out;      // nf planes
+  int nx, ny, nz, nf;
+  int double_well;  // 1: f = W u^2 (1-u)^2 (nf == 1); 0: Fan-Chen
+  float dw2;        // 2 W
+  float alpha, two_gamma, four_gamma, cb2g, c3b6g;  // Fan-Chen: a, 2g, 4g, b - 2g, 3b - 6g
+  float kc[8];      // kappa / m * 27-point stiffness, by offset class (x!=0) + 2(y!=0) + 4(z!=0)
+  float inv_dt, mob;
+  float cell;       // hx hy hz
+  int unscaled;     // multiply the result by the lumped mass m_i
+};
+cudaError_t launch_residual3d(const Implicit3DArgs& a, cudaStream_t s);
+cudaError_t launch_jvp3d(const Implicit3DArgs& a, cudaStream_t s);
+
+// Krylov vector kernels (FP32 vectors, FP64 inner products).
+constexpr int kMaxBasis = 32;  // GMRES restart length + 1
+struct LinComb {
+  float c[kMaxBasis];
+};
+int krylov_partial_blocks();
+cudaError_t launch_dots(const float* V, int64_t ldv, int k, const float* w, int64_t n,
+                        double* partials, double* out, cudaStream_t s);
+cudaError_t launch_update(const float* V, int64_t ldv, int k, const double* coef, float* w,
+                          int64_t n, double* partials, double* norm_out, cudaStream_t s);
+cudaError_t launch_axpby(float a, const float* x, float b, float* y, int64_t n, cudaStream_t s);
+cudaError_t launch_lincomb(const float* V, int64_t ldv, int k, const LinComb& y, float* x,
+                           int64_t n, cudaStream_t s);
+cudaError_t launch_mass_norm(const float* g, int nx, int ny, int nz, int nf, double cell,
+                             double* partials, double* out, cudaStream_t s);
+
 }  // namespace pf

@@ -1,0 +1,130 @@
+"""GPU parity of the 3-D implicit operators and the Newton-GMRES step vs the oracle.
+
+The JVP and residual (Eq. 14) are compared element by element with the FP64
+oracle; the Newton root is compared with the oracle's FP64 Newton root (tight
+tolerances on both sides, so the difference is the FP32 noise floor); at the
+grain-growth size (128^3, 8 order parameters) the GPU root is re-evaluated by
+the oracle's FP64 residual, a property that holds at any size.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import pf_inputs as G
+
+pytestmark = pytest.mark.gpu
+
+FC = dict(alpha=1.0, beta=1.0, gamma=1.5)
+
+
+def _pf():
+    import paper_2601_06079_gb300 as pf
+    return pf
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def solver3d(shape, nf, model="fanchen", h=1.0, kappa=1.0, mob=1.0, dt=0.5, W=1.0):
+    pf = _pf()
+    s = pf.Solver(shape, h=h, model=model, n_fields=nf)
+    s.set_params(W=W, kappa=kappa, mobility=mob, dt=dt, shift=0.0, **FC)
+    return s
+
+
+def oracle3d(shape, nf, model="fanchen", h=1.0, kappa=1.0, mob=1.0, W=1.0):
+    return O.Problem(shape, h=h, energy="fan_chen" if model == "fanchen" else "double_well",
+                     nf=nf, kappa=kappa, mob=mob, W=W, **FC)
+
+
+def cu(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+@pytest.mark.parametrize("shape,nf,h", [((5, 6, 7), 1, 1.0), ((9, 10, 11), 3, 0.8),
+                                        ((17, 9, 12), 8, 1.0), ((3, 2, 4), 2, (1.0, 0.7, 1.3))])
+def test_jvp_and_residual_match_oracle(shape, nf, h):
+    s = solver3d(shape, nf, h=h, kappa=0.9, mob=1.1)
+    P = oracle3d(shape, nf, h=h, kappa=0.9, mob=1.1)
+    U = G.random_field(1, (nf,) + shape, 0.0, 1.0)
+    Un = G.random_field(2, (nf,) + shape, 0.0, 1.0)
+    v = G.random_field(3, (nf,) + shape)
+    if nf == 1:
+        U, Un, v = U[0], Un[0], v[0]
+    Jv = s.jvp(cu(U), cu(v)).cpu().numpy()
+    ref = P.implicit_jvp(0.5, U, v)
+    assert rel(Jv, ref) <= 2e-6
+    R = s.implicit_residual(cu(Un), cu(U)).cpu().numpy()
+    ref = P.implicit_residual(0.5, Un, U)
+    assert rel(R, ref) <= 2e-6
+
+
+def test_double_well_3d_jvp_matches_oracle():
+    shape = (8, 9, 10)
+    s = solver3d(shape, 1, model="ac", kappa=0.7, mob=1.3, W=1.2)
+    P = oracle3d(shape, 1, model="ac", kappa=0.7, mob=1.3, W=1.2)
+    U = G.random_field(4, shape, 0.0, 1.0)
+    v = G.random_field(5, shape)
+    assert rel(s.jvp(cu(U), cu(v)).cpu().numpy(), P.implicit_jvp(0.5, U, v)) <= 2e-6
+
+
+@pytest.mark.parametrize("shape,nf", [((12, 10, 9), 4), ((9, 17, 8), 8)])
+def test_newton_root_matches_oracle(shape, nf):
+    U0 = np.clip(0.5 + 0.6 * G.random_field(7, (nf,) + shape), 0, 1).astype(np.float32)
+    s = solver3d(shape, nf)
+    t = cu(U0)
+    st = s.step_implicit(t, 1, newton_rtol=1e-6, gmres_rtol=1e-4)
+    assert st["converged"] and st["newton_iters"] >= 2
+    P = oracle3d(shape, nf)
+    ref, ost = P.newton(0.5, U0, abs_tol=1e-10)
+    assert ost["ok"]
+    assert rel(t.cpu().numpy(), ref) <= 1e-5
+
+
+def test_multi_step_implicit_matches_oracle():
+    shape, nf = (10, 11, 9), 3
+    U0 = np.clip(0.5 + 0.6 * G.random_field(9, (nf,) + shape), 0, 1).astype(np.float32)
+    s = solver3d(shape, nf)
+    t = cu(U0)
+    st = s.step_implicit(t, 4, newton_rtol=1e-6, gmres_rtol=1e-4)
+    assert st["converged"]
+    P = oracle3d(shape, nf)
+    ref = U0.astype(np.float64)
+    for _ in range(4):
+        ref, ost = P.newton(0.5, ref, abs_tol=1e-10)
+    assert rel(t.cpu().numpy(), ref) <= 2e-5
+    assert P.energy(t.cpu().numpy()) < P.energy(U0)
+
+
+def test_uniform_state_needs_no_newton_iteration():
+    s = solver3d((6, 7, 8), 2)
+    t = torch.zeros((2, 6, 7, 8), device="cuda")
+    st = s.step_implicit(t, 2)
+    assert st["newton_iters"] == 0 and torch.count_nonzero(t) == 0
+
+
+def test_explicit_3d_matches_oracle():
+    shape, nf = (7, 9, 8), 2
+    U0 = G.random_field(3, (nf,) + shape, 0.0, 1.0)
+    s = solver3d(shape, nf, dt=0.02)
+    t = cu(U0)
+    s.step_explicit(t, 25)
+    ref = oracle3d(shape, nf).ac_explicit(U0, 0.02, 25)
+    assert rel(t.cpu().numpy(), ref) <= 1e-5
+
+
+def test_grain_growth_128_cubed_root_reevaluated_by_oracle():
+    # 128^3 nodes, 8 Fan-Chen order parameters (Voronoi start), dt = 0.5
+    U0 = G.voronoi_grains(1, n=128, n_seeds=64, n_op=8)
+    s = solver3d((128, 128, 128), 8)
+    t = cu(U0)
+    st = s.step_implicit(t, 1)
+    assert st["converged"]
+    P = oracle3d((128, 128, 128), 8)
+    R = P.implicit_residual(0.5, U0, t.cpu().numpy())
+    ref = np.linalg.norm(P.lumped_mass()[None] * U0.astype(np.float64) / 0.5)
+    assert np.linalg.norm(R) <= 2e-5 * ref
