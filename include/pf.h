@@ -68,9 +68,11 @@ typedef struct {
   double shift;       /* the FP32 working state is stored as U - shift (exact change of
                          variable that keeps rounding relative to the deviation); 0.5 suits
                          the double well, 0 the Fan-Chen model */
-  const float* mobility_field; /* CH only: device, one multiplier per node, M(x) = M m(x)
+  const float* mobility_field; /* 2-D CH only: device, one multiplier per node, M(x) = M m(x)
                                   interpolated by Q1 at Gauss points; NULL = uniform.
-                                  Must stay valid while the context uses it. */
+                                  Must stay valid while the context uses it.  With a field,
+                                  pf_step_explicit uses the element form of K_M (tiled
+                                  kernel) instead of the fused stencil kernel. */
 } pf_params;
 
 /* Newton-Krylov controls for the implicit step (Eq. 13-14).  NULL = defaults. */
@@ -137,6 +139,31 @@ pf_status pf_jvp(pf_ctx* ctx, const float* U, const float* v, float* Jv);
 /* Implicit residual of Eq. 14 (3-D): R = M (U - Un) / dt + L r(U).  Device arrays,
  * n_fields * N FP32.  Enqueues only. */
 pf_status pf_implicit_residual(pf_ctx* ctx, const float* Un, const float* U, float* R);
+
+/* Bytes of caller-owned device workspace pf_adjoint needs for n_steps steps
+ * with a checkpoint every ckpt_every steps: (ceil(n_steps/ckpt_every) + 1)
+ * checkpoint planes, ckpt_every segment planes, 3 more planes and small
+ * reduction buffers.  2-D Cahn-Hilliard only. */
+pf_status pf_adjoint_workspace(pf_ctx* ctx, int64_t n_steps, int ckpt_every, size_t* bytes);
+
+/* Loss and gradients of the explicit 2-D Cahn-Hilliard trajectory (Eq. 12 with
+ * the split form of Eq. 9-10 and the per-node mobility of pf_params), by the
+ * discrete adjoint of the explicit map (sensitivities in the sense of Supp. 2,
+ * Eq. II.1-II.6, taken through the time-stepping map):
+ *   loss = 1/2 sum_i w_i (c_i^N - target_i)^2, w_i = m_i (nodal_loss = 0) or 1.
+ * Forward: n_steps steps from state0 (device, not modified), storing the state
+ * every ckpt_every steps; reverse: each segment is recomputed from its
+ * checkpoint, then stepped backwards.
+ *   adj_ws, adj_bytes   device workspace of pf_adjoint_workspace() bytes (256-aligned)
+ *   loss                host, 1 double (may be NULL)
+ *   grad_scalars        host, 3 doubles: dLoss/dkappa, dLoss/dW, dLoss/dM (may be NULL)
+ *   grad_mobility       device, N doubles: dLoss/dm_i for the mobility field (may be NULL)
+ *   grad_state0         device, N floats: dLoss/dc^0 (may be NULL)
+ * With no mobility field bound the field is taken as 1 everywhere.  State and
+ * adjoint are FP32, all gradient sums FP64.  Synchronises the stream. */
+pf_status pf_adjoint(pf_ctx* ctx, const float* state0, const float* target, int64_t n_steps,
+                     int ckpt_every, int nodal_loss, void* adj_ws, size_t adj_bytes, double* loss,
+                     double* grad_scalars, double* grad_mobility, float* grad_state0);
 
 /* Discrete free energy E_h = sum_e sum_q w_q |J| [f(U_q) + kappa/2 |grad U_q|^2]
  * (Eq. 5-6) and, per field, the mass integral sum_i m_i U_i, accumulated in FP64.

@@ -14,8 +14,9 @@ from __future__ import annotations
 import torch
 
 from . import _lib
-from ._lib import (PF_MODEL_AC, PF_MODEL_CH, PF_MODEL_FANCHEN, pf_bind_workspace,  # noqa: F401
-                   pf_create_mesh, pf_destroy, pf_energy, pf_energy2d_static,
+from ._lib import (PF_MODEL_AC, PF_MODEL_CH, PF_MODEL_FANCHEN, pf_adjoint,  # noqa: F401
+                   pf_adjoint_workspace, pf_bind_workspace, pf_create_mesh, pf_destroy,
+                   pf_energy, pf_energy2d_static,
                    pf_implicit_residual, pf_jvp, pf_last_error, pf_set_params, pf_step_explicit,
                    pf_step_implicit)
 
@@ -112,6 +113,23 @@ class Solver:
                                          self._state(out)))
         return out
 
+    def adjoint(self, c0, target, n_steps, ckpt_every=100, nodal_loss=False, want_field=True,
+                want_state=False):
+        """Loss 1/2 sum w_i (c^N_i - target_i)^2 and its gradients by the discrete
+        adjoint of the explicit CH map (2-D CH).  Returns (loss, grads) with grads
+        = {kappa, W, M, mobility_field (float64 tensor), c0 (float32 tensor)}."""
+        st, nbytes = pf_adjoint_workspace(self._ctx, n_steps, ckpt_every)
+        self._check(st)
+        ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
+        gm = torch.empty(self.shape, dtype=torch.float64, device=self.device) if want_field else None
+        g0 = torch.empty(self.shape, dtype=torch.float32, device=self.device) if want_state else None
+        st, loss, gs = pf_adjoint(self._ctx, self._state(c0), self._state(target), n_steps,
+                                  ckpt_every, int(nodal_loss), ws.data_ptr(), ws.numel(),
+                                  gm.data_ptr() if gm is not None else 0,
+                                  g0.data_ptr() if g0 is not None else 0)
+        self._check(st)
+        return loss, {"kappa": gs[0], "W": gs[1], "M": gs[2], "mobility_field": gm, "c0": g0}
+
     def energy(self, state):
         """(E_h, mass integral) in FP64 (Eq. 5-6); synchronises the stream."""
         st, e, m = pf_energy(self._ctx, self._state(state))
@@ -128,3 +146,42 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+class _CHMisfit(torch.autograd.Function):
+    """Loss of an explicit CH trajectory with gradients from the library's
+    hand-written adjoint kernels (forward computes loss and all gradients in
+    one pf_adjoint call; backward scales them by the incoming gradient)."""
+
+    @staticmethod
+    def forward(ctx, mobility_field, kappa, W, M, c0, target, dt, n_steps, ckpt_every, h, nodal):
+        shape = tuple(c0.shape)
+        s = Solver(shape, h=h, model="ch", device=c0.device)
+        s.set_params(W=float(W), kappa=float(kappa), mobility=float(M), dt=dt,
+                     mobility_field=mobility_field.detach())
+        loss, g = s.adjoint(c0.detach().contiguous(), target.detach().contiguous(), n_steps,
+                            ckpt_every, nodal_loss=nodal, want_field=True, want_state=True)
+        dev = c0.device
+        ctx.save_for_backward(g["mobility_field"].to(mobility_field.dtype),
+                              torch.tensor(g["kappa"], dtype=torch.float64, device=dev),
+                              torch.tensor(g["W"], dtype=torch.float64, device=dev),
+                              torch.tensor(g["M"], dtype=torch.float64, device=dev),
+                              g["c0"])
+        return torch.tensor(loss, dtype=torch.float64, device=dev)
+
+    @staticmethod
+    def backward(ctx, go):
+        gm, gk, gw, gM, g0 = ctx.saved_tensors
+        return (go * gm, (go * gk).to(torch.float64), (go * gw).to(torch.float64),
+                (go * gM).to(torch.float64), (go * g0).to(g0.dtype), None, None, None, None,
+                None, None)
+
+
+def ch_misfit(mobility_field, kappa, W, M, c0, target, dt, n_steps, ckpt_every=100, h=1.0,
+              nodal_loss=False):
+    """Differentiable CH trajectory misfit: 1/2 sum_i m_i (c^N_i - target_i)^2 after
+    n_steps explicit steps from c0, as a function of the per-node mobility field
+    and the scalars kappa, W, M (0-d tensors).  Gradients come from the discrete
+    adjoint (pf_adjoint), not from autograd tracing."""
+    return _CHMisfit.apply(mobility_field, kappa, W, M, c0, target, dt, n_steps, ckpt_every, h,
+                           nodal_loss)

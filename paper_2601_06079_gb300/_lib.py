@@ -80,6 +80,12 @@ def lib():
         L.pf_jvp.argtypes = [ctx, C.c_void_p, C.c_void_p, C.c_void_p]
         L.pf_implicit_residual.restype = st
         L.pf_implicit_residual.argtypes = [ctx, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.pf_adjoint_workspace.restype = st
+        L.pf_adjoint_workspace.argtypes = [ctx, C.c_int64, C.c_int, C.POINTER(C.c_size_t)]
+        L.pf_adjoint.restype = st
+        L.pf_adjoint.argtypes = [ctx, C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_int,
+                                 C.c_void_p, C.c_size_t, C.POINTER(C.c_double),
+                                 C.POINTER(C.c_double), C.c_void_p, C.c_void_p]
         L.pf_energy.restype = st
         L.pf_energy.argtypes = [ctx, C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.pf_energy2d_static.restype = st
@@ -97,7 +103,8 @@ def lib():
 def exported_symbols():
     """Names declared in include/pf.h (checked against the .so by the tests)."""
     return ["pf_create_mesh", "pf_bind_workspace", "pf_set_params", "pf_step_explicit",
-            "pf_step_implicit", "pf_jvp", "pf_implicit_residual", "pf_energy",
+            "pf_step_implicit", "pf_jvp", "pf_implicit_residual", "pf_adjoint_workspace",
+            "pf_adjoint", "pf_energy",
             "pf_energy2d_static", "pf_last_error", "pf_destroy"]
 
 
@@ -139,6 +146,23 @@ def pf_jvp(ctx, U_ptr, v_ptr, out_ptr):
 def pf_implicit_residual(ctx, Un_ptr, U_ptr, out_ptr):
     return lib().pf_implicit_residual(ctx, C.c_void_p(Un_ptr), C.c_void_p(U_ptr),
                                       C.c_void_p(out_ptr))
+
+
+def pf_adjoint_workspace(ctx, n_steps, ckpt_every):
+    b = C.c_size_t(0)
+    s = lib().pf_adjoint_workspace(ctx, int(n_steps), int(ckpt_every), C.byref(b))
+    return s, b.value
+
+
+def pf_adjoint(ctx, state0_ptr, target_ptr, n_steps, ckpt_every, nodal_loss, ws_ptr, ws_bytes,
+               grad_mob_ptr, grad_state0_ptr):
+    loss = C.c_double(0)
+    gs = (C.c_double * 3)()
+    s = lib().pf_adjoint(ctx, C.c_void_p(state0_ptr), C.c_void_p(target_ptr), int(n_steps),
+                         int(ckpt_every), int(nodal_loss), C.c_void_p(ws_ptr), ws_bytes,
+                         C.byref(loss), gs, C.c_void_p(grad_mob_ptr) if grad_mob_ptr else None,
+                         C.c_void_p(grad_state0_ptr) if grad_state0_ptr else None)
+    return s, loss.value, list(gs)
 
 
 def pf_energy(ctx, state_ptr):

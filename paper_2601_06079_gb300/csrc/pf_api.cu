@@ -36,6 +36,7 @@ struct pf_ctx {
   // derived coefficients
   pf::Explicit2DArgs ex{};
   pf::Implicit3DArgs im{};
+  pf::ChMobArgs mob{};
 
   // 3-D workspace segments (each n_fields * N floats)
   float* u = nullptr;   // current iterate / state
@@ -200,6 +201,73 @@ pf_status ensure_graph(pf_ctx* c) {
     return cuda_fail(c, ie, "cudaGraphInstantiate");
   }
   return PF_OK;
+}
+
+// ---- 2-D CH with a mobility field: plain-layout steps and the adjoint ------
+
+int64_t nodes2d(const pf_ctx* c) { return c->n[0] * c->n[1]; }
+
+// n steps from d_in into d_out (both plain planes) through the ping-pong planes
+pf_status mob_steps(pf_ctx* c, const float* d_in, float* d_out, int64_t n) {
+  const int64_t N = nodes2d(c);
+  if (n == 0) {
+    if (d_out != d_in)
+      PF_CUDA(cudaMemcpyAsync(d_out, d_in, sizeof(float) * N, cudaMemcpyDeviceToDevice, c->stream));
+    return PF_OK;
+  }
+  pf::ChMobArgs a = c->mob;
+  const float* cur = d_in;
+  for (int64_t s = 0; s < n; ++s) {
+    float* dst = (s == n - 1) ? d_out : ((s % 2 == 0) ? c->buf_a : c->buf_b);
+    a.d = cur;
+    PF_CUDA(pf::launch_ch_mob_step(a, dst, c->stream));
+    cur = dst;
+  }
+  return PF_OK;
+}
+
+pf_status step_explicit_mob(pf_ctx* c, float* state, int64_t n_steps) {
+  const int64_t N = nodes2d(c);
+  const float shift = (float)c->par.shift;
+  float* cur = c->buf_a;
+  float* oth = c->buf_b;
+  PF_CUDA(pf::launch_add(state, cur, N, -shift, c->stream));
+  pf::ChMobArgs a = c->mob;
+  for (int64_t s = 0; s < n_steps; ++s) {
+    a.d = cur;
+    PF_CUDA(pf::launch_ch_mob_step(a, oth, c->stream));
+    std::swap(cur, oth);
+  }
+  PF_CUDA(pf::launch_add(cur, state, N, shift, c->stream));
+  return PF_OK;
+}
+
+struct AdjLayout {
+  size_t ck, seg, y0, y1, ones, acc, small, total;
+  int64_t nck;
+};
+
+AdjLayout adj_layout(const pf_ctx* c, int64_t n_steps, int ckpt) {
+  AdjLayout L{};
+  const size_t field = align_up(sizeof(float) * (size_t)nodes2d(c), 256);
+  L.nck = (n_steps + ckpt - 1) / ckpt + 1;
+  size_t off = 0;
+  L.ck = off;
+  off += field * L.nck;
+  L.seg = off;
+  off += field * ckpt;
+  L.y0 = off;
+  off += field;
+  L.y1 = off;
+  off += field;
+  L.ones = off;
+  off += field;
+  L.acc = off;
+  off += align_up(sizeof(double) * 3 * pf::ch_mob_blocks((int)c->n[0], (int)c->n[1]), 256);
+  L.small = off;
+  off += align_up(sizeof(double) * 512, 256);
+  L.total = off;
+  return L;
 }
 
 // ---- 3-D: residual / JVP launches, explicit steps, Newton-GMRES -----------
@@ -425,8 +493,8 @@ pf_status pf_set_params(pf_ctx* c, const pf_params* p) {
       !isfinite(p->dt) || !isfinite(p->kappa) || !isfinite(p->mobility) || !isfinite(p->W) ||
       !isfinite(p->shift))
     return fail(c, PF_ERR_ARG, "invalid parameters (need dt > 0, mobility > 0, kappa, W >= 0)");
-  if (p->mobility_field)
-    return fail(c, PF_ERR_ARG, "per-node mobility field is not supported by pf_step_explicit yet");
+  if (p->mobility_field && !(c->dim == 2 && c->model == PF_MODEL_CH))
+    return fail(c, PF_ERR_ARG, "a per-node mobility field needs a 2-D Cahn-Hilliard mesh");
   c->par = *p;
   c->par_set = true;
   destroy_graph(c);
@@ -458,6 +526,26 @@ pf_status pf_set_params(pf_ctx* c, const pf_params* p) {
     a.p3 = (float)(fp[3] / 4);
     a.k1 = stiffness2d(hx, hy, p->kappa / m);
     a.k2 = stiffness2d(hx, hy, -p->dt * p->mobility / m);
+    pf::ChMobArgs& b = c->mob;
+    b.nx = a.nx;
+    b.ny = a.ny;
+    b.mfield = p->mobility_field;
+    b.p0 = (float)fp[0];
+    b.p1 = (float)fp[1];
+    b.p2 = (float)fp[2];
+    b.p3 = (float)fp[3];
+    // second derivative of f at s + d, expanded about s (exact quadratic in d)
+    b.s0 = (float)(W * (2 - 12 * s + 12 * s * s));
+    b.s1 = (float)(W * (-12 + 24 * s));
+    b.s2 = (float)(12 * W);
+    b.k = stiffness2d(hx, hy, 1.0 / m);
+    b.kappa = (float)p->kappa;
+    b.M = (float)p->mobility;
+    b.W = (float)W;
+    b.dt = (float)p->dt;
+    b.ihx = (float)(1.0 / hx);
+    b.ihy = (float)(1.0 / hy);
+    b.cell = m;
   }
   pf::pack_explicit2d(a);
   destroy_graph(c);
@@ -472,6 +560,7 @@ pf_status pf_step_explicit(pf_ctx* c, float* state, int64_t n_steps) {
   if (n_steps < 0) return fail(c, PF_ERR_ARG, "n_steps < 0");
   if (n_steps == 0) return PF_OK;
   if (c->dim == 3) return step_explicit3d(c, state, n_steps);
+  if (c->par.mobility_field) return step_explicit_mob(c, state, n_steps);
   const float shift = (float)c->par.shift;
   const int nx = (int)c->n[0], ny = (int)c->n[1];
   // working copies with the mirror frame: d = u - shift (both planes fully defined)
@@ -585,6 +674,106 @@ pf_status pf_step_implicit(pf_ctx* c, float* state, int64_t n_steps, const float
   PF_CUDA(cudaStreamSynchronize(c->stream));
   if (stats) *stats = s;
   return PF_OK;
+}
+
+pf_status pf_adjoint_workspace(pf_ctx* c, int64_t n_steps, int ckpt_every, size_t* bytes) {
+  if (!c || !bytes) return PF_ERR_ARG;
+  if (c->dim != 2 || c->model != PF_MODEL_CH)
+    return fail(c, PF_ERR_ARG, "the adjoint needs a 2-D Cahn-Hilliard mesh");
+  if (n_steps < 1 || ckpt_every < 1) return fail(c, PF_ERR_ARG, "n_steps and ckpt_every must be >= 1");
+  *bytes = adj_layout(c, n_steps, ckpt_every).total;
+  return PF_OK;
+}
+
+pf_status pf_adjoint(pf_ctx* c, const float* state0, const float* target, int64_t n_steps,
+                     int ckpt_every, int nodal_loss, void* adj_ws, size_t adj_bytes, double* loss,
+                     double* grad_scalars, double* grad_mobility, float* grad_state0) {
+  if (!c) return PF_ERR_ARG;
+  pf_status st = check_ready(c);
+  if (st != PF_OK) return st;
+  if (c->dim != 2 || c->model != PF_MODEL_CH)
+    return fail(c, PF_ERR_ARG, "the adjoint needs a 2-D Cahn-Hilliard mesh");
+  if (!state0 || !target || !adj_ws) return fail(c, PF_ERR_ARG, "null array");
+  if (n_steps < 1 || ckpt_every < 1) return fail(c, PF_ERR_ARG, "n_steps and ckpt_every must be >= 1");
+  const AdjLayout L = adj_layout(c, n_steps, ckpt_every);
+  if (adj_bytes < L.total || (uintptr_t)adj_ws % 256)
+    return fail(c, PF_ERR_ARG, "adjoint workspace too small or misaligned (%zu < %zu)", adj_bytes,
+                L.total);
+  const int nx = (int)c->n[0], ny = (int)c->n[1];
+  const int64_t N = nodes2d(c);
+  const size_t field = align_up(sizeof(float) * (size_t)N, 256);
+  char* ws = (char*)adj_ws;
+  auto ck = [&](int64_t i) { return (float*)(ws + L.ck + field * i); };
+  auto seg = [&](int64_t i) { return (float*)(ws + L.seg + field * i); };
+  float* y0 = (float*)(ws + L.y0);
+  float* y1 = (float*)(ws + L.y1);
+  float* ones = (float*)(ws + L.ones);
+  double* acc = (double*)(ws + L.acc);
+  double* small = (double*)(ws + L.small);
+  const int nb = pf::ch_mob_blocks(nx, ny);
+  const float shift = (float)c->par.shift;
+  const double cell = c->h[0] * c->h[1];
+  const float* saved_field = c->mob.mfield;
+  if (!c->mob.mfield) {  // uniform mobility: a field of ones
+    PF_CUDA(cudaMemsetAsync(ones, 0, sizeof(float) * N, c->stream));
+    PF_CUDA(pf::launch_add(ones, ones, N, 1.0f, c->stream));
+    c->mob.mfield = ones;
+  }
+  pf::ChMobArgs a = c->mob;
+  // forward with checkpoints: ck(j) = d^{j * ckpt_every}, ck(last) = d^N
+  const int64_t last = (n_steps + ckpt_every - 1) / ckpt_every;
+  PF_CUDA(pf::launch_add(state0, ck(0), N, -shift, c->stream));
+  for (int64_t j = 0; j < last && st == PF_OK; ++j) {
+    const int64_t len = std::min<int64_t>(ckpt_every, n_steps - j * ckpt_every);
+    st = mob_steps(c, ck(j), ck(j + 1), len);
+  }
+  if (st == PF_OK) {
+    PF_CUDA(pf::launch_loss(ck(last), shift, target, nx, ny, cell, nodal_loss, y0, small + 8,
+                            small, c->stream));
+    PF_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * 3 * nb, c->stream));
+    if (grad_mobility) PF_CUDA(cudaMemsetAsync(grad_mobility, 0, sizeof(double) * N, c->stream));
+    float* yin = y0;
+    float* yout = y1;
+    for (int64_t j = last - 1; j >= 0 && st == PF_OK; --j) {
+      const int64_t start = j * ckpt_every;
+      const int64_t len = std::min<int64_t>(ckpt_every, n_steps - start);
+      // recompute d^{start} .. d^{start+len-1} into the segment buffer
+      PF_CUDA(cudaMemcpyAsync(seg(0), ck(j), sizeof(float) * N, cudaMemcpyDeviceToDevice,
+                              c->stream));
+      for (int64_t t = 1; t < len && st == PF_OK; ++t) st = mob_steps(c, seg(t - 1), seg(t), 1);
+      for (int64_t t = len - 1; t >= 0 && st == PF_OK; --t) {
+        a.d = seg(t);
+        cudaError_t e = pf::launch_ch_adj_step(a, yin, yout, grad_mobility, acc, c->stream);
+        if (e != cudaSuccess) {
+          c->mob.mfield = saved_field;
+          return cuda_fail(c, e, "adjoint step");
+        }
+        std::swap(yin, yout);
+      }
+    }
+    if (st == PF_OK) {
+      cudaError_t e = pf::launch_colsum(acc, nb, 3, 3, small + 1, c->stream);
+      if (e == cudaSuccess && grad_state0)
+        e = pf::launch_mass_scale(yin, nx, ny, cell, grad_state0, c->stream);
+      double host[4] = {0, 0, 0, 0};
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(host, small, sizeof(host), cudaMemcpyDeviceToHost, c->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+      if (e != cudaSuccess) {
+        c->mob.mfield = saved_field;
+        return cuda_fail(c, e, "adjoint reductions");
+      }
+      if (loss) *loss = host[0];
+      if (grad_scalars) {
+        grad_scalars[0] = host[1];
+        grad_scalars[1] = host[2];
+        grad_scalars[2] = host[3];
+      }
+      if (!std::isfinite(host[0])) st = fail(c, PF_ERR_NONFINITE, "non-finite loss");
+    }
+  }
+  c->mob.mfield = saved_field;
+  return st;
 }
 
 pf_status pf_jvp(pf_ctx* c, const float* U, const float* v, float* Jv) {

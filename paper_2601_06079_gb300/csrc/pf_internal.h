@@ -64,6 +64,31 @@ int energy2d_blocks(int nx, int ny);
 cudaError_t launch_energy2d(const Energy2DArgs& a, double* partials, double* result,
                             cudaStream_t s);
 
+// 2-D Cahn-Hilliard with a per-node mobility field: explicit step and its
+// discrete adjoint (plain row-major planes, shifted state d = c - s).
+struct ChMobArgs {
+  const float* d;       // shifted state at which the operators are evaluated
+  const float* mfield;  // mobility multiplier per node
+  int nx, ny;
+  float p0, p1, p2, p3;  // f'(s + d) = p0 + d (p1 + d (p2 + d p3))
+  float s0, s1, s2;      // f''(s + d) = s0 + d (s1 + d s2)
+  Stencil2D k;           // Q1 stiffness stencil / cell
+  float kappa, M, W, dt, ihx, ihy;
+  double cell;
+};
+int ch_mob_blocks(int nx, int ny);
+cudaError_t launch_ch_mob_step(const ChMobArgs& a, float* out, cudaStream_t s);
+cudaError_t launch_ch_adj_step(const ChMobArgs& a, const float* yin, float* yout,
+                               double* grad_m, double* acc, cudaStream_t s);
+cudaError_t launch_loss(const float* d, float shift, const float* target, int nx, int ny,
+                        double cell, int nodal, float* y, double* partials, double* out,
+                        cudaStream_t s);
+cudaError_t launch_colsum(const double* in, int nb, int stride, int k, double* out,
+                          cudaStream_t s);
+cudaError_t launch_mass_scale(const float* y, int nx, int ny, double cell, float* out,
+                              cudaStream_t s);
+cudaError_t launch_add(const float* in, float* out, int64_t n, float add, cudaStream_t s);
+
 // 3-D implicit operators (Eq. 13-14), scaled by the lumped mass unless unscaled.
 struct Implicit3DArgs {
   const float* U;  // state at which r / H is evaluated (nf planes)
