@@ -165,6 +165,49 @@ pf_status pf_adjoint(pf_ctx* ctx, const float* state0, const float* target, int6
                      int ckpt_every, int nodal_loss, void* adj_ws, size_t adj_bytes, double* loss,
                      double* grad_scalars, double* grad_mobility, float* grad_state0);
 
+/* Ensemble stepping modes for pf_step_ensemble. */
+enum {
+  PF_ENS_PERSISTENT = 0, /* one persistent launch for all steps (graph-captured), grid barrier */
+  PF_ENS_PER_STEP = 1,   /* one launch per step covering every instance */
+  PF_ENS_PLAIN = 2       /* the single-mesh fused step, one launch per instance and step */
+};
+
+/* Create a context for `count` independent 2-D Allen-Cahn instances (a batched
+ * ensemble, the array-programming idea of Sec. 2.4 applied across whole
+ * problems).  Instance i has nx[i] x ny[i] nodes (each >= 4) and spacing
+ * h[2i], h[2i+1] (h may be NULL: 1).  States are packed: instance i occupies
+ * offsets[i] .. offsets[i+1]-1 of one FP32 array (host out, count+1 entries).
+ * Host only; reports the workspace size to bind with pf_bind_workspace. */
+pf_status pf_create_ensemble(pf_ctx** out, int count, const int64_t* nx, const int64_t* ny,
+                             const double* h, void* stream, size_t* workspace_bytes,
+                             int64_t* offsets);
+
+/* Per-instance parameters (host array of `count`; W, kappa, mobility = L, dt;
+ * one shared shift; no mobility field).  Needs the workspace bound; copies the
+ * per-instance arguments to the device and synchronises the stream. */
+pf_status pf_set_ensemble_params(pf_ctx* ctx, const pf_params* params);
+
+/* Autotuner: for each size class (equal nx, ny) times `reps` batched steps for
+ * each band height in {6, 12, 24} rows and keeps the fastest.  ty_out (host,
+ * count) receives the choice per instance, us_out (host, 3 per class in order
+ * of first appearance) the timings; either may be NULL.  Overwrites the
+ * working planes; synchronises the stream. */
+pf_status pf_tune_ensemble(pf_ctx* ctx, int reps, int* ty_out, double* us_out);
+
+/* Advance every instance of the packed state (device, in/out) by n_steps
+ * explicit steps (Eq. 12) in the given mode.  PF_ENS_PERSISTENT synchronises
+ * the stream and returns PF_ERR_TIMEOUT if a grid-barrier wait expired
+ * (about one second); the other modes only enqueue. */
+pf_status pf_step_ensemble(pf_ctx* ctx, float* packed_state, int64_t n_steps, int mode);
+
+/* Failure-detection self-test of the bounded grid barrier used by the persistent
+ * ensemble: two co-resident blocks meet at a barrier that also expects
+ * `phantom` (0 or 1) arrivals that never come.  phantom = 0 must return PF_OK;
+ * phantom = 1 must return PF_ERR_TIMEOUT after about limit_cycles SM clocks,
+ * with the context still usable.  dev_scratch: device, 3 unsigned ints. */
+pf_status pf_barrier_selftest(unsigned* dev_scratch, long long limit_cycles, int phantom,
+                              void* stream);
+
 /* Discrete free energy E_h = sum_e sum_q w_q |J| [f(U_q) + kappa/2 |grad U_q|^2]
  * (Eq. 5-6) and, per field, the mass integral sum_i m_i U_i, accumulated in FP64.
  * energy: host, 1 double; mass: host, n_fields doubles (either may be NULL).

@@ -14,8 +14,11 @@ from __future__ import annotations
 import torch
 
 from . import _lib
-from ._lib import (PF_MODEL_AC, PF_MODEL_CH, PF_MODEL_FANCHEN, pf_adjoint,  # noqa: F401
-                   pf_adjoint_workspace, pf_bind_workspace, pf_create_mesh, pf_destroy,
+from ._lib import (PF_ENS_PER_STEP, PF_ENS_PERSISTENT, PF_ENS_PLAIN,  # noqa: F401
+                   PF_MODEL_AC, PF_MODEL_CH, PF_MODEL_FANCHEN, pf_adjoint,
+                   pf_adjoint_workspace, pf_barrier_selftest, pf_bind_workspace,
+                   pf_create_ensemble, pf_create_mesh, pf_destroy, pf_set_ensemble_params,
+                   pf_step_ensemble, pf_tune_ensemble,
                    pf_energy, pf_energy2d_static,
                    pf_implicit_residual, pf_jvp, pf_last_error, pf_set_params, pf_step_explicit,
                    pf_step_implicit)
@@ -135,6 +138,70 @@ class Solver:
         st, e, m = pf_energy(self._ctx, self._state(state))
         self._check(st)
         return e, m
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            pf_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Ensemble:
+    """A batch of independent 2-D Allen-Cahn meshes advanced together.
+
+    shapes: list of (ny, nx); params: list of dicts (W, kappa, L, dt).  The
+    packed state is one float32 CUDA tensor; instance i is
+    state[offsets[i]:offsets[i+1]].view(shapes[i]).
+    """
+
+    MODES = {"persistent": PF_ENS_PERSISTENT, "per_step": PF_ENS_PER_STEP, "plain": PF_ENS_PLAIN}
+
+    def __init__(self, shapes, device="cuda", stream=None):
+        self.shapes = [tuple(int(v) for v in s) for s in shapes]
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        st, self._ctx, ws, self.offsets = pf_create_ensemble(
+            [s[1] for s in self.shapes], [s[0] for s in self.shapes], None,
+            self.stream.cuda_stream)
+        if st != 0:
+            raise PFError(st, "pf_create_ensemble rejected the instances")
+        self._ws = torch.empty(max(ws, 256), dtype=torch.uint8, device=self.device)
+        self._check(pf_bind_workspace(self._ctx, self._ws.data_ptr(), self._ws.numel()))
+        self.nclasses = len(set(self.shapes))
+
+    def _check(self, st):
+        if st != 0:
+            raise PFError(st, pf_last_error(self._ctx))
+
+    def set_params(self, params, shift=0.5):
+        ps = [_lib.pf_params(p["W"], p["kappa"], p["L"], p["dt"], 1.0, 1.0, 1.5, shift, None)
+              for p in params]
+        self._check(pf_set_ensemble_params(self._ctx, ps))
+
+    def tune(self, reps=10):
+        st, ty, us = pf_tune_ensemble(self._ctx, reps, len(self.shapes), self.nclasses)
+        self._check(st)
+        return ty, us
+
+    def pack(self, fields):
+        return torch.cat([torch.as_tensor(f, dtype=torch.float32).reshape(-1) for f in fields]
+                         ).to(self.device).contiguous()
+
+    def unpack(self, state):
+        return [state[self.offsets[i]:self.offsets[i + 1]].view(self.shapes[i])
+                for i in range(len(self.shapes))]
+
+    def step(self, state, n_steps, mode="persistent"):
+        if not (state.is_cuda and state.dtype == torch.float32 and state.is_contiguous()
+                and state.numel() == self.offsets[-1]):
+            raise ValueError("packed state must be a contiguous float32 CUDA tensor")
+        self._check(pf_step_ensemble(self._ctx, state.data_ptr(), n_steps, self.MODES[mode]))
+        return state
 
     def close(self):
         if getattr(self, "_ctx", None):

@@ -24,6 +24,10 @@ PF_MODEL_AC = 0
 PF_MODEL_CH = 1
 PF_MODEL_FANCHEN = 2
 
+PF_ENS_PERSISTENT = 0
+PF_ENS_PER_STEP = 1
+PF_ENS_PLAIN = 2
+
 STATUS_NAMES = {0: "PF_OK", -1: "PF_ERR_ARG", -2: "PF_ERR_CUDA", -3: "PF_ERR_NOT_CONVERGED",
                 -4: "PF_ERR_NONFINITE", -5: "PF_ERR_TIMEOUT", -6: "PF_ERR_STATE"}
 
@@ -86,6 +90,18 @@ def lib():
         L.pf_adjoint.argtypes = [ctx, C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_int,
                                  C.c_void_p, C.c_size_t, C.POINTER(C.c_double),
                                  C.POINTER(C.c_double), C.c_void_p, C.c_void_p]
+        L.pf_create_ensemble.restype = st
+        L.pf_create_ensemble.argtypes = [C.POINTER(ctx), C.c_int, C.POINTER(C.c_int64),
+                                         C.POINTER(C.c_int64), C.POINTER(C.c_double), C.c_void_p,
+                                         C.POINTER(C.c_size_t), C.POINTER(C.c_int64)]
+        L.pf_set_ensemble_params.restype = st
+        L.pf_set_ensemble_params.argtypes = [ctx, C.POINTER(pf_params)]
+        L.pf_tune_ensemble.restype = st
+        L.pf_tune_ensemble.argtypes = [ctx, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]
+        L.pf_step_ensemble.restype = st
+        L.pf_step_ensemble.argtypes = [ctx, C.c_void_p, C.c_int64, C.c_int]
+        L.pf_barrier_selftest.restype = st
+        L.pf_barrier_selftest.argtypes = [C.c_void_p, C.c_longlong, C.c_int, C.c_void_p]
         L.pf_energy.restype = st
         L.pf_energy.argtypes = [ctx, C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.pf_energy2d_static.restype = st
@@ -104,7 +120,8 @@ def exported_symbols():
     """Names declared in include/pf.h (checked against the .so by the tests)."""
     return ["pf_create_mesh", "pf_bind_workspace", "pf_set_params", "pf_step_explicit",
             "pf_step_implicit", "pf_jvp", "pf_implicit_residual", "pf_adjoint_workspace",
-            "pf_adjoint", "pf_energy",
+            "pf_adjoint", "pf_create_ensemble", "pf_set_ensemble_params", "pf_tune_ensemble",
+            "pf_step_ensemble", "pf_barrier_selftest", "pf_energy",
             "pf_energy2d_static", "pf_last_error", "pf_destroy"]
 
 
@@ -163,6 +180,38 @@ def pf_adjoint(ctx, state0_ptr, target_ptr, n_steps, ckpt_every, nodal_loss, ws_
                          C.byref(loss), gs, C.c_void_p(grad_mob_ptr) if grad_mob_ptr else None,
                          C.c_void_p(grad_state0_ptr) if grad_state0_ptr else None)
     return s, loss.value, list(gs)
+
+
+def pf_create_ensemble(nx, ny, h, stream):
+    n = len(nx)
+    ctx = C.c_void_p()
+    ws = C.c_size_t(0)
+    offs = (C.c_int64 * (n + 1))()
+    hh = None if h is None else (C.c_double * (2 * n))(*[v for pair in h for v in pair])
+    s = lib().pf_create_ensemble(C.byref(ctx), n, (C.c_int64 * n)(*nx), (C.c_int64 * n)(*ny), hh,
+                                 C.c_void_p(stream), C.byref(ws), offs)
+    return s, ctx, ws.value, list(offs)
+
+
+def pf_set_ensemble_params(ctx, params):
+    arr = (pf_params * len(params))(*params)
+    return lib().pf_set_ensemble_params(ctx, arr)
+
+
+def pf_tune_ensemble(ctx, reps, count, nclasses):
+    ty = (C.c_int * count)()
+    us = (C.c_double * (3 * nclasses))()
+    s = lib().pf_tune_ensemble(ctx, reps, ty, us)
+    return s, list(ty), list(us)
+
+
+def pf_step_ensemble(ctx, state_ptr, n_steps, mode):
+    return lib().pf_step_ensemble(ctx, C.c_void_p(state_ptr), int(n_steps), int(mode))
+
+
+def pf_barrier_selftest(scratch_ptr, limit_cycles, phantom, stream):
+    return lib().pf_barrier_selftest(C.c_void_p(scratch_ptr), int(limit_cycles), int(phantom),
+                                     C.c_void_p(stream))
 
 
 def pf_energy(ctx, state_ptr):

@@ -240,8 +240,16 @@ __device__ __forceinline__ void store_out(float* __restrict__ base0, int64_t pit
 
 // One warp task: the band of kTY output rows starting at y0, columns of
 // warp column bx.
-template <bool kCH, bool kIso, int kTY>
-__device__ __forceinline__ void sweep_task(const Explicit2DArgs& a, int bx, int y0) {
+template <bool kCoherent>
+__device__ __forceinline__ u64 ld_row(const float* p) {
+  // coherent (L2) loads when the planes were written earlier in the same launch
+  return kCoherent ? __ldcg(reinterpret_cast<const u64*>(p))
+                   : __ldg(reinterpret_cast<const u64*>(p));
+}
+
+template <bool kCH, bool kIso, int kTY, bool kCoherent = false>
+__device__ __forceinline__ void sweep_task(const Explicit2DArgs& a, const float* in, float* out,
+                                           const Coef& K, int bx, int y0) {
   constexpr int kLag = kCH ? 2 : 1;
   constexpr int kWarm = 2 * kLag;  // rows consumed before the first finished row
   const int lane = threadIdx.x & 31;
@@ -254,15 +262,14 @@ __device__ __forceinline__ void sweep_task(const Explicit2DArgs& a, int bx, int 
   const bool ghost_rows = y0 <= 2 || y0 + kTY + 3 >= ny;
   const bool plain = writer && !ghost_cols && !ghost_rows;
   // origin of the real mesh inside the ghost-padded planes
-  const float* __restrict__ in0 = a.in + kGhost * pitch + kGhost;
-  float* __restrict__ out0 = a.out + kGhost * pitch + kGhost;
+  const float* __restrict__ in0 = in + kGhost * pitch + kGhost;
+  float* __restrict__ out0 = out + kGhost * pitch + kGhost;
   const float* src = in0 + (int64_t)(y0 - kLag) * pitch + x;
-  const Coef K{a.pair};
   Window w;
   u64 ahead[kAhead];  // rows k .. k+kAhead-1 in flight
 #pragma unroll
   for (int j = 0; j < kAhead; ++j) {
-    ahead[j] = __ldg(reinterpret_cast<const u64*>(src));
+    ahead[j] = ld_row<kCoherent>(src);
     src += pitch;
   }
 #pragma unroll
@@ -270,7 +277,7 @@ __device__ __forceinline__ void sweep_task(const Explicit2DArgs& a, int bx, int 
     const u64 P = ahead[0];
 #pragma unroll
     for (int j = 0; j + 1 < kAhead; ++j) ahead[j] = ahead[j + 1];
-    ahead[kAhead - 1] = __ldg(reinterpret_cast<const u64*>(src));
+    ahead[kAhead - 1] = ld_row<kCoherent>(src);
     src += pitch;
     sweep_row<kCH, kIso>(P, w, K);
   }
@@ -279,7 +286,7 @@ __device__ __forceinline__ void sweep_task(const Explicit2DArgs& a, int bx, int 
     const u64 P = ahead[0];
 #pragma unroll
     for (int j = 0; j + 1 < kAhead; ++j) ahead[j] = ahead[j + 1];
-    ahead[kAhead - 1] = __ldg(reinterpret_cast<const u64*>(src));
+    ahead[kAhead - 1] = ld_row<kCoherent>(src);
     src += pitch;
     const u64 o = sweep_row<kCH, kIso>(P, w, K);
     const int y = y0 + it;
@@ -296,7 +303,148 @@ template <bool kCH, bool kIso, int kTY>
 __global__ void __launch_bounds__(kWarps * 32) k_explicit2d(const Explicit2DArgs a) {
   const int warp = threadIdx.x >> 5;
   const int y0 = (blockIdx.y * kWarps + warp) * kTY;
-  if (y0 < a.ny) sweep_task<kCH, kIso, kTY>(a, blockIdx.x, y0);
+  if (y0 < a.ny) sweep_task<kCH, kIso, kTY>(a, a.in, a.out, Coef{a.pair}, blockIdx.x, y0);
+}
+
+// ---------------------------------------------------------------------------
+// Batched ensembles of independent 2-D Allen-Cahn instances (different sizes
+// and parameters).  Every instance has its own ghost-padded planes A/B and its
+// own packed coefficients; the warp tasks of all instances -- (instance,
+// column of 60, band of ty rows) -- form one list, so one launch advances the
+// whole ensemble.  The persistent form keeps one launch resident for all
+// steps, with a bounded grid barrier between steps.
+
+template <bool kIso, bool kCoherent>
+__device__ __forceinline__ void ensemble_task(const EnsTask& t, const Explicit2DArgs* inst,
+                                              int parity) {
+  const Explicit2DArgs& a = inst[t.inst];
+  unsigned long long pair[19];
+#pragma unroll
+  for (int i = 0; i < 19; ++i) pair[i] = a.pair[i];
+  const Coef K{pair};
+  const float* in = parity ? a.out : a.in;
+  float* out = parity ? const_cast<float*>(a.in) : a.out;
+  switch (t.ty) {
+    case 6: sweep_task<false, kIso, 6, kCoherent>(a, in, out, K, t.bx, t.y0); break;
+    case 12: sweep_task<false, kIso, 12, kCoherent>(a, in, out, K, t.bx, t.y0); break;
+    default: sweep_task<false, kIso, 24, kCoherent>(a, in, out, K, t.bx, t.y0); break;
+  }
+}
+
+template <bool kIso>
+__global__ void __launch_bounds__(kEnsThreads) k_ensemble_step(const EnsTask* __restrict__ tasks,
+                                                              int ntasks,
+                                                              const Explicit2DArgs* inst,
+                                                              int parity) {
+  const int warps = kEnsThreads / 32;
+  for (int t = blockIdx.x * warps + (threadIdx.x >> 5); t < ntasks; t += gridDim.x * warps)
+    ensemble_task<kIso, false>(tasks[t], inst, parity);
+}
+
+// Grid-wide barrier for a co-resident (cooperative) grid.  bar[0] counts
+// arrivals, bar[1] is the generation, bar[2] the error flag.  A block that
+// waits longer than `limit` clock cycles sets the flag and reports failure.
+__device__ bool grid_barrier(unsigned* bar, long long limit) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned* vgen = bar + 1;
+    const unsigned gen = *vgen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(bar, 1u);
+    if (arrived == gridDim.x - 1) {
+      bar[0] = 0;
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*vgen == gen) {
+        if (clock64() - t0 > limit) {
+          atomicExch(bar + 2, 1u);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+template <bool kIso>
+__global__ void __launch_bounds__(kEnsThreads) k_ensemble_persistent(
+    const EnsTask* __restrict__ tasks, int ntasks, const Explicit2DArgs* inst, int n_steps,
+    unsigned* bar, long long limit) {
+  const int warps = kEnsThreads / 32;
+  for (int s = 0; s < n_steps; ++s) {
+    for (int t = blockIdx.x * warps + (threadIdx.x >> 5); t < ntasks; t += gridDim.x * warps)
+      ensemble_task<kIso, true>(tasks[t], inst, s & 1);
+    if (!grid_barrier(bar, limit)) return;
+  }
+}
+
+// Self-test of the bounded barrier: `extra` phantom arrivals are expected that
+// never come, so every block's wait must expire and set the error flag.
+__global__ void k_barrier_selftest(unsigned* bar, long long limit, int extra) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned* vgen = bar + 1;
+    const unsigned gen = *vgen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(bar, 1u);
+    if (arrived == gridDim.x + extra - 1) {
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*vgen == gen) {
+        if (clock64() - t0 > limit) {
+          atomicExch(bar + 2, 1u);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// all instances' plain states (packed) <-> their padded working planes
+__global__ void k_ens_to_work(const float* __restrict__ packed, const int64_t* __restrict__ off,
+                              const Explicit2DArgs* inst, float sub) {
+  const Explicit2DArgs& a = inst[blockIdx.y];
+  const int nx = a.nx, ny = a.ny;
+  const int64_t pitch = a.pitch, n = pitch * (int64_t)a.rows;
+  const float* in = packed + off[blockIdx.y];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int u = (int)(i % pitch), v = (int)(i / pitch);
+    const int x = u - kGhost, y = v - kGhost;
+    float val = 0.0f;
+    if (x >= -kGhost && x < nx + kGhost && y >= -kGhost && y < ny + kGhost)
+      val = in[(int64_t)reflect_row(y, ny) * nx + reflect_col(x, nx)] - sub;
+    const_cast<float*>(a.in)[i] = val;
+    a.out[i] = val;
+  }
+}
+
+__global__ void k_ens_from_work(float* __restrict__ packed, const int64_t* __restrict__ off,
+                                const Explicit2DArgs* inst, int parity, float add) {
+  const Explicit2DArgs& a = inst[blockIdx.y];
+  const int nx = a.nx;
+  const int64_t n = (int64_t)nx * a.ny;
+  const float* work = parity ? a.out : a.in;
+  float* out = packed + off[blockIdx.y];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % nx), y = (int)(i / nx);
+    out[i] = work[(int64_t)(y + kGhost) * a.pitch + x + kGhost] + add;
+  }
 }
 
 // Plain <-> padded working layout.  Working cell (u, v) holds real node
@@ -379,6 +527,70 @@ void pack_explicit2d(Explicit2DArgs& a) {
   }
 }
 
+cudaError_t launch_ensemble_step(const EnsTask* tasks, int ntasks, const Explicit2DArgs* inst,
+                                 int parity, bool iso, int grid, cudaStream_t s) {
+  if (iso)
+    k_ensemble_step<true><<<grid, kEnsThreads, 0, s>>>(tasks, ntasks, inst, parity);
+  else
+    k_ensemble_step<false><<<grid, kEnsThreads, 0, s>>>(tasks, ntasks, inst, parity);
+  return cudaGetLastError();
+}
+
+int ensemble_persistent_grid(bool iso) {
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  cudaError_t e = iso ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                            &per, k_ensemble_persistent<true>, kEnsThreads, 0)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                            &per, k_ensemble_persistent<false>, kEnsThreads, 0);
+  if (e != cudaSuccess) return 0;
+  return sms * per;
+}
+
+cudaError_t launch_ensemble_persistent(const EnsTask* tasks, int ntasks, const Explicit2DArgs* inst,
+                                       int n_steps, unsigned* bar, long long limit, bool iso,
+                                       int grid, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kEnsThreads);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return iso ? cudaLaunchKernelEx(&cfg, k_ensemble_persistent<true>, tasks, ntasks, inst, n_steps,
+                                  bar, limit)
+             : cudaLaunchKernelEx(&cfg, k_ensemble_persistent<false>, tasks, ntasks, inst, n_steps,
+                                  bar, limit);
+}
+
+cudaError_t launch_ens_to_work(const float* packed, const int64_t* off, const Explicit2DArgs* inst,
+                               int count, float shift, cudaStream_t s) {
+  k_ens_to_work<<<dim3(64, count), 256, 0, s>>>(packed, off, inst, shift);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ens_from_work(float* packed, const int64_t* off, const Explicit2DArgs* inst,
+                                 int count, int parity, float shift, cudaStream_t s) {
+  k_ens_from_work<<<dim3(64, count), 256, 0, s>>>(packed, off, inst, parity, shift);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_barrier_selftest(unsigned* bar, long long limit, int extra, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2);
+  cfg.blockDim = dim3(32);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_barrier_selftest, bar, limit, extra);
+}
+
 int work_pitch(int nx) {
   const int gx = (nx + kOutCols - 1) / kOutCols;
   const int p = gx * kOutCols + 2 * kGhost + 2 * kPair;
@@ -386,8 +598,9 @@ int work_pitch(int nx) {
 }
 
 int work_rows(int ny) {
-  // the last band reads up to kTY + kLag + kAhead rows past its first row
-  const int ty = kTYAc > kTYCh ? kTYAc : kTYCh;
+  // the last band reads up to ty + kLag + kAhead rows past its first row
+  int ty = kTYAc > kTYCh ? kTYAc : kTYCh;
+  if (ty < kMaxEnsTY) ty = kMaxEnsTY;
   return ny + ty + kAhead + 2 * kGhost + 4;
 }
 

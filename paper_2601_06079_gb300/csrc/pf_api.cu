@@ -51,6 +51,21 @@ struct pf_ctx {
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
 
+  // batched ensemble (count > 0): instances' sizes, tuned band heights, device arrays
+  int ens_count = 0;
+  std::vector<int64_t> ens_nx, ens_ny;
+  std::vector<double> ens_hx, ens_hy;
+  std::vector<int> ens_ty;
+  std::vector<int64_t> ens_off;                 // packed-state offsets (count + 1)
+  std::vector<pf::Explicit2DArgs> ens_args;     // host copy of the per-instance arguments
+  std::vector<pf::EnsTask> ens_host_tasks;
+  pf::Explicit2DArgs* ens_dargs = nullptr;
+  pf::EnsTask* ens_tasks = nullptr;
+  int64_t* ens_doff = nullptr;
+  unsigned* ens_bar = nullptr;
+  int ens_ntasks = 0;
+  bool ens_iso = true;
+
   std::string err;
 };
 
@@ -270,6 +285,68 @@ AdjLayout adj_layout(const pf_ctx* c, int64_t n_steps, int ckpt) {
   return L;
 }
 
+// ---- batched ensembles of 2-D Allen-Cahn instances --------------------------
+
+struct EnsLayout {
+  std::vector<size_t> plane;  // offset of instance i's plane A (B follows)
+  std::vector<size_t> plane_bytes;
+  size_t args, tasks, offs, bar, total;
+  int max_tasks;
+};
+
+int ens_tasks_for(int nx, int ny, int ty) {
+  return ((nx + pf::kEnsOutCols - 1) / pf::kEnsOutCols) * ((ny + ty - 1) / ty);
+}
+
+EnsLayout ens_layout(const pf_ctx* c) {
+  EnsLayout L;
+  size_t off = 0;
+  L.max_tasks = 0;
+  for (int i = 0; i < c->ens_count; ++i) {
+    const int nx = (int)c->ens_nx[i], ny = (int)c->ens_ny[i];
+    const size_t b = align_up(sizeof(float) * (size_t)pf::work_pitch(nx) * pf::work_rows(ny), 256);
+    L.plane.push_back(off);
+    L.plane_bytes.push_back(b);
+    off += 2 * b;
+    L.max_tasks += ens_tasks_for(nx, ny, 6);
+  }
+  L.args = off;
+  off += align_up(sizeof(pf::Explicit2DArgs) * c->ens_count, 256);
+  L.tasks = off;
+  off += align_up(sizeof(pf::EnsTask) * (size_t)L.max_tasks, 256);
+  L.offs = off;
+  off += align_up(sizeof(int64_t) * (c->ens_count + 1), 256);
+  L.bar = off;
+  off += 256;
+  L.total = off;
+  return L;
+}
+
+std::vector<pf::EnsTask> ens_build_tasks(const pf_ctx* c, const std::vector<int>& which) {
+  std::vector<pf::EnsTask> t;
+  for (int i : which) {
+    const int nx = (int)c->ens_nx[i], ny = (int)c->ens_ny[i], ty = c->ens_ty[i];
+    const int gx = (nx + pf::kEnsOutCols - 1) / pf::kEnsOutCols;
+    for (int y0 = 0; y0 < ny; y0 += ty)
+      for (int bx = 0; bx < gx; ++bx) t.push_back(pf::EnsTask{i, bx, y0, ty});
+  }
+  return t;
+}
+
+pf_status ens_upload_tasks(pf_ctx* c, const std::vector<pf::EnsTask>& t) {
+  c->ens_ntasks = (int)t.size();
+  c->ens_host_tasks = t;
+  PF_CUDA(cudaMemcpyAsync(c->ens_tasks, c->ens_host_tasks.data(), sizeof(pf::EnsTask) * t.size(),
+                          cudaMemcpyHostToDevice, c->stream));
+  PF_CUDA(cudaStreamSynchronize(c->stream));
+  return PF_OK;
+}
+
+int ens_step_grid(int ntasks) {
+  const int warps = pf::kEnsThreads / 32;
+  return std::max(1, (ntasks + warps - 1) / warps);
+}
+
 // ---- 3-D: residual / JVP launches, explicit steps, Newton-GMRES -----------
 
 pf_status check_ready(pf_ctx* c) {
@@ -465,6 +542,21 @@ pf_status pf_bind_workspace(pf_ctx* c, void* dev_ptr, size_t bytes) {
     return fail(c, PF_ERR_ARG, "workspace must be a non-null 256-byte aligned device pointer");
   if (bytes < c->ws_bytes)
     return fail(c, PF_ERR_ARG, "workspace too small: %zu < %zu bytes", bytes, c->ws_bytes);
+  if (c->ens_count > 0) {
+    const EnsLayout E = ens_layout(c);
+    c->ws = (char*)dev_ptr;
+    for (int i = 0; i < c->ens_count; ++i) {
+      pf::Explicit2DArgs& x = c->ens_args[i];
+      x.in = (float*)(c->ws + E.plane[i]);
+      x.out = (float*)(c->ws + E.plane[i] + E.plane_bytes[i]);
+    }
+    c->ens_dargs = (pf::Explicit2DArgs*)(c->ws + E.args);
+    c->ens_tasks = (pf::EnsTask*)(c->ws + E.tasks);
+    c->ens_doff = (int64_t*)(c->ws + E.offs);
+    c->ens_bar = (unsigned*)(c->ws + E.bar);
+    destroy_graph(c);
+    return PF_OK;
+  }
   const Layout L = layout(c);
   c->ws = (char*)dev_ptr;
   c->partials = (double*)(c->ws + L.partials);
@@ -674,6 +766,231 @@ pf_status pf_step_implicit(pf_ctx* c, float* state, int64_t n_steps, const float
   PF_CUDA(cudaStreamSynchronize(c->stream));
   if (stats) *stats = s;
   return PF_OK;
+}
+
+pf_status pf_create_ensemble(pf_ctx** out, int count, const int64_t* nx, const int64_t* ny,
+                             const double* h, void* stream, size_t* workspace_bytes,
+                             int64_t* offsets) {
+  if (!out || !nx || !ny || !workspace_bytes || count < 1 || count > (1 << 20)) return PF_ERR_ARG;
+  *out = nullptr;
+  int64_t total = 0;
+  for (int i = 0; i < count; ++i) {
+    if (nx[i] < 4 || ny[i] < 4 || nx[i] > (1 << 20) || ny[i] > (1 << 20)) return PF_ERR_ARG;
+    if (h && (!(h[2 * i] > 0) || !(h[2 * i + 1] > 0))) return PF_ERR_ARG;
+    total += nx[i] * ny[i];
+    if (total > ((int64_t)1 << 33)) return PF_ERR_ARG;
+  }
+  pf_ctx* c = new (std::nothrow) pf_ctx();
+  if (!c) return PF_ERR_ARG;
+  c->dim = 2;
+  c->model = PF_MODEL_AC;
+  c->nf = 1;
+  c->stream = (cudaStream_t)stream;
+  c->ens_count = count;
+  c->ens_off.push_back(0);
+  for (int i = 0; i < count; ++i) {
+    c->ens_nx.push_back(nx[i]);
+    c->ens_ny.push_back(ny[i]);
+    c->ens_hx.push_back(h ? h[2 * i] : 1.0);
+    c->ens_hy.push_back(h ? h[2 * i + 1] : 1.0);
+    c->ens_ty.push_back(12);
+    c->ens_off.push_back(c->ens_off.back() + nx[i] * ny[i]);
+    pf::Explicit2DArgs x{};
+    x.nx = (int)nx[i];
+    x.ny = (int)ny[i];
+    x.pitch = pf::work_pitch(x.nx);
+    x.rows = pf::work_rows(x.ny);
+    c->ens_args.push_back(x);
+  }
+  c->n[0] = nx[0];
+  c->n[1] = ny[0];
+  c->ws_bytes = ens_layout(c).total;
+  *workspace_bytes = c->ws_bytes;
+  if (offsets)
+    for (int i = 0; i <= count; ++i) offsets[i] = c->ens_off[i];
+  *out = c;
+  return PF_OK;
+}
+
+pf_status pf_set_ensemble_params(pf_ctx* c, const pf_params* p) {
+  if (!c) return PF_ERR_ARG;
+  if (c->ens_count < 1) return fail(c, PF_ERR_ARG, "not an ensemble context");
+  if (!c->ws) return fail(c, PF_ERR_STATE, "no workspace bound");
+  if (!p) return fail(c, PF_ERR_ARG, "params is NULL");
+  c->ens_iso = true;
+  for (int i = 0; i < c->ens_count; ++i) {
+    const pf_params& q = p[i];
+    if (!(q.dt > 0.0) || !(q.kappa >= 0.0) || !(q.mobility > 0.0) || !(q.W >= 0.0) ||
+        !std::isfinite(q.dt) || !std::isfinite(q.kappa) || !std::isfinite(q.mobility) ||
+        !std::isfinite(q.W) || !std::isfinite(q.shift) || q.mobility_field)
+      return fail(c, PF_ERR_ARG, "invalid parameters for instance %d", i);
+    if (q.shift != p[0].shift) return fail(c, PF_ERR_ARG, "all instances must share one shift");
+    pf::Explicit2DArgs& a = c->ens_args[i];
+    const double s = q.shift, W = q.W, hx = c->ens_hx[i], hy = c->ens_hy[i], m = hx * hy;
+    const double fp[4] = {W * (2 * s - 6 * s * s + 4 * s * s * s), W * (2 - 12 * s + 12 * s * s),
+                          W * (-12 + 24 * s) / 2, 4 * W};
+    const double f = -q.dt * q.mobility;
+    a.p0 = (float)(f * fp[0] / 4);
+    a.p1 = (float)(f * fp[1] / 4);
+    a.p2 = (float)(f * fp[2] / 4);
+    a.p3 = (float)(f * fp[3] / 4);
+    a.k1 = stiffness2d(hx, hy, f * q.kappa / m);
+    a.k2 = stiffness2d(hx, hy, 0.0);
+    pf::pack_explicit2d(a);
+    if (!(a.k1.cx == a.k1.cd && a.k1.cy == a.k1.cd)) c->ens_iso = false;
+  }
+  c->par = p[0];
+  c->par_set = true;
+  PF_CUDA(cudaMemcpyAsync(c->ens_dargs, c->ens_args.data(),
+                          sizeof(pf::Explicit2DArgs) * c->ens_count, cudaMemcpyHostToDevice,
+                          c->stream));
+  PF_CUDA(cudaMemcpyAsync(c->ens_doff, c->ens_off.data(), sizeof(int64_t) * (c->ens_count + 1),
+                          cudaMemcpyHostToDevice, c->stream));
+  std::vector<int> all(c->ens_count);
+  for (int i = 0; i < c->ens_count; ++i) all[i] = i;
+  return ens_upload_tasks(c, ens_build_tasks(c, all));
+}
+
+pf_status pf_tune_ensemble(pf_ctx* c, int reps, int* ty_out, double* us_out) {
+  if (!c) return PF_ERR_ARG;
+  if (c->ens_count < 1) return fail(c, PF_ERR_ARG, "not an ensemble context");
+  if (!c->ws || !c->par_set) return fail(c, PF_ERR_STATE, "workspace or parameters missing");
+  if (reps < 1) return fail(c, PF_ERR_ARG, "reps must be >= 1");
+  const int cand[3] = {6, 12, 24};
+  // planes hold defined values while timing (the step is data-independent in cost)
+  for (int i = 0; i < c->ens_count; ++i) {
+    const pf::Explicit2DArgs& x = c->ens_args[i];
+    PF_CUDA(cudaMemsetAsync(const_cast<float*>(x.in), 0, sizeof(float) * x.pitch * x.rows, c->stream));
+    PF_CUDA(cudaMemsetAsync(x.out, 0, sizeof(float) * x.pitch * x.rows, c->stream));
+  }
+  cudaEvent_t e0, e1;
+  PF_CUDA(cudaEventCreate(&e0));
+  PF_CUDA(cudaEventCreate(&e1));
+  std::vector<std::pair<int64_t, int64_t>> classes;
+  for (int i = 0; i < c->ens_count; ++i) {
+    auto k = std::make_pair(c->ens_nx[i], c->ens_ny[i]);
+    if (std::find(classes.begin(), classes.end(), k) == classes.end()) classes.push_back(k);
+  }
+  pf_status st = PF_OK;
+  for (size_t ci = 0; ci < classes.size() && st == PF_OK; ++ci) {
+    std::vector<int> members;
+    for (int i = 0; i < c->ens_count; ++i)
+      if (c->ens_nx[i] == classes[ci].first && c->ens_ny[i] == classes[ci].second) members.push_back(i);
+    double best = 1e30;
+    int best_ty = 12;
+    for (int k = 0; k < 3 && st == PF_OK; ++k) {
+      for (int i : members) c->ens_ty[i] = cand[k];
+      st = ens_upload_tasks(c, ens_build_tasks(c, members));
+      if (st != PF_OK) break;
+      const int grid = ens_step_grid(c->ens_ntasks);
+      cudaError_t e = pf::launch_ensemble_step(c->ens_tasks, c->ens_ntasks, c->ens_dargs, 0,
+                                               c->ens_iso, grid, c->stream);  // warm-up
+      if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+      for (int r = 0; r < reps && e == cudaSuccess; ++r)
+        e = pf::launch_ensemble_step(c->ens_tasks, c->ens_ntasks, c->ens_dargs, r & 1, c->ens_iso,
+                                     grid, c->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) {
+        st = cuda_fail(c, e, "ensemble tuning");
+        break;
+      }
+      const double us = 1e3 * ms / reps;
+      if (us_out) us_out[3 * ci + k] = us;
+      if (us < best) {
+        best = us;
+        best_ty = cand[k];
+      }
+    }
+    for (int i : members) c->ens_ty[i] = best_ty;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != PF_OK) return st;
+  if (ty_out)
+    for (int i = 0; i < c->ens_count; ++i) ty_out[i] = c->ens_ty[i];
+  std::vector<int> all(c->ens_count);
+  for (int i = 0; i < c->ens_count; ++i) all[i] = i;
+  destroy_graph(c);
+  return ens_upload_tasks(c, ens_build_tasks(c, all));
+}
+
+pf_status pf_step_ensemble(pf_ctx* c, float* packed, int64_t n_steps, int mode) {
+  if (!c) return PF_ERR_ARG;
+  if (c->ens_count < 1) return fail(c, PF_ERR_ARG, "not an ensemble context");
+  if (!c->ws || !c->par_set) return fail(c, PF_ERR_STATE, "workspace or parameters missing");
+  if (!packed) return fail(c, PF_ERR_ARG, "state is NULL");
+  if (n_steps < 0 || n_steps > INT32_MAX) return fail(c, PF_ERR_ARG, "bad n_steps");
+  if (mode < PF_ENS_PERSISTENT || mode > PF_ENS_PLAIN) return fail(c, PF_ERR_ARG, "bad mode");
+  if (n_steps == 0) return PF_OK;
+  const float shift = (float)c->par.shift;
+  PF_CUDA(pf::launch_ens_to_work(packed, c->ens_doff, c->ens_dargs, c->ens_count, shift, c->stream));
+  if (mode == PF_ENS_PERSISTENT) {
+    const int grid = pf::ensemble_persistent_grid(c->ens_iso);
+    if (grid < 1) return fail(c, PF_ERR_CUDA, "cannot size the persistent grid");
+    PF_CUDA(cudaMemsetAsync(c->ens_bar, 0, 3 * sizeof(unsigned), c->stream));
+    // one persistent launch for all steps, recorded as a one-node CUDA graph
+    if (!c->cap_stream) PF_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    PF_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t le = pf::launch_ensemble_persistent(c->ens_tasks, c->ens_ntasks, c->ens_dargs,
+                                                    (int)n_steps, c->ens_bar, 2000000000LL,
+                                                    c->ens_iso, grid, c->cap_stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(c->cap_stream, &g);
+    if (le != cudaSuccess || ee != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return cuda_fail(c, le != cudaSuccess ? le : ee, "capture persistent ensemble launch");
+    }
+    cudaGraphExec_t ex = nullptr;
+    cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) return cuda_fail(c, ie, "instantiate persistent ensemble graph");
+    cudaError_t re = cudaGraphLaunch(ex, c->stream);
+    cudaGraphExecDestroy(ex);
+    if (re != cudaSuccess) return cuda_fail(c, re, "launch persistent ensemble graph");
+  } else if (mode == PF_ENS_PER_STEP) {
+    const int grid = ens_step_grid(c->ens_ntasks);
+    for (int64_t s = 0; s < n_steps; ++s)
+      PF_CUDA(pf::launch_ensemble_step(c->ens_tasks, c->ens_ntasks, c->ens_dargs, (int)(s & 1),
+                                       c->ens_iso, grid, c->stream));
+  } else {  // plain: the single-instance fused step, one launch per instance and step
+    for (int64_t s = 0; s < n_steps; ++s)
+      for (int i = 0; i < c->ens_count; ++i) {
+        pf::Explicit2DArgs a = c->ens_args[i];
+        if (s & 1) {
+          a.in = a.out;
+          a.out = const_cast<float*>(c->ens_args[i].in);
+        }
+        PF_CUDA(pf::launch_ac2d(a, c->stream));
+      }
+  }
+  PF_CUDA(pf::launch_ens_from_work(packed, c->ens_doff, c->ens_dargs, c->ens_count,
+                                   (int)(n_steps & 1), shift, c->stream));
+  if (mode == PF_ENS_PERSISTENT) {
+    unsigned flag = 0;
+    PF_CUDA(cudaMemcpyAsync(&flag, c->ens_bar + 2, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                            c->stream));
+    PF_CUDA(cudaStreamSynchronize(c->stream));
+    if (flag) return fail(c, PF_ERR_TIMEOUT, "grid barrier wait expired in the persistent ensemble");
+  }
+  return PF_OK;
+}
+
+pf_status pf_barrier_selftest(unsigned* dev_scratch, long long limit_cycles, int phantom,
+                              void* stream) {
+  if (!dev_scratch || limit_cycles < 1 || phantom < 0 || phantom > 1) return PF_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemsetAsync(dev_scratch, 0, 3 * sizeof(unsigned), s) != cudaSuccess) return PF_ERR_CUDA;
+  if (pf::launch_barrier_selftest(dev_scratch, limit_cycles, phantom, s) != cudaSuccess)
+    return PF_ERR_CUDA;
+  unsigned flag = 0;
+  if (cudaMemcpyAsync(&flag, dev_scratch + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return PF_ERR_CUDA;
+  return flag ? PF_ERR_TIMEOUT : PF_OK;
 }
 
 pf_status pf_adjoint_workspace(pf_ctx* c, int64_t n_steps, int ckpt_every, size_t* bytes) {

@@ -29,6 +29,7 @@ struct Explicit2DArgs {
   const float* in;
   float* out;
   int nx, ny;
+  int rows;       // rows of the ghost-padded working planes
   int64_t pitch;  // row pitch of the ghost-padded working planes (floats)
   // f'(shift + d) / 4 as p0 + d (p1 + d (p2 + d p3)), times the stage factor
   float p0, p1, p2, p3;
@@ -42,6 +43,28 @@ struct Explicit2DArgs {
 void pack_explicit2d(Explicit2DArgs& a);
 
 cudaError_t launch_ac2d(const Explicit2DArgs& a, cudaStream_t s);
+
+// Batched ensembles of 2-D Allen-Cahn instances.
+struct EnsTask {
+  int inst;  // instance
+  int bx;    // warp column (60 output columns each)
+  int y0;    // first output row of the band
+  int ty;    // band height: 6, 12 or 24
+};
+constexpr int kEnsThreads = 128;
+constexpr int kMaxEnsTY = 24;
+constexpr int kEnsOutCols = 60;
+cudaError_t launch_ensemble_step(const EnsTask* tasks, int ntasks, const Explicit2DArgs* inst,
+                                 int parity, bool iso, int grid, cudaStream_t s);
+int ensemble_persistent_grid(bool iso);
+cudaError_t launch_barrier_selftest(unsigned* bar, long long limit, int extra, cudaStream_t s);
+cudaError_t launch_ensemble_persistent(const EnsTask* tasks, int ntasks, const Explicit2DArgs* inst,
+                                       int n_steps, unsigned* bar, long long limit, bool iso,
+                                       int grid, cudaStream_t s);
+cudaError_t launch_ens_to_work(const float* packed, const int64_t* off, const Explicit2DArgs* inst,
+                               int count, float shift, cudaStream_t s);
+cudaError_t launch_ens_from_work(float* packed, const int64_t* off, const Explicit2DArgs* inst,
+                                 int count, int parity, float shift, cudaStream_t s);
 cudaError_t launch_ch2d(const Explicit2DArgs& a, cudaStream_t s);
 // Ghost-padded working planes: work_pitch(nx) x work_rows(ny) floats each.
 int work_pitch(int nx);

@@ -1,0 +1,97 @@
+"""Batched ensembles of 2-D Allen-Cahn instances (uneven sizes, per-instance
+W, kappa, L): every stepping mode against the FP64 oracle, bitwise agreement
+between the modes and before/after autotuning, and the bounded-barrier
+failure path."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import pf_inputs as G
+
+pytestmark = pytest.mark.gpu
+
+
+def _pf():
+    import paper_2601_06079_gb300 as pf
+    return pf
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+SHAPES = [(64, 64), (37, 100), (128, 128), (91, 37), (130, 256), (4, 5)]
+
+
+def make(shapes, seed=1):
+    pf = _pf()
+    e = pf.Ensemble(shapes)
+    inst = G.batched_instances(seed, count=len(shapes))
+    params = [dict(W=p["W"], kappa=p["kappa"], L=p["L"], dt=0.01) for p in inst]
+    e.set_params(params)
+    fields = [G.ac_initial(seed + i, s) for i, s in enumerate(shapes)]
+    return e, params, fields
+
+
+@pytest.mark.parametrize("mode", ["persistent", "per_step", "plain"])
+def test_modes_match_oracle(mode):
+    e, params, fields = make(SHAPES)
+    st = e.pack(fields)
+    e.step(st, 30, mode)
+    torch.cuda.synchronize()
+    for f, p, out in zip(fields, params, e.unpack(st)):
+        ref = O.Problem(f.shape, W=p["W"], kappa=p["kappa"], mob=p["L"]).ac_explicit(f, 0.01, 30)
+        assert rel(out.cpu().numpy(), ref) <= 1e-5
+
+
+def test_modes_agree_bitwise_and_tuning_keeps_results():
+    e, params, fields = make(SHAPES, seed=3)
+    outs = {}
+    for mode in ("plain", "per_step", "persistent"):
+        st = e.pack(fields)
+        e.step(st, 17, mode)
+        outs[mode] = st.clone()
+    assert torch.equal(outs["plain"], outs["per_step"])
+    assert torch.equal(outs["plain"], outs["persistent"])
+    ty, us = e.tune(reps=3)
+    assert set(ty) <= {6, 12, 24} and all(u > 0 for u in us)
+    st = e.pack(fields)
+    e.step(st, 17, "persistent")
+    assert torch.equal(st, outs["plain"])
+
+
+def test_256_instance_ensemble_1000_steps():
+    pf = _pf()
+    inst = G.batched_instances(1, count=256)
+    shapes = [(p["n"], p["n"]) for p in inst]
+    e = pf.Ensemble(shapes)
+    params = [dict(W=p["W"], kappa=p["kappa"], L=p["L"], dt=0.01) for p in inst]
+    e.set_params(params)
+    e.tune(reps=3)
+    fields = [G.ac_initial(100 + i, s) for i, s in enumerate(shapes)]
+    st = e.pack(fields)
+    e.step(st, 1000, "persistent")
+    out = e.unpack(st)
+    checked = 0
+    for i, s in enumerate(shapes):  # the 128^2 instances are cheap enough for the oracle
+        if s == (128, 128) and checked < 2:
+            p = params[i]
+            ref = O.Problem(s, W=p["W"], kappa=p["kappa"], mob=p["L"]).ac_explicit(
+                fields[i], 0.01, 1000)
+            assert rel(out[i].cpu().numpy(), ref) <= 1e-5
+            checked += 1
+    assert checked == 2
+    st2 = e.pack(fields)
+    e.step(st2, 1000, "per_step")
+    assert torch.equal(st, st2)
+
+
+def test_bounded_barrier_reports_timeout_and_context_survives():
+    pf = _pf()
+    scratch = torch.zeros(4, dtype=torch.int32, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    assert pf.pf_barrier_selftest(scratch.data_ptr(), 20_000_000, 0, s) == pf._lib.PF_OK
+    assert pf.pf_barrier_selftest(scratch.data_ptr(), 2_000_000, 1, s) == pf._lib.PF_ERR_TIMEOUT
+    x = torch.ones(8, device="cuda") * 2
+    assert float(x.sum()) == 16.0  # the context still works
