@@ -82,6 +82,10 @@ def lib():
         L.or_newton.argtypes = [M, Pp, C.c_double, P, P, C.c_double, C.c_int, C.c_int,
                                 C.c_double, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                 C.POINTER(C.c_double)]
+        I = C.c_int
+        L.or_conv3d_fwd.argtypes = [P, I, I, I, I, P, P, I, P]
+        L.or_conv3d_bwd_data.argtypes = [P, I, I, I, I, P, I, P]
+        L.or_conv3d_bwd_weight.argtypes = [P, I, I, I, I, P, I, P, P]
         L.or_ch_adjoint.restype = C.c_double
         L.or_ch_adjoint.argtypes = [M, Pp, C.c_double, C.c_int64, P, P, C.c_int, P, P, P]
         _LIB = L
@@ -221,3 +225,36 @@ class Problem:
                                    _ptr(target), int(nodal_loss), _ptr(gs),
                                    _ptr(gmf) if want_field else None, _ptr(lam0))
         return loss, dict(kappa=gs[0], W=gs[1], M=gs[2], mob_field=gmf, c0=lam0)
+
+
+# ---- 3x3x3 convolution of the learned surrogate (one sample, [C][D][H][W]) ----
+
+def conv3d(x, w, b=None):
+    """y = conv(x, w) + b: 3x3x3 stencil, stride 1, zero padding 1.  w[co][ci][3][3][3]."""
+    x, w = _f64(x), _f64(w)
+    ci, d, h, ww = x.shape
+    co = w.shape[0]
+    y = np.zeros((co, d, h, ww))
+    bb = None if b is None else _f64(b)
+    lib().or_conv3d_fwd(_ptr(x), ci, d, h, ww, _ptr(w), None if bb is None else _ptr(bb), co,
+                        _ptr(y))
+    return y
+
+
+def conv3d_bwd_data(dy, w):
+    dy, w = _f64(dy), _f64(w)
+    co, d, h, ww = dy.shape
+    ci = w.shape[1]
+    dx = np.zeros((ci, d, h, ww))
+    lib().or_conv3d_bwd_data(_ptr(dy), co, d, h, ww, _ptr(w), ci, _ptr(dx))
+    return dx
+
+
+def conv3d_bwd_weight(x, dy):
+    x, dy = _f64(x), _f64(dy)
+    ci, d, h, ww = x.shape
+    co = dy.shape[0]
+    dw = np.zeros((co, ci, 3, 3, 3))
+    db = np.zeros(co)
+    lib().or_conv3d_bwd_weight(_ptr(x), ci, d, h, ww, _ptr(dy), co, _ptr(dw), _ptr(db))
+    return dw, db

@@ -603,3 +603,73 @@ double or_ch_adjoint(const or_mesh* m, const or_params* p, double dt, int64_t ns
   free(traj); free(mass); free(mu); free(lam); free(y); free(z); free(w); free(t1); free(gm);
   return loss;
 }
+
+/* ---- 3x3x3 convolution, stride 1, zero padding 1 (surrogate layers) -------
+ * y[o][z][yy][x] = bias[o] + sum_{i, kz, ky, kx} w[o][i][kz][ky][kx] x[i][z+kz-1][yy+ky-1][x+kx-1]
+ * with x = 0 outside the volume.  The two backward routines are the exact
+ * transposes: dx = W^T dy and dW = dy x^T (summed over voxels), dbias = sum dy. */
+
+static double xat(const double* x, int d, int h, int w, int i, int z, int y, int xx) {
+  if (z < 0 || z >= d || y < 0 || y >= h || xx < 0 || xx >= w) return 0.0;
+  return x[(((int64_t)i * d + z) * h + y) * w + xx];
+}
+
+void or_conv3d_fwd(const double* x, int ci, int d, int h, int w, const double* wt,
+                   const double* bias, int co, double* y) {
+#pragma omp parallel for collapse(2)
+  for (int o = 0; o < co; ++o)
+    for (int z = 0; z < d; ++z)
+      for (int yy = 0; yy < h; ++yy)
+        for (int xx = 0; xx < w; ++xx) {
+          double s = bias ? bias[o] : 0.0;
+          for (int i = 0; i < ci; ++i)
+            for (int kz = 0; kz < 3; ++kz)
+              for (int ky = 0; ky < 3; ++ky)
+                for (int kx = 0; kx < 3; ++kx)
+                  s += wt[((((int64_t)o * ci + i) * 3 + kz) * 3 + ky) * 3 + kx] *
+                       xat(x, d, h, w, i, z + kz - 1, yy + ky - 1, xx + kx - 1);
+          y[(((int64_t)o * d + z) * h + yy) * w + xx] = s;
+        }
+}
+
+void or_conv3d_bwd_data(const double* dy, int co, int d, int h, int w, const double* wt, int ci,
+                        double* dx) {
+  /* dx[i][p] = sum_{o, k} w[o][i][k] dy[o][p - k + 1]  (the transpose of the forward map) */
+#pragma omp parallel for collapse(2)
+  for (int i = 0; i < ci; ++i)
+    for (int z = 0; z < d; ++z)
+      for (int yy = 0; yy < h; ++yy)
+        for (int xx = 0; xx < w; ++xx) {
+          double s = 0.0;
+          for (int o = 0; o < co; ++o)
+            for (int kz = 0; kz < 3; ++kz)
+              for (int ky = 0; ky < 3; ++ky)
+                for (int kx = 0; kx < 3; ++kx)
+                  s += wt[((((int64_t)o * ci + i) * 3 + kz) * 3 + ky) * 3 + kx] *
+                       xat(dy, d, h, w, o, z - kz + 1, yy - ky + 1, xx - kx + 1);
+          dx[(((int64_t)i * d + z) * h + yy) * w + xx] = s;
+        }
+}
+
+void or_conv3d_bwd_weight(const double* x, int ci, int d, int h, int w, const double* dy, int co,
+                          double* dwt, double* dbias) {
+#pragma omp parallel for collapse(2)
+  for (int o = 0; o < co; ++o)
+    for (int i = 0; i < ci; ++i)
+      for (int k = 0; k < 27; ++k) {
+        const int kz = k / 9, ky = (k / 3) % 3, kx = k % 3;
+        double s = 0.0;
+        for (int z = 0; z < d; ++z)
+          for (int yy = 0; yy < h; ++yy)
+            for (int xx = 0; xx < w; ++xx)
+              s += dy[(((int64_t)o * d + z) * h + yy) * w + xx] *
+                   xat(x, d, h, w, i, z + kz - 1, yy + ky - 1, xx + kx - 1);
+        dwt[(((int64_t)o * ci + i) * 27) + k] = s;
+      }
+  if (dbias)
+    for (int o = 0; o < co; ++o) {
+      double s = 0.0;
+      for (int64_t p = 0; p < (int64_t)d * h * w; ++p) s += dy[(int64_t)o * d * h * w + p];
+      dbias[o] = s;
+    }
+}

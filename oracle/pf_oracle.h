@@ -62,4 +62,13 @@ int or_newton(const or_mesh* m, const or_params* p, double dt, const double* Un,
 double or_ch_adjoint(const or_mesh* m, const or_params* p, double dt, int64_t nsteps,
                      const double* c0, const double* target, int nodal_loss,
                      double* grad_scalars, double* grad_mob_field, double* lambda0);
+/* 3-D convolution with a 3x3x3 kernel, stride 1, zero padding of 1 (the layer
+ * of the learned surrogate).  Layouts: x[c][d][h][w] (one sample), weights
+ * w[co][ci][kz][ky][kx], bias[co]. */
+void or_conv3d_fwd(const double* x, int ci, int d, int h, int w, const double* wt,
+                   const double* bias, int co, double* y);
+void or_conv3d_bwd_data(const double* dy, int co, int d, int h, int w, const double* wt, int ci,
+                        double* dx);
+void or_conv3d_bwd_weight(const double* x, int ci, int d, int h, int w, const double* dy, int co,
+                          double* dwt, double* dbias);
 #endif
