@@ -239,6 +239,44 @@ pf_status pf_energy2d_static(const float* state, int64_t nx, int64_t ny, double 
                              double W, double kappa, double* out, void* stream,
                              const char** err);
 
+/* ---- Learned warm start for the implicit step (no counterpart in the paper) ----
+ * A 3-D U-Net (4 levels, 32 channels, 3x3x3 convolutions, BF16 operands, FP32
+ * accumulation; 15 layers) maps U^n (8 order parameters) to an estimate of
+ * U^{n+1} - U^n.  Parameters are an FP32 array of pf_surrogate_param_count()
+ * values: per layer [27][c_out][c_in] weights then c_out biases, in layer order
+ * 16->32, 32->32 x 13, 32->16 (inputs padded 8 -> 16 channels, outputs 16 -> 8).
+ * Fields are planar FP32 [batch][8][d][h][w]; d a multiple of 16, h and w of 64. */
+pf_status pf_surrogate_param_count(int64_t* n_params);
+
+/* Device workspace bytes for one call on [batch][8][d][h][w] (training = 1 adds
+ * the gradient buffers).  Host only. */
+pf_status pf_surrogate_workspace(int batch, int d, int h, int w, int training, size_t* bytes);
+
+/* out = x + net(x): the warm-start guess for U^{n+1}.  All device pointers;
+ * enqueues on `stream`. */
+pf_status pf_surrogate_predict(const float* params, const float* x, float* out, int batch, int d,
+                               int h, int w, void* workspace, size_t bytes, void* stream);
+
+/* One Adam step (lr, beta1 0.9, beta2 0.999, eps 1e-8; step >= 1 for the bias
+ * correction) on the mean-squared error between net(x) and y - x.  params,
+ * adam_m, adam_v: device FP32 (updated in place); loss: host (may be NULL; if
+ * given the stream is synchronised). */
+pf_status pf_surrogate_train_step(float* params, float* adam_m, float* adam_v, int step,
+                                  double lr, const float* x, const float* y, int batch, int d,
+                                  int h, int w, void* workspace, size_t bytes, void* stream,
+                                  double* loss);
+
+/* Single-layer probe of the surrogate's convolution kernels (tests): one sample,
+ * planar FP32 [c][d][h][w]; weights [27][c_out][c_in] FP32 (rounded to BF16
+ * inside).  (c_in, c_out) in {(16,32), (32,32), (32,16)}; d even, h and w
+ * multiples of 8.  mode 0: out = conv(x) + bias; mode 1: out = conv^T(dy);
+ * mode 2: out = [dW (27 x c_out x c_in), db (c_out)] for dy.  Workspace of at
+ * least 2V(c_in + c_out) + 4 * 27 c_in c_out + 128 V + 16,809,984 bytes
+ * (V = d h w, plus 256-byte alignment per part). */
+pf_status pf_conv3d_check(int mode, int cin, int cout, int d, int h, int w, const float* x,
+                          const float* wt, const float* bias, const float* dy, float* out,
+                          void* workspace, size_t bytes, void* stream);
+
 /* Human-readable description of the last failure on this context. */
 const char* pf_last_error(const pf_ctx* ctx);
 

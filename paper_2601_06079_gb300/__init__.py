@@ -18,7 +18,9 @@ from ._lib import (PF_ENS_PER_STEP, PF_ENS_PERSISTENT, PF_ENS_PLAIN,  # noqa: F4
                    PF_MODEL_AC, PF_MODEL_CH, PF_MODEL_FANCHEN, pf_adjoint,
                    pf_adjoint_workspace, pf_barrier_selftest, pf_bind_workspace,
                    pf_create_ensemble, pf_create_mesh, pf_destroy, pf_set_ensemble_params,
-                   pf_step_ensemble, pf_tune_ensemble,
+                   pf_step_ensemble, pf_tune_ensemble, pf_surrogate_param_count,
+                   pf_surrogate_workspace, pf_surrogate_predict, pf_surrogate_train_step,
+                   pf_conv3d_check,
                    pf_energy, pf_energy2d_static,
                    pf_implicit_residual, pf_jvp, pf_last_error, pf_set_params, pf_step_explicit,
                    pf_step_implicit)
@@ -213,6 +215,88 @@ class Ensemble:
             self.close()
         except Exception:
             pass
+
+
+class Surrogate:
+    """Learned warm start for the implicit step (a 3-D conv U-Net, see
+    pf_surrogate_* in include/pf.h).  Parameters live in FP32 CUDA tensors;
+    init() draws them from a seeded He-normal recipe (input channels 8-15 and
+    output channels 8-15 are zero and stay zero)."""
+
+    LAYERS = [(16, 32)] + [(32, 32)] * 13 + [(32, 16)]
+
+    def __init__(self, device="cuda", stream=None):
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        st, self.n_params = pf_surrogate_param_count()
+        if st != 0:
+            raise PFError(st, "pf_surrogate_param_count")
+        self.params = torch.zeros(self.n_params, dtype=torch.float32, device=self.device)
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.step = 0
+        self._ws = {}
+
+    def init(self, seed=0, out_scale=0.1):
+        import numpy as np
+
+        import pf_inputs as G
+        chunks = []
+        for l, (ci, co) in enumerate(self.LAYERS):
+            fan_in = 27 * (8 if l == 0 else ci)
+            z = G.uniform(seed * 1000 + l, 27 * co * ci * 2, 0.0, 1.0, "surrogate")
+            u1, u2 = np.maximum(z[0::2], 1e-12), z[1::2]
+            normal = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)  # Box-Muller
+            w = (normal * np.sqrt(2.0 / fan_in)).reshape(27, co, ci)
+            if l == 0:
+                w[:, :, 8:] = 0.0
+            if l == len(self.LAYERS) - 1:
+                w *= out_scale
+                w[:, 8:, :] = 0.0
+            chunks += [w.ravel(), np.zeros(co)]
+        self.params.copy_(torch.from_numpy(np.concatenate(chunks).astype(np.float32)))
+        self.m.zero_()
+        self.v.zero_()
+        self.step = 0
+
+    def _workspace(self, batch, d, h, w, training):
+        key = (batch, d, h, w, bool(training))
+        if key not in self._ws:
+            st, nb = pf_surrogate_workspace(batch, d, h, w, training)
+            if st != 0:
+                raise PFError(st, f"unsupported surrogate volume {key}")
+            self._ws[key] = torch.empty(nb, dtype=torch.uint8, device=self.device)
+        return self._ws[key]
+
+    @staticmethod
+    def _dims(x):
+        b, nf, d, h, w = x.shape
+        if nf != 8:
+            raise ValueError("the surrogate takes 8 order parameters")
+        return b, d, h, w
+
+    def predict(self, x, out=None):
+        """out = x + net(x) for x [batch][8][d][h][w] float32 CUDA."""
+        b, d, h, w = self._dims(x)
+        out = torch.empty_like(x) if out is None else out
+        ws = self._workspace(b, d, h, w, False)
+        st = pf_surrogate_predict(self.params.data_ptr(), x.data_ptr(), out.data_ptr(), b, d, h, w,
+                                  ws.data_ptr(), ws.numel(), self.stream.cuda_stream)
+        if st != 0:
+            raise PFError(st, "pf_surrogate_predict")
+        return out
+
+    def train_step(self, x, y, lr=1e-3):
+        b, d, h, w = self._dims(x)
+        ws = self._workspace(b, d, h, w, True)
+        self.step += 1
+        st, loss = pf_surrogate_train_step(self.params.data_ptr(), self.m.data_ptr(),
+                                           self.v.data_ptr(), self.step, lr, x.data_ptr(),
+                                           y.data_ptr(), b, d, h, w, ws.data_ptr(), ws.numel(),
+                                           self.stream.cuda_stream)
+        if st != 0:
+            raise PFError(st, "pf_surrogate_train_step")
+        return loss
 
 
 class _CHMisfit(torch.autograd.Function):

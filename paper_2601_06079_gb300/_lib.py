@@ -102,6 +102,23 @@ def lib():
         L.pf_step_ensemble.argtypes = [ctx, C.c_void_p, C.c_int64, C.c_int]
         L.pf_barrier_selftest.restype = st
         L.pf_barrier_selftest.argtypes = [C.c_void_p, C.c_longlong, C.c_int, C.c_void_p]
+        L.pf_surrogate_param_count.restype = st
+        L.pf_surrogate_param_count.argtypes = [C.POINTER(C.c_int64)]
+        L.pf_surrogate_workspace.restype = st
+        L.pf_surrogate_workspace.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                             C.POINTER(C.c_size_t)]
+        L.pf_surrogate_predict.restype = st
+        L.pf_surrogate_predict.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
+                                           C.c_int, C.c_int, C.c_void_p, C.c_size_t, C.c_void_p]
+        L.pf_surrogate_train_step.restype = st
+        L.pf_surrogate_train_step.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                              C.c_double, C.c_void_p, C.c_void_p, C.c_int,
+                                              C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_size_t,
+                                              C.c_void_p, C.POINTER(C.c_double)]
+        L.pf_conv3d_check.restype = st
+        L.pf_conv3d_check.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_void_p, C.c_size_t, C.c_void_p]
         L.pf_energy.restype = st
         L.pf_energy.argtypes = [ctx, C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.pf_energy2d_static.restype = st
@@ -121,7 +138,9 @@ def exported_symbols():
     return ["pf_create_mesh", "pf_bind_workspace", "pf_set_params", "pf_step_explicit",
             "pf_step_implicit", "pf_jvp", "pf_implicit_residual", "pf_adjoint_workspace",
             "pf_adjoint", "pf_create_ensemble", "pf_set_ensemble_params", "pf_tune_ensemble",
-            "pf_step_ensemble", "pf_barrier_selftest", "pf_energy",
+            "pf_step_ensemble", "pf_barrier_selftest", "pf_surrogate_param_count",
+            "pf_surrogate_workspace", "pf_surrogate_predict", "pf_surrogate_train_step",
+            "pf_conv3d_check", "pf_energy",
             "pf_energy2d_static", "pf_last_error", "pf_destroy"]
 
 
@@ -212,6 +231,38 @@ def pf_step_ensemble(ctx, state_ptr, n_steps, mode):
 def pf_barrier_selftest(scratch_ptr, limit_cycles, phantom, stream):
     return lib().pf_barrier_selftest(C.c_void_p(scratch_ptr), int(limit_cycles), int(phantom),
                                      C.c_void_p(stream))
+
+
+def pf_surrogate_param_count():
+    n = C.c_int64(0)
+    s = lib().pf_surrogate_param_count(C.byref(n))
+    return s, n.value
+
+
+def pf_surrogate_workspace(batch, d, h, w, training):
+    b = C.c_size_t(0)
+    s = lib().pf_surrogate_workspace(batch, d, h, w, int(training), C.byref(b))
+    return s, b.value
+
+
+def pf_surrogate_predict(params, x, out, batch, d, h, w, ws, nbytes, stream):
+    return lib().pf_surrogate_predict(C.c_void_p(params), C.c_void_p(x), C.c_void_p(out), batch,
+                                      d, h, w, C.c_void_p(ws), nbytes, C.c_void_p(stream))
+
+
+def pf_surrogate_train_step(params, m, v, step, lr, x, y, batch, d, h, w, ws, nbytes, stream):
+    loss = C.c_double(0)
+    s = lib().pf_surrogate_train_step(C.c_void_p(params), C.c_void_p(m), C.c_void_p(v), step, lr,
+                                      C.c_void_p(x), C.c_void_p(y), batch, d, h, w,
+                                      C.c_void_p(ws), nbytes, C.c_void_p(stream), C.byref(loss))
+    return s, loss.value
+
+
+def pf_conv3d_check(mode, cin, cout, d, h, w, x, wt, bias, dy, out, ws, nbytes, stream):
+    return lib().pf_conv3d_check(mode, cin, cout, d, h, w, C.c_void_p(x), C.c_void_p(wt),
+                                 C.c_void_p(bias) if bias else None,
+                                 C.c_void_p(dy) if dy else None, C.c_void_p(out), C.c_void_p(ws),
+                                 nbytes, C.c_void_p(stream))
 
 
 def pf_energy(ctx, state_ptr):
