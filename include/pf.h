@@ -245,26 +245,40 @@ pf_status pf_energy2d_static(const float* state, int64_t nx, int64_t ny, double 
  * U^{n+1} - U^n.  Parameters are an FP32 array of pf_surrogate_param_count()
  * values: per layer [27][c_out][c_in] weights then c_out biases, in layer order
  * 16->32, 32->32 x 13, 32->16 (inputs padded 8 -> 16 channels, outputs 16 -> 8).
- * Fields are planar FP32 [batch][8][d][h][w]; d a multiple of 16, h and w of 64. */
+ * Inputs are planar FP32 [batch][n_in][d][h][w] with n_in = 8 (the state) or 16
+ * (the state followed by 8 feature channels in the units of an increment, e.g.
+ * the explicit-Euler increment; the network sees them divided by out_scale);
+ * outputs [batch][8][d][h][w]; d a multiple of 16, h and w of 64.  out_scale
+ * must be positive and finite; anything else is PF_ERR_ARG. */
 pf_status pf_surrogate_param_count(int64_t* n_params);
 
 /* Device workspace bytes for one call on [batch][8][d][h][w] (training = 1 adds
  * the gradient buffers).  Host only. */
 pf_status pf_surrogate_workspace(int batch, int d, int h, int w, int training, size_t* bytes);
 
-/* out = x + net(x): the warm-start guess for U^{n+1}.  All device pointers;
- * enqueues on `stream`. */
-pf_status pf_surrogate_predict(const float* params, const float* x, float* out, int batch, int d,
-                               int h, int w, void* workspace, size_t bytes, void* stream);
+/* out = x[:8] + out_scale * net(x): the warm-start guess for U^{n+1}.  out_scale is
+ * the typical size of an increment (the network works on increments of order
+ * one).  All device pointers; enqueues on `stream`. */
+pf_status pf_surrogate_predict(const float* params, float out_scale, const float* x, int n_in,
+                               float* out, int batch, int d, int h, int w, void* workspace,
+                               size_t bytes, void* stream);
 
 /* One Adam step (lr, beta1 0.9, beta2 0.999, eps 1e-8; step >= 1 for the bias
- * correction) on the mean-squared error between net(x) and y - x.  params,
- * adam_m, adam_v: device FP32 (updated in place); loss: host (may be NULL; if
- * given the stream is synchronised). */
-pf_status pf_surrogate_train_step(float* params, float* adam_m, float* adam_v, int step,
-                                  double lr, const float* x, const float* y, int batch, int d,
-                                  int h, int w, void* workspace, size_t bytes, void* stream,
-                                  double* loss);
+ * correction) on the mean-squared error between out_scale * net(x) and y - x[:8].
+ * params, adam_m, adam_v: device FP32 (updated in place); loss: host (may be
+ * NULL; if given the stream is synchronised). */
+pf_status pf_surrogate_train_step(float* params, float out_scale, float* adam_m, float* adam_v,
+                                  int step, double lr, const float* x, int n_in, const float* y,
+                                  int batch, int d, int h, int w, void* workspace, size_t bytes,
+                                  void* stream, double* loss);
+
+/* Loss (as pf_surrogate_train_step) and its gradient with respect to every
+ * parameter, written to grad (device FP32, pf_surrogate_param_count values),
+ * without updating anything.  Workspace: pf_surrogate_workspace(..., training = 1).
+ * loss: host (may be NULL; if given the stream is synchronised). */
+pf_status pf_surrogate_loss_grad(const float* params, float out_scale, const float* x, int n_in,
+                                 const float* y, int batch, int d, int h, int w, void* workspace,
+                                 size_t bytes, void* stream, double* loss, float* grad);
 
 /* Single-layer probe of the surrogate's convolution kernels (tests): one sample,
  * planar FP32 [c][d][h][w]; weights [27][c_out][c_in] FP32 (rounded to BF16

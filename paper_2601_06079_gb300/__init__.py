@@ -20,7 +20,7 @@ from ._lib import (PF_ENS_PER_STEP, PF_ENS_PERSISTENT, PF_ENS_PLAIN,  # noqa: F4
                    pf_create_ensemble, pf_create_mesh, pf_destroy, pf_set_ensemble_params,
                    pf_step_ensemble, pf_tune_ensemble, pf_surrogate_param_count,
                    pf_surrogate_workspace, pf_surrogate_predict, pf_surrogate_train_step,
-                   pf_conv3d_check,
+                   pf_conv3d_check, pf_surrogate_loss_grad,
                    pf_energy, pf_energy2d_static,
                    pf_implicit_residual, pf_jvp, pf_last_error, pf_set_params, pf_step_explicit,
                    pf_step_implicit)
@@ -225,9 +225,10 @@ class Surrogate:
 
     LAYERS = [(16, 32)] + [(32, 32)] * 13 + [(32, 16)]
 
-    def __init__(self, device="cuda", stream=None):
+    def __init__(self, device="cuda", stream=None, features=False):
         self.device = torch.device(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.features = features  # 16 input channels: state + explicit-Euler increment
         st, self.n_params = pf_surrogate_param_count()
         if st != 0:
             raise PFError(st, "pf_surrogate_param_count")
@@ -235,23 +236,24 @@ class Surrogate:
         self.m = torch.zeros_like(self.params)
         self.v = torch.zeros_like(self.params)
         self.step = 0
+        self.out_scale = 1.0  # typical increment size; the network predicts increment / out_scale
         self._ws = {}
 
-    def init(self, seed=0, out_scale=0.1):
+    def init(self, seed=0, last_layer_scale=0.1):
         import numpy as np
 
         import pf_inputs as G
         chunks = []
         for l, (ci, co) in enumerate(self.LAYERS):
-            fan_in = 27 * (8 if l == 0 else ci)
+            fan_in = 27 * (8 if l == 0 and not self.features else ci)
             z = G.uniform(seed * 1000 + l, 27 * co * ci * 2, 0.0, 1.0, "surrogate")
             u1, u2 = np.maximum(z[0::2], 1e-12), z[1::2]
             normal = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)  # Box-Muller
             w = (normal * np.sqrt(2.0 / fan_in)).reshape(27, co, ci)
-            if l == 0:
+            if l == 0 and not self.features:
                 w[:, :, 8:] = 0.0
             if l == len(self.LAYERS) - 1:
-                w *= out_scale
+                w *= last_layer_scale
                 w[:, 8:, :] = 0.0
             chunks += [w.ravel(), np.zeros(co)]
         self.params.copy_(torch.from_numpy(np.concatenate(chunks).astype(np.float32)))
@@ -270,30 +272,43 @@ class Surrogate:
 
     @staticmethod
     def _dims(x):
-        b, nf, d, h, w = x.shape
-        if nf != 8:
-            raise ValueError("the surrogate takes 8 order parameters")
-        return b, d, h, w
+        b, nin, d, h, w = x.shape
+        if nin not in (8, 16):
+            raise ValueError("the surrogate takes 8 order parameters (+ 8 feature channels)")
+        return b, nin, d, h, w
 
     def predict(self, x, out=None):
-        """out = x + net(x) for x [batch][8][d][h][w] float32 CUDA."""
-        b, d, h, w = self._dims(x)
-        out = torch.empty_like(x) if out is None else out
+        """out = x[:, :8] + out_scale * net(x) for x [batch][8 or 16][d][h][w] float32 CUDA."""
+        b, nin, d, h, w = self._dims(x)
+        out = torch.empty((b, 8, d, h, w), device=x.device) if out is None else out
         ws = self._workspace(b, d, h, w, False)
-        st = pf_surrogate_predict(self.params.data_ptr(), x.data_ptr(), out.data_ptr(), b, d, h, w,
-                                  ws.data_ptr(), ws.numel(), self.stream.cuda_stream)
+        st = pf_surrogate_predict(self.params.data_ptr(), self.out_scale, x.data_ptr(), nin,
+                                  out.data_ptr(), b, d, h, w, ws.data_ptr(), ws.numel(),
+                                  self.stream.cuda_stream)
         if st != 0:
             raise PFError(st, "pf_surrogate_predict")
         return out
 
+    def loss_grad(self, x, y):
+        """(loss, gradient tensor) without an update."""
+        b, nin, d, h, w = self._dims(x)
+        ws = self._workspace(b, d, h, w, True)
+        g = torch.empty_like(self.params)
+        st, loss = pf_surrogate_loss_grad(self.params.data_ptr(), self.out_scale, x.data_ptr(),
+                                          nin, y.data_ptr(), b, d, h, w, ws.data_ptr(),
+                                          ws.numel(), self.stream.cuda_stream, g.data_ptr())
+        if st != 0:
+            raise PFError(st, "pf_surrogate_loss_grad")
+        return loss, g
+
     def train_step(self, x, y, lr=1e-3):
-        b, d, h, w = self._dims(x)
+        b, nin, d, h, w = self._dims(x)
         ws = self._workspace(b, d, h, w, True)
         self.step += 1
-        st, loss = pf_surrogate_train_step(self.params.data_ptr(), self.m.data_ptr(),
-                                           self.v.data_ptr(), self.step, lr, x.data_ptr(),
-                                           y.data_ptr(), b, d, h, w, ws.data_ptr(), ws.numel(),
-                                           self.stream.cuda_stream)
+        st, loss = pf_surrogate_train_step(self.params.data_ptr(), self.out_scale,
+                                           self.m.data_ptr(), self.v.data_ptr(), self.step, lr,
+                                           x.data_ptr(), nin, y.data_ptr(), b, d, h, w,
+                                           ws.data_ptr(), ws.numel(), self.stream.cuda_stream)
         if st != 0:
             raise PFError(st, "pf_surrogate_train_step")
         return loss

@@ -108,13 +108,20 @@ def lib():
         L.pf_surrogate_workspace.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                              C.POINTER(C.c_size_t)]
         L.pf_surrogate_predict.restype = st
-        L.pf_surrogate_predict.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
-                                           C.c_int, C.c_int, C.c_void_p, C.c_size_t, C.c_void_p]
+        L.pf_surrogate_predict.argtypes = [C.c_void_p, C.c_float, C.c_void_p, C.c_int, C.c_void_p,
+                                           C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p,
+                                           C.c_size_t, C.c_void_p]
         L.pf_surrogate_train_step.restype = st
-        L.pf_surrogate_train_step.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
-                                              C.c_double, C.c_void_p, C.c_void_p, C.c_int,
-                                              C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_size_t,
-                                              C.c_void_p, C.POINTER(C.c_double)]
+        L.pf_surrogate_train_step.argtypes = [C.c_void_p, C.c_float, C.c_void_p, C.c_void_p,
+                                              C.c_int, C.c_double, C.c_void_p, C.c_int,
+                                              C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
+                                              C.c_void_p, C.c_size_t, C.c_void_p,
+                                              C.POINTER(C.c_double)]
+        L.pf_surrogate_loss_grad.restype = st
+        L.pf_surrogate_loss_grad.argtypes = [C.c_void_p, C.c_float, C.c_void_p, C.c_int,
+                                             C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
+                                             C.c_void_p, C.c_size_t, C.c_void_p,
+                                             C.POINTER(C.c_double), C.c_void_p]
         L.pf_conv3d_check.restype = st
         L.pf_conv3d_check.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -140,6 +147,7 @@ def exported_symbols():
             "pf_adjoint", "pf_create_ensemble", "pf_set_ensemble_params", "pf_tune_ensemble",
             "pf_step_ensemble", "pf_barrier_selftest", "pf_surrogate_param_count",
             "pf_surrogate_workspace", "pf_surrogate_predict", "pf_surrogate_train_step",
+            "pf_surrogate_loss_grad",
             "pf_conv3d_check", "pf_energy",
             "pf_energy2d_static", "pf_last_error", "pf_destroy"]
 
@@ -245,16 +253,28 @@ def pf_surrogate_workspace(batch, d, h, w, training):
     return s, b.value
 
 
-def pf_surrogate_predict(params, x, out, batch, d, h, w, ws, nbytes, stream):
-    return lib().pf_surrogate_predict(C.c_void_p(params), C.c_void_p(x), C.c_void_p(out), batch,
-                                      d, h, w, C.c_void_p(ws), nbytes, C.c_void_p(stream))
+def pf_surrogate_predict(params, out_scale, x, n_in, out, batch, d, h, w, ws, nbytes, stream):
+    return lib().pf_surrogate_predict(C.c_void_p(params), out_scale, C.c_void_p(x), n_in,
+                                      C.c_void_p(out), batch, d, h, w, C.c_void_p(ws), nbytes,
+                                      C.c_void_p(stream))
 
 
-def pf_surrogate_train_step(params, m, v, step, lr, x, y, batch, d, h, w, ws, nbytes, stream):
+def pf_surrogate_train_step(params, out_scale, m, v, step, lr, x, n_in, y, batch, d, h, w, ws,
+                            nbytes, stream):
     loss = C.c_double(0)
-    s = lib().pf_surrogate_train_step(C.c_void_p(params), C.c_void_p(m), C.c_void_p(v), step, lr,
-                                      C.c_void_p(x), C.c_void_p(y), batch, d, h, w,
-                                      C.c_void_p(ws), nbytes, C.c_void_p(stream), C.byref(loss))
+    s = lib().pf_surrogate_train_step(C.c_void_p(params), out_scale, C.c_void_p(m), C.c_void_p(v),
+                                      step, lr, C.c_void_p(x), n_in, C.c_void_p(y), batch, d, h,
+                                      w, C.c_void_p(ws), nbytes, C.c_void_p(stream),
+                                      C.byref(loss))
+    return s, loss.value
+
+
+def pf_surrogate_loss_grad(params, out_scale, x, n_in, y, batch, d, h, w, ws, nbytes, stream,
+                           grad):
+    loss = C.c_double(0)
+    s = lib().pf_surrogate_loss_grad(C.c_void_p(params), out_scale, C.c_void_p(x), n_in,
+                                     C.c_void_p(y), batch, d, h, w, C.c_void_p(ws), nbytes,
+                                     C.c_void_p(stream), C.byref(loss), C.c_void_p(grad))
     return s, loss.value
 
 

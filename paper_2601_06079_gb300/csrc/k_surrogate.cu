@@ -20,24 +20,28 @@ unsigned blocks_for(int64_t n) {
   return (unsigned)(b < 4096 ? b : 4096);
 }
 
-// planar [B][nf][V] FP32 -> NDHWC BF16 [B][V][C] (channels >= nf are zero)
+// planar [B][nf][V] FP32 -> NDHWC BF16 [B][V][C] (channels >= nf are zero;
+// channels k0.. are multiplied by fs)
 __global__ void k_planar_to_ndhwc(const float* __restrict__ in, int nf, int C, int B, int64_t V,
-                                  __nv_bfloat16* __restrict__ out) {
+                                  int k0, float fs, __nv_bfloat16* __restrict__ out) {
   const int64_t n = (int64_t)B * V * C;
   for (int64_t i = gtid(); i < n; i += grid_stride()) {
     const int c = (int)(i % C);
     const int64_t v = (i / C) % V, b = i / (C * V);
-    out[i] = __float2bfloat16(c < nf ? in[(b * nf + c) * V + v] : 0.0f);
+    const float a = c < nf ? in[(b * nf + c) * V + v] : 0.0f;
+    out[i] = __float2bfloat16(c < k0 ? a : a * fs);
   }
 }
 
-// out planar [B][nf][V] = base (planar) + first nf channels of y (NDHWC FP32, C channels)
+// out planar [B][nf][V] = base + a * first nf channels of y (NDHWC FP32, C
+// channels); base is planar with nb channels per sample (its first nf used)
 __global__ void k_ndhwc_to_planar_add(const float* __restrict__ y, int C, int nf, int B, int64_t V,
-                                      const float* __restrict__ base, float* __restrict__ out) {
+                                      const float* __restrict__ base, int nb, float a,
+                                      float* __restrict__ out) {
   const int64_t n = (int64_t)B * nf * V;
   for (int64_t i = gtid(); i < n; i += grid_stride()) {
     const int64_t v = i % V, f = (i / V) % nf, b = i / (nf * V);
-    out[i] = (base ? base[i] : 0.0f) + y[(b * V + v) * C + f];
+    out[i] = fmaf(a, y[(b * V + v) * C + f], base ? base[(b * nb + f) * V + v] : 0.0f);
   }
 }
 
@@ -137,12 +141,14 @@ __global__ void k_relu_mask(__nv_bfloat16* __restrict__ g, const __nv_bfloat16* 
     if (!(__bfloat162float(y[i]) > 0.0f)) g[i] = __float2bfloat16(0.0f);
 }
 
-// Mean-squared loss between the first nf channels of pred (NDHWC FP32, C ch)
-// and target = y - x (planar FP32); writes dL/dpred (NDHWC BF16, zero beyond
-// nf) and per-block partial sums of the squared error.
-__global__ void k_mse(const float* __restrict__ pred, int C, int nf, int B, int64_t V,
-                      const float* __restrict__ x, const float* __restrict__ y, float scale,
-                      __nv_bfloat16* __restrict__ grad, double* __restrict__ partials) {
+// Mean-squared loss between a * (first nf channels of pred) (NDHWC FP32, C ch)
+// and target = y - x (planar FP32, x with nx channels of which the first nf
+// are the state); writes dL/dpred (NDHWC BF16, zero beyond nf) and per-block
+// partial sums of the squared error.
+__global__ void k_mse(const float* __restrict__ pred, int C, int nf, int nxc, int B, int64_t V,
+                      const float* __restrict__ x, const float* __restrict__ y, float a,
+                      float scale, __nv_bfloat16* __restrict__ grad,
+                      double* __restrict__ partials) {
   __shared__ double red[kT];
   double acc = 0.0;
   const int64_t n = (int64_t)B * V * C;
@@ -152,9 +158,9 @@ __global__ void k_mse(const float* __restrict__ pred, int C, int nf, int B, int6
     if (c < nf) {
       const int64_t v = (i / C) % V, b = i / (C * V);
       const int64_t p = (b * nf + c) * V + v;
-      const float r = pred[i] - (y[p] - x[p]);
+      const float r = fmaf(a, pred[i], -(y[p] - x[(b * nxc + c) * V + v]));
       acc += (double)r * r;
-      gval = 2.0f * scale * r;
+      gval = 2.0f * scale * a * r;
     }
     grad[i] = __float2bfloat16(gval);
   }
@@ -204,16 +210,18 @@ __global__ void k_adam(float* __restrict__ p, float* __restrict__ m, float* __re
 
 }  // namespace
 
-cudaError_t launch_planar_to_ndhwc(const float* in, int nf, int C, int B, int64_t V, void* out,
-                                   cudaStream_t s) {
-  k_planar_to_ndhwc<<<blocks_for((int64_t)B * V * C), kT, 0, s>>>(in, nf, C, B, V,
+cudaError_t launch_planar_to_ndhwc(const float* in, int nf, int C, int B, int64_t V, int k0,
+                                   float fs, void* out, cudaStream_t s) {
+  k_planar_to_ndhwc<<<blocks_for((int64_t)B * V * C), kT, 0, s>>>(in, nf, C, B, V, k0, fs,
                                                                   (__nv_bfloat16*)out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_ndhwc_to_planar_add(const float* y, int C, int nf, int B, int64_t V,
-                                       const float* base, float* out, cudaStream_t s) {
-  k_ndhwc_to_planar_add<<<blocks_for((int64_t)B * nf * V), kT, 0, s>>>(y, C, nf, B, V, base, out);
+                                       const float* base, int nb, float a, float* out,
+                                       cudaStream_t s) {
+  k_ndhwc_to_planar_add<<<blocks_for((int64_t)B * nf * V), kT, 0, s>>>(y, C, nf, B, V, base, nb,
+                                                                      a, out);
   return cudaGetLastError();
 }
 
@@ -252,10 +260,11 @@ cudaError_t launch_relu_mask(void* g, const void* y, int64_t n, cudaStream_t s) 
 
 int mse_blocks() { return 1024; }
 
-cudaError_t launch_mse(const float* pred, int C, int nf, int B, int64_t V, const float* x,
-                       const float* y, float scale, void* grad, double* partials, double* loss,
-                       cudaStream_t s) {
-  k_mse<<<mse_blocks(), kT, 0, s>>>(pred, C, nf, B, V, x, y, scale, (__nv_bfloat16*)grad, partials);
+cudaError_t launch_mse(const float* pred, int C, int nf, int nxc, int B, int64_t V,
+                       const float* x, const float* y, float a, float scale, void* grad,
+                       double* partials, double* loss, cudaStream_t s) {
+  k_mse<<<mse_blocks(), kT, 0, s>>>(pred, C, nf, nxc, B, V, x, y, a, scale, (__nv_bfloat16*)grad,
+                                    partials);
   k_sum_doubles<<<1, 32, 0, s>>>(partials, mse_blocks(), (double)scale, loss);
   return cudaGetLastError();
 }

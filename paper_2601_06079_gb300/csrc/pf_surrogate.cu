@@ -94,6 +94,8 @@ Plan make_plan(int B, int D, int H, int W, bool training) {
   return p;
 }
 
+bool scale_ok(float a) { return a > 0.0f && isfinite(a); }
+
 bool dims_ok(int B, int D, int H, int W) {
   return B >= 1 && D >= 16 && H >= 64 && W >= 64 && D % 16 == 0 && H % 64 == 0 && W % 64 == 0 &&
          (int64_t)B * D * H * W <= ((int64_t)1 << 31);
@@ -148,10 +150,11 @@ pf_status conv_layer(const Net& n, const float* params, int l) {
   return PF_OK;
 }
 
-pf_status forward(const Net& n, const float* params, const float* x) {
+pf_status forward(const Net& n, const float* params, const float* x, int n_in, float out_scale) {
   const Plan& p = n.p;
   const int64_t V0 = p.V[0] / p.B;
-  SG_CUDA(pf::launch_planar_to_ndhwc(x, kNF, kCin0, p.B, V0, n.at<void>(p.x16), n.s));
+  SG_CUDA(pf::launch_planar_to_ndhwc(x, n_in, kCin0, p.B, V0, kNF, 1.0f / out_scale,
+                                     n.at<void>(p.x16), n.s));
   pf_status st;
   for (int l = 0; l < kNL; ++l) {
     if (l == 2 || l == 4 || l == 6) {  // pool the previous level's last activation
@@ -248,41 +251,69 @@ pf_status pf_surrogate_workspace(int batch, int d, int h, int w, int training, s
   return PF_OK;
 }
 
-pf_status pf_surrogate_predict(const float* params, const float* x, float* out, int batch, int d,
-                               int h, int w, void* ws, size_t bytes, void* stream) {
-  if (!params || !x || !out || !ws || !dims_ok(batch, d, h, w)) return PF_ERR_ARG;
+pf_status pf_surrogate_predict(const float* params, float out_scale, const float* x, int n_in,
+                               float* out, int batch, int d, int h, int w, void* ws, size_t bytes,
+                               void* stream) {
+  if (!params || !x || !out || !ws || !dims_ok(batch, d, h, w) || !scale_ok(out_scale) ||
+      (n_in != kNF && n_in != kCin0))
+    return PF_ERR_ARG;
   const Plan p = make_plan(batch, d, h, w, false);
   if (bytes < p.total || (uintptr_t)ws % 256) return PF_ERR_ARG;
   Net n{p, (char*)ws, (cudaStream_t)stream};
   pf_status st = convert_all(n, params, false);
   if (st != PF_OK) return st;
-  if ((st = forward(n, params, x)) != PF_OK) return st;
+  if ((st = forward(n, params, x, n_in, out_scale)) != PF_OK) return st;
   SG_CUDA(pf::launch_ndhwc_to_planar_add(n.at<float>(p.y32), kCout, kNF, batch,
-                                         (int64_t)d * h * w, x, out, n.s));
+                                         (int64_t)d * h * w, x, n_in, out_scale, out, n.s));
   return PF_OK;
 }
 
-pf_status pf_surrogate_train_step(float* params, float* adam_m, float* adam_v, int step,
-                                  double lr, const float* x, const float* y, int batch, int d,
-                                  int h, int w, void* ws, size_t bytes, void* stream,
-                                  double* loss) {
+pf_status pf_surrogate_train_step(float* params, float out_scale, float* adam_m, float* adam_v,
+                                  int step, double lr, const float* x, int n_in, const float* y,
+                                  int batch, int d, int h, int w, void* ws, size_t bytes,
+                                  void* stream, double* loss) {
   if (!params || !adam_m || !adam_v || !x || !y || !ws || step < 1 || !(lr > 0) ||
-      !dims_ok(batch, d, h, w))
+      !dims_ok(batch, d, h, w) || !scale_ok(out_scale) || (n_in != kNF && n_in != kCin0))
     return PF_ERR_ARG;
   const Plan p = make_plan(batch, d, h, w, true);
   if (bytes < p.total || (uintptr_t)ws % 256) return PF_ERR_ARG;
   Net n{p, (char*)ws, (cudaStream_t)stream};
   pf_status st = convert_all(n, params, true);
   if (st != PF_OK) return st;
-  if ((st = forward(n, params, x)) != PF_OK) return st;
+  if ((st = forward(n, params, x, n_in, out_scale)) != PF_OK) return st;
   const int64_t V = (int64_t)d * h * w;
   const float scale = (float)(1.0 / ((double)batch * V * kNF));
-  SG_CUDA(pf::launch_mse(n.at<float>(p.y32), kCout, kNF, batch, V, x, y, scale,
+  SG_CUDA(pf::launch_mse(n.at<float>(p.y32), kCout, kNF, n_in, batch, V, x, y, out_scale, scale,
                          n.at<void>(p.gy), n.at<double>(p.msep), n.at<double>(p.loss), n.s));
   float* grad = n.at<float>(p.grad);
   if ((st = backward(n, grad)) != PF_OK) return st;
   SG_CUDA(pf::launch_adam(params, adam_m, adam_v, grad, param_count(), (float)lr, 0.9f, 0.999f,
                           1e-8f, step, n.s));
+  if (loss) {
+    SG_CUDA(cudaMemcpyAsync(loss, n.at<double>(p.loss), sizeof(double), cudaMemcpyDeviceToHost,
+                            n.s));
+    SG_CUDA(cudaStreamSynchronize(n.s));
+  }
+  return PF_OK;
+}
+
+pf_status pf_surrogate_loss_grad(const float* params, float out_scale, const float* x, int n_in,
+                                 const float* y, int batch, int d, int h, int w, void* ws,
+                                 size_t bytes, void* stream, double* loss, float* grad) {
+  if (!params || !x || !y || !ws || !grad || !dims_ok(batch, d, h, w) || !scale_ok(out_scale) ||
+      (n_in != kNF && n_in != kCin0))
+    return PF_ERR_ARG;
+  const Plan p = make_plan(batch, d, h, w, true);
+  if (bytes < p.total || (uintptr_t)ws % 256) return PF_ERR_ARG;
+  Net n{p, (char*)ws, (cudaStream_t)stream};
+  pf_status st = convert_all(n, params, true);
+  if (st != PF_OK) return st;
+  if ((st = forward(n, params, x, n_in, out_scale)) != PF_OK) return st;
+  const int64_t V = (int64_t)d * h * w;
+  const float scale = (float)(1.0 / ((double)batch * V * kNF));
+  SG_CUDA(pf::launch_mse(n.at<float>(p.y32), kCout, kNF, n_in, batch, V, x, y, out_scale, scale,
+                         n.at<void>(p.gy), n.at<double>(p.msep), n.at<double>(p.loss), n.s));
+  if ((st = backward(n, grad)) != PF_OK) return st;
   if (loss) {
     SG_CUDA(cudaMemcpyAsync(loss, n.at<double>(p.loss), sizeof(double), cudaMemcpyDeviceToHost,
                             n.s));
@@ -320,16 +351,16 @@ pf_status pf_conv3d_check(int mode, int cin, int cout, int d, int h, int w, cons
   p += al(4 * V * kC);
   float* part = (float*)p;
   SG_CUDA(pf::launch_convert_weights(wt, cin, cout, wf, wb, s));
-  SG_CUDA(pf::launch_planar_to_ndhwc(x, cin, cin, 1, V, xb, s));
+  SG_CUDA(pf::launch_planar_to_ndhwc(x, cin, cin, 1, V, cin, 1.0f, xb, s));
   if (mode == 0) {
     SG_CUDA(pf::launch_conv3d(cin, cout, xb, wf, bias, 0, nullptr, y32, 1, d, h, w, kConvGrid, s));
-    SG_CUDA(pf::launch_ndhwc_to_planar_add(y32, cout, cout, 1, V, nullptr, out, s));
+    SG_CUDA(pf::launch_ndhwc_to_planar_add(y32, cout, cout, 1, V, nullptr, 0, 1.0f, out, s));
   } else {
-    SG_CUDA(pf::launch_planar_to_ndhwc(dy, cout, cout, 1, V, db16, s));
+    SG_CUDA(pf::launch_planar_to_ndhwc(dy, cout, cout, 1, V, cout, 1.0f, db16, s));
     if (mode == 1) {
       SG_CUDA(pf::launch_conv3d(cout, cin, db16, wb, nullptr, 0, nullptr, y32, 1, d, h, w,
                                 kConvGrid, s));
-      SG_CUDA(pf::launch_ndhwc_to_planar_add(y32, cin, cin, 1, V, nullptr, out, s));
+      SG_CUDA(pf::launch_ndhwc_to_planar_add(y32, cin, cin, 1, V, nullptr, 0, 1.0f, out, s));
     } else {
       const int blocks = pf::conv_wgrad_blocks(1, d, h, w, kWgradBlocks);
       SG_CUDA(pf::launch_conv3d_wgrad(cin, cout, xb, db16, part, out, 1, d, h, w, blocks, s));

@@ -57,7 +57,7 @@ def test_conv_kernels_match_oracle(mode, cin, cout, shape):
 def test_surrogate_zero_output_layer_is_identity_and_training_reduces_loss():
     import paper_2601_06079_gb300 as pf
     s = pf.Surrogate()
-    s.init(seed=1, out_scale=0.0)
+    s.init(seed=1, last_layer_scale=0.0)
     x = torch.from_numpy(G.random_field(3, (2, 8, 16, 64, 64), 0.0, 1.0)).cuda()
     assert torch.equal(s.predict(x), x)
     # learn a smooth target increment: y - x = 0.1 * (x shifted by one voxel in z)
@@ -66,3 +66,23 @@ def test_surrogate_zero_output_layer_is_identity_and_training_reduces_loss():
     losses = [s.train_step(x, y, lr=2e-3) for _ in range(60)]
     assert np.isfinite(losses).all()
     assert losses[-1] < 0.3 * losses[0]
+
+
+def test_whole_network_gradient_matches_torch_autograd_reference():
+    import paper_2601_06079_gb300 as pf
+    from tests import _torch_unet as R
+    s = pf.Surrogate()
+    s.init(seed=3, last_layer_scale=1.0)
+    x = torch.from_numpy(G.random_field(4, (1, 8, 16, 64, 64), 0.0, 1.0)).cuda()
+    y = x + 0.2 * torch.from_numpy(G.random_field(5, (1, 8, 16, 64, 64))).cuda()
+    loss, g = s.loss_grad(x, y)
+    p = s.params.detach().cpu().to(torch.bfloat16).double().requires_grad_(True)
+    xr = x.cpu().to(torch.bfloat16).double()
+    lr = R.loss(p, xr, y.cpu().double())
+    lr.backward()
+    gr = p.grad.numpy()
+    gg = g.cpu().double().numpy()
+    assert abs(loss - lr.item()) <= 2e-2 * lr.item()
+    cos = float(np.dot(gg, gr) / (np.linalg.norm(gg) * np.linalg.norm(gr)))
+    assert cos > 0.99, cos
+    assert np.linalg.norm(gg - gr) <= 0.1 * np.linalg.norm(gr)
