@@ -81,7 +81,8 @@ typedef struct {
   int gmres_restart;    /* GMRES restart length m, 1..31 (default 30) */
   int gmres_max_iters;  /* GMRES iterations per Newton correction (default 300) */
   double newton_rtol;   /* stop when ||R||_2 <= newton_rtol * ||M U^n / dt||_2 (default 1e-5) */
-  double gmres_rtol;    /* inexact-Newton forcing: ||r_gmres|| <= gmres_rtol ||G|| (default 1e-3) */
+  double gmres_rtol;    /* inexact-Newton forcing: GMRES stops at ||r|| <= max(gmres_rtol ||G||,
+                           a tenth of the Newton target) (default 1e-3; no oversolving) */
 } pf_newton_opts;
 
 typedef struct {
@@ -241,14 +242,17 @@ pf_status pf_energy2d_static(const float* state, int64_t nx, int64_t ny, double 
 
 /* ---- Learned warm start for the implicit step (no counterpart in the paper) ----
  * A 3-D U-Net (4 levels, 32 channels, 3x3x3 convolutions, BF16 operands, FP32
- * accumulation; 15 layers) maps U^n (8 order parameters) to an estimate of
- * U^{n+1} - U^n.  Parameters are an FP32 array of pf_surrogate_param_count()
- * values: per layer [27][c_out][c_in] weights then c_out biases, in layer order
- * 16->32, 32->32 x 13, 32->16 (inputs padded 8 -> 16 channels, outputs 16 -> 8).
- * Inputs are planar FP32 [batch][n_in][d][h][w] with n_in = 8 (the state) or 16
- * (the state followed by 8 feature channels in the units of an increment, e.g.
- * the explicit-Euler increment; the network sees them divided by out_scale);
- * outputs [batch][8][d][h][w]; d a multiple of 16, h and w of 64.  out_scale
+ * accumulation; 15 layers) gives the first Newton iterate for U^{n+1}.
+ * Parameters are an FP32 array of pf_surrogate_param_count() values: per layer
+ * [27][c_out][c_in] weights then c_out biases, in layer order 16->32,
+ * 32->32 x 13, 32->16 (inputs padded to 16 channels, outputs 16 -> 8 used).
+ * Inputs are planar FP32 [batch][n_in][d][h][w]:
+ *   n_in = 8:  x = U^n.  Guess = U^n + s * net, s = out_scale.
+ *   n_in = 16: x = [U^n; U^{n-1}].  The network sees U^n and the previous
+ *              increment divided by s_b = out_scale * RMS_b(U^n - U^{n-1})
+ *              (per sample b, floored at 1e-30); guess = U^n + (U^n - U^{n-1})
+ *              + s_b * net, i.e. a learned correction to linear extrapolation.
+ * Outputs [batch][8][d][h][w]; d a multiple of 16, h and w of 64.  out_scale
  * must be positive and finite; anything else is PF_ERR_ARG. */
 pf_status pf_surrogate_param_count(int64_t* n_params);
 
@@ -256,37 +260,50 @@ pf_status pf_surrogate_param_count(int64_t* n_params);
  * the gradient buffers).  Host only. */
 pf_status pf_surrogate_workspace(int batch, int d, int h, int w, int training, size_t* bytes);
 
-/* out = x[:8] + out_scale * net(x): the warm-start guess for U^{n+1}.  out_scale is
- * the typical size of an increment (the network works on increments of order
- * one).  All device pointers; enqueues on `stream`. */
+/* out = the warm-start guess for U^{n+1} (see above).  All device pointers;
+ * runs on `stream` and synchronises it.  Levels
+ * whose (d, h, w) allow it (h multiple of 16) run the tcgen05 convolution;
+ * PF_ERR_TIMEOUT if one of its bounded pipeline waits expired. */
 pf_status pf_surrogate_predict(const float* params, float out_scale, const float* x, int n_in,
                                float* out, int batch, int d, int h, int w, void* workspace,
                                size_t bytes, void* stream);
 
 /* One Adam step (lr, beta1 0.9, beta2 0.999, eps 1e-8; step >= 1 for the bias
- * correction) on the mean-squared error between out_scale * net(x) and y - x[:8].
+ * correction) on the loss of the guess against y = U^{n+1} (planar
+ * [batch][8][d][h][w]): with e the error field of the guess, in state units
+ * for n_in = 8 and in units of s_b for n_in = 16 (every sample then weighs
+ * the same whatever the size of its increment),
+ *   loss = mean over nodes and fields of ((I + stiff K) e)^2,
+ * K the assembled Q1 stiffness of the unit-spaced crop (natural boundary).
+ * stiff = dt L kappa / h^2 weighs e the way the linear part of the implicit
+ * Jacobian (Eq. 14) does, relative to its mass term; stiff = 0 is the plain
+ * mean-squared error.  stiff < 0 or non-finite is PF_ERR_ARG.
  * params, adam_m, adam_v: device FP32 (updated in place); loss: host (may be
  * NULL; if given the stream is synchronised). */
 pf_status pf_surrogate_train_step(float* params, float out_scale, float* adam_m, float* adam_v,
                                   int step, double lr, const float* x, int n_in, const float* y,
-                                  int batch, int d, int h, int w, void* workspace, size_t bytes,
-                                  void* stream, double* loss);
+                                  double stiff, int batch, int d, int h, int w, void* workspace,
+                                  size_t bytes, void* stream, double* loss);
 
 /* Loss (as pf_surrogate_train_step) and its gradient with respect to every
  * parameter, written to grad (device FP32, pf_surrogate_param_count values),
  * without updating anything.  Workspace: pf_surrogate_workspace(..., training = 1).
  * loss: host (may be NULL; if given the stream is synchronised). */
 pf_status pf_surrogate_loss_grad(const float* params, float out_scale, const float* x, int n_in,
-                                 const float* y, int batch, int d, int h, int w, void* workspace,
-                                 size_t bytes, void* stream, double* loss, float* grad);
+                                 const float* y, double stiff, int batch, int d, int h, int w,
+                                 void* workspace, size_t bytes, void* stream, double* loss,
+                                 float* grad);
 
 /* Single-layer probe of the surrogate's convolution kernels (tests): one sample,
  * planar FP32 [c][d][h][w]; weights [27][c_out][c_in] FP32 (rounded to BF16
  * inside).  (c_in, c_out) in {(16,32), (32,32), (32,16)}; d even, h and w
  * multiples of 8.  mode 0: out = conv(x) + bias; mode 1: out = conv^T(dy);
- * mode 2: out = [dW (27 x c_out x c_in), db (c_out)] for dy.  Workspace of at
- * least 2V(c_in + c_out) + 4 * 27 c_in c_out + 128 V + 16,809,984 bytes
- * (V = d h w, plus 256-byte alignment per part). */
+ * mode 2: out = [dW (27 x c_out x c_in), db (c_out)] for dy.  Modes 0 and 1
+ * run the tcgen05 kernel when h is a multiple of 16 (else mma.sync); modes 3
+ * and 4 are 0 and 1 on the mma.sync kernel.  Workspace (256-byte aligned) of
+ * at least 2V(c_in + c_out) + 4 * 27 c_in c_out + 128 V + 16,809,984 bytes
+ * plus 256 per part (V = d h w).  Synchronises the stream; PF_ERR_TIMEOUT if a
+ * tensor-core pipeline wait expired. */
 pf_status pf_conv3d_check(int mode, int cin, int cout, int d, int h, int w, const float* x,
                           const float* wt, const float* bias, const float* dy, float* out,
                           void* workspace, size_t bytes, void* stream);

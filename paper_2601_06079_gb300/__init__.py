@@ -220,15 +220,21 @@ class Ensemble:
 class Surrogate:
     """Learned warm start for the implicit step (a 3-D conv U-Net, see
     pf_surrogate_* in include/pf.h).  Parameters live in FP32 CUDA tensors;
-    init() draws them from a seeded He-normal recipe (input channels 8-15 and
-    output channels 8-15 are zero and stay zero)."""
+    init() draws them from a seeded He-normal recipe (output channels 8-15 are
+    zero and stay zero; so are input channels 8-15 without history).
+
+    history=False: input U^n (8 channels), guess U^n + out_scale * net.
+    history=True:  input [U^n; U^{n-1}] (16 channels), guess
+                   U^n + (U^n - U^{n-1}) + s * net with s = out_scale * RMS(U^n - U^{n-1}):
+                   a learned correction to linear extrapolation, in units of the
+                   previous increment."""
 
     LAYERS = [(16, 32)] + [(32, 32)] * 13 + [(32, 16)]
 
-    def __init__(self, device="cuda", stream=None, features=False):
+    def __init__(self, device="cuda", stream=None, history=False):
         self.device = torch.device(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-        self.features = features  # 16 input channels: state + explicit-Euler increment
+        self.history = history
         st, self.n_params = pf_surrogate_param_count()
         if st != 0:
             raise PFError(st, "pf_surrogate_param_count")
@@ -236,7 +242,7 @@ class Surrogate:
         self.m = torch.zeros_like(self.params)
         self.v = torch.zeros_like(self.params)
         self.step = 0
-        self.out_scale = 1.0  # typical increment size; the network predicts increment / out_scale
+        self.out_scale = 1.0  # output unit (absolute without history, relative with it)
         self._ws = {}
 
     def init(self, seed=0, last_layer_scale=0.1):
@@ -245,12 +251,12 @@ class Surrogate:
         import pf_inputs as G
         chunks = []
         for l, (ci, co) in enumerate(self.LAYERS):
-            fan_in = 27 * (8 if l == 0 and not self.features else ci)
+            fan_in = 27 * (8 if l == 0 and not self.history else ci)
             z = G.uniform(seed * 1000 + l, 27 * co * ci * 2, 0.0, 1.0, "surrogate")
             u1, u2 = np.maximum(z[0::2], 1e-12), z[1::2]
             normal = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)  # Box-Muller
             w = (normal * np.sqrt(2.0 / fan_in)).reshape(27, co, ci)
-            if l == 0 and not self.features:
+            if l == 0 and not self.history:
                 w[:, :, 8:] = 0.0
             if l == len(self.LAYERS) - 1:
                 w *= last_layer_scale
@@ -270,15 +276,15 @@ class Surrogate:
             self._ws[key] = torch.empty(nb, dtype=torch.uint8, device=self.device)
         return self._ws[key]
 
-    @staticmethod
-    def _dims(x):
+    def _dims(self, x):
         b, nin, d, h, w = x.shape
-        if nin not in (8, 16):
-            raise ValueError("the surrogate takes 8 order parameters (+ 8 feature channels)")
+        if nin != (16 if self.history else 8):
+            raise ValueError("input channels: 8 = U^n, or 16 = [U^n; U^{n-1}] with history")
         return b, nin, d, h, w
 
     def predict(self, x, out=None):
-        """out = x[:, :8] + out_scale * net(x) for x [batch][8 or 16][d][h][w] float32 CUDA."""
+        """Guess for U^{n+1} ([batch][8][d][h][w]) from x ([batch][8 or 16][d][h][w],
+        float32 CUDA); see the class docstring."""
         b, nin, d, h, w = self._dims(x)
         out = torch.empty((b, 8, d, h, w), device=x.device) if out is None else out
         ws = self._workspace(b, d, h, w, False)
@@ -289,25 +295,26 @@ class Surrogate:
             raise PFError(st, "pf_surrogate_predict")
         return out
 
-    def loss_grad(self, x, y):
-        """(loss, gradient tensor) without an update."""
+    def loss_grad(self, x, y, stiff=0.0):
+        """(loss, gradient tensor) without an update; stiff weighs the error by
+        (I + stiff K) (see pf_surrogate_train_step)."""
         b, nin, d, h, w = self._dims(x)
         ws = self._workspace(b, d, h, w, True)
         g = torch.empty_like(self.params)
         st, loss = pf_surrogate_loss_grad(self.params.data_ptr(), self.out_scale, x.data_ptr(),
-                                          nin, y.data_ptr(), b, d, h, w, ws.data_ptr(),
+                                          nin, y.data_ptr(), stiff, b, d, h, w, ws.data_ptr(),
                                           ws.numel(), self.stream.cuda_stream, g.data_ptr())
         if st != 0:
             raise PFError(st, "pf_surrogate_loss_grad")
         return loss, g
 
-    def train_step(self, x, y, lr=1e-3):
+    def train_step(self, x, y, lr=1e-3, stiff=0.0):
         b, nin, d, h, w = self._dims(x)
         ws = self._workspace(b, d, h, w, True)
         self.step += 1
         st, loss = pf_surrogate_train_step(self.params.data_ptr(), self.out_scale,
                                            self.m.data_ptr(), self.v.data_ptr(), self.step, lr,
-                                           x.data_ptr(), nin, y.data_ptr(), b, d, h, w,
+                                           x.data_ptr(), nin, y.data_ptr(), stiff, b, d, h, w,
                                            ws.data_ptr(), ws.numel(), self.stream.cuda_stream)
         if st != 0:
             raise PFError(st, "pf_surrogate_train_step")

@@ -114,13 +114,13 @@ def lib():
         L.pf_surrogate_train_step.restype = st
         L.pf_surrogate_train_step.argtypes = [C.c_void_p, C.c_float, C.c_void_p, C.c_void_p,
                                               C.c_int, C.c_double, C.c_void_p, C.c_int,
-                                              C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
-                                              C.c_void_p, C.c_size_t, C.c_void_p,
+                                              C.c_void_p, C.c_double, C.c_int, C.c_int, C.c_int,
+                                              C.c_int, C.c_void_p, C.c_size_t, C.c_void_p,
                                               C.POINTER(C.c_double)]
         L.pf_surrogate_loss_grad.restype = st
         L.pf_surrogate_loss_grad.argtypes = [C.c_void_p, C.c_float, C.c_void_p, C.c_int,
-                                             C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
-                                             C.c_void_p, C.c_size_t, C.c_void_p,
+                                             C.c_void_p, C.c_double, C.c_int, C.c_int, C.c_int,
+                                             C.c_int, C.c_void_p, C.c_size_t, C.c_void_p,
                                              C.POINTER(C.c_double), C.c_void_p]
         L.pf_conv3d_check.restype = st
         L.pf_conv3d_check.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
@@ -259,21 +259,21 @@ def pf_surrogate_predict(params, out_scale, x, n_in, out, batch, d, h, w, ws, nb
                                       C.c_void_p(stream))
 
 
-def pf_surrogate_train_step(params, out_scale, m, v, step, lr, x, n_in, y, batch, d, h, w, ws,
-                            nbytes, stream):
+def pf_surrogate_train_step(params, out_scale, m, v, step, lr, x, n_in, y, stiff, batch, d, h,
+                            w, ws, nbytes, stream):
     loss = C.c_double(0)
     s = lib().pf_surrogate_train_step(C.c_void_p(params), out_scale, C.c_void_p(m), C.c_void_p(v),
-                                      step, lr, C.c_void_p(x), n_in, C.c_void_p(y), batch, d, h,
-                                      w, C.c_void_p(ws), nbytes, C.c_void_p(stream),
+                                      step, lr, C.c_void_p(x), n_in, C.c_void_p(y), stiff, batch,
+                                      d, h, w, C.c_void_p(ws), nbytes, C.c_void_p(stream),
                                       C.byref(loss))
     return s, loss.value
 
 
-def pf_surrogate_loss_grad(params, out_scale, x, n_in, y, batch, d, h, w, ws, nbytes, stream,
-                           grad):
+def pf_surrogate_loss_grad(params, out_scale, x, n_in, y, stiff, batch, d, h, w, ws, nbytes,
+                           stream, grad):
     loss = C.c_double(0)
     s = lib().pf_surrogate_loss_grad(C.c_void_p(params), out_scale, C.c_void_p(x), n_in,
-                                     C.c_void_p(y), batch, d, h, w, C.c_void_p(ws), nbytes,
+                                     C.c_void_p(y), stiff, batch, d, h, w, C.c_void_p(ws), nbytes,
                                      C.c_void_p(stream), C.byref(loss), C.c_void_p(grad))
     return s, loss.value
 

@@ -1,0 +1,412 @@
+// 3x3x3 convolution of the learned surrogate on the 5th-generation tensor
+// cores: tcgen05.mma (BF16 operands from shared memory, FP32 accumulators in
+// tensor memory), input tiles brought in by TMA, warp-specialised pipeline.
+//
+// Implicit GEMM without an im2col buffer.  A block owns a 2x16x8 (z, y, x)
+// output tile, i.e. two M = 128 GEMMs (one per z plane) of N = c_out columns
+// and K = 27 taps x c_in.  The input halo (4x18x10 voxels) is staged by TMA
+// as c_in/8 "chunk planes": plane k holds channels 8k..8k+7 of every halo
+// voxel, 16 bytes per voxel, voxels in (z, y, x) order.  In that layout the
+// 8 x-neighbours of an output row are one contiguous 128-byte core matrix,
+// so the A operand of every tap is just a shared-memory descriptor whose
+// start address is shifted by the tap offset:
+//   core matrices along M (y rows) are HX * 16 bytes apart     (SBO),
+//   core matrices along K (channel chunks) are a plane apart    (LBO).
+// The weights of the layer sit in shared memory once per block in the same
+// canonical no-swizzle K-major layout ([tap][chunk][c_out][8 channels]).
+//
+// Roles (192 threads): warp 0 issues the TMA loads (3-stage ring) and owns
+// the tensor-memory allocation; warp 1 issues the MMAs from one thread and
+// commits them to mbarriers; warps 2-5 drain the accumulators
+// (tcgen05.ld 32x32b, lane quarter = warp % 4), add the bias, apply the ReLU
+// and store NDHWC.  Accumulators are double-buffered so the epilogue of tile
+// i overlaps the MMAs of tile i+1.  Every wait is bounded: on expiry the
+// block records an error code, stops issuing work, waits (bounded) for its
+// own copies and MMAs in flight, frees its tensor memory and returns.
+#include "pf_internal.h"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+namespace pf {
+namespace {
+
+constexpr int TZ = 2, TY = 16, TX = 8;                  // output tile
+constexpr int HZ = TZ + 2, HY = TY + 2, HX = TX + 2;    // halo tile
+constexpr uint32_t kPlane = HZ * HY * HX * 16;          // bytes per chunk plane (11520)
+constexpr int kStages = 3;
+constexpr int kThreads = 192;
+constexpr long long kWaitCycles = 4000000000ll;          // about 2 s at 2 GHz
+
+struct __align__(8) Ctrl {
+  uint64_t full[kStages], empty[kStages], accf[2], acce[2], done;
+  uint32_t tmem;
+  int abort;
+};
+
+__device__ __forceinline__ uint32_t su32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  // no-swizzle canonical layout; bits 46-47 = 1 (descriptor version)
+  return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)(lbo >> 4) << 16) |
+         ((uint64_t)(sbo >> 4) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ void bar_init(uint64_t* b, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count));
+}
+
+__device__ __forceinline__ bool bar_try(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(su32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase of parity `parity`; false on expiry or when
+// another role has already given up.
+__device__ bool bar_wait(uint64_t* b, uint32_t parity, volatile int* abort, int* err) {
+  const long long t0 = clock64();
+  while (!bar_try(b, parity)) {
+    if (*abort) return false;
+    if (clock64() - t0 > kWaitCycles) {
+      *abort = 1;
+      atomicExch(err, 1);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void bar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+
+__device__ __forceinline__ void bar_expect(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void tma_load5(uint32_t dst, const CUtensorMap* map, int c, int x,
+                                          int y, int z, int b, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c), "r"(x), "r"(y), "r"(z), "r"(b),
+      "r"(su32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                        uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* b) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          su32(b))
+      : "memory");
+}
+
+template <int N>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, float* v);
+
+template <>
+__device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <>
+__device__ __forceinline__ void tmem_ld<32>(uint32_t taddr, float* v) {
+  tmem_ld<16>(taddr, v);
+  tmem_ld<16>(taddr + 16, v + 16);
+}
+
+template <int CIN, int COUT>
+struct Cfg {
+  static constexpr uint32_t kWBytes = 27u * (CIN / 8) * COUT * 16;
+  static constexpr uint32_t kStage = (CIN / 8) * kPlane;
+  static constexpr uint32_t kCols = 4 * COUT;  // 2 buffers x 2 z planes x COUT
+  static constexpr uint32_t kSmem = 128 + kWBytes + kStages * kStage + sizeof(Ctrl);
+  // kind::f16, FP32 accumulate, BF16 A and B, both K-major, N = COUT, M = 128
+  static constexpr uint32_t kIdesc =
+      (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(COUT >> 3) << 17) | ((128u >> 4) << 24);
+};
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_conv3d_tc(const __grid_constant__ CUtensorMap xmap, const __nv_bfloat16* __restrict__ wt,
+                const float* __restrict__ bias, int relu, __nv_bfloat16* y16, float* y32, int B,
+                int D, int H, int W, int* err) {
+  using C = Cfg<CIN, COUT>;
+  extern __shared__ unsigned char smem_raw[];
+  // 128-byte aligned base (TMA destinations and descriptors)
+  const uint32_t raw = su32(smem_raw);
+  unsigned char* base = smem_raw + ((128 - (raw & 127)) & 127);
+  unsigned char* sW = base;
+  unsigned char* sIn = base + C::kWBytes;
+  Ctrl* ctl = reinterpret_cast<Ctrl*>(sIn + kStages * C::kStage);
+  volatile int* abort = &ctl->abort;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tiles_x = W / TX, tiles_y = H / TY, tiles_z = D / TZ;
+  const int ntiles = B * tiles_z * tiles_y * tiles_x;
+
+  // weights [27][COUT][CIN] -> [27][CIN/8][COUT][8]
+  for (int i = threadIdx.x; i < 27 * COUT * (CIN / 8); i += kThreads) {
+    const int kc = i % (CIN / 8), co = (i / (CIN / 8)) % COUT, tap = i / ((CIN / 8) * COUT);
+    *reinterpret_cast<uint4*>(sW + ((tap * (CIN / 8) + kc) * COUT + co) * 16) =
+        *reinterpret_cast<const uint4*>(wt + (int64_t)i * 8);
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      bar_init(&ctl->full[s], 1);
+      bar_init(&ctl->empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      bar_init(&ctl->accf[a], 1);
+      bar_init(&ctl->acce[a], 128);
+    }
+    bar_init(&ctl->done, 1);
+    ctl->abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     su32(&ctl->tmem)),
+                 "r"(C::kCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // weights -> async proxy
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = ctl->tmem;
+
+  if (warp == 0) {
+    // ---- TMA producer ----
+    if (lane == 0) {
+      int i = 0;
+      for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+        const int s = i % kStages;
+        if (i >= kStages && !bar_wait(&ctl->empty[s], ((i / kStages) - 1) & 1, abort, err)) break;
+        const int tx = t % tiles_x, ty = (t / tiles_x) % tiles_y;
+        const int tz = (t / (tiles_x * tiles_y)) % tiles_z, b = t / (tiles_x * tiles_y * tiles_z);
+        bar_expect(&ctl->full[s], C::kStage);
+        const uint32_t dst = su32(sIn + s * C::kStage);
+#pragma unroll
+        for (int k = 0; k < CIN / 8; ++k)
+          tma_load5(dst + k * kPlane, &xmap, 8 * k, tx * TX - 1, ty * TY - 1, tz * TZ - 1, b,
+                    &ctl->full[s]);
+      }
+      // wait (bounded) for the copies still in flight before the block may exit
+      const int issued = i;
+      for (int s = 0; s < kStages && s < issued; ++s) {
+        const int last = s + ((issued - 1 - s) / kStages) * kStages;
+        const long long t0 = clock64();
+        while (!bar_try(&ctl->full[s], (last / kStages) & 1) && clock64() - t0 < kWaitCycles) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer ----
+    if (lane == 0) {
+      int i = 0;
+      for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+        const int s = i % kStages, a = i & 1;
+        if (!bar_wait(&ctl->full[s], (i / kStages) & 1, abort, err)) break;
+        if (i >= 2 && !bar_wait(&ctl->acce[a], ((i >> 1) - 1) & 1, abort, err)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // descriptors of the stage / weight bases; every (tap, chunk, z) operand
+        // is a compile-time byte offset added to the 16-byte address field
+        const uint64_t a_desc = sdesc(su32(sIn + s * C::kStage), kPlane, HX * 16);
+        const uint64_t b_desc = sdesc(su32(sW), COUT * 16, 128);
+        const uint32_t d0 = tmem + a * 2 * COUT;
+#pragma unroll
+        for (int tap = 0; tap < 27; ++tap) {
+          const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+#pragma unroll
+          for (int kc = 0; kc < CIN / 16; ++kc) {
+            const uint64_t bd = b_desc + (uint64_t)(((tap * (CIN / 8) + 2 * kc) * COUT * 16) >> 4);
+#pragma unroll
+            for (int z = 0; z < TZ; ++z) {
+              const uint32_t off = (((z + dz) * HY + dy) * HX + dx) * 16 + 2 * kc * kPlane;
+              mma_f16(d0 + z * COUT, a_desc + (uint64_t)(off >> 4), bd, C::kIdesc,
+                      (tap | kc) != 0);
+            }
+          }
+        }
+        mma_commit(&ctl->empty[s]);
+        mma_commit(&ctl->accf[a]);
+      }
+      // all MMAs of this block are complete once `done` flips
+      mma_commit(&ctl->done);
+      const long long t0 = clock64();
+      while (!bar_try(&ctl->done, 0) && clock64() - t0 < kWaitCycles) {
+      }
+    }
+  } else {
+    // ---- epilogue: warps 2..5, TMEM lane quarter q = warp % 4 ----
+    const int q = warp & 3;
+    const int row = q * 32 + lane;  // M row = y * 8 + x
+    const int yy = row >> 3, xx = row & 7;
+    float bv[COUT];
+#pragma unroll
+    for (int c = 0; c < COUT; ++c) bv[c] = bias ? bias[c] : 0.0f;
+    int i = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+      const int a = i & 1;
+      // warp-uniform outcome: tcgen05.ld below needs the whole warp converged
+      const bool ok = bar_wait(&ctl->accf[a], (i >> 1) & 1, abort, err);
+      if (!__all_sync(0xffffffffu, ok)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int tx = t % tiles_x, ty = (t / tiles_x) % tiles_y;
+      const int tz = (t / (tiles_x * tiles_y)) % tiles_z, b = t / (tiles_x * tiles_y * tiles_z);
+#pragma unroll
+      for (int z = 0; z < TZ; ++z) {
+        float v[COUT];
+        tmem_ld<COUT>(tmem + ((uint32_t)(q * 32) << 16) + a * 2 * COUT + z * COUT, v);
+#pragma unroll
+        for (int c = 0; c < COUT; ++c) {
+          v[c] += bv[c];
+          if (relu) v[c] = fmaxf(v[c], 0.0f);
+        }
+        const int64_t vox =
+            (((int64_t)b * D + tz * TZ + z) * H + ty * TY + yy) * W + tx * TX + xx;
+        if (y16) {
+          uint4* dst = reinterpret_cast<uint4*>(y16 + vox * COUT);
+#pragma unroll
+          for (int c = 0; c < COUT / 8; ++c) {
+            uint4 o;
+            __nv_bfloat162 h0 = __floats2bfloat162_rn(v[8 * c + 0], v[8 * c + 1]);
+            __nv_bfloat162 h1 = __floats2bfloat162_rn(v[8 * c + 2], v[8 * c + 3]);
+            __nv_bfloat162 h2 = __floats2bfloat162_rn(v[8 * c + 4], v[8 * c + 5]);
+            __nv_bfloat162 h3 = __floats2bfloat162_rn(v[8 * c + 6], v[8 * c + 7]);
+            o.x = *reinterpret_cast<uint32_t*>(&h0);
+            o.y = *reinterpret_cast<uint32_t*>(&h1);
+            o.z = *reinterpret_cast<uint32_t*>(&h2);
+            o.w = *reinterpret_cast<uint32_t*>(&h3);
+            dst[c] = o;
+          }
+        }
+        if (y32) {
+          float4* dst = reinterpret_cast<float4*>(y32 + vox * COUT);
+#pragma unroll
+          for (int c = 0; c < COUT / 4; ++c)
+            dst[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      bar_arrive(&ctl->acce[a]);
+    }
+  }
+
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  __syncwarp();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(C::kCols));
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      n = 148;
+  }
+  return n;
+}
+
+template <int CIN, int COUT>
+cudaError_t tc_launch(const void* x, const void* wt, const float* bias, int relu, void* y16,
+                      float* y32, int B, int D, int H, int W, int* err, cudaStream_t s) {
+  using C = Cfg<CIN, COUT>;
+  auto enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  // NDHWC BF16 viewed as 5-D (C, W, H, D, B), innermost first; box = one
+  // 8-channel chunk of the 4x18x10 halo; out-of-range voxels read as zero.
+  CUtensorMap map;
+  const cuuint64_t dims[5] = {(cuuint64_t)CIN, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D,
+                              (cuuint64_t)B};
+  const cuuint64_t strides[4] = {(cuuint64_t)CIN * 2, (cuuint64_t)W * CIN * 2,
+                                 (cuuint64_t)H * W * CIN * 2, (cuuint64_t)D * H * W * CIN * 2};
+  const cuuint32_t box[5] = {8, HX, HY, HZ, 1};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(x), dims, strides, box,
+          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_conv3d_tc<CIN, COUT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  const int ntiles = B * (D / TZ) * (H / TY) * (W / TX);
+  const int grid = ntiles < sm_count() ? ntiles : sm_count();
+  k_conv3d_tc<CIN, COUT><<<grid, kThreads, C::kSmem, s>>>(
+      map, (const __nv_bfloat16*)wt, bias, relu, (__nv_bfloat16*)y16, y32, B, D, H, W, err);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool conv3d_tc_shape_ok(int B, int D, int H, int W) {
+  return B >= 1 && D >= TZ && H >= TY && W >= TX && D % TZ == 0 && H % TY == 0 && W % TX == 0;
+}
+
+cudaError_t launch_conv3d_tc(int cin, int cout, const void* x, const void* wt, const float* bias,
+                             int relu, void* y16, float* y32, int B, int D, int H, int W,
+                             int* err, cudaStream_t s) {
+  if (!conv3d_tc_shape_ok(B, D, H, W) || !err || (uintptr_t)x % 16) return cudaErrorInvalidValue;
+  if (cin == 16 && cout == 32)
+    return tc_launch<16, 32>(x, wt, bias, relu, y16, y32, B, D, H, W, err, s);
+  if (cin == 32 && cout == 32)
+    return tc_launch<32, 32>(x, wt, bias, relu, y16, y32, B, D, H, W, err, s);
+  if (cin == 32 && cout == 16)
+    return tc_launch<32, 16>(x, wt, bias, relu, y16, y32, B, D, H, W, err, s);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace pf

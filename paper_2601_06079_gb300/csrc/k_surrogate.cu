@@ -20,149 +20,94 @@ unsigned blocks_for(int64_t n) {
   return (unsigned)(b < 4096 ? b : 4096);
 }
 
-// planar [B][nf][V] FP32 -> NDHWC BF16 [B][V][C] (channels >= nf are zero;
-// channels k0.. are multiplied by fs)
+// 8 BF16 channels (16 bytes) <-> 8 floats
+__device__ __forceinline__ void unpack8(const uint4& u, float* f) {
+  const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float2 t = __bfloat1622float2(h[k]);
+    f[2 * k] = t.x;
+    f[2 * k + 1] = t.y;
+  }
+}
+
+__device__ __forceinline__ uint4 pack8(const float* f) {
+  uint4 u;
+  __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&u);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) h[k] = __floats2bfloat162_rn(f[2 * k], f[2 * k + 1]);
+  return u;
+}
+
+// planar [B][nf][V] FP32 -> NDHWC BF16 [B][V][C], one thread per voxel (the
+// planar reads coalesce across the warp, the voxel's C channels go out as
+// 16-byte stores).  mode 0: channels < nf copied, the rest zero.  mode 1
+// (nf = 16, two consecutive states [U^n; U^{n-1}]): channels 0..7 = U^n,
+// 8..15 = (U^n - U^{n-1}) / sig[b], the rest zero.
 __global__ void k_planar_to_ndhwc(const float* __restrict__ in, int nf, int C, int B, int64_t V,
-                                  int k0, float fs, __nv_bfloat16* __restrict__ out) {
-  const int64_t n = (int64_t)B * V * C;
+                                  int mode, const float* __restrict__ sig,
+                                  __nv_bfloat16* __restrict__ out) {
+  const int64_t n = (int64_t)B * V;
   for (int64_t i = gtid(); i < n; i += grid_stride()) {
-    const int c = (int)(i % C);
-    const int64_t v = (i / C) % V, b = i / (C * V);
-    const float a = c < nf ? in[(b * nf + c) * V + v] : 0.0f;
-    out[i] = __float2bfloat16(c < k0 ? a : a * fs);
+    const int64_t v = i % V, b = i / V;
+    const float inv = mode ? 1.0f / sig[b] : 1.0f;
+    uint4* dst = reinterpret_cast<uint4*>(out + i * C);
+    for (int c0 = 0; c0 < C; c0 += 8) {
+      float f[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int c = c0 + k;
+        float a = c < nf ? in[(b * nf + c) * V + v] : 0.0f;
+        if (mode && c >= 8 && c < 16) a = (in[(b * nf + c - 8) * V + v] - a) * inv;
+        f[k] = a;
+      }
+      dst[c0 / 8] = pack8(f);
+    }
   }
 }
 
-// out planar [B][nf][V] = base + a * first nf channels of y (NDHWC FP32, C
-// channels); base is planar with nb channels per sample (its first nf used)
+// out planar [B][nf][V] = base + (mode 1: base[:nf] - base[nf:2nf]) + sig[b] * y
+// (first nf channels of the NDHWC FP32 y with C channels); base is planar with
+// nb channels per sample and may be null (then mode must be 0); sig null = 1.
+// One thread per voxel.
 __global__ void k_ndhwc_to_planar_add(const float* __restrict__ y, int C, int nf, int B, int64_t V,
-                                      const float* __restrict__ base, int nb, float a,
-                                      float* __restrict__ out) {
-  const int64_t n = (int64_t)B * nf * V;
+                                      const float* __restrict__ base, int nb, int mode,
+                                      const float* __restrict__ sig, float* __restrict__ out) {
+  const int64_t n = (int64_t)B * V;
   for (int64_t i = gtid(); i < n; i += grid_stride()) {
-    const int64_t v = i % V, f = (i / V) % nf, b = i / (nf * V);
-    out[i] = fmaf(a, y[(b * V + v) * C + f], base ? base[(b * nb + f) * V + v] : 0.0f);
-  }
-}
-
-// 2x2x2 average pooling, NDHWC, C channels; (D, H, W) are the fine sizes
-__global__ void k_pool(const __nv_bfloat16* __restrict__ in, int B, int D, int H, int W, int C,
-                       __nv_bfloat16* __restrict__ out) {
-  const int d = D / 2, h = H / 2, w = W / 2;
-  const int64_t n = (int64_t)B * d * h * w * C;
-  for (int64_t i = gtid(); i < n; i += grid_stride()) {
-    const int c = (int)(i % C);
-    int64_t r = i / C;
-    const int x = (int)(r % w);
-    r /= w;
-    const int y = (int)(r % h);
-    r /= h;
-    const int z = (int)(r % d);
-    const int64_t b = r / d;
-    float s = 0.0f;
+    const int64_t v = i % V, b = i / V;
+    const float a = sig ? sig[b] : 1.0f;
+    const float* src = y + i * C;
+    for (int f = 0; f < nf; f += 4) {
+      const float4 t = *reinterpret_cast<const float4*>(src + f);
+      const float tv[4] = {t.x, t.y, t.z, t.w};
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int64_t src = ((((b * D) + 2 * z + (k >> 2)) * H + 2 * y + ((k >> 1) & 1)) * W + 2 * x +
-                           (k & 1)) * C + c;
-      s += __bfloat162float(in[src]);
+      for (int k = 0; k < 4; ++k) {
+        if (f + k >= nf) break;
+        float o = 0.0f;
+        if (base) {
+          const float u = base[(b * nb + f + k) * V + v];
+          o = mode ? 2.0f * u - base[(b * nb + nf + f + k) * V + v] : u;
+        }
+        out[(b * nf + f + k) * V + v] = fmaf(a, tv[k], o);
+      }
     }
-    out[i] = __float2bfloat16(0.125f * s);
   }
 }
 
-// nearest 2x upsampling of `coarse` plus `skip` (fine sizes D, H, W)
-__global__ void k_up_add(const __nv_bfloat16* __restrict__ coarse,
-                         const __nv_bfloat16* __restrict__ skip, int B, int D, int H, int W, int C,
-                         __nv_bfloat16* __restrict__ out) {
-  const int64_t n = (int64_t)B * D * H * W * C;
-  for (int64_t i = gtid(); i < n; i += grid_stride()) {
-    const int c = (int)(i % C);
-    int64_t r = i / C;
-    const int x = (int)(r % W);
-    r /= W;
-    const int y = (int)(r % H);
-    r /= H;
-    const int z = (int)(r % D);
-    const int64_t b = r / D;
-    const int64_t src = ((((b * (D / 2)) + z / 2) * (H / 2) + y / 2) * (W / 2) + x / 2) * C + c;
-    out[i] = __float2bfloat16(__bfloat162float(coarse[src]) + __bfloat162float(skip[i]));
-  }
-}
-
-// Backward of up_add and of pool into one fine gradient, and the coarse one:
-//   g_fine  = g_out (skip) [+ g_pool_coarse / 8 broadcast]      (fine sizes)
-//   g_coarse = sum over each 2x2x2 block of g_out                 (coarse sizes)
-__global__ void k_down_sum(const __nv_bfloat16* __restrict__ g, int B, int D, int H, int W, int C,
-                           __nv_bfloat16* __restrict__ out) {
-  const int d = D / 2, h = H / 2, w = W / 2;
-  const int64_t n = (int64_t)B * d * h * w * C;
-  for (int64_t i = gtid(); i < n; i += grid_stride()) {
-    const int c = (int)(i % C);
-    int64_t r = i / C;
-    const int x = (int)(r % w);
-    r /= w;
-    const int y = (int)(r % h);
-    r /= h;
-    const int z = (int)(r % d);
-    const int64_t b = r / d;
-    float s = 0.0f;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int64_t src = ((((b * D) + 2 * z + (k >> 2)) * H + 2 * y + ((k >> 1) & 1)) * W + 2 * x +
-                           (k & 1)) * C + c;
-      s += __bfloat162float(g[src]);
-    }
-    out[i] = __float2bfloat16(s);
-  }
-}
-
-// acc (fine) += pool-backward of g_coarse: every fine voxel gets g_coarse / 8
-__global__ void k_pool_back_add(const __nv_bfloat16* __restrict__ gc, int B, int D, int H, int W,
-                                int C, __nv_bfloat16* __restrict__ acc) {
-  const int64_t n = (int64_t)B * D * H * W * C;
-  for (int64_t i = gtid(); i < n; i += grid_stride()) {
-    const int c = (int)(i % C);
-    int64_t r = i / C;
-    const int x = (int)(r % W);
-    r /= W;
-    const int y = (int)(r % H);
-    r /= H;
-    const int z = (int)(r % D);
-    const int64_t b = r / D;
-    const int64_t src = ((((b * (D / 2)) + z / 2) * (H / 2) + y / 2) * (W / 2) + x / 2) * C + c;
-    acc[i] = __float2bfloat16(__bfloat162float(acc[i]) + 0.125f * __bfloat162float(gc[src]));
-  }
-}
-
-// g <- g * (y > 0)   (ReLU backward, in place)
-__global__ void k_relu_mask(__nv_bfloat16* __restrict__ g, const __nv_bfloat16* __restrict__ y,
-                            int64_t n) {
-  for (int64_t i = gtid(); i < n; i += grid_stride())
-    if (!(__bfloat162float(y[i]) > 0.0f)) g[i] = __float2bfloat16(0.0f);
-}
-
-// Mean-squared loss between a * (first nf channels of pred) (NDHWC FP32, C ch)
-// and target = y - x (planar FP32, x with nx channels of which the first nf
-// are the state); writes dL/dpred (NDHWC BF16, zero beyond nf) and per-block
-// partial sums of the squared error.
-__global__ void k_mse(const float* __restrict__ pred, int C, int nf, int nxc, int B, int64_t V,
-                      const float* __restrict__ x, const float* __restrict__ y, float a,
-                      float scale, __nv_bfloat16* __restrict__ grad,
-                      double* __restrict__ partials) {
+// Per-sample output unit: sig[b] = a (mode 0) or a * RMS over the sample of
+// U^n - U^{n-1} (mode 1, x = [U^n; U^{n-1}] with 2 nf channels), floored at
+// 1e-30.  part holds gridDim.x partial sums per sample (fixed-order reduction).
+__global__ void k_incr_sumsq(const float* __restrict__ x, int nf, int64_t V,
+                             double* __restrict__ part) {
   __shared__ double red[kT];
+  const int b = blockIdx.y;
+  const float* u = x + (int64_t)b * 2 * nf * V;
   double acc = 0.0;
-  const int64_t n = (int64_t)B * V * C;
-  for (int64_t i = gtid(); i < n; i += grid_stride()) {
-    const int c = (int)(i % C);
-    float gval = 0.0f;
-    if (c < nf) {
-      const int64_t v = (i / C) % V, b = i / (C * V);
-      const int64_t p = (b * nf + c) * V + v;
-      const float r = fmaf(a, pred[i], -(y[p] - x[(b * nxc + c) * V + v]));
-      acc += (double)r * r;
-      gval = 2.0f * scale * a * r;
-    }
-    grad[i] = __float2bfloat16(gval);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)nf * V;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double d = (double)u[i] - (double)u[nf * V + i];
+    acc += d * d;
   }
   red[threadIdx.x] = acc;
   __syncthreads();
@@ -170,7 +115,200 @@ __global__ void k_mse(const float* __restrict__ pred, int C, int nf, int nxc, in
     if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
     __syncthreads();
   }
+  if (threadIdx.x == 0) part[b * gridDim.x + blockIdx.x] = red[0];
+}
+
+__global__ void k_incr_scale(const double* __restrict__ part, int nblk, int B, double count,
+                             float a, int mode, float* __restrict__ sig) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  if (!mode) {
+    sig[b] = a;
+    return;
+  }
+  double ss = 0.0;
+  for (int k = 0; k < nblk; ++k) ss += part[b * nblk + k];
+  sig[b] = fmaxf(a * (float)sqrt(ss / count), 1e-30f);
+}
+
+// Voxel index helpers for NDHWC: i = ((b * D + z) * H + y) * W + x
+struct Vox {
+  int64_t b;
+  int z, y, x;
+};
+
+__device__ __forceinline__ Vox split(int64_t i, int D, int H, int W) {
+  Vox v;
+  v.x = (int)(i % W);
+  i /= W;
+  v.y = (int)(i % H);
+  i /= H;
+  v.z = (int)(i % D);
+  v.b = i / D;
+  return v;
+}
+
+// Sum (scaled) of the 8 fine voxels under every coarse voxel; one thread per
+// (coarse voxel, 8-channel chunk).  (D, H, W) are the fine sizes.
+__global__ void k_block_sum(const __nv_bfloat16* __restrict__ in, int B, int D, int H, int W,
+                            int C, float scale, __nv_bfloat16* __restrict__ out) {
+  const int d = D / 2, h = H / 2, w = W / 2, nc = C / 8;
+  const int64_t n = (int64_t)B * d * h * w * nc;
+  for (int64_t i = gtid(); i < n; i += grid_stride()) {
+    const int c = (int)(i % nc);
+    const Vox o = split(i / nc, d, h, w);
+    float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int64_t src = (((o.b * D + 2 * o.z + (k >> 2)) * H + 2 * o.y + ((k >> 1) & 1)) * W +
+                           2 * o.x + (k & 1)) * C + 8 * c;
+      float f[8];
+      unpack8(*reinterpret_cast<const uint4*>(in + src), f);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) s[j] += f[j];
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s[j] *= scale;
+    reinterpret_cast<uint4*>(out)[i] = pack8(s);
+  }
+}
+
+// out(fine) = acc(fine) + scale * coarse(parent voxel); one thread per (fine
+// voxel, 8-channel chunk).  Serves the nearest upsampling + skip of the
+// decoder (scale 1) and the backward of the average pooling (scale 1/8).
+// acc and out may be the same buffer (in-place accumulation).
+__global__ void k_up_add(const __nv_bfloat16* __restrict__ coarse, const __nv_bfloat16* acc,
+                         int B, int D, int H, int W, int C, float scale, __nv_bfloat16* out) {
+  const int nc = C / 8;
+  const int64_t n = (int64_t)B * D * H * W * nc;
+  for (int64_t i = gtid(); i < n; i += grid_stride()) {
+    const int c = (int)(i % nc);
+    const Vox o = split(i / nc, D, H, W);
+    const int64_t src =
+        (((o.b * (D / 2) + o.z / 2) * (H / 2) + o.y / 2) * (W / 2) + o.x / 2) * C + 8 * c;
+    float a[8], f[8];
+    unpack8(*reinterpret_cast<const uint4*>(coarse + src), a);
+    unpack8(reinterpret_cast<const uint4*>(acc)[i], f);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) f[j] = fmaf(scale, a[j], f[j]);
+    reinterpret_cast<uint4*>(out)[i] = pack8(f);
+  }
+}
+
+// g <- g * (y > 0)   (ReLU backward, in place), 8 channels per thread
+__global__ void k_relu_mask(__nv_bfloat16* __restrict__ g, const __nv_bfloat16* __restrict__ y,
+                            int64_t n8) {
+  for (int64_t i = gtid(); i < n8; i += grid_stride()) {
+    float gv[8], yv[8];
+    unpack8(reinterpret_cast<const uint4*>(g)[i], gv);
+    unpack8(reinterpret_cast<const uint4*>(y)[i], yv);
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (!(yv[j] > 0.0f)) gv[j] = 0.0f;
+    reinterpret_cast<uint4*>(g)[i] = pack8(gv);
+  }
+}
+
+// Error field of the prediction against the target state y = U^{n+1} (planar,
+// nf channels) for inputs x (planar, nxc channels, U^n first):
+//   mode 0: r = sig_b * pred - (y - U^n)                       (state units)
+//   mode 1: r = pred - (y - U^n - (U^n - U^{n-1})) / sig_b     (units of sig_b)
+// pred = first nf channels of the NDHWC FP32 network output (C channels);
+// r is written planar [B][nf][V].
+__global__ void k_err(const float* __restrict__ pred, int C, int nf, int nxc, int B, int64_t V,
+                      const float* __restrict__ x, const float* __restrict__ y, int mode,
+                      const float* __restrict__ sig, float* __restrict__ r) {
+  const int64_t n = (int64_t)B * nf * V;
+  for (int64_t i = gtid(); i < n; i += grid_stride()) {
+    const int64_t v = i % V, c = (i / V) % nf, b = i / (nf * V);
+    const float u = x[(b * nxc + c) * V + v];
+    float t = y[i] - u;
+    const float p = pred[(b * V + v) * C + c];
+    if (mode) {
+      t -= u - x[(b * nxc + nf + c) * V + v];
+      r[i] = p - t / sig[b];
+    } else {
+      r[i] = fmaf(sig[b], p, -t);
+    }
+  }
+}
+
+// out = in + c * (M^-1 K in) on planes of D x H x W nodes (h = 1): K is the
+// assembled Q1 stiffness of the unit-spaced mesh (27-point stencil: centre
+// 8/3, face neighbours 0, edge neighbours -1/6, corner neighbours -1/12) and
+// M its lumped mass; at the boundary the mirror-extended stencil gives M^-1 K
+// exactly.  Written as in + c * w * S(in) with S the mirror stencil and
+// w = M / h^3 for the symmetric form (I + c K) used by the loss:
+//   sym = 0: out = in + c * S(in)            (= (I + c M^-1 K) in)
+//   sym = 1: out = in + c * w * S(in)        (= (I + c K) in, symmetric)
+__global__ void k_apply_stiff(const float* __restrict__ in, int64_t planes, int D, int H, int W,
+                              float c, int sym, float* __restrict__ out) {
+  const int64_t V = (int64_t)D * H * W;
+  const int64_t n = planes * V;
+  for (int64_t i = gtid(); i < n; i += grid_stride()) {
+    const int64_t p = i / V;
+    const int64_t v = i % V;
+    const int x = (int)(v % W), y = (int)((v / W) % H), z = (int)(v / ((int64_t)W * H));
+    const float* pl = in + p * V;
+    float acc = 0.0f;
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz) {
+      int zz = z + dz;
+      zz = zz < 0 ? -zz : (zz >= D ? 2 * D - 2 - zz : zz);
+#pragma unroll
+      for (int dy = -1; dy <= 1; ++dy) {
+        int yy = y + dy;
+        yy = yy < 0 ? -yy : (yy >= H ? 2 * H - 2 - yy : yy);
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int k = (dz != 0) + (dy != 0) + (dx != 0);
+          if (k == 1) continue;
+          const float wgt = k == 0 ? 8.0f / 3.0f : (k == 2 ? -1.0f / 6.0f : -1.0f / 12.0f);
+          int xx = x + dx;
+          xx = xx < 0 ? -xx : (xx >= W ? 2 * W - 2 - xx : xx);
+          acc = fmaf(wgt, pl[((int64_t)zz * H + yy) * W + xx], acc);
+        }
+      }
+    }
+    float w = 1.0f;
+    if (sym) {
+      if (x == 0 || x == W - 1) w *= 0.5f;
+      if (y == 0 || y == H - 1) w *= 0.5f;
+      if (z == 0 || z == D - 1) w *= 0.5f;
+    }
+    out[i] = fmaf(c * w, acc, pl[v]);
+  }
+}
+
+// Per-block partial sums of q^2 over n values.
+__global__ void k_sumsq(const float* __restrict__ q, int64_t n, double* __restrict__ partials) {
+  __shared__ double red[kT];
+  double acc = 0.0;
+  for (int64_t i = gtid(); i < n; i += grid_stride()) acc += (double)q[i] * q[i];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = kT / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
   if (threadIdx.x == 0) partials[blockIdx.x] = red[0];
+}
+
+// dL/dpred (NDHWC BF16, C channels, zero beyond nf) from g = dL/dr / 2 (planar):
+// 2 * scale * g * dr/dpred with dr/dpred = sig_b (mode 0) or 1 (mode 1).
+__global__ void k_grad_out(const float* __restrict__ g, int C, int nf, int B, int64_t V, int mode,
+                           const float* __restrict__ sig, float scale,
+                           __nv_bfloat16* __restrict__ grad) {
+  const int64_t n = (int64_t)B * V * C;
+  for (int64_t i = gtid(); i < n; i += grid_stride()) {
+    const int c = (int)(i % C);
+    float gv = 0.0f;
+    if (c < nf) {
+      const int64_t v = (i / C) % V, b = i / (C * V);
+      gv = 2.0f * scale * g[(b * nf + c) * V + v] * (mode ? 1.0f : sig[b]);
+    }
+    grad[i] = __float2bfloat16(gv);
+  }
 }
 
 __global__ void k_sum_doubles(const double* __restrict__ p, int n, double scale, double* out) {
@@ -210,62 +348,94 @@ __global__ void k_adam(float* __restrict__ p, float* __restrict__ m, float* __re
 
 }  // namespace
 
-cudaError_t launch_planar_to_ndhwc(const float* in, int nf, int C, int B, int64_t V, int k0,
-                                   float fs, void* out, cudaStream_t s) {
-  k_planar_to_ndhwc<<<blocks_for((int64_t)B * V * C), kT, 0, s>>>(in, nf, C, B, V, k0, fs,
-                                                                  (__nv_bfloat16*)out);
+cudaError_t launch_planar_to_ndhwc(const float* in, int nf, int C, int B, int64_t V, int mode,
+                                   const float* sig, void* out, cudaStream_t s) {
+  if (C % 8 || (mode && (nf != 16 || C < 16 || !sig))) return cudaErrorInvalidValue;
+  k_planar_to_ndhwc<<<blocks_for((int64_t)B * V), kT, 0, s>>>(in, nf, C, B, V, mode, sig,
+                                                             (__nv_bfloat16*)out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_ndhwc_to_planar_add(const float* y, int C, int nf, int B, int64_t V,
-                                       const float* base, int nb, float a, float* out,
-                                       cudaStream_t s) {
-  k_ndhwc_to_planar_add<<<blocks_for((int64_t)B * nf * V), kT, 0, s>>>(y, C, nf, B, V, base, nb,
-                                                                      a, out);
+                                       const float* base, int nb, int mode, const float* sig,
+                                       float* out, cudaStream_t s) {
+  if (C % 4 || nf > C || (mode && (!base || nb < 2 * nf))) return cudaErrorInvalidValue;
+  k_ndhwc_to_planar_add<<<blocks_for((int64_t)B * V), kT, 0, s>>>(y, C, nf, B, V, base, nb, mode,
+                                                                 sig, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_incr_scale(const float* x, int nf, int B, int64_t V, float a, int mode,
+                              double* part, int nblk, float* sig, cudaStream_t s) {
+  if (mode) {
+    k_incr_sumsq<<<dim3(nblk, B), kT, 0, s>>>(x, nf, V, part);
+    if (cudaGetLastError() != cudaSuccess) return cudaErrorLaunchFailure;
+  }
+  k_incr_scale<<<(B + 127) / 128, 128, 0, s>>>(part, nblk, B, (double)nf * V, a, mode, sig);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pool(const void* in, int B, int D, int H, int W, int C, void* out,
                         cudaStream_t s) {
-  k_pool<<<blocks_for((int64_t)B * D * H * W * C / 8), kT, 0, s>>>(
-      (const __nv_bfloat16*)in, B, D, H, W, C, (__nv_bfloat16*)out);
+  k_block_sum<<<blocks_for((int64_t)B * D * H * W * C / 64), kT, 0, s>>>(
+      (const __nv_bfloat16*)in, B, D, H, W, C, 0.125f, (__nv_bfloat16*)out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_up_add(const void* coarse, const void* skip, int B, int D, int H, int W, int C,
                           void* out, cudaStream_t s) {
-  k_up_add<<<blocks_for((int64_t)B * D * H * W * C), kT, 0, s>>>(
-      (const __nv_bfloat16*)coarse, (const __nv_bfloat16*)skip, B, D, H, W, C, (__nv_bfloat16*)out);
+  k_up_add<<<blocks_for((int64_t)B * D * H * W * C / 8), kT, 0, s>>>(
+      (const __nv_bfloat16*)coarse, (const __nv_bfloat16*)skip, B, D, H, W, C, 1.0f,
+      (__nv_bfloat16*)out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_down_sum(const void* g, int B, int D, int H, int W, int C, void* out,
                             cudaStream_t s) {
-  k_down_sum<<<blocks_for((int64_t)B * D * H * W * C / 8), kT, 0, s>>>(
-      (const __nv_bfloat16*)g, B, D, H, W, C, (__nv_bfloat16*)out);
+  k_block_sum<<<blocks_for((int64_t)B * D * H * W * C / 64), kT, 0, s>>>(
+      (const __nv_bfloat16*)g, B, D, H, W, C, 1.0f, (__nv_bfloat16*)out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pool_back_add(const void* gc, int B, int D, int H, int W, int C, void* acc,
                                  cudaStream_t s) {
-  k_pool_back_add<<<blocks_for((int64_t)B * D * H * W * C), kT, 0, s>>>(
-      (const __nv_bfloat16*)gc, B, D, H, W, C, (__nv_bfloat16*)acc);
+  k_up_add<<<blocks_for((int64_t)B * D * H * W * C / 8), kT, 0, s>>>(
+      (const __nv_bfloat16*)gc, (const __nv_bfloat16*)acc, B, D, H, W, C, 0.125f,
+      (__nv_bfloat16*)acc);
   return cudaGetLastError();
 }
 
 cudaError_t launch_relu_mask(void* g, const void* y, int64_t n, cudaStream_t s) {
-  k_relu_mask<<<blocks_for(n), kT, 0, s>>>((__nv_bfloat16*)g, (const __nv_bfloat16*)y, n);
+  if (n % 8) return cudaErrorInvalidValue;
+  k_relu_mask<<<blocks_for(n / 8), kT, 0, s>>>((__nv_bfloat16*)g, (const __nv_bfloat16*)y, n / 8);
   return cudaGetLastError();
 }
 
 int mse_blocks() { return 1024; }
 
-cudaError_t launch_mse(const float* pred, int C, int nf, int nxc, int B, int64_t V,
-                       const float* x, const float* y, float a, float scale, void* grad,
-                       double* partials, double* loss, cudaStream_t s) {
-  k_mse<<<mse_blocks(), kT, 0, s>>>(pred, C, nf, nxc, B, V, x, y, a, scale, (__nv_bfloat16*)grad,
-                                    partials);
+// loss = scale * sum q^2 with q = (I + c K) r (c = 0: plain squared error),
+// r the error field of k_err; dL/dpred follows from dL/dr = 2 scale (I + c K) q.
+cudaError_t launch_mse(const float* pred, int C, int nf, int nxc, int B, int D, int H, int W,
+                       const float* x, const float* y, int mode, const float* sig, float c,
+                       float scale, float* r, float* q, void* grad, double* partials,
+                       double* loss, cudaStream_t s) {
+  const int64_t V = (int64_t)D * H * W;
+  const int64_t n = (int64_t)B * nf * V;
+  k_err<<<blocks_for(n), kT, 0, s>>>(pred, C, nf, nxc, B, V, x, y, mode, sig, r);
+  const float* qq = r;
+  if (c != 0.0f) {
+    k_apply_stiff<<<blocks_for(n), kT, 0, s>>>(r, (int64_t)B * nf, D, H, W, c, 1, q);
+    qq = q;
+  }
+  k_sumsq<<<mse_blocks(), kT, 0, s>>>(qq, n, partials);
   k_sum_doubles<<<1, 32, 0, s>>>(partials, mse_blocks(), (double)scale, loss);
+  const float* g = qq;
+  if (c != 0.0f) {
+    k_apply_stiff<<<blocks_for(n), kT, 0, s>>>(q, (int64_t)B * nf, D, H, W, c, 1, r);
+    g = r;
+  }
+  k_grad_out<<<blocks_for((int64_t)B * V * C), kT, 0, s>>>(g, C, nf, B, V, mode, sig, scale,
+                                                          (__nv_bfloat16*)grad);
   return cudaGetLastError();
 }
 

@@ -147,18 +147,27 @@ cudaError_t launch_mass_norm(const float* g, int nx, int ny, int nz, int nf, dou
 
 // Learned surrogate: 3x3x3 convolution kernels (BF16 tensor cores) and the
 // element-wise layers around them.  Activations NDHWC BF16.
+// mma.sync implicit GEMM (any D even, H and W multiples of 8):
 cudaError_t launch_conv3d(int cin, int cout, const void* x, const void* wt, const float* bias,
                           int relu, void* y16, float* y32, int B, int D, int H, int W, int grid,
                           cudaStream_t s);
+// tcgen05 + TMA implicit GEMM (D even, H multiple of 16, W of 8); *err is set
+// to 1 when a pipeline wait expired (the output is then incomplete).
+bool conv3d_tc_shape_ok(int B, int D, int H, int W);
+cudaError_t launch_conv3d_tc(int cin, int cout, const void* x, const void* wt, const float* bias,
+                             int relu, void* y16, float* y32, int B, int D, int H, int W,
+                             int* err, cudaStream_t s);
 int conv_wgrad_blocks(int B, int D, int H, int W, int max_blocks);
 cudaError_t launch_conv3d_wgrad(int cin, int cout, const void* x, const void* dy, float* part,
                                 float* dw, int B, int D, int H, int W, int blocks, cudaStream_t s);
 cudaError_t launch_bias_grad(const void* dy, int C, int64_t nvox, float* db, cudaStream_t s);
-cudaError_t launch_planar_to_ndhwc(const float* in, int nf, int C, int B, int64_t V, int k0,
-                                   float fs, void* out, cudaStream_t s);
+cudaError_t launch_planar_to_ndhwc(const float* in, int nf, int C, int B, int64_t V, int mode,
+                                   const float* sig, void* out, cudaStream_t s);
 cudaError_t launch_ndhwc_to_planar_add(const float* y, int C, int nf, int B, int64_t V,
-                                       const float* base, int nb, float a, float* out,
-                                       cudaStream_t s);
+                                       const float* base, int nb, int mode, const float* sig,
+                                       float* out, cudaStream_t s);
+cudaError_t launch_incr_scale(const float* x, int nf, int B, int64_t V, float a, int mode,
+                              double* part, int nblk, float* sig, cudaStream_t s);
 cudaError_t launch_pool(const void* in, int B, int D, int H, int W, int C, void* out,
                         cudaStream_t s);
 cudaError_t launch_up_add(const void* coarse, const void* skip, int B, int D, int H, int W, int C,
@@ -168,9 +177,10 @@ cudaError_t launch_down_sum(const void* g, int B, int D, int H, int W, int C, vo
 cudaError_t launch_pool_back_add(const void* gc, int B, int D, int H, int W, int C, void* acc,
                                  cudaStream_t s);
 cudaError_t launch_relu_mask(void* g, const void* y, int64_t n, cudaStream_t s);
-cudaError_t launch_mse(const float* pred, int C, int nf, int nxc, int B, int64_t V,
-                       const float* x, const float* y, float a, float scale, void* grad,
-                       double* partials, double* loss, cudaStream_t s);
+cudaError_t launch_mse(const float* pred, int C, int nf, int nxc, int B, int D, int H, int W,
+                       const float* x, const float* y, int mode, const float* sig, float c,
+                       float scale, float* r, float* q, void* grad, double* partials,
+                       double* loss, cudaStream_t s);
 cudaError_t launch_convert_weights(const float* w, int ci, int co, void* fwd, void* bwd,
                                    cudaStream_t s);
 cudaError_t launch_adam(float* p, float* m, float* v, const float* g, int64_t n, float lr,

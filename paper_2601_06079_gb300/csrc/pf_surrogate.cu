@@ -36,6 +36,7 @@ constexpr int kCin0 = 16;     // padded input channels
 constexpr int kCout = 16;     // padded output channels
 constexpr int kConvGrid = 304;
 constexpr int kWgradBlocks = 152;
+constexpr int kSigBlocks = 64;  // blocks per sample of the increment-scale reduction
 
 int64_t w_count(int l) { return (int64_t)27 * kLayers[l].cin * kLayers[l].cout; }
 int64_t w_off(int l) {
@@ -53,7 +54,7 @@ struct Plan {
   int64_t V[4];  // voxels (all samples) per level
   // byte offsets into the workspace
   size_t x16, act[kNL], pool[4], up[4], y32, wf[kNL], wb[kNL];
-  size_t gy, g[4][3], grad, part, msep, loss;
+  size_t gy, g[4][3], grad, part, msep, loss, err, sig, sigp, res, resq;
   size_t total;
 };
 
@@ -77,6 +78,9 @@ Plan make_plan(int B, int D, int H, int W, bool training) {
     p.up[l - 1] = take(2 * p.V[l - 1] * kC);
   }
   p.y32 = take(4 * p.V[0] * kCout);
+  p.err = take(sizeof(int));
+  p.sig = take(sizeof(float) * B);
+  p.sigp = take(sizeof(double) * kSigBlocks * B);
   for (int l = 0; l < kNL; ++l) {
     p.wf[l] = take(2 * w_count(l));
     p.wb[l] = take(2 * w_count(l));
@@ -88,6 +92,8 @@ Plan make_plan(int B, int D, int H, int W, bool training) {
     p.grad = take(4 * param_count());
     p.part = take(4 * (size_t)kWgradBlocks * 27 * kC * kC);
     p.msep = take(8 * 1024);
+    p.res = take(4 * p.V[0] * kNF);
+    p.resq = take(4 * p.V[0] * kNF);
     p.loss = take(8);
   }
   p.total = off;
@@ -111,6 +117,7 @@ struct Net {
   const Plan& p;
   char* ws;
   cudaStream_t s;
+  bool tc;  // tcgen05 convolutions where the level's shape allows
   template <class T>
   T* at(size_t off) const {
     return reinterpret_cast<T*>(ws + off);
@@ -124,6 +131,30 @@ pf_status convert_all(const Net& n, const float* params, bool with_bwd) {
                                        n.at<void>(n.p.wf[l]),
                                        with_bwd ? n.at<void>(n.p.wb[l]) : nullptr, n.s));
   return PF_OK;
+}
+
+// One convolution: the tcgen05 kernel where the shape allows, else mma.sync.
+cudaError_t conv(const Net& n, int cin, int cout, const void* x, const void* wt, const float* bias,
+                 int relu, void* y16, float* y32, int d, int h, int w) {
+  if (n.tc && pf::conv3d_tc_shape_ok(n.p.B, d, h, w))
+    return pf::launch_conv3d_tc(cin, cout, x, wt, bias, relu, y16, y32, n.p.B, d, h, w,
+                                n.at<int>(n.p.err), n.s);
+  return pf::launch_conv3d(cin, cout, x, wt, bias, relu, y16, y32, n.p.B, d, h, w, kConvGrid,
+                           n.s);
+}
+
+// Zero the pipeline-timeout flag before a call; read it after the stream
+// has been synchronised.
+pf_status clear_err(const Net& n) {
+  SG_CUDA(cudaMemsetAsync(n.at<int>(n.p.err), 0, sizeof(int), n.s));
+  return PF_OK;
+}
+
+pf_status check_err(const Net& n) {
+  int e = 0;
+  SG_CUDA(cudaMemcpyAsync(&e, n.at<int>(n.p.err), sizeof(int), cudaMemcpyDeviceToHost, n.s));
+  SG_CUDA(cudaStreamSynchronize(n.s));
+  return e ? PF_ERR_TIMEOUT : PF_OK;
 }
 
 const void* layer_input(const Net& n, int l) {
@@ -143,17 +174,24 @@ pf_status conv_layer(const Net& n, const float* params, int l) {
   const LayerDef& L = kLayers[l];
   const int lv = L.level;
   const bool last = (l == kNL - 1);
-  SG_CUDA(pf::launch_conv3d(L.cin, L.cout, layer_input(n, l), n.at<void>(n.p.wf[l]),
-                            params + b_off(l), L.relu, last ? nullptr : n.at<void>(n.p.act[l]),
-                            last ? n.at<float>(n.p.y32) : nullptr, n.p.B, n.dim(lv, 0),
-                            n.dim(lv, 1), n.dim(lv, 2), kConvGrid, n.s));
+  SG_CUDA(conv(n, L.cin, L.cout, layer_input(n, l), n.at<void>(n.p.wf[l]), params + b_off(l),
+               L.relu, last ? nullptr : n.at<void>(n.p.act[l]),
+               last ? n.at<float>(n.p.y32) : nullptr, n.dim(lv, 0), n.dim(lv, 1), n.dim(lv, 2)));
   return PF_OK;
 }
+
+// Input mode: 8 channels = U^n alone (output unit out_scale); 16 channels =
+// [U^n; U^{n-1}] (the network sees U^n and the previous increment in units of
+// its own RMS; the output unit is out_scale times that RMS).
+int in_mode(int n_in) { return n_in == 2 * kNF ? 1 : 0; }
 
 pf_status forward(const Net& n, const float* params, const float* x, int n_in, float out_scale) {
   const Plan& p = n.p;
   const int64_t V0 = p.V[0] / p.B;
-  SG_CUDA(pf::launch_planar_to_ndhwc(x, n_in, kCin0, p.B, V0, kNF, 1.0f / out_scale,
+  const int mode = in_mode(n_in);
+  SG_CUDA(pf::launch_incr_scale(x, kNF, p.B, V0, out_scale, mode, n.at<double>(p.sigp),
+                                kSigBlocks, n.at<float>(p.sig), n.s));
+  SG_CUDA(pf::launch_planar_to_ndhwc(x, n_in, kCin0, p.B, V0, mode, n.at<float>(p.sig),
                                      n.at<void>(p.x16), n.s));
   pf_status st;
   for (int l = 0; l < kNL; ++l) {
@@ -186,9 +224,7 @@ pf_status backward_layer(const Net& n, int l, void* dy, void* dx, float* grad) {
   SG_CUDA(pf::launch_conv3d_wgrad(L.cin, L.cout, layer_input(n, l), dy, n.at<float>(n.p.part),
                                   grad + w_off(l), n.p.B, d, h, w, blocks, n.s));
   SG_CUDA(pf::launch_bias_grad(dy, L.cout, nvox, grad + b_off(l), n.s));
-  if (dx)
-    SG_CUDA(pf::launch_conv3d(L.cout, L.cin, dy, n.at<void>(n.p.wb[l]), nullptr, 0, dx, nullptr,
-                              n.p.B, d, h, w, kConvGrid, n.s));
+  if (dx) SG_CUDA(conv(n, L.cout, L.cin, dy, n.at<void>(n.p.wb[l]), nullptr, 0, dx, nullptr, d, h, w));
   return PF_OK;
 }
 
@@ -259,32 +295,36 @@ pf_status pf_surrogate_predict(const float* params, float out_scale, const float
     return PF_ERR_ARG;
   const Plan p = make_plan(batch, d, h, w, false);
   if (bytes < p.total || (uintptr_t)ws % 256) return PF_ERR_ARG;
-  Net n{p, (char*)ws, (cudaStream_t)stream};
-  pf_status st = convert_all(n, params, false);
-  if (st != PF_OK) return st;
+  Net n{p, (char*)ws, (cudaStream_t)stream, true};
+  pf_status st = clear_err(n);
+  if (st != PF_OK || (st = convert_all(n, params, false)) != PF_OK) return st;
   if ((st = forward(n, params, x, n_in, out_scale)) != PF_OK) return st;
   SG_CUDA(pf::launch_ndhwc_to_planar_add(n.at<float>(p.y32), kCout, kNF, batch,
-                                         (int64_t)d * h * w, x, n_in, out_scale, out, n.s));
-  return PF_OK;
+                                         (int64_t)d * h * w, x, n_in, in_mode(n_in),
+                                         n.at<float>(p.sig), out, n.s));
+  return check_err(n);
 }
 
 pf_status pf_surrogate_train_step(float* params, float out_scale, float* adam_m, float* adam_v,
                                   int step, double lr, const float* x, int n_in, const float* y,
-                                  int batch, int d, int h, int w, void* ws, size_t bytes,
-                                  void* stream, double* loss) {
+                                  double stiff, int batch, int d, int h, int w, void* ws,
+                                  size_t bytes, void* stream, double* loss) {
   if (!params || !adam_m || !adam_v || !x || !y || !ws || step < 1 || !(lr > 0) ||
+      !(stiff >= 0) || !isfinite(stiff) ||
       !dims_ok(batch, d, h, w) || !scale_ok(out_scale) || (n_in != kNF && n_in != kCin0))
     return PF_ERR_ARG;
   const Plan p = make_plan(batch, d, h, w, true);
   if (bytes < p.total || (uintptr_t)ws % 256) return PF_ERR_ARG;
-  Net n{p, (char*)ws, (cudaStream_t)stream};
-  pf_status st = convert_all(n, params, true);
-  if (st != PF_OK) return st;
+  Net n{p, (char*)ws, (cudaStream_t)stream, true};
+  pf_status st = clear_err(n);
+  if (st != PF_OK || (st = convert_all(n, params, true)) != PF_OK) return st;
   if ((st = forward(n, params, x, n_in, out_scale)) != PF_OK) return st;
   const int64_t V = (int64_t)d * h * w;
   const float scale = (float)(1.0 / ((double)batch * V * kNF));
-  SG_CUDA(pf::launch_mse(n.at<float>(p.y32), kCout, kNF, n_in, batch, V, x, y, out_scale, scale,
-                         n.at<void>(p.gy), n.at<double>(p.msep), n.at<double>(p.loss), n.s));
+  SG_CUDA(pf::launch_mse(n.at<float>(p.y32), kCout, kNF, n_in, batch, d, h, w, x, y,
+                         in_mode(n_in), n.at<float>(p.sig), (float)stiff, scale,
+                         n.at<float>(p.res), n.at<float>(p.resq), n.at<void>(p.gy),
+                         n.at<double>(p.msep), n.at<double>(p.loss), n.s));
   float* grad = n.at<float>(p.grad);
   if ((st = backward(n, grad)) != PF_OK) return st;
   SG_CUDA(pf::launch_adam(params, adam_m, adam_v, grad, param_count(), (float)lr, 0.9f, 0.999f,
@@ -292,32 +332,36 @@ pf_status pf_surrogate_train_step(float* params, float out_scale, float* adam_m,
   if (loss) {
     SG_CUDA(cudaMemcpyAsync(loss, n.at<double>(p.loss), sizeof(double), cudaMemcpyDeviceToHost,
                             n.s));
-    SG_CUDA(cudaStreamSynchronize(n.s));
+    return check_err(n);
   }
   return PF_OK;
 }
 
 pf_status pf_surrogate_loss_grad(const float* params, float out_scale, const float* x, int n_in,
-                                 const float* y, int batch, int d, int h, int w, void* ws,
-                                 size_t bytes, void* stream, double* loss, float* grad) {
+                                 const float* y, double stiff, int batch, int d, int h, int w,
+                                 void* ws, size_t bytes, void* stream, double* loss,
+                                 float* grad) {
   if (!params || !x || !y || !ws || !grad || !dims_ok(batch, d, h, w) || !scale_ok(out_scale) ||
+      !(stiff >= 0) || !isfinite(stiff) ||
       (n_in != kNF && n_in != kCin0))
     return PF_ERR_ARG;
   const Plan p = make_plan(batch, d, h, w, true);
   if (bytes < p.total || (uintptr_t)ws % 256) return PF_ERR_ARG;
-  Net n{p, (char*)ws, (cudaStream_t)stream};
-  pf_status st = convert_all(n, params, true);
-  if (st != PF_OK) return st;
+  Net n{p, (char*)ws, (cudaStream_t)stream, true};
+  pf_status st = clear_err(n);
+  if (st != PF_OK || (st = convert_all(n, params, true)) != PF_OK) return st;
   if ((st = forward(n, params, x, n_in, out_scale)) != PF_OK) return st;
   const int64_t V = (int64_t)d * h * w;
   const float scale = (float)(1.0 / ((double)batch * V * kNF));
-  SG_CUDA(pf::launch_mse(n.at<float>(p.y32), kCout, kNF, n_in, batch, V, x, y, out_scale, scale,
-                         n.at<void>(p.gy), n.at<double>(p.msep), n.at<double>(p.loss), n.s));
+  SG_CUDA(pf::launch_mse(n.at<float>(p.y32), kCout, kNF, n_in, batch, d, h, w, x, y,
+                         in_mode(n_in), n.at<float>(p.sig), (float)stiff, scale,
+                         n.at<float>(p.res), n.at<float>(p.resq), n.at<void>(p.gy),
+                         n.at<double>(p.msep), n.at<double>(p.loss), n.s));
   if ((st = backward(n, grad)) != PF_OK) return st;
   if (loss) {
     SG_CUDA(cudaMemcpyAsync(loss, n.at<double>(p.loss), sizeof(double), cudaMemcpyDeviceToHost,
                             n.s));
-    SG_CUDA(cudaStreamSynchronize(n.s));
+    return check_err(n);
   }
   return PF_OK;
 }
@@ -327,16 +371,18 @@ pf_status pf_conv3d_check(int mode, int cin, int cout, int d, int h, int w, cons
                           void* ws, size_t bytes, void* stream) {
   // Single-layer probe of the convolution kernels for parity tests: planar FP32
   // in and out ([c][d][h][w], one sample), weights [27][c_out][c_in] FP32.
-  // mode 0: out = conv(x) + bias; 1: out = conv^T(dy); 2: out = [dW (27 c_out c_in), db].
+  // mode 0: out = conv(x) + bias; 1: out = conv^T(dy); 2: out = [dW (27 c_out c_in), db];
+  // modes 0 and 1 take the tcgen05 kernel where the shape allows, 3 and 4 are
+  // 0 and 1 on the mma.sync kernel.
   const bool ok_c = (cin == 16 && cout == 32) || (cin == 32 && cout == 32) ||
                     (cin == 32 && cout == 16);
-  if (!ok_c || mode < 0 || mode > 2 || !x || !wt || !out || !ws || d % 2 || h % 8 || w % 8 ||
+  if (!ok_c || mode < 0 || mode > 4 || !x || !wt || !out || !ws || d % 2 || h % 8 || w % 8 ||
       d < 2 || h < 8 || w < 8)
     return PF_ERR_ARG;
   const int64_t V = (int64_t)d * h * w;
   size_t need = al(2 * V * cin) + al(2 * V * cout) + 2 * al(2 * 27 * cin * cout) + al(4 * V * kC) +
-                al(4 * (size_t)kWgradBlocks * 27 * cin * cout);
-  if (bytes < need || (mode != 0 && !dy)) return PF_ERR_ARG;
+                al(4 * (size_t)kWgradBlocks * 27 * cin * cout) + al(sizeof(int));
+  if (bytes < need || (mode != 0 && mode != 3 && !dy) || (uintptr_t)ws % 256) return PF_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   char* p = (char*)ws;
   void* xb = p;
@@ -350,24 +396,34 @@ pf_status pf_conv3d_check(int mode, int cin, int cout, int d, int h, int w, cons
   float* y32 = (float*)p;
   p += al(4 * V * kC);
   float* part = (float*)p;
+  p += al(4 * (size_t)kWgradBlocks * 27 * cin * cout);
+  int* err = (int*)p;
+  const bool tc = (mode == 0 || mode == 1) && pf::conv3d_tc_shape_ok(1, d, h, w);
+  auto run = [&](int ci, int co, const void* in, const void* wts, const float* bs) {
+    return tc ? pf::launch_conv3d_tc(ci, co, in, wts, bs, 0, nullptr, y32, 1, d, h, w, err, s)
+              : pf::launch_conv3d(ci, co, in, wts, bs, 0, nullptr, y32, 1, d, h, w, kConvGrid, s);
+  };
+  SG_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
   SG_CUDA(pf::launch_convert_weights(wt, cin, cout, wf, wb, s));
-  SG_CUDA(pf::launch_planar_to_ndhwc(x, cin, cin, 1, V, cin, 1.0f, xb, s));
-  if (mode == 0) {
-    SG_CUDA(pf::launch_conv3d(cin, cout, xb, wf, bias, 0, nullptr, y32, 1, d, h, w, kConvGrid, s));
-    SG_CUDA(pf::launch_ndhwc_to_planar_add(y32, cout, cout, 1, V, nullptr, 0, 1.0f, out, s));
+  SG_CUDA(pf::launch_planar_to_ndhwc(x, cin, cin, 1, V, 0, nullptr, xb, s));
+  if (mode == 0 || mode == 3) {
+    SG_CUDA(run(cin, cout, xb, wf, bias));
+    SG_CUDA(pf::launch_ndhwc_to_planar_add(y32, cout, cout, 1, V, nullptr, 0, 0, nullptr, out, s));
   } else {
-    SG_CUDA(pf::launch_planar_to_ndhwc(dy, cout, cout, 1, V, cout, 1.0f, db16, s));
-    if (mode == 1) {
-      SG_CUDA(pf::launch_conv3d(cout, cin, db16, wb, nullptr, 0, nullptr, y32, 1, d, h, w,
-                                kConvGrid, s));
-      SG_CUDA(pf::launch_ndhwc_to_planar_add(y32, cin, cin, 1, V, nullptr, 0, 1.0f, out, s));
+    SG_CUDA(pf::launch_planar_to_ndhwc(dy, cout, cout, 1, V, 0, nullptr, db16, s));
+    if (mode == 1 || mode == 4) {
+      SG_CUDA(run(cout, cin, db16, wb, nullptr));
+      SG_CUDA(pf::launch_ndhwc_to_planar_add(y32, cin, cin, 1, V, nullptr, 0, 0, nullptr, out, s));
     } else {
       const int blocks = pf::conv_wgrad_blocks(1, d, h, w, kWgradBlocks);
       SG_CUDA(pf::launch_conv3d_wgrad(cin, cout, xb, db16, part, out, 1, d, h, w, blocks, s));
       SG_CUDA(pf::launch_bias_grad(db16, cout, V, out + 27 * cin * cout, s));
     }
   }
-  return PF_OK;
+  int e = 0;
+  SG_CUDA(cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  SG_CUDA(cudaStreamSynchronize(s));
+  return e ? PF_ERR_TIMEOUT : PF_OK;
 }
 
 }  // extern "C"

@@ -1,18 +1,20 @@
 """Learned warm start for the implicit grain-growth step (Eq. 13-14).
 
 The solver generates its own training data: implicit trajectories of the
-Fan-Chen grain-growth model from seeded Voronoi starts, each consecutive pair
-(U^n, U^{n+1}) a sample.  The surrogate (pf_surrogate_*) sees U^n and, with
-features=True, the residual L r(U^n) of Eq. 14 at U = U^n (the explicit-Euler
-direction, computed by the solver's own residual kernel); it is trained on
-random crops of those pairs to predict U^{n+1} - U^n and then supplies the
-first Newton iterate.  The previous state U^n stays the fallback and the
-reference point.  Newton's converged residual is the judge: both starts are iterated to
-the same tolerance, so the gain shows up as fewer Newton / GMRES iterations
-and less wall time at the same accuracy.
+Fan-Chen grain-growth model from seeded Voronoi starts.  With history (the
+default) the surrogate (pf_surrogate_*) sees two consecutive states
+[U^n; U^{n-1}] and predicts a correction to linear extrapolation,
+U^{n+1} ~ U^n + (U^n - U^{n-1}) + s * net, in units s of the RMS of the
+previous increment, so that the slow late stages of coarsening weigh as much
+in training as the fast early ones.  Its output is the first Newton iterate;
+the previous state U^n stays the fallback (first step, or no surrogate) and
+the reference point.  Newton's converged residual is the judge: every start
+is iterated to the same tolerance, so the gain shows up as fewer Newton /
+GMRES iterations and less wall time at the same accuracy.
 
 All arithmetic runs in the library's kernels; this module only orchestrates
-calls and draws crop positions from the seeded generator.
+calls, copies states into the network's input buffer and draws crop positions
+from the seeded generator.
 """
 from __future__ import annotations
 
@@ -49,20 +51,8 @@ def trajectories(solver, seeds, n_steps, n_grains=64):
     return out
 
 
-def inputs(solver, U, x=None):
-    """Network input for state(s) U [.., 8, n, n, n]: [U, L r(U)] with 16
-    channels (the residual from the solver's kernel, Eq. 14 at U = U^n)."""
-    lead = U.shape[:-4]
-    Ub = U.reshape(-1, *U.shape[-4:])
-    x = torch.empty((Ub.shape[0], 16) + tuple(U.shape[-3:]), device=U.device) if x is None else x
-    for i in range(Ub.shape[0]):
-        x[i, :8].copy_(Ub[i])
-        solver.implicit_residual(Ub[i], Ub[i], out=x[i, 8:])
-    return x.reshape(*lead, 16, *U.shape[-3:])
-
-
 def increment_scale(trajs):
-    """RMS of U^{n+1} - U^n over the training pairs (the network's output unit)."""
+    """RMS of U^{n+1} - U^n over the training pairs (output unit without history)."""
     s, n = 0.0, 0
     for t in trajs:
         d = t[1:] - t[:-1]
@@ -71,32 +61,33 @@ def increment_scale(trajs):
     return (s / n) ** 0.5
 
 
-def train(surr, trajs, iters, crop=64, batch=2, lr=1e-3, seed=0, log_every=0, lr_final=None,
-          feats=None):
-    """Adam on random (pair, crop) samples; crops are crop x crop x crop
-    (the volume itself when it is not larger).  The learning rate decays
-    geometrically to lr_final (default lr / 10).  feats: per trajectory the
-    16-channel inputs of its states (inputs()), for a surrogate with features."""
+def train(surr, trajs, iters, crop=64, batch=4, lr=1e-3, seed=0, log_every=0, lr_final=None,
+          stiff=0.0):
+    """Adam on random (state, crop) samples; crops are crop^3 (the volume itself
+    when it is not larger).  The learning rate decays geometrically to
+    lr_final (default lr / 10).  stiff > 0 weighs the error by (I + stiff K),
+    the linear part of the implicit Jacobian relative to its mass term
+    (stiff = dt L kappa / h^2)."""
     rng = np.random.default_rng(seed)
-    surr.out_scale = increment_scale(trajs)
+    hist = surr.history
+    surr.out_scale = 1.0 if hist else increment_scale(trajs)
     lr_final = lr / 10 if lr_final is None else lr_final
     losses = []
     for it in range(iters):
         xs, ys = [], []
         for _ in range(batch):
-            j = rng.integers(len(trajs))
-            t = trajs[j]
-            k = rng.integers(t.shape[0] - 1)
+            t = trajs[rng.integers(len(trajs))]
+            k = rng.integers(1, t.shape[0] - 1) if hist else rng.integers(t.shape[0] - 1)
             n = t.shape[-1]
             c = min(crop, n)
             o = [rng.integers(n - c + 1) for _ in range(3)]
-            sl = (slice(o[0], o[0] + c), slice(o[1], o[1] + c), slice(o[2], o[2] + c))
-            xs.append((t if feats is None else feats[j])[k][(slice(None),) + sl])
-            ys.append(t[k + 1][(slice(None),) + sl])
+            sl = (slice(None), slice(o[0], o[0] + c), slice(o[1], o[1] + c), slice(o[2], o[2] + c))
+            xs.append(torch.cat([t[k][sl], t[k - 1][sl]]) if hist else t[k][sl])
+            ys.append(t[k + 1][sl])
         x = torch.stack(xs).contiguous()
         y = torch.stack(ys).contiguous()
         rate = lr * (lr_final / lr) ** (it / max(1, iters - 1))
-        losses.append(surr.train_step(x, y, lr=rate))
+        losses.append(surr.train_step(x, y, lr=rate, stiff=stiff))
         if log_every and (it + 1) % log_every == 0:
             print(f"  train {it + 1}: loss {losses[-1]:.3e}", flush=True)
     return losses
@@ -104,24 +95,31 @@ def train(surr, trajs, iters, crop=64, batch=2, lr=1e-3, seed=0, log_every=0, lr
 
 def run(solver, U0, n_steps, surr=None, newton_rtol=1e-5):
     """n_steps implicit steps from U0 with the plain start (surr None) or the
-    learned one; returns (final state, totals, per-step initial residuals)."""
+    learned one; returns (final state, totals, per-step initial residuals).
+    A history surrogate falls back to the plain start on the first step."""
     U = U0.clone()
     tot = dict(newton_iters=0, gmres_iters=0, seconds=0.0, predict_seconds=0.0)
     r0 = []
     guess = torch.empty_like(U)
     x = None
-    if surr is not None and surr.features:
-        x = torch.empty((1, 16) + tuple(U.shape[1:]), device=U.device)
+    if surr is not None:
+        x = torch.empty((1, 16 if surr.history else 8) + tuple(U.shape[1:]), device=U.device)
+    have_prev = False
     for _ in range(n_steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         g = None
-        if surr is not None:
-            surr.predict(U[None] if x is None else inputs(solver, U[None], x), out=guess[None])
+        if surr is not None and (have_prev or not surr.history):
+            x[0, :8].copy_(U)
+            surr.predict(x, out=guess[None])
             torch.cuda.synchronize()
             tot["predict_seconds"] += time.perf_counter() - t0
             g = guess
+        if surr is not None and surr.history:
+            x[0, 8:].copy_(U)  # U^n becomes the previous state of the next step
+            have_prev = True
         st = solver.step_implicit(U, 1, guess=g, newton_rtol=newton_rtol)
+        torch.cuda.synchronize()
         tot["seconds"] += time.perf_counter() - t0
         tot["newton_iters"] += st["newton_iters"]
         tot["gmres_iters"] += st["gmres_iters"]

@@ -21,9 +21,9 @@ def unpack(params):
 
 
 def forward(params, x):
-    """x: [B][8][D][H][W] -> 16-channel increment estimate."""
+    """x: [B][8 or 16][D][H][W] network input -> 16-channel output."""
     Ws = unpack(params)
-    h = torch.cat([x, torch.zeros_like(x)], dim=1)
+    h = x if x.shape[1] == 16 else torch.cat([x, torch.zeros_like(x)], dim=1)
 
     def conv(l, t):
         w, b = Ws[l]
@@ -44,3 +44,43 @@ def forward(params, x):
 def loss(params, x, y):
     out = forward(params, x)[:, :8]
     return ((out - (y - x)) ** 2).mean()
+
+
+def history_input(x):
+    """[U^n; U^{n-1}] -> (network input [U^n, dU / s], s per sample), dU = U^n - U^{n-1},
+    s = RMS of dU over the sample."""
+    u, du = x[:, :8], x[:, :8] - x[:, 8:]
+    s = du.pow(2).mean(dim=(1, 2, 3, 4), keepdim=True).sqrt()
+    return torch.cat([u, du / s], dim=1), s
+
+
+def stiff_apply(e, c):
+    """(I + c K) e for fields e [B][F][D][H][W] on the unit-spaced mesh: K is the
+    assembled Q1 stiffness with natural boundaries, written as the 27-point
+    stencil on the mirror-extended field times the lumped-mass weight
+    (1/2 per boundary axis)."""
+    B, F_, D, H, W = e.shape
+    k = torch.zeros(3, 3, 3, dtype=e.dtype)
+    for dz in range(3):
+        for dy in range(3):
+            for dx in range(3):
+                n = (dz != 1) + (dy != 1) + (dx != 1)
+                k[dz, dy, dx] = {0: 8.0 / 3.0, 1: 0.0, 2: -1.0 / 6.0, 3: -1.0 / 12.0}[n]
+    t = F.pad(e.reshape(B * F_, 1, D, H, W), (1, 1, 1, 1, 1, 1), mode="reflect")
+    se = F.conv3d(t, k[None, None]).reshape(B, F_, D, H, W)
+    w = torch.ones(D, H, W, dtype=e.dtype)
+    w[0] *= 0.5
+    w[-1] *= 0.5
+    w[:, 0] *= 0.5
+    w[:, -1] *= 0.5
+    w[:, :, 0] *= 0.5
+    w[:, :, -1] *= 0.5
+    return e + c * w * se
+
+
+def loss_history(params, h, x, y, s, stiff=0.0):
+    """Loss in units of s of the guess U^n + dU + s * net(h) against y, the
+    error weighted by (I + stiff K)."""
+    out = forward(params, h)[:, :8]
+    u, du = x[:, :8], x[:, :8] - x[:, 8:]
+    return (stiff_apply(out - (y - u - du) / s, stiff) ** 2).mean()

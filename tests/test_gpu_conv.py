@@ -19,7 +19,10 @@ def rel(a, b):
     return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
 
 
-def run(mode, cin, cout, shape, seed):
+def run(mode, cin, cout, shape, seed, with_ref=True):
+    """mode 0/1: forward / data gradient on the tcgen05 kernel where the shape
+    allows (D even, H % 16 == 0, W % 8 == 0), else mma.sync; 3/4: the same on
+    the mma.sync kernel; 2: weight and bias gradients."""
     from paper_2601_06079_gb300 import _lib
     d, h, w = shape
     x = bf16(G.random_field(seed, (cin, d, h, w)))
@@ -28,7 +31,8 @@ def run(mode, cin, cout, shape, seed):
     dy = bf16(G.random_field(seed + 3, (cout, d, h, w)))
     w_or = wt.reshape(3, 3, 3, cout, cin).transpose(3, 4, 0, 1, 2)  # [co][ci][kz][ky][kx]
     cu = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
-    nout = {0: cout * d * h * w, 1: cin * d * h * w, 2: 27 * cin * cout + cout}[mode]
+    nout = {0: cout * d * h * w, 1: cin * d * h * w, 2: 27 * cin * cout + cout,
+            3: cout * d * h * w, 4: cin * d * h * w}[mode]
     out = torch.zeros(nout, device="cuda")
     ws = torch.empty(64 << 20, dtype=torch.uint8, device="cuda")
     X, Wt, B, DY = cu(x), cu(wt), cu(b), cu(dy)
@@ -37,9 +41,11 @@ def run(mode, cin, cout, shape, seed):
                               torch.cuda.current_stream().cuda_stream)
     assert st == 0
     got = out.cpu().numpy().astype(np.float64)
-    if mode == 0:
+    if not with_ref:
+        return got
+    if mode in (0, 3):
         return got.reshape(cout, d, h, w), O.conv3d(x, w_or, b)
-    if mode == 1:
+    if mode in (1, 4):
         return got.reshape(cin, d, h, w), O.conv3d_bwd_data(dy, w_or)
     dw, db = O.conv3d_bwd_weight(x, dy)
     dw = dw.transpose(2, 3, 4, 0, 1).reshape(27, cout, cin)     # back to [tap][co][ci]
@@ -47,11 +53,27 @@ def run(mode, cin, cout, shape, seed):
 
 
 @pytest.mark.parametrize("cin,cout", [(16, 32), (32, 32), (32, 16)])
-@pytest.mark.parametrize("mode", [0, 1, 2])
-@pytest.mark.parametrize("shape", [(2, 8, 8), (6, 16, 24)])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("shape", [(2, 8, 8), (6, 16, 24), (2, 16, 8), (4, 32, 16)])
 def test_conv_kernels_match_oracle(mode, cin, cout, shape):
     got, ref = run(mode, cin, cout, shape, seed=10 * mode + cin + cout)
     assert rel(got, ref) <= 2e-5
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_tcgen05_conv_many_tiles_per_block_matches_oracle(mode):
+    # 512 output tiles: every block runs several tiles, so the 3-stage TMA ring
+    # and the two accumulator buffers wrap and their barrier phases flip
+    got, ref = run(mode, 32, 32, (16, 64, 128), seed=50 + mode)
+    assert rel(got, ref) <= 2e-5
+
+
+@pytest.mark.parametrize("cin,cout", [(16, 32), (32, 32), (32, 16)])
+def test_tcgen05_and_mma_sync_convolutions_agree(cin, cout):
+    for m_tc, m_mma in ((0, 3), (1, 4)):
+        a = run(m_tc, cin, cout, (8, 32, 64), seed=60 + cin + cout, with_ref=False)
+        b = run(m_mma, cin, cout, (8, 32, 64), seed=60 + cin + cout, with_ref=False)
+        assert rel(a, b) <= 1e-5
 
 
 def test_surrogate_zero_output_layer_is_identity_and_training_reduces_loss():
@@ -86,3 +108,35 @@ def test_whole_network_gradient_matches_torch_autograd_reference():
     cos = float(np.dot(gg, gr) / (np.linalg.norm(gg) * np.linalg.norm(gr)))
     assert cos > 0.99, cos
     assert np.linalg.norm(gg - gr) <= 0.1 * np.linalg.norm(gr)
+
+
+def test_history_network_gradient_matches_torch_autograd_reference():
+    # 16-channel input [U^n; U^{n-1}]: the library normalises the previous
+    # increment by its RMS, predicts in those units and weighs every sample alike
+    import paper_2601_06079_gb300 as pf
+    from tests import _torch_unet as R
+    s = pf.Surrogate(history=True)
+    s.init(seed=4, last_layer_scale=1.0)
+    u = torch.from_numpy(G.random_field(6, (2, 8, 16, 64, 64), 0.0, 1.0)).cuda()
+    du = torch.from_numpy(G.random_field(7, (2, 8, 16, 64, 64))).cuda()
+    du[1] *= 0.1  # second sample: a ten times smaller increment
+    x = torch.cat([u, u - 0.01 * du], dim=1).contiguous()
+    y = (u + 0.012 * du + 0.002 * torch.from_numpy(G.random_field(8, (2, 8, 16, 64, 64))).cuda())
+    xd = x.cpu().double()
+    h, sc = R.history_input(xd)
+    h = h.float().to(torch.bfloat16).double()  # the library rounds the network input to BF16
+    for stiff in (0.0, 0.5):
+        loss, g = s.loss_grad(x, y, stiff=stiff)
+        p = s.params.detach().cpu().to(torch.bfloat16).double().requires_grad_(True)
+        lr = R.loss_history(p, h, xd, y.cpu().double(), sc, stiff)
+        lr.backward()
+        gr, gg = p.grad.numpy(), g.cpu().double().numpy()
+        assert abs(loss - lr.item()) <= 2e-2 * lr.item()
+        cos = float(np.dot(gg, gr) / (np.linalg.norm(gg) * np.linalg.norm(gr)))
+        assert cos > 0.99, (stiff, cos)
+        assert np.linalg.norm(gg - gr) <= 0.1 * np.linalg.norm(gr)
+    # zero output layer: the guess is exactly linear extrapolation
+    s.init(seed=4, last_layer_scale=0.0)
+    guess = s.predict(x)
+    ref = 2 * x[:, :8] - x[:, 8:]
+    assert float((guess - ref).abs().max()) <= 1e-6

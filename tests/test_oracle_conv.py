@@ -68,3 +68,17 @@ def test_weight_gradient_matches_central_fd():
         bp[o] += eps
         bm[o] -= eps
         assert abs(db[o] - (loss(w, bp) - loss(w, bm)) / (2 * eps)) < 1e-6 * max(1, abs(db[o]))
+
+
+def test_torch_reference_stiffness_weight_is_the_assembled_q1_stiffness():
+    # the loss weighting (I + c K) of the surrogate's torch reference, against
+    # the oracle's element-by-element assembly of K (natural boundaries, h = 1)
+    import torch
+    from tests import _torch_unet as R
+    rng = np.random.default_rng(3)
+    e = rng.standard_normal((1, 2, 5, 6, 7))
+    got = R.stiff_apply(torch.from_numpy(e), 1.0).numpy() - e
+    P = O.Problem((5, 6, 7), h=1.0, energy="double_well", nf=1, mob=1.0)
+    for f in range(2):
+        ref = P.mobility_stiffness_apply(e[0, f])
+        assert np.abs(got[0, f] - ref).max() <= 1e-12 * np.abs(ref).max()
