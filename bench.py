@@ -13,6 +13,15 @@ trajectories the L2 is flushed by writing a 512 MiB buffer.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+The line also carries "forms": each chosen execution form against its plain
+counterpart on the same inputs at the same accuracy -- the fused graph-replayed
+CH step vs one launch per step vs the plain two-pass step (2048^2); the
+256-instance AC ensemble in one persistent launch vs per-step vs per-instance
+launches; the checkpointed adjoint vs the forward trajectory (512^2, 2000
+steps); and Newton from the learned warm start vs the plain U^n start for 200
+implicit grain-growth steps on 128^3 x 8 fields (surrogate trained in the run
+on trajectories from other seeds).  --no-forms skips them.
+
 --impl reference times the FP64 CPU oracle (the only other arm this
 method has) on a bounded sample of the same workload on the host cores.
 With N > 1 (torchrun) every rank runs an independent replica: the method is
@@ -240,11 +249,171 @@ def run_ours(args):
         "gpu_launches": args.steps * (N_TSTEPS + 4),
         "clocks": clk.summary(),
     }
+    if not args.no_forms:
+        line["forms"] = {"explicit_ch_2048": forms_explicit(dev, stream, flush, c0_host),
+                         "ensemble_256_ac": forms_ensemble(dev, stream, flush),
+                         "adjoint_ch_512": forms_adjoint(dev, stream),
+                         "implicit_warm_start_128": forms_warm_start(dev)}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_sample_steps)
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def _rel(a, b):
+    import torch
+    a, b = a.double(), b.double()
+    return float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+
+
+def _timed(stream, fn, flush=None):
+    """Device time (s) of fn() on `stream`, CUDA events, L2 flushed before."""
+    import torch
+    if flush is not None:
+        flush.zero_()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    fn()
+    b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b) / 1e3
+
+
+def forms_explicit(dev, stream, flush, c0_host, n_steps=2048):
+    """CH 2048^2: fused + graph (default) vs fused per launch vs plain two-pass."""
+    import torch
+
+    import paper_2601_06079_gb300 as pf
+    solver = pf.Solver((N_SIDE, N_SIDE), h=1.0, model="ch", device=dev, stream=stream)
+    solver.set_params(**PAR, shift=0.5)
+    c = torch.empty((N_SIDE, N_SIDE), dtype=torch.float32, device=dev)
+    out, res = {}, {}
+    for form in ("fused_graph", "fused_stream", "two_pass"):
+        solver.set_form(form)
+        c.copy_(c0_host)
+        solver.step_explicit(c, 128)  # warm (graph capture, caches)
+        c.copy_(c0_host)
+        t = _timed(stream, lambda: solver.step_explicit(c, n_steps), flush)
+        res[form] = c.clone()
+        nodes = N_SIDE * N_SIDE
+        out[form] = {"dof_steps_per_s": nodes * DOF_PER_NODE * n_steps / t,
+                     "us_per_step": 1e6 * t / n_steps,
+                     "hbm_frac_of_measured_at_8B": 8 * nodes * n_steps / t / 1e9 / _peaks()[0]}
+    for form in ("fused_stream", "two_pass"):
+        out[form]["rel_l2_vs_fused_graph"] = _rel(res[form], res["fused_graph"])
+        out[form]["fused_graph_speedup"] = (out[form]["us_per_step"] /
+                                            out["fused_graph"]["us_per_step"])
+    out["steps"] = n_steps
+    out["accuracy_gate"] = "each form <= 1e-5 rel L2 vs the FP64 oracle (tests/test_gpu_forms.py)"
+    return out
+
+
+def forms_ensemble(dev, stream, flush, n_steps=1000):
+    """256 uneven AC instances: one persistent graph-captured launch vs one
+    launch per step vs one fused launch per instance and step."""
+    import torch
+
+    import paper_2601_06079_gb300 as pf
+    import pf_inputs as G
+    inst = G.batched_instances(1, count=256)
+    shapes = [(p["n"], p["n"]) for p in inst]
+    e = pf.Ensemble(shapes, device=dev, stream=stream)
+    e.set_params([dict(W=p["W"], kappa=p["kappa"], L=p["L"], dt=0.01) for p in inst])
+    fields = [G.ac_initial(1 + i, s) for i, s in enumerate(shapes)]
+    st0 = e.pack(fields)
+    ty, _ = e.tune(reps=3)
+    nodes = int(st0.numel())
+    rows = {str(k): ty.count(k) for k in sorted(set(ty))}
+    out, res = {"instances": 256, "nodes": nodes, "steps": n_steps,
+                "tuned_band_rows_per_size_class": rows}, {}
+    for mode in ("persistent", "per_step", "plain"):
+        st = st0.clone()
+        e.step(st, 8, mode)  # warm
+        st.copy_(st0)
+        t = _timed(stream, lambda: e.step(st, n_steps, mode), flush)
+        res[mode] = st
+        out[mode] = {"node_steps_per_s": nodes * n_steps / t, "ms": 1e3 * t,
+                     "hbm_frac_of_measured_at_8B": 8 * nodes * n_steps / t / 1e9 / _peaks()[0]}
+    for mode in ("per_step", "plain"):
+        out[mode]["bitwise_equal_to_persistent"] = bool(torch.equal(res[mode], res["persistent"]))
+        out[mode]["persistent_speedup"] = out[mode]["ms"] / out["persistent"]["ms"]
+    return out
+
+
+def forms_warm_start(dev, n=128, n_eval=200, seeds=4, traj_steps=40, iters=1500):
+    """3-D grain growth (8 Fan-Chen order parameters, 128^3, dt 0.5): Newton
+    from the plain U^n start vs the learned history surrogate (trained here on
+    trajectories from other seeds) vs its zero-correction ablation (pure linear
+    extrapolation through the same network path), same Newton tolerance."""
+    import numpy as np
+    import torch
+
+    import paper_2601_06079_gb300 as pf
+    import pf_inputs as G
+    from paper_2601_06079_gb300 import warmstart as WS
+    solver = WS.grain_solver(n, device=dev)
+    t0 = time.perf_counter()
+    data = WS.trajectories(solver, seeds=list(range(101, 101 + seeds)), n_steps=traj_steps)
+    t_data = time.perf_counter() - t0
+    surr = pf.Surrogate(device=dev, history=True)
+    surr.init(seed=7, last_layer_scale=0.0)
+    t0 = time.perf_counter()
+    losses = WS.train(surr, data, iters=iters, crop=64, batch=4, lr=3e-4, seed=1, stiff=0.5)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del data
+    zero = pf.Surrogate(device=dev, history=True)
+    zero.init(seed=7, last_layer_scale=0.0)
+    U0 = torch.from_numpy(G.voronoi_grains(1, n=n, n_seeds=64, n_op=8)).to(dev)
+    out = {"mesh": f"{n}^3 nodes x 8 order parameters", "dt": 0.5, "steps": n_eval,
+           "newton_rtol": 1e-5, "train": {"trajectories": f"seeds 101..{100 + seeds}, "
+                                                           f"{traj_steps} steps each",
+                                          "iters": iters, "seconds_data": t_data,
+                                          "seconds_train": t_train,
+                                          "loss_first_last_50": [float(np.mean(losses[:50])),
+                                                                 float(np.mean(losses[-50:]))]}}
+    res = {}
+    for name, s in (("plain", None), ("learned", surr), ("extrapolation_only", zero)):
+        U, tot, r0 = WS.run(solver, U0, n_eval, s)
+        res[name] = U
+        out[name] = {"newton_iters": tot["newton_iters"], "gmres_iters": tot["gmres_iters"],
+                     "seconds": tot["seconds"], "predict_seconds": tot["predict_seconds"],
+                     "mean_initial_residual": float(np.mean(r0))}
+    for name in ("learned", "extrapolation_only"):
+        out[name]["rel_l2_end_state_vs_plain"] = _rel(res[name], res["plain"])
+        out[name]["speedup_vs_plain"] = out["plain"]["seconds"] / out[name]["seconds"]
+    return out
+
+
+def forms_adjoint(dev, stream, n=512, n_steps=2000, ckpt=100):
+    """CH 512^2, 2000 steps with a per-node mobility field: loss + all gradients
+    by the checkpointed discrete adjoint vs the forward trajectory alone."""
+    import torch
+
+    import paper_2601_06079_gb300 as pf
+    import pf_inputs as G
+    mob = torch.from_numpy(G.gaussian_mobility(3, (n, n))).to(dev)
+    c0 = torch.from_numpy(G.ch_initial(5, (n, n))).to(dev)
+    s = pf.Solver((n, n), h=1.0, model="ch", device=dev, stream=stream)
+    s.set_params(W=1.0, kappa=0.5, mobility=1.0, dt=1e-3, mobility_field=mob)
+    target = c0.clone()
+    s.step_explicit(target, n_steps)
+    c = c0.clone()
+    s.step_explicit(c, 64)
+    c.copy_(c0)
+    t_fwd = _timed(stream, lambda: s.step_explicit(c, n_steps))
+    s.adjoint(c0, target, 200, ckpt)  # warm
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss, g = s.adjoint(c0, target, n_steps, ckpt)
+    torch.cuda.synchronize()
+    t_adj = time.perf_counter() - t0
+    return {"mesh": f"{n}x{n}", "steps": n_steps, "checkpoint_every": ckpt,
+            "forward_ms": 1e3 * t_fwd, "adjoint_ms": 1e3 * t_adj,
+            "adjoint_over_forward": t_adj / t_fwd,
+            "gradients": "kappa, W, M, 262,144-entry mobility field, c0",
+            "accuracy_gate": "<= 1e-4 vs central FD and the oracle adjoint (tests/test_gpu_adjoint.py)"}
 
 
 def cpu_baseline(sample_steps):
@@ -295,20 +464,54 @@ def run_reference(args):
 
 
 def run_profile(args):
-    """Untimed launches of the bench workload for ncu captures."""
+    """Untimed launches of one workload for ncu captures (--target):
+    ch        the bench's CH 2048^2 trajectory (--tsteps steps per trajectory)
+    surrogate two warm-start predictions on 128^3 x 8 fields (tcgen05 convolutions)
+    jvp       three Fan-Chen Jacobian-vector products on 128^3 x 8 fields
+    ensemble  20 persistent steps of the 256-instance AC ensemble"""
     import torch
 
     import paper_2601_06079_gb300 as pf
     import pf_inputs as G
 
-    c = torch.from_numpy(G.ch_initial(1, (N_SIDE, N_SIDE))).cuda()
-    solver = pf.Solver((N_SIDE, N_SIDE), h=1.0, model="ch")
-    solver.set_params(**PAR, shift=0.5)
-    for _ in range(args.warmup + args.steps):
-        solver.step_explicit(c, args.tsteps)
-    E, M = solver.energy(c)
-    torch.cuda.synchronize()
-    print(f"profile run done: energy {E:.6f} mass {M:.6f}")
+    if args.target == "ch":
+        c = torch.from_numpy(G.ch_initial(1, (N_SIDE, N_SIDE))).cuda()
+        solver = pf.Solver((N_SIDE, N_SIDE), h=1.0, model="ch")
+        solver.set_params(**PAR, shift=0.5)
+        for _ in range(args.warmup + args.steps):
+            solver.step_explicit(c, args.tsteps)
+        E, M = solver.energy(c)
+        torch.cuda.synchronize()
+        print(f"profile run done: energy {E:.6f} mass {M:.6f}")
+    elif args.target == "surrogate":
+        n = 128
+        s = pf.Surrogate(history=True)
+        s.init(seed=1, last_layer_scale=1.0)
+        u = torch.from_numpy(G.voronoi_grains(1, n=n, n_seeds=64, n_op=8)).cuda()
+        x = torch.cat([u, 0.99 * u]).reshape(1, 16, n, n, n).contiguous()
+        for _ in range(2):
+            out = s.predict(x)
+        torch.cuda.synchronize()
+        print(f"profile run done: guess norm {float(out.norm()):.6f}")
+    elif args.target == "jvp":
+        from paper_2601_06079_gb300 import warmstart as WS
+        n = 128
+        solver = WS.grain_solver(n)
+        U = torch.from_numpy(G.voronoi_grains(1, n=n, n_seeds=64, n_op=8)).cuda()
+        v = torch.from_numpy(G.random_field(2, (8, n, n, n))).cuda()
+        for _ in range(3):
+            jv = solver.jvp(U, v)
+        torch.cuda.synchronize()
+        print(f"profile run done: |Jv| {float(jv.norm()):.6f}")
+    else:
+        inst = G.batched_instances(1, count=256)
+        shapes = [(p["n"], p["n"]) for p in inst]
+        e = pf.Ensemble(shapes)
+        e.set_params([dict(W=p["W"], kappa=p["kappa"], L=p["L"], dt=0.01) for p in inst])
+        st = e.pack([G.ac_initial(1 + i, sh) for i, sh in enumerate(shapes)])
+        e.step(st, 20, "persistent")
+        torch.cuda.synchronize()
+        print(f"profile run done: mean {float(st.mean()):.6f}")
 
 
 def main():
@@ -319,9 +522,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-sample-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the comparison of execution forms (fused/graph/batched/"
+                         "warm start/adjoint) against their plain counterparts")
     ap.add_argument("--profile", action="store_true",
-                    help="run --steps trajectories of --tsteps time steps untimed (for ncu)")
+                    help="run one workload untimed for ncu (see --target)")
     ap.add_argument("--tsteps", type=int, default=N_TSTEPS)
+    ap.add_argument("--target", default="ch", choices=["ch", "surrogate", "jvp", "ensemble"],
+                    help="workload of --profile")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -116,9 +116,23 @@ pf_status pf_set_params(pf_ctx* ctx, const pf_params* p);
 
 /* Advance `state` (device, n_fields * N FP32, in/out) by n_steps >= 0 explicit
  * Euler steps with the lumped mass, Eq. 12: AC U <- U - dt L r(U)/m;
- * CH c <- c - dt K_M mu / m with m mu = r(c).  2-D: one fused kernel per step;
- * 3-D: residual kernel then update.  Enqueues only. */
+ * CH c <- c - dt K_M mu / m with m mu = r(c).  2-D: one fused kernel per step
+ * (see pf_set_form); 3-D: residual kernel then update.  Enqueues only. */
 pf_status pf_step_explicit(pf_ctx* ctx, float* state, int64_t n_steps);
+
+/* Execution form of the 2-D explicit step (AC and CH without a mobility field;
+ * no counterpart in the paper, which has one array program).  All forms
+ * compute the same discretisation in FP32 on the shifted state:
+ *   PF_FORM_FUSED_GRAPH   one fused kernel per step, replayed from a CUDA graph
+ *                         of 64 steps (default)
+ *   PF_FORM_FUSED_STREAM  the same kernel, one launch per step from the host
+ *   PF_FORM_TWO_PASS      the plain form: node-centric quadrature with index
+ *                         reflection, CH's mu written to and read back from
+ *                         HBM between two launches per step; the state buffer
+ *                         doubles as the mu plane during the call.
+ * PF_ERR_ARG for any other value.  Host only. */
+enum { PF_FORM_FUSED_GRAPH = 0, PF_FORM_FUSED_STREAM = 1, PF_FORM_TWO_PASS = 2 };
+pf_status pf_set_form(pf_ctx* ctx, int form);
 
 /* Advance `state` (device, 3-D, in/out) by n_steps backward-Euler steps, Eq. 13:
  * each step solves R(U) = M (U - U^n)/dt + L r(U) = 0 (Eq. 14) by Newton, each

@@ -86,6 +86,14 @@ class Solver:
             raise ValueError(f"state has {t.numel()} values, mesh needs {want}")
         return t.data_ptr()
 
+    FORMS = {"fused_graph": _lib.PF_FORM_FUSED_GRAPH, "fused_stream": _lib.PF_FORM_FUSED_STREAM,
+             "two_pass": _lib.PF_FORM_TWO_PASS}
+
+    def set_form(self, form):
+        """Execution form of the 2-D explicit step: 'fused_graph' (default),
+        'fused_stream' (one launch per step) or 'two_pass' (the plain form)."""
+        self._check(_lib.pf_set_form(self._ctx, self.FORMS[form]))
+
     def step_explicit(self, state, n_steps):
         """Advance `state` in place by n_steps explicit Euler steps (Eq. 12)."""
         self._check(pf_step_explicit(self._ctx, self._state(state), n_steps))

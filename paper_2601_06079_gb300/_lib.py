@@ -132,6 +132,8 @@ def lib():
         L.pf_energy2d_static.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_double,
                                          C.c_double, C.c_double, C.c_double, C.c_void_p,
                                          C.c_void_p, C.POINTER(C.c_char_p)]
+        L.pf_set_form.restype = st
+        L.pf_set_form.argtypes = [ctx, C.c_int]
         L.pf_last_error.restype = C.c_char_p
         L.pf_last_error.argtypes = [ctx]
         L.pf_destroy.restype = None
@@ -143,6 +145,7 @@ def lib():
 def exported_symbols():
     """Names declared in include/pf.h (checked against the .so by the tests)."""
     return ["pf_create_mesh", "pf_bind_workspace", "pf_set_params", "pf_step_explicit",
+            "pf_set_form",
             "pf_step_implicit", "pf_jvp", "pf_implicit_residual", "pf_adjoint_workspace",
             "pf_adjoint", "pf_create_ensemble", "pf_set_ensemble_params", "pf_tune_ensemble",
             "pf_step_ensemble", "pf_barrier_selftest", "pf_surrogate_param_count",
@@ -170,6 +173,13 @@ def pf_bind_workspace(ctx, ptr, nbytes):
 
 def pf_set_params(ctx, params: pf_params):
     return lib().pf_set_params(ctx, C.byref(params))
+
+
+PF_FORM_FUSED_GRAPH, PF_FORM_FUSED_STREAM, PF_FORM_TWO_PASS = 0, 1, 2
+
+
+def pf_set_form(ctx, form):
+    return lib().pf_set_form(ctx, int(form))
 
 
 def pf_step_explicit(ctx, state_ptr, n_steps):

@@ -26,6 +26,7 @@ struct pf_ctx {
   char* ws = nullptr;
   pf_params par{};
   bool par_set = false;
+  int form = PF_FORM_FUSED_GRAPH;  // execution form of the 2-D explicit step
 
   // workspace segments
   float* buf_a = nullptr;
@@ -582,6 +583,14 @@ pf_status pf_bind_workspace(pf_ctx* c, void* dev_ptr, size_t bytes) {
   return PF_OK;
 }
 
+pf_status pf_set_form(pf_ctx* c, int form) {
+  if (!c) return PF_ERR_ARG;
+  if (form != PF_FORM_FUSED_GRAPH && form != PF_FORM_FUSED_STREAM && form != PF_FORM_TWO_PASS)
+    return fail(c, PF_ERR_ARG, "unknown execution form %d", form);
+  c->form = form;
+  return PF_OK;
+}
+
 pf_status pf_set_params(pf_ctx* c, const pf_params* p) {
   if (!c) return PF_ERR_ARG;
   if (!p) return fail(c, PF_ERR_ARG, "params is NULL");
@@ -648,6 +657,23 @@ pf_status pf_set_params(pf_ctx* c, const pf_params* p) {
   return PF_OK;
 }
 
+// The plain two-pass form: working planes without the ghost frame (buf_a,
+// buf_b as nx x ny arrays), mu in the caller's state buffer meanwhile.
+pf_status step_plain2d(pf_ctx* c, float* state, int64_t n_steps) {
+  const int64_t N = nodes2d(c);
+  const float shift = (float)c->par.shift;
+  const bool ch = c->model == PF_MODEL_CH;
+  float* cur = c->buf_a;
+  float* oth = c->buf_b;
+  PF_CUDA(pf::launch_add(state, cur, N, -shift, c->stream));
+  for (int64_t s = 0; s < n_steps; ++s) {
+    PF_CUDA(pf::launch_plain2d(ch, c->ex, cur, state, oth, c->stream));
+    std::swap(cur, oth);
+  }
+  PF_CUDA(pf::launch_add(cur, state, N, shift, c->stream));
+  return PF_OK;
+}
+
 pf_status pf_step_explicit(pf_ctx* c, float* state, int64_t n_steps) {
   if (!c) return PF_ERR_ARG;
   if (!c->ws) return fail(c, PF_ERR_STATE, "no workspace bound");
@@ -657,13 +683,14 @@ pf_status pf_step_explicit(pf_ctx* c, float* state, int64_t n_steps) {
   if (n_steps == 0) return PF_OK;
   if (c->dim == 3) return step_explicit3d(c, state, n_steps);
   if (c->par.mobility_field) return step_explicit_mob(c, state, n_steps);
+  if (c->form == PF_FORM_TWO_PASS) return step_plain2d(c, state, n_steps);
   const float shift = (float)c->par.shift;
   const int nx = (int)c->n[0], ny = (int)c->n[1];
   // working copies with the mirror frame: d = u - shift (both planes fully defined)
   PF_CUDA(pf::launch_to_work(state, c->buf_a, nx, ny, shift, c->stream));
   PF_CUDA(pf::launch_to_work(state, c->buf_b, nx, ny, shift, c->stream));
   int64_t left = n_steps;
-  if (left >= kGraphSteps) {
+  if (left >= kGraphSteps && c->form == PF_FORM_FUSED_GRAPH) {
     pf_status st = ensure_graph(c);
     if (st != PF_OK) return st;
     for (; left >= kGraphSteps; left -= kGraphSteps) PF_CUDA(cudaGraphLaunch(c->graph, c->stream));

@@ -43,6 +43,9 @@ struct Explicit2DArgs {
 void pack_explicit2d(Explicit2DArgs& a);
 
 cudaError_t launch_ac2d(const Explicit2DArgs& a, cudaStream_t s);
+// The plain two-pass comparison form (d, mu, out: nx x ny arrays without frame).
+cudaError_t launch_plain2d(bool ch, const Explicit2DArgs& a, const float* d, float* mu, float* out,
+                           cudaStream_t s);
 
 // Batched ensembles of 2-D Allen-Cahn instances.
 struct EnsTask {
