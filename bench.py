@@ -468,7 +468,8 @@ def run_profile(args):
     ch        the bench's CH 2048^2 trajectory (--tsteps steps per trajectory)
     surrogate two warm-start predictions on 128^3 x 8 fields (tcgen05 convolutions)
     jvp       three Fan-Chen Jacobian-vector products on 128^3 x 8 fields
-    ensemble  20 persistent steps of the 256-instance AC ensemble"""
+    ensemble  20 steps of the 256-instance AC ensemble, one launch per step (the
+              persistent mode runs the same task body behind a grid barrier)"""
     import torch
 
     import paper_2601_06079_gb300 as pf
@@ -509,7 +510,7 @@ def run_profile(args):
         e = pf.Ensemble(shapes)
         e.set_params([dict(W=p["W"], kappa=p["kappa"], L=p["L"], dt=0.01) for p in inst])
         st = e.pack([G.ac_initial(1 + i, sh) for i, sh in enumerate(shapes)])
-        e.step(st, 20, "persistent")
+        e.step(st, 20, "per_step")
         torch.cuda.synchronize()
         print(f"profile run done: mean {float(st.mean()):.6f}")
 
