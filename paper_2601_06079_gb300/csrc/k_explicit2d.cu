@@ -38,13 +38,19 @@ typedef unsigned long long u64;  // packed FP32 pair: low half = lower column
 constexpr int kPair = 2;                          // columns per lane
 constexpr int kOutCols = 32 * kPair - 2 * kPair;  // 60 output columns per warp
 #ifndef PF_WARPS
-#define PF_WARPS 1
+#define PF_WARPS 2
 #endif
 constexpr int kWarps = PF_WARPS;                  // warps per block, stacked in y
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kGhost = 2;  // mirror frame around the working planes
 #ifndef PF_ROWS_AHEAD
 #define PF_ROWS_AHEAD 3
+#endif
+#ifndef PF_MINB
+#define PF_MINB 1  // minimum resident blocks per SM asked of the register allocator
+#endif
+#ifndef PF_PDL
+#define PF_PDL 0  // 1: programmatic dependent launch, dependents released at block end
 #endif
 constexpr int kAhead = PF_ROWS_AHEAD;  // rows loaded ahead of use (divides the unroll of 6)
 
@@ -300,10 +306,16 @@ __device__ __forceinline__ void sweep_task(const Explicit2DArgs& a, const float*
 // One warp per block and one (column, band) task per warp: many small blocks
 // spread evenly over the SMs and keep each scheduler fed from several warps.
 template <bool kCH, bool kIso, int kTY>
-__global__ void __launch_bounds__(kWarps * 32) k_explicit2d(const Explicit2DArgs a) {
+__global__ void __launch_bounds__(kWarps * 32, PF_MINB) k_explicit2d(const Explicit2DArgs a) {
+#if PF_PDL
+  asm volatile("griddepcontrol.wait;" ::: "memory");  // the previous step is complete
+#endif
   const int warp = threadIdx.x >> 5;
   const int y0 = (blockIdx.y * kWarps + warp) * kTY;
   if (y0 < a.ny) sweep_task<kCH, kIso, kTY>(a, a.in, a.out, Coef{a.pair}, blockIdx.x, y0);
+#if PF_PDL
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#endif
 }
 
 // ---------------------------------------------------------------------------
@@ -475,7 +487,7 @@ __global__ void k_from_work(const float* __restrict__ work, float* __restrict__ 
 }
 
 #ifndef PF_TY_CH
-#define PF_TY_CH 12
+#define PF_TY_CH 6
 #endif
 #ifndef PF_TY_AC
 #define PF_TY_AC 12
@@ -486,8 +498,21 @@ constexpr int kTYCh = PF_TY_CH;
 template <bool kCH, bool kIso, int kTY>
 cudaError_t launch(const Explicit2DArgs& a, cudaStream_t s) {
   const dim3 grid((a.nx + kOutCols - 1) / kOutCols, (a.ny + kWarps * kTY - 1) / (kWarps * kTY));
+#if PF_PDL
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(kWarps * 32);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_explicit2d<kCH, kIso, kTY>, a);
+#else
   k_explicit2d<kCH, kIso, kTY><<<grid, kWarps * 32, 0, s>>>(a);
   return cudaGetLastError();
+#endif
 }
 
 bool is_iso(const Stencil2D& k) { return k.cx == k.cd && k.cy == k.cd; }

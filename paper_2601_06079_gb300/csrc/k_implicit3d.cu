@@ -28,7 +28,10 @@ constexpr int kN = kT + 2;            // staged nodes per edge (1 halo each side
 constexpr int kE = kT + 1;            // elements per edge touching the tile
 constexpr int kNodes = kN * kN * kN;  // 1000
 constexpr int kElems = kE * kE * kE;  // 729
-constexpr int kThreads = 256;
+#ifndef PF_IMP_THREADS
+#define PF_IMP_THREADS 1024
+#endif
+constexpr int kThreads = PF_IMP_THREADS;
 
 __device__ __forceinline__ int mirror(int k, int n) {
   const int p = 2 * (n - 1);
@@ -84,9 +87,11 @@ __global__ void __launch_bounds__(kThreads) k_implicit3d(const Implicit3DArgs a)
   extern __shared__ float smem[];
   float* sU = smem;                          // [NF][kNodes]
   float* sW = sU + NF * kNodes;              // v (JVP) or U^n (residual)
-  float* sS = sW + NF * kNodes;              // [kElems][8] S2 at Gauss points
-  float* sTq = sS + kElems * 8;              // [kElems][8] T (JVP only)
-  float* sE = sTq + (kJVP ? kElems * 8 : 0); // [kElems][8] corner contributions of one field
+  // per-element values are stored [8][kElems] (Gauss point or corner major), so
+  // that consecutive threads (consecutive elements) hit consecutive banks
+  float* sS = sW + NF * kNodes;              // [8][kElems] S2 at Gauss points
+  float* sTq = sS + kElems * 8;              // [8][kElems] T (JVP only)
+  float* sE = sTq + (kJVP ? kElems * 8 : 0); // [8][kElems] corner contributions of one field
 
   const int tiles_x = (a.nx + kT - 1) / kT, tiles_y = (a.ny + kT - 1) / kT;
   const int tile = blockIdx.x;
@@ -136,8 +141,8 @@ __global__ void __launch_bounds__(kThreads) k_implicit3d(const Implicit3DArgs a)
     }
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      sS[e * 8 + q] = S2[q];
-      if (kJVP) sTq[e * 8 + q] = T[q];
+      sS[q * kElems + e] = S2[q];
+      if (kJVP) sTq[q * kElems + e] = T[q];
     }
   }
   __syncthreads();
@@ -161,7 +166,7 @@ __global__ void __launch_bounds__(kThreads) k_implicit3d(const Implicit3DArgs a)
       }
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        const float u = uq[q], s2 = sS[e * 8 + q];
+        const float u = uq[q], s2 = sS[q * kElems + e];
         if (a.double_well) {
           // f = W u^2 (1-u)^2:  f' = 2W u (1-u)(1-2u),  f'' = 2W (1 - 6u + 6u^2)
           hq[q] = kJVP ? a.dw2 * fmaf(6.0f * u, u - 1.0f, 1.0f) * vq[q]
@@ -170,13 +175,14 @@ __global__ void __launch_bounds__(kThreads) k_implicit3d(const Implicit3DArgs a)
           // Fan-Chen: f'_f = u (-a + 2g S2 + (b - 2g) u^2)
           //           (H v)_f = (-a + 2g S2 + (3b - 6g) u^2) v_f + 4g u T
           const float base_c = fmaf(a.two_gamma, s2, -a.alpha);
-          hq[q] = kJVP ? fmaf(fmaf(a.c3b6g, u * u, base_c), vq[q], a.four_gamma * u * sTq[e * 8 + q])
+          hq[q] = kJVP ? fmaf(fmaf(a.c3b6g, u * u, base_c), vq[q],
+                              a.four_gamma * u * sTq[q * kElems + e])
                        : u * fmaf(a.cb2g, u * u, base_c);
         }
       }
       project3(hq, out);
 #pragma unroll
-      for (int k = 0; k < 8; ++k) sE[e * 8 + k] = out[k];
+      for (int k = 0; k < 8; ++k) sE[k * kElems + e] = out[k];
     }
     __syncthreads();
     // node gather: 8 elements around the node, stiffness stencil, mass term
@@ -188,7 +194,7 @@ __global__ void __launch_bounds__(kThreads) k_implicit3d(const Implicit3DArgs a)
 #pragma unroll
       for (int k = 0; k < 8; ++k) {  // element with corner k at this node
         const int ex = lx - (k & 1), ey = ly - ((k >> 1) & 1), ez = lz - (k >> 2);
-        acc += sE[((ez * kE + ey) * kE + ex) * 8 + k];
+        acc += sE[k * kElems + (ez * kE + ey) * kE + ex];
       }
       const float* V = kJVP ? Wf : Uf;  // the stiffness acts on v (JVP) or U (residual)
       const int c0 = nidx(lx, ly, lz);
