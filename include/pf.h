@@ -258,16 +258,19 @@ pf_status pf_energy2d_static(const float* state, int64_t nx, int64_t ny, double 
  * A 3-D U-Net (4 levels, 32 channels, 3x3x3 convolutions, BF16 operands, FP32
  * accumulation; 15 layers) gives the first Newton iterate for U^{n+1}.
  * Parameters are an FP32 array of pf_surrogate_param_count() values: per layer
- * [27][c_out][c_in] weights then c_out biases, in layer order 16->32,
- * 32->32 x 13, 32->16 (inputs padded to 16 channels, outputs 16 -> 8 used).
- * Inputs are planar FP32 [batch][n_in][d][h][w]:
+ * [27][c_out][c_in] weights then c_out biases, in layer order 32->32 x 14,
+ * 32->16 (inputs padded to 32 channels, outputs 16 -> 8 used).
+ * Inputs are planar FP32 [batch][n_in][d][h][w], the current state and up to
+ * two earlier ones:
  *   n_in = 8:  x = U^n.  Guess = U^n + s * net, s = out_scale.
- *   n_in = 16: x = [U^n; U^{n-1}].  The network sees U^n and the previous
- *              increment divided by s_b = out_scale * RMS_b(U^n - U^{n-1})
- *              (per sample b, floored at 1e-30); guess = U^n + (U^n - U^{n-1})
- *              + s_b * net, i.e. a learned correction to linear extrapolation.
- * Outputs [batch][8][d][h][w]; d a multiple of 16, h and w of 64.  out_scale
- * must be positive and finite; anything else is PF_ERR_ARG. */
+ *   n_in = 16: x = [U^n; U^{n-1}].  Guess = 2 U^n - U^{n-1} + s_b * net.
+ *   n_in = 24: x = [U^n; U^{n-1}; U^{n-2}].  Guess = 3 U^n - 3 U^{n-1} + U^{n-2}
+ *              + s_b * net.
+ * With history the network sees U^n and the increments U^{n-k+1} - U^{n-k}
+ * divided by s_b = out_scale * RMS_b(U^n - U^{n-1}) (per sample b, floored at
+ * 1e-30): a learned correction to linear / quadratic extrapolation in units of
+ * the last increment.  Outputs [batch][8][d][h][w]; d a multiple of 16, h and
+ * w of 64.  out_scale must be positive and finite; anything else is PF_ERR_ARG. */
 pf_status pf_surrogate_param_count(int64_t* n_params);
 
 /* Device workspace bytes for one call on [batch][8][d][h][w] (training = 1 adds
@@ -285,8 +288,8 @@ pf_status pf_surrogate_predict(const float* params, float out_scale, const float
 /* One Adam step (lr, beta1 0.9, beta2 0.999, eps 1e-8; step >= 1 for the bias
  * correction) on the loss of the guess against y = U^{n+1} (planar
  * [batch][8][d][h][w]): with e the error field of the guess, in state units
- * for n_in = 8 and in units of s_b for n_in = 16 (every sample then weighs
- * the same whatever the size of its increment),
+ * for n_in = 8 and in units of s_b with history (every sample then weighs the
+ * same whatever the size of its increment),
  *   loss = mean over nodes and fields of ((I + stiff K) e)^2,
  * K the assembled Q1 stiffness of the unit-spaced crop (natural boundary).
  * stiff = dt L kappa / h^2 weighs e the way the linear part of the implicit

@@ -228,21 +228,23 @@ class Ensemble:
 class Surrogate:
     """Learned warm start for the implicit step (a 3-D conv U-Net, see
     pf_surrogate_* in include/pf.h).  Parameters live in FP32 CUDA tensors;
-    init() draws them from a seeded He-normal recipe (output channels 8-15 are
-    zero and stay zero; so are input channels 8-15 without history).
+    init() draws them from a seeded He-normal recipe (output channels 8-15 and
+    the input channels beyond 8 (history + 1) are zero and stay zero).
 
-    history=False: input U^n (8 channels), guess U^n + out_scale * net.
-    history=True:  input [U^n; U^{n-1}] (16 channels), guess
-                   U^n + (U^n - U^{n-1}) + s * net with s = out_scale * RMS(U^n - U^{n-1}):
-                   a learned correction to linear extrapolation, in units of the
-                   previous increment."""
+    history = 0: input U^n (8 channels), guess U^n + out_scale * net.
+    history = 1: input [U^n; U^{n-1}], guess 2 U^n - U^{n-1} + s * net.
+    history = 2: input [U^n; U^{n-1}; U^{n-2}], guess 3 U^n - 3 U^{n-1} + U^{n-2} + s * net.
+    With history s = out_scale * RMS(U^n - U^{n-1}): a learned correction to
+    linear / quadratic extrapolation in units of the last increment.  A
+    history-2 network also accepts 16-channel inputs (its third-state weights
+    then see zeros), which is how the second step of a run is predicted."""
 
-    LAYERS = [(16, 32)] + [(32, 32)] * 13 + [(32, 16)]
+    LAYERS = [(32, 32)] * 14 + [(32, 16)]
 
-    def __init__(self, device="cuda", stream=None, history=False):
+    def __init__(self, device="cuda", stream=None, history=0):
         self.device = torch.device(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-        self.history = history
+        self.history = int(history)
         st, self.n_params = pf_surrogate_param_count()
         if st != 0:
             raise PFError(st, "pf_surrogate_param_count")
@@ -259,13 +261,14 @@ class Surrogate:
         import pf_inputs as G
         chunks = []
         for l, (ci, co) in enumerate(self.LAYERS):
-            fan_in = 27 * (8 if l == 0 and not self.history else ci)
+            used = 8 * (self.history + 1)
+            fan_in = 27 * (used if l == 0 else ci)
             z = G.uniform(seed * 1000 + l, 27 * co * ci * 2, 0.0, 1.0, "surrogate")
             u1, u2 = np.maximum(z[0::2], 1e-12), z[1::2]
             normal = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)  # Box-Muller
             w = (normal * np.sqrt(2.0 / fan_in)).reshape(27, co, ci)
-            if l == 0 and not self.history:
-                w[:, :, 8:] = 0.0
+            if l == 0:
+                w[:, :, used:] = 0.0
             if l == len(self.LAYERS) - 1:
                 w *= last_layer_scale
                 w[:, 8:, :] = 0.0
@@ -286,8 +289,8 @@ class Surrogate:
 
     def _dims(self, x):
         b, nin, d, h, w = x.shape
-        if nin != (16 if self.history else 8):
-            raise ValueError("input channels: 8 = U^n, or 16 = [U^n; U^{n-1}] with history")
+        if nin % 8 or not 8 <= nin <= 8 * (self.history + 1):
+            raise ValueError("input channels: 8 (U^n) times 1 + the states of history used")
         return b, nin, d, h, w
 
     def predict(self, x, out=None):

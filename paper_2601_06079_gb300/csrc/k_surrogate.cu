@@ -41,9 +41,10 @@ __device__ __forceinline__ uint4 pack8(const float* f) {
 
 // planar [B][nf][V] FP32 -> NDHWC BF16 [B][V][C], one thread per voxel (the
 // planar reads coalesce across the warp, the voxel's C channels go out as
-// 16-byte stores).  mode 0: channels < nf copied, the rest zero.  mode 1
-// (nf = 16, two consecutive states [U^n; U^{n-1}]): channels 0..7 = U^n,
-// 8..15 = (U^n - U^{n-1}) / sig[b], the rest zero.
+// 16-byte stores).  mode 0: channels < nf copied, the rest zero.  mode h = 1, 2
+// (nf = 8 (h + 1): the states [U^n; U^{n-1}; ...; U^{n-h}]): channels 0..7 =
+// U^n, then for k = 1..h the increment (U^{n-k+1} - U^{n-k}) / sig[b], the
+// rest zero.
 __global__ void k_planar_to_ndhwc(const float* __restrict__ in, int nf, int C, int B, int64_t V,
                                   int mode, const float* __restrict__ sig,
                                   __nv_bfloat16* __restrict__ out) {
@@ -58,7 +59,7 @@ __global__ void k_planar_to_ndhwc(const float* __restrict__ in, int nf, int C, i
       for (int k = 0; k < 8; ++k) {
         const int c = c0 + k;
         float a = c < nf ? in[(b * nf + c) * V + v] : 0.0f;
-        if (mode && c >= 8 && c < 16) a = (in[(b * nf + c - 8) * V + v] - a) * inv;
+        if (mode && c >= 8 && c < nf) a = (in[(b * nf + c - 8) * V + v] - a) * inv;
         f[k] = a;
       }
       dst[c0 / 8] = pack8(f);
@@ -66,10 +67,19 @@ __global__ void k_planar_to_ndhwc(const float* __restrict__ in, int nf, int C, i
   }
 }
 
-// out planar [B][nf][V] = base + (mode 1: base[:nf] - base[nf:2nf]) + sig[b] * y
-// (first nf channels of the NDHWC FP32 y with C channels); base is planar with
-// nb channels per sample and may be null (then mode must be 0); sig null = 1.
-// One thread per voxel.
+// out planar [B][nf][V] = skip + sig[b] * y (first nf channels of the NDHWC
+// FP32 y with C channels), sig null = 1.  base: planar with nb channels per
+// sample, or null (then mode must be 0).  The skip is mode 0: base[:nf] (U^n);
+// mode 1: 2 U^n - U^{n-1} (linear extrapolation); mode 2: 3 U^n - 3 U^{n-1} +
+// U^{n-2} (quadratic extrapolation).  One thread per voxel.
+__device__ __forceinline__ float skip_value(const float* __restrict__ base, int64_t s0, int64_t st,
+                                            int mode) {
+  const float u = base[s0];
+  if (mode == 1) return 2.0f * u - base[s0 + st];
+  if (mode == 2) return fmaf(3.0f, u - base[s0 + st], base[s0 + 2 * st]);
+  return u;
+}
+
 __global__ void k_ndhwc_to_planar_add(const float* __restrict__ y, int C, int nf, int B, int64_t V,
                                       const float* __restrict__ base, int nb, int mode,
                                       const float* __restrict__ sig, float* __restrict__ out) {
@@ -84,11 +94,8 @@ __global__ void k_ndhwc_to_planar_add(const float* __restrict__ y, int C, int nf
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         if (f + k >= nf) break;
-        float o = 0.0f;
-        if (base) {
-          const float u = base[(b * nb + f + k) * V + v];
-          o = mode ? 2.0f * u - base[(b * nb + nf + f + k) * V + v] : u;
-        }
+        const float o = base ? skip_value(base, (b * nb + f + k) * V + v, (int64_t)nf * V, mode)
+                             : 0.0f;
         out[(b * nf + f + k) * V + v] = fmaf(a, tv[k], o);
       }
     }
@@ -96,13 +103,14 @@ __global__ void k_ndhwc_to_planar_add(const float* __restrict__ y, int C, int nf
 }
 
 // Per-sample output unit: sig[b] = a (mode 0) or a * RMS over the sample of
-// U^n - U^{n-1} (mode 1, x = [U^n; U^{n-1}] with 2 nf channels), floored at
-// 1e-30.  part holds gridDim.x partial sums per sample (fixed-order reduction).
-__global__ void k_incr_sumsq(const float* __restrict__ x, int nf, int64_t V,
+// U^n - U^{n-1} (modes 1, 2: x holds nxc = nf (mode + 1) channels per sample,
+// U^n first), floored at 1e-30.  part holds gridDim.x partial sums per sample
+// (fixed-order reduction).
+__global__ void k_incr_sumsq(const float* __restrict__ x, int nf, int nxc, int64_t V,
                              double* __restrict__ part) {
   __shared__ double red[kT];
   const int b = blockIdx.y;
-  const float* u = x + (int64_t)b * 2 * nf * V;
+  const float* u = x + (int64_t)b * nxc * V;
   double acc = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)nf * V;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -210,9 +218,10 @@ __global__ void k_relu_mask(__nv_bfloat16* __restrict__ g, const __nv_bfloat16* 
 }
 
 // Error field of the prediction against the target state y = U^{n+1} (planar,
-// nf channels) for inputs x (planar, nxc channels, U^n first):
+// nf channels) for inputs x (planar, nxc channels, U^n first), with the skip
+// of k_ndhwc_to_planar_add:
 //   mode 0: r = sig_b * pred - (y - U^n)                       (state units)
-//   mode 1: r = pred - (y - U^n - (U^n - U^{n-1})) / sig_b     (units of sig_b)
+//   mode h: r = pred - (y - skip) / sig_b                      (units of sig_b)
 // pred = first nf channels of the NDHWC FP32 network output (C channels);
 // r is written planar [B][nf][V].
 __global__ void k_err(const float* __restrict__ pred, int C, int nf, int nxc, int B, int64_t V,
@@ -221,15 +230,10 @@ __global__ void k_err(const float* __restrict__ pred, int C, int nf, int nxc, in
   const int64_t n = (int64_t)B * nf * V;
   for (int64_t i = gtid(); i < n; i += grid_stride()) {
     const int64_t v = i % V, c = (i / V) % nf, b = i / (nf * V);
-    const float u = x[(b * nxc + c) * V + v];
-    float t = y[i] - u;
+    const int64_t s0 = (b * nxc + c) * V + v;
+    const float t = y[i] - skip_value(x, s0, (int64_t)nf * V, mode);
     const float p = pred[(b * V + v) * C + c];
-    if (mode) {
-      t -= u - x[(b * nxc + nf + c) * V + v];
-      r[i] = p - t / sig[b];
-    } else {
-      r[i] = fmaf(sig[b], p, -t);
-    }
+    r[i] = mode ? p - t / sig[b] : fmaf(sig[b], p, -t);
   }
 }
 
@@ -350,7 +354,7 @@ __global__ void k_adam(float* __restrict__ p, float* __restrict__ m, float* __re
 
 cudaError_t launch_planar_to_ndhwc(const float* in, int nf, int C, int B, int64_t V, int mode,
                                    const float* sig, void* out, cudaStream_t s) {
-  if (C % 8 || (mode && (nf != 16 || C < 16 || !sig))) return cudaErrorInvalidValue;
+  if (C % 8 || nf > C || (mode && (nf != 8 * (mode + 1) || !sig))) return cudaErrorInvalidValue;
   k_planar_to_ndhwc<<<blocks_for((int64_t)B * V), kT, 0, s>>>(in, nf, C, B, V, mode, sig,
                                                              (__nv_bfloat16*)out);
   return cudaGetLastError();
@@ -359,7 +363,7 @@ cudaError_t launch_planar_to_ndhwc(const float* in, int nf, int C, int B, int64_
 cudaError_t launch_ndhwc_to_planar_add(const float* y, int C, int nf, int B, int64_t V,
                                        const float* base, int nb, int mode, const float* sig,
                                        float* out, cudaStream_t s) {
-  if (C % 4 || nf > C || (mode && (!base || nb < 2 * nf))) return cudaErrorInvalidValue;
+  if (C % 4 || nf > C || (mode && (!base || nb < (mode + 1) * nf))) return cudaErrorInvalidValue;
   k_ndhwc_to_planar_add<<<blocks_for((int64_t)B * V), kT, 0, s>>>(y, C, nf, B, V, base, nb, mode,
                                                                  sig, out);
   return cudaGetLastError();
@@ -368,7 +372,7 @@ cudaError_t launch_ndhwc_to_planar_add(const float* y, int C, int nf, int B, int
 cudaError_t launch_incr_scale(const float* x, int nf, int B, int64_t V, float a, int mode,
                               double* part, int nblk, float* sig, cudaStream_t s) {
   if (mode) {
-    k_incr_sumsq<<<dim3(nblk, B), kT, 0, s>>>(x, nf, V, part);
+    k_incr_sumsq<<<dim3(nblk, B), kT, 0, s>>>(x, nf, nf * (mode + 1), V, part);
     if (cudaGetLastError() != cudaSuccess) return cudaErrorLaunchFailure;
   }
   k_incr_scale<<<(B + 127) / 128, 128, 0, s>>>(part, nblk, B, (double)nf * V, a, mode, sig);

@@ -1,10 +1,11 @@
 // Learned warm start for the implicit step: a small 3-D U-Net (4 levels, 32
 // channels, 3x3x3 convolutions, BF16 operands with FP32 accumulation) that
-// maps U^n to an estimate of U^{n+1} - U^n.  Forward, backward and the Adam
-// update all run in this library's kernels; the caller owns every buffer.
+// maps U^n (and up to two earlier states) to a correction of the first Newton
+// iterate for U^{n+1}.  Forward, backward and the Adam update all run in this
+// library's kernels; the caller owns every buffer.
 //
-// Layers (input channels padded 8 -> 16, output 16 -> first 8 used):
-//   level 0: c0 16->32, c1 32->32 (skip s0) ; pool
+// Layers (input channels padded 8/16/24 -> 32, output 16 -> first 8 used):
+//   level 0: c0 32->32, c1 32->32 (skip s0) ; pool
 //   level 1: c2, c3 (skip s1) ; pool      level 2: c4, c5 (skip s2) ; pool
 //   level 3: c6, c7 ; up + s2 -> c8, c9 ; up + s1 -> c10, c11 ; up + s0 -> c12, c13
 //   c14 32->16 (no ReLU) -> increment.
@@ -27,12 +28,12 @@ struct LayerDef {
 
 constexpr int kNL = 15;
 constexpr LayerDef kLayers[kNL] = {
-    {16, 32, 1, 0}, {32, 32, 1, 0}, {32, 32, 1, 1}, {32, 32, 1, 1}, {32, 32, 1, 2},
+    {32, 32, 1, 0}, {32, 32, 1, 0}, {32, 32, 1, 1}, {32, 32, 1, 1}, {32, 32, 1, 2},
     {32, 32, 1, 2}, {32, 32, 1, 3}, {32, 32, 1, 3}, {32, 32, 1, 2}, {32, 32, 1, 2},
     {32, 32, 1, 1}, {32, 32, 1, 1}, {32, 32, 1, 0}, {32, 32, 1, 0}, {32, 16, 0, 0}};
 constexpr int kNF = 8;        // order parameters
 constexpr int kC = 32;        // feature channels
-constexpr int kCin0 = 16;     // padded input channels
+constexpr int kCin0 = 32;     // padded input channels
 constexpr int kCout = 16;     // padded output channels
 constexpr int kConvGrid = 304;
 constexpr int kWgradBlocks = 152;
@@ -180,10 +181,12 @@ pf_status conv_layer(const Net& n, const float* params, int l) {
   return PF_OK;
 }
 
-// Input mode: 8 channels = U^n alone (output unit out_scale); 16 channels =
-// [U^n; U^{n-1}] (the network sees U^n and the previous increment in units of
-// its own RMS; the output unit is out_scale times that RMS).
-int in_mode(int n_in) { return n_in == 2 * kNF ? 1 : 0; }
+// Input mode = number of previous states: 8 channels = U^n alone (output unit
+// out_scale); 16 = [U^n; U^{n-1}] and 24 = [U^n; U^{n-1}; U^{n-2}] (the network
+// sees U^n and the increments in units of the RMS of the last one; the output
+// unit is out_scale times that RMS, on top of linear or quadratic extrapolation).
+int in_mode(int n_in) { return n_in / kNF - 1; }
+bool n_in_ok(int n_in) { return n_in == kNF || n_in == 2 * kNF || n_in == 3 * kNF; }
 
 pf_status forward(const Net& n, const float* params, const float* x, int n_in, float out_scale) {
   const Plan& p = n.p;
@@ -291,7 +294,7 @@ pf_status pf_surrogate_predict(const float* params, float out_scale, const float
                                float* out, int batch, int d, int h, int w, void* ws, size_t bytes,
                                void* stream) {
   if (!params || !x || !out || !ws || !dims_ok(batch, d, h, w) || !scale_ok(out_scale) ||
-      (n_in != kNF && n_in != kCin0))
+      !n_in_ok(n_in))
     return PF_ERR_ARG;
   const Plan p = make_plan(batch, d, h, w, false);
   if (bytes < p.total || (uintptr_t)ws % 256) return PF_ERR_ARG;
@@ -311,7 +314,7 @@ pf_status pf_surrogate_train_step(float* params, float out_scale, float* adam_m,
                                   size_t bytes, void* stream, double* loss) {
   if (!params || !adam_m || !adam_v || !x || !y || !ws || step < 1 || !(lr > 0) ||
       !(stiff >= 0) || !isfinite(stiff) ||
-      !dims_ok(batch, d, h, w) || !scale_ok(out_scale) || (n_in != kNF && n_in != kCin0))
+      !dims_ok(batch, d, h, w) || !scale_ok(out_scale) || !n_in_ok(n_in))
     return PF_ERR_ARG;
   const Plan p = make_plan(batch, d, h, w, true);
   if (bytes < p.total || (uintptr_t)ws % 256) return PF_ERR_ARG;
@@ -343,7 +346,7 @@ pf_status pf_surrogate_loss_grad(const float* params, float out_scale, const flo
                                  float* grad) {
   if (!params || !x || !y || !ws || !grad || !dims_ok(batch, d, h, w) || !scale_ok(out_scale) ||
       !(stiff >= 0) || !isfinite(stiff) ||
-      (n_in != kNF && n_in != kCin0))
+      !n_in_ok(n_in))
     return PF_ERR_ARG;
   const Plan p = make_plan(batch, d, h, w, true);
   if (bytes < p.total || (uintptr_t)ws % 256) return PF_ERR_ARG;

@@ -1,14 +1,15 @@
 """Learned warm start for the implicit grain-growth step (Eq. 13-14).
 
 The solver generates its own training data: implicit trajectories of the
-Fan-Chen grain-growth model from seeded Voronoi starts.  With history (the
-default) the surrogate (pf_surrogate_*) sees two consecutive states
-[U^n; U^{n-1}] and predicts a correction to linear extrapolation,
-U^{n+1} ~ U^n + (U^n - U^{n-1}) + s * net, in units s of the RMS of the
-previous increment, so that the slow late stages of coarsening weigh as much
-in training as the fast early ones.  Its output is the first Newton iterate;
-the previous state U^n stays the fallback (first step, or no surrogate) and
-the reference point.  Newton's converged residual is the judge: every start
+Fan-Chen grain-growth model from seeded Voronoi starts.  A surrogate with
+history h (pf_surrogate_*) sees the current state and h earlier ones and
+predicts a correction to polynomial extrapolation through them (h = 2:
+U^{n+1} ~ 3 U^n - 3 U^{n-1} + U^{n-2} + s * net), in units s of the RMS of
+the last increment, so that the slow late stages of coarsening weigh as much
+in training as the fast early ones.  Its output is the first Newton iterate.
+While fewer earlier states exist the surrogate runs with what there is (the
+second step of a run uses one earlier state), and the plain start U^n is the
+fallback on the first step and without a surrogate.  Newton's converged residual is the judge: every start
 is iterated to the same tolerance, so the gain shows up as fewer Newton /
 GMRES iterations and less wall time at the same accuracy.
 
@@ -71,18 +72,19 @@ def train(surr, trajs, iters, crop=64, batch=4, lr=1e-3, seed=0, log_every=0, lr
     rng = np.random.default_rng(seed)
     hist = surr.history
     surr.out_scale = 1.0 if hist else increment_scale(trajs)
+    assert all(t.shape[0] >= hist + 2 for t in trajs), "trajectories too short for the history"
     lr_final = lr / 10 if lr_final is None else lr_final
     losses = []
     for it in range(iters):
         xs, ys = [], []
         for _ in range(batch):
             t = trajs[rng.integers(len(trajs))]
-            k = rng.integers(1, t.shape[0] - 1) if hist else rng.integers(t.shape[0] - 1)
+            k = rng.integers(hist, t.shape[0] - 1)
             n = t.shape[-1]
             c = min(crop, n)
             o = [rng.integers(n - c + 1) for _ in range(3)]
             sl = (slice(None), slice(o[0], o[0] + c), slice(o[1], o[1] + c), slice(o[2], o[2] + c))
-            xs.append(torch.cat([t[k][sl], t[k - 1][sl]]) if hist else t[k][sl])
+            xs.append(torch.cat([t[k - j][sl] for j in range(hist + 1)]))
             ys.append(t[k + 1][sl])
         x = torch.stack(xs).contiguous()
         y = torch.stack(ys).contiguous()
@@ -96,28 +98,32 @@ def train(surr, trajs, iters, crop=64, batch=4, lr=1e-3, seed=0, log_every=0, lr
 def run(solver, U0, n_steps, surr=None, newton_rtol=1e-5):
     """n_steps implicit steps from U0 with the plain start (surr None) or the
     learned one; returns (final state, totals, per-step initial residuals).
-    A history surrogate falls back to the plain start on the first step."""
+    A history surrogate falls back to the plain start on the first step and
+    uses the earlier states there are until it has all of them."""
     U = U0.clone()
     tot = dict(newton_iters=0, gmres_iters=0, seconds=0.0, predict_seconds=0.0)
     r0 = []
     guess = torch.empty_like(U)
+    h = surr.history if surr is not None else 0
     x = None
     if surr is not None:
-        x = torch.empty((1, 16 if surr.history else 8) + tuple(U.shape[1:]), device=U.device)
-    have_prev = False
+        x = torch.empty((1, 8 * (h + 1)) + tuple(U.shape[1:]), device=U.device)
+    avail = 0  # earlier states held in x[0, 8:]
     for _ in range(n_steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         g = None
-        if surr is not None and (have_prev or not surr.history):
+        if surr is not None and (avail > 0 or h == 0):
             x[0, :8].copy_(U)
-            surr.predict(x, out=guess[None])
+            surr.predict(x[:, :8 * (avail + 1)], out=guess[None])
             torch.cuda.synchronize()
             tot["predict_seconds"] += time.perf_counter() - t0
             g = guess
-        if surr is not None and surr.history:
-            x[0, 8:].copy_(U)  # U^n becomes the previous state of the next step
-            have_prev = True
+        if h > 0:  # U^n becomes the first earlier state of the next step
+            for j in range(min(avail, h - 1), 0, -1):
+                x[0, 8 * (j + 1):8 * (j + 2)].copy_(x[0, 8 * j:8 * (j + 1)])
+            x[0, 8:16].copy_(U)
+            avail = min(avail + 1, h)
         st = solver.step_implicit(U, 1, guess=g, newton_rtol=newton_rtol)
         torch.cuda.synchronize()
         tot["seconds"] += time.perf_counter() - t0

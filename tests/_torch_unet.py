@@ -4,7 +4,7 @@ FP64 on the CPU, to check the library's whole-network gradient."""
 import torch
 import torch.nn.functional as F
 
-LAYERS = [(16, 32, 1, 0), (32, 32, 1, 0), (32, 32, 1, 1), (32, 32, 1, 1), (32, 32, 1, 2),
+LAYERS = [(32, 32, 1, 0), (32, 32, 1, 0), (32, 32, 1, 1), (32, 32, 1, 1), (32, 32, 1, 2),
           (32, 32, 1, 2), (32, 32, 1, 3), (32, 32, 1, 3), (32, 32, 1, 2), (32, 32, 1, 2),
           (32, 32, 1, 1), (32, 32, 1, 1), (32, 32, 1, 0), (32, 32, 1, 0), (32, 16, 0, 0)]
 
@@ -23,7 +23,8 @@ def unpack(params):
 def forward(params, x):
     """x: [B][8 or 16][D][H][W] network input -> 16-channel output."""
     Ws = unpack(params)
-    h = x if x.shape[1] == 16 else torch.cat([x, torch.zeros_like(x)], dim=1)
+    pad = torch.zeros((x.shape[0], 32 - x.shape[1]) + tuple(x.shape[2:]), dtype=x.dtype)
+    h = torch.cat([x, pad], dim=1)
 
     def conv(l, t):
         w, b = Ws[l]
@@ -47,11 +48,20 @@ def loss(params, x, y):
 
 
 def history_input(x):
-    """[U^n; U^{n-1}] -> (network input [U^n, dU / s], s per sample), dU = U^n - U^{n-1},
-    s = RMS of dU over the sample."""
-    u, du = x[:, :8], x[:, :8] - x[:, 8:]
-    s = du.pow(2).mean(dim=(1, 2, 3, 4), keepdim=True).sqrt()
-    return torch.cat([u, du / s], dim=1), s
+    """[U^n; U^{n-1}; ...] -> (network input [U^n, dU_1 / s, dU_2 / s, ...], s per
+    sample), dU_k = U^{n-k+1} - U^{n-k}, s = RMS of dU_1 over the sample."""
+    h = x.shape[1] // 8 - 1
+    st = [x[:, 8 * k:8 * (k + 1)] for k in range(h + 1)]
+    du = [st[k] - st[k + 1] for k in range(h)]
+    s = du[0].pow(2).mean(dim=(1, 2, 3, 4), keepdim=True).sqrt()
+    return torch.cat([st[0]] + [d / s for d in du], dim=1), s
+
+
+def extrapolate(x):
+    """Linear (2 states) or quadratic (3 states) extrapolation to the next state."""
+    h = x.shape[1] // 8 - 1
+    st = [x[:, 8 * k:8 * (k + 1)] for k in range(h + 1)]
+    return 2 * st[0] - st[1] if h == 1 else 3 * st[0] - 3 * st[1] + st[2]
 
 
 def stiff_apply(e, c):
@@ -79,8 +89,7 @@ def stiff_apply(e, c):
 
 
 def loss_history(params, h, x, y, s, stiff=0.0):
-    """Loss in units of s of the guess U^n + dU + s * net(h) against y, the
-    error weighted by (I + stiff K)."""
+    """Loss in units of s of the guess extrapolate(x) + s * net(h) against y,
+    the error weighted by (I + stiff K)."""
     out = forward(params, h)[:, :8]
-    u, du = x[:, :8], x[:, :8] - x[:, 8:]
-    return (stiff_apply(out - (y - u - du) / s, stiff) ** 2).mean()
+    return (stiff_apply(out - (y - extrapolate(x)) / s, stiff) ** 2).mean()

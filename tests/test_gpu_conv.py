@@ -110,17 +110,20 @@ def test_whole_network_gradient_matches_torch_autograd_reference():
     assert np.linalg.norm(gg - gr) <= 0.1 * np.linalg.norm(gr)
 
 
-def test_history_network_gradient_matches_torch_autograd_reference():
-    # 16-channel input [U^n; U^{n-1}]: the library normalises the previous
-    # increment by its RMS, predicts in those units and weighs every sample alike
+@pytest.mark.parametrize("hist", [1, 2])
+def test_history_network_gradient_matches_torch_autograd_reference(hist):
+    # inputs [U^n; U^{n-1}(; U^{n-2})]: the library normalises the increments by
+    # the RMS of the last one, predicts a correction to linear / quadratic
+    # extrapolation in those units and weighs every sample alike
     import paper_2601_06079_gb300 as pf
     from tests import _torch_unet as R
-    s = pf.Surrogate(history=True)
+    s = pf.Surrogate(history=hist)
     s.init(seed=4, last_layer_scale=1.0)
     u = torch.from_numpy(G.random_field(6, (2, 8, 16, 64, 64), 0.0, 1.0)).cuda()
     du = torch.from_numpy(G.random_field(7, (2, 8, 16, 64, 64))).cuda()
     du[1] *= 0.1  # second sample: a ten times smaller increment
-    x = torch.cat([u, u - 0.01 * du], dim=1).contiguous()
+    states = [u - 0.01 * k * du * (1.0 + 0.1 * k) for k in range(hist + 1)]
+    x = torch.cat(states, dim=1).contiguous()
     y = (u + 0.012 * du + 0.002 * torch.from_numpy(G.random_field(8, (2, 8, 16, 64, 64))).cuda())
     xd = x.cpu().double()
     h, sc = R.history_input(xd)
@@ -135,8 +138,8 @@ def test_history_network_gradient_matches_torch_autograd_reference():
         cos = float(np.dot(gg, gr) / (np.linalg.norm(gg) * np.linalg.norm(gr)))
         assert cos > 0.99, (stiff, cos)
         assert np.linalg.norm(gg - gr) <= 0.1 * np.linalg.norm(gr)
-    # zero output layer: the guess is exactly linear extrapolation
+    # zero output layer: the guess is exactly the extrapolation
     s.init(seed=4, last_layer_scale=0.0)
     guess = s.predict(x)
-    ref = 2 * x[:, :8] - x[:, 8:]
-    assert float((guess - ref).abs().max()) <= 1e-6
+    ref = R.extrapolate(xd).float().cuda()
+    assert float((guess - ref).abs().max()) <= 2e-6
