@@ -279,7 +279,7 @@ pf_status pf_surrogate_workspace(int batch, int d, int h, int w, int training, s
 
 /* out = the warm-start guess for U^{n+1} (see above).  All device pointers;
  * runs on `stream` and synchronises it.  Levels
- * whose (d, h, w) allow it (h multiple of 16) run the tcgen05 convolution;
+ * whose (d, h) allow it (d even, h a multiple of 8) run the tcgen05 convolution;
  * PF_ERR_TIMEOUT if one of its bounded pipeline waits expired. */
 pf_status pf_surrogate_predict(const float* params, float out_scale, const float* x, int n_in,
                                float* out, int batch, int d, int h, int w, void* workspace,
@@ -316,7 +316,7 @@ pf_status pf_surrogate_loss_grad(const float* params, float out_scale, const flo
  * inside).  (c_in, c_out) in {(16,32), (32,32), (32,16)}; d even, h and w
  * multiples of 8.  mode 0: out = conv(x) + bias; mode 1: out = conv^T(dy);
  * mode 2: out = [dW (27 x c_out x c_in), db (c_out)] for dy.  Modes 0 and 1
- * run the tcgen05 kernel when h is a multiple of 16 (else mma.sync); modes 3
+ * run the tcgen05 kernel (d even, h a multiple of 8 -- always here); modes 3
  * and 4 are 0 and 1 on the mma.sync kernel.  Workspace (256-byte aligned) of
  * at least 2V(c_in + c_out) + 4 * 27 c_in c_out + 128 V + 16,809,984 bytes
  * plus 256 per part (V = d h w).  Synchronises the stream; PF_ERR_TIMEOUT if a

@@ -2,27 +2,34 @@
 // cores: tcgen05.mma (BF16 operands from shared memory, FP32 accumulators in
 // tensor memory), input tiles brought in by TMA, warp-specialised pipeline.
 //
-// Implicit GEMM without an im2col buffer.  A block owns a 2x16x8 (z, y, x)
-// output tile, i.e. two M = 128 GEMMs (one per z plane) of N = c_out columns
-// and K = 27 taps x c_in.  The input halo (4x18x10 voxels) is staged by TMA
-// as c_in/8 "chunk planes": plane k holds channels 8k..8k+7 of every halo
-// voxel, 16 bytes per voxel, voxels in (z, y, x) order.  In that layout the
-// 8 x-neighbours of an output row are one contiguous 128-byte core matrix,
-// so the A operand of every tap is just a shared-memory descriptor whose
-// start address is shifted by the tap offset:
-//   core matrices along M (y rows) are HX * 16 bytes apart     (SBO),
-//   core matrices along K (channel chunks) are a plane apart    (LBO).
-// The weights of the layer sit in shared memory once per block in the same
-// canonical no-swizzle K-major layout ([tap][chunk][c_out][8 channels]).
+// Implicit GEMM without an im2col buffer, with the three x-taps folded into
+// N.  A block owns a 2x8x14 (z, y, x) output tile.  Per z plane one GEMM
+//   D[(y, x'), (dx, co)] = sum over (dz, dy, ci) of X[z+dz, y+dy, x'] W[dz, dy, dx, co, ci]
+// runs over the 8 x 16 positions x' of a 16-wide halo row (M = 128) and the
+// c_out outputs of all three x-taps (N = 3 c_out, K = 9 c_in); the epilogue
+// then adds D[x, dx=0] + D[x+1, dx=1] + D[x+2, dx=2] with two lane shuffles.
+// With c_out = 32 every MMA is 128 x 96 x 16 instead of 128 x 32 x 16: a third
+// of the instructions for the same work, and fewer shared-memory operand
+// bytes per flop.
+//
+// The input halo (4 x 10 x 16 voxels) is staged by TMA as c_in/8 "chunk
+// planes": plane k holds channels 8k..8k+7 of every halo voxel, 16 bytes per
+// voxel, voxels in (z, y, x') order.  Eight x'-neighbours are one contiguous
+// 128-byte core matrix and a halo row is two of them, so the A operand of
+// every (dz, dy) is a shared-memory descriptor at a shifted start address:
+// core matrices along M are 128 bytes apart (SBO), along K a plane apart
+// (LBO).  The weights of the layer sit in shared memory once per block in the
+// same canonical no-swizzle K-major layout ([dz dy][chunk][dx co][8 channels]).
 //
 // Roles (192 threads): warp 0 issues the TMA loads (3-stage ring) and owns
 // the tensor-memory allocation; warp 1 issues the MMAs from one thread and
 // commits them to mbarriers; warps 2-5 drain the accumulators
-// (tcgen05.ld 32x32b, lane quarter = warp % 4), add the bias, apply the ReLU
-// and store NDHWC.  Accumulators are double-buffered so the epilogue of tile
-// i overlaps the MMAs of tile i+1.  Every wait is bounded: on expiry the
-// block records an error code, stops issuing work, waits (bounded) for its
-// own copies and MMAs in flight, frees its tensor memory and returns.
+// (tcgen05.ld 32x32b, lane quarter = warp % 4), combine the x-taps, add the
+// bias, apply the ReLU and store NDHWC.  Accumulators are double-buffered so
+// the epilogue of tile i overlaps the MMAs of tile i+1.  Every wait is
+// bounded: on expiry the block records an error code, stops issuing work,
+// waits (bounded) for its own copies and MMAs in flight, frees its tensor
+// memory and returns.
 #include "pf_internal.h"
 
 #include <cuda.h>
@@ -32,9 +39,12 @@
 namespace pf {
 namespace {
 
-constexpr int TZ = 2, TY = 16, TX = 8;                  // output tile
-constexpr int HZ = TZ + 2, HY = TY + 2, HX = TX + 2;    // halo tile
-constexpr uint32_t kPlane = HZ * HY * HX * 16;          // bytes per chunk plane (11520)
+constexpr int TZ = 2, TY = 8, TX = 14;                  // output tile
+constexpr int HZ = TZ + 2, HY = TY + 2, HX = 16;        // halo tile (16-wide rows)
+constexpr uint32_t kPlane = HZ * HY * HX * 16;          // bytes per chunk plane (10240)
+#ifndef PF_CONV_SWIZZLE
+#define PF_CONV_SWIZZLE 1  // 1: one swizzled voxel-major TMA box per stage; 0: chunk planes
+#endif
 constexpr int kStages = 3;
 constexpr int kThreads = 192;
 constexpr long long kWaitCycles = 4000000000ll;          // about 2 s at 2 GHz
@@ -49,10 +59,12 @@ __device__ __forceinline__ uint32_t su32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  // no-swizzle canonical layout; bits 46-47 = 1 (descriptor version)
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo,
+                                          uint64_t layout = 0) {
+  // canonical K-major layout; bits 46-47 = 1 (descriptor version), bits 61-63 the
+  // swizzle (0 none, 6 32-byte, 4 64-byte)
   return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)(lbo >> 4) << 16) |
-         ((uint64_t)(sbo >> 4) << 32) | (1ull << 46);
+         ((uint64_t)(sbo >> 4) << 32) | (1ull << 46) | (layout << 61);
 }
 
 __device__ __forceinline__ void bar_init(uint64_t* b, int count) {
@@ -140,19 +152,37 @@ __device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, float* v) {
 
 template <>
 __device__ __forceinline__ void tmem_ld<32>(uint32_t taddr, float* v) {
-  tmem_ld<16>(taddr, v);
-  tmem_ld<16>(taddr + 16, v + 16);
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
+
 
 template <int CIN, int COUT>
 struct Cfg {
-  static constexpr uint32_t kWBytes = 27u * (CIN / 8) * COUT * 16;
+  static constexpr int kNB = 3 * COUT;  // GEMM N: (dx, c_out)
+  static constexpr uint32_t kWBytes = 9u * (CIN / 8) * kNB * 16;
   static constexpr uint32_t kStage = (CIN / 8) * kPlane;
-  static constexpr uint32_t kCols = 4 * COUT;  // 2 buffers x 2 z planes x COUT
-  static constexpr uint32_t kSmem = 128 + kWBytes + kStages * kStage + sizeof(Ctrl);
-  // kind::f16, FP32 accumulate, BF16 A and B, both K-major, N = COUT, M = 128
+  static constexpr uint32_t kUsed = 2 * TZ * kNB;  // 2 buffers x 2 z planes x N columns
+  static constexpr uint32_t kCols = kUsed <= 32 ? 32 : kUsed <= 64 ? 64 : kUsed <= 128 ? 128
+                                    : kUsed <= 256 ? 256 : 512;
+  // at least 120 KB, so that one block owns an SM and its tensor memory
+  static constexpr uint32_t kSmemUse = 1024 + kWBytes + kStages * kStage + sizeof(Ctrl);
+  static constexpr uint32_t kSmem = kSmemUse > 120u * 1024 ? kSmemUse : 120u * 1024;
+  // kind::f16, FP32 accumulate, BF16 A and B, both K-major, N = 3 COUT, M = 128
   static constexpr uint32_t kIdesc =
-      (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(COUT >> 3) << 17) | ((128u >> 4) << 24);
+      (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kNB >> 3) << 17) | ((128u >> 4) << 24);
+  static_assert(kUsed <= 512 && kNB % 16 == 0 && kNB <= 256, "accumulator shape");
 };
 
 template <int CIN, int COUT>
@@ -164,20 +194,21 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ unsigned char smem_raw[];
   // 128-byte aligned base (TMA destinations and descriptors)
   const uint32_t raw = su32(smem_raw);
-  unsigned char* base = smem_raw + ((128 - (raw & 127)) & 127);
+  unsigned char* base = smem_raw + ((1024 - (raw & 1023)) & 1023);  // swizzle atoms repeat at 1 KB
   unsigned char* sW = base;
   unsigned char* sIn = base + C::kWBytes;
   Ctrl* ctl = reinterpret_cast<Ctrl*>(sIn + kStages * C::kStage);
   volatile int* abort = &ctl->abort;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tiles_x = W / TX, tiles_y = H / TY, tiles_z = D / TZ;
+  const int tiles_x = (W + TX - 1) / TX, tiles_y = H / TY, tiles_z = D / TZ;
   const int ntiles = B * tiles_z * tiles_y * tiles_x;
 
-  // weights [27][COUT][CIN] -> [27][CIN/8][COUT][8]
+  // weights [27][COUT][CIN] -> [9 (dz dy)][CIN/8][3 COUT (dx co)][8]
   for (int i = threadIdx.x; i < 27 * COUT * (CIN / 8); i += kThreads) {
     const int kc = i % (CIN / 8), co = (i / (CIN / 8)) % COUT, tap = i / ((CIN / 8) * COUT);
-    *reinterpret_cast<uint4*>(sW + ((tap * (CIN / 8) + kc) * COUT + co) * 16) =
+    const int dzdy = tap / 3, dx = tap % 3;
+    *reinterpret_cast<uint4*>(sW + ((dzdy * (CIN / 8) + kc) * C::kNB + dx * COUT + co) * 16) =
         *reinterpret_cast<const uint4*>(wt + (int64_t)i * 8);
   }
   if (threadIdx.x == 0) {
@@ -216,10 +247,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int tz = (t / (tiles_x * tiles_y)) % tiles_z, b = t / (tiles_x * tiles_y * tiles_z);
         bar_expect(&ctl->full[s], C::kStage);
         const uint32_t dst = su32(sIn + s * C::kStage);
+#if PF_CONV_SWIZZLE
+        // one box of whole voxels: [z][y][x'][CIN], rows of CIN * 2 bytes, swizzled
+        tma_load5(dst, &xmap, 0, tx * TX - 1, ty * TY - 1, tz * TZ - 1, b, &ctl->full[s]);
+#else
 #pragma unroll
         for (int k = 0; k < CIN / 8; ++k)
           tma_load5(dst + k * kPlane, &xmap, 8 * k, tx * TX - 1, ty * TY - 1, tz * TZ - 1, b,
                     &ctl->full[s]);
+#endif
       }
       // wait (bounded) for the copies still in flight before the block may exit
       const int issued = i;
@@ -239,22 +275,33 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!bar_wait(&ctl->full[s], (i / kStages) & 1, abort, err)) break;
         if (i >= 2 && !bar_wait(&ctl->acce[a], ((i >> 1) - 1) & 1, abort, err)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // descriptors of the stage / weight bases; every (tap, chunk, z) operand
+        // descriptors of the stage / weight bases; every (dz dy, chunk, z) operand
         // is a compile-time byte offset added to the 16-byte address field
-        const uint64_t a_desc = sdesc(su32(sIn + s * C::kStage), kPlane, HX * 16);
-        const uint64_t b_desc = sdesc(su32(sW), COUT * 16, 128);
-        const uint32_t d0 = tmem + a * 2 * COUT;
+#if PF_CONV_SWIZZLE
+        // rows = voxels of CIN * 2 bytes, 8-row swizzle atoms 8 CIN * 2 bytes apart
+        const uint64_t a_desc =
+            sdesc(su32(sIn + s * C::kStage), 16, 8 * CIN * 2, CIN == 32 ? 4ull : 6ull);
+#else
+        const uint64_t a_desc = sdesc(su32(sIn + s * C::kStage), kPlane, 128);
+#endif
+        const uint64_t b_desc = sdesc(su32(sW), C::kNB * 16, 128);
+        const uint32_t d0 = tmem + a * TZ * C::kNB;
 #pragma unroll
-        for (int tap = 0; tap < 27; ++tap) {
-          const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+        for (int dzdy = 0; dzdy < 9; ++dzdy) {
+          const int dz = dzdy / 3, dy = dzdy % 3;
 #pragma unroll
           for (int kc = 0; kc < CIN / 16; ++kc) {
-            const uint64_t bd = b_desc + (uint64_t)(((tap * (CIN / 8) + 2 * kc) * COUT * 16) >> 4);
+            const uint64_t bd =
+                b_desc + (uint64_t)(((dzdy * (CIN / 8) + 2 * kc) * C::kNB * 16) >> 4);
 #pragma unroll
             for (int z = 0; z < TZ; ++z) {
-              const uint32_t off = (((z + dz) * HY + dy) * HX + dx) * 16 + 2 * kc * kPlane;
-              mma_f16(d0 + z * COUT, a_desc + (uint64_t)(off >> 4), bd, C::kIdesc,
-                      (tap | kc) != 0);
+#if PF_CONV_SWIZZLE
+              const uint32_t off = ((z + dz) * HY + dy) * HX * CIN * 2 + kc * 32;
+#else
+              const uint32_t off = ((z + dz) * HY + dy) * HX * 16 + 2 * kc * kPlane;
+#endif
+              mma_f16(d0 + z * C::kNB, a_desc + (uint64_t)(off >> 4), bd, C::kIdesc,
+                      (dzdy | kc) != 0);
             }
           }
         }
@@ -270,8 +317,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else {
     // ---- epilogue: warps 2..5, TMEM lane quarter q = warp % 4 ----
     const int q = warp & 3;
-    const int row = q * 32 + lane;  // M row = y * 8 + x
-    const int yy = row >> 3, xx = row & 7;
+    const int row = q * 32 + lane;  // M row = y * 16 + x'
+    const int yy = row >> 4, xx = row & 15;
     float bv[COUT];
 #pragma unroll
     for (int c = 0; c < COUT; ++c) bv[c] = bias ? bias[c] : 0.0f;
@@ -284,40 +331,49 @@ __global__ void __launch_bounds__(kThreads, 1)
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int tx = t % tiles_x, ty = (t / tiles_x) % tiles_y;
       const int tz = (t / (tiles_x * tiles_y)) % tiles_z, b = t / (tiles_x * tiles_y * tiles_z);
+      const int gx = tx * TX + xx;
+      const bool store = xx < TX && gx < W;
 #pragma unroll
       for (int z = 0; z < TZ; ++z) {
-        float v[COUT];
-        tmem_ld<COUT>(tmem + ((uint32_t)(q * 32) << 16) + a * 2 * COUT + z * COUT, v);
+        __syncwarp();  // converged for the .sync.aligned loads after the divergent stores
+        const uint32_t col = tmem + ((uint32_t)(q * 32) << 16) + a * TZ * C::kNB + z * C::kNB;
+        float v[COUT], w1[COUT], w2[COUT];
+        tmem_ld<COUT>(col, v);               // dx = 0, at x' = x
+        tmem_ld<COUT>(col + COUT, w1);       // dx = 1, taken from x' = x + 1
+        tmem_ld<COUT>(col + 2 * COUT, w2);   // dx = 2, taken from x' = x + 2
 #pragma unroll
         for (int c = 0; c < COUT; ++c) {
-          v[c] += bv[c];
+          v[c] += __shfl_down_sync(0xffffffffu, w1[c], 1) + bv[c];
+          v[c] += __shfl_down_sync(0xffffffffu, w2[c], 2);
           if (relu) v[c] = fmaxf(v[c], 0.0f);
         }
-        const int64_t vox =
-            (((int64_t)b * D + tz * TZ + z) * H + ty * TY + yy) * W + tx * TX + xx;
-        if (y16) {
-          uint4* dst = reinterpret_cast<uint4*>(y16 + vox * COUT);
+        if (store) {
+          const int64_t vox = (((int64_t)b * D + tz * TZ + z) * H + ty * TY + yy) * W + gx;
+          if (y16) {
+            uint4* dst = reinterpret_cast<uint4*>(y16 + vox * COUT);
 #pragma unroll
-          for (int c = 0; c < COUT / 8; ++c) {
-            uint4 o;
-            __nv_bfloat162 h0 = __floats2bfloat162_rn(v[8 * c + 0], v[8 * c + 1]);
-            __nv_bfloat162 h1 = __floats2bfloat162_rn(v[8 * c + 2], v[8 * c + 3]);
-            __nv_bfloat162 h2 = __floats2bfloat162_rn(v[8 * c + 4], v[8 * c + 5]);
-            __nv_bfloat162 h3 = __floats2bfloat162_rn(v[8 * c + 6], v[8 * c + 7]);
-            o.x = *reinterpret_cast<uint32_t*>(&h0);
-            o.y = *reinterpret_cast<uint32_t*>(&h1);
-            o.z = *reinterpret_cast<uint32_t*>(&h2);
-            o.w = *reinterpret_cast<uint32_t*>(&h3);
-            dst[c] = o;
+            for (int c = 0; c < COUT / 8; ++c) {
+              uint4 o;
+              __nv_bfloat162 h0 = __floats2bfloat162_rn(v[8 * c + 0], v[8 * c + 1]);
+              __nv_bfloat162 h1 = __floats2bfloat162_rn(v[8 * c + 2], v[8 * c + 3]);
+              __nv_bfloat162 h2 = __floats2bfloat162_rn(v[8 * c + 4], v[8 * c + 5]);
+              __nv_bfloat162 h3 = __floats2bfloat162_rn(v[8 * c + 6], v[8 * c + 7]);
+              o.x = *reinterpret_cast<uint32_t*>(&h0);
+              o.y = *reinterpret_cast<uint32_t*>(&h1);
+              o.z = *reinterpret_cast<uint32_t*>(&h2);
+              o.w = *reinterpret_cast<uint32_t*>(&h3);
+              dst[c] = o;
+            }
+          }
+          if (y32) {
+            float4* dst = reinterpret_cast<float4*>(y32 + vox * COUT);
+#pragma unroll
+            for (int c = 0; c < COUT / 4; ++c)
+              dst[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
           }
         }
-        if (y32) {
-          float4* dst = reinterpret_cast<float4*>(y32 + vox * COUT);
-#pragma unroll
-          for (int c = 0; c < COUT / 4; ++c)
-            dst[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
-        }
       }
+      __syncwarp();
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       bar_arrive(&ctl->acce[a]);
     }
@@ -369,10 +425,16 @@ cudaError_t tc_launch(const void* x, const void* wt, const float* bias, int relu
                               (cuuint64_t)B};
   const cuuint64_t strides[4] = {(cuuint64_t)CIN * 2, (cuuint64_t)W * CIN * 2,
                                  (cuuint64_t)H * W * CIN * 2, (cuuint64_t)D * H * W * CIN * 2};
+#if PF_CONV_SWIZZLE
+  const cuuint32_t box[5] = {(cuuint32_t)CIN, HX, HY, HZ, 1};
+  const CUtensorMapSwizzle swz = CIN == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B;
+#else
   const cuuint32_t box[5] = {8, HX, HY, HZ, 1};
+  const CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_NONE;
+#endif
   const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(x), dims, strides, box,
-          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
           CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
@@ -383,7 +445,7 @@ cudaError_t tc_launch(const void* x, const void* wt, const float* bias, int relu
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  const int ntiles = B * (D / TZ) * (H / TY) * (W / TX);
+  const int ntiles = B * (D / TZ) * (H / TY) * ((W + TX - 1) / TX);
   const int grid = ntiles < sm_count() ? ntiles : sm_count();
   k_conv3d_tc<CIN, COUT><<<grid, kThreads, C::kSmem, s>>>(
       map, (const __nv_bfloat16*)wt, bias, relu, (__nv_bfloat16*)y16, y32, B, D, H, W, err);
@@ -393,7 +455,7 @@ cudaError_t tc_launch(const void* x, const void* wt, const float* bias, int relu
 }  // namespace
 
 bool conv3d_tc_shape_ok(int B, int D, int H, int W) {
-  return B >= 1 && D >= TZ && H >= TY && W >= TX && D % TZ == 0 && H % TY == 0 && W % TX == 0;
+  return B >= 1 && D >= TZ && H >= TY && W >= 1 && D % TZ == 0 && H % TY == 0;
 }
 
 cudaError_t launch_conv3d_tc(int cin, int cout, const void* x, const void* wt, const float* bias,

@@ -49,6 +49,12 @@ constexpr int kGhost = 2;  // mirror frame around the working planes
 #ifndef PF_MINB
 #define PF_MINB 1  // minimum resident blocks per SM asked of the register allocator
 #endif
+#ifndef PF_ENS_MINB
+#define PF_ENS_MINB 6  // minimum resident ensemble blocks per SM asked of the register allocator
+#endif
+#ifndef PF_ENS_COEF
+#define PF_ENS_COEF 2  // ensemble coefficients: 0 registers, 1 instance table, 2 shared memory
+#endif
 #ifndef PF_PDL
 #define PF_PDL 0  // 1: programmatic dependent launch, dependents released at block end
 #endif
@@ -330,10 +336,21 @@ template <bool kIso, bool kCoherent>
 __device__ __forceinline__ void ensemble_task(const EnsTask& t, const Explicit2DArgs* inst,
                                               int parity) {
   const Explicit2DArgs& a = inst[t.inst];
+#if PF_ENS_COEF == 0
   unsigned long long pair[19];
 #pragma unroll
   for (int i = 0; i < 19; ++i) pair[i] = a.pair[i];
   const Coef K{pair};
+#elif PF_ENS_COEF == 1
+  const Coef K{a.pair};  // read through the instance table (L1-resident, warp-uniform)
+#else
+  __shared__ unsigned long long s_pair[kEnsThreads / 32][20];
+  unsigned long long* sp = s_pair[threadIdx.x >> 5];
+  __syncwarp();
+  if ((threadIdx.x & 31) < 19) sp[threadIdx.x & 31] = a.pair[threadIdx.x & 31];
+  __syncwarp();
+  const Coef K{sp};
+#endif
   const float* in = parity ? a.out : a.in;
   float* out = parity ? const_cast<float*>(a.in) : a.out;
   switch (t.ty) {
@@ -344,7 +361,7 @@ __device__ __forceinline__ void ensemble_task(const EnsTask& t, const Explicit2D
 }
 
 template <bool kIso>
-__global__ void __launch_bounds__(kEnsThreads) k_ensemble_step(const EnsTask* __restrict__ tasks,
+__global__ void __launch_bounds__(kEnsThreads, PF_ENS_MINB) k_ensemble_step(const EnsTask* __restrict__ tasks,
                                                               int ntasks,
                                                               const Explicit2DArgs* inst,
                                                               int parity) {
@@ -387,7 +404,7 @@ __device__ bool grid_barrier(unsigned* bar, long long limit) {
 }
 
 template <bool kIso>
-__global__ void __launch_bounds__(kEnsThreads) k_ensemble_persistent(
+__global__ void __launch_bounds__(kEnsThreads, PF_ENS_MINB) k_ensemble_persistent(
     const EnsTask* __restrict__ tasks, int ntasks, const Explicit2DArgs* inst, int n_steps,
     unsigned* bar, long long limit) {
   const int warps = kEnsThreads / 32;

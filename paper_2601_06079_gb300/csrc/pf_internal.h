@@ -154,7 +154,7 @@ cudaError_t launch_mass_norm(const float* g, int nx, int ny, int nz, int nf, dou
 cudaError_t launch_conv3d(int cin, int cout, const void* x, const void* wt, const float* bias,
                           int relu, void* y16, float* y32, int B, int D, int H, int W, int grid,
                           cudaStream_t s);
-// tcgen05 + TMA implicit GEMM (D even, H multiple of 16, W of 8); *err is set
+// tcgen05 + TMA implicit GEMM (D even, H multiple of 8, any W); *err is set
 // to 1 when a pipeline wait expired (the output is then incomplete).
 bool conv3d_tc_shape_ok(int B, int D, int H, int W);
 cudaError_t launch_conv3d_tc(int cin, int cout, const void* x, const void* wt, const float* bias,
