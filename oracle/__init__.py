@@ -38,6 +38,7 @@ _LIB = None
 
 OR_DOUBLE_WELL = 0
 OR_FAN_CHEN = 1
+OR_COUPLED = 2
 
 
 class Mesh(C.Structure):
@@ -48,7 +49,7 @@ class Params(C.Structure):
     _fields_ = [("energy", C.c_int), ("nf", C.c_int), ("W", C.c_double),
                 ("kappa", C.c_double), ("mob", C.c_double), ("alpha", C.c_double),
                 ("beta", C.c_double), ("gamma", C.c_double),
-                ("mob_field", C.POINTER(C.c_double))]
+                ("mob_field", C.POINTER(C.c_double)), ("mob2", C.c_double)]
 
 
 def lib():
@@ -71,6 +72,7 @@ def lib():
         L.or_ac_explicit.argtypes = [M, Pp, C.c_double, C.c_int64, P]
         L.or_ch_chemical_potential.argtypes = [M, Pp, P, P]
         L.or_ch_explicit.argtypes = [M, Pp, C.c_double, C.c_int64, P]
+        L.or_coupled_explicit.argtypes = [M, Pp, C.c_double, C.c_int64, P]
         L.or_mass_integral.restype = C.c_double
         L.or_mass_integral.argtypes = [M, P]
         L.or_implicit_residual.argtypes = [M, Pp, C.c_double, P, P, P]
@@ -113,19 +115,21 @@ class Problem:
     """A mesh plus the material parameters of one phase-field model.
 
     energy: 'double_well' (f = W c^2 (1-c)^2, Eq. 5-6 with the Supp. 3
-    polynomial) or 'fan_chen' (grain growth); nf fields; kappa; mob = L (AC) or
-    M (CH); mob_field = per-node mobility multiplier (CH only).
+    polynomial), 'fan_chen' (grain growth) or 'coupled' (Eq. 7 with the Supp. 3
+    polynomials; fields [c, eta], no c gradient term; mob = M_c, mob2 = M_eta,
+    kappa = kappa_eta); nf fields; mob = L (AC) or M (CH); mob_field =
+    per-node mobility multiplier (CH only).
     """
 
     def __init__(self, shape, h=1.0, energy="double_well", nf=1, W=1.0, kappa=1.0, mob=1.0,
-                 alpha=1.0, beta=1.0, gamma=1.5, mob_field=None):
+                 alpha=1.0, beta=1.0, gamma=1.5, mob_field=None, mob2=0.0):
         self.shape = tuple(shape)
-        self.nf = nf
+        self.nf = 2 if energy == "coupled" else nf
         self.m = mesh(self.shape, h)
         self._mf = None if mob_field is None else _f64(mob_field).ravel()
-        self.p = Params(OR_DOUBLE_WELL if energy == "double_well" else OR_FAN_CHEN, nf, W, kappa,
-                        mob, alpha, beta, gamma,
-                        None if self._mf is None else _ptr(self._mf))
+        kind = {"double_well": OR_DOUBLE_WELL, "fan_chen": OR_FAN_CHEN, "coupled": OR_COUPLED}
+        self.p = Params(kind[energy], self.nf, W, kappa, mob, alpha, beta, gamma,
+                        None if self._mf is None else _ptr(self._mf), mob2)
         self.nnodes = int(np.prod(self.shape))
 
     def _fshape(self):
@@ -184,6 +188,12 @@ class Problem:
         c = _f64(c).copy()
         lib().or_ch_explicit(C.byref(self.m), C.byref(self.p), dt, nsteps, _ptr(c))
         return c
+
+    def coupled_explicit(self, U, dt, nsteps):
+        """Coupled AC-CH explicit steps (Eq. 7, 9-12): U = [c, eta] planes."""
+        U = _f64(U).copy()
+        lib().or_coupled_explicit(C.byref(self.m), C.byref(self.p), dt, nsteps, _ptr(U))
+        return U
 
     def implicit_residual(self, dt, Un, U):
         Un, U = _f64(Un), _f64(U)

@@ -69,9 +69,41 @@ int64_t or_nnodes(const or_mesh* m) {
   return m->n[0] * m->n[1] * (m->dim == 3 ? m->n[2] : 1);
 }
 
-/* ---- local free-energy density and its derivatives (Eq. 5-6) ---------- */
+/* ---- local free-energy density and its derivatives (Eq. 5-7) ---------- */
+
+/* Coupled Allen-Cahn / Cahn-Hilliard (Eq. 7) with the polynomials printed in
+ * Supp. 3: phase free energies f_alpha(c), f_beta(c) and the interpolation
+ * h(eta) = 10 eta^3 - 15 eta^4 + 6 eta^5.  Coefficients in increasing powers. */
+static const double kFa[5] = {-1.6704, -4.776, 5.1622, -2.7375, 1.3687};
+static const double kFb[3] = {-1.5924, -5.9746, 5.0};
+
+static double poly(const double* a, int n, double x) {
+  double s = 0.0;
+  for (int k = n - 1; k >= 0; --k) s = s * x + a[k];
+  return s;
+}
+static double dpoly(const double* a, int n, double x) {
+  double s = 0.0;
+  for (int k = n - 1; k >= 1; --k) s = s * x + k * a[k];
+  return s;
+}
+static double d2poly(const double* a, int n, double x) {
+  double s = 0.0;
+  for (int k = n - 1; k >= 2; --k) s = s * x + k * (k - 1) * a[k];
+  return s;
+}
+static const double kH[6] = {0.0, 0.0, 0.0, 10.0, -15.0, 6.0};
+
+/* gradient-energy coefficient of field f: the coupled model has no c gradient term */
+static double kappa_of(const or_params* p, int f) {
+  return (p->energy == OR_COUPLED && f == 0) ? 0.0 : p->kappa;
+}
 
 static double f_local(const or_params* p, const double* u) {
+  if (p->energy == OR_COUPLED) {
+    const double h = poly(kH, 6, u[1]);
+    return poly(kFa, 5, u[0]) * (1.0 - h) + poly(kFb, 3, u[0]) * h;
+  }
   if (p->energy == OR_DOUBLE_WELL) {
     double c = u[0];
     return p->W * c * c * (1.0 - c) * (1.0 - c);
@@ -86,6 +118,12 @@ static double f_local(const or_params* p, const double* u) {
 }
 
 static void df_local(const or_params* p, const double* u, double* g) {
+  if (p->energy == OR_COUPLED) {
+    const double h = poly(kH, 6, u[1]);
+    g[0] = dpoly(kFa, 5, u[0]) * (1.0 - h) + dpoly(kFb, 3, u[0]) * h;
+    g[1] = (poly(kFb, 3, u[0]) - poly(kFa, 5, u[0])) * dpoly(kH, 6, u[1]);
+    return;
+  }
   if (p->energy == OR_DOUBLE_WELL) {
     double c = u[0];
     g[0] = 2.0 * p->W * c * (1.0 - c) * (1.0 - 2.0 * c);
@@ -101,6 +139,13 @@ static void df_local(const or_params* p, const double* u, double* g) {
 
 static void d2f_local(const or_params* p, const double* u, double* H) {
   const int nf = p->nf;
+  if (p->energy == OR_COUPLED) {
+    const double h = poly(kH, 6, u[1]), dh = dpoly(kH, 6, u[1]);
+    H[0] = d2poly(kFa, 5, u[0]) * (1.0 - h) + d2poly(kFb, 3, u[0]) * h;
+    H[1] = H[2] = (dpoly(kFb, 3, u[0]) - dpoly(kFa, 5, u[0])) * dh;
+    H[3] = (poly(kFb, 3, u[0]) - poly(kFa, 5, u[0])) * d2poly(kH, 6, u[1]);
+    return;
+  }
   if (p->energy == OR_DOUBLE_WELL) {
     double c = u[0];
     H[0] = 2.0 * p->W * (1.0 - 6.0 * c + 6.0 * c * c);
@@ -192,9 +237,9 @@ static void energy_elem(const or_mesh* m, const or_elem* e, const int64_t* nodes
     for (int f = 0; f < nf; ++f) {
       double g[3];
       interp(e, nodes, c->U + f * c->NN, q, &u[f], g);
-      grad2 += g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+      grad2 += kappa_of(c->p, f) * (g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
     }
-    s += e->wq * (f_local(c->p, u) + 0.5 * c->p->kappa * grad2);
+    s += e->wq * (f_local(c->p, u) + 0.5 * grad2);
   }
   /* the element's first node identifies it uniquely */
   c->per_elem[nodes[0]] = s;
@@ -229,7 +274,7 @@ static void residual_elem(const or_mesh* m, const or_elem* e, const int64_t* nod
       for (int a = 0; a < e->nn; ++a) {
         double gradterm = 0.0;
         for (int k = 0; k < m->dim; ++k) gradterm += g[f][k] * e->G[q][a][k];
-        c->r[f * c->NN + nodes[a]] += e->wq * (df[f] * e->N[q][a] + c->p->kappa * gradterm);
+        c->r[f * c->NN + nodes[a]] += e->wq * (df[f] * e->N[q][a] + kappa_of(c->p, f) * gradterm);
       }
   }
 }
@@ -263,7 +308,7 @@ static void hessian_elem(const or_mesh* m, const or_elem* e, const int64_t* node
       for (int a = 0; a < e->nn; ++a) {
         double gradterm = 0.0;
         for (int k = 0; k < m->dim; ++k) gradterm += gv[f][k] * e->G[q][a][k];
-        c->out[f * c->NN + nodes[a]] += e->wq * (hv * e->N[q][a] + c->p->kappa * gradterm);
+        c->out[f * c->NN + nodes[a]] += e->wq * (hv * e->N[q][a] + kappa_of(c->p, f) * gradterm);
       }
     }
   }
@@ -359,6 +404,32 @@ void or_ch_explicit(const or_mesh* m, const or_params* p, double dt, int64_t nst
   }
   free(kmu);
   free(mu);
+  free(mass);
+}
+
+/* Coupled Allen-Cahn / Cahn-Hilliard, explicit Euler with the lumped mass
+ * (Eq. 1-2 and 9-12 with the energy of Eq. 7):
+ *   m_i mu_i = dE_h/dc_i,  c <- c - dt K_{M_c} mu / m        (conserved c)
+ *   eta <- eta - dt M_eta (dE_h/deta) / m                     (non-conserved eta)
+ * both from the state at the start of the step. */
+void or_coupled_explicit(const or_mesh* m, const or_params* p, double dt, int64_t nsteps,
+                         double* U) {
+  const int64_t NN = or_nnodes(m);
+  double* mass = (double*)malloc(sizeof(double) * NN);
+  double* r = (double*)malloc(sizeof(double) * NN * 2);
+  double* kmu = (double*)malloc(sizeof(double) * NN);
+  or_lumped_mass(m, mass);
+  for (int64_t s = 0; s < nsteps; ++s) {
+    or_residual(m, p, U, r);
+    for (int64_t i = 0; i < NN; ++i) r[i] /= mass[i];       /* mu */
+    or_mobility_stiffness_apply(m, p, r, kmu);                /* K_{M_c} mu (p->mob = M_c) */
+    for (int64_t i = 0; i < NN; ++i) {
+      U[i] -= dt * kmu[i] / mass[i];
+      U[NN + i] -= dt * p->mob2 * r[NN + i] / mass[i];
+    }
+  }
+  free(kmu);
+  free(r);
   free(mass);
 }
 

@@ -26,7 +26,7 @@ typedef struct {
   double h[3];    /* node spacing per axis */
 } or_mesh;
 
-enum { OR_DOUBLE_WELL = 0, OR_FAN_CHEN = 1 };
+enum { OR_DOUBLE_WELL = 0, OR_FAN_CHEN = 1, OR_COUPLED = 2 };
 
 typedef struct {
   int energy;               /* OR_DOUBLE_WELL or OR_FAN_CHEN */
@@ -36,6 +36,7 @@ typedef struct {
   double mob;               /* scalar mobility (L for AC, M for CH) */
   double alpha, beta, gamma;/* Fan-Chen: f = sum(-a/2 e^2 + b/4 e^4) + g sum_{i<j} e_i^2 e_j^2 */
   const double* mob_field;  /* per-node mobility multiplier (CH), NULL = 1 */
+  double mob2;              /* coupled AC-CH: M_eta (mob is M_c) */
 } or_params;
 
 int64_t or_nnodes(const or_mesh* m);
@@ -49,6 +50,9 @@ void or_mobility_stiffness_apply(const or_mesh* m, const or_params* p,
 void or_ac_explicit(const or_mesh* m, const or_params* p, double dt, int64_t nsteps, double* U);
 void or_ch_chemical_potential(const or_mesh* m, const or_params* p, const double* c, double* mu);
 void or_ch_explicit(const or_mesh* m, const or_params* p, double dt, int64_t nsteps, double* c);
+/* Coupled Allen-Cahn / Cahn-Hilliard (Eq. 7, Supp. 3): U = [c; eta] (2 planes). */
+void or_coupled_explicit(const or_mesh* m, const or_params* p, double dt, int64_t nsteps,
+                         double* U);
 double or_mass_integral(const or_mesh* m, const double* c);
 void or_implicit_residual(const or_mesh* m, const or_params* p, double dt, const double* Un,
                           const double* U, double* R);

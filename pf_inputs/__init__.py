@@ -34,6 +34,7 @@ _PURPOSE = {
     "vector": 6,
     "target": 7,
     "surrogate": 8,
+    "coupled": 9,
 }
 
 
@@ -148,3 +149,22 @@ def batched_instances(seed: int, count: int = 256, sizes=(128, 256, 384, 512),
     par = np.exp(lw)
     return [dict(n=int(ns[i]), W=float(par[i, 0]), kappa=float(par[i, 1]), L=float(par[i, 2]))
             for i in range(count)]
+
+
+def coupled_initial(seed: int, shape, n_disks: int = 12, c_mean: float = 0.6,
+                    c_noise: float = 0.02, width: float = 2.0) -> np.ndarray:
+    """Start state [c, eta] (2, ny, nx) FP32 for the coupled Allen-Cahn /
+    Cahn-Hilliard model: eta = smooth disks (tanh profile of the given width in
+    nodes, radii 5..15 % of the shorter side) in an eta = 0 matrix; c =
+    c_mean + U(-c_noise, c_noise)."""
+    ny, nx = shape
+    r = uniform(seed, 3 * n_disks + ny * nx, 0.0, 1.0, "coupled")
+    cx, cy = r[:n_disks] * (nx - 1), r[n_disks:2 * n_disks] * (ny - 1)
+    rad = (0.05 + 0.10 * r[2 * n_disks:3 * n_disks]) * min(nx, ny)
+    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    eta = np.zeros((ny, nx))
+    for k in range(n_disks):
+        d = np.sqrt((x - cx[k]) ** 2 + (y - cy[k]) ** 2)
+        eta = np.maximum(eta, 0.5 * (1.0 - np.tanh((d - rad[k]) / width)))
+    c = c_mean + c_noise * (2.0 * r[3 * n_disks:].reshape(ny, nx) - 1.0)
+    return np.stack([c, eta]).astype(np.float32)
