@@ -17,7 +17,7 @@ The line also carries "forms": each chosen execution form against its plain
 counterpart on the same inputs at the same accuracy -- the fused graph-replayed
 CH step vs one launch per step vs the plain two-pass step (2048^2); the
 256-instance AC ensemble in one persistent launch vs per-step vs per-instance
-launches; the checkpointed adjoint vs the forward trajectory (512^2, 2000
+launches; the coupled Allen-Cahn / Cahn-Hilliard step (2048^2); the checkpointed adjoint vs the forward trajectory (512^2, 2000
 steps); and Newton from the learned warm start vs the plain U^n start for 200
 implicit grain-growth steps on 128^3 x 8 fields (surrogate trained in the run
 on trajectories from other seeds; the zero-correction ablation -- quadratic
@@ -255,6 +255,7 @@ def run_ours(args):
     if not args.no_forms:
         line["forms"] = {"explicit_ch_2048": forms_explicit(dev, stream, flush, c0_host),
                          "ensemble_256_ac": forms_ensemble(dev, stream, flush),
+                         "coupled_acch_2048": forms_coupled(dev, stream, flush),
                          "adjoint_ch_512": forms_adjoint(dev, stream),
                          "implicit_warm_start_128": forms_warm_start(dev)}
     if not args.no_cpu_baseline:
@@ -310,6 +311,30 @@ def forms_explicit(dev, stream, flush, c0_host, n_steps=2048):
     out["steps"] = n_steps
     out["accuracy_gate"] = "each form <= 1e-5 rel L2 vs the FP64 oracle (tests/test_gpu_forms.py)"
     return out
+
+
+def forms_coupled(dev, stream, flush, n=2048, n_steps=1000):
+    """Coupled Allen-Cahn / Cahn-Hilliard (Eq. 7 with the Supp. 3 polynomials):
+    the fused step on a 2048^2 mesh (3 DOF per node: c, mu, eta; 16 algorithmic
+    bytes per node-step: c and eta read and written)."""
+    import torch
+
+    import paper_2601_06079_gb300 as pf
+    import pf_inputs as G
+    s = pf.Solver((n, n), h=1.0, model="coupled", device=dev, stream=stream)
+    s.set_params(kappa=0.3, mobility=1.0, mobility2=150.0, dt=1e-3)
+    U0 = torch.from_numpy(G.coupled_initial(1, (n, n))).to(dev)
+    U = U0.clone()
+    s.step_explicit(U, 16)
+    U.copy_(U0)
+    t = _timed(stream, lambda: s.step_explicit(U, n_steps), flush)
+    nodes = n * n
+    return {"mesh": f"{n}x{n}", "steps": n_steps, "dof_per_node": 3,
+            "M_c": 1.0, "M_eta": 150.0, "kappa_eta": 0.3, "dt": 1e-3,
+            "dof_steps_per_s": 3 * nodes * n_steps / t, "us_per_step": 1e6 * t / n_steps,
+            "hbm_frac_of_measured_at_16B": 16 * nodes * n_steps / t / 1e9 / _peaks()[0],
+            "accuracy_gate": "<= 1e-5 rel L2 per field vs the FP64 oracle "
+                             "(tests/test_gpu_coupled.py)"}
 
 
 def forms_ensemble(dev, stream, flush, n_steps=1000):
@@ -473,7 +498,8 @@ def run_profile(args):
     surrogate two warm-start predictions on 128^3 x 8 fields (tcgen05 convolutions)
     jvp       three Fan-Chen Jacobian-vector products on 128^3 x 8 fields
     ensemble  20 steps of the 256-instance AC ensemble, one launch per step (the
-              persistent mode runs the same task body behind a grid barrier)"""
+              persistent mode runs the same task body behind a grid barrier)
+    coupled   20 coupled Allen-Cahn / Cahn-Hilliard steps on 2048^2"""
     import torch
 
     import paper_2601_06079_gb300 as pf
@@ -508,6 +534,13 @@ def run_profile(args):
             jv = solver.jvp(U, v)
         torch.cuda.synchronize()
         print(f"profile run done: |Jv| {float(jv.norm()):.6f}")
+    elif args.target == "coupled":
+        s = pf.Solver((N_SIDE, N_SIDE), h=1.0, model="coupled")
+        s.set_params(kappa=0.3, mobility=1.0, mobility2=150.0, dt=1e-3)
+        U = torch.from_numpy(G.coupled_initial(1, (N_SIDE, N_SIDE))).cuda()
+        s.step_explicit(U, 20)
+        torch.cuda.synchronize()
+        print(f"profile run done: mean eta {float(U[1].mean()):.6f}")
     else:
         inst = G.batched_instances(1, count=256)
         shapes = [(p["n"], p["n"]) for p in inst]
@@ -533,7 +566,8 @@ def main():
     ap.add_argument("--profile", action="store_true",
                     help="run one workload untimed for ncu (see --target)")
     ap.add_argument("--tsteps", type=int, default=N_TSTEPS)
-    ap.add_argument("--target", default="ch", choices=["ch", "surrogate", "jvp", "ensemble"],
+    ap.add_argument("--target", default="ch",
+                    choices=["ch", "surrogate", "jvp", "ensemble", "coupled"],
                     help="workload of --profile")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -54,7 +54,9 @@ typedef enum {
 typedef enum {
   PF_MODEL_AC = 0,      /* Allen-Cahn, double well f = W u^2 (1-u)^2 (Eq. 1, 5; Supp. 3) */
   PF_MODEL_CH = 1,      /* Cahn-Hilliard split form, same f (Eq. 2, 6, 9, 10) */
-  PF_MODEL_FANCHEN = 2  /* n_fields Allen-Cahn order parameters, Fan-Chen grain-growth energy */
+  PF_MODEL_FANCHEN = 2, /* n_fields Allen-Cahn order parameters, Fan-Chen grain-growth energy */
+  PF_MODEL_COUPLED = 3  /* coupled Allen-Cahn / Cahn-Hilliard (Eq. 7 with the Supp. 3 polynomials
+                           f_alpha, f_beta, h): fields [c; eta], 2-D explicit steps */
 } pf_model;
 
 typedef struct {
@@ -73,6 +75,8 @@ typedef struct {
                                   Must stay valid while the context uses it.  With a field,
                                   pf_step_explicit uses the element form of K_M (tiled
                                   kernel) instead of the fused stencil kernel. */
+  double mobility2;   /* COUPLED: M_eta, the order-parameter mobility (mobility is M_c,
+                         kappa is kappa_eta, shift applies to c; W unused) */
 } pf_params;
 
 /* Newton-Krylov controls for the implicit step (Eq. 13-14).  NULL = defaults. */
@@ -94,8 +98,9 @@ typedef struct {
 } pf_newton_stats;
 
 /* Create a solver context for a uniform Q1 mesh.
- *   dim              2 (AC, CH: explicit steps, energy) or 3 (AC with one field or
- *                    FANCHEN: explicit and implicit steps, JVP, residual)
+ *   dim              2 (AC, CH: explicit steps, energy; COUPLED: explicit steps, with
+ *                    n_fields = 2 planes [c; eta]) or 3 (AC with one field or FANCHEN:
+ *                    explicit and implicit steps, JVP, residual)
  *   nodes[3]         nodes per axis (x, y, z); nodes[2] ignored in 2-D; each >= 2
  *                    (>= 3 along every axis for CH)
  *   h[3]             node spacing per axis (> 0)
@@ -116,7 +121,9 @@ pf_status pf_set_params(pf_ctx* ctx, const pf_params* p);
 
 /* Advance `state` (device, n_fields * N FP32, in/out) by n_steps >= 0 explicit
  * Euler steps with the lumped mass, Eq. 12: AC U <- U - dt L r(U)/m;
- * CH c <- c - dt K_M mu / m with m mu = r(c).  2-D: one fused kernel per step
+ * CH c <- c - dt K_M mu / m with m mu = r(c); COUPLED (Eq. 7) c <- c - dt M_c K mu / m
+ * with m mu = dE/dc (no c gradient term) and eta <- eta - dt M_eta (dE/deta) / m, both
+ * from the start of the step (one fused kernel per step, one launch per step).  2-D: one fused kernel per step
  * (see pf_set_form); 3-D: residual kernel then update.  Enqueues only. */
 pf_status pf_step_explicit(pf_ctx* ctx, float* state, int64_t n_steps);
 

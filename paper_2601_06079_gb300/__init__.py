@@ -15,7 +15,7 @@ import torch
 
 from . import _lib
 from ._lib import (PF_ENS_PER_STEP, PF_ENS_PERSISTENT, PF_ENS_PLAIN,  # noqa: F401
-                   PF_MODEL_AC, PF_MODEL_CH, PF_MODEL_FANCHEN, pf_adjoint,
+                   PF_MODEL_AC, PF_MODEL_CH, PF_MODEL_COUPLED, PF_MODEL_FANCHEN, pf_adjoint,
                    pf_adjoint_workspace, pf_barrier_selftest, pf_bind_workspace,
                    pf_create_ensemble, pf_create_mesh, pf_destroy, pf_set_ensemble_params,
                    pf_step_ensemble, pf_tune_ensemble, pf_surrogate_param_count,
@@ -25,7 +25,8 @@ from ._lib import (PF_ENS_PER_STEP, PF_ENS_PERSISTENT, PF_ENS_PLAIN,  # noqa: F4
                    pf_implicit_residual, pf_jvp, pf_last_error, pf_set_params, pf_step_explicit,
                    pf_step_implicit)
 
-_MODELS = {"ac": PF_MODEL_AC, "ch": PF_MODEL_CH, "fanchen": PF_MODEL_FANCHEN}
+_MODELS = {"ac": PF_MODEL_AC, "ch": PF_MODEL_CH, "fanchen": PF_MODEL_FANCHEN,
+           "coupled": PF_MODEL_COUPLED}
 
 
 class PFError(RuntimeError):
@@ -38,11 +39,14 @@ class Solver:
     """One mesh + model + parameter set on one CUDA device and stream.
 
     shape: node counts (ny, nx) or (nz, ny, nx); h: spacing (scalar or per
-    axis, x first); model: 'ac' | 'ch' | 'fanchen'.  The workspace is a torch
-    uint8 tensor owned by this object and bound to the library context.
+    axis, x first); model: 'ac' | 'ch' | 'fanchen' | 'coupled' (2-D, state
+    [c; eta] with n_fields = 2).  The workspace is a torch uint8 tensor owned
+    by this object and bound to the library context.
     """
 
     def __init__(self, shape, h=1.0, model="ac", n_fields=1, device="cuda", stream=None):
+        if model == "coupled":
+            n_fields = 2
         self.shape = tuple(int(s) for s in shape)
         self.dim = len(self.shape)
         self.device = torch.device(device)
@@ -67,14 +71,16 @@ class Solver:
             raise PFError(st, pf_last_error(self._ctx))
 
     def set_params(self, W=1.0, kappa=1.0, mobility=1.0, dt=0.01, shift=None,
-                   alpha=1.0, beta=1.0, gamma=1.5, mobility_field=None):
+                   alpha=1.0, beta=1.0, gamma=1.5, mobility_field=None, mobility2=0.0):
+        """Material and step parameters.  Coupled model: mobility = M_c,
+        mobility2 = M_eta, kappa = kappa_eta, shift applies to c."""
         if shift is None:
-            shift = 0.5 if self.model in ("ac", "ch") else 0.0
+            shift = {"ac": 0.5, "ch": 0.5, "coupled": 0.6}.get(self.model, 0.0)
         mf = None
         if mobility_field is not None:
             mf = mobility_field.to(self.device, torch.float32).contiguous()
         p = _lib.pf_params(W, kappa, mobility, dt, alpha, beta, gamma, shift,
-                           None if mf is None else mf.data_ptr())
+                           None if mf is None else mf.data_ptr(), mobility2)
         self._check(pf_set_params(self._ctx, p))
         self._params, self._keep = p, mf
 

@@ -23,6 +23,7 @@ PF_ERR_STATE = -6
 PF_MODEL_AC = 0
 PF_MODEL_CH = 1
 PF_MODEL_FANCHEN = 2
+PF_MODEL_COUPLED = 3
 
 PF_ENS_PERSISTENT = 0
 PF_ENS_PER_STEP = 1
@@ -36,7 +37,7 @@ class pf_params(C.Structure):
     _fields_ = [("W", C.c_double), ("kappa", C.c_double), ("mobility", C.c_double),
                 ("dt", C.c_double), ("fc_alpha", C.c_double), ("fc_beta", C.c_double),
                 ("fc_gamma", C.c_double), ("shift", C.c_double),
-                ("mobility_field", C.c_void_p)]
+                ("mobility_field", C.c_void_p), ("mobility2", C.c_double)]
 
 
 class pf_newton_opts(C.Structure):

@@ -27,6 +27,7 @@ struct pf_ctx {
   pf_params par{};
   bool par_set = false;
   int form = PF_FORM_FUSED_GRAPH;  // execution form of the 2-D explicit step
+  pf::Coupled2DArgs cp{};          // coupled AC-CH step constants
 
   // workspace segments
   float* buf_a = nullptr;
@@ -111,8 +112,9 @@ Layout layout(const pf_ctx* c) {
   Layout L{};
   size_t off = 0;
   if (c->dim == 2) {
-    const size_t field = align_up(
-        sizeof(float) * (size_t)pf::work_pitch((int)c->n[0]) * pf::work_rows((int)c->n[1]), 256);
+    const size_t field = align_up(sizeof(float) * (size_t)pf::work_pitch((int)c->n[0]) *
+                                      pf::work_rows((int)c->n[1]) * c->nf,
+                                  256);
     L.a = off;
     off += field;
     L.b = off;
@@ -503,9 +505,13 @@ pf_status pf_create_mesh(pf_ctx** out, int dim, const int64_t nodes[3], const do
                          pf_model model, int n_fields, void* stream, size_t* workspace_bytes) {
   if (!out || !nodes || !h || !workspace_bytes) return PF_ERR_ARG;
   *out = nullptr;
-  if (dim == 2) {  // explicit AC / CH
-    if (model != PF_MODEL_AC && model != PF_MODEL_CH) return PF_ERR_ARG;
-    if (n_fields != 1) return PF_ERR_ARG;
+  if (dim == 2) {  // explicit AC / CH, coupled AC-CH
+    if (model == PF_MODEL_COUPLED) {
+      if (n_fields != 2) return PF_ERR_ARG;
+    } else {
+      if (model != PF_MODEL_AC && model != PF_MODEL_CH) return PF_ERR_ARG;
+      if (n_fields != 1) return PF_ERR_ARG;
+    }
   } else if (dim == 3) {  // AC (double well, one field) or Fan-Chen (1..8 fields)
     if (model == PF_MODEL_AC) {
       if (n_fields != 1) return PF_ERR_ARG;
@@ -517,7 +523,7 @@ pf_status pf_create_mesh(pf_ctx** out, int dim, const int64_t nodes[3], const do
   } else {
     return PF_ERR_ARG;
   }
-  const int64_t minn = (model == PF_MODEL_CH) ? 3 : 2;
+  const int64_t minn = (model == PF_MODEL_CH || model == PF_MODEL_COUPLED) ? 3 : 2;
   int64_t total = 1;
   for (int k = 0; k < dim; ++k) {
     if (nodes[k] < minn || nodes[k] > (int64_t)1 << 20) return PF_ERR_ARG;
@@ -583,6 +589,65 @@ pf_status pf_bind_workspace(pf_ctx* c, void* dev_ptr, size_t bytes) {
   return PF_OK;
 }
 
+// Coupled AC-CH (Eq. 7) with the Supp. 3 polynomials, coefficients of
+// increasing powers: f_alpha(c), f_beta(c), h(eta).  The c polynomials are
+// re-expanded about the shift s, in d = c - s, on the host in FP64.
+void shift_poly(const double* a, int n, double s, double* out) {
+  for (int k = 0; k < n; ++k) out[k] = 0.0;
+  for (int j = 0; j < n; ++j) {  // a_j (s + d)^j = a_j sum_k C(j,k) s^(j-k) d^k
+    double binom = 1.0;
+    for (int k = 0; k <= j; ++k) {
+      out[k] += a[j] * binom * std::pow(s, j - k);
+      binom = binom * (j - k) / (k + 1);
+    }
+  }
+}
+
+void set_params_coupled(pf_ctx* c, const pf_params* p) {
+  static const double fa[5] = {-1.6704, -4.776, 5.1622, -2.7375, 1.3687};
+  static const double fb[3] = {-1.5924, -5.9746, 5.0};
+  static const double h[6] = {0.0, 0.0, 0.0, 10.0, -15.0, 6.0};
+  pf::Coupled2DArgs& a = c->cp;
+  a.nx = (int)c->n[0];
+  a.ny = (int)c->n[1];
+  double sa[5], sb[3];
+  shift_poly(fa, 5, p->shift, sa);
+  shift_poly(fb, 3, p->shift, sb);
+  for (int k = 0; k < 5; ++k) a.fa[k] = (float)sa[k];
+  for (int k = 0; k < 4; ++k) a.dfa[k] = (float)((k + 1) * sa[k + 1]);
+  for (int k = 0; k < 3; ++k) a.fb[k] = (float)sb[k];
+  for (int k = 0; k < 2; ++k) a.dfb[k] = (float)((k + 1) * sb[k + 1]);
+  for (int k = 0; k < 6; ++k) a.h[k] = (float)h[k];
+  for (int k = 0; k < 5; ++k) a.dh[k] = (float)((k + 1) * h[k + 1]);
+  const double hx = c->h[0], hy = c->h[1], m = hx * hy;
+  a.k1 = stiffness2d(hx, hy, p->kappa / m);
+  a.k2 = stiffness2d(hx, hy, -p->dt * p->mobility / m);
+  a.neg_dt_meta = (float)(-p->dt * p->mobility2);
+}
+
+// The coupled step: working planes [c - shift; eta] without a frame in buf_a /
+// buf_b (ping-pong), one fused launch per step.
+pf_status step_coupled2d(pf_ctx* c, float* state, int64_t n_steps) {
+  const int64_t N = nodes2d(c);
+  const float shift = (float)c->par.shift;
+  float* cur = c->buf_a;
+  float* oth = c->buf_b;
+  PF_CUDA(pf::launch_add(state, cur, N, -shift, c->stream));
+  PF_CUDA(cudaMemcpyAsync(cur + N, state + N, sizeof(float) * N, cudaMemcpyDeviceToDevice,
+                          c->stream));
+  pf::Coupled2DArgs a = c->cp;
+  for (int64_t s = 0; s < n_steps; ++s) {
+    a.in = cur;
+    a.out = oth;
+    PF_CUDA(pf::launch_coupled2d(a, c->stream));
+    std::swap(cur, oth);
+  }
+  PF_CUDA(pf::launch_add(cur, state, N, shift, c->stream));
+  PF_CUDA(cudaMemcpyAsync(state + N, cur + N, sizeof(float) * N, cudaMemcpyDeviceToDevice,
+                          c->stream));
+  return PF_OK;
+}
+
 pf_status pf_set_form(pf_ctx* c, int form) {
   if (!c) return PF_ERR_ARG;
   if (form != PF_FORM_FUSED_GRAPH && form != PF_FORM_FUSED_STREAM && form != PF_FORM_TWO_PASS)
@@ -600,11 +665,17 @@ pf_status pf_set_params(pf_ctx* c, const pf_params* p) {
     return fail(c, PF_ERR_ARG, "invalid parameters (need dt > 0, mobility > 0, kappa, W >= 0)");
   if (p->mobility_field && !(c->dim == 2 && c->model == PF_MODEL_CH))
     return fail(c, PF_ERR_ARG, "a per-node mobility field needs a 2-D Cahn-Hilliard mesh");
+  if (c->model == PF_MODEL_COUPLED && (!(p->mobility2 > 0.0) || !isfinite(p->mobility2)))
+    return fail(c, PF_ERR_ARG, "the coupled model needs mobility2 = M_eta > 0");
   c->par = *p;
   c->par_set = true;
   destroy_graph(c);
   if (c->dim == 3) {
     set_params3d(c, p);
+    return PF_OK;
+  }
+  if (c->model == PF_MODEL_COUPLED) {
+    set_params_coupled(c, p);
     return PF_OK;
   }
 
@@ -682,6 +753,7 @@ pf_status pf_step_explicit(pf_ctx* c, float* state, int64_t n_steps) {
   if (n_steps < 0) return fail(c, PF_ERR_ARG, "n_steps < 0");
   if (n_steps == 0) return PF_OK;
   if (c->dim == 3) return step_explicit3d(c, state, n_steps);
+  if (c->model == PF_MODEL_COUPLED) return step_coupled2d(c, state, n_steps);
   if (c->par.mobility_field) return step_explicit_mob(c, state, n_steps);
   if (c->form == PF_FORM_TWO_PASS) return step_plain2d(c, state, n_steps);
   const float shift = (float)c->par.shift;
@@ -713,6 +785,8 @@ pf_status pf_energy(pf_ctx* c, const float* state, double* energy, double* mass)
   if (!c->par_set) return fail(c, PF_ERR_STATE, "parameters not set");
   if (!state) return fail(c, PF_ERR_ARG, "state is NULL");
   if (c->dim != 2) return fail(c, PF_ERR_ARG, "pf_energy supports 2-D meshes");
+  if (c->model == PF_MODEL_COUPLED)
+    return fail(c, PF_ERR_ARG, "pf_energy supports the AC and CH models");
   const double W = c->par.W;
   pf::Energy2DArgs a{};
   a.d = state;  // unshifted: f(u) = W (u^2 - 2 u^3 + u^4)

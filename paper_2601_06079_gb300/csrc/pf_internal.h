@@ -43,6 +43,19 @@ struct Explicit2DArgs {
 void pack_explicit2d(Explicit2DArgs& a);
 
 cudaError_t launch_ac2d(const Explicit2DArgs& a, cudaStream_t s);
+
+// Coupled Allen-Cahn / Cahn-Hilliard step (planes [c - shift; eta], no frame).
+struct Coupled2DArgs {
+  const float* in;
+  float* out;
+  int nx, ny;
+  float fa[5], dfa[4], fb[3], dfb[2];  // f_alpha, f_beta and derivatives in d = c - shift
+  float h[6], dh[5];                   // h(eta), h'(eta)
+  Stencil2D k1;                        // kappa_eta / m K
+  Stencil2D k2;                        // -dt M_c / m K
+  float neg_dt_meta;                   // -dt M_eta
+};
+cudaError_t launch_coupled2d(const Coupled2DArgs& a, cudaStream_t s);
 // The plain two-pass comparison form (d, mu, out: nx x ny arrays without frame).
 cudaError_t launch_plain2d(bool ch, const Explicit2DArgs& a, const float* d, float* mu, float* out,
                            cudaStream_t s);
