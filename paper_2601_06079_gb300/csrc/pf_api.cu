@@ -28,6 +28,7 @@ struct pf_ctx {
   bool par_set = false;
   int form = PF_FORM_FUSED_GRAPH;  // execution form of the 2-D explicit step
   pf::Coupled2DArgs cp{};          // coupled AC-CH step constants
+  pf::Implicit2DArgs im2{};        // 2-D implicit operators (AC)
 
   // workspace segments
   float* buf_a = nullptr;
@@ -108,6 +109,11 @@ struct Layout {
 constexpr int kVec3d = 4;  // U, U^n, G, D before the Krylov basis
 constexpr double kNoOversolve = 0.1;  // GMRES floor, as a fraction of Newton's tolerance
 
+// meshes with the implicit step (and its Krylov vectors): 3-D, and 2-D Allen-Cahn
+bool has_implicit(const pf_ctx* c) {
+  return c->ens_count == 0 && (c->dim == 3 || c->model == PF_MODEL_AC);
+}
+
 Layout layout(const pf_ctx* c) {
   Layout L{};
   size_t off = 0;
@@ -119,7 +125,8 @@ Layout layout(const pf_ctx* c) {
     off += field;
     L.b = off;
     off += field;
-  } else {
+  }
+  if (has_implicit(c)) {
     L.vec = align_up(sizeof(float) * (size_t)nnodes(c) * c->nf, 256);
     L.vecs = off;
     off += L.vec * (kVec3d + pf::kMaxBasis);
@@ -360,6 +367,14 @@ pf_status check_ready(pf_ctx* c) {
 }
 
 cudaError_t residual3d(pf_ctx* c, const float* U, const float* Un, float* out, int unscaled) {
+  if (c->dim == 2) {
+    pf::Implicit2DArgs a = c->im2;
+    a.U = U;
+    a.W = Un;
+    a.out = out;
+    a.unscaled = unscaled;
+    return pf::launch_residual2d(a, c->stream);
+  }
   pf::Implicit3DArgs a = c->im;
   a.U = U;
   a.W = Un;
@@ -369,6 +384,14 @@ cudaError_t residual3d(pf_ctx* c, const float* U, const float* Un, float* out, i
 }
 
 cudaError_t jvp3d(pf_ctx* c, const float* U, const float* v, float* out, int unscaled) {
+  if (c->dim == 2) {
+    pf::Implicit2DArgs a = c->im2;
+    a.U = U;
+    a.W = v;
+    a.out = out;
+    a.unscaled = unscaled;
+    return pf::launch_jvp2d(a, c->stream);
+  }
   pf::Implicit3DArgs a = c->im;
   a.U = U;
   a.W = v;
@@ -576,7 +599,8 @@ pf_status pf_bind_workspace(pf_ctx* c, void* dev_ptr, size_t bytes) {
   if (c->dim == 2) {
     c->buf_a = (float*)(c->ws + L.a);
     c->buf_b = (float*)(c->ws + L.b);
-  } else {
+  }
+  if (has_implicit(c)) {
     char* v = c->ws + L.vecs;
     c->u = (float*)v;
     c->un = (float*)(v + L.vec);
@@ -677,6 +701,17 @@ pf_status pf_set_params(pf_ctx* c, const pf_params* p) {
   if (c->model == PF_MODEL_COUPLED) {
     set_params_coupled(c, p);
     return PF_OK;
+  }
+  if (c->model == PF_MODEL_AC) {
+    pf::Implicit2DArgs& b = c->im2;
+    b.nx = (int)c->n[0];
+    b.ny = (int)c->n[1];
+    b.dw2 = (float)(2.0 * p->W);
+    b.k = stiffness2d(c->h[0], c->h[1], p->kappa / (c->h[0] * c->h[1]));
+    b.inv_dt = (float)(1.0 / p->dt);
+    b.mob = (float)p->mobility;
+    b.cell = (float)(c->h[0] * c->h[1]);
+    b.unscaled = 0;
   }
 
   const double s = p->shift, W = p->W;
@@ -817,7 +852,8 @@ pf_status pf_step_implicit(pf_ctx* c, float* state, int64_t n_steps, const float
   if (!c) return PF_ERR_ARG;
   pf_status st = check_ready(c);
   if (st != PF_OK) return st;
-  if (c->dim != 3) return fail(c, PF_ERR_ARG, "pf_step_implicit supports 3-D meshes");
+  if (!has_implicit(c))
+    return fail(c, PF_ERR_ARG, "pf_step_implicit supports 3-D meshes and 2-D Allen-Cahn");
   if (!state) return fail(c, PF_ERR_ARG, "state is NULL");
   if (n_steps < 0) return fail(c, PF_ERR_ARG, "n_steps < 0");
   pf_newton_opts o{20, 30, 300, 1e-5, 1e-3};
@@ -1206,7 +1242,7 @@ pf_status pf_jvp(pf_ctx* c, const float* U, const float* v, float* Jv) {
   if (!c) return PF_ERR_ARG;
   pf_status st = check_ready(c);
   if (st != PF_OK) return st;
-  if (c->dim != 3) return fail(c, PF_ERR_ARG, "pf_jvp supports 3-D meshes");
+  if (!has_implicit(c)) return fail(c, PF_ERR_ARG, "pf_jvp supports 3-D meshes and 2-D Allen-Cahn");
   if (!U || !v || !Jv) return fail(c, PF_ERR_ARG, "null array");
   PF_CUDA(jvp3d(c, U, v, Jv, 1));
   return PF_OK;
@@ -1216,7 +1252,8 @@ pf_status pf_implicit_residual(pf_ctx* c, const float* Un, const float* U, float
   if (!c) return PF_ERR_ARG;
   pf_status st = check_ready(c);
   if (st != PF_OK) return st;
-  if (c->dim != 3) return fail(c, PF_ERR_ARG, "pf_implicit_residual supports 3-D meshes");
+  if (!has_implicit(c))
+    return fail(c, PF_ERR_ARG, "pf_implicit_residual supports 3-D meshes and 2-D Allen-Cahn");
   if (!U || !Un || !R) return fail(c, PF_ERR_ARG, "null array");
   PF_CUDA(residual3d(c, U, Un, R, 1));
   return PF_OK;

@@ -143,6 +143,21 @@ struct Implicit3DArgs {
   int unscaled;     // multiply the result by the lumped mass m_i
 };
 cudaError_t launch_residual3d(const Implicit3DArgs& a, cudaStream_t s);
+
+// The same operators on a 2-D mesh for the Allen-Cahn double well (one field).
+struct Implicit2DArgs {
+  const float* U;  // state at which r / H is evaluated
+  const float* W;  // JVP: direction v; residual: U^n
+  float* out;
+  int nx, ny;
+  float dw2;       // 2 W
+  Stencil2D k;     // kappa / m K
+  float inv_dt, mob;
+  float cell;      // hx hy
+  int unscaled;    // multiply the result by the lumped mass m_i
+};
+cudaError_t launch_residual2d(const Implicit2DArgs& a, cudaStream_t s);
+cudaError_t launch_jvp2d(const Implicit2DArgs& a, cudaStream_t s);
 cudaError_t launch_jvp3d(const Implicit3DArgs& a, cudaStream_t s);
 
 // Krylov vector kernels (FP32 vectors, FP64 inner products).

@@ -128,3 +128,55 @@ def test_grain_growth_128_cubed_root_reevaluated_by_oracle():
     R = P.implicit_residual(0.5, U0, t.cpu().numpy())
     ref = np.linalg.norm(P.lumped_mass()[None] * U0.astype(np.float64) / 0.5)
     assert np.linalg.norm(R) <= 2e-5 * ref
+
+
+# ---------------------------------------------------------------- 2-D Allen-Cahn
+
+
+def _ac2d(shape, h, W=1.3, kappa=0.7, L=1.1, dt=0.5):
+    import paper_2601_06079_gb300 as pf
+    s = pf.Solver(shape, h=h, model="ac")
+    s.set_params(W=W, kappa=kappa, mobility=L, dt=dt)
+    P = O.Problem(shape, h=h, energy="double_well", W=W, kappa=kappa, mob=L)
+    return s, P
+
+
+@pytest.mark.parametrize("shape,h", [((37, 45), 1.0), ((64, 130), (0.9, 1.2)), ((3, 5), 1.0)])
+def test_2d_jvp_and_residual_match_oracle(shape, h):
+    s, P = _ac2d(shape, h)
+    U = G.ac_initial(3, shape, 0.2, 0.8)
+    Un = G.ac_initial(4, shape, 0.2, 0.8)
+    v = G.random_field(5, shape)
+    cu = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+    assert rel(s.jvp(cu(U), cu(v)).cpu().numpy(), P.implicit_jvp(0.5, U, v)) <= 2e-6
+    assert rel(s.implicit_residual(cu(Un), cu(U)).cpu().numpy(),
+               P.implicit_residual(0.5, Un, U)) <= 2e-6
+
+
+def test_2d_newton_steps_match_oracle():
+    # the paper's implicit benchmarks take large steps; 4 backward-Euler steps of
+    # dt = 0.5 from a noisy start on a ragged mesh
+    shape = (67, 90)
+    s, P = _ac2d(shape, 1.0)
+    U0 = G.ac_initial(6, shape, 0.3, 0.7)
+    t = torch.from_numpy(U0).cuda()
+    st = s.step_implicit(t, 4, newton_rtol=1e-6, gmres_rtol=1e-4)
+    assert st["converged"]
+    ref = U0.astype(np.float64)
+    for _ in range(4):
+        ref, info = P.newton(0.5, ref, abs_tol=1e-12, gmres_rtol=1e-10)
+        assert info["ok"]
+    assert rel(t.cpu().numpy(), ref) <= 2e-5
+
+
+def test_2d_implicit_root_reevaluated_by_oracle_at_1024():
+    shape = (1024, 1024)
+    s, P = _ac2d(shape, 1.0, W=1.0, kappa=1.0, L=1.0, dt=1.0)
+    U0 = G.ac_initial(7, shape)
+    t = torch.from_numpy(U0).cuda()
+    st = s.step_implicit(t, 1)
+    assert st["converged"] and st["newton_iters"] >= 1
+    R = P.implicit_residual(1.0, U0.astype(np.float64), t.cpu().numpy().astype(np.float64))
+    m = P.lumped_mass()
+    ref = np.linalg.norm(m * U0.astype(np.float64) / 1.0)
+    assert np.linalg.norm(R) <= 2e-5 * ref
