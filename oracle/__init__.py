@@ -20,6 +20,9 @@ Parity pins (tests/test_oracle_*.py check them without a GPU):
   ch_explicit          cosine-mode growth factor; exact mass conservation;
                          monotone energy decrease
   hessian / jvp        central FD of the residual; symmetry u.Jv = v.Ju
+  chsplit (implicit CH) JVP = central FD of the residual; exact conservation of
+                       c; first-order agreement with the explicit step as dt -> 0;
+                       energy decrease
   newton / gmres       FP64 re-evaluation of the root's residual; GMRES on a
                          problem with known solution
   ch_adjoint           central FD of the loss (scalars, a smooth direction of
@@ -73,6 +76,12 @@ def lib():
         L.or_ch_chemical_potential.argtypes = [M, Pp, P, P]
         L.or_ch_explicit.argtypes = [M, Pp, C.c_double, C.c_int64, P]
         L.or_coupled_explicit.argtypes = [M, Pp, C.c_double, C.c_int64, P]
+        L.or_chsplit_residual.argtypes = [M, Pp, C.c_double, P, P, P]
+        L.or_chsplit_jvp.argtypes = [M, Pp, C.c_double, P, P, P]
+        L.or_chsplit_newton.restype = C.c_int
+        L.or_chsplit_newton.argtypes = [M, Pp, C.c_double, P, P, C.c_double, C.c_int, C.c_int,
+                                        C.c_double, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                        C.POINTER(C.c_double)]
         L.or_mass_integral.restype = C.c_double
         L.or_mass_integral.argtypes = [M, P]
         L.or_implicit_residual.argtypes = [M, Pp, C.c_double, P, P, P]
@@ -223,6 +232,33 @@ class Problem:
         ok = lib().or_newton(C.byref(self.m), C.byref(self.p), dt, _ptr(Un), _ptr(U), abs_tol,
                              max_newton, restart, gmres_rtol, C.byref(ni), C.byref(gi),
                              C.byref(fn))
+        return U, dict(ok=bool(ok), newton_iters=ni.value, gmres_iters=gi.value,
+                       final_norm=fn.value)
+
+    # -- implicit split Cahn-Hilliard (Eq. 9-10, 13): U = [c, mu] --
+    def chsplit_residual(self, dt, cn, U):
+        cn, U = _f64(cn), _f64(U)
+        out = np.zeros((2,) + self.shape)
+        lib().or_chsplit_residual(C.byref(self.m), C.byref(self.p), dt, _ptr(cn), _ptr(U),
+                                  _ptr(out))
+        return out
+
+    def chsplit_jvp(self, dt, U, v):
+        U, v = _f64(U), _f64(v)
+        out = np.zeros((2,) + self.shape)
+        lib().or_chsplit_jvp(C.byref(self.m), C.byref(self.p), dt, _ptr(U), _ptr(v), _ptr(out))
+        return out
+
+    def chsplit_newton(self, dt, cn, U0=None, abs_tol=1e-10, max_newton=30, restart=30,
+                       gmres_rtol=1e-10):
+        """One backward-Euler step of the split CH system from composition cn;
+        U0 = [c, mu] initial guess (default [cn, M^-1 r(cn)])."""
+        cn = _f64(cn)
+        U = (np.stack([cn, self.chemical_potential(cn)]) if U0 is None else _f64(U0)).copy()
+        ni, gi, fn = C.c_int(0), C.c_int(0), C.c_double(0)
+        ok = lib().or_chsplit_newton(C.byref(self.m), C.byref(self.p), dt, _ptr(cn), _ptr(U),
+                                     abs_tol, max_newton, restart, gmres_rtol, C.byref(ni),
+                                     C.byref(gi), C.byref(fn))
         return U, dict(ok=bool(ok), newton_iters=ni.value, gmres_iters=gi.value,
                        final_norm=fn.value)
 

@@ -481,11 +481,12 @@ static double dot(const double* a, const double* b, int64_t n) {
 }
 
 /* Textbook restarted GMRES(restart) (Saad & Schultz 1986) for J x = b with
- * modified Gram-Schmidt and Givens rotations; x holds the initial guess.
- * Returns 1 when ||b - J x|| <= rtol ||b||. */
-int or_gmres(const or_mesh* m, const or_params* p, double dt, const double* U, const double* b,
-             double* x, int restart, int maxit, double rtol, int* iters_out) {
-  const int64_t n = or_nnodes(m) * p->nf;
+ * modified Gram-Schmidt and Givens rotations; J is applied by `apply`, x holds
+ * the initial guess.  Returns 1 when ||b - J x|| <= rtol ||b||. */
+typedef void (*or_apply_fn)(const void* ctx, const double* x, double* y);
+
+static int gmres_op(or_apply_fn apply, const void* ctx, int64_t n, const double* b, double* x,
+                    int restart, int maxit, double rtol, int* iters_out) {
   const int R = restart;
   double* V = (double*)malloc(sizeof(double) * n * (R + 1));
   double* H = (double*)calloc((size_t)(R + 1) * R, sizeof(double));
@@ -501,7 +502,7 @@ int or_gmres(const or_mesh* m, const or_params* p, double dt, const double* U, c
     converged = 1;
   }
   while (!converged && total < maxit) {
-    or_implicit_jvp(m, p, dt, U, x, w);
+    apply(ctx, x, w);
     for (int64_t i = 0; i < n; ++i) V[i] = b[i] - w[i];
     double beta = sqrt(dot(V, V, n));
     if (beta <= rtol * bnorm) { converged = 1; break; }
@@ -511,7 +512,7 @@ int or_gmres(const or_mesh* m, const or_params* p, double dt, const double* U, c
     int k = 0;
     for (; k < R && total < maxit; ++k, ++total) {
       double* vk1 = V + (int64_t)(k + 1) * n;
-      or_implicit_jvp(m, p, dt, U, V + (int64_t)k * n, vk1);
+      apply(ctx, V + (int64_t)k * n, vk1);
       for (int j = 0; j <= k; ++j) {
         const double hjk = dot(vk1, V + (int64_t)j * n, n);
         H[j * R + k] = hjk;
@@ -548,25 +549,49 @@ int or_gmres(const or_mesh* m, const or_params* p, double dt, const double* U, c
   return converged;
 }
 
-/* Newton-Raphson on Eq. 14 (U holds the initial guess on entry, the root on
- * exit); each correction solves J d = -R with GMRES.  Returns 1 when
- * ||R||_2 <= abs_tol. */
-int or_newton(const or_mesh* m, const or_params* p, double dt, const double* Un, double* U,
-              double abs_tol, int max_newton, int restart, double gmres_rtol,
-              int* newton_iters, int* gmres_iters, double* final_norm) {
-  const int64_t n = or_nnodes(m) * p->nf;
+typedef struct { const or_mesh* m; const or_params* p; double dt; const double* U; } jvp_ctx;
+
+static void apply_implicit_jvp(const void* vctx, const double* x, double* y) {
+  const jvp_ctx* c = (const jvp_ctx*)vctx;
+  or_implicit_jvp(c->m, c->p, c->dt, c->U, x, y);
+}
+
+int or_gmres(const or_mesh* m, const or_params* p, double dt, const double* U, const double* b,
+             double* x, int restart, int maxit, double rtol, int* iters_out) {
+  const jvp_ctx ctx = {m, p, dt, U};
+  return gmres_op(apply_implicit_jvp, &ctx, or_nnodes(m) * p->nf, b, x, restart, maxit, rtol,
+                  iters_out);
+}
+
+/* Newton-Raphson on a residual R(U) with Jacobian action J (U holds the initial
+ * guess on entry, the root on exit); each correction solves J d = -R with
+ * GMRES.  Returns 1 when ||R||_2 <= abs_tol. */
+typedef void (*or_residual_fn)(const void* ctx, const double* U, double* R);
+typedef void (*or_jacobian_fn)(const void* ctx, const double* U, const double* v, double* Jv);
+
+typedef struct { or_jacobian_fn jac; const void* ctx; const double* U; } lin_ctx;
+
+static void apply_linearised(const void* vctx, const double* x, double* y) {
+  const lin_ctx* c = (const lin_ctx*)vctx;
+  c->jac(c->ctx, c->U, x, y);
+}
+
+static int newton_op(or_residual_fn res, or_jacobian_fn jac, const void* ctx, int64_t n,
+                     double* U, double abs_tol, int max_newton, int restart, double gmres_rtol,
+                     int* newton_iters, int* gmres_iters, double* final_norm) {
   double* R = (double*)malloc(sizeof(double) * n);
   double* d = (double*)malloc(sizeof(double) * n);
   int it = 0, gtot = 0, ok = 0;
   double rn = 0.0;
   for (;;) {
-    or_implicit_residual(m, p, dt, Un, U, R);
+    res(ctx, U, R);
     rn = sqrt(dot(R, R, n));
     if (rn <= abs_tol) { ok = 1; break; }
     if (it >= max_newton) break;
     for (int64_t i = 0; i < n; ++i) { R[i] = -R[i]; d[i] = 0.0; }
     int gi = 0;
-    or_gmres(m, p, dt, U, R, d, restart, 50 * restart, gmres_rtol, &gi);
+    const lin_ctx lc = {jac, ctx, U};
+    gmres_op(apply_linearised, &lc, n, R, d, restart, 50 * restart, gmres_rtol, &gi);
     gtot += gi;
     for (int64_t i = 0; i < n; ++i) U[i] += d[i];
     ++it;
@@ -577,6 +602,80 @@ int or_newton(const or_mesh* m, const or_params* p, double dt, const double* Un,
   free(R);
   free(d);
   return ok;
+}
+
+typedef struct { const or_mesh* m; const or_params* p; double dt; const double* Un; } step_ctx;
+
+static void res_implicit(const void* vctx, const double* U, double* R) {
+  const step_ctx* c = (const step_ctx*)vctx;
+  or_implicit_residual(c->m, c->p, c->dt, c->Un, U, R);
+}
+
+static void jac_implicit(const void* vctx, const double* U, const double* v, double* Jv) {
+  const step_ctx* c = (const step_ctx*)vctx;
+  or_implicit_jvp(c->m, c->p, c->dt, U, v, Jv);
+}
+
+/* Newton-Raphson on Eq. 14 (gradient-flow form). */
+int or_newton(const or_mesh* m, const or_params* p, double dt, const double* Un, double* U,
+              double abs_tol, int max_newton, int restart, double gmres_rtol,
+              int* newton_iters, int* gmres_iters, double* final_norm) {
+  const step_ctx ctx = {m, p, dt, Un};
+  return newton_op(res_implicit, jac_implicit, &ctx, or_nnodes(m) * p->nf, U, abs_tol,
+                   max_newton, restart, gmres_rtol, newton_iters, gmres_iters, final_norm);
+}
+
+/* ---- implicit split Cahn-Hilliard (Eq. 9-10 with backward Euler, Eq. 13) --
+ * Unknowns U = [c; mu] (2 N values), the previous composition cn:
+ *   R_c  = M (c - cn) / dt + K_M mu
+ *   R_mu = M mu - r(c)            (r = dE_h/dc: f'(c) by Gauss quadrature + kappa K c)
+ * Jacobian action on v = [v_c; v_mu]:
+ *   J_c  = M v_c / dt + K_M v_mu
+ *   J_mu = M v_mu - H(c) v_c      (H the Hessian of E_h)  */
+void or_chsplit_residual(const or_mesh* m, const or_params* p, double dt, const double* cn,
+                         const double* U, double* R) {
+  const int64_t NN = or_nnodes(m);
+  double* mass = (double*)malloc(sizeof(double) * NN);
+  or_lumped_mass(m, mass);
+  or_mobility_stiffness_apply(m, p, U + NN, R);  /* K_M mu */
+  or_residual(m, p, U, R + NN);                   /* r(c) */
+  for (int64_t i = 0; i < NN; ++i) {
+    R[i] += mass[i] * (U[i] - cn[i]) / dt;
+    R[NN + i] = mass[i] * U[NN + i] - R[NN + i];
+  }
+  free(mass);
+}
+
+void or_chsplit_jvp(const or_mesh* m, const or_params* p, double dt, const double* U,
+                    const double* v, double* Jv) {
+  const int64_t NN = or_nnodes(m);
+  double* mass = (double*)malloc(sizeof(double) * NN);
+  or_lumped_mass(m, mass);
+  or_mobility_stiffness_apply(m, p, v + NN, Jv);  /* K_M v_mu */
+  or_hessian_apply(m, p, U, v, Jv + NN);           /* H(c) v_c */
+  for (int64_t i = 0; i < NN; ++i) {
+    Jv[i] += mass[i] * v[i] / dt;
+    Jv[NN + i] = mass[i] * v[NN + i] - Jv[NN + i];
+  }
+  free(mass);
+}
+
+static void res_chsplit(const void* vctx, const double* U, double* R) {
+  const step_ctx* c = (const step_ctx*)vctx;
+  or_chsplit_residual(c->m, c->p, c->dt, c->Un, U, R);
+}
+
+static void jac_chsplit(const void* vctx, const double* U, const double* v, double* Jv) {
+  const step_ctx* c = (const step_ctx*)vctx;
+  or_chsplit_jvp(c->m, c->p, c->dt, U, v, Jv);
+}
+
+int or_chsplit_newton(const or_mesh* m, const or_params* p, double dt, const double* cn,
+                      double* U, double abs_tol, int max_newton, int restart, double gmres_rtol,
+                      int* newton_iters, int* gmres_iters, double* final_norm) {
+  const step_ctx ctx = {m, p, dt, cn};
+  return newton_op(res_chsplit, jac_chsplit, &ctx, 2 * or_nnodes(m), U, abs_tol, max_newton,
+                   restart, gmres_rtol, newton_iters, gmres_iters, final_norm);
 }
 
 /* ---- discrete adjoint of the explicit Cahn-Hilliard map (Supp. 2) -------

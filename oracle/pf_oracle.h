@@ -50,6 +50,14 @@ void or_mobility_stiffness_apply(const or_mesh* m, const or_params* p,
 void or_ac_explicit(const or_mesh* m, const or_params* p, double dt, int64_t nsteps, double* U);
 void or_ch_chemical_potential(const or_mesh* m, const or_params* p, const double* c, double* mu);
 void or_ch_explicit(const or_mesh* m, const or_params* p, double dt, int64_t nsteps, double* c);
+/* Implicit split Cahn-Hilliard: U = [c; mu] (2 planes), cn the previous c. */
+void or_chsplit_residual(const or_mesh* m, const or_params* p, double dt, const double* cn,
+                         const double* U, double* R);
+void or_chsplit_jvp(const or_mesh* m, const or_params* p, double dt, const double* U,
+                    const double* v, double* Jv);
+int or_chsplit_newton(const or_mesh* m, const or_params* p, double dt, const double* cn,
+                      double* U, double abs_tol, int max_newton, int restart, double gmres_rtol,
+                      int* newton_iters, int* gmres_iters, double* final_norm);
 /* Coupled Allen-Cahn / Cahn-Hilliard (Eq. 7, Supp. 3): U = [c; eta] (2 planes). */
 void or_coupled_explicit(const or_mesh* m, const or_params* p, double dt, int64_t nsteps,
                          double* U);
