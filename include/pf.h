@@ -98,8 +98,8 @@ typedef struct {
 } pf_newton_stats;
 
 /* Create a solver context for a uniform Q1 mesh.
- *   dim              2 (AC: explicit and implicit steps, JVP, residual, energy; CH:
- *                    explicit steps, energy; COUPLED: explicit steps, with n_fields = 2
+ *   dim              2 (AC, CH: explicit and implicit steps, JVP, residual, energy
+ *                    (CH implicit: the split system); COUPLED: explicit steps, n_fields = 2
  *                    planes [c; eta]) or 3 (AC with one field or FANCHEN: explicit and
  *                    implicit steps, JVP, residual)
  *   nodes[3]         nodes per axis (x, y, z); nodes[2] ignored in 2-D; each >= 2
@@ -142,8 +142,11 @@ pf_status pf_step_explicit(pf_ctx* ctx, float* state, int64_t n_steps);
 enum { PF_FORM_FUSED_GRAPH = 0, PF_FORM_FUSED_STREAM = 1, PF_FORM_TWO_PASS = 2 };
 pf_status pf_set_form(pf_ctx* ctx, int form);
 
-/* Advance `state` (device, 3-D or 2-D Allen-Cahn, in/out) by n_steps backward-Euler
- * steps, Eq. 13:
+/* Advance `state` (device, 3-D, 2-D Allen-Cahn or 2-D Cahn-Hilliard, in/out) by n_steps
+ * backward-Euler steps, Eq. 13.  2-D Cahn-Hilliard solves the split system of
+ * Eq. 9-10 for [c; mu]: R = [M (c - c^n)/dt + K_M mu;  M mu - r(c)] (state and
+ * guess hold c alone; mu starts at M^-1 r of the starting c; the Newton target
+ * is rtol ||M c^n / dt||; no per-node mobility field).  Otherwise:
  * each step solves R(U) = M (U - U^n)/dt + L r(U) = 0 (Eq. 14) by Newton, each
  * correction by restarted GMRES(m) on the Jacobian-vector product (matrix-free;
  * Krylov vectors FP32, inner products FP64, CGS2 orthogonalisation).
@@ -155,14 +158,16 @@ pf_status pf_step_implicit(pf_ctx* ctx, float* state, int64_t n_steps, const flo
                            const pf_newton_opts* opts, pf_newton_stats* stats);
 
 /* Jacobian-vector product of Eq. 14 (3-D, or 2-D Allen-Cahn):
- * Jv = M v / dt + L (F''(U) v + kappa K v),
+ * Jv = M v / dt + L (F''(U) v + kappa K v); 2-D Cahn-Hilliard: the split system's
+ * J [v_c; v_mu] = [M v_c / dt + K_M v_mu;  M v_mu - H(c) v_c] on 2N-value vectors.
  * with F''(U) v = sum_e sum_q w|J| H_f(U_q) v_q N_i (the Hessian of the local
  * energy) and K the Q1 stiffness.  U, v, Jv: device, n_fields * N FP32.
  * Enqueues only. */
 pf_status pf_jvp(pf_ctx* ctx, const float* U, const float* v, float* Jv);
 
-/* Implicit residual of Eq. 14 (3-D, or 2-D Allen-Cahn): R = M (U - Un) / dt + L r(U).
- * Device arrays, n_fields * N FP32.  Enqueues only. */
+/* Implicit residual of Eq. 14 (3-D, or 2-D Allen-Cahn): R = M (U - Un) / dt + L r(U);
+ * 2-D Cahn-Hilliard: the split system's residual at U = [c; mu] (2N values) with the
+ * first plane of Un = c^n.  Device arrays, n_fields * N FP32.  Enqueues only. */
 pf_status pf_implicit_residual(pf_ctx* ctx, const float* Un, const float* U, float* R);
 
 /* Bytes of caller-owned device workspace pf_adjoint needs for n_steps steps

@@ -119,17 +119,29 @@ class Solver:
         out["status"] = st
         return out
 
+    def _vec(self, t):
+        """A Newton-system vector: the state, or [c; mu] (two planes) for 2-D CH."""
+        if self.model == "ch" and self.dim == 2:
+            n = int(torch.tensor(self.shape).prod())
+            if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+                    and t.numel() == 2 * n):
+                raise ValueError(f"2-D CH Newton vectors are [c; mu]: {2 * n} float32 values")
+            return t.data_ptr()
+        return self._state(t)
+
     def jvp(self, U, v, out=None):
-        """J v of Eq. 14 (unscaled: includes the lumped mass)."""
+        """J v of Eq. 14 (unscaled: includes the lumped mass); 2-D CH: the split
+        system's Jacobian action on [v_c; v_mu] at [c; mu]."""
         out = torch.empty_like(v) if out is None else out
-        self._check(pf_jvp(self._ctx, self._state(U), self._state(v), self._state(out)))
+        self._check(pf_jvp(self._ctx, self._vec(U), self._vec(v), self._vec(out)))
         return out
 
     def implicit_residual(self, Un, U, out=None):
-        """R = M (U - Un)/dt + L r(U) of Eq. 14."""
+        """R = M (U - Un)/dt + L r(U) of Eq. 14; 2-D CH: the split system's
+        residual at U = [c; mu] with Un = [c^n; (ignored)]."""
         out = torch.empty_like(U) if out is None else out
-        self._check(pf_implicit_residual(self._ctx, self._state(Un), self._state(U),
-                                         self._state(out)))
+        self._check(pf_implicit_residual(self._ctx, self._vec(Un), self._vec(U),
+                                         self._vec(out)))
         return out
 
     def adjoint(self, c0, target, n_steps, ckpt_every=100, nodal_loss=False, want_field=True,

@@ -1,11 +1,14 @@
-// 2-D implicit-step operators for the Allen-Cahn double well (JAX-PF
-// Eq. 13-14 on a 2-D Q1 mesh):
-//   R(U) = M (U - U^n)/dt + L r(U),     J v = M v / dt + L H(U) v,
-// r the gradient and H the Hessian of E_h = sum_e sum_q w|J| [f(U_q) +
-// kappa/2 |grad U_q|^2], f = W u^2 (1-u)^2.  As in 3-D both are evaluated
-// scaled by the lumped mass (G = M^-1 R, M^-1 J v) on a tile with mirror
-// images beyond the mesh, where every node uses the interior formula; an
-// optional final multiplication by m_i gives R and J v themselves.
+// 2-D implicit-step operators (JAX-PF Eq. 13-14 on a 2-D Q1 mesh) with the
+// double well f = W u^2 (1-u)^2, r the gradient and H the Hessian of
+// E_h = sum_e sum_q w|J| [f(U_q) + kappa/2 |grad U_q|^2]:
+//   Allen-Cahn:  R(U) = M (U - U^n)/dt + L r(U),     J v = M v / dt + L H(U) v
+//   split Cahn-Hilliard (Eq. 9-10), unknowns [c; mu]:
+//                R = [M (c - c^n)/dt + K_M mu;  M mu - r(c)]
+//                J [v_c; v_mu] = [M v_c / dt + K_M v_mu;  M v_mu - H(c) v_c]
+// As in 3-D all are evaluated scaled by the lumped mass (M^-1 R, M^-1 J v) on
+// a tile with mirror images beyond the mesh, where every node uses the
+// interior formula; an optional final multiplication by m_i gives R and J v
+// themselves.
 //
 // One block per 32 x 16 node tile: U and v (or U^n) are staged with a 1-node
 // halo; every element touching the tile evaluates f'(u_q) (residual) or
@@ -31,18 +34,28 @@ __device__ __forceinline__ int mirror(int k, int n) {
 
 __device__ __forceinline__ float gpt(int i) { return i ? kGHi : kGLo; }
 
-template <bool kJVP>
+// 9-point stencil s at node (y, x) of a staged plane
+template <int W_>
+__device__ __forceinline__ float stencil(const float (*V)[W_], int y, int x, const Stencil2D& k) {
+  return k.c0 * V[y][x] + k.cx * (V[y][x - 1] + V[y][x + 1]) + k.cy * (V[y - 1][x] + V[y + 1][x]) +
+         k.cd * (V[y - 1][x - 1] + V[y - 1][x + 1] + V[y + 1][x - 1] + V[y + 1][x + 1]);
+}
+
+template <bool kJVP, bool kCH>
 __global__ void __launch_bounds__(kThreads) k_implicit2d(const Implicit2DArgs a) {
-  __shared__ float sU[SY][SX], sW[SY][SX];
+  // sU: U (AC) or c; sW: U^n / v (AC) or c^n / v_c; sM (CH): mu (residual) or v_mu (JVP)
+  __shared__ float sU[SY][SX], sW[SY][SX], sM[kCH ? SY : 1][kCH ? SX : 1];
   __shared__ float sE[4][EY][EX];
   const int tiles_x = (a.nx + TX - 1) / TX;
   const int x0 = (blockIdx.x % tiles_x) * TX, y0 = (blockIdx.x / tiles_x) * TY;
+  const int64_t N = (int64_t)a.nx * a.ny;
 
   for (int i = threadIdx.x; i < SX * SY; i += kThreads) {
     const int lx = i % SX, ly = i / SX;
     const int64_t g = (int64_t)mirror(y0 - 1 + ly, a.ny) * a.nx + mirror(x0 - 1 + lx, a.nx);
     sU[ly][lx] = a.U[g];
     sW[ly][lx] = a.W[g];
+    if (kCH) sM[ly][lx] = kJVP ? a.W[N + g] : a.U[N + g];
   }
   __syncthreads();
 
@@ -87,18 +100,22 @@ __global__ void __launch_bounds__(kThreads) k_implicit2d(const Implicit2DArgs a)
     const int x = lx + 1, y = ly + 1;
     const float acc = sE[0][y][x] + sE[1][y][x - 1] + sE[2][y - 1][x] + sE[3][y - 1][x - 1];
     const float (*V)[SX] = kJVP ? sW : sU;  // the stiffness acts on v (JVP) or U (residual)
-    const Stencil2D& k = a.k;
-    const float ks = k.c0 * V[y][x] + k.cx * (V[y][x - 1] + V[y][x + 1]) +
-                     k.cy * (V[y - 1][x] + V[y + 1][x]) +
-                     k.cd * (V[y - 1][x - 1] + V[y - 1][x + 1] + V[y + 1][x - 1] + V[y + 1][x + 1]);
+    const float ks = stencil(V, y, x, a.k);
     const float own = kJVP ? sW[y][x] : (sU[y][x] - sW[y][x]);
-    float g = fmaf(own, a.inv_dt, a.mob * (acc + ks));
+    float wm = 1.0f;
     if (a.unscaled) {
       const float wx = (gx == 0 || gx == a.nx - 1) ? 0.5f : 1.0f;
       const float wy = (gy == 0 || gy == a.ny - 1) ? 0.5f : 1.0f;
-      g *= a.cell * wx * wy;
+      wm = a.cell * wx * wy;
     }
-    a.out[(int64_t)gy * a.nx + gx] = g;
+    const int64_t o = (int64_t)gy * a.nx + gx;
+    if (kCH) {
+      // c row: own / dt + M_c m^-1 K (mu or v_mu);  mu row: (mu or v_mu) - m^-1 (r or H v_c)
+      a.out[o] = wm * fmaf(own, a.inv_dt, stencil(sM, y, x, a.km));
+      a.out[N + o] = wm * (sM[y][x] - (acc + ks));
+    } else {
+      a.out[o] = wm * fmaf(own, a.inv_dt, a.mob * (acc + ks));
+    }
   }
 }
 
@@ -106,13 +123,19 @@ __global__ void __launch_bounds__(kThreads) k_implicit2d(const Implicit2DArgs a)
 
 cudaError_t launch_residual2d(const Implicit2DArgs& a, cudaStream_t s) {
   const int tiles = ((a.nx + TX - 1) / TX) * ((a.ny + TY - 1) / TY);
-  k_implicit2d<false><<<tiles, kThreads, 0, s>>>(a);
+  if (a.ch)
+    k_implicit2d<false, true><<<tiles, kThreads, 0, s>>>(a);
+  else
+    k_implicit2d<false, false><<<tiles, kThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_jvp2d(const Implicit2DArgs& a, cudaStream_t s) {
   const int tiles = ((a.nx + TX - 1) / TX) * ((a.ny + TY - 1) / TY);
-  k_implicit2d<true><<<tiles, kThreads, 0, s>>>(a);
+  if (a.ch)
+    k_implicit2d<true, true><<<tiles, kThreads, 0, s>>>(a);
+  else
+    k_implicit2d<true, false><<<tiles, kThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -111,8 +111,13 @@ constexpr double kNoOversolve = 0.1;  // GMRES floor, as a fraction of Newton's 
 
 // meshes with the implicit step (and its Krylov vectors): 3-D, and 2-D Allen-Cahn
 bool has_implicit(const pf_ctx* c) {
-  return c->ens_count == 0 && (c->dim == 3 || c->model == PF_MODEL_AC);
+  return c->ens_count == 0 &&
+         (c->dim == 3 || c->model == PF_MODEL_AC || c->model == PF_MODEL_CH);
 }
+
+// 2-D Cahn-Hilliard solves the split system for [c; mu]: two planes per vector
+bool split_ch(const pf_ctx* c) { return c->dim == 2 && c->model == PF_MODEL_CH; }
+int imp_nf(const pf_ctx* c) { return split_ch(c) ? 2 : c->nf; }
 
 Layout layout(const pf_ctx* c) {
   Layout L{};
@@ -127,7 +132,7 @@ Layout layout(const pf_ctx* c) {
     off += field;
   }
   if (has_implicit(c)) {
-    L.vec = align_up(sizeof(float) * (size_t)nnodes(c) * c->nf, 256);
+    L.vec = align_up(sizeof(float) * (size_t)nnodes(c) * imp_nf(c), 256);
     L.vecs = off;
     off += L.vec * (kVec3d + pf::kMaxBasis);
   }
@@ -400,7 +405,7 @@ cudaError_t jvp3d(pf_ctx* c, const float* U, const float* v, float* out, int uns
   return pf::launch_jvp3d(a, c->stream);
 }
 
-int64_t vec_len(const pf_ctx* c) { return nnodes(c) * c->nf; }
+int64_t vec_len(const pf_ctx* c) { return nnodes(c) * imp_nf(c); }
 
 // U <- U - dt G with G = L M^-1 r(U) (the residual with U^n = U)
 pf_status step_explicit3d(pf_ctx* c, float* state, int64_t n_steps) {
@@ -415,7 +420,7 @@ pf_status step_explicit3d(pf_ctx* c, float* state, int64_t n_steps) {
 
 // ||M g||_2 in FP64 (weights = lumped mass), returned on the host
 pf_status mass_norm(pf_ctx* c, const float* g, double* out) {
-  PF_CUDA(pf::launch_mass_norm(g, (int)c->n[0], (int)c->n[1], (int)c->n[2], c->nf,
+  PF_CUDA(pf::launch_mass_norm(g, (int)c->n[0], (int)c->n[1], (int)c->n[2], imp_nf(c),
                                c->h[0] * c->h[1] * c->h[2], c->partials, c->result, c->stream));
   double h;
   PF_CUDA(cudaMemcpyAsync(&h, c->result, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -702,16 +707,19 @@ pf_status pf_set_params(pf_ctx* c, const pf_params* p) {
     set_params_coupled(c, p);
     return PF_OK;
   }
-  if (c->model == PF_MODEL_AC) {
+  if (c->model == PF_MODEL_AC || c->model == PF_MODEL_CH) {
     pf::Implicit2DArgs& b = c->im2;
+    const double cell = c->h[0] * c->h[1];
     b.nx = (int)c->n[0];
     b.ny = (int)c->n[1];
     b.dw2 = (float)(2.0 * p->W);
-    b.k = stiffness2d(c->h[0], c->h[1], p->kappa / (c->h[0] * c->h[1]));
+    b.k = stiffness2d(c->h[0], c->h[1], p->kappa / cell);
+    b.km = stiffness2d(c->h[0], c->h[1], p->mobility / cell);
     b.inv_dt = (float)(1.0 / p->dt);
     b.mob = (float)p->mobility;
-    b.cell = (float)(c->h[0] * c->h[1]);
+    b.cell = (float)cell;
     b.unscaled = 0;
+    b.ch = c->model == PF_MODEL_CH;
   }
 
   const double s = p->shift, W = p->W;
@@ -853,8 +861,10 @@ pf_status pf_step_implicit(pf_ctx* c, float* state, int64_t n_steps, const float
   pf_status st = check_ready(c);
   if (st != PF_OK) return st;
   if (!has_implicit(c))
-    return fail(c, PF_ERR_ARG, "pf_step_implicit supports 3-D meshes and 2-D Allen-Cahn");
+    return fail(c, PF_ERR_ARG, "pf_step_implicit supports 3-D meshes and 2-D AC / CH");
   if (!state) return fail(c, PF_ERR_ARG, "state is NULL");
+  if (c->par.mobility_field)
+    return fail(c, PF_ERR_ARG, "pf_step_implicit has no per-node mobility field");
   if (n_steps < 0) return fail(c, PF_ERR_ARG, "n_steps < 0");
   pf_newton_opts o{20, 30, 300, 1e-5, 1e-3};
   if (opts) o = *opts;
@@ -865,10 +875,21 @@ pf_status pf_step_implicit(pf_ctx* c, float* state, int64_t n_steps, const float
   pf_newton_stats s{0, 0, 1, 0.0, 0.0};
   const int64_t n = vec_len(c);
   const double inv_dt = 1.0 / c->par.dt;
+  const int64_t n_state = split_ch(c) ? nnodes(c) : n;  // CH: the state is c alone
   for (int64_t step = 0; step < n_steps; ++step) {
-    PF_CUDA(cudaMemcpyAsync(c->un, state, sizeof(float) * n, cudaMemcpyDeviceToDevice, c->stream));
+    PF_CUDA(cudaMemcpyAsync(c->un, state, sizeof(float) * n_state, cudaMemcpyDeviceToDevice,
+                            c->stream));
     const float* start = (step == 0 && guess) ? guess : state;
-    PF_CUDA(cudaMemcpyAsync(c->u, start, sizeof(float) * n, cudaMemcpyDeviceToDevice, c->stream));
+    PF_CUDA(cudaMemcpyAsync(c->u, start, sizeof(float) * n_state, cudaMemcpyDeviceToDevice,
+                            c->stream));
+    if (split_ch(c)) {
+      // mu of the starting c: with mu = 0 the mu row of M^-1 R is -M^-1 r(c)
+      const int64_t N = nnodes(c);
+      PF_CUDA(cudaMemsetAsync(c->un + N, 0, sizeof(float) * N, c->stream));
+      PF_CUDA(cudaMemsetAsync(c->u + N, 0, sizeof(float) * N, c->stream));
+      PF_CUDA(residual3d(c, c->u, c->un, c->g, 0));
+      PF_CUDA(pf::launch_axpby(-1.0f, c->g + N, 0.0f, c->u + N, N, c->stream));
+    }
     double ref;
     st = mass_norm(c, c->un, &ref);  // ||M U^n||; the target is rtol ||M U^n / dt||
     if (st != PF_OK) return st;
@@ -900,7 +921,8 @@ pf_status pf_step_implicit(pf_ctx* c, float* state, int64_t n_steps, const float
     }
     s.final_residual = rn;
     if (!ok) s.converged = 0;
-    PF_CUDA(cudaMemcpyAsync(state, c->u, sizeof(float) * n, cudaMemcpyDeviceToDevice, c->stream));
+    PF_CUDA(cudaMemcpyAsync(state, c->u, sizeof(float) * n_state, cudaMemcpyDeviceToDevice,
+                            c->stream));
     if (!ok) {
       PF_CUDA(cudaStreamSynchronize(c->stream));
       if (stats) *stats = s;
@@ -1242,7 +1264,7 @@ pf_status pf_jvp(pf_ctx* c, const float* U, const float* v, float* Jv) {
   if (!c) return PF_ERR_ARG;
   pf_status st = check_ready(c);
   if (st != PF_OK) return st;
-  if (!has_implicit(c)) return fail(c, PF_ERR_ARG, "pf_jvp supports 3-D meshes and 2-D Allen-Cahn");
+  if (!has_implicit(c)) return fail(c, PF_ERR_ARG, "pf_jvp supports 3-D meshes and 2-D AC / CH");
   if (!U || !v || !Jv) return fail(c, PF_ERR_ARG, "null array");
   PF_CUDA(jvp3d(c, U, v, Jv, 1));
   return PF_OK;
@@ -1253,7 +1275,7 @@ pf_status pf_implicit_residual(pf_ctx* c, const float* Un, const float* U, float
   pf_status st = check_ready(c);
   if (st != PF_OK) return st;
   if (!has_implicit(c))
-    return fail(c, PF_ERR_ARG, "pf_implicit_residual supports 3-D meshes and 2-D Allen-Cahn");
+    return fail(c, PF_ERR_ARG, "pf_implicit_residual supports 3-D meshes and 2-D AC / CH");
   if (!U || !Un || !R) return fail(c, PF_ERR_ARG, "null array");
   PF_CUDA(residual3d(c, U, Un, R, 1));
   return PF_OK;

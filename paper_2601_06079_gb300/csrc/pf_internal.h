@@ -144,17 +144,20 @@ struct Implicit3DArgs {
 };
 cudaError_t launch_residual3d(const Implicit3DArgs& a, cudaStream_t s);
 
-// The same operators on a 2-D mesh for the Allen-Cahn double well (one field).
+// The same operators on a 2-D mesh with the double well: Allen-Cahn (one
+// plane) or the split Cahn-Hilliard system (planes [c; mu]).
 struct Implicit2DArgs {
-  const float* U;  // state at which r / H is evaluated
-  const float* W;  // JVP: direction v; residual: U^n
+  const float* U;  // state at which r / H is evaluated (CH: [c; mu])
+  const float* W;  // JVP: direction v; residual: U^n (CH: c^n in the first plane)
   float* out;
   int nx, ny;
   float dw2;       // 2 W
   Stencil2D k;     // kappa / m K
+  Stencil2D km;    // CH: M_c / m K
   float inv_dt, mob;
   float cell;      // hx hy
   int unscaled;    // multiply the result by the lumped mass m_i
+  int ch;          // 1: split Cahn-Hilliard
 };
 cudaError_t launch_residual2d(const Implicit2DArgs& a, cudaStream_t s);
 cudaError_t launch_jvp2d(const Implicit2DArgs& a, cudaStream_t s);

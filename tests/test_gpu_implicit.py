@@ -180,3 +180,58 @@ def test_2d_implicit_root_reevaluated_by_oracle_at_1024():
     m = P.lumped_mass()
     ref = np.linalg.norm(m * U0.astype(np.float64) / 1.0)
     assert np.linalg.norm(R) <= 2e-5 * ref
+
+
+# ---------------------------------------------------------------- 2-D split Cahn-Hilliard
+
+
+def _ch2d(shape, h, dt=0.05):
+    import paper_2601_06079_gb300 as pf
+    s = pf.Solver(shape, h=h, model="ch")
+    s.set_params(W=1.0, kappa=0.5, mobility=1.0, dt=dt)
+    P = O.Problem(shape, h=h, W=1.0, kappa=0.5, mob=1.0)
+    return s, P
+
+
+@pytest.mark.parametrize("shape,h", [((37, 45), 1.0), ((64, 130), (0.9, 1.2)), ((3, 4), 1.0)])
+def test_2d_ch_split_jvp_and_residual_match_oracle(shape, h):
+    s, P = _ch2d(shape, h)
+    cn = G.ch_initial(3, shape)
+    U = np.stack([G.ch_initial(4, shape), G.random_field(5, shape)])
+    v = np.stack([G.random_field(6, shape), G.random_field(7, shape)])
+    Un = np.stack([cn, np.zeros(shape, np.float32)])
+    cu = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+    assert rel(s.jvp(cu(U), cu(v)).cpu().numpy(), P.chsplit_jvp(0.05, U, v)) <= 2e-6
+    assert rel(s.implicit_residual(cu(Un), cu(U)).cpu().numpy(),
+               P.chsplit_residual(0.05, cn, U)) <= 2e-6
+
+
+def test_2d_ch_implicit_steps_match_oracle_and_conserve_c():
+    shape = (67, 90)
+    s, P = _ch2d(shape, 1.0, dt=0.05)
+    c0 = G.ch_initial(8, shape)
+    t = torch.from_numpy(c0).cuda()
+    st = s.step_implicit(t, 3, newton_rtol=1e-7, gmres_rtol=1e-5)
+    assert st["converged"]
+    ref = c0.astype(np.float64)
+    for _ in range(3):
+        U, info = P.chsplit_newton(0.05, ref, abs_tol=1e-9)
+        assert info["ok"]
+        ref = U[0]
+    got = t.cpu().numpy()
+    assert rel(got, ref) <= 1e-5
+    m0 = P.mass_integral(c0.astype(np.float64))
+    assert abs(P.mass_integral(got.astype(np.float64)) - m0) <= 1e-6 * abs(m0)
+
+
+def test_2d_ch_implicit_large_step_1024():
+    # a step 1000x the explicit one of the bench (dt 1e-3), as the paper's
+    # implicit benchmarks take: Newton converges and c is conserved
+    shape = (1024, 1024)
+    s, P = _ch2d(shape, 1.0, dt=1.0)
+    c0 = G.ch_initial(9, shape)
+    t = torch.from_numpy(c0).cuda()
+    st = s.step_implicit(t, 2)
+    assert st["converged"] and st["newton_iters"] >= 2
+    m0 = P.mass_integral(c0.astype(np.float64))
+    assert abs(P.mass_integral(t.cpu().numpy().astype(np.float64)) - m0) <= 1e-6 * abs(m0)
