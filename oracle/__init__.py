@@ -20,6 +20,7 @@ Parity pins (tests/test_oracle_*.py check them without a GPU):
   ch_explicit          cosine-mode growth factor; exact mass conservation;
                          monotone energy decrease
   hessian / jvp        central FD of the residual; symmetry u.Jv = v.Ju
+  implicit_adjoint     central FD of the objective in L and kappa
   chsplit (implicit CH) JVP = central FD of the residual; exact conservation of
                        c; first-order agreement with the explicit step as dt -> 0;
                        energy decrease
@@ -76,6 +77,8 @@ def lib():
         L.or_ch_chemical_potential.argtypes = [M, Pp, P, P]
         L.or_ch_explicit.argtypes = [M, Pp, C.c_double, C.c_int64, P]
         L.or_coupled_explicit.argtypes = [M, Pp, C.c_double, C.c_int64, P]
+        L.or_implicit_adjoint.restype = C.c_double
+        L.or_implicit_adjoint.argtypes = [M, Pp, C.c_double, C.c_int64, P, C.c_double, P]
         L.or_chsplit_residual.argtypes = [M, Pp, C.c_double, P, P, P]
         L.or_chsplit_jvp.argtypes = [M, Pp, C.c_double, P, P, P]
         L.or_chsplit_newton.restype = C.c_int
@@ -234,6 +237,15 @@ class Problem:
                              C.byref(fn))
         return U, dict(ok=bool(ok), newton_iters=ni.value, gmres_iters=gi.value,
                        final_norm=fn.value)
+
+    def implicit_adjoint(self, U0, dt, nsteps, abs_tol=1e-12):
+        """Objective O = domain average of U^N after nsteps implicit steps (Eq. 19)
+        and its sensitivities [dO/dL, dO/dkappa] by the adjoint of Supp. 2."""
+        U0 = _f64(U0)
+        g = np.zeros(2)
+        O = lib().or_implicit_adjoint(C.byref(self.m), C.byref(self.p), dt, nsteps, _ptr(U0),
+                                      abs_tol, _ptr(g))
+        return O, g
 
     # -- implicit split Cahn-Hilliard (Eq. 9-10, 13): U = [c, mu] --
     def chsplit_residual(self, dt, cn, U):

@@ -625,6 +625,59 @@ int or_newton(const or_mesh* m, const or_params* p, double dt, const double* Un,
                    max_newton, restart, gmres_rtol, newton_iters, gmres_iters, final_norm);
 }
 
+/* ---- adjoint of the implicit Allen-Cahn trajectory (Supp. 2, Eq. II.1-II.6) --
+ * Steps C(U^{n+1}; U^n, theta) = M (U^{n+1} - U^n)/dt + L r(U^{n+1}) = 0 from U^0,
+ * objective O = (1/V) sum_i m_i U^N_i (the domain average, Eq. 19), parameters
+ * theta = (L, kappa).  Reverse sweep with lambda^N = dO/dU^N:
+ *   (dC/dU^{n+1})^T mu = lambda^{n+1}   (J = M/dt + L H symmetric: one GMRES solve)
+ *   dO/dL     -= mu . r(U^{n+1})
+ *   dO/dkappa -= mu . L K U^{n+1}
+ *   lambda^n   = -(dC/dU^n)^T mu = M mu / dt
+ * Newton steps to abs_tol; grads = [dO/dL, dO/dkappa].  Returns O. */
+double or_implicit_adjoint(const or_mesh* m, const or_params* p, double dt, int64_t nsteps,
+                           const double* U0, double abs_tol, double* grads) {
+  const int64_t NN = or_nnodes(m), n = NN * p->nf;
+  double* traj = (double*)malloc(sizeof(double) * n * (nsteps + 1));
+  double* mass = (double*)malloc(sizeof(double) * NN);
+  double* lam = (double*)malloc(sizeof(double) * n);
+  double* mu = (double*)malloc(sizeof(double) * n);
+  double* t1 = (double*)malloc(sizeof(double) * n);
+  or_lumped_mass(m, mass);
+  double V = 0.0;
+  for (int64_t i = 0; i < NN; ++i) V += mass[i];
+  memcpy(traj, U0, sizeof(double) * n);
+  for (int64_t s = 0; s < nsteps; ++s) {
+    double* U = traj + (s + 1) * n;
+    memcpy(U, traj + s * n, sizeof(double) * n);
+    or_newton(m, p, dt, traj + s * n, U, abs_tol, 50, 30, 1e-12, NULL, NULL, NULL);
+  }
+  double O = 0.0;
+  for (int f = 0; f < p->nf; ++f)
+    for (int64_t i = 0; i < NN; ++i) {
+      O += mass[i] * traj[nsteps * n + f * NN + i] / V;
+      lam[f * NN + i] = mass[i] / V;
+    }
+  /* K U alone: the residual of the gradient energy with kappa = 1 and no local energy */
+  or_params pK = *p;
+  pK.kappa = 1.0;
+  pK.W = 0.0;
+  pK.alpha = pK.beta = pK.gamma = 0.0;
+  grads[0] = grads[1] = 0.0;
+  for (int64_t s = nsteps - 1; s >= 0; --s) {
+    const double* U = traj + (s + 1) * n;
+    memset(mu, 0, sizeof(double) * n);
+    or_gmres(m, p, dt, U, lam, mu, 30, 3000, 1e-13, NULL);
+    or_residual(m, p, U, t1);  /* r(U) */
+    grads[0] -= dot(mu, t1, n);
+    or_residual(m, &pK, U, t1);  /* K U */
+    grads[1] -= p->mob * dot(mu, t1, n);
+    for (int f = 0; f < p->nf; ++f)
+      for (int64_t i = 0; i < NN; ++i) lam[f * NN + i] = mass[i] * mu[f * NN + i] / dt;
+  }
+  free(traj); free(mass); free(lam); free(mu); free(t1);
+  return O;
+}
+
 /* ---- implicit split Cahn-Hilliard (Eq. 9-10 with backward Euler, Eq. 13) --
  * Unknowns U = [c; mu] (2 N values), the previous composition cn:
  *   R_c  = M (c - cn) / dt + K_M mu

@@ -50,6 +50,9 @@ void or_mobility_stiffness_apply(const or_mesh* m, const or_params* p,
 void or_ac_explicit(const or_mesh* m, const or_params* p, double dt, int64_t nsteps, double* U);
 void or_ch_chemical_potential(const or_mesh* m, const or_params* p, const double* c, double* mu);
 void or_ch_explicit(const or_mesh* m, const or_params* p, double dt, int64_t nsteps, double* c);
+/* Adjoint of an implicit Allen-Cahn trajectory: O = mean of U^N, grads = [dO/dL, dO/dkappa]. */
+double or_implicit_adjoint(const or_mesh* m, const or_params* p, double dt, int64_t nsteps,
+                           const double* U0, double abs_tol, double* grads);
 /* Implicit split Cahn-Hilliard: U = [c; mu] (2 planes), cn the previous c. */
 void or_chsplit_residual(const or_mesh* m, const or_params* p, double dt, const double* cn,
                          const double* U, double* R);

@@ -62,3 +62,22 @@ def test_gradient_flow_newton_reaches_its_root():
     U, info = P.newton(0.5, Un, abs_tol=1e-12)
     assert info["ok"]
     assert np.linalg.norm(P.implicit_residual(0.5, Un, U)) <= 1e-12
+
+
+def test_implicit_adjoint_sensitivities_match_central_differences():
+    # Table 1 setting: a 64 x 64 mesh on a domain of 100 x 100, objective the
+    # domain average of the order parameter (Eq. 19), theta = (L, kappa); dt L
+    # max|f''| < 1 keeps every implicit step's root unique (so O is smooth in theta)
+    shape, h = (64, 64), 100.0 / 63.0
+    U0 = G.ac_initial(11, shape, 0.2, 0.8).astype(np.float64)
+
+    def obj(L, kappa):
+        P = O.Problem(shape, h=h, W=1.0, kappa=kappa, mob=L)
+        return P.implicit_adjoint(U0, 0.5, 6)
+
+    O0, g = obj(1.0, 2.0)
+    eps = 1e-5
+    fd = [(obj(1.0 + eps, 2.0)[0] - obj(1.0 - eps, 2.0)[0]) / (2 * eps),
+          (obj(1.0, 2.0 + eps)[0] - obj(1.0, 2.0 - eps)[0]) / (2 * eps)]
+    for a, b in zip(g, fd):
+        assert abs(a - b) <= 1e-6 * max(abs(b), 1e-3), (g, fd)
