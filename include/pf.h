@@ -170,6 +170,25 @@ pf_status pf_jvp(pf_ctx* ctx, const float* U, const float* v, float* Jv);
  * first plane of Un = c^n.  Device arrays, n_fields * N FP32.  Enqueues only. */
 pf_status pf_implicit_residual(pf_ctx* ctx, const float* Un, const float* U, float* R);
 
+/* Bytes of caller-owned device workspace pf_implicit_adjoint needs for n_steps
+ * steps: n_steps + 3 state vectors (every state of the trajectory is kept) and
+ * 256 bytes.  Gradient-flow meshes only (3-D, 2-D Allen-Cahn).  Host only. */
+pf_status pf_implicit_adjoint_workspace(pf_ctx* ctx, int64_t n_steps, size_t* bytes);
+
+/* Sensitivities of an implicit trajectory by the adjoint method of Supp. 2
+ * (Eq. II.1-II.6): n_steps backward-Euler steps (Eq. 13-14, Newton-GMRES with
+ * opts, may be NULL) from U0 (device), objective O = (1/V) sum_i m_i U^N_i (the
+ * domain average of Eq. 19), theta = (L, kappa).  Reverse sweep per step: one
+ * GMRES solve of J(U^{n+1})^T mu = lambda^{n+1} (J = M/dt + L H is symmetric),
+ * dO/dL -= mu . r(U^{n+1}), dO/dkappa -= mu . L K U^{n+1}, lambda^n = M mu / dt.
+ * objective, grads[2] = [dO/dL, dO/dkappa]: host.  workspace: device, >=
+ * pf_implicit_adjoint_workspace bytes, 256-byte aligned.  stats (host, may be
+ * NULL): forward Newton/GMRES counts plus the adjoint GMRES iterations.
+ * Synchronises the stream. */
+pf_status pf_implicit_adjoint(pf_ctx* ctx, const float* U0, int64_t n_steps,
+                              const pf_newton_opts* opts, void* workspace, size_t bytes,
+                              double* objective, double* grads, pf_newton_stats* stats);
+
 /* Bytes of caller-owned device workspace pf_adjoint needs for n_steps steps
  * with a checkpoint every ckpt_every steps: (ceil(n_steps/ckpt_every) + 1)
  * checkpoint planes, ckpt_every segment planes, 3 more planes and small

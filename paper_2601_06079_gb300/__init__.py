@@ -129,6 +129,25 @@ class Solver:
             return t.data_ptr()
         return self._state(t)
 
+    def implicit_adjoint(self, U0, n_steps, max_newton=20, gmres_restart=30,
+                         gmres_max_iters=300, newton_rtol=1e-5, gmres_rtol=1e-3):
+        """Objective O = domain average of U^N after n_steps implicit steps from U0
+        (Eq. 19) and its sensitivities {L, kappa} by the adjoint of Supp. 2
+        (pf_implicit_adjoint).  Returns (O, grads, stats)."""
+        C = _lib.C
+        nb = C.c_size_t(0)
+        self._check(_lib.lib().pf_implicit_adjoint_workspace(self._ctx, n_steps, C.byref(nb)))
+        ws = torch.empty(max(nb.value, 256), dtype=torch.uint8, device=self.device)
+        opts = _lib.pf_newton_opts(max_newton, gmres_restart, gmres_max_iters, newton_rtol,
+                                   gmres_rtol)
+        O, g = C.c_double(0), (C.c_double * 2)()
+        stats = _lib.pf_newton_stats()
+        self._check(_lib.lib().pf_implicit_adjoint(self._ctx, C.c_void_p(self._state(U0)), n_steps,
+                                                   C.byref(opts), C.c_void_p(ws.data_ptr()),
+                                                   ws.numel(), C.byref(O), g, C.byref(stats)))
+        return O.value, {"L": g[0], "kappa": g[1]}, {k: getattr(stats, k)
+                                                     for k, _ in _lib.pf_newton_stats._fields_}
+
     def jvp(self, U, v, out=None):
         """J v of Eq. 14 (unscaled: includes the lumped mass); 2-D CH: the split
         system's Jacobian action on [v_c; v_mu] at [c; mu]."""

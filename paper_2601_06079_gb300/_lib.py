@@ -133,6 +133,12 @@ def lib():
         L.pf_energy2d_static.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_double,
                                          C.c_double, C.c_double, C.c_double, C.c_void_p,
                                          C.c_void_p, C.POINTER(C.c_char_p)]
+        L.pf_implicit_adjoint_workspace.restype = st
+        L.pf_implicit_adjoint_workspace.argtypes = [ctx, C.c_int64, C.POINTER(C.c_size_t)]
+        L.pf_implicit_adjoint.restype = st
+        L.pf_implicit_adjoint.argtypes = [ctx, C.c_void_p, C.c_int64, C.POINTER(pf_newton_opts),
+                                          C.c_void_p, C.c_size_t, C.POINTER(C.c_double),
+                                          C.POINTER(C.c_double), C.POINTER(pf_newton_stats)]
         L.pf_set_form.restype = st
         L.pf_set_form.argtypes = [ctx, C.c_int]
         L.pf_last_error.restype = C.c_char_p
@@ -148,7 +154,8 @@ def exported_symbols():
     return ["pf_create_mesh", "pf_bind_workspace", "pf_set_params", "pf_step_explicit",
             "pf_set_form",
             "pf_step_implicit", "pf_jvp", "pf_implicit_residual", "pf_adjoint_workspace",
-            "pf_adjoint", "pf_create_ensemble", "pf_set_ensemble_params", "pf_tune_ensemble",
+            "pf_adjoint", "pf_implicit_adjoint_workspace", "pf_implicit_adjoint",
+            "pf_create_ensemble", "pf_set_ensemble_params", "pf_tune_ensemble",
             "pf_step_ensemble", "pf_barrier_selftest", "pf_surrogate_param_count",
             "pf_surrogate_workspace", "pf_surrogate_predict", "pf_surrogate_train_step",
             "pf_surrogate_loss_grad",

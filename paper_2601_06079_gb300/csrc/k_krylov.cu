@@ -155,6 +155,23 @@ __global__ void __launch_bounds__(kThreads) k_mass_norm(const float* __restrict_
   if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
+// out = a * m_i^(+1 or -1) * in over nf planes of nx x ny x nz nodes, m the
+// lumped mass (cell times 1/2 per boundary axis; nz = 1 is a 2-D mesh)
+__global__ void k_mass_mul(const float* __restrict__ in, float* __restrict__ out, int nx, int ny,
+                           int nz, int nf, double cell, float a, int inverse) {
+  const int64_t N = (int64_t)nx * ny * nz, n = N * nf;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t node = i % N;
+    const int x = (int)(node % nx), y = (int)((node / nx) % ny), z = (int)(node / ((int64_t)nx * ny));
+    double m = cell;
+    if (x == 0 || x == nx - 1) m *= 0.5;
+    if (y == 0 || y == ny - 1) m *= 0.5;
+    if (nz > 1 && (z == 0 || z == nz - 1)) m *= 0.5;
+    out[i] = (float)((double)a * (inverse ? (double)in[i] / m : m * (double)in[i]));
+  }
+}
+
 unsigned elementwise_blocks(int64_t n) {
   int64_t b = (n + 255) / 256;
   return (unsigned)(b < 152 * 8 ? b : 152 * 8);
@@ -186,6 +203,13 @@ cudaError_t launch_axpby(float a, const float* x, float b, float* y, int64_t n, 
 cudaError_t launch_lincomb(const float* V, int64_t ldv, int k, const LinComb& y, float* x,
                            int64_t n, cudaStream_t s) {
   k_lincomb<<<elementwise_blocks(n), 256, 0, s>>>(V, ldv, k, y, x, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mass_mul(const float* in, float* out, int nx, int ny, int nz, int nf,
+                            double cell, float a, int inverse, cudaStream_t s) {
+  k_mass_mul<<<elementwise_blocks((int64_t)nx * ny * nz * nf), 256, 0, s>>>(in, out, nx, ny, nz, nf,
+                                                                          cell, a, inverse);
   return cudaGetLastError();
 }
 

@@ -1160,6 +1160,43 @@ pf_status pf_barrier_selftest(unsigned* dev_scratch, long long limit_cycles, int
   return flag ? PF_ERR_TIMEOUT : PF_OK;
 }
 
+// ---- adjoint of an implicit trajectory (Supp. 2, Eq. II.1-II.6) ----------
+
+size_t iadj_vec(const pf_ctx* c) { return align_up(sizeof(float) * (size_t)vec_len(c), 256); }
+
+bool iadj_ok(const pf_ctx* c) { return has_implicit(c) && !split_ch(c); }
+
+// out = L K U (unscaled): the residual with no local energy and kappa = 1 at U^n = U
+cudaError_t stiff_only(pf_ctx* c, const float* U, float* out) {
+  if (c->dim == 2) {
+    pf::Implicit2DArgs a = c->im2;
+    a.dw2 = 0.0f;
+    a.k = stiffness2d(c->h[0], c->h[1], 1.0 / (c->h[0] * c->h[1]));
+    a.U = U;
+    a.W = U;
+    a.out = out;
+    a.unscaled = 1;
+    return pf::launch_residual2d(a, c->stream);
+  }
+  pf::Implicit3DArgs a = c->im;
+  a.dw2 = 0.0f;
+  a.alpha = a.two_gamma = a.four_gamma = a.cb2g = a.c3b6g = 0.0f;
+  stiffness3d(c->h, 1.0 / (c->h[0] * c->h[1] * c->h[2]), a.kc);
+  a.U = U;
+  a.W = U;
+  a.out = out;
+  a.unscaled = 1;
+  return pf::launch_residual3d(a, c->stream);
+}
+
+// FP64 dot product of two device vectors of the context's length, on the host
+pf_status dot_host(pf_ctx* c, const float* a, const float* b, double* scratch, double* out) {
+  PF_CUDA(pf::launch_dots(a, 0, 1, b, vec_len(c), c->partials, scratch, c->stream));
+  PF_CUDA(cudaMemcpyAsync(out, scratch, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  PF_CUDA(cudaStreamSynchronize(c->stream));
+  return PF_OK;
+}
+
 pf_status pf_adjoint_workspace(pf_ctx* c, int64_t n_steps, int ckpt_every, size_t* bytes) {
   if (!c || !bytes) return PF_ERR_ARG;
   if (c->dim != 2 || c->model != PF_MODEL_CH)
@@ -1288,6 +1325,92 @@ void pf_destroy(pf_ctx* c) {
   destroy_graph(c);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
+}
+
+pf_status pf_implicit_adjoint_workspace(pf_ctx* c, int64_t n_steps, size_t* bytes) {
+  if (!c || !bytes) return PF_ERR_ARG;
+  if (!iadj_ok(c))
+    return fail(c, PF_ERR_ARG, "the implicit adjoint needs a gradient-flow mesh (3-D, 2-D AC)");
+  if (n_steps < 1) return fail(c, PF_ERR_ARG, "n_steps must be >= 1");
+  *bytes = iadj_vec(c) * (size_t)(n_steps + 3) + 256;
+  return PF_OK;
+}
+
+pf_status pf_implicit_adjoint(pf_ctx* c, const float* U0, int64_t n_steps,
+                              const pf_newton_opts* opts, void* ws, size_t bytes,
+                              double* objective, double* grads, pf_newton_stats* stats) {
+  if (!c) return PF_ERR_ARG;
+  pf_status st = check_ready(c);
+  if (st != PF_OK) return st;
+  size_t need = 0;
+  if ((st = pf_implicit_adjoint_workspace(c, n_steps, &need)) != PF_OK) return st;
+  if (!U0 || !ws || !objective || !grads) return fail(c, PF_ERR_ARG, "null argument");
+  if (bytes < need || (uintptr_t)ws % 256)
+    return fail(c, PF_ERR_ARG, "implicit adjoint workspace too small or misaligned (%zu < %zu)",
+                bytes, need);
+  const int64_t n = vec_len(c);
+  const size_t vb = iadj_vec(c);
+  char* w = (char*)ws;
+  auto traj = [&](int64_t s) { return (float*)(w + vb * (size_t)s); };
+  float* lam = (float*)(w + vb * (size_t)(n_steps + 1));
+  float* tmp = (float*)(w + vb * (size_t)(n_steps + 2));
+  double* dscr = (double*)(w + vb * (size_t)(n_steps + 3));
+  const int nz = c->dim == 3 ? (int)c->n[2] : 1;
+  const double cell = c->h[0] * c->h[1] * c->h[2];
+  const double dt = c->par.dt, L = c->par.mobility;
+  pf_newton_stats tot{0, 0, 1, 0.0, 0.0};
+
+  // forward: the implicit trajectory, every state kept
+  PF_CUDA(cudaMemcpyAsync(traj(0), U0, sizeof(float) * n, cudaMemcpyDeviceToDevice, c->stream));
+  for (int64_t s = 0; s < n_steps; ++s) {
+    PF_CUDA(cudaMemcpyAsync(traj(s + 1), traj(s), sizeof(float) * n, cudaMemcpyDeviceToDevice,
+                            c->stream));
+    pf_newton_stats one{};
+    st = pf_step_implicit(c, traj(s + 1), 1, nullptr, opts, &one);
+    tot.newton_iters += one.newton_iters;
+    tot.gmres_iters += one.gmres_iters;
+    if (s == 0) tot.initial_residual = one.initial_residual;
+    tot.final_residual = one.final_residual;
+    if (st != PF_OK) {
+      if (stats) *stats = tot;
+      return st;
+    }
+  }
+  // objective O = (1/V) sum_i m_i U^N_i (Eq. 19) and lambda^N = dO/dU^N = m / V
+  double V = 1.0;
+  for (int k = 0; k < c->dim; ++k) V *= (double)(c->n[k] - 1) * c->h[k];
+  PF_CUDA(cudaMemsetAsync(tmp, 0, sizeof(float) * n, c->stream));
+  PF_CUDA(pf::launch_add(tmp, tmp, n, 1.0f, c->stream));
+  PF_CUDA(pf::launch_mass_mul(tmp, lam, (int)c->n[0], (int)c->n[1], nz, imp_nf(c), cell,
+                              (float)(1.0 / V), 0, c->stream));
+  if ((st = dot_host(c, lam, traj(n_steps), dscr, objective)) != PF_OK) return st;
+  // reverse sweep: J(U^{n+1})^T mu = lambda (J symmetric), gradients, lambda <- M mu / dt
+  grads[0] = grads[1] = 0.0;
+  const int restart = opts ? opts->gmres_restart : 30;
+  const int maxit = opts ? opts->gmres_max_iters : 300;
+  for (int64_t s = n_steps - 1; s >= 0; --s) {
+    const float* U = traj(s + 1);
+    PF_CUDA(cudaMemcpyAsync(c->u, U, sizeof(float) * n, cudaMemcpyDeviceToDevice, c->stream));
+    PF_CUDA(pf::launch_mass_mul(lam, c->g, (int)c->n[0], (int)c->n[1], nz, imp_nf(c), cell,
+                                -1.0f, 1, c->stream));  // G = -M^-1 lambda
+    int gi = 0;
+    double rel = 0.0;
+    if ((st = gmres3d(c, restart, 10 * maxit, 1e-6, 0.0, &gi, &rel)) != PF_OK) return st;
+    tot.gmres_iters += gi;
+    double d = 0.0;
+    PF_CUDA(residual3d(c, U, U, tmp, 1));  // L r(U)
+    if ((st = dot_host(c, c->d, tmp, dscr, &d)) != PF_OK) return st;
+    grads[0] -= d / L;                     // dC/dL = r(U)
+    PF_CUDA(stiff_only(c, U, tmp));        // L K U
+    if ((st = dot_host(c, c->d, tmp, dscr, &d)) != PF_OK) return st;
+    grads[1] -= d;                         // dC/dkappa = L K U
+    PF_CUDA(pf::launch_mass_mul(c->d, lam, (int)c->n[0], (int)c->n[1], nz, imp_nf(c), cell,
+                                (float)(1.0 / dt), 0, c->stream));
+  }
+  if (stats) *stats = tot;
+  if (!std::isfinite(*objective) || !std::isfinite(grads[0]) || !std::isfinite(grads[1]))
+    return fail(c, PF_ERR_NONFINITE, "non-finite adjoint result");
+  return PF_OK;
 }
 
 }  // extern "C"

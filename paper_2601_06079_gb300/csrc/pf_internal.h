@@ -174,6 +174,8 @@ cudaError_t launch_dots(const float* V, int64_t ldv, int k, const float* w, int6
 cudaError_t launch_update(const float* V, int64_t ldv, int k, const double* coef, float* w,
                           int64_t n, double* partials, double* norm_out, cudaStream_t s);
 cudaError_t launch_axpby(float a, const float* x, float b, float* y, int64_t n, cudaStream_t s);
+cudaError_t launch_mass_mul(const float* in, float* out, int nx, int ny, int nz, int nf,
+                            double cell, float a, int inverse, cudaStream_t s);
 cudaError_t launch_lincomb(const float* V, int64_t ldv, int k, const LinComb& y, float* x,
                            int64_t n, cudaStream_t s);
 cudaError_t launch_mass_norm(const float* g, int nx, int ny, int nz, int nf, double cell,
