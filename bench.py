@@ -257,6 +257,7 @@ def run_ours(args):
                          "ensemble_256_ac": forms_ensemble(dev, stream, flush),
                          "coupled_acch_2048": forms_coupled(dev, stream, flush),
                          "implicit_2d_2048": forms_implicit_2d(dev, stream),
+                         "implicit_adjoint_ac_1024": forms_implicit_adjoint(dev, stream),
                          "adjoint_ch_512": forms_adjoint(dev, stream),
                          "implicit_warm_start_128": forms_warm_start(dev)}
     if not args.no_cpu_baseline:
@@ -373,6 +374,36 @@ def forms_implicit_2d(dev, stream, n=2048, n_steps=50):
     out["accuracy_gate"] = ("Newton roots vs the oracle's FP64 Newton steps "
                             "(tests/test_gpu_implicit.py)")
     return out
+
+
+def forms_implicit_adjoint(dev, stream, n=1024, n_steps=10):
+    """Sensitivities of an implicit Allen-Cahn trajectory (Supp. 2 adjoint;
+    objective of Eq. 19, theta = (L, kappa)) on 1024^2, dt 0.5: the forward
+    trajectory alone vs forward + reverse sweep."""
+    import torch
+
+    import paper_2601_06079_gb300 as pf
+    import pf_inputs as G
+    s = pf.Solver((n, n), h=1.0, model="ac", device=dev, stream=stream)
+    s.set_params(W=1.0, kappa=1.0, mobility=1.0, dt=0.5)
+    U0 = torch.from_numpy(G.ac_initial(2, (n, n), 0.2, 0.8)).to(dev)
+    s.implicit_adjoint(U0, 1)  # warm
+    U = U0.clone()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    fwd = s.step_implicit(U, n_steps)
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    O, g, st = s.implicit_adjoint(U0, n_steps)
+    torch.cuda.synchronize()
+    t_adj = time.perf_counter() - t0
+    return {"mesh": f"{n}x{n}", "steps": n_steps, "dt": 0.5, "objective": O, "grads": g,
+            "forward_s": t_fwd, "forward_plus_adjoint_s": t_adj,
+            "adjoint_over_forward": t_adj / t_fwd,
+            "forward_gmres_iters": fwd["gmres_iters"], "total_gmres_iters": st["gmres_iters"],
+            "accuracy_gate": "<= 0.1 per mille (L) / 0.5 per mille (kappa) vs the FP64 oracle "
+                             "adjoint in the Table 1 setting (tests/test_gpu_implicit.py)"}
 
 
 def forms_ensemble(dev, stream, flush, n_steps=1000):
