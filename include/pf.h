@@ -351,7 +351,10 @@ pf_status pf_surrogate_loss_grad(const float* params, float out_scale, const flo
  * multiples of 8.  mode 0: out = conv(x) + bias; mode 1: out = conv^T(dy);
  * mode 2: out = [dW (27 x c_out x c_in), db (c_out)] for dy.  Modes 0 and 1
  * run the tcgen05 kernel (d even, h a multiple of 8 -- always here); modes 3
- * and 4 are 0 and 1 on the mma.sync kernel.  Workspace (256-byte aligned) of
+ * and 4 are 0 and 1 on the mma.sync kernel; mode 5 is the failure-path
+ * self-test: mode 0 with no input copies issued, so every bounded pipeline
+ * wait expires (about 2 s), the kernel frees its tensor memory and returns,
+ * and the call reports PF_ERR_TIMEOUT with the context still usable.  Workspace (256-byte aligned) of
  * at least 2V(c_in + c_out) + 4 * 27 c_in c_out + 128 V + 16,809,984 bytes
  * plus 256 per part (V = d h w).  Synchronises the stream; PF_ERR_TIMEOUT if a
  * tensor-core pipeline wait expired. */

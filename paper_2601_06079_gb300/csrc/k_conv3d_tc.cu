@@ -189,7 +189,7 @@ template <int CIN, int COUT>
 __global__ void __launch_bounds__(kThreads, 1)
     k_conv3d_tc(const __grid_constant__ CUtensorMap xmap, const __nv_bfloat16* __restrict__ wt,
                 const float* __restrict__ bias, int relu, __nv_bfloat16* y16, float* y32, int B,
-                int D, int H, int W, int* err) {
+                int D, int H, int W, int* err, int selftest) {
   using C = Cfg<CIN, COUT>;
   extern __shared__ unsigned char smem_raw[];
   // 128-byte aligned base (TMA destinations and descriptors)
@@ -238,9 +238,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp == 0) {
     // ---- TMA producer ----
+    // (selftest: issue nothing, so that the MMA thread's bounded wait on the
+    // first stage must expire and every role takes the error path)
     if (lane == 0) {
       int i = 0;
-      for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+      for (int t = blockIdx.x; t < ntiles && !selftest; t += gridDim.x, ++i) {
         const int s = i % kStages;
         if (i >= kStages && !bar_wait(&ctl->empty[s], ((i / kStages) - 1) & 1, abort, err)) break;
         const int tx = t % tiles_x, ty = (t / tiles_x) % tiles_y;
@@ -414,7 +416,8 @@ int sm_count() {
 
 template <int CIN, int COUT>
 cudaError_t tc_launch(const void* x, const void* wt, const float* bias, int relu, void* y16,
-                      float* y32, int B, int D, int H, int W, int* err, cudaStream_t s) {
+                      float* y32, int B, int D, int H, int W, int* err, int selftest,
+                      cudaStream_t s) {
   using C = Cfg<CIN, COUT>;
   auto enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
@@ -448,7 +451,8 @@ cudaError_t tc_launch(const void* x, const void* wt, const float* bias, int relu
   const int ntiles = B * (D / TZ) * (H / TY) * ((W + TX - 1) / TX);
   const int grid = ntiles < sm_count() ? ntiles : sm_count();
   k_conv3d_tc<CIN, COUT><<<grid, kThreads, C::kSmem, s>>>(
-      map, (const __nv_bfloat16*)wt, bias, relu, (__nv_bfloat16*)y16, y32, B, D, H, W, err);
+      map, (const __nv_bfloat16*)wt, bias, relu, (__nv_bfloat16*)y16, y32, B, D, H, W, err,
+      selftest);
   return cudaGetLastError();
 }
 
@@ -460,14 +464,14 @@ bool conv3d_tc_shape_ok(int B, int D, int H, int W) {
 
 cudaError_t launch_conv3d_tc(int cin, int cout, const void* x, const void* wt, const float* bias,
                              int relu, void* y16, float* y32, int B, int D, int H, int W,
-                             int* err, cudaStream_t s) {
+                             int* err, cudaStream_t s, int selftest) {
   if (!conv3d_tc_shape_ok(B, D, H, W) || !err || (uintptr_t)x % 16) return cudaErrorInvalidValue;
   if (cin == 16 && cout == 32)
-    return tc_launch<16, 32>(x, wt, bias, relu, y16, y32, B, D, H, W, err, s);
+    return tc_launch<16, 32>(x, wt, bias, relu, y16, y32, B, D, H, W, err, selftest, s);
   if (cin == 32 && cout == 32)
-    return tc_launch<32, 32>(x, wt, bias, relu, y16, y32, B, D, H, W, err, s);
+    return tc_launch<32, 32>(x, wt, bias, relu, y16, y32, B, D, H, W, err, selftest, s);
   if (cin == 32 && cout == 16)
-    return tc_launch<32, 16>(x, wt, bias, relu, y16, y32, B, D, H, W, err, s);
+    return tc_launch<32, 16>(x, wt, bias, relu, y16, y32, B, D, H, W, err, selftest, s);
   return cudaErrorInvalidValue;
 }
 

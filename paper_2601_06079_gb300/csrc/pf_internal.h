@@ -189,10 +189,11 @@ cudaError_t launch_conv3d(int cin, int cout, const void* x, const void* wt, cons
                           cudaStream_t s);
 // tcgen05 + TMA implicit GEMM (D even, H multiple of 8, any W); *err is set
 // to 1 when a pipeline wait expired (the output is then incomplete).
+// selftest = 1 issues no input copies, so that the waits must expire.
 bool conv3d_tc_shape_ok(int B, int D, int H, int W);
 cudaError_t launch_conv3d_tc(int cin, int cout, const void* x, const void* wt, const float* bias,
                              int relu, void* y16, float* y32, int B, int D, int H, int W,
-                             int* err, cudaStream_t s);
+                             int* err, cudaStream_t s, int selftest = 0);
 int conv_wgrad_blocks(int B, int D, int H, int W, int max_blocks);
 cudaError_t launch_conv3d_wgrad(int cin, int cout, const void* x, const void* dy, float* part,
                                 float* dw, int B, int D, int H, int W, int blocks, cudaStream_t s);

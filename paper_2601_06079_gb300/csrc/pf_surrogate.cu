@@ -376,16 +376,18 @@ pf_status pf_conv3d_check(int mode, int cin, int cout, int d, int h, int w, cons
   // in and out ([c][d][h][w], one sample), weights [27][c_out][c_in] FP32.
   // mode 0: out = conv(x) + bias; 1: out = conv^T(dy); 2: out = [dW (27 c_out c_in), db];
   // modes 0 and 1 take the tcgen05 kernel where the shape allows, 3 and 4 are
-  // 0 and 1 on the mma.sync kernel.
+  // 0 and 1 on the mma.sync kernel; 5 is mode 0 on the tcgen05 kernel with no
+  // input copies issued (the bounded pipeline waits must expire: PF_ERR_TIMEOUT).
   const bool ok_c = (cin == 16 && cout == 32) || (cin == 32 && cout == 32) ||
                     (cin == 32 && cout == 16);
-  if (!ok_c || mode < 0 || mode > 4 || !x || !wt || !out || !ws || d % 2 || h % 8 || w % 8 ||
+  if (!ok_c || mode < 0 || mode > 5 || !x || !wt || !out || !ws || d % 2 || h % 8 || w % 8 ||
       d < 2 || h < 8 || w < 8)
     return PF_ERR_ARG;
   const int64_t V = (int64_t)d * h * w;
   size_t need = al(2 * V * cin) + al(2 * V * cout) + 2 * al(2 * 27 * cin * cout) + al(4 * V * kC) +
                 al(4 * (size_t)kWgradBlocks * 27 * cin * cout) + al(sizeof(int));
-  if (bytes < need || (mode != 0 && mode != 3 && !dy) || (uintptr_t)ws % 256) return PF_ERR_ARG;
+  if (bytes < need || (mode == 1 || mode == 2 || mode == 4) && !dy || (uintptr_t)ws % 256)
+    return PF_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   char* p = (char*)ws;
   void* xb = p;
@@ -401,15 +403,18 @@ pf_status pf_conv3d_check(int mode, int cin, int cout, int d, int h, int w, cons
   float* part = (float*)p;
   p += al(4 * (size_t)kWgradBlocks * 27 * cin * cout);
   int* err = (int*)p;
-  const bool tc = (mode == 0 || mode == 1) && pf::conv3d_tc_shape_ok(1, d, h, w);
+  const bool tc = (mode == 0 || mode == 1 || mode == 5) && pf::conv3d_tc_shape_ok(1, d, h, w);
+  const int selftest = mode == 5;
+  if (mode == 5 && !tc) return PF_ERR_ARG;
   auto run = [&](int ci, int co, const void* in, const void* wts, const float* bs) {
-    return tc ? pf::launch_conv3d_tc(ci, co, in, wts, bs, 0, nullptr, y32, 1, d, h, w, err, s)
+    return tc ? pf::launch_conv3d_tc(ci, co, in, wts, bs, 0, nullptr, y32, 1, d, h, w, err, s,
+                                     selftest)
               : pf::launch_conv3d(ci, co, in, wts, bs, 0, nullptr, y32, 1, d, h, w, kConvGrid, s);
   };
   SG_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
   SG_CUDA(pf::launch_convert_weights(wt, cin, cout, wf, wb, s));
   SG_CUDA(pf::launch_planar_to_ndhwc(x, cin, cin, 1, V, 0, nullptr, xb, s));
-  if (mode == 0 || mode == 3) {
+  if (mode == 0 || mode == 3 || mode == 5) {
     SG_CUDA(run(cin, cout, xb, wf, bias));
     SG_CUDA(pf::launch_ndhwc_to_planar_add(y32, cout, cout, 1, V, nullptr, 0, 0, nullptr, out, s));
   } else {

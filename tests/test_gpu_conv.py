@@ -144,3 +144,23 @@ def test_history_network_gradient_matches_torch_autograd_reference(hist):
     guess = s.predict(x)
     ref = R.extrapolate(xd).float().cuda()
     assert float((guess - ref).abs().max()) <= 2e-6
+
+
+def test_tcgen05_pipeline_timeout_is_reported_and_recoverable():
+    # no input copies are issued: every bounded wait of the warp-specialised
+    # pipeline must expire, free its tensor memory and report PF_ERR_TIMEOUT;
+    # the next call on the same context then runs normally
+    from paper_2601_06079_gb300 import _lib
+    d, h, w = 4, 16, 16
+    x = torch.from_numpy(G.random_field(1, (32, d, h, w))).cuda()
+    wt = torch.from_numpy(0.1 * G.random_field(2, (27, 32, 32))).cuda()
+    b = torch.zeros(32, device="cuda")
+    out = torch.zeros(32 * d * h * w, device="cuda")
+    ws = torch.empty(64 << 20, dtype=torch.uint8, device="cuda")
+    args = lambda mode: (mode, 32, 32, d, h, w, x.data_ptr(), wt.data_ptr(), b.data_ptr(), 0,
+                         out.data_ptr(), ws.data_ptr(), ws.numel(),
+                         torch.cuda.current_stream().cuda_stream)
+    assert _lib.pf_conv3d_check(*args(5)) == _lib.PF_ERR_TIMEOUT
+    assert _lib.pf_conv3d_check(*args(0)) == 0
+    got, ref = run(0, 32, 32, (d, h, w), seed=1)
+    assert rel(got, ref) <= 2e-5
