@@ -29,6 +29,14 @@ Parity pins (tests/test_oracle_*.py check them without a GPU):
   ch_adjoint           central FD of the loss (scalars, a smooth direction of
                          the mobility field, single nodes); per-step
                          dot-product test against the linearised forward map
+  Elastic (Eq. 3-4, III.1, 21-22)
+                       element stiffness against an independent 3-point Gauss
+                         assembly; symmetry, the six rigid-body modes; uniform-
+                         strain energy and the patch test; uniform eigenstrain
+                         solved exactly (u = m x); the volume identity
+                         V = V0 + int tr eps0 of a traction-free body; Eshelby's
+                         radial solution of a spherical inclusion; adjoint
+                         sensitivities against central FD and E-invariance
 """
 from __future__ import annotations
 
@@ -102,6 +110,16 @@ def lib():
         L.or_conv3d_bwd_weight.argtypes = [P, I, I, I, I, P, I, P, P]
         L.or_ch_adjoint.restype = C.c_double
         L.or_ch_adjoint.argtypes = [M, Pp, C.c_double, C.c_int64, P, P, C.c_int, P, P, P]
+        D = C.c_double
+        L.or_elastic_lame.argtypes = [D, D, P, P]
+        L.or_elastic_apply.argtypes = [M, D, D, P, P]
+        L.or_elastic_rhs.argtypes = [M, D, D, D, D, D, P]
+        L.or_elastic_volume_functional.restype = D
+        L.or_elastic_volume_functional.argtypes = [M, P]
+        L.or_elastic_cg.restype = C.c_int
+        L.or_elastic_cg.argtypes = [M, D, D, P, P, D, C.c_int, C.POINTER(C.c_int)]
+        L.or_elastic_sensitivity.restype = D
+        L.or_elastic_sensitivity.argtypes = [M, D, D, D, D, D, P, D, C.c_int, P, P]
         _LIB = L
     return _LIB
 
@@ -316,3 +334,72 @@ def conv3d_bwd_weight(x, dy):
     db = np.zeros(co)
     lib().or_conv3d_bwd_weight(_ptr(x), ci, d, h, ww, _ptr(dy), co, _ptr(dw), _ptr(db))
     return dw, db
+
+
+# ---- Eshelby inclusion: linear elasticity with a misfit eigenstrain ----
+
+class Elastic:
+    """Q1 small-strain elasticity on a (nz, ny, nx) node grid with spacing h
+    (Eq. 3-4); displacements [3][nz][ny][nx] (x, y, z components).  The
+    eigenstrain is m phi(r) I, phi = (1 - tanh(l (r - a))) / 2, r = |x| from
+    node (0, 0, 0) (Eq. III.1, inclusion reading); x = 0, y = 0, z = 0 are
+    symmetry planes, the other faces traction-free."""
+
+    def __init__(self, shape, h=1.0):
+        assert len(shape) == 3
+        self.shape = tuple(shape)
+        self.m = mesh(self.shape, h)
+
+    def _out(self):
+        return np.zeros((3,) + self.shape)
+
+    @staticmethod
+    def lame(E, nu):
+        lam, mu = np.zeros(1), np.zeros(1)
+        lib().or_elastic_lame(E, nu, _ptr(lam), _ptr(mu))
+        return float(lam[0]), float(mu[0])
+
+    def apply(self, u, lam, mu):
+        """K u, assembled over all elements, no constraints."""
+        u = _f64(u)
+        out = self._out()
+        lib().or_elastic_apply(C.byref(self.m), lam, mu, _ptr(u), _ptr(out))
+        return out
+
+    def rhs(self, lam, mu, m, l, a):
+        """Eigenstrain load f = int B^T C eps0."""
+        f = self._out()
+        lib().or_elastic_rhs(C.byref(self.m), lam, mu, m, l, a, _ptr(f))
+        return f
+
+    def volume_functional(self):
+        """(V0, g) with V = V0 + g . u the small-strain volume."""
+        g = self._out()
+        V0 = lib().or_elastic_volume_functional(C.byref(self.m), _ptr(g))
+        return V0, g
+
+    def cg(self, b, lam, mu, rtol=1e-12, maxit=20000):
+        """K u = b on the unconstrained degrees of freedom (CG from zero)."""
+        b = _f64(b)
+        u = self._out()
+        it = C.c_int(0)
+        ok = lib().or_elastic_cg(C.byref(self.m), lam, mu, _ptr(b), _ptr(u), rtol, maxit,
+                                 C.byref(it))
+        return u, bool(ok), it.value
+
+    def solve(self, E, nu, m, l, a, rtol=1e-12, maxit=20000):
+        lam, mu = self.lame(E, nu)
+        return self.cg(self.rhs(lam, mu, m, l, a), lam, mu, rtol, maxit)
+
+    def sensitivity(self, E, nu, m, l, a, g=None, rtol=1e-12, maxit=20000):
+        """(O, [dO/dE, dO/dnu], u) for O = g . u (g = the volume functional if
+        None, and then O = V includes V0), Eq. 21-22."""
+        V0 = 0.0
+        if g is None:
+            V0, g = self.volume_functional()
+        g = _f64(g)
+        u = self._out()
+        grads = np.zeros(2)
+        O = lib().or_elastic_sensitivity(C.byref(self.m), E, nu, m, l, a, _ptr(g), rtol, maxit,
+                                         _ptr(u), _ptr(grads))
+        return O + V0, grads, u

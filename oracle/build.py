@@ -10,19 +10,19 @@ import os
 import subprocess
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "pf_oracle.c")
+_SRCS = [os.path.join(_HERE, "pf_oracle.c"), os.path.join(_HERE, "or_elastic.c")]
 _OUT_DIR = os.path.join(_HERE, "_build")
 _OUT = os.path.join(_OUT_DIR, "liboracle.so")
 
 
 def build(force: bool = False) -> str:
-    deps = [_SRC, os.path.join(_HERE, "pf_oracle.h")]
+    deps = _SRCS + [os.path.join(_HERE, "pf_oracle.h")]
     if (not force and os.path.exists(_OUT)
             and os.path.getmtime(_OUT) >= max(os.path.getmtime(d) for d in deps)):
         return _OUT
     os.makedirs(_OUT_DIR, exist_ok=True)
     tmp = _OUT + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-Wall", "-o", tmp, _SRC,
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-Wall", "-o", tmp, *_SRCS,
            "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _OUT)

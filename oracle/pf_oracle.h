@@ -86,4 +86,18 @@ void or_conv3d_bwd_data(const double* dy, int co, int d, int h, int w, const dou
                         double* dx);
 void or_conv3d_bwd_weight(const double* x, int ci, int d, int h, int w, const double* dy, int co,
                           double* dwt, double* dbias);
+/* ---- Eshelby inclusion: linear elasticity with a misfit eigenstrain
+ * (Eq. 3-4, Supp. 3 Eq. III.1, objective Eq. 21-22); or_elastic.c.  dim 3,
+ * displacements component-major u[c*nnodes + node]. ---- */
+void or_elastic_lame(double E, double nu, double* lam, double* mu);
+void or_elastic_apply(const or_mesh* m, double lam, double mu, const double* u, double* out);
+void or_elastic_rhs(const or_mesh* m, double lam, double mu, double em, double el, double ea,
+                    double* f);
+double or_elastic_volume_functional(const or_mesh* m, double* g);
+int or_elastic_cg(const or_mesh* m, double lam, double mu, const double* b, double* u,
+                  double rtol, int maxit, int* iters);
+double or_elastic_sensitivity(const or_mesh* m, double E, double nu, double em, double el,
+                              double ea, const double* g, double rtol, int maxit, double* u_out,
+                              double* grads);
+
 #endif
