@@ -362,6 +362,67 @@ pf_status pf_conv3d_check(int mode, int cin, int cout, int d, int h, int w, cons
                           const float* wt, const float* bias, const float* dy, float* out,
                           void* workspace, size_t bytes, void* stream);
 
+/* ---- Eshelby inclusion: misfit elasticity (Eq. 3-4; eigenstrain Supp. 3
+ * Eq. III.1; objective and sensitivities Eq. 21-22) ----
+ * Small-strain isotropic elasticity on a uniform 3-D grid of Q1 hexahedra
+ * (2x2x2 Gauss), div sigma = 0, sigma = C : (eps - eps0), with
+ *   eps0 = m phi(r) I,  phi = (1 - tanh(l (r - a))) / 2,  r = |x|,
+ * x measured from node (0, 0, 0).  The inclusion sits at that corner, so the
+ * planes x = 0, y = 0, z = 0 are symmetry planes (normal displacement zero)
+ * and the other faces are traction-free.  Displacements are FP32 device arrays
+ * [3][nz][ny][nx] (x, y, z components, x fastest).  Context-free: every call
+ * takes the problem description by pointer.  PF_ERR_ARG for n < 2, h <= 0,
+ * E <= 0, nu outside (-1, 1/2) or non-finite m, l, a. */
+typedef struct {
+  int64_t n[3];  /* nodes per axis (x, y, z) */
+  double h[3];   /* node spacing per axis */
+  double E, nu;  /* Young's modulus, Poisson's ratio */
+  double m, l, a;/* misfit strain, interface sharpness (1/length), inclusion radius */
+} pf_elastic;
+
+typedef struct {
+  int iterations;      /* CG iterations (both solves for pf_elastic_sensitivity) */
+  int converged;
+  double initial_residual, final_residual; /* |r| of the (first) solve, FP64 */
+} pf_cg_stats;
+
+/* Device workspace bytes for pf_elastic_solve / pf_elastic_sensitivity (7
+ * vectors of 3 nx ny nz floats plus scalars).  Host only. */
+pf_status pf_elastic_workspace(const pf_elastic* e, size_t* bytes);
+
+/* Ku = K u (matrix-free, all elements of the mesh); constrain = 1 zeroes the
+ * rows of the symmetry-plane constraints.  u and Ku distinct device arrays.
+ * Enqueued on `stream`, no synchronisation. */
+pf_status pf_elastic_apply(const pf_elastic* e, const float* u, float* Ku, int constrain,
+                           void* stream);
+
+/* unit = 0: f = int B^T C eps0 (the eigenstrain load);  unit = 1: g with
+ * V = V0 + g . u the small-strain volume int (1 + tr eps(u)) of Eq. 21.
+ * No constraint applied.  Enqueued on `stream`. */
+pf_status pf_elastic_load(const pf_elastic* e, int unit, float* f, void* stream);
+
+/* Conjugate gradients for K u = b on the free degrees of freedom (b = NULL:
+ * the eigenstrain load; b's constrained entries are ignored), from u = 0,
+ * FP32 vectors and FP64 inner products, until |r| <= rtol |b| (checked every
+ * 8 iterations) or max_iter.  Workspace 256-byte aligned, pf_elastic_workspace
+ * bytes.  Synchronises the stream.  PF_ERR_NOT_CONVERGED at max_iter (u holds
+ * the last iterate), PF_ERR_NONFINITE on a non-finite residual. */
+pf_status pf_elastic_solve(const pf_elastic* e, const float* b, float* u, double rtol,
+                           int max_iter, void* workspace, size_t bytes, void* stream,
+                           pf_cg_stats* stats);
+
+/* Objective O = g . u of the equilibrium displacement u (written to `u`) and
+ * grads = [dO/dE, dO/dnu] by the adjoint of the linear system: K lambda = g,
+ * dO/dtheta = lambda . (df/dtheta - dK/dtheta u).  g = NULL takes the volume
+ * functional, and then O = V includes the undeformed volume V0.  With uniform
+ * moduli u does not depend on E, and V does not depend on E or nu (the mean
+ * strain of a traction-free body equals its mean eigenstrain), so those
+ * sensitivities are zero up to the solver tolerance.  Same workspace, errors
+ * and synchronisation as pf_elastic_solve; stats sum both solves. */
+pf_status pf_elastic_sensitivity(const pf_elastic* e, const float* g, float* u, double rtol,
+                                 int max_iter, void* workspace, size_t bytes, void* stream,
+                                 double* objective, double* grads, pf_cg_stats* stats);
+
 /* Human-readable description of the last failure on this context. */
 const char* pf_last_error(const pf_ctx* ctx);
 

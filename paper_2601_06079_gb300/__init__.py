@@ -11,6 +11,8 @@ streams only; every step of the method runs in the library's CUDA kernels.
 """
 from __future__ import annotations
 
+import ctypes as C
+
 import torch
 
 from . import _lib
@@ -367,6 +369,76 @@ class Surrogate:
         if st != 0:
             raise PFError(st, "pf_surrogate_train_step")
         return loss
+
+
+class Elastic:
+    """Eshelby-inclusion elasticity (Eq. 3-4, eigenstrain of Supp. 3 Eq. III.1,
+    objective Eq. 21-22; pf_elastic_* in include/pf.h) on a (nz, ny, nx) node
+    grid.  Displacements are float32 CUDA tensors [3, nz, ny, nx]; the
+    inclusion sits at node (0, 0, 0) with symmetry planes x, y, z = 0."""
+
+    def __init__(self, shape, h=1.0, E=22.5, nu=0.3, m=0.01, l=0.5, a=20.0, device="cuda",
+                 stream=None):
+        assert len(shape) == 3
+        self.shape = tuple(int(v) for v in shape)
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        hs = (float(h),) * 3 if isinstance(h, (int, float)) else tuple(float(v) for v in h)
+        self.e = _lib.pf_elastic((C.c_int64 * 3)(*reversed(self.shape)), (C.c_double * 3)(*hs),
+                                 E, nu, m, l, a)
+        self._ws = None
+        self.stats = _lib.pf_cg_stats()
+
+    def set(self, **kw):
+        for k, v in kw.items():
+            setattr(self.e, k, float(v))
+
+    def _check(self, st, what):
+        if st != 0:
+            raise PFError(st, what)
+
+    def _sp(self):
+        return self.stream.cuda_stream
+
+    def _workspace(self):
+        if self._ws is None:
+            st, n = _lib.pf_elastic_workspace(self.e)
+            self._check(st, "pf_elastic_workspace")
+            self._ws = torch.empty(n, dtype=torch.uint8, device=self.device)
+        return self._ws
+
+    def empty(self):
+        return torch.empty((3,) + self.shape, dtype=torch.float32, device=self.device)
+
+    def apply(self, u, out=None, constrain=False):
+        out = self.empty() if out is None else out
+        self._check(_lib.pf_elastic_apply(self.e, u.data_ptr(), out.data_ptr(), int(constrain),
+                                          self._sp()), "pf_elastic_apply")
+        return out
+
+    def load(self, unit=False, out=None):
+        out = self.empty() if out is None else out
+        self._check(_lib.pf_elastic_load(self.e, int(unit), out.data_ptr(), self._sp()),
+                    "pf_elastic_load")
+        return out
+
+    def solve(self, b=None, u=None, rtol=1e-6, max_iter=20000):
+        u = self.empty() if u is None else u
+        ws = self._workspace()
+        self._check(_lib.pf_elastic_solve(self.e, b.data_ptr() if b is not None else None,
+                                          u.data_ptr(), rtol, max_iter, ws.data_ptr(), ws.numel(),
+                                          self._sp(), self.stats), "pf_elastic_solve")
+        return u
+
+    def sensitivity(self, g=None, u=None, rtol=1e-6, max_iter=20000):
+        """(O, {"E": dO/dE, "nu": dO/dnu}, u), O = g . u or the volume V."""
+        u = self.empty() if u is None else u
+        ws = self._workspace()
+        st, O, grads = _lib.pf_elastic_sensitivity(
+            self.e, g.data_ptr() if g is not None else None, u.data_ptr(), rtol, max_iter,
+            ws.data_ptr(), ws.numel(), self._sp(), self.stats)
+        self._check(st, "pf_elastic_sensitivity")
+        return O, {"E": grads[0], "nu": grads[1]}, u
 
 
 class _CHMisfit(torch.autograd.Function):

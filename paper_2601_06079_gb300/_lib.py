@@ -40,6 +40,16 @@ class pf_params(C.Structure):
                 ("mobility_field", C.c_void_p), ("mobility2", C.c_double)]
 
 
+class pf_elastic(C.Structure):
+    _fields_ = [("n", C.c_int64 * 3), ("h", C.c_double * 3), ("E", C.c_double),
+                ("nu", C.c_double), ("m", C.c_double), ("l", C.c_double), ("a", C.c_double)]
+
+
+class pf_cg_stats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("converged", C.c_int),
+                ("initial_residual", C.c_double), ("final_residual", C.c_double)]
+
+
 class pf_newton_opts(C.Structure):
     _fields_ = [("max_newton", C.c_int), ("gmres_restart", C.c_int), ("gmres_max_iters", C.c_int),
                 ("newton_rtol", C.c_double), ("gmres_rtol", C.c_double)]
@@ -141,6 +151,21 @@ def lib():
                                           C.POINTER(C.c_double), C.POINTER(pf_newton_stats)]
         L.pf_set_form.restype = st
         L.pf_set_form.argtypes = [ctx, C.c_int]
+        E = C.POINTER(pf_elastic)
+        vp = C.c_void_p
+        L.pf_elastic_workspace.restype = st
+        L.pf_elastic_workspace.argtypes = [E, C.POINTER(C.c_size_t)]
+        L.pf_elastic_apply.restype = st
+        L.pf_elastic_apply.argtypes = [E, vp, vp, C.c_int, vp]
+        L.pf_elastic_load.restype = st
+        L.pf_elastic_load.argtypes = [E, C.c_int, vp, vp]
+        L.pf_elastic_solve.restype = st
+        L.pf_elastic_solve.argtypes = [E, vp, vp, C.c_double, C.c_int, vp, C.c_size_t, vp,
+                                       C.POINTER(pf_cg_stats)]
+        L.pf_elastic_sensitivity.restype = st
+        L.pf_elastic_sensitivity.argtypes = [E, vp, vp, C.c_double, C.c_int, vp, C.c_size_t, vp,
+                                             C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                             C.POINTER(pf_cg_stats)]
         L.pf_last_error.restype = C.c_char_p
         L.pf_last_error.argtypes = [ctx]
         L.pf_destroy.restype = None
@@ -159,7 +184,8 @@ def exported_symbols():
             "pf_step_ensemble", "pf_barrier_selftest", "pf_surrogate_param_count",
             "pf_surrogate_workspace", "pf_surrogate_predict", "pf_surrogate_train_step",
             "pf_surrogate_loss_grad",
-            "pf_conv3d_check", "pf_energy",
+            "pf_conv3d_check", "pf_energy", "pf_elastic_workspace", "pf_elastic_apply",
+            "pf_elastic_load", "pf_elastic_solve", "pf_elastic_sensitivity",
             "pf_energy2d_static", "pf_last_error", "pf_destroy"]
 
 
@@ -316,6 +342,36 @@ def pf_energy2d_static(state_ptr, nx, ny, hx, hy, W, kappa, out_ptr, stream):
     s = lib().pf_energy2d_static(C.c_void_p(state_ptr), nx, ny, hx, hy, W, kappa,
                                  C.c_void_p(out_ptr), C.c_void_p(stream), C.byref(msg))
     return s, (msg.value.decode() if msg.value else "")
+
+
+def pf_elastic_workspace(e):
+    n = C.c_size_t(0)
+    s = lib().pf_elastic_workspace(C.byref(e), C.byref(n))
+    return s, n.value
+
+
+def pf_elastic_apply(e, u, Ku, constrain, stream):
+    return lib().pf_elastic_apply(C.byref(e), C.c_void_p(u), C.c_void_p(Ku), int(constrain),
+                                  C.c_void_p(stream))
+
+
+def pf_elastic_load(e, unit, f, stream):
+    return lib().pf_elastic_load(C.byref(e), int(unit), C.c_void_p(f), C.c_void_p(stream))
+
+
+def pf_elastic_solve(e, b, u, rtol, max_iter, ws, nbytes, stream, stats):
+    return lib().pf_elastic_solve(C.byref(e), C.c_void_p(b) if b else None, C.c_void_p(u),
+                                  float(rtol), int(max_iter), C.c_void_p(ws), nbytes,
+                                  C.c_void_p(stream), C.byref(stats))
+
+
+def pf_elastic_sensitivity(e, g, u, rtol, max_iter, ws, nbytes, stream, stats):
+    obj = C.c_double(0.0)
+    grads = (C.c_double * 2)()
+    s = lib().pf_elastic_sensitivity(C.byref(e), C.c_void_p(g) if g else None, C.c_void_p(u),
+                                     float(rtol), int(max_iter), C.c_void_p(ws), nbytes,
+                                     C.c_void_p(stream), C.byref(obj), grads, C.byref(stats))
+    return s, obj.value, [grads[0], grads[1]]
 
 
 def pf_last_error(ctx) -> str:

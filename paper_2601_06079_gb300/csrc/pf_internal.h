@@ -163,6 +163,33 @@ cudaError_t launch_residual2d(const Implicit2DArgs& a, cudaStream_t s);
 cudaError_t launch_jvp2d(const Implicit2DArgs& a, cudaStream_t s);
 cudaError_t launch_jvp3d(const Implicit3DArgs& a, cudaStream_t s);
 
+// Eshelby-inclusion elasticity (Eq. 3-4, III.1): K u with the element
+// stiffness ke[(a*3+i)*24 + b*3+j] of the uniform box element and its
+// assembled interior stencil ks[(o*3+i)*3+j], o = (dz+1)*9 + (dy+1)*3 + (dx+1).
+struct Elastic3DArgs {
+  const float* u;
+  float* out;
+  int nx, ny, nz;
+  int constrain;  // zero the rows of the symmetry-plane constraints
+  float ke[24 * 24];
+  float ks[27 * 9];
+};
+// load: w d_i N_a(q) s(q) summed per node; s = scale * phi(|x_q|) (unit = 0,
+// phi = (1 - tanh(l (r - a))) / 2) or scale (unit = 1)
+struct ElasticLoadArgs {
+  int nx, ny, nz;
+  int unit, constrain;
+  float hx, hy, hz, ihx, ihy, ihz, wq, scale, l, a;
+};
+cudaError_t launch_elastic_apply(const Elastic3DArgs& a, cudaStream_t s);
+cudaError_t launch_elastic_load(const ElasticLoadArgs& a, float* f, cudaStream_t s);
+cudaError_t launch_elastic_constrain(float* v, int nx, int ny, int nz, cudaStream_t s);
+// CG updates with device scalars sc[0..1] = r.r (ping-pong by slot), sc[2] = p.Ap
+cudaError_t launch_cg_xr(float* x, float* r, const float* p, const float* Ap, int64_t n,
+                         const double* sc, int slot, cudaStream_t s);
+cudaError_t launch_cg_p(const float* r, float* p, int64_t n, const double* sc, int slot,
+                        cudaStream_t s);
+
 // Krylov vector kernels (FP32 vectors, FP64 inner products).
 constexpr int kMaxBasis = 32;  // GMRES restart length + 1
 struct LinComb {
