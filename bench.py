@@ -259,7 +259,8 @@ def run_ours(args):
                          "implicit_2d_2048": forms_implicit_2d(dev, stream),
                          "implicit_adjoint_ac_1024": forms_implicit_adjoint(dev, stream),
                          "adjoint_ch_512": forms_adjoint(dev, stream),
-                         "implicit_warm_start_128": forms_warm_start(dev)}
+                         "implicit_warm_start_128": forms_warm_start(dev),
+                         "eshelby_129": forms_eshelby(dev, stream, flush)}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_sample_steps)
     print(json.dumps(line), flush=True)
@@ -404,6 +405,53 @@ def forms_implicit_adjoint(dev, stream, n=1024, n_steps=10):
             "forward_gmres_iters": fwd["gmres_iters"], "total_gmres_iters": st["gmres_iters"],
             "accuracy_gate": "<= 0.1 per mille (L) / 0.5 per mille (kappa) vs the FP64 oracle "
                              "adjoint in the Table 1 setting (tests/test_gpu_implicit.py)"}
+
+
+def forms_eshelby(dev, stream, flush, n=129):
+    """Eshelby inclusion (Eq. 3-4, eigenstrain of Supp. 3 Eq. III.1, objective
+    and sensitivities of Eq. 21-22) on the 100^3 cube with n^3 nodes, E = 22.5,
+    nu = 0.3, m = 0.01, l = 0.5, a = 20: the stiffness operator alone (L2
+    flushed before each launch), the CG solve (rtol 1e-6) and the volume with
+    its adjoint sensitivities (two solves)."""
+    import torch
+
+    import paper_2601_06079_gb300 as pf
+    h = 100.0 / (n - 1)
+    el = pf.Elastic((n, n, n), h, E=22.5, nu=0.3, m=0.01, l=0.5, a=20.0, device=dev,
+                    stream=stream)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1)
+    u = torch.rand((3, n, n, n), generator=gen, device=dev) * 2 - 1
+    out = el.empty()
+    for _ in range(3):
+        el.apply(u, out)
+    t_apply = sorted(_timed(stream, lambda: el.apply(u, out), flush) for _ in range(21))[10]
+    nodes = n ** 3
+    flop = 546  # per interior node: 26 offsets x 9 FMA + 78 differences
+    peak_tflops = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 lanes x 2 flop x max SM clock
+    el.solve(rtol=1e-6)  # warm
+    x = el.empty()
+    t_solve = _timed(stream, lambda: el.solve(u=x, rtol=1e-6))
+    it_solve = el.stats.iterations
+    res = {}
+
+    def sens():
+        res["out"] = el.sensitivity(u=x, rtol=1e-6)
+    t_sens = _timed(stream, sens)
+    V, grads, _ = res["out"]
+    return {"mesh": f"{n}^3 nodes, h = {h:g}", "dof": 3 * nodes,
+            "apply_us": t_apply * 1e6,
+            "apply_roofline": {"bound": "alu", "achieved": flop * nodes / t_apply / 1e12,
+                               "peak": peak_tflops, "unit": "TFLOP/s",
+                               "frac": flop * nodes / t_apply / 1e12 / peak_tflops,
+                               "hbm_gbs_at_24B_per_node": 24 * nodes / t_apply / 1e9},
+            "solve_ms": t_solve * 1e3, "cg_iterations": it_solve,
+            "dof_iterations_per_s": 3 * nodes * it_solve / t_solve,
+            "sensitivity_ms": t_sens * 1e3, "sensitivity_cg_iterations": el.stats.iterations,
+            "volume_change": V - 100.0 ** 3, "dV_dE": grads["E"], "dV_dnu": grads["nu"],
+            "accuracy_gate": "operator and loads <= 2e-6 rel vs the FP64 oracle; solution, "
+                             "objective <= 1e-5 and dO/dnu <= 1e-4 vs the oracle adjoint "
+                             "(tests/test_gpu_elastic.py)"}
 
 
 def forms_ensemble(dev, stream, flush, n_steps=1000):
@@ -568,7 +616,8 @@ def run_profile(args):
     jvp       three Fan-Chen Jacobian-vector products on 128^3 x 8 fields
     ensemble  20 steps of the 256-instance AC ensemble, one launch per step (the
               persistent mode runs the same task body behind a grid barrier)
-    coupled   20 coupled Allen-Cahn / Cahn-Hilliard steps on 2048^2"""
+    coupled   20 coupled Allen-Cahn / Cahn-Hilliard steps on 2048^2
+    elastic   five Eshelby stiffness applications on 129^3 x 3 components"""
     import torch
 
     import paper_2601_06079_gb300 as pf
@@ -603,6 +652,14 @@ def run_profile(args):
             jv = solver.jvp(U, v)
         torch.cuda.synchronize()
         print(f"profile run done: |Jv| {float(jv.norm()):.6f}")
+    elif args.target == "elastic":
+        n = 129
+        el = pf.Elastic((n, n, n), 100.0 / (n - 1))
+        u = torch.from_numpy(G.random_field(3, (3, n, n, n))).cuda()
+        for _ in range(5):
+            Ku = el.apply(u)
+        torch.cuda.synchronize()
+        print(f"profile run done: |Ku| {float(Ku.norm()):.6f}")
     elif args.target == "coupled":
         s = pf.Solver((N_SIDE, N_SIDE), h=1.0, model="coupled")
         s.set_params(kappa=0.3, mobility=1.0, mobility2=150.0, dt=1e-3)
@@ -636,7 +693,7 @@ def main():
                     help="run one workload untimed for ncu (see --target)")
     ap.add_argument("--tsteps", type=int, default=N_TSTEPS)
     ap.add_argument("--target", default="ch",
-                    choices=["ch", "surrogate", "jvp", "ensemble", "coupled"],
+                    choices=["ch", "surrogate", "jvp", "ensemble", "coupled", "elastic"],
                     help="workload of --profile")
     args = ap.parse_args()
     if args.warmup < 3:

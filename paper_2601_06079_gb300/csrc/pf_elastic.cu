@@ -5,6 +5,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
+
 #include "pf_internal.h"
 
 namespace {
@@ -89,6 +91,7 @@ void fill_apply(const pf_elastic* e, double lam, double mu, int constrain, Elast
   a->ny = (int)e->n[1];
   a->nz = (int)e->n[2];
   a->constrain = constrain;
+  a->dot = nullptr;
   for (int r = 0; r < 24; ++r)
     for (int c = 0; c < 24; ++c) a->ke[r * 24 + c] = (float)K[r][c];
   // assembled interior stencil: offset o = b - a over all 8 elements of a node
@@ -132,7 +135,11 @@ Layout layout(const pf_elastic* e) {
   Layout L;
   L.vec = ((size_t)(3 * nodes(e)) * sizeof(float) + 255) / 256 * 256;
   L.off_part = 7 * L.vec;
-  L.off_sc = L.off_part + ((size_t)pf::krylov_partial_blocks() * sizeof(double) + 255) / 256 * 256;
+  // FP64 partials, shared in turn by the apply, the update and launch_dots
+  size_t np = (size_t)pf::krylov_partial_blocks();
+  np = std::max(np, (size_t)pf::cg_blocks());
+  np = std::max(np, (size_t)pf::elastic_apply_blocks((int)e->n[0], (int)e->n[1], (int)e->n[2]));
+  L.off_sc = L.off_part + (np * sizeof(double) + 255) / 256 * 256;
   L.total = L.off_sc + 256;
   return L;
 }
@@ -142,8 +149,24 @@ Layout layout(const pf_elastic* e) {
     if ((x) != cudaSuccess) return PF_ERR_CUDA;     \
   } while (0)
 
+// One CG iteration (slot = iteration parity): Ap = K p with the p.Ap partials,
+// sc[2] = p.Ap, x += alpha p, r -= alpha Ap with the new r.r partials,
+// sc[1 - slot] = r.r, p = r + beta p.
+cudaError_t cg_iteration(const Elastic3DArgs& A, int64_t n, int napply, float* x, float* r,
+                         float* p, float* Ap, double* part, double* sc, int slot,
+                         cudaStream_t s) {
+  cudaError_t e;
+  if ((e = pf::launch_elastic_apply(A, s)) != cudaSuccess) return e;
+  if ((e = pf::launch_sum_part(part, napply, sc + 2, s)) != cudaSuccess) return e;
+  if ((e = pf::launch_cg_xr(x, r, p, Ap, n, sc, slot, part, s)) != cudaSuccess) return e;
+  if ((e = pf::launch_sum_part(part, pf::cg_blocks(), sc + (1 - slot), s)) != cudaSuccess) return e;
+  return pf::launch_cg_p(r, p, n, sc, slot, s);
+}
+
 // K x = b on the free degrees of freedom (b's constrained entries are
-// ignored), from x = 0; vectors r, p, Ap are workspace.
+// ignored), from x = 0; vectors r, p, Ap are workspace.  Iterations run in
+// groups of kCheckEvery replayed from a CUDA graph (captured once per call on
+// a private stream), with a convergence check on the host after each group.
 pf_status cg(const pf_elastic* e, const Elastic3DArgs& base, const float* b, float* x, float* r,
              float* p, float* Ap, double* part, double* sc, double rtol, int max_iter,
              cudaStream_t s, pf_cg_stats* st) {
@@ -172,30 +195,69 @@ pf_status cg(const pf_elastic* e, const Elastic3DArgs& base, const float* b, flo
   Elastic3DArgs A = base;
   A.u = p;
   A.out = Ap;
-  int it = 0;
-  double rr = rr0;
-  while (it < max_iter) {
-    const int slot = it & 1;
-    EL_CUDA(pf::launch_elastic_apply(A, s));
-    EL_CUDA(pf::launch_dots(p, 0, 1, Ap, n, part, sc + 2, s));
-    EL_CUDA(pf::launch_cg_xr(x, r, p, Ap, n, sc, slot, s));
-    EL_CUDA(pf::launch_dots(r, 0, 1, r, n, part, sc + (1 - slot), s));
-    EL_CUDA(pf::launch_cg_p(r, p, n, sc, slot, s));
-    ++it;
-    if (it % kCheckEvery == 0 || it == max_iter) {
-      EL_CUDA(cudaMemcpyAsync(h_sc, sc, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
-      EL_CUDA(cudaStreamSynchronize(s));
-      rr = h_sc[it & 1];  // the slot the last iteration wrote
-      if (!isfinite(rr)) return PF_ERR_NONFINITE;
-      if (rr <= stop) break;
+  A.dot = part;
+  const int napply = pf::elastic_apply_blocks(A.nx, A.ny, A.nz);
+  // the graph of kCheckEvery iterations (even, so slots repeat per group)
+  cudaGraphExec_t exec = nullptr;
+  if (max_iter >= kCheckEvery) {
+    cudaStream_t cs = nullptr;
+    EL_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    cudaError_t le = cudaSuccess;
+    if (ce == cudaSuccess) {
+      for (int k = 0; k < kCheckEvery && le == cudaSuccess; ++k)
+        le = cg_iteration(A, n, napply, x, r, p, Ap, part, sc, k & 1, cs);
+      cudaGraph_t g = nullptr;
+      ce = cudaStreamEndCapture(cs, &g);
+      if (ce == cudaSuccess && le == cudaSuccess) ce = cudaGraphInstantiate(&exec, g, 0);
+      if (g) cudaGraphDestroy(g);
+    }
+    cudaStreamDestroy(cs);
+    if (ce != cudaSuccess || le != cudaSuccess) {
+      if (exec) cudaGraphExecDestroy(exec);
+      return PF_ERR_CUDA;
     }
   }
+  int it = 0;
+  double rr = rr0;
+  pf_status result = PF_ERR_NOT_CONVERGED;
+  while (it < max_iter) {
+    cudaError_t le;
+    if (exec && max_iter - it >= kCheckEvery) {
+      le = cudaGraphLaunch(exec, s);
+      it += kCheckEvery;
+    } else {
+      le = cg_iteration(A, n, napply, x, r, p, Ap, part, sc, it & 1, s);
+      ++it;
+    }
+    if (le != cudaSuccess) {
+      result = PF_ERR_CUDA;
+      break;
+    }
+    if (it % kCheckEvery == 0 || it == max_iter) {
+      if (cudaMemcpyAsync(h_sc, sc, 2 * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess) {
+        result = PF_ERR_CUDA;
+        break;
+      }
+      rr = h_sc[it & 1];  // the slot the last iteration wrote
+      if (!isfinite(rr)) {
+        result = PF_ERR_NONFINITE;
+        break;
+      }
+      if (rr <= stop) {
+        result = PF_OK;
+        break;
+      }
+    }
+  }
+  if (exec) cudaGraphExecDestroy(exec);
   if (st) {
     st->iterations = it;
-    st->converged = rr <= stop;
+    st->converged = result == PF_OK;
     st->final_residual = sqrt(rr);
   }
-  return rr <= stop ? PF_OK : PF_ERR_NOT_CONVERGED;
+  return result;
 }
 
 }  // namespace

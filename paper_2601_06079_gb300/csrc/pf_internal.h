@@ -169,6 +169,7 @@ cudaError_t launch_jvp3d(const Implicit3DArgs& a, cudaStream_t s);
 struct Elastic3DArgs {
   const float* u;
   float* out;
+  double* dot;  // optional: per-block FP64 partials of u . out (elastic_apply_blocks entries)
   int nx, ny, nz;
   int constrain;  // zero the rows of the symmetry-plane constraints
   float ke[24 * 24];
@@ -181,12 +182,16 @@ struct ElasticLoadArgs {
   int unit, constrain;
   float hx, hy, hz, ihx, ihy, ihz, wq, scale, l, a;
 };
+int elastic_apply_blocks(int nx, int ny, int nz);
+int cg_blocks();  // blocks (and r.r partials) of launch_cg_xr
 cudaError_t launch_elastic_apply(const Elastic3DArgs& a, cudaStream_t s);
+cudaError_t launch_sum_part(const double* part, int nb, double* out, cudaStream_t s);
 cudaError_t launch_elastic_load(const ElasticLoadArgs& a, float* f, cudaStream_t s);
 cudaError_t launch_elastic_constrain(float* v, int nx, int ny, int nz, cudaStream_t s);
-// CG updates with device scalars sc[0..1] = r.r (ping-pong by slot), sc[2] = p.Ap
+// CG updates with device scalars sc[0..1] = r.r (ping-pong by slot), sc[2] = p.Ap;
+// launch_cg_xr also leaves the new r.r as cg_blocks() FP64 partials in part
 cudaError_t launch_cg_xr(float* x, float* r, const float* p, const float* Ap, int64_t n,
-                         const double* sc, int slot, cudaStream_t s);
+                         const double* sc, int slot, double* part, cudaStream_t s);
 cudaError_t launch_cg_p(const float* r, float* p, int64_t n, const double* sc, int slot,
                         cudaStream_t s);
 
