@@ -4,14 +4,15 @@
 // fused conjugate-gradient updates.  Displacements are component-major FP32
 // planes u[c * N + node], c = x, y, z.
 //
-// K u is node-centric and needs no atomics: a thread sweeps a column of nodes
-// along z with the 3 x 3 x 3 neighbourhood of all three components in
-// registers (one new 3 x 3 plane, 27 loads coalesced along x, per node) and
-// applies
-//   interior nodes: the assembled 27-point stencil, 3 x 3 coefficients per
-//                   offset (243 FMA);
-//   boundary nodes: the element stiffness of each of its (up to 8) elements
-//                   that lie inside the mesh, row block of the node's corner.
+// K u is node-centric and needs no atomics, in two launches:
+//   interior nodes: a thread sweeps a column along z with the 3 x 3 x 3
+//                   neighbourhood of all three components in registers (one
+//                   new plane, 27 loads coalesced along x, per node) and
+//                   applies the assembled 27-point stencil, 3 x 3
+//                   coefficients per offset;
+//   boundary nodes: one thread per node applies the element stiffness of
+//                   each of its (up to 8) elements that lie inside the mesh,
+//                   row block of the node's corner.
 // Both coefficient tables come from the element stiffness of the uniform
 // box element in closed form (host, FP64) and travel as kernel parameters,
 // whose uniform reads feed the FMAs directly.  K annihilates translations, so
@@ -43,85 +44,187 @@ __device__ double block_sum(double v) {
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
-constexpr int kBX = 32, kBY = 4;  // (x, y) columns per block
-constexpr int kZChunk = 16;        // nodes per column and thread
+constexpr int kBX = 32, kBY = 4;  // (x, y) columns per interior block (kBX * kBY = kThreads)
+constexpr int kZChunk = 15;        // interior nodes per column and thread (a multiple of 3)
 
-// load the 3 x 3 (x, y) neighbourhood of plane z (clamped into the mesh)
-__device__ __forceinline__ void load_plane(const Elastic3DArgs& a, int64_t N, int x, int y, int z,
-                                           float p[9][3]) {
-  const int zz = clampi(z, 0, a.nz - 1);
+// 3 x 3 (x, y) neighbourhood of interior column (x, y) in plane z
+__device__ __forceinline__ void load_plane(const float* __restrict__ u, int64_t N, int64_t nx,
+                                           int64_t row0, float p[9][3]) {
+  // row0: index of node (x - 1, y - 1) in plane z
 #pragma unroll
-  for (int dy = -1; dy <= 1; ++dy) {
-    const int yy = clampi(y + dy, 0, a.ny - 1);
+  for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
-    for (int dx = -1; dx <= 1; ++dx) {
-      const int xx = clampi(x + dx, 0, a.nx - 1);
-      const int64_t g = ((int64_t)zz * a.ny + yy) * a.nx + xx;
+    for (int dx = 0; dx < 3; ++dx)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) p[(dy + 1) * 3 + (dx + 1)][c] = __ldg(a.u + c * N + g);
-    }
+      for (int c = 0; c < 3; ++c) p[dy * 3 + dx][c] = __ldg(u + c * N + row0 + dy * nx + dx);
+}
+
+// K u at an interior node from its three planes, on differences to the node
+__device__ __forceinline__ void interior_node(const Elastic3DArgs& a, const float (&pm)[9][3],
+                                              const float (&pc)[9][3], const float (&pp)[9][3],
+                                              float out[3]) {
+  out[0] = out[1] = out[2] = 0.0f;
+#pragma unroll
+  for (int o = 0; o < 27; ++o) {
+    if (o == 13) continue;
+    const float(&pl)[9][3] = o < 9 ? pm : (o < 18 ? pc : pp);
+    const int k = o % 9;
+    float d[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) d[j] = pl[k][j] - pc[4][j];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) out[i] = fmaf(a.ks[(o * 3 + i) * 3 + j], d[j], out[i]);
   }
 }
 
-// One thread per (x, y) column and chunk of kZChunk nodes along z: a window
-// of three planes of the 3 x 3 neighbourhood slides down z in registers, so
-// each node costs one plane of 27 loads instead of its 81 neighbours.
-//
-// With a.dot set, each block also writes the FP64 partial sum of u . Ku over
-// its nodes to a.dot[block] (fixed order: the CG step's p . Ap).
+// Interior nodes (1 <= x, y, z <= n - 2): one thread per (x, y) column and
+// kZChunk nodes along z.  Three planes of the 3 x 3 neighbourhood rotate
+// through registers (the loop is unrolled by 3, so the rotation is renaming),
+// and each node costs one plane of 27 loads at unclamped row addresses.
+// With kDot each block writes the FP64 partial of u . Ku over its nodes to
+// a.dot[block] (fixed order).
+#ifndef PF_EL_MINB
+#define PF_EL_MINB 4  // minimum resident interior blocks per SM asked of the register allocator
+#endif
+#ifndef PF_EL_UNROLL3
+#define PF_EL_UNROLL3 0  // 1: z loop unrolled by 3 (plane rotation by renaming, more registers)
+#endif
+
 template <bool kDot>
-__global__ void __launch_bounds__(kBX * kBY) k_elastic_apply(const Elastic3DArgs a) {
+__device__ __forceinline__ float interior_block(const Elastic3DArgs& a, int bx, int by, int bz) {
   const int64_t N = (int64_t)a.nx * a.ny * a.nz;
-  const int x = blockIdx.x * kBX + threadIdx.x, y = blockIdx.y * kBY + threadIdx.y;
+  const int64_t nx = a.nx, plane = (int64_t)a.nx * a.ny;
+  const int x = 1 + bx * kBX + (threadIdx.x % kBX), y = 1 + by * kBY + (threadIdx.x / kBX);
   float dot = 0.0f;  // this thread's at most kZChunk nodes; blocks sum in FP64
-  if (x < a.nx && y < a.ny) {
-  const int z0 = blockIdx.z * kZChunk, z1 = min(z0 + kZChunk, a.nz);
-  float pm[9][3], pc[9][3], pp[9][3];  // planes z - 1, z, z + 1 (rows beyond the mesh clamped)
-  load_plane(a, N, x, y, z0 - 1, pm);
-  load_plane(a, N, x, y, z0, pc);
-  const bool xy_in = x > 0 && y > 0 && x < a.nx - 1 && y < a.ny - 1;
-  for (int z = z0; z < z1; ++z) {
-    load_plane(a, N, x, y, z + 1, pp);
-    // neighbourhood o = (dz+1)*9 + (dy+1)*3 + (dx+1) as differences to the
-    // node's own values (o = 13 is the node itself)
-    float v[27][3];
-#pragma unroll
-    for (int k = 0; k < 9; ++k)
+  if (x < a.nx - 1 && y < a.ny - 1) {
+    const int z0 = 1 + bz * kZChunk, z1 = min(z0 + kZChunk, a.nz - 1);
+    const int64_t col0 = (int64_t)(y - 1) * nx + (x - 1);
+    float P0[9][3], P1[9][3], P2[9][3];
+    load_plane(a.u, N, nx, (z0 - 1) * plane + col0, P0);
+    load_plane(a.u, N, nx, z0 * plane + col0, P1);
+    auto node = [&](int z, const float(&pm)[9][3], const float(&pc)[9][3],
+                    const float(&pp)[9][3]) {
+      float out[3];
+      interior_node(a, pm, pc, pp, out);
+      const int64_t g = z * plane + col0 + nx + 1;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        v[k][c] = pm[k][c] - pc[4][c];
-        v[9 + k][c] = pc[k][c] - pc[4][c];
-        v[18 + k][c] = pp[k][c] - pc[4][c];
+        a.out[c * N + g] = out[c];
+        if (kDot) dot = fmaf(pc[4][c], out[c], dot);
+      }
+    };
+#if PF_EL_UNROLL3
+    for (int z = z0; z < z1; z += 3) {
+      load_plane(a.u, N, nx, (z + 1) * plane + col0, P2);
+      node(z, P0, P1, P2);
+      if (z + 1 >= z1) break;
+      load_plane(a.u, N, nx, (z + 2) * plane + col0, P0);
+      node(z + 1, P1, P2, P0);
+      if (z + 2 >= z1) break;
+      load_plane(a.u, N, nx, (z + 3) * plane + col0, P1);
+      node(z + 2, P2, P0, P1);
+    }
+#else
+#pragma unroll 1
+    for (int z = z0; z < z1; ++z) {
+      load_plane(a.u, N, nx, (z + 1) * plane + col0, P2);
+      node(z, P0, P1, P2);
+#pragma unroll
+      for (int k = 0; k < 9; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          P0[k][c] = P1[k][c];
+          P1[k][c] = P2[k][c];
+        }
+    }
+#endif
+  }
+  return dot;
+}
+
+// boundary node number i -> (x, y, z): the two z faces, then the two y faces
+// without their z rows, then the two x faces without their y and z rows
+__device__ __forceinline__ void boundary_node(int64_t i, int nx, int ny, int nz, int& x, int& y,
+                                              int& z) {
+  const int64_t fz = (int64_t)nx * ny, fy = (int64_t)nx * (nz - 2);
+  if (i < 2 * fz) {
+    z = i < fz ? 0 : nz - 1;
+    const int64_t r = i % fz;
+    y = (int)(r / nx);
+    x = (int)(r % nx);
+  } else if ((i -= 2 * fz) < 2 * fy) {
+    y = i < fy ? 0 : ny - 1;
+    const int64_t r = i % fy;
+    z = 1 + (int)(r / nx);
+    x = (int)(r % nx);
+  } else {
+    i -= 2 * fy;
+    const int64_t fx = (int64_t)(ny - 2) * (nz - 2);
+    x = i < fx ? 0 : nx - 1;
+    const int64_t r = i % fx;
+    z = 1 + (int)(r / (ny - 2));
+    y = 1 + (int)(r % (ny - 2));
+  }
+}
+
+__host__ __device__ int64_t boundary_count(int nx, int ny, int nz) {
+  return 2 * (int64_t)nx * ny + 2 * (int64_t)nx * (nz - 2) + 2 * (int64_t)(ny - 2) * (nz - 2);
+}
+
+// Boundary nodes: one thread per node, its 3 x 3 x 3 neighbourhood (clamped
+// into the mesh) as differences, and the element-stiffness row blocks of the
+// (up to 8) elements inside the mesh; then the symmetry-plane constraints.
+template <bool kDot>
+__device__ __forceinline__ float boundary_block(const Elastic3DArgs& a, int blk) {
+  const int64_t N = (int64_t)a.nx * a.ny * a.nz;
+  const int64_t nb = boundary_count(a.nx, a.ny, a.nz);
+  const int64_t i = (int64_t)blk * kThreads + threadIdx.x;
+  float dot = 0.0f;
+  if (i < nb) {
+    int x, y, z;
+    boundary_node(i, a.nx, a.ny, a.nz, x, y, z);
+    float v[27][3];
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz) {
+      const int zz = clampi(z + dz, 0, a.nz - 1);
+#pragma unroll
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int yy = clampi(y + dy, 0, a.ny - 1);
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int xx = clampi(x + dx, 0, a.nx - 1);
+          const int64_t g = ((int64_t)zz * a.ny + yy) * a.nx + xx;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) v[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)][c] = __ldg(a.u + c * N + g);
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 0; o < 27; ++o)
+      if (o != 13) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v[o][c] -= v[13][c];
       }
     float out[3] = {0.0f, 0.0f, 0.0f};
-    if (xy_in && z > 0 && z < a.nz - 1) {
+    // element with lower corner (x - ox, y - oy, z - oz): this node is its
+    // corner a = ox + 2 oy + 4 oz; its corner b is at offset (b - a) per axis
 #pragma unroll
-      for (int o = 0; o < 27; ++o)
-        if (o != 13) {
+    for (int oct = 0; oct < 8; ++oct) {
+      const int ox = oct & 1, oy = (oct >> 1) & 1, oz = oct >> 2;
+      const int ex = x - ox, ey = y - oy, ez = z - oz;
+      if (ex < 0 || ey < 0 || ez < 0 || ex > a.nx - 2 || ey > a.ny - 2 || ez > a.nz - 2) continue;
 #pragma unroll
-          for (int i = 0; i < 3; ++i)
+      for (int b = 0; b < 8; ++b) {
+        const int bx = b & 1, by = (b >> 1) & 1, bz = b >> 2;
+        const int o = (bz - oz + 1) * 9 + (by - oy + 1) * 3 + (bx - ox + 1);
+        if (o == 13) continue;  // the node itself: a zero difference
 #pragma unroll
-            for (int j = 0; j < 3; ++j) out[i] = fmaf(a.ks[(o * 3 + i) * 3 + j], v[o][j], out[i]);
-        }
-    } else {
-      // element with lower corner (x - ox, y - oy, z - oz): this node is its
-      // corner a = ox + 2 oy + 4 oz; its corner b is at offset (b - a) per axis
+        for (int ii = 0; ii < 3; ++ii)
 #pragma unroll
-      for (int oct = 0; oct < 8; ++oct) {
-        const int ox = oct & 1, oy = (oct >> 1) & 1, oz = oct >> 2;
-        const int ex = x - ox, ey = y - oy, ez = z - oz;
-        if (ex < 0 || ey < 0 || ez < 0 || ex > a.nx - 2 || ey > a.ny - 2 || ez > a.nz - 2) continue;
-#pragma unroll
-        for (int b = 0; b < 8; ++b) {
-          const int bx = b & 1, by = (b >> 1) & 1, bz = b >> 2;
-          const int o = (bz - oz + 1) * 9 + (by - oy + 1) * 3 + (bx - ox + 1);
-          if (o == 13) continue;  // the node itself: a zero difference
-#pragma unroll
-          for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = 0; j < 3; ++j)
-              out[i] = fmaf(a.ke[(oct * 3 + i) * 24 + b * 3 + j], v[o][j], out[i]);
-        }
+          for (int j = 0; j < 3; ++j)
+            out[ii] = fmaf(a.ke[(oct * 3 + ii) * 24 + b * 3 + j], v[o][j], out[ii]);
       }
     }
     if (a.constrain) {  // symmetry planes: u_x on x = 0, u_y on y = 0, u_z on z = 0
@@ -129,25 +232,32 @@ __global__ void __launch_bounds__(kBX * kBY) k_elastic_apply(const Elastic3DArgs
       if (y == 0) out[1] = 0.0f;
       if (z == 0) out[2] = 0.0f;
     }
-    const int64_t node = ((int64_t)z * a.ny + y) * a.nx + x;
+    const int64_t g = ((int64_t)z * a.ny + y) * a.nx + x;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      a.out[c * N + node] = out[c];
-      if (kDot) dot = fmaf(pc[4][c], out[c], dot);
+      a.out[c * N + g] = out[c];
+      if (kDot) dot = fmaf(v[13][c], out[c], dot);
     }
-#pragma unroll
-    for (int k = 0; k < 9; ++k)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        pm[k][c] = pc[k][c];
-        pc[k][c] = pp[k][c];
-      }
   }
-  }
+  return dot;
+}
+
+// One launch for both: blocks [0, ni) are interior column blocks (gx x gy x gz
+// of them), the rest boundary blocks, so the boundary work fills the tail of
+// the interior wave.  With kDot each block writes the FP64 partial of u . Ku
+// over its nodes to a.dot[block] (fixed order).
+template <bool kDot>
+__global__ void __launch_bounds__(kThreads, PF_EL_MINB) k_elastic_apply(const Elastic3DArgs a, int gx,
+                                                                       int gy, int ni) {
+  const int b = blockIdx.x;
+  float dot;
+  if (b < ni)
+    dot = interior_block<kDot>(a, b % gx, (b / gx) % gy, b / (gx * gy));
+  else
+    dot = boundary_block<kDot>(a, b - ni);
   if (kDot) {
     const double s = block_sum((double)dot);
-    if (threadIdx.x == 0 && threadIdx.y == 0)
-      a.dot[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = s;
+    if (threadIdx.x == 0) a.dot[b] = s;
   }
 }
 
@@ -247,20 +357,31 @@ int blocks_for(int64_t n) {
   return (int)(b < 152 * 8 ? b : 152 * 8);
 }
 
+dim3 interior_grid(int nx, int ny, int nz) {
+  if (nx < 3 || ny < 3 || nz < 3) return dim3(0, 0, 0);
+  return dim3((nx - 2 + kBX - 1) / kBX, (ny - 2 + kBY - 1) / kBY, (nz - 2 + kZChunk - 1) / kZChunk);
+}
+
+int boundary_blocks(int nx, int ny, int nz) {
+  return (int)((boundary_count(nx, ny, nz) + kThreads - 1) / kThreads);
+}
+
 }  // namespace
 
 int elastic_apply_blocks(int nx, int ny, int nz) {
-  return ((nx + kBX - 1) / kBX) * ((ny + kBY - 1) / kBY) * ((nz + kZChunk - 1) / kZChunk);
+  const dim3 g = interior_grid(nx, ny, nz);
+  return (int)(g.x * g.y * g.z) + boundary_blocks(nx, ny, nz);
 }
 
 int cg_blocks() { return 152 * 8; }
 
 cudaError_t launch_elastic_apply(const Elastic3DArgs& a, cudaStream_t s) {
-  const dim3 grid((a.nx + kBX - 1) / kBX, (a.ny + kBY - 1) / kBY, (a.nz + kZChunk - 1) / kZChunk);
+  const dim3 gi = interior_grid(a.nx, a.ny, a.nz);
+  const int ni = (int)(gi.x * gi.y * gi.z), nb = boundary_blocks(a.nx, a.ny, a.nz);
   if (a.dot)
-    k_elastic_apply<true><<<grid, dim3(kBX, kBY), 0, s>>>(a);
+    k_elastic_apply<true><<<ni + nb, kThreads, 0, s>>>(a, (int)gi.x, (int)gi.y, ni);
   else
-    k_elastic_apply<false><<<grid, dim3(kBX, kBY), 0, s>>>(a);
+    k_elastic_apply<false><<<ni + nb, kThreads, 0, s>>>(a, (int)gi.x, (int)gi.y, ni);
   return cudaGetLastError();
 }
 
