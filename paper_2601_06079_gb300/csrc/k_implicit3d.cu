@@ -14,9 +14,21 @@
 //   phase 1: per element and Gauss point, S2 = sum_f U_f^2 (and T =
 //            sum_f U_f v_f for the JVP), the only couplings between fields;
 //   phase 2: per field, the Gauss values (trilinear, sum-factorised), the
-//            pointwise f' or H v, the weights back to the 8 corners into a
-//            per-element buffer, then a node-centric gather of the 8 element
-//            contributions plus the assembled 27-point stiffness stencil.
+//            pointwise f' or H v, and the gradient term kappa grad w . grad N_a
+//            (w = v for the JVP, U for the residual), all weighted back to the
+//            8 corners into a per-element buffer; then a node-centric gather
+//            of the 8 element contributions and the mass term.
+// The gradient term needs no extra loads: the three passes of the
+// sum-factorised interpolation already form the element's differences along
+// x, y and z, which (interpolated in the other directions) are the Gauss-point
+// derivatives; their weights back enter the matching passes of the projection.
+// 2x2x2 Gauss integrates the Q1 stiffness exactly, so this is the assembled
+// 27-point stencil, evaluated element by element on differences.
+// Fields travel in pairs: shared memory holds (field 2p, field 2p+1) side by
+// side (a zero field pads an odd count), one 64-bit load fetches both, and
+// every interpolation, pointwise term, projection and stencil runs on packed
+// FP32 pairs with the f32x2 instructions of sm_100+, halving both the
+// shared-memory loads and the FP32 instructions of the per-field work.
 // No atomics: the gather order is fixed, so results are bitwise repeatable.
 #include "pf_internal.h"
 
@@ -29,9 +41,48 @@ constexpr int kE = kT + 1;            // elements per edge touching the tile
 constexpr int kNodes = kN * kN * kN;  // 1000
 constexpr int kElems = kE * kE * kE;  // 729
 #ifndef PF_IMP_THREADS
-#define PF_IMP_THREADS 1024
+#define PF_IMP_THREADS 768
 #endif
 constexpr int kThreads = PF_IMP_THREADS;
+
+typedef unsigned long long u64;  // packed FP32 pair: low half = the even field
+
+__device__ __forceinline__ u64 pk(float lo, float hi) {
+  u64 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float plo(u64 v) {
+  float l, h;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(l), "=f"(h) : "l"(v));
+  return l;
+}
+__device__ __forceinline__ float phi(u64 v) {
+  float l, h;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(l), "=f"(h) : "l"(v));
+  return h;
+}
+__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
+  u64 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ u64 add2(u64 a, u64 b) {
+  u64 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ u64 sub2(u64 a, u64 b) {
+  u64 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ u64 mul2(u64 a, u64 b) {
+  u64 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ u64 bc(float v) { return pk(v, v); }
 
 __device__ __forceinline__ int mirror(int k, int n) {
   const int p = 2 * (n - 1);
@@ -41,22 +92,22 @@ __device__ __forceinline__ int mirror(int k, int n) {
 }
 
 // values at the two Gauss points of a segment from its end values
-__device__ __forceinline__ void interp1(float a, float b, float& lo, float& hi) {
-  const float d = b - a;
-  lo = fmaf(kGLo, d, a);
-  hi = fmaf(kGHi, d, a);
+__device__ __forceinline__ void interp1(u64 a, u64 b, u64& lo, u64& hi) {
+  const u64 d = sub2(b, a);
+  lo = fma2(bc(kGLo), d, a);
+  hi = fma2(bc(kGHi), d, a);
 }
 
 // weights back: contributions of the two Gauss values to the segment's ends
-__device__ __forceinline__ void project1(float lo, float hi, float& a, float& b) {
-  const float d = hi - lo;
-  a = fmaf(kGLo, d, lo);      // g_hi lo + g_lo hi
-  b = fmaf(-kGLo, d, hi);     // g_lo lo + g_hi hi
+__device__ __forceinline__ void project1(u64 lo, u64 hi, u64& a, u64& b) {
+  const u64 d = sub2(hi, lo);
+  a = fma2(bc(kGLo), d, lo);   // g_hi lo + g_lo hi
+  b = fma2(bc(-kGLo), d, hi);  // g_lo lo + g_hi hi
 }
 
 // 8 corner values c[z][y][x] -> 8 Gauss values q[z][y][x] (tensor product)
-__device__ __forceinline__ void interp3(const float c[8], float q[8]) {
-  float t[8], u[8];
+__device__ __forceinline__ void interp3(const u64 c[8], u64 q[8]) {
+  u64 t[8], u[8];
 #pragma unroll
   for (int zy = 0; zy < 4; ++zy) interp1(c[2 * zy], c[2 * zy + 1], t[2 * zy], t[2 * zy + 1]);
 #pragma unroll
@@ -67,31 +118,101 @@ __device__ __forceinline__ void interp3(const float c[8], float q[8]) {
   for (int yx = 0; yx < 4; ++yx) interp1(u[yx], u[4 + yx], q[yx], q[4 + yx]);
 }
 
-// transpose of interp3: Gauss values -> corner contributions
-__device__ __forceinline__ void project3(const float q[8], float c[8]) {
-  float t[8], u[8];
+// interp3 plus the Gauss-point derivatives in local coordinates (one unit
+// per element edge): gx[qz][qy] = d/dx (constant along x), gy[qz][qx],
+// gz[qy][qx], each formed from the differences the passes already take
+__device__ __forceinline__ void interp3_grad(const u64 c[8], u64 q[8], u64 gx[4], u64 gy[4],
+                                             u64 gz[4]) {
+  u64 t[8], u[8], d1[4], d2[4];
 #pragma unroll
-  for (int yx = 0; yx < 4; ++yx) project1(q[yx], q[4 + yx], t[yx], t[4 + yx]);
+  for (int zy = 0; zy < 4; ++zy) {  // x pass: d1[zy] = x-difference on edge (y, z)
+    d1[zy] = sub2(c[2 * zy + 1], c[2 * zy]);
+    t[2 * zy] = fma2(bc(kGLo), d1[zy], c[2 * zy]);
+    t[2 * zy + 1] = fma2(bc(kGHi), d1[zy], c[2 * zy]);
+  }
 #pragma unroll
   for (int z = 0; z < 2; ++z)
 #pragma unroll
-    for (int x = 0; x < 2; ++x) project1(t[4 * z + x], t[4 * z + 2 + x], u[4 * z + x], u[4 * z + 2 + x]);
+    for (int x = 0; x < 2; ++x) {  // y pass: d2[2z + x] = y-difference at (qx = x, z)
+      const u64 a = t[4 * z + x];
+      d2[2 * z + x] = sub2(t[4 * z + 2 + x], a);
+      u[4 * z + x] = fma2(bc(kGLo), d2[2 * z + x], a);
+      u[4 * z + 2 + x] = fma2(bc(kGHi), d2[2 * z + x], a);
+    }
 #pragma unroll
-  for (int zy = 0; zy < 4; ++zy) project1(u[2 * zy], u[2 * zy + 1], c[2 * zy], c[2 * zy + 1]);
+  for (int yx = 0; yx < 4; ++yx) {  // z pass: its differences are d/dz at (qy, qx)
+    gz[yx] = sub2(u[4 + yx], u[yx]);
+    q[yx] = fma2(bc(kGLo), gz[yx], u[yx]);
+    q[4 + yx] = fma2(bc(kGHi), gz[yx], u[yx]);
+  }
+  // d/dy at (qz, qx): d2 interpolated along z
+#pragma unroll
+  for (int x = 0; x < 2; ++x) interp1(d2[x], d2[2 + x], gy[x], gy[2 + x]);
+  // d/dx at (qz, qy): d1[y + 2z] interpolated along y, then z
+  u64 e[4];
+#pragma unroll
+  for (int z = 0; z < 2; ++z) interp1(d1[2 * z], d1[2 * z + 1], e[2 * z], e[2 * z + 1]);
+#pragma unroll
+  for (int y = 0; y < 2; ++y) interp1(e[y], e[2 + y], gx[y], gx[2 + y]);
+}
+
+// transpose of interp3 (Gauss values -> corner contributions) plus the
+// gradient term sum_q grad w . grad N_a with per-axis weights k[d] = 2 kappa / h_d^2
+// (the factor 2 sums the two Gauss points along the derivative's own axis,
+// where the derivative is constant).  Each derivative enters the projection
+// after the pass along its own axis, with the sign of N_a' on that axis.
+__device__ __forceinline__ void project3_grad(const u64 q[8], const u64 gx[4], const u64 gy[4],
+                                              const u64 gz[4], const float k[3], u64 c[8]) {
+  u64 t[8], u[8];
+#pragma unroll
+  for (int yx = 0; yx < 4; ++yx) {  // z pass; t[4 az + yx]
+    project1(q[yx], q[4 + yx], t[yx], t[4 + yx]);
+    t[yx] = fma2(bc(-k[2]), gz[yx], t[yx]);
+    t[4 + yx] = fma2(bc(k[2]), gz[yx], t[4 + yx]);
+  }
+  u64 py[4];  // d/dy weighted back along z: py[2 az + qx]
+#pragma unroll
+  for (int x = 0; x < 2; ++x) project1(gy[x], gy[2 + x], py[x], py[2 + x]);
+#pragma unroll
+  for (int z = 0; z < 2; ++z)
+#pragma unroll
+    for (int x = 0; x < 2; ++x) {  // y pass; u[4 az + 2 ay + qx]
+      project1(t[4 * z + x], t[4 * z + 2 + x], u[4 * z + x], u[4 * z + 2 + x]);
+      u[4 * z + x] = fma2(bc(-k[1]), py[2 * z + x], u[4 * z + x]);
+      u[4 * z + 2 + x] = fma2(bc(k[1]), py[2 * z + x], u[4 * z + 2 + x]);
+    }
+  u64 e[4], px[4];  // d/dx weighted back along y, then z: px[2 az + ay]
+#pragma unroll
+  for (int z = 0; z < 2; ++z) project1(gx[2 * z], gx[2 * z + 1], e[2 * z], e[2 * z + 1]);
+#pragma unroll
+  for (int y = 0; y < 2; ++y) project1(e[y], e[2 + y], px[y], px[2 + y]);
+#pragma unroll
+  for (int zy = 0; zy < 4; ++zy) {  // x pass; c[2 zy + ax]
+    project1(u[2 * zy], u[2 * zy + 1], c[2 * zy], c[2 * zy + 1]);
+    c[2 * zy] = fma2(bc(-k[0]), px[zy], c[2 * zy]);
+    c[2 * zy + 1] = fma2(bc(k[0]), px[zy], c[2 * zy + 1]);
+  }
 }
 
 __device__ __forceinline__ int nidx(int x, int y, int z) { return (z * kN + y) * kN + x; }
 
+// the 8 corners of element base (staged-node index of its lower corner)
+__device__ __forceinline__ void corners(const u64* P, int base, u64 c[8]) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) c[k] = P[base + ((k >> 2) * kN + ((k >> 1) & 1)) * kN + (k & 1)];
+}
+
 template <int NF, bool kJVP>
 __global__ void __launch_bounds__(kThreads) k_implicit3d(const Implicit3DArgs a) {
-  extern __shared__ float smem[];
-  float* sU = smem;                          // [NF][kNodes]
-  float* sW = sU + NF * kNodes;              // v (JVP) or U^n (residual)
+  constexpr int NP = (NF + 1) / 2;  // field pairs
+  extern __shared__ u64 smem[];
+  u64* sU = smem;                                // [NP][kNodes] (field 2p, 2p+1)
+  u64* sW = sU + NP * kNodes;                    // v (JVP) or U^n (residual)
+  u64* sE = sW + NP * kNodes;                    // [8][kElems] corner contributions of a pair
   // per-element values are stored [8][kElems] (Gauss point or corner major), so
   // that consecutive threads (consecutive elements) hit consecutive banks
-  float* sS = sW + NF * kNodes;              // [8][kElems] S2 at Gauss points
-  float* sTq = sS + kElems * 8;              // [8][kElems] T (JVP only)
-  float* sE = sTq + (kJVP ? kElems * 8 : 0); // [8][kElems] corner contributions of one field
+  float* sS = reinterpret_cast<float*>(sE + 8 * kElems);  // [8][kElems] S2 at Gauss points
+  float* sTq = sS + kElems * 8;                            // [8][kElems] T (JVP only)
 
   const int tiles_x = (a.nx + kT - 1) / kT, tiles_y = (a.ny + kT - 1) / kT;
   const int tile = blockIdx.x;
@@ -99,16 +220,17 @@ __global__ void __launch_bounds__(kThreads) k_implicit3d(const Implicit3DArgs a)
             z0 = (tile / (tiles_x * tiles_y)) * kT;
   const int64_t N = (int64_t)a.nx * a.ny * a.nz;
 
-  // stage U and v / U^n with mirror images beyond the mesh
+  // stage U and v / U^n with mirror images beyond the mesh, fields in pairs
   for (int i = threadIdx.x; i < kNodes; i += kThreads) {
     const int lx = i % kN, ly = (i / kN) % kN, lz = i / (kN * kN);
     const int gx = mirror(x0 - 1 + lx, a.nx), gy = mirror(y0 - 1 + ly, a.ny),
               gz = mirror(z0 - 1 + lz, a.nz);
     const int64_t g = ((int64_t)gz * a.ny + gy) * a.nx + gx;
 #pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      sU[f * kNodes + i] = a.U[f * N + g];
-      sW[f * kNodes + i] = a.W[f * N + g];
+    for (int p = 0; p < NP; ++p) {
+      const int f0 = 2 * p, f1 = 2 * p + 1;
+      sU[p * kNodes + i] = pk(a.U[f0 * N + g], f1 < NF ? a.U[f1 * N + g] : 0.0f);
+      sW[p * kNodes + i] = pk(a.W[f0 * N + g], f1 < NF ? a.W[f1 * N + g] : 0.0f);
     }
   }
   __syncthreads();
@@ -117,108 +239,101 @@ __global__ void __launch_bounds__(kThreads) k_implicit3d(const Implicit3DArgs a)
   for (int e = threadIdx.x; e < kElems; e += kThreads) {
     const int ex = e % kE, ey = (e / kE) % kE, ez = e / (kE * kE);
     const int base = nidx(ex, ey, ez);
-    float S2[8], T[8];
+    u64 S2[8], T[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) S2[q] = T[q] = 0.0f;
+    for (int q = 0; q < 8; ++q) S2[q] = T[q] = 0;
 #pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      float c[8], uq[8];
-#pragma unroll
-      for (int k = 0; k < 8; ++k)
-        c[k] = sU[f * kNodes + base + ((k >> 2) * kN + ((k >> 1) & 1)) * kN + (k & 1)];
+    for (int p = 0; p < NP; ++p) {
+      u64 c[8], uq[8];
+      corners(sU + p * kNodes, base, c);
       interp3(c, uq);
       if (kJVP) {
-        float vq[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-          c[k] = sW[f * kNodes + base + ((k >> 2) * kN + ((k >> 1) & 1)) * kN + (k & 1)];
+        u64 vq[8];
+        corners(sW + p * kNodes, base, c);
         interp3(c, vq);
 #pragma unroll
-        for (int q = 0; q < 8; ++q) T[q] = fmaf(uq[q], vq[q], T[q]);
+        for (int q = 0; q < 8; ++q) T[q] = fma2(uq[q], vq[q], T[q]);
       }
 #pragma unroll
-      for (int q = 0; q < 8; ++q) S2[q] = fmaf(uq[q], uq[q], S2[q]);
+      for (int q = 0; q < 8; ++q) S2[q] = fma2(uq[q], uq[q], S2[q]);
     }
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      sS[q * kElems + e] = S2[q];
-      if (kJVP) sTq[q * kElems + e] = T[q];
+      sS[q * kElems + e] = plo(S2[q]) + phi(S2[q]);
+      if (kJVP) sTq[q * kElems + e] = plo(T[q]) + phi(T[q]);
     }
   }
   __syncthreads();
 
-  // phase 2: one field at a time
-  for (int f = 0; f < NF; ++f) {
-    const float* Uf = sU + f * kNodes;
-    const float* Wf = sW + f * kNodes;
+  // phase 2: one field pair at a time
+  for (int p = 0; p < NP; ++p) {
+    const u64* Up = sU + p * kNodes;
+    const u64* Wp = sW + p * kNodes;
     for (int e = threadIdx.x; e < kElems; e += kThreads) {
       const int ex = e % kE, ey = (e / kE) % kE, ez = e / (kE * kE);
       const int base = nidx(ex, ey, ez);
-      float c[8], uq[8], vq[8], hq[8], out[8];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) c[k] = Uf[base + ((k >> 2) * kN + ((k >> 1) & 1)) * kN + (k & 1)];
-      interp3(c, uq);
+      u64 c[8], uq[8], vq[8], hq[8], out[8], gx[4], gy[4], gz[4];
+      corners(Up, base, c);
+      // the gradient term acts on v (JVP) or on U (residual)
       if (kJVP) {
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-          c[k] = Wf[base + ((k >> 2) * kN + ((k >> 1) & 1)) * kN + (k & 1)];
-        interp3(c, vq);
+        interp3(c, uq);
+        corners(Wp, base, c);
+        interp3_grad(c, vq, gx, gy, gz);
+      } else {
+        interp3_grad(c, uq, gx, gy, gz);
       }
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        const float u = uq[q], s2 = sS[q * kElems + e];
+        const u64 u = uq[q], uu = mul2(u, u);
         if (a.double_well) {
           // f = W u^2 (1-u)^2:  f' = 2W u (1-u)(1-2u),  f'' = 2W (1 - 6u + 6u^2)
-          hq[q] = kJVP ? a.dw2 * fmaf(6.0f * u, u - 1.0f, 1.0f) * vq[q]
-                       : a.dw2 * u * (1.0f - u) * (1.0f - 2.0f * u);
+          if (kJVP) {
+            const u64 f2 = fma2(bc(6.0f), sub2(uu, u), bc(1.0f));
+            hq[q] = mul2(mul2(bc(a.dw2), f2), vq[q]);
+          } else {
+            const u64 om = sub2(bc(1.0f), u);                  // 1 - u
+            const u64 o2 = fma2(bc(-2.0f), u, bc(1.0f));       // 1 - 2u
+            hq[q] = mul2(mul2(bc(a.dw2), u), mul2(om, o2));
+          }
         } else {
           // Fan-Chen: f'_f = u (-a + 2g S2 + (b - 2g) u^2)
           //           (H v)_f = (-a + 2g S2 + (3b - 6g) u^2) v_f + 4g u T
-          const float base_c = fmaf(a.two_gamma, s2, -a.alpha);
-          hq[q] = kJVP ? fmaf(fmaf(a.c3b6g, u * u, base_c), vq[q],
-                              a.four_gamma * u * sTq[q * kElems + e])
-                       : u * fmaf(a.cb2g, u * u, base_c);
+          const u64 base_c = bc(fmaf(a.two_gamma, sS[q * kElems + e], -a.alpha));
+          hq[q] = kJVP ? fma2(fma2(bc(a.c3b6g), uu, base_c), vq[q],
+                              mul2(bc(a.four_gamma * sTq[q * kElems + e]), u))
+                       : mul2(u, fma2(bc(a.cb2g), uu, base_c));
         }
       }
-      project3(hq, out);
+      project3_grad(hq, gx, gy, gz, a.kg, out);
 #pragma unroll
       for (int k = 0; k < 8; ++k) sE[k * kElems + e] = out[k];
     }
     __syncthreads();
-    // node gather: 8 elements around the node, stiffness stencil, mass term
+    // node gather: 8 elements around the node, mass term
     for (int i = threadIdx.x; i < kT * kT * kT; i += kThreads) {
       const int lx = 1 + i % kT, ly = 1 + (i / kT) % kT, lz = 1 + i / (kT * kT);
       const int gx = x0 + lx - 1, gy = y0 + ly - 1, gz = z0 + lz - 1;
       if (gx >= a.nx || gy >= a.ny || gz >= a.nz) continue;
-      float acc = 0.0f;
+      u64 acc = sE[(lz * kE + ly) * kE + lx];  // k = 0
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {  // element with corner k at this node
+      for (int k = 1; k < 8; ++k) {  // element with corner k at this node
         const int ex = lx - (k & 1), ey = ly - ((k >> 1) & 1), ez = lz - (k >> 2);
-        acc += sE[k * kElems + (ez * kE + ey) * kE + ex];
+        acc = add2(acc, sE[k * kElems + (ez * kE + ey) * kE + ex]);
       }
-      const float* V = kJVP ? Wf : Uf;  // the stiffness acts on v (JVP) or U (residual)
       const int c0 = nidx(lx, ly, lz);
-      float ks = a.kc[0] * V[c0];
-#pragma unroll
-      for (int dz = -1; dz <= 1; ++dz)
-#pragma unroll
-        for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-          for (int dx = -1; dx <= 1; ++dx) {
-            const int cls = (dx != 0) + 2 * (dy != 0) + 4 * (dz != 0);
-            if (cls == 0) continue;
-            ks = fmaf(a.kc[cls], V[c0 + (dz * kN + dy) * kN + dx], ks);
-          }
-      // G = (u - u^n)/dt + L (F/m + kappa K u / m)   or   v/dt + L (H v / m + kappa K v / m)
-      const float own = kJVP ? Wf[c0] : (Uf[c0] - Wf[c0]);
-      float g = fmaf(own, a.inv_dt, a.mob * (0.125f * acc + ks));
+      // G = (u - u^n)/dt + L (F + kappa K u) / m   or   v/dt + L (H v + kappa K v) / m,
+      // the element sums carrying weight |cell|/8 over the interior mass |cell|
+      const u64 own = kJVP ? Wp[c0] : sub2(Up[c0], Wp[c0]);
+      u64 g = fma2(own, bc(a.inv_dt), mul2(bc(0.125f * a.mob), acc));
       if (a.unscaled) {
         const float wx = (gx == 0 || gx == a.nx - 1) ? 0.5f : 1.0f;
         const float wy = (gy == 0 || gy == a.ny - 1) ? 0.5f : 1.0f;
         const float wz = (gz == 0 || gz == a.nz - 1) ? 0.5f : 1.0f;
-        g *= a.cell * wx * wy * wz;
+        g = mul2(g, bc(a.cell * wx * wy * wz));
       }
-      a.out[f * N + ((int64_t)gz * a.ny + gy) * a.nx + gx] = g;
+      const int64_t o = ((int64_t)gz * a.ny + gy) * a.nx + gx;
+      a.out[(2 * p) * N + o] = plo(g);
+      if (2 * p + 1 < NF) a.out[(2 * p + 1) * N + o] = phi(g);
     }
     __syncthreads();
   }
@@ -226,8 +341,9 @@ __global__ void __launch_bounds__(kThreads) k_implicit3d(const Implicit3DArgs a)
 
 template <int NF, bool kJVP>
 cudaError_t launch_nf(const Implicit3DArgs& a, cudaStream_t s) {
-  const size_t smem =
-      sizeof(float) * (2 * NF * kNodes + kElems * 8 * (kJVP ? 3 : 2));
+  constexpr int NP = (NF + 1) / 2;
+  const size_t smem = sizeof(u64) * (2 * NP * kNodes + 8 * kElems) +
+                      sizeof(float) * kElems * 8 * (kJVP ? 2 : 1);
   static bool configured[2] = {false, false};
   if (!configured[kJVP]) {
     cudaError_t e = cudaFuncSetAttribute(k_implicit3d<NF, kJVP>,

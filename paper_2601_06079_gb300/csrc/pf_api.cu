@@ -158,24 +158,6 @@ pf::Stencil2D stiffness2d(double hx, double hy, double scale) {
   return s;
 }
 
-// 27-point Q1 stiffness stencil of a uniform 3-D grid by offset class
-// (x!=0) + 2 (y!=0) + 4 (z!=0): sum over axes d of S_d * prod_{e != d} M_e with
-// the 1-D stiffness S(0) = 2/h, S(1) = -1/h and mass M(0) = 4h/6, M(1) = h/6
-// (2x2x2 Gauss integrates it exactly), times `scale`.
-void stiffness3d(const double h[3], double scale, float kc[8]) {
-  for (int cls = 0; cls < 8; ++cls) {
-    double s = 0.0;
-    for (int d = 0; d < 3; ++d) {
-      const bool off_d = (cls >> d) & 1;
-      double t = off_d ? -1.0 / h[d] : 2.0 / h[d];
-      for (int e = 0; e < 3; ++e)
-        if (e != d) t *= ((cls >> e) & 1) ? h[e] / 6.0 : 4.0 * h[e] / 6.0;
-      s += t;
-    }
-    kc[cls] = (float)(scale * s);
-  }
-}
-
 void set_params3d(pf_ctx* c, const pf_params* p) {
   pf::Implicit3DArgs& a = c->im;
   a.nx = (int)c->n[0];
@@ -190,7 +172,7 @@ void set_params3d(pf_ctx* c, const pf_params* p) {
   a.cb2g = (float)(p->fc_beta - 2.0 * p->fc_gamma);
   a.c3b6g = (float)(3.0 * p->fc_beta - 6.0 * p->fc_gamma);
   const double cell = c->h[0] * c->h[1] * c->h[2];
-  stiffness3d(c->h, p->kappa / cell, a.kc);
+  for (int d = 0; d < 3; ++d) a.kg[d] = (float)(2.0 * p->kappa / (c->h[d] * c->h[d]));
   a.inv_dt = (float)(1.0 / p->dt);
   a.mob = (float)p->mobility;
   a.cell = (float)cell;
@@ -1181,7 +1163,7 @@ cudaError_t stiff_only(pf_ctx* c, const float* U, float* out) {
   pf::Implicit3DArgs a = c->im;
   a.dw2 = 0.0f;
   a.alpha = a.two_gamma = a.four_gamma = a.cb2g = a.c3b6g = 0.0f;
-  stiffness3d(c->h, 1.0 / (c->h[0] * c->h[1] * c->h[2]), a.kc);
+  for (int d = 0; d < 3; ++d) a.kg[d] = (float)(2.0 / (c->h[d] * c->h[d]));  // kappa = 1
   a.U = U;
   a.W = U;
   a.out = out;

@@ -137,7 +137,7 @@ struct Implicit3DArgs {
   int double_well;  // 1: f = W u^2 (1-u)^2 (nf == 1); 0: Fan-Chen
   float dw2;        // 2 W
   float alpha, two_gamma, four_gamma, cb2g, c3b6g;  // Fan-Chen: a, 2g, 4g, b - 2g, 3b - 6g
-  float kc[8];      // kappa / m * 27-point stiffness, by offset class (x!=0) + 2(y!=0) + 4(z!=0)
+  float kg[3];      // 2 kappa / h_d^2: weights of the element gradient term per axis
   float inv_dt, mob;
   float cell;       // hx hy hz
   int unscaled;     // multiply the result by the lumped mass m_i
