@@ -8,9 +8,9 @@
 // halves, so every node uses the interior formula (an optional final
 // multiplication by m_i gives R and J v themselves).
 //
-// Work split: one block per 8x8x8 node tile.  The block stages U (and v, or
-// U^n) for the 10^3 nodes around it in shared memory, mirrored at the mesh
-// boundary, then evaluates all 9^3 elements touching the tile:
+// Work split: one block per 8 x 8 x kTZ node tile.  The block stages U (and v,
+// or U^n) for the nodes around it (one halo layer) in shared memory, mirrored
+// at the mesh boundary, then evaluates all elements touching the tile:
 //   phase 1: per element and Gauss point, S2 = sum_f U_f^2 (and T =
 //            sum_f U_f v_f for the JVP), the only couplings between fields;
 //   phase 2: per field, the Gauss values (trilinear, sum-factorised), the
@@ -35,11 +35,14 @@
 namespace pf {
 namespace {
 
-constexpr int kT = 8;                 // output nodes per tile edge
-constexpr int kN = kT + 2;            // staged nodes per edge (1 halo each side)
-constexpr int kE = kT + 1;            // elements per edge touching the tile
-constexpr int kNodes = kN * kN * kN;  // 1000
-constexpr int kElems = kE * kE * kE;  // 729
+#ifndef PF_IMP_TZ
+#define PF_IMP_TZ 8
+#endif
+constexpr int kTX = 8, kTY = 8, kTZ = PF_IMP_TZ;        // output nodes per tile edge
+constexpr int kNX = kTX + 2, kNY = kTY + 2, kNZ = kTZ + 2;  // staged nodes (1 halo each side)
+constexpr int kEX = kTX + 1, kEY = kTY + 1, kEZ = kTZ + 1;  // elements touching the tile
+constexpr int kNodes = kNX * kNY * kNZ;
+constexpr int kElems = kEX * kEY * kEZ;
 #ifndef PF_IMP_THREADS
 #define PF_IMP_THREADS 768
 #endif
@@ -194,12 +197,12 @@ __device__ __forceinline__ void project3_grad(const u64 q[8], const u64 gx[4], c
   }
 }
 
-__device__ __forceinline__ int nidx(int x, int y, int z) { return (z * kN + y) * kN + x; }
+__device__ __forceinline__ int nidx(int x, int y, int z) { return (z * kNY + y) * kNX + x; }
 
 // the 8 corners of element base (staged-node index of its lower corner)
 __device__ __forceinline__ void corners(const u64* P, int base, u64 c[8]) {
 #pragma unroll
-  for (int k = 0; k < 8; ++k) c[k] = P[base + ((k >> 2) * kN + ((k >> 1) & 1)) * kN + (k & 1)];
+  for (int k = 0; k < 8; ++k) c[k] = P[base + ((k >> 2) * kNY + ((k >> 1) & 1)) * kNX + (k & 1)];
 }
 
 template <int NF, bool kJVP>
@@ -214,15 +217,15 @@ __global__ void __launch_bounds__(kThreads) k_implicit3d(const Implicit3DArgs a)
   float* sS = reinterpret_cast<float*>(sE + 8 * kElems);  // [8][kElems] S2 at Gauss points
   float* sTq = sS + kElems * 8;                            // [8][kElems] T (JVP only)
 
-  const int tiles_x = (a.nx + kT - 1) / kT, tiles_y = (a.ny + kT - 1) / kT;
+  const int tiles_x = (a.nx + kTX - 1) / kTX, tiles_y = (a.ny + kTY - 1) / kTY;
   const int tile = blockIdx.x;
-  const int x0 = (tile % tiles_x) * kT, y0 = ((tile / tiles_x) % tiles_y) * kT,
-            z0 = (tile / (tiles_x * tiles_y)) * kT;
+  const int x0 = (tile % tiles_x) * kTX, y0 = ((tile / tiles_x) % tiles_y) * kTY,
+            z0 = (tile / (tiles_x * tiles_y)) * kTZ;
   const int64_t N = (int64_t)a.nx * a.ny * a.nz;
 
   // stage U and v / U^n with mirror images beyond the mesh, fields in pairs
   for (int i = threadIdx.x; i < kNodes; i += kThreads) {
-    const int lx = i % kN, ly = (i / kN) % kN, lz = i / (kN * kN);
+    const int lx = i % kNX, ly = (i / kNX) % kNY, lz = i / (kNX * kNY);
     const int gx = mirror(x0 - 1 + lx, a.nx), gy = mirror(y0 - 1 + ly, a.ny),
               gz = mirror(z0 - 1 + lz, a.nz);
     const int64_t g = ((int64_t)gz * a.ny + gy) * a.nx + gx;
@@ -237,7 +240,7 @@ __global__ void __launch_bounds__(kThreads) k_implicit3d(const Implicit3DArgs a)
 
   // phase 1: field couplings at the Gauss points of every element
   for (int e = threadIdx.x; e < kElems; e += kThreads) {
-    const int ex = e % kE, ey = (e / kE) % kE, ez = e / (kE * kE);
+    const int ex = e % kEX, ey = (e / kEX) % kEY, ez = e / (kEX * kEY);
     const int base = nidx(ex, ey, ez);
     u64 S2[8], T[8];
 #pragma unroll
@@ -270,7 +273,7 @@ __global__ void __launch_bounds__(kThreads) k_implicit3d(const Implicit3DArgs a)
     const u64* Up = sU + p * kNodes;
     const u64* Wp = sW + p * kNodes;
     for (int e = threadIdx.x; e < kElems; e += kThreads) {
-      const int ex = e % kE, ey = (e / kE) % kE, ez = e / (kE * kE);
+      const int ex = e % kEX, ey = (e / kEX) % kEY, ez = e / (kEX * kEY);
       const int base = nidx(ex, ey, ez);
       u64 c[8], uq[8], vq[8], hq[8], out[8], gx[4], gy[4], gz[4];
       corners(Up, base, c);
@@ -310,15 +313,15 @@ __global__ void __launch_bounds__(kThreads) k_implicit3d(const Implicit3DArgs a)
     }
     __syncthreads();
     // node gather: 8 elements around the node, mass term
-    for (int i = threadIdx.x; i < kT * kT * kT; i += kThreads) {
-      const int lx = 1 + i % kT, ly = 1 + (i / kT) % kT, lz = 1 + i / (kT * kT);
+    for (int i = threadIdx.x; i < kTX * kTY * kTZ; i += kThreads) {
+      const int lx = 1 + i % kTX, ly = 1 + (i / kTX) % kTY, lz = 1 + i / (kTX * kTY);
       const int gx = x0 + lx - 1, gy = y0 + ly - 1, gz = z0 + lz - 1;
       if (gx >= a.nx || gy >= a.ny || gz >= a.nz) continue;
-      u64 acc = sE[(lz * kE + ly) * kE + lx];  // k = 0
+      u64 acc = sE[(lz * kEY + ly) * kEX + lx];  // k = 0
 #pragma unroll
       for (int k = 1; k < 8; ++k) {  // element with corner k at this node
         const int ex = lx - (k & 1), ey = ly - ((k >> 1) & 1), ez = lz - (k >> 2);
-        acc = add2(acc, sE[k * kElems + (ez * kE + ey) * kE + ex]);
+        acc = add2(acc, sE[k * kElems + (ez * kEY + ey) * kEX + ex]);
       }
       const int c0 = nidx(lx, ly, lz);
       // G = (u - u^n)/dt + L (F + kappa K u) / m   or   v/dt + L (H v + kappa K v) / m,
@@ -351,7 +354,8 @@ cudaError_t launch_nf(const Implicit3DArgs& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     configured[kJVP] = true;
   }
-  const int tiles = ((a.nx + kT - 1) / kT) * ((a.ny + kT - 1) / kT) * ((a.nz + kT - 1) / kT);
+  const int tiles =
+      ((a.nx + kTX - 1) / kTX) * ((a.ny + kTY - 1) / kTY) * ((a.nz + kTZ - 1) / kTZ);
   k_implicit3d<NF, kJVP><<<tiles, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
