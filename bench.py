@@ -72,6 +72,23 @@ def _dist():
     return ws, rank, int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def job_rate(t_local, units_local, device=None):
+    """Whole-job throughput over the ranks of the default process group: the
+    units all ranks processed divided by the slowest rank's time (max over
+    ranks).  Returns (rate, t_max).  Without an initialised group it is the
+    local rate.  `device` holds the reduction tensors (a CUDA device under
+    NCCL, None = CPU under gloo)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return units_local / t_local, t_local
+    t = torch.tensor([float(t_local)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(u.item()) / float(t.item()), float(t.item())
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -189,13 +206,8 @@ def run_ours(args):
         barrier()
     for a, b in ev:
         times.append(a.elapsed_time(b) / 1e3)
-    t_total = sum(times)
-    if ws > 1:
-        tt = torch.tensor([t_total], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_total = float(tt.item())
     nodes = N_SIDE * N_SIDE
-    value = ws * nodes * DOF_PER_NODE * N_TSTEPS * args.steps / t_total
+    value, t_total = job_rate(sum(times), nodes * DOF_PER_NODE * N_TSTEPS * args.steps, dev)
     ms_per_step = 1e3 * t_total / args.steps
     step_launch_s = t_total / (args.steps * N_TSTEPS)
 
@@ -213,12 +225,8 @@ def run_ours(args):
         b.record(stream)
         e2e_ev.append((a, b))
     barrier()
-    t_e2e = sum(a.elapsed_time(b) for a, b in e2e_ev) / 1e3
-    if ws > 1:
-        tt = torch.tensor([t_e2e], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_e2e = float(tt.item())
-    e2e_value = ws * nodes * DOF_PER_NODE * N_TSTEPS * args.steps / t_e2e
+    e2e_value, t_e2e = job_rate(sum(a.elapsed_time(b) for a, b in e2e_ev) / 1e3,
+                                nodes * DOF_PER_NODE * N_TSTEPS * args.steps, dev)
 
     if rank != 0:
         if ws > 1:
