@@ -307,19 +307,39 @@ __global__ void __launch_bounds__(kThreads) k_elastic_load(ElasticLoadArgs a, fl
 // iteration parity `slot`), sc[2] = p.Ap.
 //   x += alpha p, r -= alpha Ap   with alpha = sc[slot] / sc[2]
 //   and part[block] = the block's FP64 partial of the new r . r
+//   (float4 over the first 4 n4 entries -- n4 = 0 unless every vector is
+//   16-byte aligned -- and scalars over the rest)
 __global__ void k_cg_xr(float* __restrict__ x, float* __restrict__ r, const float* __restrict__ p,
-                        const float* __restrict__ Ap, int64_t n, const double* __restrict__ sc,
-                        int slot, double* __restrict__ part) {
+                        const float* __restrict__ Ap, int64_t n, int64_t n4,
+                        const double* __restrict__ sc, int slot, double* __restrict__ part) {
   const float alpha = (float)(sc[slot] / sc[2]);
-  double rr = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  float rr = 0.0f;  // at most a few dozen squares per thread; blocks sum in FP64
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = tid; i < n4; i += nth) {
+    float4 xv = reinterpret_cast<float4*>(x)[i], rv = reinterpret_cast<float4*>(r)[i];
+    const float4 pv = reinterpret_cast<const float4*>(p)[i], av = reinterpret_cast<const float4*>(Ap)[i];
+    xv.x = fmaf(alpha, pv.x, xv.x);
+    xv.y = fmaf(alpha, pv.y, xv.y);
+    xv.z = fmaf(alpha, pv.z, xv.z);
+    xv.w = fmaf(alpha, pv.w, xv.w);
+    rv.x = fmaf(-alpha, av.x, rv.x);
+    rv.y = fmaf(-alpha, av.y, rv.y);
+    rv.z = fmaf(-alpha, av.z, rv.z);
+    rv.w = fmaf(-alpha, av.w, rv.w);
+    reinterpret_cast<float4*>(x)[i] = xv;
+    reinterpret_cast<float4*>(r)[i] = rv;
+    rr = fmaf(rv.x, rv.x, rr);
+    rr = fmaf(rv.y, rv.y, rr);
+    rr = fmaf(rv.z, rv.z, rr);
+    rr = fmaf(rv.w, rv.w, rr);
+  }
+  for (int64_t i = 4 * n4 + tid; i < n; i += nth) {
     x[i] = fmaf(alpha, p[i], x[i]);
     const float ri = fmaf(-alpha, Ap[i], r[i]);
     r[i] = ri;
-    rr += (double)(ri * ri);
+    rr = fmaf(ri, ri, rr);
   }
-  const double s = block_sum(rr);
+  const double s = block_sum((double)rr);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
@@ -332,12 +352,20 @@ __global__ void k_sum_part(const double* __restrict__ part, int nb, double* __re
 }
 
 //   p = r + beta p   with beta = sc[1 - slot] / sc[slot]
-__global__ void k_cg_p(const float* __restrict__ r, float* __restrict__ p, int64_t n,
+__global__ void k_cg_p(const float* __restrict__ r, float* __restrict__ p, int64_t n, int64_t n4,
                        const double* __restrict__ sc, int slot) {
   const float beta = (float)(sc[1 - slot] / sc[slot]);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = fmaf(beta, p[i], r[i]);
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = tid; i < n4; i += nth) {
+    float4 pv = reinterpret_cast<float4*>(p)[i];
+    const float4 rv = reinterpret_cast<const float4*>(r)[i];
+    pv.x = fmaf(beta, pv.x, rv.x);
+    pv.y = fmaf(beta, pv.y, rv.y);
+    pv.z = fmaf(beta, pv.z, rv.z);
+    pv.w = fmaf(beta, pv.w, rv.w);
+    reinterpret_cast<float4*>(p)[i] = pv;
+  }
+  for (int64_t i = 4 * n4 + tid; i < n; i += nth) p[i] = fmaf(beta, p[i], r[i]);
 }
 
 // zero the constrained entries (symmetry planes) of a displacement vector
@@ -403,13 +431,15 @@ cudaError_t launch_elastic_constrain(float* v, int nx, int ny, int nz, cudaStrea
 
 cudaError_t launch_cg_xr(float* x, float* r, const float* p, const float* Ap, int64_t n,
                          const double* sc, int slot, double* part, cudaStream_t s) {
-  k_cg_xr<<<cg_blocks(), 256, 0, s>>>(x, r, p, Ap, n, sc, slot, part);
+  const bool al = (((uintptr_t)x | (uintptr_t)r | (uintptr_t)p | (uintptr_t)Ap) & 15) == 0;
+  k_cg_xr<<<cg_blocks(), 256, 0, s>>>(x, r, p, Ap, n, al ? n / 4 : 0, sc, slot, part);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cg_p(const float* r, float* p, int64_t n, const double* sc, int slot,
                         cudaStream_t s) {
-  k_cg_p<<<blocks_for(n), 256, 0, s>>>(r, p, n, sc, slot);
+  const bool al = (((uintptr_t)r | (uintptr_t)p) & 15) == 0;
+  k_cg_p<<<blocks_for(n), 256, 0, s>>>(r, p, n, al ? n / 4 : 0, sc, slot);
   return cudaGetLastError();
 }
 

@@ -138,3 +138,17 @@ def test_invalid_arguments_are_rejected():
                             kw["m"], kw["l"], kw["a"])
         st, _ = _lib.pf_elastic_workspace(e)
         assert st == _lib.PF_ERR_ARG
+
+
+def test_solve_into_unaligned_buffer_matches_aligned():
+    # the CG updates take a float4 path only when every vector is 16-byte
+    # aligned; a displacement buffer offset by one float takes the scalar path
+    shape, h = (9, 10, 11), (10.0, 10.0, 10.0)
+    el = gpu(shape, h, E=E0, nu=NU0, m=0.01, l=0.3, a=40.0)
+    u0 = el.solve(rtol=1e-6).clone()
+    n = 3 * 9 * 10 * 11
+    buf = torch.zeros(n + 1, device="cuda")
+    u1 = buf[1:].view((3,) + shape)
+    assert u1.data_ptr() % 16 != 0
+    el.solve(u=u1, rtol=1e-6)
+    assert rel(u1.cpu().numpy(), u0.cpu().numpy()) <= 1e-6
