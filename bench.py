@@ -435,7 +435,9 @@ def forms_eshelby(dev, stream, flush, n=129):
         el.apply(u, out)
     t_apply = sorted(_timed(stream, lambda: el.apply(u, out), flush) for _ in range(21))[10]
     nodes = n ** 3
-    flop = 546  # per interior node: 26 offsets x 9 FMA + 78 differences
+    # per interior node: 13 mirror pairs x 3 components x 3 adds (two
+    # differences and their sum) + 75 FMA (39 diagonal, 36 nonzero couplings)
+    flop = 13 * 3 * 3 + 2 * 75
     peak_tflops = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 lanes x 2 flop x max SM clock
     el.solve(rtol=1e-6)  # warm
     x = el.empty()

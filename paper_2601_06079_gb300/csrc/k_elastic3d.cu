@@ -59,23 +59,33 @@ __device__ __forceinline__ void load_plane(const float* __restrict__ u, int64_t 
       for (int c = 0; c < 3; ++c) p[dy * 3 + dx][c] = __ldg(u + c * N + row0 + dy * nx + dx);
 }
 
-// K u at an interior node from its three planes, on differences to the node
+// K u at an interior node from its three planes, on differences to the node.
+// The assembled stencil of the uniform isotropic grid is centrally symmetric,
+// K(-o) = K(o), so each mirror pair of offsets acts once on the sum of its two
+// differences; and a coupling K_ij(o), i != j, is a product of central
+// differences along i and j, so it vanishes unless o_i and o_j are both
+// nonzero -- those terms are left out at compile time (75 FMA instead of 234).
 __device__ __forceinline__ void interior_node(const Elastic3DArgs& a, const float (&pm)[9][3],
                                               const float (&pc)[9][3], const float (&pp)[9][3],
                                               float out[3]) {
   out[0] = out[1] = out[2] = 0.0f;
 #pragma unroll
-  for (int o = 0; o < 27; ++o) {
-    if (o == 13) continue;
-    const float(&pl)[9][3] = o < 9 ? pm : (o < 18 ? pc : pp);
-    const int k = o % 9;
-    float d[3];
+  for (int o = 14; o < 27; ++o) {  // one offset of each pair (o, 26 - o)
+    const int m = 26 - o;
+    const int off[3] = {o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1};
+    const float(&po)[9][3] = o < 9 ? pm : (o < 18 ? pc : pp);
+    const float(&pq)[9][3] = m < 9 ? pm : (m < 18 ? pc : pp);
+    float s[3];
 #pragma unroll
-    for (int j = 0; j < 3; ++j) d[j] = pl[k][j] - pc[4][j];
+    for (int j = 0; j < 3; ++j) s[j] = (po[o % 9][j] - pc[4][j]) + (pq[m % 9][j] - pc[4][j]);
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < 3; ++i) {
+      out[i] = fmaf(a.ks[(o * 3 + i) * 3 + i], s[i], out[i]);
 #pragma unroll
-      for (int j = 0; j < 3; ++j) out[i] = fmaf(a.ks[(o * 3 + i) * 3 + j], d[j], out[i]);
+      for (int j = 0; j < 3; ++j)
+        if (j != i && off[i] != 0 && off[j] != 0)
+          out[i] = fmaf(a.ks[(o * 3 + i) * 3 + j], s[j], out[i]);
+    }
   }
 }
 
