@@ -23,12 +23,17 @@ constexpr int kThreads = 256;
 constexpr int S2X = TX + 4, S2Y = TY + 4;  // nodes with a 2-node halo
 constexpr int EX = TX + 3, EY = TY + 3;    // elements touching the 1-halo nodes
 
-__device__ __forceinline__ int mirror(int k, int n) {
-  const int p = 2 * (n - 1);
-  k %= p;
-  if (k < 0) k += p;
-  return k < n ? k : p - k;
+// Single mirror image about the end nodes, then clamped into the mesh: exact
+// for the 2-node halo of stored nodes (the coupled model needs at least 3
+// nodes per axis);
+// positions further out (the far side of a ragged last tile) only feed
+// outputs that are not stored, and the clamp keeps their loads in bounds.
+__device__ __forceinline__ int reflect(int k, int n) {
+  k = k < 0 ? -k : k;
+  k = k >= n ? 2 * (n - 1) - k : k;
+  return k < 0 ? 0 : (k >= n ? n - 1 : k);
 }
+
 
 __device__ __forceinline__ float gpt(int i) { return i ? kGHi : kGLo; }
 
@@ -40,12 +45,46 @@ struct Tile {
   float Ee[4][EY][EX];    // per-element corner terms of the eta residual
 };
 
-// Horner evaluation of sum_k a[k] x^k (N coefficients)
+typedef unsigned long long u64;  // packed FP32 pair: the two x Gauss points of a row
+
+__device__ __forceinline__ u64 pk(float lo, float hi) {
+  u64 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float plo(u64 v) {
+  float l, h;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(l), "=f"(h) : "l"(v));
+  return l;
+}
+__device__ __forceinline__ float phi(u64 v) {
+  float l, h;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(l), "=f"(h) : "l"(v));
+  return h;
+}
+__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
+  u64 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ u64 sub2(u64 a, u64 b) {
+  u64 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ u64 mul2(u64 a, u64 b) {
+  u64 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ u64 bc(float v) { return pk(v, v); }
+
+// Horner evaluation of sum_k a[k] x^k (N coefficients) on a packed pair
 template <int N>
-__device__ __forceinline__ float horner(const float* a, float x) {
-  float s = a[N - 1];
+__device__ __forceinline__ u64 horner2(const float* a, u64 x) {
+  u64 s = bc(a[N - 1]);
 #pragma unroll
-  for (int k = N - 2; k >= 0; --k) s = fmaf(s, x, a[k]);
+  for (int k = N - 2; k >= 0; --k) s = fma2(s, x, bc(a[k]));
   return s;
 }
 
@@ -57,45 +96,50 @@ __global__ void __launch_bounds__(kThreads) k_coupled2d(const Coupled2DArgs a) {
 
   for (int i = threadIdx.x; i < S2X * S2Y; i += kThreads) {
     const int lx = i % S2X, ly = i / S2X;
-    const int64_t g = (int64_t)mirror(y0 - 2 + ly, a.ny) * a.nx + mirror(x0 - 2 + lx, a.nx);
+    const int64_t g = (int64_t)reflect(y0 - 2 + ly, a.ny) * a.nx + reflect(x0 - 2 + lx, a.nx);
     T.c[ly][lx] = a.in[g];
     T.e[ly][lx] = a.in[N + g];
   }
   __syncthreads();
 
   // elements (ex, ey) with lower-left node (ex, ey) in 2-halo coordinates, for
-  // the elements that touch the 1-halo nodes: ex, ey in [0, EX), [0, EY)
+  // the elements that touch the 1-halo nodes: ex, ey in [0, EX), [0, EY).
+  // The two Gauss points of a row (xi = g_lo, g_hi) travel as one packed
+  // pair, so every interpolation and polynomial is one f32x2 instruction
+  // for two points; rows qy = 0, 1 are the pairs P[0], P[1].
+  const u64 X = pk(kGLo, kGHi);
   for (int i = threadIdx.x; i < EX * EY; i += kThreads) {
     const int ex = i % EX, ey = i / EX;
-    const float cc[4] = {T.c[ey][ex], T.c[ey][ex + 1], T.c[ey + 1][ex], T.c[ey + 1][ex + 1]};
-    const float ee[4] = {T.e[ey][ex], T.e[ey][ex + 1], T.e[ey + 1][ex], T.e[ey + 1][ex + 1]};
-    float gc[4], ge[4];
+    const float c0 = T.c[ey][ex], c1 = T.c[ey][ex + 1], c2 = T.c[ey + 1][ex], c3 = T.c[ey + 1][ex + 1];
+    const float e0 = T.e[ey][ex], e1 = T.e[ey][ex + 1], e2 = T.e[ey + 1][ex], e3 = T.e[ey + 1][ex + 1];
+    // bottom and top rows at the two x Gauss points, then the two y Gauss points
+    const u64 cb = fma2(X, bc(c1 - c0), bc(c0)), ct = fma2(X, bc(c3 - c2), bc(c2));
+    const u64 eb = fma2(X, bc(e1 - e0), bc(e0)), etp = fma2(X, bc(e3 - e2), bc(e2));
+    const u64 dc = sub2(ct, cb), de = sub2(etp, eb);
+    u64 gc[2], ge[2];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float xi = gpt(q & 1), et = gpt(q >> 1);
-      const float cb = fmaf(xi, cc[1] - cc[0], cc[0]), ct = fmaf(xi, cc[3] - cc[2], cc[2]);
-      const float eb = fmaf(xi, ee[1] - ee[0], ee[0]), etp = fmaf(xi, ee[3] - ee[2], ee[2]);
-      const float d = fmaf(et, ct - cb, cb);   // shifted c at the Gauss point
-      const float n = fmaf(et, etp - eb, eb);  // eta at the Gauss point
-      const float h = horner<6>(a.h, n), dh = horner<5>(a.dh, n);
-      const float dfa = horner<4>(a.dfa, d), dfb = horner<2>(a.dfb, d);
-      const float fa = horner<5>(a.fa, d), fb = horner<3>(a.fb, d);
-      gc[q] = fmaf(h, dfb - dfa, dfa);  // f_a' (1 - h) + f_b' h
-      ge[q] = (fb - fa) * dh;
+    for (int qy = 0; qy < 2; ++qy) {
+      const u64 et = bc(gpt(qy));
+      const u64 d = fma2(et, dc, cb);   // shifted c at the row's two Gauss points
+      const u64 n = fma2(et, de, eb);   // eta there
+      const u64 h = horner2<6>(a.h, n), dh = horner2<5>(a.dh, n);
+      const u64 dfa = horner2<4>(a.dfa, d), dfb = horner2<2>(a.dfb, d);
+      const u64 fa = horner2<5>(a.fa, d), fb = horner2<3>(a.fb, d);
+      gc[qy] = fma2(h, sub2(dfb, dfa), dfa);  // f_a' (1 - h) + f_b' h
+      ge[qy] = mul2(sub2(fb, fa), dh);
     }
-    // 1/4 sum_q v_q N_a(q): the Gauss weight |cell|/4 over the interior mass |cell|
+    // 1/4 sum_q v_q N_a(q): the Gauss weight |cell|/4 over the interior mass
+    // |cell|, folded into the packed weights N_a of the two x points per row
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      float sc = 0.0f, se = 0.0f;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float xi = gpt(q & 1), et = gpt(q >> 1);
-        const float na = ((c & 1) ? xi : 1.0f - xi) * ((c >> 1) ? et : 1.0f - et);
-        sc = fmaf(gc[q], na, sc);
-        se = fmaf(ge[q], na, se);
-      }
-      T.Ec[c][ey][ex] = 0.25f * sc;
-      T.Ee[c][ey][ex] = 0.25f * se;
+      const float wlo = (c & 1) ? kGLo : 1.0f - kGLo, whi = (c & 1) ? kGHi : 1.0f - kGHi;
+      const float y0 = 0.25f * ((c >> 1) ? kGLo : 1.0f - kGLo);
+      const float y1 = 0.25f * ((c >> 1) ? kGHi : 1.0f - kGHi);
+      const u64 w0 = pk(wlo * y0, whi * y0), w1 = pk(wlo * y1, whi * y1);
+      const u64 sc = fma2(w1, gc[1], mul2(w0, gc[0]));
+      const u64 se = fma2(w1, ge[1], mul2(w0, ge[0]));
+      T.Ec[c][ey][ex] = plo(sc) + phi(sc);
+      T.Ee[c][ey][ex] = plo(se) + phi(se);
     }
   }
   __syncthreads();

@@ -87,12 +87,16 @@ __device__ __forceinline__ u64 mul2(u64 a, u64 b) {
 }
 __device__ __forceinline__ u64 bc(float v) { return pk(v, v); }
 
-__device__ __forceinline__ int mirror(int k, int n) {
-  const int p = 2 * (n - 1);
-  k %= p;
-  if (k < 0) k += p;
-  return k < n ? k : p - k;
+// Single mirror image about the end nodes, then clamped into the mesh: exact
+// for the 1-node halo of stored nodes when the mesh has at least 2 nodes;
+// positions further out (the far side of a ragged last tile) only feed
+// outputs that are not stored, and the clamp keeps their loads in bounds.
+__device__ __forceinline__ int reflect(int k, int n) {
+  k = k < 0 ? -k : k;
+  k = k >= n ? 2 * (n - 1) - k : k;
+  return k < 0 ? 0 : (k >= n ? n - 1 : k);
 }
+
 
 // values at the two Gauss points of a segment from its end values
 __device__ __forceinline__ void interp1(u64 a, u64 b, u64& lo, u64& hi) {
@@ -226,8 +230,8 @@ __global__ void __launch_bounds__(kThreads) k_implicit3d(const Implicit3DArgs a)
   // stage U and v / U^n with mirror images beyond the mesh, fields in pairs
   for (int i = threadIdx.x; i < kNodes; i += kThreads) {
     const int lx = i % kNX, ly = (i / kNX) % kNY, lz = i / (kNX * kNY);
-    const int gx = mirror(x0 - 1 + lx, a.nx), gy = mirror(y0 - 1 + ly, a.ny),
-              gz = mirror(z0 - 1 + lz, a.nz);
+    const int gx = reflect(x0 - 1 + lx, a.nx), gy = reflect(y0 - 1 + ly, a.ny),
+              gz = reflect(z0 - 1 + lz, a.nz);
     const int64_t g = ((int64_t)gz * a.ny + gy) * a.nx + gx;
 #pragma unroll
     for (int p = 0; p < NP; ++p) {

@@ -35,7 +35,8 @@ def oracle(U0, h, n_steps):
 
 
 @pytest.mark.parametrize("shape,h", [((33, 41), 1.0), ((67, 35), (0.9, 1.2)), ((3, 4), 1.0),
-                                     ((100, 130), 1.0)])
+                                     ((100, 130), 1.0), ((3, 9), 1.0), ((6, 3), 1.0),
+                                     ((17, 33), 1.0)])
 def test_coupled_matches_oracle(shape, h):
     U0 = G.coupled_initial(5, shape)
     got, _, _ = run(U0, h, 150)
