@@ -268,7 +268,8 @@ def run_ours(args):
                          "implicit_adjoint_ac_1024": forms_implicit_adjoint(dev, stream),
                          "adjoint_ch_512": forms_adjoint(dev, stream),
                          "implicit_warm_start_128": forms_warm_start(dev),
-                         "eshelby_129": forms_eshelby(dev, stream, flush)}
+                         "eshelby_129": forms_eshelby(dev, stream, flush),
+                         "jvp_128_fanchen8": forms_jvp(dev, stream, flush)}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_sample_steps)
     print(json.dumps(line), flush=True)
@@ -462,6 +463,36 @@ def forms_eshelby(dev, stream, flush, n=129):
             "accuracy_gate": "operator and loads <= 2e-6 rel vs the FP64 oracle; solution, "
                              "objective <= 1e-5 and dO/dnu <= 1e-4 vs the oracle adjoint "
                              "(tests/test_gpu_elastic.py)"}
+
+
+def forms_jvp(dev, stream, flush, n=128):
+    """The Jacobian-vector product of the implicit step (Eq. 14; Fan-Chen
+    Hessian, 8 order parameters, 128^3 nodes) alone, L2 flushed before each
+    launch: against HBM (96 B per node: U, v in, J v out) and against the FP32
+    ALU, counting per node (one element per node) the Gauss values of U and v
+    for 8 fields (960 flop), S2 and T (256), the Hessian action (512), the
+    gradient term (240), the weights back (1,104) and the gather (96)."""
+    import paper_2601_06079_gb300 as pf  # noqa: F401
+    import pf_inputs as G
+    import torch
+    from paper_2601_06079_gb300 import warmstart as WS
+    solver = WS.grain_solver(n, device=dev)
+    U = torch.from_numpy(G.voronoi_grains(1, n=n, n_seeds=64, n_op=8)).to(dev)
+    v = torch.from_numpy(G.random_field(2, (8, n, n, n))).to(dev)
+    out = torch.empty_like(U)
+    for _ in range(3):
+        solver.jvp(U, v, out)
+    t = sorted(_timed(stream, lambda: solver.jvp(U, v, out), flush) for _ in range(11))[5]
+    nodes = n ** 3
+    hbm, _ = _peaks()
+    flop = 960 + 256 + 512 + 240 + 1104 + 96
+    peak_tflops = 152 * 128 * 2 * 2.07e9 / 1e12
+    return {"mesh": f"{n}^3 nodes x 8 order parameters", "us": t * 1e6,
+            "hbm": {"achieved_gbs": 96 * nodes / t / 1e9, "peak_gbs": hbm,
+                    "frac": 96 * nodes / t / 1e9 / hbm},
+            "alu": {"flop_per_node": flop, "achieved_tflops": flop * nodes / t / 1e12,
+                    "peak_tflops": peak_tflops, "frac": flop * nodes / t / 1e12 / peak_tflops},
+            "accuracy_gate": "<= 2e-6 rel vs the FP64 oracle JVP (tests/test_gpu_implicit.py)"}
 
 
 def forms_ensemble(dev, stream, flush, n_steps=1000):
