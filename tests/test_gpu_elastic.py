@@ -152,3 +152,25 @@ def test_solve_into_unaligned_buffer_matches_aligned():
     assert u1.data_ptr() % 16 != 0
     el.solve(u=u1, rtol=1e-6)
     assert rel(u1.cpu().numpy(), u0.cpu().numpy()) <= 1e-6
+
+
+def test_zero_misfit_and_iteration_cap():
+    # m = 0: the load vanishes, CG stops before its first iteration with u = 0,
+    # V = V0 and zero sensitivities; a cap of 8 iterations on a real load
+    # reports PF_ERR_NOT_CONVERGED with the stats of the partial solve
+    import paper_2601_06079_gb300 as pf
+    from paper_2601_06079_gb300 import _lib
+    shape, h = (9, 9, 9), (12.5, 12.5, 12.5)
+    el = gpu(shape, h, E=E0, nu=NU0, m=0.0, l=0.3, a=40.0)
+    u = el.solve()
+    assert el.stats.iterations == 0 and el.stats.converged == 1
+    assert float(u.abs().max()) == 0.0
+    V, gr, _ = el.sensitivity()
+    assert V == pytest.approx(8 * 12.5 * 8 * 12.5 * 8 * 12.5, rel=1e-12)
+    assert gr["E"] == 0.0 and gr["nu"] == 0.0
+    el.set(m=0.01)
+    with pytest.raises(pf.PFError) as ex:
+        el.solve(rtol=1e-12, max_iter=8)
+    assert ex.value.status == _lib.PF_ERR_NOT_CONVERGED
+    assert el.stats.iterations == 8 and el.stats.converged == 0
+    assert el.stats.final_residual < el.stats.initial_residual
