@@ -225,7 +225,12 @@ __global__ void __launch_bounds__(kThreads) k_ch_adj_step(const ChMobArgs a, con
     }
   }
   __syncthreads();
-  double dM = 0.0;
+  // per-node products in FP32 (GB300's FP64 rate is a small fraction of its
+  // FP32 rate); each thread's two or three nodes sum in FP32, the block sums
+  // and the running mobility gradient in FP64.  The lumped mass m_i is
+  // cell * frac, with cell applied once per thread.
+  float dM = 0.0f;
+  const float ngm = (float)(-(double)a.dt * a.M * a.cell);  // -dt M cell
   for (int i = threadIdx.x; i < S1X * S1Y; i += kThreads) {
     const int x = 1 + i % S1X, y = 1 + i / S1X;
     const float w = gather4(T.E, y, x);
@@ -233,12 +238,10 @@ __global__ void __launch_bounds__(kThreads) k_ch_adj_step(const ChMobArgs a, con
     const int gx = x0 + x - 2, gy = y0 + y - 2;
     const bool tile_node = x >= 2 && x < TX + 2 && y >= 2 && y < TY + 2;
     if (tile_node && gx < a.nx && gy < a.ny) {
-      const double frac = ((gx == 0 || gx == a.nx - 1) ? 0.5 : 1.0) *
-                          ((gy == 0 || gy == a.ny - 1) ? 0.5 : 1.0);
-      const double mi = a.cell * frac;
-      dM += mi * (double)w * (double)T.mu[y - 1][x - 1];
-      if (grad_m)
-        grad_m[(int64_t)gy * a.nx + gx] += -(double)a.dt * a.M * mi * (double)gather4(T.G, y, x);
+      const float frac = ((gx == 0 || gx == a.nx - 1) ? 0.5f : 1.0f) *
+                         ((gy == 0 || gy == a.ny - 1) ? 0.5f : 1.0f);
+      dM = fmaf(frac * w, T.mu[y - 1][x - 1], dM);
+      if (grad_m) grad_m[(int64_t)gy * a.nx + gx] += (double)(ngm * frac * gather4(T.G, y, x));
     }
   }
   __syncthreads();
@@ -260,7 +263,7 @@ __global__ void __launch_bounds__(kThreads) k_ch_adj_step(const ChMobArgs a, con
     for (int k = 0; k < 4; ++k) T.E[k][ey][ex] = o[k];
   }
   __syncthreads();
-  double dK = 0.0, dW = 0.0;
+  float dK = 0.0f, dW = 0.0f;
   for (int i = threadIdx.x; i < TX * TY; i += kThreads) {
     const int x = 2 + i % TX, y = 2 + i / TX;
     const int gx = x0 + x - 2, gy = y0 + y - 2;
@@ -268,14 +271,14 @@ __global__ void __launch_bounds__(kThreads) k_ch_adj_step(const ChMobArgs a, con
     const float w = T.w[y - 1][x - 1];
     const float Hw = gather4(T.E, y, x) + a.kappa * stencil9(&T.w[y - 1][x - 1], S1X, a.k);
     yout[(int64_t)gy * a.nx + gx] = fmaf(-a.dt, Hw, T.y[y][x]);
-    const double frac = ((gx == 0 || gx == a.nx - 1) ? 0.5 : 1.0) *
-                        ((gy == 0 || gy == a.ny - 1) ? 0.5 : 1.0);
-    const double mw = a.cell * frac * (double)w;
-    dK += mw * (double)T.Kc[y - 1][x - 1];
-    dW += mw * (double)T.F[y - 1][x - 1];
+    const float frac = ((gx == 0 || gx == a.nx - 1) ? 0.5f : 1.0f) *
+                       ((gy == 0 || gy == a.ny - 1) ? 0.5f : 1.0f);
+    const float mw = frac * w;
+    dK = fmaf(mw, T.Kc[y - 1][x - 1], dK);
+    dW = fmaf(mw, T.F[y - 1][x - 1], dW);
   }
   // block sums (fixed order), accumulated across steps in this block's slot
-  double v[3] = {dK, dW, dM};
+  double v[3] = {a.cell * (double)dK, a.cell * (double)dW, a.cell * (double)dM};
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
 #pragma unroll

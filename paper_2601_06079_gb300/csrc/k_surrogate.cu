@@ -111,12 +111,23 @@ __global__ void k_incr_sumsq(const float* __restrict__ x, int nf, int nxc, int64
   __shared__ double red[kT];
   const int b = blockIdx.y;
   const float* u = x + (int64_t)b * nxc * V;
+  // differences and squares in FP32, runs of 16 summed in FP32 and the runs in
+  // FP64: GB300's FP64 rate is a small fraction of its FP32 rate, so no FP64
+  // arithmetic per element
   double acc = 0.0;
+  float run = 0.0f;
+  int k = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)nf * V;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const double d = (double)u[i] - (double)u[nf * V + i];
-    acc += d * d;
+    const float d = u[i] - u[nf * V + i];
+    run = fmaf(d, d, run);
+    if (++k == 16) {
+      acc += (double)run;
+      run = 0.0f;
+      k = 0;
+    }
   }
+  acc += (double)run;
   red[threadIdx.x] = acc;
   __syncthreads();
   for (int o = kT / 2; o > 0; o >>= 1) {
@@ -287,8 +298,18 @@ __global__ void k_apply_stiff(const float* __restrict__ in, int64_t planes, int 
 // Per-block partial sums of q^2 over n values.
 __global__ void k_sumsq(const float* __restrict__ q, int64_t n, double* __restrict__ partials) {
   __shared__ double red[kT];
-  double acc = 0.0;
-  for (int64_t i = gtid(); i < n; i += grid_stride()) acc += (double)q[i] * q[i];
+  double acc = 0.0;  // runs of 16 squares in FP32, the runs in FP64 (see k_incr_sumsq)
+  float run = 0.0f;
+  int k = 0;
+  for (int64_t i = gtid(); i < n; i += grid_stride()) {
+    run = fmaf(q[i], q[i], run);
+    if (++k == 16) {
+      acc += (double)run;
+      run = 0.0f;
+      k = 0;
+    }
+  }
+  acc += (double)run;
   red[threadIdx.x] = acc;
   __syncthreads();
   for (int o = kT / 2; o > 0; o >>= 1) {
