@@ -133,42 +133,55 @@ __global__ void k_lincomb(const float* __restrict__ V, int64_t ldv, int k, LinCo
   }
 }
 
-// partials of sum_i (m_i g_i)^2 over all fields: m_i = cell * boundary factors
+// lumped-mass boundary factor of a node: 1/2 per axis on which it is an end
+// node (nz = 1 is a 2-D mesh); node < 2^31 (the mesh limit)
+__device__ __forceinline__ float mass_factor(int node, int nx, int ny, int nz) {
+  const int x = node % nx, y = (node / nx) % ny, z = node / (nx * ny);
+  float m = 1.0f;
+  if (x == 0 || x == nx - 1) m *= 0.5f;
+  if (y == 0 || y == ny - 1) m *= 0.5f;
+  if (nz > 1 && (z == 0 || z == nz - 1)) m *= 0.5f;
+  return m;
+}
+
+// partials of sum_i (m_i g_i)^2 over all fields: m_i = cell * boundary
+// factor.  Products in FP32 (GB300's FP64 rate is a small fraction of its
+// FP32 rate), runs of 16 squares in FP32, the runs and the block sum in FP64.
 __global__ void __launch_bounds__(kThreads) k_mass_norm(const float* __restrict__ g, int nx,
-                                                        int ny, int nz, int nf, double cell,
+                                                        int ny, int nz, int nf, float cell,
                                                         double* __restrict__ partials) {
   __shared__ double scratch[kThreads / 32];
-  const int64_t N = (int64_t)nx * ny * nz, n = N * nf;
+  const int N = nx * ny * nz;
   double acc = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * kThreads) {
-    const int64_t node = i % N;
-    const int x = (int)(node % nx), y = (int)((node / nx) % ny), z = (int)(node / ((int64_t)nx * ny));
-    double m = cell;
-    if (x == 0 || x == nx - 1) m *= 0.5;
-    if (y == 0 || y == ny - 1) m *= 0.5;
-    if (nz > 1 && (z == 0 || z == nz - 1)) m *= 0.5;
-    const double v = m * (double)g[i];
-    acc += v * v;
+  float run = 0.0f;
+  int k = 0;
+  for (int node = blockIdx.x * kThreads + threadIdx.x; node < N; node += gridDim.x * kThreads) {
+    const float m = cell * mass_factor(node, nx, ny, nz);
+    for (int f = 0; f < nf; ++f) {
+      const float v = m * g[(int64_t)f * N + node];
+      run = fmaf(v, v, run);
+      if (++k == 16) {
+        acc += (double)run;
+        run = 0.0f;
+        k = 0;
+      }
+    }
   }
+  acc += (double)run;
   acc = block_sum(acc, scratch);
   if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
 // out = a * m_i^(+1 or -1) * in over nf planes of nx x ny x nz nodes, m the
-// lumped mass (cell times 1/2 per boundary axis; nz = 1 is a 2-D mesh)
+// lumped mass (cell times 1/2 per boundary axis; nz = 1 is a 2-D mesh);
+// inv_cell = 1 / cell, so that the inverse is a multiplication
 __global__ void k_mass_mul(const float* __restrict__ in, float* __restrict__ out, int nx, int ny,
-                           int nz, int nf, double cell, float a, int inverse) {
-  const int64_t N = (int64_t)nx * ny * nz, n = N * nf;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t node = i % N;
-    const int x = (int)(node % nx), y = (int)((node / nx) % ny), z = (int)(node / ((int64_t)nx * ny));
-    double m = cell;
-    if (x == 0 || x == nx - 1) m *= 0.5;
-    if (y == 0 || y == ny - 1) m *= 0.5;
-    if (nz > 1 && (z == 0 || z == nz - 1)) m *= 0.5;
-    out[i] = (float)((double)a * (inverse ? (double)in[i] / m : m * (double)in[i]));
+                           int nz, int nf, float cell, float inv_cell, float a, int inverse) {
+  const int N = nx * ny * nz;
+  for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < N; node += gridDim.x * blockDim.x) {
+    const float fac = mass_factor(node, nx, ny, nz);
+    const float sc = a * (inverse ? inv_cell / fac : cell * fac);  // fac is a power of 2
+    for (int f = 0; f < nf; ++f) out[(int64_t)f * N + node] = sc * in[(int64_t)f * N + node];
   }
 }
 
@@ -208,14 +221,14 @@ cudaError_t launch_lincomb(const float* V, int64_t ldv, int k, const LinComb& y,
 
 cudaError_t launch_mass_mul(const float* in, float* out, int nx, int ny, int nz, int nf,
                             double cell, float a, int inverse, cudaStream_t s) {
-  k_mass_mul<<<elementwise_blocks((int64_t)nx * ny * nz * nf), 256, 0, s>>>(in, out, nx, ny, nz, nf,
-                                                                          cell, a, inverse);
+  k_mass_mul<<<elementwise_blocks((int64_t)nx * ny * nz), 256, 0, s>>>(
+      in, out, nx, ny, nz, nf, (float)cell, (float)(1.0 / cell), a, inverse);
   return cudaGetLastError();
 }
 
 cudaError_t launch_mass_norm(const float* g, int nx, int ny, int nz, int nf, double cell,
                              double* partials, double* out, cudaStream_t s) {
-  k_mass_norm<<<kBlocks, kThreads, 0, s>>>(g, nx, ny, nz, nf, cell, partials);
+  k_mass_norm<<<kBlocks, kThreads, 0, s>>>(g, nx, ny, nz, nf, (float)cell, partials);
   k_sum_partials_cols<<<1, kThreads, 0, s>>>(partials, kBlocks, 1, out);
   return cudaGetLastError();
 }
