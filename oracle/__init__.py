@@ -110,6 +110,7 @@ def lib():
         L.or_conv3d_bwd_weight.argtypes = [P, I, I, I, I, P, I, P, P]
         L.or_ch_adjoint.restype = C.c_double
         L.or_ch_adjoint.argtypes = [M, Pp, C.c_double, C.c_int64, P, P, C.c_int, P, P, P]
+        L.or_set_threads.argtypes = [C.c_int]
         D = C.c_double
         L.or_elastic_lame.argtypes = [D, D, P, P]
         L.or_elastic_apply.argtypes = [M, D, D, P, P]
@@ -403,3 +404,8 @@ class Elastic:
         O = lib().or_elastic_sensitivity(C.byref(self.m), E, nu, m, l, a, _ptr(g), rtol, maxit,
                                          _ptr(u), _ptr(grads))
         return O + V0, grads, u
+
+
+def set_threads(n):
+    """Threads of the oracle's OpenMP loops (n <= 0: one per processor)."""
+    lib().or_set_threads(int(n))

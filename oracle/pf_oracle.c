@@ -21,6 +21,7 @@
  *   Eq. 13, 14  implicit Euler residual R = M (U - U^n)/dt + r(U)
  *   Supp. 2     adjoint sensitivities (here the discrete adjoint of Eq. 12)
  */
+#include <omp.h>
 #include "pf_oracle.h"
 
 #include <math.h>
@@ -896,3 +897,6 @@ void or_conv3d_bwd_weight(const double* x, int ci, int d, int h, int w, const do
       dbias[o] = s;
     }
 }
+
+/* threads of the OpenMP loops (<= 0: the runtime's default) */
+void or_set_threads(int n) { omp_set_num_threads(n > 0 ? n : omp_get_num_procs()); }

@@ -100,4 +100,7 @@ double or_elastic_sensitivity(const or_mesh* m, double E, double nu, double em, 
                               double ea, const double* g, double rtol, int maxit, double* u_out,
                               double* grads);
 
+/* threads of the OpenMP loops (<= 0: one per processor) */
+void or_set_threads(int n);
+
 #endif
