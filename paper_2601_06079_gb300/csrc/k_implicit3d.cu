@@ -56,13 +56,13 @@ __device__ __forceinline__ u64 pk(float lo, float hi) {
   return r;
 }
 __device__ __forceinline__ float plo(u64 v) {
-  float l, h;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(l), "=f"(h) : "l"(v));
+  float l;
+  asm("{ .reg .f32 t; mov.b64 {%0, t}, %1; }" : "=f"(l) : "l"(v));
   return l;
 }
 __device__ __forceinline__ float phi(u64 v) {
-  float l, h;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(l), "=f"(h) : "l"(v));
+  float h;
+  asm("{ .reg .f32 t; mov.b64 {t, %0}, %1; }" : "=f"(h) : "l"(v));
   return h;
 }
 __device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
