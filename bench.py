@@ -527,7 +527,7 @@ def forms_ensemble(dev, stream, flush, n_steps=1000):
     return out
 
 
-def forms_warm_start(dev, n=128, n_eval=200, seeds=4, traj_steps=100, iters=2000):
+def forms_warm_start(dev, n=128, n_eval=200, seeds=4, traj_steps=100, iters=2000, lr=3e-4):
     """3-D grain growth (8 Fan-Chen order parameters, 128^3, dt 0.5): Newton
     from the plain U^n start vs the learned history-2 surrogate (trained here
     on trajectories from other seeds) vs its zero-correction ablation (pure
@@ -546,7 +546,7 @@ def forms_warm_start(dev, n=128, n_eval=200, seeds=4, traj_steps=100, iters=2000
     surr = pf.Surrogate(device=dev, history=2)
     surr.init(seed=7, last_layer_scale=0.0)
     t0 = time.perf_counter()
-    losses = WS.train(surr, data, iters=iters, crop=64, batch=4, lr=1e-4, seed=1, stiff=0.5)
+    losses = WS.train(surr, data, iters=iters, crop=64, batch=4, lr=lr, seed=1, stiff=0.5)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     del data
@@ -556,7 +556,7 @@ def forms_warm_start(dev, n=128, n_eval=200, seeds=4, traj_steps=100, iters=2000
     out = {"mesh": f"{n}^3 nodes x 8 order parameters", "dt": 0.5, "steps": n_eval,
            "newton_rtol": 1e-5, "history": 2,
            "train": {"trajectories": f"seeds 101..{100 + seeds}, {traj_steps} steps each",
-                     "iters": iters, "seconds_data": t_data, "seconds_train": t_train,
+                     "iters": iters, "lr": lr, "seconds_data": t_data, "seconds_train": t_train,
                      "loss_first_last_50": [float(np.mean(losses[:50])),
                                             float(np.mean(losses[-50:]))]}}
     res = {}

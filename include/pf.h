@@ -299,11 +299,13 @@ pf_status pf_energy2d_static(const float* state, int64_t nx, int64_t ny, double 
  *   n_in = 8:  x = U^n.  Guess = U^n + s * net, s = out_scale.
  *   n_in = 16: x = [U^n; U^{n-1}].  Guess = 2 U^n - U^{n-1} + s_b * net.
  *   n_in = 24: x = [U^n; U^{n-1}; U^{n-2}].  Guess = 3 U^n - 3 U^{n-1} + U^{n-2}
- *              + s_b * net.
+ *              + c_b * net.
  * With history the network sees U^n and the increments U^{n-k+1} - U^{n-k}
  * divided by s_b = out_scale * RMS_b(U^n - U^{n-1}) (per sample b, floored at
- * 1e-30): a learned correction to linear / quadratic extrapolation in units of
- * the last increment.  Outputs [batch][8][d][h][w]; d a multiple of 16, h and
+ * 1e-30): a learned correction to linear extrapolation in units of the last
+ * increment, or to quadratic extrapolation in units of its curvature,
+ * c_b = max(out_scale * RMS_b(U^n - 2 U^{n-1} + U^{n-2}), 1e-3 s_b), so that
+ * the correction shrinks where the trajectory is nearly quadratic.  Outputs [batch][8][d][h][w]; d a multiple of 16, h and
  * w of 64.  out_scale must be positive and finite; anything else is PF_ERR_ARG. */
 pf_status pf_surrogate_param_count(int64_t* n_params);
 

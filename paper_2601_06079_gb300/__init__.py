@@ -272,9 +272,11 @@ class Surrogate:
 
     history = 0: input U^n (8 channels), guess U^n + out_scale * net.
     history = 1: input [U^n; U^{n-1}], guess 2 U^n - U^{n-1} + s * net.
-    history = 2: input [U^n; U^{n-1}; U^{n-2}], guess 3 U^n - 3 U^{n-1} + U^{n-2} + s * net.
-    With history s = out_scale * RMS(U^n - U^{n-1}): a learned correction to
-    linear / quadratic extrapolation in units of the last increment.  A
+    history = 2: input [U^n; U^{n-1}; U^{n-2}], guess 3 U^n - 3 U^{n-1} + U^{n-2} + c * net.
+    With history the inputs are the increments in units s = out_scale *
+    RMS(U^n - U^{n-1}); the correction is in units of the last increment (s,
+    linear extrapolation) or of the curvature (c = max(out_scale * RMS(U^n -
+    2 U^{n-1} + U^{n-2}), 1e-3 s), quadratic extrapolation).  A
     history-2 network also accepts 16-channel inputs (its third-state weights
     then see zeros), which is how the second step of a run is predicted."""
 

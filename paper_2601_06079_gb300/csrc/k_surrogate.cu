@@ -106,8 +106,9 @@ __global__ void k_ndhwc_to_planar_add(const float* __restrict__ y, int C, int nf
 // U^n - U^{n-1} (modes 1, 2: x holds nxc = nf (mode + 1) channels per sample,
 // U^n first), floored at 1e-30.  part holds gridDim.x partial sums per sample
 // (fixed-order reduction).
+//   second = 1 (mode 2): the second difference U^n - 2 U^{n-1} + U^{n-2} instead
 __global__ void k_incr_sumsq(const float* __restrict__ x, int nf, int nxc, int64_t V,
-                             double* __restrict__ part) {
+                             int second, double* __restrict__ part) {
   __shared__ double red[kT];
   const int b = blockIdx.y;
   const float* u = x + (int64_t)b * nxc * V;
@@ -119,7 +120,8 @@ __global__ void k_incr_sumsq(const float* __restrict__ x, int nf, int nxc, int64
   int k = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)nf * V;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const float d = u[i] - u[nf * V + i];
+    const float d = second ? (u[i] - u[nf * V + i]) - (u[nf * V + i] - u[2 * nf * V + i])
+                           : u[i] - u[nf * V + i];
     run = fmaf(d, d, run);
     if (++k == 16) {
       acc += (double)run;
@@ -148,6 +150,18 @@ __global__ void k_incr_scale(const double* __restrict__ part, int nblk, int B, d
   double ss = 0.0;
   for (int k = 0; k < nblk; ++k) ss += part[b * nblk + k];
   sig[b] = fmaxf(a * (float)sqrt(ss / count), 1e-30f);
+}
+
+// output unit of the quadratic-extrapolation model: a * RMS of the second
+// difference, floored at 1e-3 of the increment unit sig[b] (a trajectory
+// with no curvature leaves a small correction rather than a vanishing unit)
+__global__ void k_curv_scale(const double* __restrict__ part, int nblk, int B, double count,
+                             float a, const float* __restrict__ sig, float* __restrict__ sigo) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  double ss = 0.0;
+  for (int k = 0; k < nblk; ++k) ss += part[b * nblk + k];
+  sigo[b] = fmaxf(fmaxf(a * (float)sqrt(ss / count), 1e-3f * sig[b]), 1e-30f);
 }
 
 // Voxel index helpers for NDHWC: i = ((b * D + z) * H + y) * W + x
@@ -391,12 +405,18 @@ cudaError_t launch_ndhwc_to_planar_add(const float* y, int C, int nf, int B, int
 }
 
 cudaError_t launch_incr_scale(const float* x, int nf, int B, int64_t V, float a, int mode,
-                              double* part, int nblk, float* sig, cudaStream_t s) {
+                              double* part, int nblk, float* sig, float* sigo, cudaStream_t s) {
   if (mode) {
-    k_incr_sumsq<<<dim3(nblk, B), kT, 0, s>>>(x, nf, nf * (mode + 1), V, part);
+    k_incr_sumsq<<<dim3(nblk, B), kT, 0, s>>>(x, nf, nf * (mode + 1), V, 0, part);
     if (cudaGetLastError() != cudaSuccess) return cudaErrorLaunchFailure;
   }
   k_incr_scale<<<(B + 127) / 128, 128, 0, s>>>(part, nblk, B, (double)nf * V, a, mode, sig);
+  if (mode == 2) {  // the partials are reused once the increment unit is formed
+    k_incr_sumsq<<<dim3(nblk, B), kT, 0, s>>>(x, nf, 3 * nf, V, 1, part);
+    k_curv_scale<<<(B + 127) / 128, 128, 0, s>>>(part, nblk, B, (double)nf * V, a, sig, sigo);
+  } else {
+    cudaMemcpyAsync(sigo, sig, sizeof(float) * B, cudaMemcpyDeviceToDevice, s);
+  }
   return cudaGetLastError();
 }
 

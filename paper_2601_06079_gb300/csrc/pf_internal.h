@@ -235,8 +235,11 @@ cudaError_t launch_planar_to_ndhwc(const float* in, int nf, int C, int B, int64_
 cudaError_t launch_ndhwc_to_planar_add(const float* y, int C, int nf, int B, int64_t V,
                                        const float* base, int nb, int mode, const float* sig,
                                        float* out, cudaStream_t s);
+// sig[b]: the input unit (a * RMS of U^n - U^{n-1}; a for mode 0); sigo[b]:
+// the output unit (= sig, except mode 2: a * RMS of U^n - 2 U^{n-1} + U^{n-2},
+// floored at 1e-3 sig[b])
 cudaError_t launch_incr_scale(const float* x, int nf, int B, int64_t V, float a, int mode,
-                              double* part, int nblk, float* sig, cudaStream_t s);
+                              double* part, int nblk, float* sig, float* sigo, cudaStream_t s);
 cudaError_t launch_pool(const void* in, int B, int D, int H, int W, int C, void* out,
                         cudaStream_t s);
 cudaError_t launch_up_add(const void* coarse, const void* skip, int B, int D, int H, int W, int C,

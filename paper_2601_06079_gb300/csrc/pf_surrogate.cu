@@ -55,7 +55,7 @@ struct Plan {
   int64_t V[4];  // voxels (all samples) per level
   // byte offsets into the workspace
   size_t x16, act[kNL], pool[4], up[4], y32, wf[kNL], wb[kNL];
-  size_t gy, g[4][3], grad, part, msep, loss, err, sig, sigp, res, resq;
+  size_t gy, g[4][3], grad, part, msep, loss, err, sig, sigo, sigp, res, resq;
   size_t total;
 };
 
@@ -81,6 +81,7 @@ Plan make_plan(int B, int D, int H, int W, bool training) {
   p.y32 = take(4 * p.V[0] * kCout);
   p.err = take(sizeof(int));
   p.sig = take(sizeof(float) * B);
+  p.sigo = take(sizeof(float) * B);
   p.sigp = take(sizeof(double) * kSigBlocks * B);
   for (int l = 0; l < kNL; ++l) {
     p.wf[l] = take(2 * w_count(l));
@@ -184,7 +185,9 @@ pf_status conv_layer(const Net& n, const float* params, int l) {
 // Input mode = number of previous states: 8 channels = U^n alone (output unit
 // out_scale); 16 = [U^n; U^{n-1}] and 24 = [U^n; U^{n-1}; U^{n-2}] (the network
 // sees U^n and the increments in units of the RMS of the last one; the output
-// unit is out_scale times that RMS, on top of linear or quadratic extrapolation).
+// unit is out_scale times that RMS on top of linear extrapolation, and
+// out_scale times the RMS of the second difference, floored at 1e-3 of the
+// increment unit, on top of quadratic extrapolation).
 int in_mode(int n_in) { return n_in / kNF - 1; }
 bool n_in_ok(int n_in) { return n_in == kNF || n_in == 2 * kNF || n_in == 3 * kNF; }
 
@@ -193,7 +196,7 @@ pf_status forward(const Net& n, const float* params, const float* x, int n_in, f
   const int64_t V0 = p.V[0] / p.B;
   const int mode = in_mode(n_in);
   SG_CUDA(pf::launch_incr_scale(x, kNF, p.B, V0, out_scale, mode, n.at<double>(p.sigp),
-                                kSigBlocks, n.at<float>(p.sig), n.s));
+                                kSigBlocks, n.at<float>(p.sig), n.at<float>(p.sigo), n.s));
   SG_CUDA(pf::launch_planar_to_ndhwc(x, n_in, kCin0, p.B, V0, mode, n.at<float>(p.sig),
                                      n.at<void>(p.x16), n.s));
   pf_status st;
@@ -304,7 +307,7 @@ pf_status pf_surrogate_predict(const float* params, float out_scale, const float
   if ((st = forward(n, params, x, n_in, out_scale)) != PF_OK) return st;
   SG_CUDA(pf::launch_ndhwc_to_planar_add(n.at<float>(p.y32), kCout, kNF, batch,
                                          (int64_t)d * h * w, x, n_in, in_mode(n_in),
-                                         n.at<float>(p.sig), out, n.s));
+                                         n.at<float>(p.sigo), out, n.s));
   return check_err(n);
 }
 
@@ -325,7 +328,7 @@ pf_status pf_surrogate_train_step(float* params, float out_scale, float* adam_m,
   const int64_t V = (int64_t)d * h * w;
   const float scale = (float)(1.0 / ((double)batch * V * kNF));
   SG_CUDA(pf::launch_mse(n.at<float>(p.y32), kCout, kNF, n_in, batch, d, h, w, x, y,
-                         in_mode(n_in), n.at<float>(p.sig), (float)stiff, scale,
+                         in_mode(n_in), n.at<float>(p.sigo), (float)stiff, scale,
                          n.at<float>(p.res), n.at<float>(p.resq), n.at<void>(p.gy),
                          n.at<double>(p.msep), n.at<double>(p.loss), n.s));
   float* grad = n.at<float>(p.grad);
@@ -357,7 +360,7 @@ pf_status pf_surrogate_loss_grad(const float* params, float out_scale, const flo
   const int64_t V = (int64_t)d * h * w;
   const float scale = (float)(1.0 / ((double)batch * V * kNF));
   SG_CUDA(pf::launch_mse(n.at<float>(p.y32), kCout, kNF, n_in, batch, d, h, w, x, y,
-                         in_mode(n_in), n.at<float>(p.sig), (float)stiff, scale,
+                         in_mode(n_in), n.at<float>(p.sigo), (float)stiff, scale,
                          n.at<float>(p.res), n.at<float>(p.resq), n.at<void>(p.gy),
                          n.at<double>(p.msep), n.at<double>(p.loss), n.s));
   if ((st = backward(n, grad)) != PF_OK) return st;

@@ -4,8 +4,9 @@ The solver generates its own training data: implicit trajectories of the
 Fan-Chen grain-growth model from seeded Voronoi starts.  A surrogate with
 history h (pf_surrogate_*) sees the current state and h earlier ones and
 predicts a correction to polynomial extrapolation through them (h = 2:
-U^{n+1} ~ 3 U^n - 3 U^{n-1} + U^{n-2} + s * net), in units s of the RMS of
-the last increment, so that the slow late stages of coarsening weigh as much
+U^{n+1} ~ 3 U^n - 3 U^{n-1} + U^{n-2} + c * net), in units c of the RMS of
+the second difference: where the trajectory is nearly quadratic the
+correction shrinks with it, and slow late stages of coarsening weigh as much
 in training as the fast early ones.  Its output is the first Newton iterate.
 While fewer earlier states exist the surrogate runs with what there is (the
 second step of a run uses one earlier state), and the plain start U^n is the

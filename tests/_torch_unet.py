@@ -57,6 +57,18 @@ def history_input(x):
     return torch.cat([st[0]] + [d / s for d in du], dim=1), s
 
 
+def output_scale(x, s):
+    """Output unit of the correction: s on top of linear extrapolation; on top of
+    quadratic extrapolation the RMS of the second difference U^n - 2 U^{n-1} +
+    U^{n-2} over the sample, floored at 1e-3 s."""
+    h = x.shape[1] // 8 - 1
+    if h < 2:
+        return s
+    st = [x[:, 8 * k:8 * (k + 1)] for k in range(3)]
+    r = (st[0] - 2 * st[1] + st[2]).pow(2).mean(dim=(1, 2, 3, 4), keepdim=True).sqrt()
+    return torch.maximum(r, 1e-3 * s)
+
+
 def extrapolate(x):
     """Linear (2 states) or quadratic (3 states) extrapolation to the next state."""
     h = x.shape[1] // 8 - 1

@@ -115,7 +115,8 @@ def test_whole_network_gradient_matches_torch_autograd_reference():
 def test_history_network_gradient_matches_torch_autograd_reference(hist):
     # inputs [U^n; U^{n-1}(; U^{n-2})]: the library normalises the increments by
     # the RMS of the last one, predicts a correction to linear / quadratic
-    # extrapolation in those units and weighs every sample alike
+    # extrapolation in units of that RMS / of the second difference's RMS, and
+    # weighs every sample alike
     import paper_2601_06079_gb300 as pf
     from tests import _torch_unet as R
     s = pf.Surrogate(history=hist)
@@ -128,11 +129,12 @@ def test_history_network_gradient_matches_torch_autograd_reference(hist):
     y = (u + 0.012 * du + 0.002 * torch.from_numpy(G.random_field(8, (2, 8, 16, 64, 64))).cuda())
     xd = x.cpu().double()
     h, sc = R.history_input(xd)
+    so = R.output_scale(xd, sc)  # the output unit: sc, or the second difference's RMS
     h = h.float().to(torch.bfloat16).double()  # the library rounds the network input to BF16
     for stiff in (0.0, 0.5):
         loss, g = s.loss_grad(x, y, stiff=stiff)
         p = s.params.detach().cpu().to(torch.bfloat16).double().requires_grad_(True)
-        lr = R.loss_history(p, h, xd, y.cpu().double(), sc, stiff)
+        lr = R.loss_history(p, h, xd, y.cpu().double(), so, stiff)
         lr.backward()
         gr, gg = p.grad.numpy(), g.cpu().double().numpy()
         assert abs(loss - lr.item()) <= 2e-2 * lr.item()
