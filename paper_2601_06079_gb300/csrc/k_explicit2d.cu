@@ -44,7 +44,7 @@ constexpr int kWarps = PF_WARPS;                  // warps per block, stacked in
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kGhost = 2;  // mirror frame around the working planes
 #ifndef PF_ROWS_AHEAD
-#define PF_ROWS_AHEAD 3
+#define PF_ROWS_AHEAD 6
 #endif
 #ifndef PF_MINB
 #define PF_MINB 1  // minimum resident blocks per SM asked of the register allocator
