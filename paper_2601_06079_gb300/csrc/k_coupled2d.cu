@@ -37,7 +37,7 @@ __device__ __forceinline__ int reflect(int k, int n) {
 
 __device__ __forceinline__ float gpt(int i) { return i ? kGHi : kGLo; }
 
-struct Tile {
+struct __align__(16) Tile {  // 8-byte aligned rows of c, e and mu (36 floats)
   float c[S2Y][S2X];      // shifted composition, 2-halo
   float e[S2Y][S2X];      // order parameter, 2-halo
   float mu[S2Y][S2X];     // chemical potential on the 1-halo nodes (same indexing)
@@ -65,6 +65,11 @@ __device__ __forceinline__ float phi(u64 v) {
 __device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
   u64 d;
   asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ u64 add2(u64 a, u64 b) {
+  u64 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
   return d;
 }
 __device__ __forceinline__ u64 sub2(u64 a, u64 b) {
@@ -153,26 +158,48 @@ __global__ void __launch_bounds__(kThreads) k_coupled2d(const Coupled2DArgs a) {
   }
   __syncthreads();
 
-  for (int i = threadIdx.x; i < TX * TY; i += kThreads) {
-    const int lx = i % TX, ly = i / TX;
+  // the updates, two adjacent nodes (x, x+1) per thread: one 64-bit load
+  // fetches a row's pair and two scalars its outer neighbours, and the 9-point
+  // stencils of mu and eta run on packed pairs
+  for (int i = threadIdx.x; i < TX * TY / 2; i += kThreads) {
+    const int lx = 2 * (i % (TX / 2)), ly = i / (TX / 2);
     const int gx = x0 + lx, gy = y0 + ly;
     if (gx >= a.nx || gy >= a.ny) continue;
-    const int x = lx + 2, y = ly + 2;
-    const Stencil2D& kc = a.k2;  // -dt M_c / m K
-    const float lap_mu = kc.c0 * T.mu[y][x] + kc.cx * (T.mu[y][x - 1] + T.mu[y][x + 1]) +
-                         kc.cy * (T.mu[y - 1][x] + T.mu[y + 1][x]) +
-                         kc.cd * (T.mu[y - 1][x - 1] + T.mu[y - 1][x + 1] + T.mu[y + 1][x - 1] +
-                                  T.mu[y + 1][x + 1]);
-    const Stencil2D& ke = a.k1;  // kappa / m K
-    const float lap_e = ke.c0 * T.e[y][x] + ke.cx * (T.e[y][x - 1] + T.e[y][x + 1]) +
-                        ke.cy * (T.e[y - 1][x] + T.e[y + 1][x]) +
-                        ke.cd * (T.e[y - 1][x - 1] + T.e[y - 1][x + 1] + T.e[y + 1][x - 1] +
-                                 T.e[y + 1][x + 1]);
-    const float re = T.Ee[0][y][x] + T.Ee[1][y][x - 1] + T.Ee[2][y - 1][x] +
-                     T.Ee[3][y - 1][x - 1] + lap_e;
+    const int x = lx + 2, y = ly + 2;  // x even: the pair is 8-byte aligned
+    // packed 9-point stencil on rows y-1 .. y+1 of a 36-wide plane; ctr_out
+    // receives the centre pair of row y
+    auto stencil_pair = [&](const float (*V)[S2X], const Stencil2D& k, u64& ctr_out) {
+      u64 ctr[3], hs[3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const u64 P = *reinterpret_cast<const u64*>(&V[y - 1 + r][x]);
+        const float l = V[y - 1 + r][x - 1], rr = V[y - 1 + r][x + 2];
+        ctr[r] = P;
+        hs[r] = pk(l + phi(P), plo(P) + rr);  // west + east of each node
+      }
+      ctr_out = ctr[1];
+      u64 o = mul2(bc(k.c0), ctr[1]);
+      o = fma2(bc(k.cx), hs[1], o);
+      o = fma2(bc(k.cy), add2(ctr[0], ctr[2]), o);
+      return fma2(bc(k.cd), add2(hs[0], hs[2]), o);
+    };
+    u64 centre, e_c;
+    const u64 lap_mu = stencil_pair(T.mu, a.k2, centre);  // -dt M_c / m K mu
+    const u64 lap_e = stencil_pair(T.e, a.k1, e_c);       // kappa / m K eta (e_c: eta itself)
+    // element terms of the eta residual around each node (rows of 35: scalar)
+    const float re0 = T.Ee[0][y][x] + T.Ee[1][y][x - 1] + T.Ee[2][y - 1][x] + T.Ee[3][y - 1][x - 1];
+    const float re1 = T.Ee[0][y][x + 1] + T.Ee[1][y][x] + T.Ee[2][y - 1][x + 1] + T.Ee[3][y - 1][x];
+    const u64 re = add2(pk(re0, re1), lap_e);
+    const u64 cc = *reinterpret_cast<const u64*>(&T.c[y][x]);
+    const u64 oc = add2(cc, lap_mu);
+    const u64 oe = fma2(bc(a.neg_dt_meta), re, e_c);
     const int64_t g = (int64_t)gy * a.nx + gx;
-    a.out[g] = T.c[y][x] + lap_mu;
-    a.out[N + g] = fmaf(a.neg_dt_meta, re, T.e[y][x]);
+    a.out[g] = plo(oc);
+    a.out[N + g] = plo(oe);
+    if (gx + 1 < a.nx) {
+      a.out[g + 1] = phi(oc);
+      a.out[N + g + 1] = phi(oe);
+    }
   }
 }
 
