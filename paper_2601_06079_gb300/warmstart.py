@@ -10,7 +10,7 @@ correction shrinks with it, and slow late stages of coarsening weigh as much
 in training as the fast early ones.  Its output is the first Newton iterate.
 While fewer earlier states exist the surrogate runs with what there is (the
 second step of a run uses one earlier state), and the plain start U^n is the
-fallback on the first step and without a surrogate.  Newton's converged residual is the judge: every start
+fallback on the first step and without a surrogate.  Newton's converged residual is the measure: every start
 is iterated to the same tolerance, so the gain shows up as fewer Newton /
 GMRES iterations and less wall time at the same accuracy.
 
