@@ -290,13 +290,9 @@ static cudaError_t conv_launch(const __nv_bfloat16* x, const __nv_bfloat16* wt, 
                                int relu, __nv_bfloat16* y16, float* y32, int B, int D, int H, int W,
                                int grid, cudaStream_t s) {
   const int smem = (27 * COUT * (CIN + 8) + kHalo * (CIN + 8)) * 2;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_conv3d<CIN, COUT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static std::atomic<unsigned long long> raised{0};
+  const cudaError_t e = raise_smem_limit(k_conv3d<CIN, COUT>, smem, raised);
+  if (e != cudaSuccess) return e;
   const int ntiles = B * (D / TZ) * (H / TY) * (W / TX);
   k_conv3d<CIN, COUT><<<grid < ntiles ? grid : ntiles, kThreads, smem, s>>>(x, wt, bias, relu, y16,
                                                                           y32, B, D, H, W);

@@ -403,15 +403,12 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-int sm_count() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-      n = 148;
-  }
-  return n;
+// streaming multiprocessors of the current device
+cudaError_t sm_count(int& n) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return e == cudaSuccess && n <= 0 ? cudaErrorInvalidDevice : e;
 }
 
 template <int CIN, int COUT>
@@ -441,15 +438,13 @@ cudaError_t tc_launch(const void* x, const void* wt, const float* bias, int relu
           CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_conv3d_tc<CIN, COUT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static std::atomic<unsigned long long> raised{0};
+  cudaError_t e = raise_smem_limit(k_conv3d_tc<CIN, COUT>, C::kSmem, raised);
+  int sms = 0;
+  if (e == cudaSuccess) e = sm_count(sms);
+  if (e != cudaSuccess) return e;
   const int ntiles = B * (D / TZ) * (H / TY) * ((W + TX - 1) / TX);
-  const int grid = ntiles < sm_count() ? ntiles : sm_count();
+  const int grid = ntiles < sms ? ntiles : sms;
   k_conv3d_tc<CIN, COUT><<<grid, kThreads, C::kSmem, s>>>(
       map, (const __nv_bfloat16*)wt, bias, relu, (__nv_bfloat16*)y16, y32, B, D, H, W, err,
       selftest);

@@ -351,13 +351,9 @@ cudaError_t launch_nf(const Implicit3DArgs& a, cudaStream_t s) {
   constexpr int NP = (NF + 1) / 2;
   const size_t smem = sizeof(u64) * (2 * NP * kNodes + 8 * kElems) +
                       sizeof(float) * kElems * 8 * (kJVP ? 2 : 1);
-  static bool configured[2] = {false, false};
-  if (!configured[kJVP]) {
-    cudaError_t e = cudaFuncSetAttribute(k_implicit3d<NF, kJVP>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured[kJVP] = true;
-  }
+  static std::atomic<unsigned long long> raised{0};
+  const cudaError_t e = raise_smem_limit(k_implicit3d<NF, kJVP>, (int)smem, raised);
+  if (e != cudaSuccess) return e;
   const int tiles =
       ((a.nx + kTX - 1) / kTX) * ((a.ny + kTY - 1) / kTY) * ((a.nz + kTZ - 1) / kTZ);
   k_implicit3d<NF, kJVP><<<tiles, kThreads, smem, s>>>(a);

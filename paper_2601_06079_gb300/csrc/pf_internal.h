@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 
 #include "../../include/pf.h"
@@ -14,6 +15,22 @@ namespace pf {
 // g_lo = N_0 at the upper point = N_1 at the lower point, and vice versa.
 constexpr float kGHi = 0.78867513459481288225f;
 constexpr float kGLo = 0.21132486540518711775f;
+
+// Raises a kernel's dynamic shared-memory limit to `bytes` on the current
+// device.  The attribute belongs to the device, so `done` (one per kernel
+// instantiation) records the devices 0..63 already raised; others are set on
+// every call.  Safe to call from several host threads.
+template <class K>
+inline cudaError_t raise_smem_limit(K* kernel, int bytes, std::atomic<unsigned long long>& done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = dev >= 0 && dev < 64 ? 1ull << dev : 0ull;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_acq_rel);
+  return e;
+}
 
 // Assembled 9-point Q1 stiffness stencil on a uniform 2-D grid, pre-scaled:
 // (K v)_i = c0 v_i + cx (v_W + v_E) + cy (v_S + v_N) + cd (v_SW + v_SE + v_NW + v_NE).
