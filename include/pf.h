@@ -112,8 +112,20 @@ typedef struct {
 pf_status pf_create_mesh(pf_ctx** out, int dim, const int64_t nodes[3], const double h[3],
                          pf_model model, int n_fields, void* stream, size_t* workspace_bytes);
 
-/* Bind caller-owned device memory (>= workspace_bytes, 256-byte aligned) as the
- * context's scratch space.  The memory must outlive the context's use of it. */
+/* Bytes of the leading part of the workspace that explicit steps (every form,
+ * Eq. 12), pf_energy, pf_jvp, pf_implicit_residual and pf_adjoint use: the 2-D
+ * working planes, the reduction buffers and, in 3-D, one residual vector.  The
+ * implicit step's vectors (Eq. 14: iterate, U^n, correction, Krylov basis) take
+ * the rest of workspace_bytes.  Host only; *bytes (host) out. */
+pf_status pf_explicit_workspace(const pf_ctx* ctx, size_t* bytes);
+
+/* Bind caller-owned device memory (256-byte aligned) as the context's scratch
+ * space.  bytes >= the workspace_bytes of pf_create_mesh serves every call;
+ * bytes >= pf_explicit_workspace serves every call but pf_step_implicit and
+ * pf_implicit_adjoint, which then return PF_ERR_STATE (nothing enqueued) until a
+ * full workspace is bound.  Smaller: PF_ERR_ARG.  Ensembles need their whole
+ * workspace_bytes.  Binding again replaces the previous memory (captured CUDA
+ * graphs are dropped).  The memory must outlive the context's use of it. */
 pf_status pf_bind_workspace(pf_ctx* ctx, void* dev_ptr, size_t bytes);
 
 /* Set the material and time-step parameters theta (Eq. 11, 15).  Host pointer p

@@ -19,6 +19,7 @@ from . import _lib
 from ._lib import (PF_ENS_PER_STEP, PF_ENS_PERSISTENT, PF_ENS_PLAIN,  # noqa: F401
                    PF_MODEL_AC, PF_MODEL_CH, PF_MODEL_COUPLED, PF_MODEL_FANCHEN, pf_adjoint,
                    pf_adjoint_workspace, pf_barrier_selftest, pf_bind_workspace,
+                   pf_explicit_workspace,
                    pf_create_ensemble, pf_create_mesh, pf_destroy, pf_set_ensemble_params,
                    pf_step_ensemble, pf_tune_ensemble, pf_surrogate_param_count,
                    pf_surrogate_workspace, pf_surrogate_predict, pf_surrogate_train_step,
@@ -43,7 +44,9 @@ class Solver:
     shape: node counts (ny, nx) or (nz, ny, nx); h: spacing (scalar or per
     axis, x first); model: 'ac' | 'ch' | 'fanchen' | 'coupled' (2-D, state
     [c; eta] with n_fields = 2).  The workspace is a torch uint8 tensor owned
-    by this object and bound to the library context.
+    by this object and bound to the library context: at first the part that
+    explicit steps and diagnostics use (pf_explicit_workspace), grown to the
+    whole workspace before the first implicit step or implicit adjoint.
     """
 
     def __init__(self, shape, h=1.0, model="ac", n_fields=1, device="cuda", stream=None):
@@ -63,10 +66,23 @@ class Solver:
                                            self.stream.cuda_stream)
         if st != 0:
             raise PFError(st, "pf_create_mesh rejected the mesh/model")
-        self._ws = torch.empty(max(ws, 256), dtype=torch.uint8, device=self.device)
-        self._check(pf_bind_workspace(self._ctx, self._ws.data_ptr(), self._ws.numel()))
+        self._ws_all = ws
+        st, ws_explicit = pf_explicit_workspace(self._ctx)
+        self._check(st)
+        self._bind(ws_explicit)
         self._params = None
         self._keep = None
+
+    def _bind(self, nbytes):
+        self._ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
+        self._check(pf_bind_workspace(self._ctx, self._ws.data_ptr(), self._ws.numel()))
+
+    def _implicit_workspace(self):
+        """Grow the bound workspace to the implicit step's size (once)."""
+        if self._ws.numel() < self._ws_all:
+            self.stream.synchronize()  # earlier work may still use the old memory
+            self._ws = None
+            self._bind(self._ws_all)
 
     def _check(self, st):
         if st != 0:
@@ -114,6 +130,7 @@ class Solver:
                                    gmres_rtol)
         stats = _lib.pf_newton_stats()
         gp = self._state(guess) if guess is not None else 0
+        self._implicit_workspace()
         st = pf_step_implicit(self._ctx, self._state(state), n_steps, gp, opts, stats)
         out = {k: getattr(stats, k) for k, _ in _lib.pf_newton_stats._fields_}
         if check:
@@ -139,6 +156,7 @@ class Solver:
         C = _lib.C
         nb = C.c_size_t(0)
         self._check(_lib.lib().pf_implicit_adjoint_workspace(self._ctx, n_steps, C.byref(nb)))
+        self._implicit_workspace()
         ws = torch.empty(max(nb.value, 256), dtype=torch.uint8, device=self.device)
         opts = _lib.pf_newton_opts(max_newton, gmres_restart, gmres_max_iters, newton_rtol,
                                    gmres_rtol)

@@ -84,6 +84,8 @@ def lib():
                                      C.POINTER(C.c_size_t)]
         L.pf_bind_workspace.restype = st
         L.pf_bind_workspace.argtypes = [ctx, C.c_void_p, C.c_size_t]
+        L.pf_explicit_workspace.restype = st
+        L.pf_explicit_workspace.argtypes = [ctx, C.POINTER(C.c_size_t)]
         L.pf_set_params.restype = st
         L.pf_set_params.argtypes = [ctx, C.POINTER(pf_params)]
         L.pf_step_explicit.restype = st
@@ -176,7 +178,8 @@ def lib():
 
 def exported_symbols():
     """Names declared in include/pf.h (checked against the .so by the tests)."""
-    return ["pf_create_mesh", "pf_bind_workspace", "pf_set_params", "pf_step_explicit",
+    return ["pf_create_mesh", "pf_explicit_workspace", "pf_bind_workspace", "pf_set_params",
+            "pf_step_explicit",
             "pf_set_form",
             "pf_step_implicit", "pf_jvp", "pf_implicit_residual", "pf_adjoint_workspace",
             "pf_adjoint", "pf_implicit_adjoint_workspace", "pf_implicit_adjoint",
@@ -199,6 +202,12 @@ def pf_create_mesh(dim, nodes, h, model, n_fields, stream):
     s = lib().pf_create_mesh(C.byref(ctx), dim, n, hh, model, n_fields, C.c_void_p(stream),
                              C.byref(ws))
     return s, ctx, ws.value
+
+
+def pf_explicit_workspace(ctx):
+    b = C.c_size_t(0)
+    s = lib().pf_explicit_workspace(ctx, C.byref(b))
+    return s, b.value
 
 
 def pf_bind_workspace(ctx, ptr, nbytes):

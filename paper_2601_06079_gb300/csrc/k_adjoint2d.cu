@@ -165,7 +165,8 @@ __device__ __forceinline__ void mob_at(const Tile& T, int ey, int ex, float M, f
 
 __global__ void __launch_bounds__(kThreads) k_ch_mob_step(const ChMobArgs a, float* out) {
   __shared__ Tile T;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int x0 = blockIdx.x * TX, y0 = block_row() * TY;
+  if (y0 >= a.ny) return;
   stage_and_mu(T, a, nullptr, x0, y0);
   // K_M mu on the elements touching the tile nodes (lower-left 1 .. T+1 in 2-halo coords)
   for (int i = threadIdx.x; i < (TX + 1) * (TY + 1); i += kThreads) {
@@ -194,7 +195,8 @@ __global__ void __launch_bounds__(kThreads) k_ch_adj_step(const ChMobArgs a, con
                                                           double* acc) {
   __shared__ Tile T;
   __shared__ double red[3][kThreads / 32];
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int x0 = blockIdx.x * TX, y0 = block_row() * TY;
+  if (y0 >= a.ny) return;
   stage_and_mu(T, a, yin, x0, y0);
   // K_M y on elements touching the 1-halo nodes; mobility gradient on those
   // touching the tile nodes (mu is known on the 1-halo nodes only)
@@ -287,7 +289,7 @@ __global__ void __launch_bounds__(kThreads) k_ch_adj_step(const ChMobArgs a, con
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    const int b = blockIdx.y * gridDim.x + blockIdx.x;
+    const int b = block_row() * gridDim.x + blockIdx.x;
     double s[3] = {0, 0, 0};
     for (int w = 0; w < kThreads / 32; ++w)
       for (int j = 0; j < 3; ++j) s[j] += red[j][w];
@@ -368,14 +370,14 @@ cudaError_t launch_add(const float* in, float* out, int64_t n, float add, cudaSt
 int ch_mob_blocks(int nx, int ny) { return ((nx + TX - 1) / TX) * ((ny + TY - 1) / TY); }
 
 cudaError_t launch_ch_mob_step(const ChMobArgs& a, float* out, cudaStream_t s) {
-  const dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY);
+  const dim3 grid = row_grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY);
   k_ch_mob_step<<<grid, kThreads, 0, s>>>(a, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_ch_adj_step(const ChMobArgs& a, const float* yin, float* yout, double* grad_m,
                                double* acc, cudaStream_t s) {
-  const dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY);
+  const dim3 grid = row_grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY);
   k_ch_adj_step<<<grid, kThreads, 0, s>>>(a, yin, yout, grad_m, acc);
   return cudaGetLastError();
 }

@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(kWarps * 32, PF_MINB) k_explicit2d(const Expli
   asm volatile("griddepcontrol.wait;" ::: "memory");  // the previous step is complete
 #endif
   const int warp = threadIdx.x >> 5;
-  const int y0 = (blockIdx.y * kWarps + warp) * kTY;
+  const int y0 = (block_row() * kWarps + warp) * kTY;
   if (y0 < a.ny) sweep_task<kCH, kIso, kTY>(a, a.in, a.out, Coef{a.pair}, blockIdx.x, y0);
 #if PF_PDL
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -444,35 +444,40 @@ __global__ void k_barrier_selftest(unsigned* bar, long long limit, int extra) {
 }
 
 // all instances' plain states (packed) <-> their padded working planes
+// (grid.y strides over the instances, so any count fits in one launch)
 __global__ void k_ens_to_work(const float* __restrict__ packed, const int64_t* __restrict__ off,
-                              const Explicit2DArgs* inst, float sub) {
-  const Explicit2DArgs& a = inst[blockIdx.y];
-  const int nx = a.nx, ny = a.ny;
-  const int64_t pitch = a.pitch, n = pitch * (int64_t)a.rows;
-  const float* in = packed + off[blockIdx.y];
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int u = (int)(i % pitch), v = (int)(i / pitch);
-    const int x = u - kGhost, y = v - kGhost;
-    float val = 0.0f;
-    if (x >= -kGhost && x < nx + kGhost && y >= -kGhost && y < ny + kGhost)
-      val = in[(int64_t)reflect_row(y, ny) * nx + reflect_col(x, nx)] - sub;
-    const_cast<float*>(a.in)[i] = val;
-    a.out[i] = val;
+                              const Explicit2DArgs* inst, int count, float sub) {
+  for (int k = blockIdx.y; k < count; k += gridDim.y) {
+    const Explicit2DArgs& a = inst[k];
+    const int nx = a.nx, ny = a.ny;
+    const int64_t pitch = a.pitch, n = pitch * (int64_t)a.rows;
+    const float* in = packed + off[k];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+      const int u = (int)(i % pitch), v = (int)(i / pitch);
+      const int x = u - kGhost, y = v - kGhost;
+      float val = 0.0f;
+      if (x >= -kGhost && x < nx + kGhost && y >= -kGhost && y < ny + kGhost)
+        val = in[(int64_t)reflect_row(y, ny) * nx + reflect_col(x, nx)] - sub;
+      const_cast<float*>(a.in)[i] = val;
+      a.out[i] = val;
+    }
   }
 }
 
 __global__ void k_ens_from_work(float* __restrict__ packed, const int64_t* __restrict__ off,
-                                const Explicit2DArgs* inst, int parity, float add) {
-  const Explicit2DArgs& a = inst[blockIdx.y];
-  const int nx = a.nx;
-  const int64_t n = (int64_t)nx * a.ny;
-  const float* work = parity ? a.out : a.in;
-  float* out = packed + off[blockIdx.y];
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(i % nx), y = (int)(i / nx);
-    out[i] = work[(int64_t)(y + kGhost) * a.pitch + x + kGhost] + add;
+                                const Explicit2DArgs* inst, int count, int parity, float add) {
+  for (int k = blockIdx.y; k < count; k += gridDim.y) {
+    const Explicit2DArgs& a = inst[k];
+    const int nx = a.nx;
+    const int64_t n = (int64_t)nx * a.ny;
+    const float* work = parity ? a.out : a.in;
+    float* out = packed + off[k];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+      const int x = (int)(i % nx), y = (int)(i / nx);
+      out[i] = work[(int64_t)(y + kGhost) * a.pitch + x + kGhost] + add;
+    }
   }
 }
 
@@ -514,7 +519,7 @@ constexpr int kTYCh = PF_TY_CH;
 
 template <bool kCH, bool kIso, int kTY>
 cudaError_t launch(const Explicit2DArgs& a, cudaStream_t s) {
-  const dim3 grid((a.nx + kOutCols - 1) / kOutCols, (a.ny + kWarps * kTY - 1) / (kWarps * kTY));
+  const dim3 grid = row_grid((a.nx + kOutCols - 1) / kOutCols, (a.ny + kWarps * kTY - 1) / (kWarps * kTY));
 #if PF_PDL
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
@@ -610,13 +615,15 @@ cudaError_t launch_ensemble_persistent(const EnsTask* tasks, int ntasks, const E
 
 cudaError_t launch_ens_to_work(const float* packed, const int64_t* off, const Explicit2DArgs* inst,
                                int count, float shift, cudaStream_t s) {
-  k_ens_to_work<<<dim3(64, count), 256, 0, s>>>(packed, off, inst, shift);
+  const unsigned gy = count < (int)kMaxGridY ? (unsigned)count : kMaxGridY;
+  k_ens_to_work<<<dim3(64, gy), 256, 0, s>>>(packed, off, inst, count, shift);
   return cudaGetLastError();
 }
 
 cudaError_t launch_ens_from_work(float* packed, const int64_t* off, const Explicit2DArgs* inst,
                                  int count, int parity, float shift, cudaStream_t s) {
-  k_ens_from_work<<<dim3(64, count), 256, 0, s>>>(packed, off, inst, parity, shift);
+  const unsigned gy = count < (int)kMaxGridY ? (unsigned)count : kMaxGridY;
+  k_ens_from_work<<<dim3(64, gy), 256, 0, s>>>(packed, off, inst, count, parity, shift);
   return cudaGetLastError();
 }
 

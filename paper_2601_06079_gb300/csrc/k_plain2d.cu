@@ -66,7 +66,7 @@ __device__ float fprime_quad(const float* __restrict__ p, int i, int j, int nx, 
 
 __global__ void __launch_bounds__(kBX* kBY) k_plain_mu(const float* __restrict__ d, Explicit2DArgs a,
                                                       float* __restrict__ mu) {
-  const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
+  const int i = blockIdx.x * kBX + threadIdx.x, j = block_row() * kBY + threadIdx.y;
   if (i >= a.nx || j >= a.ny) return;
   mu[(int64_t)j * a.nx + i] = fprime_quad(d, i, j, a.nx, a.ny, a) + stencil(d, i, j, a.nx, a.ny, a.k1);
 }
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(kBX* kBY) k_plain_mu(const float* __restrict__
 __global__ void __launch_bounds__(kBX* kBY) k_plain_c(const float* __restrict__ d,
                                                      const float* __restrict__ mu, Explicit2DArgs a,
                                                      float* __restrict__ out) {
-  const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
+  const int i = blockIdx.x * kBX + threadIdx.x, j = block_row() * kBY + threadIdx.y;
   if (i >= a.nx || j >= a.ny) return;
   const int64_t k = (int64_t)j * a.nx + i;
   out[k] = d[k] + stencil(mu, i, j, a.nx, a.ny, a.k2);
@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(kBX* kBY) k_plain_c(const float* __restrict__ 
 
 __global__ void __launch_bounds__(kBX* kBY) k_plain_ac(const float* __restrict__ d, Explicit2DArgs a,
                                                       float* __restrict__ out) {
-  const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
+  const int i = blockIdx.x * kBX + threadIdx.x, j = block_row() * kBY + threadIdx.y;
   if (i >= a.nx || j >= a.ny) return;
   const int64_t k = (int64_t)j * a.nx + i;
   out[k] = d[k] + fprime_quad(d, i, j, a.nx, a.ny, a) + stencil(d, i, j, a.nx, a.ny, a.k1);
@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(kBX* kBY) k_plain_ac(const float* __restrict__
 
 cudaError_t launch_plain2d(bool ch, const Explicit2DArgs& a, const float* d, float* mu, float* out,
                            cudaStream_t s) {
-  const dim3 blk(kBX, kBY), grd((a.nx + kBX - 1) / kBX, (a.ny + kBY - 1) / kBY);
+  const dim3 blk(kBX, kBY), grd = row_grid((a.nx + kBX - 1) / kBX, (a.ny + kBY - 1) / kBY);
   if (ch) {
     k_plain_mu<<<grd, blk, 0, s>>>(d, a, mu);
     cudaError_t e = cudaGetLastError();

@@ -22,7 +22,9 @@ struct pf_ctx {
   int nf = 1;
   cudaStream_t stream = nullptr;
 
-  size_t ws_bytes = 0;
+  size_t ws_bytes = 0;     // workspace for every operation
+  size_t ws_explicit = 0;  // prefix that explicit steps and diagnostics use
+  size_t ws_bound = 0;     // bytes bound by pf_bind_workspace
   char* ws = nullptr;
   pf_params par{};
   bool par_set = false;
@@ -102,8 +104,13 @@ pf_status cuda_fail(pf_ctx* c, cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_fail(c, e_, #call); \
   } while (0)
 
+// Workspace layout.  Everything explicit steps and the diagnostics touch
+// comes first (`explicit_total` bytes): the 2-D working planes, the reduction
+// buffers and, in 3-D, the residual vector G.  The implicit step's vectors
+// (U, U^n, the Newton correction and the Krylov basis) follow, so a mesh that
+// is only stepped explicitly binds the prefix alone.
 struct Layout {
-  size_t a, b, partials, result, vec, vecs, small, total;
+  size_t a, b, partials, result, vec, vecs, small, explicit_total, total;
 };
 
 constexpr int kVec3d = 4;  // U, U^n, G, D before the Krylov basis
@@ -131,11 +138,6 @@ Layout layout(const pf_ctx* c) {
     L.b = off;
     off += field;
   }
-  if (has_implicit(c)) {
-    L.vec = align_up(sizeof(float) * (size_t)nnodes(c) * imp_nf(c), 256);
-    L.vecs = off;
-    off += L.vec * (kVec3d + pf::kMaxBasis);
-  }
   L.partials = off;
   const size_t np = (size_t)std::max(2 * 1024, pf::krylov_partial_blocks() * pf::kMaxBasis);
   off += align_up(sizeof(double) * np, 256);
@@ -143,8 +145,26 @@ Layout layout(const pf_ctx* c) {
   off += 256;
   L.small = off;
   off += align_up(sizeof(double) * 4 * pf::kMaxBasis, 256);
+  L.explicit_total = off;
+  if (has_implicit(c)) {
+    L.vec = align_up(sizeof(float) * (size_t)nnodes(c) * imp_nf(c), 256);
+    L.vecs = off;  // G first: the 3-D explicit step needs it
+    if (c->dim == 3) L.explicit_total = off + L.vec;
+    off += L.vec * (kVec3d + pf::kMaxBasis);
+  }
   L.total = off;
   return L;
+}
+
+// true once the bound workspace covers the implicit step's vectors
+bool implicit_bound(const pf_ctx* c) { return c->ws && c->ws_bound >= c->ws_bytes; }
+
+pf_status need_implicit_ws(pf_ctx* c) {
+  if (implicit_bound(c)) return PF_OK;
+  return fail(c, PF_ERR_STATE,
+              "the bound workspace (%zu bytes) covers explicit steps only; implicit steps "
+              "need %zu bytes",
+              c->ws_bound, c->ws_bytes);
 }
 
 // 9-point Q1 stiffness stencil for spacing hx, hy (2x2 Gauss is exact for it).
@@ -551,9 +571,17 @@ pf_status pf_create_mesh(pf_ctx** out, int dim, const int64_t nodes[3], const do
   c->model = model;
   c->nf = n_fields;
   c->stream = (cudaStream_t)stream;
-  c->ws_bytes = layout(c).total;
+  const Layout L = layout(c);
+  c->ws_bytes = L.total;
+  c->ws_explicit = L.explicit_total;
   *workspace_bytes = c->ws_bytes;
   *out = c;
+  return PF_OK;
+}
+
+pf_status pf_explicit_workspace(const pf_ctx* c, size_t* bytes) {
+  if (!c || !bytes) return PF_ERR_ARG;
+  *bytes = c->ens_count > 0 ? c->ws_bytes : c->ws_explicit;
   return PF_OK;
 }
 
@@ -561,8 +589,10 @@ pf_status pf_bind_workspace(pf_ctx* c, void* dev_ptr, size_t bytes) {
   if (!c) return PF_ERR_ARG;
   if (!dev_ptr || (uintptr_t)dev_ptr % 256 != 0)
     return fail(c, PF_ERR_ARG, "workspace must be a non-null 256-byte aligned device pointer");
-  if (bytes < c->ws_bytes)
-    return fail(c, PF_ERR_ARG, "workspace too small: %zu < %zu bytes", bytes, c->ws_bytes);
+  const size_t need = c->ens_count > 0 ? c->ws_bytes : c->ws_explicit;
+  if (bytes < need)
+    return fail(c, PF_ERR_ARG, "workspace too small: %zu < %zu bytes", bytes, need);
+  c->ws_bound = bytes;
   if (c->ens_count > 0) {
     const EnsLayout E = ens_layout(c);
     c->ws = (char*)dev_ptr;
@@ -587,13 +617,16 @@ pf_status pf_bind_workspace(pf_ctx* c, void* dev_ptr, size_t bytes) {
     c->buf_a = (float*)(c->ws + L.a);
     c->buf_b = (float*)(c->ws + L.b);
   }
+  c->u = c->un = c->g = c->d = c->basis = nullptr;
   if (has_implicit(c)) {
     char* v = c->ws + L.vecs;
-    c->u = (float*)v;
-    c->un = (float*)(v + L.vec);
-    c->g = (float*)(v + 2 * L.vec);
-    c->d = (float*)(v + 3 * L.vec);
-    c->basis = (float*)(v + kVec3d * L.vec);
+    if (bytes >= L.vecs + L.vec) c->g = (float*)v;
+    if (implicit_bound(c)) {
+      c->u = (float*)(v + L.vec);
+      c->un = (float*)(v + 2 * L.vec);
+      c->d = (float*)(v + 3 * L.vec);
+      c->basis = (float*)(v + kVec3d * L.vec);
+    }
     c->ldv = (int64_t)(L.vec / sizeof(float));
   }
   destroy_graph(c);
@@ -844,6 +877,7 @@ pf_status pf_step_implicit(pf_ctx* c, float* state, int64_t n_steps, const float
   if (st != PF_OK) return st;
   if (!has_implicit(c))
     return fail(c, PF_ERR_ARG, "pf_step_implicit supports 3-D meshes and 2-D AC / CH");
+  if ((st = need_implicit_ws(c)) != PF_OK) return st;
   if (!state) return fail(c, PF_ERR_ARG, "state is NULL");
   if (c->par.mobility_field)
     return fail(c, PF_ERR_ARG, "pf_step_implicit has no per-node mobility field");
@@ -1326,6 +1360,7 @@ pf_status pf_implicit_adjoint(pf_ctx* c, const float* U0, int64_t n_steps,
   if (st != PF_OK) return st;
   size_t need = 0;
   if ((st = pf_implicit_adjoint_workspace(c, n_steps, &need)) != PF_OK) return st;
+  if ((st = need_implicit_ws(c)) != PF_OK) return st;
   if (!U0 || !ws || !objective || !grads) return fail(c, PF_ERR_ARG, "null argument");
   if (bytes < need || (uintptr_t)ws % 256)
     return fail(c, PF_ERR_ARG, "implicit adjoint workspace too small or misaligned (%zu < %zu)",

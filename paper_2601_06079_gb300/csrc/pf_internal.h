@@ -16,6 +16,19 @@ namespace pf {
 constexpr float kGHi = 0.78867513459481288225f;
 constexpr float kGLo = 0.21132486540518711775f;
 
+// 2-D launches put rows of blocks on grid.y, which holds at most 65,535; a
+// taller mesh (up to 2^20 node rows) continues on grid.z.  block_row() is the
+// block's row; rows past the last (when `rows` is not a multiple of the y
+// extent) must return at once.
+constexpr unsigned kMaxGridY = 65535;
+inline dim3 row_grid(unsigned cols, unsigned rows) {
+  const unsigned y = rows == 0 ? 1 : (rows < kMaxGridY ? rows : kMaxGridY);
+  return dim3(cols, y, (rows + y - 1) / y);
+}
+#ifdef __CUDACC__
+__device__ __forceinline__ int block_row() { return (int)(blockIdx.z * gridDim.y + blockIdx.y); }
+#endif
+
 // Raises a kernel's dynamic shared-memory limit to `bytes` on the current
 // device.  The attribute belongs to the device, so `done` (one per kernel
 // instantiation) records the devices 0..63 already raised; others are set on

@@ -43,7 +43,9 @@ def test_create_mesh_validates_on_host(libpf):
     assert _lib.pf_step_explicit(ctx, 0x1000, 1) == _lib.PF_ERR_STATE
     assert "workspace" in _lib.pf_last_error(ctx)
     assert _lib.pf_bind_workspace(ctx, 0x1001, ws) == _lib.PF_ERR_ARG  # misaligned
-    assert _lib.pf_bind_workspace(ctx, 0x1000, ws - 1) == _lib.PF_ERR_ARG  # too small
+    st, ex = _lib.pf_explicit_workspace(ctx)
+    assert st == 0 and 2 * 64 * 64 * 4 <= ex < ws
+    assert _lib.pf_bind_workspace(ctx, 0x1000, ex - 1) == _lib.PF_ERR_ARG  # too small
     _lib.pf_destroy(ctx)
     for bad in ([1, 64], [64, 0]):
         st, _, _ = _lib.pf_create_mesh(2, bad, [1.0, 1.0], _lib.PF_MODEL_AC, 1, 0)
@@ -53,3 +55,41 @@ def test_create_mesh_validates_on_host(libpf):
     st, _, _ = _lib.pf_create_mesh(2, [8, 8], [1.0, -1.0], _lib.PF_MODEL_AC, 1, 0)
     assert st == _lib.PF_ERR_ARG
     _lib.pf_destroy(None)
+
+
+def test_explicit_only_workspace_refuses_implicit_steps_on_host(libpf):
+    # the explicit prefix serves explicit steps; the implicit step and the
+    # implicit adjoint report PF_ERR_STATE before enqueueing anything
+    from paper_2601_06079_gb300 import _lib
+    _lib.lib()
+    for dim, nodes, model in [(2, [64, 48], _lib.PF_MODEL_CH), (2, [64, 48], _lib.PF_MODEL_AC),
+                              (3, [16, 16, 16], _lib.PF_MODEL_FANCHEN)]:
+        st, ctx, ws = _lib.pf_create_mesh(dim, nodes, [1.0] * dim, model, 1, 0)
+        assert st == 0
+        st, ex = _lib.pf_explicit_workspace(ctx)
+        assert st == 0 and 0 < ex < ws
+        if dim == 3:  # one residual vector for the 3-D explicit step
+            assert ex >= 16 ** 3 * 4
+        assert _lib.pf_bind_workspace(ctx, 0x100000, ex) == 0
+        assert _lib.pf_set_params(ctx, _lib.pf_params(1.0, 0.5, 1.0, 1e-3, 1.0, 1.0, 1.5,
+                                                      0.5, None, 0.0)) == 0
+        opts, stats = _lib.pf_newton_opts(20, 30, 300, 1e-5, 1e-3), _lib.pf_newton_stats()
+        assert _lib.pf_step_implicit(ctx, 0x2000, 1, 0, opts, stats) == _lib.PF_ERR_STATE
+        assert "explicit steps only" in _lib.pf_last_error(ctx)
+        if model == _lib.PF_MODEL_CH:  # no implicit adjoint for the split CH system
+            _lib.pf_destroy(ctx)
+            continue
+        nb = _lib.C.c_size_t(0)
+        assert _lib.lib().pf_implicit_adjoint_workspace(ctx, 2, _lib.C.byref(nb)) == 0
+        O, g = _lib.C.c_double(0), (_lib.C.c_double * 2)()
+        st = _lib.lib().pf_implicit_adjoint(ctx, _lib.C.c_void_p(0x2000), 2, _lib.C.byref(opts),
+                                            _lib.C.c_void_p(0x4000), nb.value, _lib.C.byref(O),
+                                            g, _lib.C.byref(stats))
+        assert st == _lib.PF_ERR_STATE
+        _lib.pf_destroy(ctx)
+    # an ensemble binds its whole workspace
+    st, ctx, ws, _ = _lib.pf_create_ensemble([16, 8], [16, 12], None, 0)
+    assert st == 0
+    st, ex = _lib.pf_explicit_workspace(ctx)
+    assert st == 0 and ex == ws
+    _lib.pf_destroy(ctx)
