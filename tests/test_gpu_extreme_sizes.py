@@ -230,3 +230,63 @@ def test_ensemble_of_more_instances_than_grid_rows():
             fields[i], 0.01, k)
         assert rel_l2(out[i].cpu().numpy(), ref) <= REL_L2, i
     e.close()
+
+
+# ------------------------------------------- 3-D vectors past 2^31 values
+
+FC = dict(alpha=1.0, beta=1.0, gamma=1.5)
+
+
+def test_fan_chen_jvp_and_residual_past_2_31_values():
+    # 648^3 nodes x 8 order parameters: one vector holds 2.18e9 values, so the
+    # field offsets exceed 2^31.  U, U^n and v repeat seeded tiles; J v and R
+    # at a node involve only the 8 elements around it, so the oracle
+    # reproduces sampled nodes from 5^3-node windows (window faces that are
+    # not mesh faces are left out).
+    free, _ = torch.cuda.mem_get_info()
+    if free < 80 * 2**30:
+        pytest.skip("needs about 60 GB of free device memory")
+    n, nf, P3 = 648, 8, (37, 41, 43)
+    TU = G.random_field(31, (nf,) + P3, 0.0, 1.0)
+    TN = G.random_field(32, (nf,) + P3, 0.0, 1.0)
+    TV = G.random_field(33, (nf,) + P3)
+
+    def tiled(T):
+        t = torch.from_numpy(T).cuda()
+        big = t.repeat(1, *[-(-n // p) for p in P3])
+        out = big[:, :n, :n, :n].contiguous()
+        del big
+        return out
+
+    def window(T, zs, ys, xs):
+        return T[:, np.asarray(zs) % P3[0]][:, :, np.asarray(ys) % P3[1]][:, :, :, np.asarray(xs) % P3[2]]
+
+    pf = _pf()
+    s = pf.Solver((n, n, n), h=1.0, model="fanchen", n_fields=nf)
+    s.set_params(W=1.0, kappa=0.9, mobility=1.1, dt=0.5, shift=0.0, **FC)
+    U, v = tiled(TU), tiled(TV)
+    Jv = s.jvp(U, v)
+    del v
+    torch.cuda.empty_cache()
+    Un = tiled(TN)
+    R = s.implicit_residual(Un, U)
+    centres = [(0, 0, 0), (n - 1, n - 1, n - 1), (n - 1, 0, n // 2), (n // 2, n // 2, n // 2),
+               (n - 2, n - 1, 1), (300, 0, n - 1), (n - 1, 500, 37 * 5)]
+    for cz, cy, cx in centres:
+        lo = [max(0, c - 2) for c in (cz, cy, cx)]
+        hi = [min(n, c + 3) for c in (cz, cy, cx)]
+        rng = [range(a, b) for a, b in zip(lo, hi)]
+        Uw, Nw, Vw = window(TU, *rng), window(TN, *rng), window(TV, *rng)
+        P = O.Problem(Uw.shape[1:], h=1.0, energy="fan_chen", nf=nf, kappa=0.9, mob=1.1,
+                      W=1.0, **FC)
+        keep = tuple(slice(0 if a == 0 else 1, (b - a) if b == n else (b - a) - 1)
+                     for a, b in zip(lo, hi))
+        sl = (slice(None),) + tuple(slice(a, b) for a, b in zip(lo, hi))
+        for gpu, ref in ((Jv, P.implicit_jvp(0.5, Uw, Vw)), (R, P.implicit_residual(0.5, Nw, Uw))):
+            g = gpu[sl].cpu().numpy()[(slice(None),) + keep]
+            r = ref[(slice(None),) + keep]
+            assert g.size > 0
+            assert rel_l2(g, r) <= 2e-6, (cz, cy, cx)
+    s.close()
+    del U, Un, Jv, R, s
+    torch.cuda.empty_cache()
