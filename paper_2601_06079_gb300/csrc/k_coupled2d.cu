@@ -18,8 +18,14 @@
 namespace pf {
 namespace {
 
-constexpr int TX = 32, TY = 16;            // output tile
-constexpr int kThreads = 256;
+#ifndef PF_CPL_TY
+#define PF_CPL_TY 16
+#endif
+#ifndef PF_CPL_THREADS
+#define PF_CPL_THREADS 256
+#endif
+constexpr int TX = 32, TY = PF_CPL_TY;     // output tile
+constexpr int kThreads = PF_CPL_THREADS;
 constexpr int S2X = TX + 4, S2Y = TY + 4;  // nodes with a 2-node halo
 constexpr int EX = TX + 3, EY = TY + 3;    // elements touching the 1-halo nodes
 
