@@ -217,9 +217,11 @@ __global__ void __launch_bounds__(kThreads) k_implicit3d(const Implicit3DArgs a)
   u64* sW = sU + NP * kNodes;                    // v (JVP) or U^n (residual)
   u64* sE = sW + NP * kNodes;                    // [8][kElems] corner contributions of a pair
   // per-element values are stored [8][kElems] (Gauss point or corner major), so
-  // that consecutive threads (consecutive elements) hit consecutive banks
-  float* sS = reinterpret_cast<float*>(sE + 8 * kElems);  // [8][kElems] S2 at Gauss points
-  float* sTq = sS + kElems * 8;                            // [8][kElems] T (JVP only)
+  // that consecutive threads (consecutive elements) hit consecutive banks.
+  // Residual: S2 at the Gauss points.  JVP: the pair (2 gamma S2 - alpha,
+  // 4 gamma T), the two coupling factors of H v, fetched by one 64-bit load.
+  float* sS = reinterpret_cast<float*>(sE + 8 * kElems);  // [8][kElems] (residual)
+  u64* sQ = sE + 8 * kElems;                               // [8][kElems] (JVP)
 
   const int tiles_x = (a.nx + kTX - 1) / kTX, tiles_y = (a.ny + kTY - 1) / kTY;
   const int tile = blockIdx.x;
@@ -266,8 +268,12 @@ __global__ void __launch_bounds__(kThreads) k_implicit3d(const Implicit3DArgs a)
     }
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      sS[q * kElems + e] = plo(S2[q]) + phi(S2[q]);
-      if (kJVP) sTq[q * kElems + e] = plo(T[q]) + phi(T[q]);
+      const float s2 = plo(S2[q]) + phi(S2[q]);
+      if (kJVP)
+        sQ[q * kElems + e] =
+            pk(fmaf(a.two_gamma, s2, -a.alpha), a.four_gamma * (plo(T[q]) + phi(T[q])));
+      else
+        sS[q * kElems + e] = s2;
     }
   }
   __syncthreads();
@@ -305,10 +311,13 @@ __global__ void __launch_bounds__(kThreads) k_implicit3d(const Implicit3DArgs a)
         } else {
           // Fan-Chen: f'_f = u (-a + 2g S2 + (b - 2g) u^2)
           //           (H v)_f = (-a + 2g S2 + (3b - 6g) u^2) v_f + 4g u T
-          const u64 base_c = bc(fmaf(a.two_gamma, sS[q * kElems + e], -a.alpha));
-          hq[q] = kJVP ? fma2(fma2(bc(a.c3b6g), uu, base_c), vq[q],
-                              mul2(bc(a.four_gamma * sTq[q * kElems + e]), u))
-                       : mul2(u, fma2(bc(a.cb2g), uu, base_c));
+          if (kJVP) {
+            const u64 st = sQ[q * kElems + e];
+            hq[q] = fma2(fma2(bc(a.c3b6g), uu, bc(plo(st))), vq[q], mul2(bc(phi(st)), u));
+          } else {
+            const u64 base_c = bc(fmaf(a.two_gamma, sS[q * kElems + e], -a.alpha));
+            hq[q] = mul2(u, fma2(bc(a.cb2g), uu, base_c));
+          }
         }
       }
       project3_grad(hq, gx, gy, gz, a.kg, out);
