@@ -19,7 +19,8 @@
  *     a mesh with N nodes occupies state[f*N .. f*N+N-1]; node
  *     (i, j, k) sits at (k*ny + j)*nx + i (x fastest).
  *   - The library never allocates device memory.  pf_create_mesh reports the
- *     workspace size; the caller allocates it and binds it with
+ *     workspace size for every call (pf_explicit_workspace the smaller part
+ *     that explicit steps need); the caller allocates it and binds it with
  *     pf_bind_workspace before any compute call.
  *   - Work is enqueued on the stream given at creation, in order, without a
  *     device synchronisation.  Calls that return host scalars (pf_energy,
@@ -107,7 +108,8 @@ typedef struct {
  *   h[3]             node spacing per axis (> 0)
  *   model, n_fields  n_fields must be 1 for AC/CH, 1..8 for FANCHEN
  *   stream           cudaStream_t (NULL = legacy default stream) on which all work runs
- *   workspace_bytes  out (host): device workspace the caller must bind
+ *   workspace_bytes  out (host): device workspace that serves every call
+ *                    (pf_explicit_workspace: the part explicit steps need)
  * Defines the discretisation of Sec. 2.2 / Eq. 11.  Host only; no CUDA call. */
 pf_status pf_create_mesh(pf_ctx** out, int dim, const int64_t nodes[3], const double h[3],
                          pf_model model, int n_fields, void* stream, size_t* workspace_bytes);
