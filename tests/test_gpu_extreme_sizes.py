@@ -290,3 +290,43 @@ def test_fan_chen_jvp_and_residual_past_2_31_values():
     s.close()
     del U, Un, Jv, R, s
     torch.cuda.empty_cache()
+
+
+# The remaining operators on meshes at the axis limit (1-D tile grids): the
+# coupled step (Eq. 7) in both orientations, the 2-D implicit operators and the
+# 3-D Fan-Chen J v with 2^20 nodes along z and an odd field count.
+
+@pytest.mark.parametrize("shape", [(1 << 20, 3), (3, 1 << 20)])
+def test_coupled_step_at_the_axis_limit(shape):
+    U0 = G.coupled_initial(41, shape)
+    par = dict(kappa=0.3, mobility=1.0, mobility2=150.0, dt=1e-3)
+    pf = _pf()
+    s = pf.Solver(shape, h=1.0, model="coupled")
+    s.set_params(**par)
+    t = _cu(U0)
+    s.step_explicit(t, 6)
+    P = O.Problem(shape, energy="coupled", kappa=0.3, mob=1.0, mob2=150.0)
+    ref = P.coupled_explicit(U0, 1e-3, 6)
+    got = t.cpu().numpy()
+    for f in range(2):
+        assert rel_l2(got[f], ref[f]) <= REL_L2, f
+
+
+def test_implicit_operators_at_the_axis_limit():
+    pf = _pf()
+    shape = (1 << 20, 3)
+    s = pf.Solver(shape, h=1.0, model="ac")
+    s.set_params(W=1.0, kappa=0.9, mobility=1.1, dt=0.5)
+    P = O.Problem(shape, W=1.0, kappa=0.9, mob=1.1)
+    U, Un = G.ac_initial(42, shape, 0.2, 0.8), G.ac_initial(43, shape, 0.2, 0.8)
+    v = G.random_field(44, shape)
+    assert rel_l2(s.jvp(_cu(U), _cu(v)).cpu().numpy(), P.implicit_jvp(0.5, U, v)) <= 2e-6
+    assert rel_l2(s.implicit_residual(_cu(Un), _cu(U)).cpu().numpy(),
+                  P.implicit_residual(0.5, Un, U)) <= 2e-6
+    shape3, nf = (1 << 20, 2, 3), 3
+    s3 = pf.Solver(shape3, h=1.0, model="fanchen", n_fields=nf)
+    s3.set_params(W=1.0, kappa=0.9, mobility=1.1, dt=0.5, shift=0.0, **FC)
+    P3 = O.Problem(shape3, h=1.0, energy="fan_chen", nf=nf, kappa=0.9, mob=1.1, W=1.0, **FC)
+    U3 = G.random_field(45, (nf,) + shape3, 0.0, 1.0)
+    v3 = G.random_field(46, (nf,) + shape3)
+    assert rel_l2(s3.jvp(_cu(U3), _cu(v3)).cpu().numpy(), P3.implicit_jvp(0.5, U3, v3)) <= 2e-6
