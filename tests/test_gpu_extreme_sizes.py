@@ -237,6 +237,36 @@ def test_ensemble_of_more_instances_than_grid_rows():
 FC = dict(alpha=1.0, beta=1.0, gamma=1.5)
 
 
+def _tiled3(T, n, P3):
+    """(c, n, n, n) device array repeating the (c,) + P3 tile T."""
+    t = torch.from_numpy(T).cuda()
+    big = t.repeat(1, *[-(-n // p) for p in P3])
+    out = big[:, :n, :n, :n].contiguous()
+    del big
+    return out
+
+
+def _window3(T, P3, zs, ys, xs):
+    return T[:, np.asarray(zs) % P3[0]][:, :, np.asarray(ys) % P3[1]][:, :, :, np.asarray(xs) % P3[2]]
+
+
+def _check_windows(n, centres, gpu_and_oracle):
+    """Compare sampled 5^3-node windows; gpu_and_oracle(rng) -> pairs of
+    (device array, oracle window array); faces that are not mesh faces drop."""
+    for cz, cy, cx in centres:
+        lo = [max(0, c - 2) for c in (cz, cy, cx)]
+        hi = [min(n, c + 3) for c in (cz, cy, cx)]
+        rng = [range(a, b) for a, b in zip(lo, hi)]
+        keep = (slice(None),) + tuple(slice(0 if a == 0 else 1, (b - a) if b == n else (b - a) - 1)
+                                      for a, b in zip(lo, hi))
+        sl = (slice(None),) + tuple(slice(a, b) for a, b in zip(lo, hi))
+        for gpu, ref in gpu_and_oracle(rng):
+            g = gpu[sl].cpu().numpy()[keep]
+            r = ref[keep]
+            assert g.size > 0
+            assert rel_l2(g, r) <= 2e-6, (cz, cy, cx)
+
+
 def test_fan_chen_jvp_and_residual_past_2_31_values():
     # 648^3 nodes x 8 order parameters: one vector holds 2.18e9 values, so the
     # field offsets exceed 2^31.  U, U^n and v repeat seeded tiles; J v and R
@@ -251,42 +281,25 @@ def test_fan_chen_jvp_and_residual_past_2_31_values():
     TN = G.random_field(32, (nf,) + P3, 0.0, 1.0)
     TV = G.random_field(33, (nf,) + P3)
 
-    def tiled(T):
-        t = torch.from_numpy(T).cuda()
-        big = t.repeat(1, *[-(-n // p) for p in P3])
-        out = big[:, :n, :n, :n].contiguous()
-        del big
-        return out
-
-    def window(T, zs, ys, xs):
-        return T[:, np.asarray(zs) % P3[0]][:, :, np.asarray(ys) % P3[1]][:, :, :, np.asarray(xs) % P3[2]]
-
     pf = _pf()
     s = pf.Solver((n, n, n), h=1.0, model="fanchen", n_fields=nf)
     s.set_params(W=1.0, kappa=0.9, mobility=1.1, dt=0.5, shift=0.0, **FC)
-    U, v = tiled(TU), tiled(TV)
+    U, v = _tiled3(TU, n, P3), _tiled3(TV, n, P3)
     Jv = s.jvp(U, v)
     del v
     torch.cuda.empty_cache()
-    Un = tiled(TN)
+    Un = _tiled3(TN, n, P3)
     R = s.implicit_residual(Un, U)
     centres = [(0, 0, 0), (n - 1, n - 1, n - 1), (n - 1, 0, n // 2), (n // 2, n // 2, n // 2),
                (n - 2, n - 1, 1), (300, 0, n - 1), (n - 1, 500, 37 * 5)]
-    for cz, cy, cx in centres:
-        lo = [max(0, c - 2) for c in (cz, cy, cx)]
-        hi = [min(n, c + 3) for c in (cz, cy, cx)]
-        rng = [range(a, b) for a, b in zip(lo, hi)]
-        Uw, Nw, Vw = window(TU, *rng), window(TN, *rng), window(TV, *rng)
+
+    def pairs(rng):
+        Uw, Nw, Vw = (_window3(T, P3, *rng) for T in (TU, TN, TV))
         P = O.Problem(Uw.shape[1:], h=1.0, energy="fan_chen", nf=nf, kappa=0.9, mob=1.1,
                       W=1.0, **FC)
-        keep = tuple(slice(0 if a == 0 else 1, (b - a) if b == n else (b - a) - 1)
-                     for a, b in zip(lo, hi))
-        sl = (slice(None),) + tuple(slice(a, b) for a, b in zip(lo, hi))
-        for gpu, ref in ((Jv, P.implicit_jvp(0.5, Uw, Vw)), (R, P.implicit_residual(0.5, Nw, Uw))):
-            g = gpu[sl].cpu().numpy()[(slice(None),) + keep]
-            r = ref[(slice(None),) + keep]
-            assert g.size > 0
-            assert rel_l2(g, r) <= 2e-6, (cz, cy, cx)
+        return ((Jv, P.implicit_jvp(0.5, Uw, Vw)), (R, P.implicit_residual(0.5, Nw, Uw)))
+
+    _check_windows(n, centres, pairs)
     s.close()
     del U, Un, Jv, R, s
     torch.cuda.empty_cache()
@@ -330,3 +343,29 @@ def test_implicit_operators_at_the_axis_limit():
     U3 = G.random_field(45, (nf,) + shape3, 0.0, 1.0)
     v3 = G.random_field(46, (nf,) + shape3)
     assert rel_l2(s3.jvp(_cu(U3), _cu(v3)).cpu().numpy(), P3.implicit_jvp(0.5, U3, v3)) <= 2e-6
+
+
+def test_elastic_stiffness_past_2_31_values():
+    # 896^3 nodes x 3 displacement components: 2.16e9 values per vector.  K u
+    # at a node involves only its 8 elements, so 5^3-node windows of a tiled
+    # random u are reproduced by the oracle (no constraints).
+    free, _ = torch.cuda.mem_get_info()
+    if free < 50 * 2**30:
+        pytest.skip("needs about 30 GB of free device memory")
+    n, P3 = 896, (37, 41, 43)
+    E, nu = 22.5, 0.3
+    T = G.random_field(51, (3,) + P3)
+    pf = _pf()
+    el = pf.Elastic((n, n, n), 1.0, E=E, nu=nu)
+    u = _tiled3(T, n, P3)
+    Ku = el.apply(u)
+    lam, mu = O.Elastic.lame(E, nu)
+
+    def pairs(rng):
+        uw = _window3(T, P3, *rng).astype(np.float64)
+        return ((Ku, O.Elastic(uw.shape[1:], 1.0).apply(uw, lam, mu)),)
+
+    _check_windows(n, [(0, 0, 0), (n - 1, n - 1, n - 1), (n - 1, 0, n // 2), (n // 2, n // 2, n // 2),
+                       (n - 2, n - 1, 1), (700, 0, n - 1), (n - 1, 600, 37 * 7)], pairs)
+    del u, Ku, el
+    torch.cuda.empty_cache()
