@@ -1,6 +1,6 @@
 """GPU parity: fused explicit AC / CH step kernels vs the FP64 oracle.
 
-Bar (the benchmark spec): relative L2 error <= 1e-5 against the FP64 oracle after the
+Bar: relative L2 error <= 1e-5 against the FP64 oracle after the
 stated steps, element by element on the same seeded FP32 inputs.
 """
 import numpy as np
