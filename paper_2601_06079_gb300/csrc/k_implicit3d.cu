@@ -276,7 +276,9 @@ __global__ void __launch_bounds__(kThreads) k_implicit3d(const Implicit3DArgs a)
         sS[q * kElems + e] = s2;
     }
   }
-  __syncthreads();
+  // no barrier: phase 2 reads element e's coupling factors in the thread that
+  // wrote them (both loops give element e to the same thread), and writes only
+  // sE, which phase 1 does not touch
 
   // phase 2: one field pair at a time
   for (int p = 0; p < NP; ++p) {
