@@ -38,15 +38,29 @@ namespace {
 #ifndef PF_IMP_TZ
 #define PF_IMP_TZ 8
 #endif
-constexpr int kTX = 8, kTY = 8, kTZ = PF_IMP_TZ;        // output nodes per tile edge
-constexpr int kNX = kTX + 2, kNY = kTY + 2, kNZ = kTZ + 2;  // staged nodes (1 halo each side)
-constexpr int kEX = kTX + 1, kEY = kTY + 1, kEZ = kTZ + 1;  // elements touching the tile
-constexpr int kNodes = kNX * kNY * kNZ;
-constexpr int kElems = kEX * kEY * kEZ;
 #ifndef PF_IMP_THREADS
 #define PF_IMP_THREADS 768
 #endif
-constexpr int kThreads = PF_IMP_THREADS;
+#ifndef PF_RES_TZ
+#define PF_RES_TZ 2
+#endif
+#ifndef PF_RES_THREADS
+#define PF_RES_THREADS 256
+#endif
+constexpr int kTX = 8, kTY = 8;                // output nodes per tile edge in x, y
+constexpr int kNX = kTX + 2, kNY = kTY + 2;    // staged nodes (1 halo each side)
+constexpr int kEX = kTX + 1, kEY = kTY + 1;    // elements touching the tile
+
+// Tile depth and block size per operator.  The JVP keeps 8^3-node tiles, one
+// 157 KB block per SM.  The residual carries half the per-element state and
+// runs faster on flat 8 x 8 x 2 tiles, three blocks per SM.
+template <bool kJVP>
+struct TileCfg {
+  static constexpr int kTZ = kJVP ? PF_IMP_TZ : PF_RES_TZ;
+  static constexpr int kThreads = kJVP ? PF_IMP_THREADS : PF_RES_THREADS;
+  static constexpr int kNodes = kNX * kNY * (kTZ + 2);
+  static constexpr int kElems = kEX * kEY * (kTZ + 1);
+};
 
 typedef unsigned long long u64;  // packed FP32 pair: low half = the even field
 
@@ -210,7 +224,9 @@ __device__ __forceinline__ void corners(const u64* P, int base, u64 c[8]) {
 }
 
 template <int NF, bool kJVP>
-__global__ void __launch_bounds__(kThreads) k_implicit3d(const Implicit3DArgs a) {
+__global__ void __launch_bounds__(TileCfg<kJVP>::kThreads) k_implicit3d(const Implicit3DArgs a) {
+  constexpr int kTZ = TileCfg<kJVP>::kTZ, kThreads = TileCfg<kJVP>::kThreads;
+  constexpr int kNodes = TileCfg<kJVP>::kNodes, kElems = TileCfg<kJVP>::kElems;
   constexpr int NP = (NF + 1) / 2;  // field pairs
   extern __shared__ u64 smem[];
   u64* sU = smem;                                // [NP][kNodes] (field 2p, 2p+1)
@@ -359,6 +375,8 @@ __global__ void __launch_bounds__(kThreads) k_implicit3d(const Implicit3DArgs a)
 
 template <int NF, bool kJVP>
 cudaError_t launch_nf(const Implicit3DArgs& a, cudaStream_t s) {
+  constexpr int kTZ = TileCfg<kJVP>::kTZ, kThreads = TileCfg<kJVP>::kThreads;
+  constexpr int kNodes = TileCfg<kJVP>::kNodes, kElems = TileCfg<kJVP>::kElems;
   constexpr int NP = (NF + 1) / 2;
   const size_t smem = sizeof(u64) * (2 * NP * kNodes + 8 * kElems) +
                       sizeof(float) * kElems * 8 * (kJVP ? 2 : 1);
