@@ -664,6 +664,7 @@ def run_profile(args):
     ch        the bench's CH 2048^2 trajectory (--tsteps steps per trajectory)
     surrogate two warm-start predictions on 128^3 x 8 fields (tcgen05 convolutions)
     jvp       three Fan-Chen Jacobian-vector products on 128^3 x 8 fields
+    residual  three Fan-Chen implicit residuals on 128^3 x 8 fields
     ensemble  20 steps of the 256-instance AC ensemble, one launch per step (the
               persistent mode runs the same task body behind a grid barrier)
     coupled   20 coupled Allen-Cahn / Cahn-Hilliard steps on 2048^2
@@ -702,6 +703,16 @@ def run_profile(args):
             jv = solver.jvp(U, v)
         torch.cuda.synchronize()
         print(f"profile run done: |Jv| {float(jv.norm()):.6f}")
+    elif args.target == "residual":
+        from paper_2601_06079_gb300 import warmstart as WS
+        n = 128
+        solver = WS.grain_solver(n)
+        U = torch.from_numpy(G.voronoi_grains(1, n=n, n_seeds=64, n_op=8)).cuda()
+        Un = torch.from_numpy(G.voronoi_grains(2, n=n, n_seeds=64, n_op=8)).cuda()
+        for _ in range(3):
+            r = solver.implicit_residual(Un, U)
+        torch.cuda.synchronize()
+        print(f"profile run done: |R| {float(r.norm()):.6f}")
     elif args.target == "elastic":
         n = 129
         el = pf.Elastic((n, n, n), 100.0 / (n - 1))
@@ -743,7 +754,8 @@ def main():
                     help="run one workload untimed for ncu (see --target)")
     ap.add_argument("--tsteps", type=int, default=N_TSTEPS)
     ap.add_argument("--target", default="ch",
-                    choices=["ch", "surrogate", "jvp", "ensemble", "coupled", "elastic"],
+                    choices=["ch", "surrogate", "jvp", "residual", "ensemble", "coupled",
+                             "elastic"],
                     help="workload of --profile")
     args = ap.parse_args()
     if args.warmup < 3:
