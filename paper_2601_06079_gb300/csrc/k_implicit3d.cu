@@ -8,11 +8,13 @@
 // halves, so every node uses the interior formula (an optional final
 // multiplication by m_i gives R and J v themselves).
 //
-// Work split: one block per 8 x 8 x kTZ node tile.  The block stages U (and v,
-// or U^n) for the nodes around it (one halo layer) in shared memory, mirrored
-// at the mesh boundary, then evaluates all elements touching the tile:
+// Work split: one block per 8 x 8 x kTZ node tile (kTZ = 8 for the JVP, 2 for
+// the residual; see TileCfg).  The block stages U (and v, or U^n) for the
+// nodes around it (one halo layer) in shared memory, mirrored at the mesh
+// boundary, then evaluates all elements touching the tile:
 //   phase 1: per element and Gauss point, S2 = sum_f U_f^2 (and T =
-//            sum_f U_f v_f for the JVP), the only couplings between fields;
+//            sum_f U_f v_f for the JVP), the only couplings between fields,
+//            kept as the Hessian's factors 2 gamma S2 - alpha and 4 gamma T;
 //   phase 2: per field, the Gauss values (trilinear, sum-factorised), the
 //            pointwise f' or H v, and the gradient term kappa grad w . grad N_a
 //            (w = v for the JVP, U for the residual), all weighted back to the
