@@ -13,8 +13,8 @@
 // nodes around it (one halo layer) in shared memory, mirrored at the mesh
 // boundary, then evaluates all elements touching the tile:
 //   phase 1: per element and Gauss point, S2 = sum_f U_f^2 (and T =
-//            sum_f U_f v_f for the JVP), the only couplings between fields,
-//            kept as the Hessian's factors 2 gamma S2 - alpha and 4 gamma T;
+//            sum_f U_f v_f for the JVP), the only couplings between fields
+//            (the JVP keeps the Hessian's factors 2 gamma S2 - alpha, 4 gamma T);
 //   phase 2: per field, the Gauss values (trilinear, sum-factorised), the
 //            pointwise f' or H v, and the gradient term kappa grad w . grad N_a
 //            (w = v for the JVP, U for the residual), all weighted back to the
