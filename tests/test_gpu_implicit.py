@@ -292,3 +292,26 @@ def test_implicit_adjoint_3d_fan_chen_matches_central_differences():
     fdk = (obj(1.0, 1.0 + eps) - obj(1.0, 1.0 - eps)) / (2 * eps)
     assert abs(g["L"] - fdL) <= 2e-2 * abs(fdL), (g, fdL)
     assert abs(g["kappa"] - fdk) <= 2e-2 * abs(fdk), (g, fdk)
+
+
+def test_workspace_growth_between_explicit_and_implicit_steps():
+    # a Solver binds the explicit part of its workspace first; the first
+    # implicit step grows it (dropping the captured explicit-step graph), and
+    # explicit steps on the new memory continue the same trajectory
+    shape = (67, 90)
+    s, P = _ac2d(shape, 1.0)
+    small = s._ws.numel()
+    U0 = G.ac_initial(11, shape, 0.3, 0.7)
+    t = torch.from_numpy(U0).cuda()
+    s.set_params(W=1.3, kappa=0.7, mobility=1.1, dt=0.01)
+    s.step_explicit(t, 130)  # two 64-step graph replays and two single steps
+    s.set_params(W=1.3, kappa=0.7, mobility=1.1, dt=0.5)
+    st = s.step_implicit(t, 1, newton_rtol=1e-6, gmres_rtol=1e-4)
+    assert st["converged"] and s._ws.numel() > small
+    s.set_params(W=1.3, kappa=0.7, mobility=1.1, dt=0.01)
+    s.step_explicit(t, 130)
+    ref = P.ac_explicit(U0, 0.01, 130)
+    ref, info = P.newton(0.5, ref, abs_tol=1e-12, gmres_rtol=1e-10)
+    assert info["ok"]
+    ref = P.ac_explicit(ref, 0.01, 130)
+    assert rel(t.cpu().numpy(), ref) <= 2e-5
