@@ -29,6 +29,6 @@ def test_uniform_fields_stay_in_range_with_the_right_mean():
     assert abs(u.mean() - 1.5) < 0.03
     c = G.ch_initial(1, (64, 80))
     assert c.dtype == np.float32 and c.shape == (64, 80)
-    assert c.min() >= 0.45 and c.max() <= 0.55
+    assert c.min() >= 0.45 - 1e-7 and c.max() <= 0.55 + 1e-7  # FP32 rounding of the bounds
     f = G.ac_initial(2, (33, 17), 0.2, 0.8)
-    assert f.min() >= 0.2 and f.max() <= 0.8
+    assert f.min() >= 0.2 - 1e-7 and f.max() <= 0.8 + 1e-7
