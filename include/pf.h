@@ -296,8 +296,11 @@ pf_status pf_energy(pf_ctx* ctx, const float* state, double* energy, double* mas
  * calls share the array and it keeps the last call's partial sums; nothing in
  * it needs to start at zero (each call overwrites every slot it reads), but
  * calls that overlap on the GPU (other streams, other threads) race on it and
- * must be serialised by the caller.  Does not synchronise; returns PF_ERR_CUDA
- * if a launch fails. */
+ * must be serialised by the caller.  The looked-up address is cached per
+ * device for the life of the process, so after cudaDeviceReset on a device
+ * this entry point must not be called on that device again in the same
+ * process (device memory it would write no longer exists).  Does not
+ * synchronise; returns PF_ERR_CUDA if a launch fails. */
 pf_status pf_energy2d_static(const float* state, int64_t nx, int64_t ny, double hx, double hy,
                              double W, double kappa, double* out, void* stream,
                              const char** err);

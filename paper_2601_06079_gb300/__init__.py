@@ -32,6 +32,17 @@ _MODELS = {"ac": PF_MODEL_AC, "ch": PF_MODEL_CH, "fanchen": PF_MODEL_FANCHEN,
            "coupled": PF_MODEL_COUPLED}
 
 
+def _on_stream(stream, nbytes, device, dtype=torch.uint8, shape=None):
+    """Allocate a library buffer from the caching allocator's pool of `stream`,
+    the stream that libpf enqueues its work on: the allocator then orders a
+    later reuse of the block after that stream's work, not after torch's
+    current stream's."""
+    with torch.cuda.stream(stream):
+        if shape is not None:
+            return torch.empty(shape, dtype=dtype, device=device)
+        return torch.empty(max(nbytes, 256), dtype=dtype, device=device)
+
+
 class PFError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{_lib.STATUS_NAMES.get(status, status)}: {msg}")
@@ -74,7 +85,7 @@ class Solver:
         self._keep = None
 
     def _bind(self, nbytes):
-        self._ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
+        self._ws = _on_stream(self.stream, nbytes, self.device)
         self._check(pf_bind_workspace(self._ctx, self._ws.data_ptr(), self._ws.numel()))
 
     def _implicit_workspace(self):
@@ -157,7 +168,7 @@ class Solver:
         nb = C.c_size_t(0)
         self._check(_lib.lib().pf_implicit_adjoint_workspace(self._ctx, n_steps, C.byref(nb)))
         self._implicit_workspace()
-        ws = torch.empty(max(nb.value, 256), dtype=torch.uint8, device=self.device)
+        ws = _on_stream(self.stream, nb.value, self.device)
         opts = _lib.pf_newton_opts(max_newton, gmres_restart, gmres_max_iters, newton_rtol,
                                    gmres_rtol)
         O, g = C.c_double(0), (C.c_double * 2)()
@@ -190,9 +201,11 @@ class Solver:
         = {kappa, W, M, mobility_field (float64 tensor), c0 (float32 tensor)}."""
         st, nbytes = pf_adjoint_workspace(self._ctx, n_steps, ckpt_every)
         self._check(st)
-        ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
-        gm = torch.empty(self.shape, dtype=torch.float64, device=self.device) if want_field else None
-        g0 = torch.empty(self.shape, dtype=torch.float32, device=self.device) if want_state else None
+        ws = _on_stream(self.stream, nbytes, self.device)
+        gm = (_on_stream(self.stream, 0, self.device, torch.float64, self.shape)
+              if want_field else None)
+        g0 = (_on_stream(self.stream, 0, self.device, torch.float32, self.shape)
+              if want_state else None)
         st, loss, gs = pf_adjoint(self._ctx, self._state(c0), self._state(target), n_steps,
                                   ckpt_every, int(nodal_loss), ws.data_ptr(), ws.numel(),
                                   gm.data_ptr() if gm is not None else 0,
@@ -208,8 +221,10 @@ class Solver:
 
     def close(self):
         if getattr(self, "_ctx", None):
+            self.stream.synchronize()  # library work may still use the workspace
             pf_destroy(self._ctx)
             self._ctx = None
+            self._ws = None
 
     def __del__(self):
         try:
@@ -237,7 +252,7 @@ class Ensemble:
             self.stream.cuda_stream)
         if st != 0:
             raise PFError(st, "pf_create_ensemble rejected the instances")
-        self._ws = torch.empty(max(ws, 256), dtype=torch.uint8, device=self.device)
+        self._ws = _on_stream(self.stream, ws, self.device)
         self._check(pf_bind_workspace(self._ctx, self._ws.data_ptr(), self._ws.numel()))
         self.nclasses = len(set(self.shapes))
 
@@ -272,8 +287,10 @@ class Ensemble:
 
     def close(self):
         if getattr(self, "_ctx", None):
+            self.stream.synchronize()  # library work may still use the workspace
             pf_destroy(self._ctx)
             self._ctx = None
+            self._ws = None
 
     def __del__(self):
         try:
@@ -343,7 +360,7 @@ class Surrogate:
             st, nb = pf_surrogate_workspace(batch, d, h, w, training)
             if st != 0:
                 raise PFError(st, f"unsupported surrogate volume {key}")
-            self._ws[key] = torch.empty(nb, dtype=torch.uint8, device=self.device)
+            self._ws[key] = _on_stream(self.stream, nb, self.device)
         return self._ws[key]
 
     def _dims(self, x):
@@ -424,7 +441,7 @@ class Elastic:
         if self._ws is None:
             st, n = _lib.pf_elastic_workspace(self.e)
             self._check(st, "pf_elastic_workspace")
-            self._ws = torch.empty(n, dtype=torch.uint8, device=self.device)
+            self._ws = _on_stream(self.stream, n, self.device)
         return self._ws
 
     def empty(self):

@@ -391,8 +391,8 @@ __global__ void k_elastic_constrain(float* __restrict__ v, int nx, int ny, int n
 }
 
 int blocks_for(int64_t n) {
-  const int64_t b = (n + 255) / 256;
-  return (int)(b < 152 * 8 ? b : 152 * 8);
+  const int64_t b = (n + 255) / 256, cap = 8 * (int64_t)device_sm_count();
+  return (int)(b < cap ? b : cap);
 }
 
 dim3 interior_grid(int nx, int ny, int nz) {
@@ -411,7 +411,8 @@ int elastic_apply_blocks(int nx, int ny, int nz) {
   return (int)(g.x * g.y * g.z) + boundary_blocks(nx, ny, nz);
 }
 
-int cg_blocks() { return 152 * 8; }
+// 8 blocks per SM, fixed per device (the r.r partials are summed in a fixed order)
+int cg_blocks() { return 8 * device_sm_count(); }
 
 cudaError_t launch_elastic_apply(const Elastic3DArgs& a, cudaStream_t s) {
   const dim3 gi = interior_grid(a.nx, a.ny, a.nz);

@@ -657,7 +657,7 @@ cudaError_t launch_to_work(const float* in, float* work, int nx, int ny, float s
                            cudaStream_t s) {
   const int64_t n = (int64_t)work_pitch(nx) * work_rows(ny);
   int64_t blocks = (n + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks > 16 * (int64_t)device_sm_count()) blocks = 16 * (int64_t)device_sm_count();
   k_to_work<<<(unsigned)blocks, 256, 0, s>>>(in, work, nx, ny, work_pitch(nx), work_rows(ny),
                                              shift);
   return cudaGetLastError();
@@ -667,7 +667,7 @@ cudaError_t launch_from_work(const float* work, float* out, int nx, int ny, floa
                              cudaStream_t s) {
   const int64_t n = (int64_t)nx * ny;
   int64_t blocks = (n + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks > 16 * (int64_t)device_sm_count()) blocks = 16 * (int64_t)device_sm_count();
   k_from_work<<<(unsigned)blocks, 256, 0, s>>>(work, out, nx, ny, work_pitch(nx), shift);
   return cudaGetLastError();
 }

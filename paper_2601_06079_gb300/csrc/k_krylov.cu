@@ -10,7 +10,6 @@ namespace pf {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kBlocks = 456;   // 3 per SM on a 152-SM GB300; fixed for determinism
 constexpr int kChunk = 8;      // products per FP32 partial sum
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -186,25 +185,27 @@ __global__ void k_mass_mul(const float* __restrict__ in, float* __restrict__ out
 }
 
 unsigned elementwise_blocks(int64_t n) {
-  int64_t b = (n + 255) / 256;
-  return (unsigned)(b < 152 * 8 ? b : 152 * 8);
+  const int64_t b = (n + 255) / 256, cap = 8 * (int64_t)device_sm_count();
+  return (unsigned)(b < cap ? b : cap);
 }
 
 }  // namespace
 
-int krylov_partial_blocks() { return kBlocks; }
+// 3 blocks per SM, fixed per device, so the reductions' order (and result)
+// never changes between calls on one device.
+int krylov_partial_blocks() { return 3 * device_sm_count(); }
 
 cudaError_t launch_dots(const float* V, int64_t ldv, int k, const float* w, int64_t n,
                         double* partials, double* out, cudaStream_t s) {
-  k_dots<<<kBlocks, kThreads, 0, s>>>(V, ldv, k, w, n, partials);
-  k_sum_partials_cols<<<1, kThreads, 0, s>>>(partials, kBlocks, k, out);
+  k_dots<<<krylov_partial_blocks(), kThreads, 0, s>>>(V, ldv, k, w, n, partials);
+  k_sum_partials_cols<<<1, kThreads, 0, s>>>(partials, krylov_partial_blocks(), k, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_update(const float* V, int64_t ldv, int k, const double* coef, float* w,
                           int64_t n, double* partials, double* norm_out, cudaStream_t s) {
-  k_update<<<kBlocks, kThreads, 0, s>>>(V, ldv, k, coef, w, n, norm_out ? partials : nullptr);
-  if (norm_out) k_sum_partials_cols<<<1, kThreads, 0, s>>>(partials, kBlocks, 1, norm_out);
+  k_update<<<krylov_partial_blocks(), kThreads, 0, s>>>(V, ldv, k, coef, w, n, norm_out ? partials : nullptr);
+  if (norm_out) k_sum_partials_cols<<<1, kThreads, 0, s>>>(partials, krylov_partial_blocks(), 1, norm_out);
   return cudaGetLastError();
 }
 
@@ -228,8 +229,8 @@ cudaError_t launch_mass_mul(const float* in, float* out, int nx, int ny, int nz,
 
 cudaError_t launch_mass_norm(const float* g, int nx, int ny, int nz, int nf, double cell,
                              double* partials, double* out, cudaStream_t s) {
-  k_mass_norm<<<kBlocks, kThreads, 0, s>>>(g, nx, ny, nz, nf, (float)cell, partials);
-  k_sum_partials_cols<<<1, kThreads, 0, s>>>(partials, kBlocks, 1, out);
+  k_mass_norm<<<krylov_partial_blocks(), kThreads, 0, s>>>(g, nx, ny, nz, nf, (float)cell, partials);
+  k_sum_partials_cols<<<1, kThreads, 0, s>>>(partials, krylov_partial_blocks(), 1, out);
   return cudaGetLastError();
 }
 

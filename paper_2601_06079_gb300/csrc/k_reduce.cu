@@ -135,7 +135,9 @@ std::mutex g_static_mutex;
 double* g_static_ptr[kMaxDevices] = {};
 
 // Device address of g_static_partials for the current device, looked up once
-// per device (host code only knows the symbol as a host-side stand-in).
+// per device (host code only knows the symbol as a host-side stand-in).  The
+// cache lives as long as the process; a cudaDeviceReset invalidates it, which
+// the header states as a usage rule.
 cudaError_t static_partials(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);

@@ -45,6 +45,24 @@ inline cudaError_t raise_smem_limit(K* kernel, int bytes, std::atomic<unsigned l
   return e;
 }
 
+// Streaming multiprocessors of the current device (cached per device 0..63).
+// Grid sizes that must not change between calls on one device (fixed-order
+// reductions, workspace sizes) derive from it, never from a constant.
+inline int device_sm_count() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (dev >= 0 && dev < 64) {
+    const int c = cache[dev].load(std::memory_order_relaxed);
+    if (c > 0) return c;
+  }
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+    sms = 1;
+  if (dev >= 0 && dev < 64) cache[dev].store(sms, std::memory_order_relaxed);
+  return sms;
+}
+
 // Assembled 9-point Q1 stiffness stencil on a uniform 2-D grid, pre-scaled:
 // (K v)_i = c0 v_i + cx (v_W + v_E) + cy (v_S + v_N) + cd (v_SW + v_SE + v_NW + v_NE).
 struct Stencil2D {

@@ -35,8 +35,10 @@ constexpr int kNF = 8;        // order parameters
 constexpr int kC = 32;        // feature channels
 constexpr int kCin0 = 32;     // padded input channels
 constexpr int kCout = 16;     // padded output channels
-constexpr int kConvGrid = 304;
-constexpr int kWgradBlocks = 152;
+// grid of the mma.sync convolution and blocks (partial sums) of the weight
+// gradient, per device
+int conv_grid() { return 2 * pf::device_sm_count(); }
+int wgrad_blocks() { return pf::device_sm_count(); }
 constexpr int kSigBlocks = 64;  // blocks per sample of the increment-scale reduction
 
 int64_t w_count(int l) { return (int64_t)27 * kLayers[l].cin * kLayers[l].cout; }
@@ -92,7 +94,7 @@ Plan make_plan(int B, int D, int H, int W, bool training) {
     for (int l = 0; l < 4; ++l)
       for (int k = 0; k < 3; ++k) p.g[l][k] = take(2 * p.V[l] * kC);
     p.grad = take(4 * param_count());
-    p.part = take(4 * (size_t)kWgradBlocks * 27 * kC * kC);
+    p.part = take(4 * (size_t)wgrad_blocks() * 27 * kC * kC);
     p.msep = take(8 * 1024);
     p.res = take(4 * p.V[0] * kNF);
     p.resq = take(4 * p.V[0] * kNF);
@@ -141,7 +143,7 @@ cudaError_t conv(const Net& n, int cin, int cout, const void* x, const void* wt,
   if (n.tc && pf::conv3d_tc_shape_ok(n.p.B, d, h, w))
     return pf::launch_conv3d_tc(cin, cout, x, wt, bias, relu, y16, y32, n.p.B, d, h, w,
                                 n.at<int>(n.p.err), n.s);
-  return pf::launch_conv3d(cin, cout, x, wt, bias, relu, y16, y32, n.p.B, d, h, w, kConvGrid,
+  return pf::launch_conv3d(cin, cout, x, wt, bias, relu, y16, y32, n.p.B, d, h, w, conv_grid(),
                            n.s);
 }
 
@@ -226,7 +228,7 @@ pf_status backward_layer(const Net& n, int l, void* dy, void* dx, float* grad) {
   const int d = n.dim(lv, 0), h = n.dim(lv, 1), w = n.dim(lv, 2);
   const int64_t nvox = (int64_t)n.p.B * d * h * w;
   if (L.relu) SG_CUDA(pf::launch_relu_mask(dy, n.at<void>(n.p.act[l]), nvox * L.cout, n.s));
-  const int blocks = pf::conv_wgrad_blocks(n.p.B, d, h, w, kWgradBlocks);
+  const int blocks = pf::conv_wgrad_blocks(n.p.B, d, h, w, wgrad_blocks());
   SG_CUDA(pf::launch_conv3d_wgrad(L.cin, L.cout, layer_input(n, l), dy, n.at<float>(n.p.part),
                                   grad + w_off(l), n.p.B, d, h, w, blocks, n.s));
   SG_CUDA(pf::launch_bias_grad(dy, L.cout, nvox, grad + b_off(l), n.s));
@@ -388,7 +390,7 @@ pf_status pf_conv3d_check(int mode, int cin, int cout, int d, int h, int w, cons
     return PF_ERR_ARG;
   const int64_t V = (int64_t)d * h * w;
   size_t need = al(2 * V * cin) + al(2 * V * cout) + 2 * al(2 * 27 * cin * cout) + al(4 * V * kC) +
-                al(4 * (size_t)kWgradBlocks * 27 * cin * cout) + al(sizeof(int));
+                al(4 * (size_t)wgrad_blocks() * 27 * cin * cout) + al(sizeof(int));
   if (bytes < need || (mode == 1 || mode == 2 || mode == 4) && !dy || (uintptr_t)ws % 256)
     return PF_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
@@ -404,7 +406,7 @@ pf_status pf_conv3d_check(int mode, int cin, int cout, int d, int h, int w, cons
   float* y32 = (float*)p;
   p += al(4 * V * kC);
   float* part = (float*)p;
-  p += al(4 * (size_t)kWgradBlocks * 27 * cin * cout);
+  p += al(4 * (size_t)wgrad_blocks() * 27 * cin * cout);
   int* err = (int*)p;
   const bool tc = (mode == 0 || mode == 1 || mode == 5) && pf::conv3d_tc_shape_ok(1, d, h, w);
   const int selftest = mode == 5;
@@ -412,7 +414,7 @@ pf_status pf_conv3d_check(int mode, int cin, int cout, int d, int h, int w, cons
   auto run = [&](int ci, int co, const void* in, const void* wts, const float* bs) {
     return tc ? pf::launch_conv3d_tc(ci, co, in, wts, bs, 0, nullptr, y32, 1, d, h, w, err, s,
                                      selftest)
-              : pf::launch_conv3d(ci, co, in, wts, bs, 0, nullptr, y32, 1, d, h, w, kConvGrid, s);
+              : pf::launch_conv3d(ci, co, in, wts, bs, 0, nullptr, y32, 1, d, h, w, conv_grid(), s);
   };
   SG_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
   SG_CUDA(pf::launch_convert_weights(wt, cin, cout, wf, wb, s));
@@ -426,7 +428,7 @@ pf_status pf_conv3d_check(int mode, int cin, int cout, int d, int h, int w, cons
       SG_CUDA(run(cout, cin, db16, wb, nullptr));
       SG_CUDA(pf::launch_ndhwc_to_planar_add(y32, cin, cin, 1, V, nullptr, 0, 0, nullptr, out, s));
     } else {
-      const int blocks = pf::conv_wgrad_blocks(1, d, h, w, kWgradBlocks);
+      const int blocks = pf::conv_wgrad_blocks(1, d, h, w, wgrad_blocks());
       SG_CUDA(pf::launch_conv3d_wgrad(cin, cout, xb, db16, part, out, 1, d, h, w, blocks, s));
       SG_CUDA(pf::launch_bias_grad(db16, cout, V, out + 27 * cin * cout, s));
     }

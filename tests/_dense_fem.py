@@ -77,3 +77,19 @@ def energy(nx, ny, hx, hy, u, f, kappa):
             gx, gy = Gx @ u[nodes], Gy @ u[nodes]
             E += wt * (f(uq) + 0.5 * kappa * (gx * gx + gy * gy))
     return E
+
+
+def mobility_stiffness(nx, ny, hx, hy, mfield, M=1.0):
+    """Dense K_M with (K_M)_ij = sum_e sum_q w_q M(x_q) grad N_i . grad N_j, where
+    the mobility at each Gauss point is the scalar M times the Q1 interpolant
+    of the per-node field m (Eq. 9, mobility inside the divergence).  Both the
+    points and the interpolation come from this module's own tables."""
+    m = np.asarray(mfield, dtype=np.float64).ravel()
+    n = nx * ny
+    KM = np.zeros((n, n))
+    for _, _, nodes in _elements(nx, ny):
+        for xl, yl, wt in _points(hx, hy):
+            N, Gx, Gy = _shape(xl, yl, hx, hy)
+            Mq = M * float(N @ m[nodes])
+            KM[np.ix_(nodes, nodes)] += wt * Mq * (np.outer(Gx, Gx) + np.outer(Gy, Gy))
+    return KM

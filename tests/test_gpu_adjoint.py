@@ -84,30 +84,34 @@ def test_checkpoint_interval_does_not_change_the_result():
         assert torch.equal(g["mobility_field"], outs[0][1]["mobility_field"])
 
 
-def test_calibration_size_512_against_oracle_on_128_and_runs_at_512():
-    # 2-D CH, 8-Gaussian mobility, target from hidden (kappa, M, W) = (0.6, 0.8, 1.1)
-    for n, steps, check in ((128, 400, True), (512, 2000, False)):
-        shape = (n, n)
-        mob = G.gaussian_mobility(1, shape, h=1.0)
-        mob_hidden = G.gaussian_mobility(2, shape, h=1.0)
-        c0 = G.ch_initial(1, shape)
-        pf = _pf()
-        gen = pf.Solver(shape, model="ch")
-        gen.set_params(W=1.1, kappa=0.6, mobility=0.8, dt=1e-3, mobility_field=cu(mob_hidden))
-        tgt = cu(c0)
-        gen.step_explicit(tgt, steps)
-        s = pf.Solver(shape, model="ch")
-        s.set_params(W=1.0, kappa=0.5, mobility=1.0, dt=1e-3, mobility_field=cu(mob))
-        loss, g = s.adjoint(cu(c0), tgt, steps, 100)
-        assert np.isfinite(loss) and loss > 0
-        assert torch.isfinite(g["mobility_field"]).all()
-        if check:
-            P = O.Problem(shape, W=1.0, kappa=0.5, mob=1.0, mob_field=mob)
-            oloss, og = P.ch_adjoint(c0, tgt.cpu().numpy(), 1e-3, steps)
-            assert abs(loss - oloss) <= 1e-4 * abs(oloss)
-            for k in ("kappa", "W", "M"):
-                assert abs(g[k] - og[k]) <= GRAD * abs(og[k]), (k, g[k], og[k])
-            assert rel(g["mobility_field"].cpu().numpy(), og["mob_field"]) <= GRAD
+@pytest.mark.parametrize("n,steps", [(128, 400), (512, 2000)])
+def test_calibration_config_against_oracle_adjoint(n, steps):
+    # 2-D CH with an 8-Gaussian mobility field; the target comes from the
+    # oracle run with the hidden (kappa, M, W) = (0.6, 0.8, 1.1) and its own
+    # hidden field.  n = 512 with 2,000 steps and a checkpoint every 100 is the
+    # calibration workload; the oracle's discrete adjoint (pinned to central
+    # differences on the CPU) holds the whole FP64 trajectory, about 4.2 GB.
+    shape = (n, n)
+    mob = G.gaussian_mobility(1, shape, h=1.0)
+    mob_hidden = G.gaussian_mobility(2, shape, h=1.0)
+    c0 = G.ch_initial(1, shape)
+    O.set_threads(0)
+    target = O.Problem(shape, W=1.1, kappa=0.6, mob=0.8, mob_field=mob_hidden).ch_explicit(
+        c0, 1e-3, steps)
+    target32 = target.astype(np.float32)
+    pf = _pf()
+    s = pf.Solver(shape, model="ch")
+    s.set_params(W=1.0, kappa=0.5, mobility=1.0, dt=1e-3, mobility_field=cu(mob))
+    loss, g = s.adjoint(cu(c0), cu(target32), steps, 100)
+    P = O.Problem(shape, W=1.0, kappa=0.5, mob=1.0, mob_field=mob)
+    oloss, og = P.ch_adjoint(c0, target32, 1e-3, steps)
+    assert oloss > 0
+    errs = {k: abs(g[k] - og[k]) / abs(og[k]) for k in ("kappa", "W", "M")}
+    errs["mobility_field"] = rel(g["mobility_field"].cpu().numpy(), og["mob_field"])
+    print(f"calibration {n}^2 x {steps}: loss rel {abs(loss - oloss) / oloss:.2e}, grads", errs)
+    assert abs(loss - oloss) <= 1e-4 * abs(oloss)
+    for k, e in errs.items():
+        assert e <= GRAD, (k, e)
 
 
 def test_autograd_function_matches_adjoint_and_oracle_fd():

@@ -100,6 +100,24 @@ def test_ch_full_size_2048_elementwise():
     assert np.abs(out - ref).max() <= 2e-6
 
 
+def test_ch_headline_2048_full_trajectory_against_oracle():
+    # The bench workload itself: 2048 x 2048 nodes, kappa = 0.5, M = W = 1,
+    # dt = 1e-3, the full 10,000 steps (t = 10, through spinodal growth), seed 1.
+    # The FP64 oracle runs the same trajectory on the host cores (several
+    # minutes).  Bars (C18): rel-L2 <= 1e-5 on c, <= 1e-4 on c - mean(c).
+    n, steps = 2048, 10_000
+    c0 = G.ch_initial(1, (n, n))
+    out, _, _ = gpu_run("ch", c0, 1.0, steps, W=1.0, kappa=0.5, mobility=1.0, dt=1e-3)
+    O.set_threads(0)
+    ref = O.Problem((n, n), W=1.0, kappa=0.5, mob=1.0).ch_explicit(c0, 1e-3, steps)
+    assert ref.max() - ref.min() > 0.3  # the instability has grown
+    e = rel_l2(out, ref)
+    e0 = rel_l2(out - ref.mean(), ref - ref.mean())
+    print(f"CH 2048^2 x 10000: rel-L2 {e:.3e}, on c - mean(c) {e0:.3e}")
+    assert e <= REL_L2
+    assert e0 <= 1e-4
+
+
 def test_ch_full_size_2048_sampled_windows():
     # after k steps a node depends only on initial data within 2k nodes, so
     # the oracle reproduces sampled nodes from windows of radius 2k + margin;

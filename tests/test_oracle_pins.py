@@ -249,6 +249,46 @@ def test_tanh_equilibrium_profile_width_and_energy():
 
 # ---------------------------------------------------------------- conservation / dissipation
 
+@pytest.mark.parametrize("shape,h", [((5, 7), (0.7, 1.3)), ((6, 4), (1.25, 0.6)), ((4, 4), 1.0)])
+def test_mobility_stiffness_matches_dense_assembly_with_field(shape, h):
+    # Eq. 9 with a per-node mobility: M(x_q) = M * sum_a N_a(x_q) m_a at every
+    # Gauss point.  Evaluating m at the nodes or averaging it per element would
+    # give a different K_M, so a random positive field on anisotropic cells
+    # separates the readings.
+    ny, nx = shape
+    hx, hy = (h, h) if np.isscalar(h) else h
+    rng = np.random.default_rng(11 + nx * ny)
+    mfield = rng.uniform(0.3, 2.5, size=shape)
+    mu = rng.standard_normal(shape)
+    M = 0.85
+    KM = D.mobility_stiffness(nx, ny, hx, hy, mfield, M)
+    P = O.Problem(shape, h=(hx, hy), mob=M, mob_field=mfield)
+    got = P.mobility_stiffness_apply(mu)
+    np.testing.assert_allclose(got.ravel(), KM @ mu.ravel(), rtol=0, atol=1e-13 * np.abs(KM).sum())
+    # the element-averaged and node-sampled readings are far from it
+    Mc, K = D.assemble(nx, ny, hx, hy)
+    assert np.abs(KM @ mu.ravel() - M * mfield.ravel() * (K @ mu.ravel())).max() > 1e-3
+
+
+def test_ch_step_with_mobility_field_matches_dense_assembly():
+    # one explicit split-CH step, c1 = c0 - dt m^-1 K_M m^-1 (F(c0) + kappa K c0),
+    # assembled from dense matrices and the dense nonlinear vector
+    ny, nx, hx, hy = 5, 6, 0.9, 1.2
+    rng = np.random.default_rng(5)
+    mfield = rng.uniform(0.5, 1.8, size=(ny, nx))
+    c0 = 0.5 + 0.2 * rng.standard_normal((ny, nx))
+    W, kappa, M, dt = 1.3, 0.7, 0.9, 0.01
+    _, K = D.assemble(nx, ny, hx, hy)
+    KM = D.mobility_stiffness(nx, ny, hx, hy, mfield, M)
+    Mc, _ = D.assemble(nx, ny, hx, hy)
+    mL = Mc.sum(1)
+    F = D.nonlinear_vector(nx, ny, hx, hy, c0, dw(W)[1])
+    mu = (F + kappa * K @ c0.ravel()) / mL
+    expect = c0.ravel() - dt * (KM @ mu) / mL
+    P = O.Problem((ny, nx), h=(hx, hy), W=W, kappa=kappa, mob=M, mob_field=mfield)
+    np.testing.assert_allclose(P.ch_explicit(c0, dt, 1).ravel(), expect, rtol=0, atol=1e-13)
+
+
 def test_ch_mass_conserved_exactly_with_mobility_field():
     shape = (24, 20)
     mob = G.gaussian_mobility(2, shape, h=1.0, width=(2.0, 6.0))
