@@ -50,6 +50,31 @@ N_TSTEPS = 10_000
 PAR = dict(W=1.0, kappa=0.5, mobility=1.0, dt=1e-3)
 DOF_PER_NODE = 2
 ALG_BYTES_PER_NODE_STEP = 8  # read c, write c; mu never leaves the chip
+# FP32 flop per node of the fused CH step, counted from the kernel's sweep (one
+# lane = two nodes): 28 packed FMA (x 2 lanes x 2 flop) + 13 packed add/sub
+# (x 2) + 8 scalar add/sub = 146 per lane-row; the warm-up rows of each band
+# and the halo lanes of each strip are excluded (they repeat this work).
+FLOP_PER_NODE_STEP = 73
+NOMINAL_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 lanes x 2 flop x max SM clock
+_FP32_PEAK = {}
+
+
+def fp32_peak(dev, stream):
+    """FP32 FMA throughput measured on this GPU in this run (pf_fp32_peak),
+    the peak of the ALU rooflines."""
+    import torch
+
+    from paper_2601_06079_gb300 import _lib
+    if dev not in _FP32_PEAK:
+        sink = torch.zeros(4, dtype=torch.float32, device=dev)
+        vals = []
+        for _ in range(3):
+            st, t = _lib.pf_fp32_peak(stream.cuda_stream, sink.data_ptr())
+            if st != 0:
+                raise RuntimeError(f"pf_fp32_peak failed ({st})")
+            vals.append(t)
+        _FP32_PEAK[dev] = max(vals)
+    return _FP32_PEAK[dev]
 WORKLOAD = "ch2d_2048x2048_10000steps"
 KERNEL_SRC = os.path.join(ROOT, "paper_2601_06079_gb300", "csrc", "k_explicit2d.cu")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ch2d_2048_dram_traffic.json")
@@ -234,6 +259,8 @@ def run_ours(args):
         return
     peak, peak_kind = _peaks()
     achieved = ALG_BYTES_PER_NODE_STEP * nodes / step_launch_s / 1e9
+    alu_peak = fp32_peak(dev, stream)
+    alu_achieved = FLOP_PER_NODE_STEP * nodes / step_launch_s / 1e12
     line = {
         "metric": "DOF-steps/s (CH split form, 2 DOF/node) & %HBM roofline",
         "value": value,
@@ -255,6 +282,13 @@ def run_ours(args):
                      "peak_source": f"{peak_kind} hbm_gbs",
                      "per_launch_s": step_launch_s,
                      "alg_bytes_per_launch": ALG_BYTES_PER_NODE_STEP * nodes},
+        # both planes stay in L2 over a trajectory: the FP32 pipe binds, so the
+        # same kernel against the measured FP32 FMA peak
+        "roofline_alu": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak,
+                         "unit": "TFLOP/s", "frac": alu_achieved / alu_peak,
+                         "flop_per_node": FLOP_PER_NODE_STEP,
+                         "peak_source": "measured FP32 FMA (pf_fp32_peak, this run)",
+                         "nominal_peak": NOMINAL_FP32_TFLOPS},
         "e2e": {"value": e2e_value, "unit": "DOF-steps/s",
                 "h2d_bytes_per_step": nodes * 4, "d2h_bytes_per_step": nodes * 4 + 16},
         "gpu_launches": args.steps * (N_TSTEPS + 4),
@@ -439,7 +473,7 @@ def forms_eshelby(dev, stream, flush, n=129):
     # per interior node: 13 mirror pairs x 3 components x 3 adds (two
     # differences and their sum) + 75 FMA (39 diagonal, 36 nonzero couplings)
     flop = 13 * 3 * 3 + 2 * 75
-    peak_tflops = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 lanes x 2 flop x max SM clock
+    peak_tflops = fp32_peak(dev, stream)
     el.solve(rtol=1e-6)  # warm
     x = el.empty()
     t_solve = _timed(stream, lambda: el.solve(u=x, rtol=1e-6))
@@ -454,6 +488,7 @@ def forms_eshelby(dev, stream, flush, n=129):
             "apply_us": t_apply * 1e6,
             "apply_roofline": {"bound": "alu", "achieved": flop * nodes / t_apply / 1e12,
                                "peak": peak_tflops, "unit": "TFLOP/s",
+                               "peak_source": "measured FP32 FMA (pf_fp32_peak, this run)",
                                "frac": flop * nodes / t_apply / 1e12 / peak_tflops,
                                "hbm_gbs_at_24B_per_node": 24 * nodes / t_apply / 1e9},
             "solve_ms": t_solve * 1e3, "cg_iterations": it_solve,
@@ -486,12 +521,13 @@ def forms_jvp(dev, stream, flush, n=128):
     nodes = n ** 3
     hbm, _ = _peaks()
     flop = 960 + 256 + 512 + 240 + 1104 + 96
-    peak_tflops = 152 * 128 * 2 * 2.07e9 / 1e12
+    peak_tflops = fp32_peak(dev, stream)
     return {"mesh": f"{n}^3 nodes x 8 order parameters", "us": t * 1e6,
             "hbm": {"achieved_gbs": 96 * nodes / t / 1e9, "peak_gbs": hbm,
                     "frac": 96 * nodes / t / 1e9 / hbm},
             "alu": {"flop_per_node": flop, "achieved_tflops": flop * nodes / t / 1e12,
-                    "peak_tflops": peak_tflops, "frac": flop * nodes / t / 1e12 / peak_tflops},
+                    "peak_tflops": peak_tflops, "frac": flop * nodes / t / 1e12 / peak_tflops,
+                    "peak_source": "measured FP32 FMA (pf_fp32_peak, this run)"},
             "accuracy_gate": "<= 2e-6 rel vs the FP64 oracle JVP (tests/test_gpu_implicit.py)"}
 
 
@@ -596,9 +632,23 @@ def forms_adjoint(dev, stream, n=512, n_steps=2000, ckpt=100):
     loss, g = s.adjoint(c0, target, n_steps, ckpt)
     torch.cuda.synchronize()
     t_adj = time.perf_counter() - t0
+    # algorithmic bytes per node: forward step with the mobility field 12 B
+    # (c in, c out, m in); reverse step 24 B (lambda in, c^n, m, lambda out, the
+    # FP64 mobility-gradient read-modify-write counted as 8 B of FP32 traffic);
+    # the checkpointed recompute repeats the forward step: 36 B per reverse step
+    hbm, kind = _peaks()
+    nodes = n * n
+    t_rev = max(t_adj - t_fwd, 1e-12)  # recompute + reverse, after the checkpointing forward
+    rev_gbs = 36 * nodes * n_steps / t_rev / 1e9
     return {"mesh": f"{n}x{n}", "steps": n_steps, "checkpoint_every": ckpt,
             "forward_ms": 1e3 * t_fwd, "adjoint_ms": 1e3 * t_adj,
             "adjoint_over_forward": t_adj / t_fwd,
+            "reverse_step_us": 1e6 * t_rev / n_steps,
+            "reverse_roofline": {"bound": "hbm", "bytes_per_node": 36, "achieved": rev_gbs,
+                                 "peak": hbm, "unit": "GB/s", "frac": rev_gbs / hbm,
+                                 "peak_source": f"{kind} hbm_gbs",
+                                 "note": "per reverse step incl. its recompute; 512^2 planes "
+                                         "stay in L2"},
             "gradients": "kappa, W, M, 262,144-entry mobility field, c0",
             "accuracy_gate": "<= 1e-4 vs central FD and the oracle adjoint (tests/test_gpu_adjoint.py)"}
 

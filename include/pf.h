@@ -193,7 +193,8 @@ pf_status pf_implicit_adjoint_workspace(pf_ctx* ctx, int64_t n_steps, size_t* by
  * (Eq. II.1-II.6): n_steps backward-Euler steps (Eq. 13-14, Newton-GMRES with
  * opts, may be NULL) from U0 (device), objective O = (1/V) sum_i m_i U^N_i (the
  * domain average of Eq. 19), theta = (L, kappa).  Reverse sweep per step: one
- * GMRES solve of J(U^{n+1})^T mu = lambda^{n+1} (J = M/dt + L H is symmetric),
+ * GMRES solve of J(U^{n+1})^T mu = lambda^{n+1} (J = M/dt + L H is symmetric;
+ * relative tolerance 1e-6, or opts->gmres_rtol where that is smaller),
  * dO/dL -= mu . r(U^{n+1}), dO/dkappa -= mu . L K U^{n+1}, lambda^n = M mu / dt.
  * objective, grads[2] = [dO/dL, dO/dkappa]: host.  workspace: device, >=
  * pf_implicit_adjoint_workspace bytes, 256-byte aligned.  stats (host, may be
@@ -443,6 +444,17 @@ pf_status pf_elastic_sensitivity(const pf_elastic* e, const float* g, float* u, 
                                  double* objective, double* grads, pf_cg_stats* stats);
 
 /* Human-readable description of the last failure on this context. */
+/* Measured FP32 FMA throughput of the current device, in TFLOP/s (2 flop per
+ * FMA).  No counterpart in the paper: it is the peak that the ALU-bound
+ * kernels' rooflines are stated against (the bench measures it in the same
+ * run).  Times a kernel of independent packed FP32 FMA chains on every SM
+ * (best of three launches after a warm-up) on `stream` (cudaStream_t, NULL =
+ * legacy default).  dev_sink: device, >= 4 bytes, that the kernel may write
+ * (it keeps the chains from being optimised away).  tflops: host, 1 double.
+ * PF_ERR_ARG for NULL pointers, PF_ERR_CUDA if a launch fails.  Synchronises
+ * the stream. */
+pf_status pf_fp32_peak(void* stream, float* dev_sink, double* tflops);
+
 const char* pf_last_error(const pf_ctx* ctx);
 
 /* Release the context (not the caller's workspace or arrays). NULL is a no-op. */

@@ -153,6 +153,8 @@ def lib():
                                           C.POINTER(C.c_double), C.POINTER(pf_newton_stats)]
         L.pf_set_form.restype = st
         L.pf_set_form.argtypes = [ctx, C.c_int]
+        L.pf_fp32_peak.restype = st
+        L.pf_fp32_peak.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]
         E = C.POINTER(pf_elastic)
         vp = C.c_void_p
         L.pf_elastic_workspace.restype = st
@@ -189,7 +191,7 @@ def exported_symbols():
             "pf_surrogate_loss_grad",
             "pf_conv3d_check", "pf_energy", "pf_elastic_workspace", "pf_elastic_apply",
             "pf_elastic_load", "pf_elastic_solve", "pf_elastic_sensitivity",
-            "pf_energy2d_static", "pf_last_error", "pf_destroy"]
+            "pf_energy2d_static", "pf_fp32_peak", "pf_last_error", "pf_destroy"]
 
 
 # --- thin same-name wrappers -------------------------------------------------
@@ -223,6 +225,12 @@ PF_FORM_FUSED_GRAPH, PF_FORM_FUSED_STREAM, PF_FORM_TWO_PASS = 0, 1, 2
 
 def pf_set_form(ctx, form):
     return lib().pf_set_form(ctx, int(form))
+
+
+def pf_fp32_peak(stream, sink_ptr):
+    t = C.c_double(0.0)
+    s = lib().pf_fp32_peak(C.c_void_p(stream), C.c_void_p(sink_ptr), C.byref(t))
+    return s, t.value
 
 
 def pf_step_explicit(ctx, state_ptr, n_steps):

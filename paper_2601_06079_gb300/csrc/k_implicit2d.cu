@@ -34,11 +34,17 @@ __device__ __forceinline__ int mirror(int k, int n) {
 
 __device__ __forceinline__ float gpt(int i) { return i ? kGHi : kGLo; }
 
-// 9-point stencil s at node (y, x) of a staged plane
+// 9-point stencil s at node (y, x) of a staged plane.  The Q1 stiffness rows
+// sum to zero (c0 = -2 cx - 2 cy - 4 cd), so K v is applied to the differences
+// v_j - v_i: for smooth fields each difference of neighbouring FP32 values is
+// exact, where c0 v_i + sum c_j v_j would cancel to a few significant bits.
 template <int W_>
 __device__ __forceinline__ float stencil(const float (*V)[W_], int y, int x, const Stencil2D& k) {
-  return k.c0 * V[y][x] + k.cx * (V[y][x - 1] + V[y][x + 1]) + k.cy * (V[y - 1][x] + V[y + 1][x]) +
-         k.cd * (V[y - 1][x - 1] + V[y - 1][x + 1] + V[y + 1][x - 1] + V[y + 1][x + 1]);
+  const float c = V[y][x];
+  return k.cx * ((V[y][x - 1] - c) + (V[y][x + 1] - c)) +
+         k.cy * ((V[y - 1][x] - c) + (V[y + 1][x] - c)) +
+         k.cd * (((V[y - 1][x - 1] - c) + (V[y - 1][x + 1] - c)) +
+                 ((V[y + 1][x - 1] - c) + (V[y + 1][x + 1] - c)));
 }
 
 template <bool kJVP, bool kCH>

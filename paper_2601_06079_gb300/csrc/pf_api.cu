@@ -1405,6 +1405,9 @@ pf_status pf_implicit_adjoint(pf_ctx* c, const float* U0, int64_t n_steps,
   grads[0] = grads[1] = 0.0;
   const int restart = opts ? opts->gmres_restart : 30;
   const int maxit = opts ? opts->gmres_max_iters : 300;
+  // adjoint solves: relative tolerance 1e-6, or the caller's GMRES tolerance if tighter
+  const double adj_rtol = (opts && opts->gmres_rtol > 0.0 && opts->gmres_rtol < 1e-6)
+                              ? opts->gmres_rtol : 1e-6;
   for (int64_t s = n_steps - 1; s >= 0; --s) {
     const float* U = traj(s + 1);
     PF_CUDA(cudaMemcpyAsync(c->u, U, sizeof(float) * n, cudaMemcpyDeviceToDevice, c->stream));
@@ -1412,7 +1415,7 @@ pf_status pf_implicit_adjoint(pf_ctx* c, const float* U0, int64_t n_steps,
                                 -1.0f, 1, c->stream));  // G = -M^-1 lambda
     int gi = 0;
     double rel = 0.0;
-    if ((st = gmres3d(c, restart, 10 * maxit, 1e-6, 0.0, &gi, &rel)) != PF_OK) return st;
+    if ((st = gmres3d(c, restart, 10 * maxit, adj_rtol, 0.0, &gi, &rel)) != PF_OK) return st;
     tot.gmres_iters += gi;
     double d = 0.0;
     PF_CUDA(residual3d(c, U, U, tmp, 1));  // L r(U)

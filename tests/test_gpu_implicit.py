@@ -248,50 +248,40 @@ def test_implicit_adjoint_matches_oracle_table1_setting():
     U0 = G.ac_initial(11, shape, 0.2, 0.8)
     s = pf.Solver(shape, h=h, model="ac")
     s.set_params(W=1.0, kappa=2.0, mobility=1.0, dt=0.5)
+    # adjoint solves to 1e-7 (FP32 Newton itself stops near 1e-7 relative)
     O_gpu, g, st = s.implicit_adjoint(torch.from_numpy(U0).cuda(), 6, newton_rtol=1e-7,
-                                      gmres_rtol=1e-6)
+                                      gmres_rtol=1e-7)
     P = O.Problem(shape, h=h, W=1.0, kappa=2.0, mob=1.0)
     O_ref, g_ref = P.implicit_adjoint(U0.astype(np.float64), 0.5, 6)
     assert abs(O_gpu - O_ref) <= 1e-6 * abs(O_ref)
+    print("Table 1 setting rel errors (L, kappa):", abs(g["L"] - g_ref[0]) / abs(g_ref[0]),
+          abs(g["kappa"] - g_ref[1]) / abs(g_ref[1]))
     assert abs(g["L"] - g_ref[0]) <= 1e-4 * abs(g_ref[0]), (g, g_ref)
-    # dO/dkappa is a small difference of large terms (mu . L K U over the mesh);
-    # with FP32 states and adjoints it holds to 0.5 per mille of the FP64 value
-    assert abs(g["kappa"] - g_ref[1]) <= 5e-4 * abs(g_ref[1]), (g, g_ref)
+    assert abs(g["kappa"] - g_ref[1]) <= 1e-4 * abs(g_ref[1]), (g, g_ref)
 
 
-def test_implicit_adjoint_3d_fan_chen_matches_central_differences():
-    # the same reverse sweep on the 3-D grain-growth operators (symmetric J)
+def test_implicit_adjoint_3d_fan_chen_matches_oracle_adjoint():
+    # the same reverse sweep on the 3-D grain-growth operators (symmetric J),
+    # against the oracle's discrete adjoint (pinned to FP64 central differences
+    # on the CPU): 16^3 nodes, 4 order parameters, 3 steps of dt = 0.5
     import paper_2601_06079_gb300 as pf
     from paper_2601_06079_gb300 import warmstart as WS
     n = 16
-    U0 = torch.from_numpy(G.voronoi_grains(3, n=n, n_seeds=6, n_op=4)).cuda()
-
-    def solver(L, kappa):
-        s = pf.Solver((n, n, n), model="fanchen", n_fields=4)
-        s.set_params(dt=0.5, **{**WS.FANCHEN, "mobility": L, "kappa": kappa})
-        return s
-    O0, g, _ = solver(1.0, 1.0).implicit_adjoint(U0, 3, newton_rtol=1e-7, gmres_rtol=1e-6)
-    # central differences of the same objective through the forward solver (FP32:
-    # a large step keeps the rounding out of the quotient)
-    eps = 2e-2
-    m = torch.ones((n, n, n), dtype=torch.float64, device="cuda")
-    for ax in range(3):
-        idx = [slice(None)] * 3
-        idx[ax] = 0
-        m[tuple(idx)] *= 0.5
-        idx[ax] = -1
-        m[tuple(idx)] *= 0.5
-    V = float((n - 1) ** 3)
-
-    def obj(L, kappa):
-        s = solver(L, kappa)
-        U = U0.clone()
-        s.step_implicit(U, 3, newton_rtol=1e-7, gmres_rtol=1e-6)
-        return float((U.double().view(4, n, n, n) * m).sum() / V)
-    fdL = (obj(1.0 + eps, 1.0) - obj(1.0 - eps, 1.0)) / (2 * eps)
-    fdk = (obj(1.0, 1.0 + eps) - obj(1.0, 1.0 - eps)) / (2 * eps)
-    assert abs(g["L"] - fdL) <= 2e-2 * abs(fdL), (g, fdL)
-    assert abs(g["kappa"] - fdk) <= 2e-2 * abs(fdk), (g, fdk)
+    U0 = G.voronoi_grains(3, n=n, n_seeds=6, n_op=4)
+    s = pf.Solver((n, n, n), model="fanchen", n_fields=4)
+    s.set_params(dt=0.5, **{**WS.FANCHEN, "mobility": 1.0, "kappa": 1.0})
+    O_gpu, g, _ = s.implicit_adjoint(torch.from_numpy(U0).cuda(), 3, newton_rtol=1e-7,
+                                     gmres_rtol=1e-6)
+    fc = WS.FANCHEN
+    P = O.Problem((n, n, n), energy="fan_chen", nf=4, kappa=1.0, mob=1.0, alpha=fc["alpha"],
+                  beta=fc["beta"], gamma=fc["gamma"])
+    O_ref, g_ref = P.implicit_adjoint(U0.astype(np.float64), 0.5, 3)
+    errs = (abs(O_gpu - O_ref) / abs(O_ref), abs(g["L"] - g_ref[0]) / abs(g_ref[0]),
+            abs(g["kappa"] - g_ref[1]) / abs(g_ref[1]))
+    print("3-D Fan-Chen implicit adjoint rel errors (O, L, kappa):", errs)
+    assert errs[0] <= 1e-6
+    assert errs[1] <= 1e-4, (g, g_ref)
+    assert errs[2] <= 1e-4, (g, g_ref)
 
 
 def test_workspace_growth_between_explicit_and_implicit_steps():
