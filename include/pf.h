@@ -369,15 +369,17 @@ pf_status pf_surrogate_loss_grad(const float* params, float out_scale, const flo
  * planar FP32 [c][d][h][w]; weights [27][c_out][c_in] FP32 (rounded to BF16
  * inside).  (c_in, c_out) in {(16,32), (32,32), (32,16)}; d even, h and w
  * multiples of 8.  mode 0: out = conv(x) + bias; mode 1: out = conv^T(dy);
- * mode 2: out = [dW (27 x c_out x c_in), db (c_out)] for dy.  Modes 0 and 1
- * run the tcgen05 kernel (d even, h a multiple of 8 -- always here); modes 3
- * and 4 are 0 and 1 on the mma.sync kernel; mode 5 is the failure-path
- * self-test: mode 0 with no input copies issued, so every bounded pipeline
- * wait expires (about 2 s), the kernel frees its tensor memory and returns,
- * and the call reports PF_ERR_TIMEOUT with the context still usable.  Workspace (256-byte aligned) of
- * at least 2V(c_in + c_out) + 4 * 27 c_in c_out + 128 V + 16,809,984 bytes
- * plus 256 per part (V = d h w).  Synchronises the stream; PF_ERR_TIMEOUT if a
- * tensor-core pipeline wait expired. */
+ * mode 2: out = [dW (27 x c_out x c_in), db (c_out)] for dy.  Modes 0, 1 and
+ * 2 run the tcgen05 kernels (d even, h and w multiples of 8 -- always here);
+ * modes 3, 4 and 6 are 0, 1 and 2 on the mma.sync kernels; mode 5 is the
+ * failure-path self-test: mode 0 with no input copies issued, so every
+ * bounded pipeline wait expires (about 2 s), the kernel frees its tensor
+ * memory and returns, and the call reports PF_ERR_TIMEOUT with the context
+ * still usable.  Workspace (256-byte aligned) of at least 2V(c_in + c_out) +
+ * 4 * 27 c_in c_out + 128 V + 147,456 S bytes plus 256 per part (V = d h w,
+ * S = the device's SM count: 22,413,312 bytes of partial sums on 152 SMs).
+ * Synchronises the stream; PF_ERR_TIMEOUT if a tensor-core pipeline wait
+ * expired. */
 pf_status pf_conv3d_check(int mode, int cin, int cout, int d, int h, int w, const float* x,
                           const float* wt, const float* bias, const float* dy, float* out,
                           void* workspace, size_t bytes, void* stream);

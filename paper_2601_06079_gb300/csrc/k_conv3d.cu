@@ -268,19 +268,66 @@ __global__ void k_sum_parts(const float* __restrict__ part, int nb, int64_t n, f
   }
 }
 
-// bias gradient: db[c] = sum over voxels dy[v][c] (one block per channel, fixed order)
-__global__ void k_bias_grad(const __nv_bfloat16* __restrict__ dy, int C, int64_t nvox, float* db) {
-  __shared__ float red[256];
-  const int c = blockIdx.x;
-  float s = 0.0f;
-  for (int64_t v = threadIdx.x; v < nvox; v += blockDim.x) s += __bfloat162float(dy[v * C + c]);
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
+// Bias gradient db[c] = sum over voxels of dy[v][c], in two fixed-order passes.
+// Pass 1: block b owns a contiguous range of voxels; a thread owns one 8-channel
+// chunk and strides over the range's voxels with 16-byte loads (four loads in
+// flight), then the threads of each chunk are summed through shared memory
+// into part[b][c].  Pass 2: one thread per channel sums the blocks in order.
+template <int C>
+__global__ void __launch_bounds__(256) k_bias_part(const __nv_bfloat16* __restrict__ dy,
+                                                   int64_t nvox, float* __restrict__ part) {
+  constexpr int NC = C / 8, VPI = 256 / NC;  // chunks per voxel, voxels per pass of the block
+  __shared__ float red[256 * 9];
+  const int c = threadIdx.x % NC, vl = threadIdx.x / NC;
+  const int64_t per = (nvox + gridDim.x - 1) / gridDim.x;
+  const int64_t v0 = (int64_t)blockIdx.x * per;
+  const int64_t v1 = v0 + per < nvox ? v0 + per : nvox;
+  float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int64_t v = v0 + vl;
+  for (; v + 3 * VPI < v1; v += 4 * VPI) {
+    uint4 q[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      q[u] = *reinterpret_cast<const uint4*>(dy + (v + u * VPI) * C + 8 * c);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&q[u]);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float2 f = __bfloat1622float2(h[j]);
+        s[2 * j] += f.x;
+        s[2 * j + 1] += f.y;
+      }
+    }
   }
-  if (threadIdx.x == 0) db[c] = red[0];
+  for (; v < v1; v += VPI) {
+    const uint4 q = *reinterpret_cast<const uint4*>(dy + v * C + 8 * c);
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&q);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float2 f = __bfloat1622float2(h[j]);
+      s[2 * j] += f.x;
+      s[2 * j + 1] += f.y;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 8; ++j) red[threadIdx.x * 9 + j] = s[j];
+  __syncthreads();
+  if (threadIdx.x < C) {
+    const int ch = threadIdx.x, k = ch / 8, j = ch % 8;
+    float t = 0.0f;
+    for (int r = 0; r < VPI; ++r) t += red[(r * NC + k) * 9 + j];
+    part[(int64_t)blockIdx.x * C + ch] = t;
+  }
+}
+
+__global__ void k_bias_final(const float* __restrict__ part, int nblk, int C, float* db) {
+  const int c = threadIdx.x;
+  if (c >= C) return;
+  float t = 0.0f;
+#pragma unroll 8
+  for (int b = 0; b < nblk; ++b) t += part[(int64_t)b * C + c];
+  db[c] = t;
 }
 
 }  // namespace
@@ -334,8 +381,20 @@ cudaError_t launch_conv3d_wgrad(int cin, int cout, const void* x, const void* dy
   return cudaGetLastError();
 }
 
-cudaError_t launch_bias_grad(const void* dy, int C, int64_t nvox, float* db, cudaStream_t s) {
-  k_bias_grad<<<C, 256, 0, s>>>((const __nv_bfloat16*)dy, C, nvox, db);
+int bias_grad_blocks() { return 4 * device_sm_count(); }
+
+cudaError_t launch_bias_grad(const void* dy, int C, int64_t nvox, float* db, float* scratch,
+                             cudaStream_t s) {
+  const __nv_bfloat16* DY = (const __nv_bfloat16*)dy;
+  int64_t nb = bias_grad_blocks();
+  if (nb > nvox) nb = nvox < 1 ? 1 : nvox;
+  if (C == 16)
+    k_bias_part<16><<<(unsigned)nb, 256, 0, s>>>(DY, nvox, scratch);
+  else if (C == 32)
+    k_bias_part<32><<<(unsigned)nb, 256, 0, s>>>(DY, nvox, scratch);
+  else
+    return cudaErrorInvalidValue;
+  k_bias_final<<<1, 32, 0, s>>>(scratch, (int)nb, C, db);
   return cudaGetLastError();
 }
 

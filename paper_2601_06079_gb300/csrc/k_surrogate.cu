@@ -112,24 +112,37 @@ __global__ void k_incr_sumsq(const float* __restrict__ x, int nf, int nxc, int64
   __shared__ double red[kT];
   const int b = blockIdx.y;
   const float* u = x + (int64_t)b * nxc * V;
-  // differences and squares in FP32, runs of 16 summed in FP32 and the runs in
-  // FP64: GB300's FP64 rate is a small fraction of its FP32 rate, so no FP64
-  // arithmetic per element
+  // differences and squares in FP32 (16-byte loads, four independent sums per
+  // thread), runs of 16 vectors summed in FP32 and the runs in FP64: GB300's
+  // FP64 rate is a small fraction of its FP32 rate, so no FP64 arithmetic per
+  // element.  nf * V is a multiple of 4 (the volume's sides are multiples of 16).
+  const float4* u0 = reinterpret_cast<const float4*>(u);
+  const float4* u1 = reinterpret_cast<const float4*>(u + nf * V);
+  const float4* u2 = reinterpret_cast<const float4*>(u + 2 * nf * V);
+  const int64_t n4 = (int64_t)nf * V / 4;
   double acc = 0.0;
-  float run = 0.0f;
+  float4 run = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   int k = 0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)nf * V;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const float d = second ? (u[i] - u[nf * V + i]) - (u[nf * V + i] - u[2 * nf * V + i])
-                           : u[i] - u[nf * V + i];
-    run = fmaf(d, d, run);
+    const float4 a0 = u0[i], a1 = u1[i];
+    float4 d = make_float4(a0.x - a1.x, a0.y - a1.y, a0.z - a1.z, a0.w - a1.w);
+    if (second) {
+      const float4 a2 = u2[i];
+      d = make_float4(d.x - (a1.x - a2.x), d.y - (a1.y - a2.y), d.z - (a1.z - a2.z),
+                      d.w - (a1.w - a2.w));
+    }
+    run.x = fmaf(d.x, d.x, run.x);
+    run.y = fmaf(d.y, d.y, run.y);
+    run.z = fmaf(d.z, d.z, run.z);
+    run.w = fmaf(d.w, d.w, run.w);
     if (++k == 16) {
-      acc += (double)run;
-      run = 0.0f;
+      acc += (double)((run.x + run.y) + (run.z + run.w));
+      run = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
       k = 0;
     }
   }
-  acc += (double)run;
+  acc += (double)((run.x + run.y) + (run.z + run.w));
   red[threadIdx.x] = acc;
   __syncthreads();
   for (int o = kT / 2; o > 0; o >>= 1) {

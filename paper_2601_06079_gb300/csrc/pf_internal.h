@@ -275,9 +275,20 @@ cudaError_t launch_conv3d_tc(int cin, int cout, const void* x, const void* wt, c
                              int relu, void* y16, float* y32, int B, int D, int H, int W,
                              int* err, cudaStream_t s, int selftest = 0);
 int conv_wgrad_blocks(int B, int D, int H, int W, int max_blocks);
+// Weight gradient on tcgen05 (k_wgrad_tc.cu): needs W % 8 == 0 and a voxel
+// count that is a multiple of 64; part holds wgrad_tc_part_floats() floats of
+// per-block partial sums; err is the pipeline-timeout flag.
+bool wgrad_tc_shape_ok(int B, int D, int H, int W);
+int wgrad_tc_blocks();
+size_t wgrad_tc_part_floats();
+cudaError_t launch_wgrad_tc(int cin, int cout, const void* x, const void* dy, float* part,
+                            float* dw, int B, int D, int H, int W, int* err, cudaStream_t s);
 cudaError_t launch_conv3d_wgrad(int cin, int cout, const void* x, const void* dy, float* part,
                                 float* dw, int B, int D, int H, int W, int blocks, cudaStream_t s);
-cudaError_t launch_bias_grad(const void* dy, int C, int64_t nvox, float* db, cudaStream_t s);
+// db[c] = sum over voxels of dy[v][c]; scratch: >= bias_grad_blocks() * C floats
+int bias_grad_blocks();
+cudaError_t launch_bias_grad(const void* dy, int C, int64_t nvox, float* db, float* scratch,
+                             cudaStream_t s);
 cudaError_t launch_planar_to_ndhwc(const float* in, int nf, int C, int B, int64_t V, int mode,
                                    const float* sig, void* out, cudaStream_t s);
 cudaError_t launch_ndhwc_to_planar_add(const float* y, int C, int nf, int B, int64_t V,

@@ -39,7 +39,12 @@ constexpr int kCout = 16;     // padded output channels
 // gradient, per device
 int conv_grid() { return 2 * pf::device_sm_count(); }
 int wgrad_blocks() { return pf::device_sm_count(); }
-constexpr int kSigBlocks = 64;  // blocks per sample of the increment-scale reduction
+// floats of weight-gradient partials: the tcgen05 kernel's or the mma.sync one's
+size_t part_floats(int cin, int cout) {
+  const size_t a = pf::wgrad_tc_part_floats(), b = (size_t)wgrad_blocks() * 27 * cin * cout;
+  return a > b ? a : b;
+}
+constexpr int kSigBlocks = 256;  // blocks per sample of the increment-scale reduction
 
 int64_t w_count(int l) { return (int64_t)27 * kLayers[l].cin * kLayers[l].cout; }
 int64_t w_off(int l) {
@@ -94,7 +99,7 @@ Plan make_plan(int B, int D, int H, int W, bool training) {
     for (int l = 0; l < 4; ++l)
       for (int k = 0; k < 3; ++k) p.g[l][k] = take(2 * p.V[l] * kC);
     p.grad = take(4 * param_count());
-    p.part = take(4 * (size_t)wgrad_blocks() * 27 * kC * kC);
+    p.part = take(4 * part_floats(kC, kC));
     p.msep = take(8 * 1024);
     p.res = take(4 * p.V[0] * kNF);
     p.resq = take(4 * p.V[0] * kNF);
@@ -228,10 +233,16 @@ pf_status backward_layer(const Net& n, int l, void* dy, void* dx, float* grad) {
   const int d = n.dim(lv, 0), h = n.dim(lv, 1), w = n.dim(lv, 2);
   const int64_t nvox = (int64_t)n.p.B * d * h * w;
   if (L.relu) SG_CUDA(pf::launch_relu_mask(dy, n.at<void>(n.p.act[l]), nvox * L.cout, n.s));
-  const int blocks = pf::conv_wgrad_blocks(n.p.B, d, h, w, wgrad_blocks());
-  SG_CUDA(pf::launch_conv3d_wgrad(L.cin, L.cout, layer_input(n, l), dy, n.at<float>(n.p.part),
-                                  grad + w_off(l), n.p.B, d, h, w, blocks, n.s));
-  SG_CUDA(pf::launch_bias_grad(dy, L.cout, nvox, grad + b_off(l), n.s));
+  if (n.tc && pf::wgrad_tc_shape_ok(n.p.B, d, h, w)) {
+    SG_CUDA(pf::launch_wgrad_tc(L.cin, L.cout, layer_input(n, l), dy, n.at<float>(n.p.part),
+                                grad + w_off(l), n.p.B, d, h, w, n.at<int>(n.p.err), n.s));
+  } else {
+    const int blocks = pf::conv_wgrad_blocks(n.p.B, d, h, w, wgrad_blocks());
+    SG_CUDA(pf::launch_conv3d_wgrad(L.cin, L.cout, layer_input(n, l), dy, n.at<float>(n.p.part),
+                                    grad + w_off(l), n.p.B, d, h, w, blocks, n.s));
+  }
+  // (the weight-gradient partials are summed by now: their buffer is free)
+  SG_CUDA(pf::launch_bias_grad(dy, L.cout, nvox, grad + b_off(l), n.at<float>(n.p.part), n.s));
   if (dx) SG_CUDA(conv(n, L.cout, L.cin, dy, n.at<void>(n.p.wb[l]), nullptr, 0, dx, nullptr, d, h, w));
   return PF_OK;
 }
@@ -380,18 +391,19 @@ pf_status pf_conv3d_check(int mode, int cin, int cout, int d, int h, int w, cons
   // Single-layer probe of the convolution kernels for parity tests: planar FP32
   // in and out ([c][d][h][w], one sample), weights [27][c_out][c_in] FP32.
   // mode 0: out = conv(x) + bias; 1: out = conv^T(dy); 2: out = [dW (27 c_out c_in), db];
-  // modes 0 and 1 take the tcgen05 kernel where the shape allows, 3 and 4 are
-  // 0 and 1 on the mma.sync kernel; 5 is mode 0 on the tcgen05 kernel with no
-  // input copies issued (the bounded pipeline waits must expire: PF_ERR_TIMEOUT).
+  // modes 0, 1 and 2 take the tcgen05 kernels where the shape allows, 3, 4 and 6
+  // are 0, 1 and 2 on the mma.sync kernels; 5 is mode 0 on the tcgen05 kernel with
+  // no input copies issued (the bounded pipeline waits must expire: PF_ERR_TIMEOUT).
   const bool ok_c = (cin == 16 && cout == 32) || (cin == 32 && cout == 32) ||
                     (cin == 32 && cout == 16);
-  if (!ok_c || mode < 0 || mode > 5 || !x || !wt || !out || !ws || d % 2 || h % 8 || w % 8 ||
+  if (!ok_c || mode < 0 || mode > 6 || !x || !wt || !out || !ws || d % 2 || h % 8 || w % 8 ||
       d < 2 || h < 8 || w < 8)
     return PF_ERR_ARG;
   const int64_t V = (int64_t)d * h * w;
   size_t need = al(2 * V * cin) + al(2 * V * cout) + 2 * al(2 * 27 * cin * cout) + al(4 * V * kC) +
-                al(4 * (size_t)wgrad_blocks() * 27 * cin * cout) + al(sizeof(int));
-  if (bytes < need || (mode == 1 || mode == 2 || mode == 4) && !dy || (uintptr_t)ws % 256)
+                al(4 * part_floats(cin, cout)) + al(sizeof(int));
+  if (bytes < need || (mode == 1 || mode == 2 || mode == 4 || mode == 6) && !dy ||
+      (uintptr_t)ws % 256)
     return PF_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   char* p = (char*)ws;
@@ -406,7 +418,7 @@ pf_status pf_conv3d_check(int mode, int cin, int cout, int d, int h, int w, cons
   float* y32 = (float*)p;
   p += al(4 * V * kC);
   float* part = (float*)p;
-  p += al(4 * (size_t)wgrad_blocks() * 27 * cin * cout);
+  p += al(4 * part_floats(cin, cout));
   int* err = (int*)p;
   const bool tc = (mode == 0 || mode == 1 || mode == 5) && pf::conv3d_tc_shape_ok(1, d, h, w);
   const int selftest = mode == 5;
@@ -428,9 +440,13 @@ pf_status pf_conv3d_check(int mode, int cin, int cout, int d, int h, int w, cons
       SG_CUDA(run(cout, cin, db16, wb, nullptr));
       SG_CUDA(pf::launch_ndhwc_to_planar_add(y32, cin, cin, 1, V, nullptr, 0, 0, nullptr, out, s));
     } else {
-      const int blocks = pf::conv_wgrad_blocks(1, d, h, w, wgrad_blocks());
-      SG_CUDA(pf::launch_conv3d_wgrad(cin, cout, xb, db16, part, out, 1, d, h, w, blocks, s));
-      SG_CUDA(pf::launch_bias_grad(db16, cout, V, out + 27 * cin * cout, s));
+      if (mode == 2 && pf::wgrad_tc_shape_ok(1, d, h, w)) {
+        SG_CUDA(pf::launch_wgrad_tc(cin, cout, xb, db16, part, out, 1, d, h, w, err, s));
+      } else {
+        const int blocks = pf::conv_wgrad_blocks(1, d, h, w, wgrad_blocks());
+        SG_CUDA(pf::launch_conv3d_wgrad(cin, cout, xb, db16, part, out, 1, d, h, w, blocks, s));
+      }
+      SG_CUDA(pf::launch_bias_grad(db16, cout, V, out + 27 * cin * cout, part, s));
     }
   }
   int e = 0;

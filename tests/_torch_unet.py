@@ -20,31 +20,80 @@ def unpack(params):
     return out
 
 
-def forward(params, x):
-    """x: [B][8 or 16][D][H][W] network input -> 16-channel output."""
+class _Bf16Store(torch.autograd.Function):
+    """A buffer the library keeps in BF16: the value is rounded on the way
+    forward, and the gradient the library stores for it is rounded on the way
+    back (both round to nearest even)."""
+
+    @staticmethod
+    def forward(ctx, t):
+        return t.to(torch.bfloat16).to(t.dtype)
+
+    @staticmethod
+    def backward(ctx, g):
+        return g.to(torch.bfloat16).to(g.dtype)
+
+
+class _Bf16Grad(torch.autograd.Function):
+    """An FP32 value whose gradient the library stores in BF16 (the network
+    output: the loss gradient is rounded before the backward pass)."""
+
+    @staticmethod
+    def forward(ctx, t):
+        return t.clone()
+
+    @staticmethod
+    def backward(ctx, g):
+        return g.to(torch.bfloat16).to(g.dtype)
+
+
+def bf16_weights(params):
+    """The parameters as the library's kernels use them: the convolution
+    weights rounded to BF16 (round to nearest even), the biases FP32."""
+    out, o = params.clone(), 0
+    for ci, co, _, _ in LAYERS:
+        n = 27 * co * ci
+        out[o:o + n] = params[o:o + n].to(torch.bfloat16).to(params.dtype)
+        o += n + co
+    return out
+
+
+def forward(params, x, bf16=False):
+    """x: [B][8 or 16][D][H][W] network input -> 16-channel output.  With bf16,
+    every buffer the library stores in BF16 (activations, pooled and upsampled
+    sums, and their gradients) is rounded as it is there; the weights and the
+    input are expected already rounded by the caller."""
     Ws = unpack(params)
     pad = torch.zeros((x.shape[0], 32 - x.shape[1]) + tuple(x.shape[2:]), dtype=x.dtype)
     h = torch.cat([x, pad], dim=1)
+    q = _Bf16Store.apply if bf16 else (lambda t: t)
+    if bf16:
+        h = q(h)
 
     def conv(l, t):
         w, b = Ws[l]
         y = F.conv3d(t, w, b, padding=1)
-        return torch.relu(y) if LAYERS[l][2] else y
+        y = torch.relu(y) if LAYERS[l][2] else y
+        return q(y) if l < len(LAYERS) - 1 else (_Bf16Grad.apply(y) if bf16 else y)
 
     up = lambda t: t.repeat_interleave(2, 2).repeat_interleave(2, 3).repeat_interleave(2, 4)
+    pool = lambda t: q(F.avg_pool3d(t, 2))
     a = conv(1, conv(0, h)); s0 = a
-    a = conv(3, conv(2, F.avg_pool3d(a, 2))); s1 = a
-    a = conv(5, conv(4, F.avg_pool3d(a, 2))); s2 = a
-    a = conv(7, conv(6, F.avg_pool3d(a, 2)))
-    a = conv(9, conv(8, up(a) + s2))
-    a = conv(11, conv(10, up(a) + s1))
-    a = conv(13, conv(12, up(a) + s0))
+    a = conv(3, conv(2, pool(a))); s1 = a
+    a = conv(5, conv(4, pool(a))); s2 = a
+    a = conv(7, conv(6, pool(a)))
+    a = conv(9, conv(8, q(up(a) + s2)))
+    a = conv(11, conv(10, q(up(a) + s1)))
+    a = conv(13, conv(12, q(up(a) + s0)))
     return conv(14, a)
 
 
-def loss(params, x, y):
-    out = forward(params, x)[:, :8]
-    return ((out - (y - x)) ** 2).mean()
+def loss(params, x, y, bf16=False, x_target=None):
+    """Mean squared error of the increment net(x) against y - x; the library
+    forms the target from the unrounded state, passed as x_target."""
+    out = forward(params, x, bf16)[:, :8]
+    xt = x if x_target is None else x_target
+    return ((out - (y - xt)) ** 2).mean()
 
 
 def history_input(x):
@@ -100,8 +149,8 @@ def stiff_apply(e, c):
     return e + c * w * se
 
 
-def loss_history(params, h, x, y, s, stiff=0.0):
+def loss_history(params, h, x, y, s, stiff=0.0, bf16=False):
     """Loss in units of s of the guess extrapolate(x) + s * net(h) against y,
     the error weighted by (I + stiff K)."""
-    out = forward(params, h)[:, :8]
+    out = forward(params, h, bf16)[:, :8]
     return (stiff_apply(out - (y - extrapolate(x)) / s, stiff) ** 2).mean()

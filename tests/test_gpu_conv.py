@@ -20,9 +20,9 @@ def rel(a, b):
 
 
 def run(mode, cin, cout, shape, seed, with_ref=True):
-    """mode 0/1: forward / data gradient on the tcgen05 kernel where the shape
-    allows (D even, H % 16 == 0, W % 8 == 0), else mma.sync; 3/4: the same on
-    the mma.sync kernel; 2: weight and bias gradients."""
+    """mode 0/1/2: forward / data gradient / weight and bias gradients on the
+    tcgen05 kernels where the shape allows (D even, H and W multiples of 8),
+    else mma.sync; 3/4/6: the same on the mma.sync kernels."""
     from paper_2601_06079_gb300 import _lib
     d, h, w = shape
     x = bf16(G.random_field(seed, (cin, d, h, w)))
@@ -32,7 +32,7 @@ def run(mode, cin, cout, shape, seed, with_ref=True):
     w_or = wt.reshape(3, 3, 3, cout, cin).transpose(3, 4, 0, 1, 2)  # [co][ci][kz][ky][kx]
     cu = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
     nout = {0: cout * d * h * w, 1: cin * d * h * w, 2: 27 * cin * cout + cout,
-            3: cout * d * h * w, 4: cin * d * h * w}[mode]
+            3: cout * d * h * w, 4: cin * d * h * w, 6: 27 * cin * cout + cout}[mode]
     out = torch.zeros(nout, device="cuda")
     ws = torch.empty(64 << 20, dtype=torch.uint8, device="cuda")
     X, Wt, B, DY = cu(x), cu(wt), cu(b), cu(dy)
@@ -53,25 +53,26 @@ def run(mode, cin, cout, shape, seed, with_ref=True):
 
 
 @pytest.mark.parametrize("cin,cout", [(16, 32), (32, 32), (32, 16)])
-@pytest.mark.parametrize("mode", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3, 4, 6])
 @pytest.mark.parametrize("shape", [(2, 8, 8), (6, 16, 24), (2, 16, 8), (4, 32, 16), (2, 8, 40)])
 def test_conv_kernels_match_oracle(mode, cin, cout, shape):
     got, ref = run(mode, cin, cout, shape, seed=10 * mode + cin + cout)
     assert rel(got, ref) <= 2e-5
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_tcgen05_conv_many_tiles_per_block_matches_oracle(mode):
     # 640 output tiles (the last x tile ragged): every block runs several
     # tiles, so the 3-stage TMA ring and the two accumulator buffers wrap and
-    # their barrier phases flip
+    # their barrier phases flip; the weight gradient runs 2,048 tiles of 64
+    # voxels, about 13 per block, through its two staging buffers
     got, ref = run(mode, 32, 32, (16, 64, 128), seed=50 + mode)
     assert rel(got, ref) <= 2e-5
 
 
 @pytest.mark.parametrize("cin,cout", [(16, 32), (32, 32), (32, 16)])
 def test_tcgen05_and_mma_sync_convolutions_agree(cin, cout):
-    for m_tc, m_mma in ((0, 3), (1, 4)):
+    for m_tc, m_mma in ((0, 3), (1, 4), (2, 6)):
         a = run(m_tc, cin, cout, (8, 32, 64), seed=60 + cin + cout, with_ref=False)
         b = run(m_mma, cin, cout, (8, 32, 64), seed=60 + cin + cout, with_ref=False)
         assert rel(a, b) <= 1e-5
@@ -91,6 +92,47 @@ def test_surrogate_zero_output_layer_is_identity_and_training_reduces_loss():
     assert losses[-1] < 0.3 * losses[0]
 
 
+# Whole-network gradients against the FP64 torch reference that rounds every
+# buffer the library stores in BF16 (weights, activations, pooled and upsampled
+# sums, the loss gradient and every data gradient) where the library does.
+# With identity convolutions (centre tap = I) every layer is exact and the two
+# agree to 1e-6: that pins all of the backward pass elementwise (the 15 layers'
+# weight and bias gradients, ReLU masks, pooling and upsampling transposes,
+# skips, loss, history units and stiffness weighting).  With random weights in
+# every layer they cannot agree that closely: a value that rounds to the other
+# BF16 neighbour (its FP32 and FP64 sums differ in the last bits) moves the
+# next layer's sums by about one BF16 unit, which makes further values round
+# the other way, so two BF16 evaluations of a 15-layer network drift apart at
+# the BF16 level (0.6 % in the output here, same with mma.sync in place of
+# tcgen05; with random weights in any single layer they agree to 1e-4).  The
+# gradients then agree to 1.1-1.5e-3 (5e-3 with the stiffness weight, whose
+# stencil enhances the high-frequency part of that noise).
+GRAD_REL_ID = 1e-5
+GRAD_REL = 2e-3
+GRAD_REL_STIFF = 1e-2
+GRAD_REL_OUT = 5e-4
+
+
+def _identity_params():
+    from tests import _torch_unet as R
+    chunks = []
+    for ci, co, _, _ in R.LAYERS:
+        w = torch.zeros(27, co, ci, dtype=torch.float64)
+        for c in range(min(ci, co)):
+            w[13, c, c] = 1.0
+        chunks += [w.reshape(-1), torch.zeros(co, dtype=torch.float64)]
+    return torch.cat(chunks)
+
+
+def _grad_errors(gg, gr):
+    """Relative L2 error over all parameters, and over the output layer's."""
+    from tests import _torch_unet as R
+    n_out = 27 * R.LAYERS[-1][0] * R.LAYERS[-1][1] + R.LAYERS[-1][1]
+    err = np.linalg.norm(gg - gr) / np.linalg.norm(gr)
+    err_out = np.linalg.norm(gg[-n_out:] - gr[-n_out:]) / np.linalg.norm(gr[-n_out:])
+    return float(err), float(err_out)
+
+
 def test_whole_network_gradient_matches_torch_autograd_reference():
     import paper_2601_06079_gb300 as pf
     from tests import _torch_unet as R
@@ -99,16 +141,19 @@ def test_whole_network_gradient_matches_torch_autograd_reference():
     x = torch.from_numpy(G.random_field(4, (1, 8, 16, 64, 64), 0.0, 1.0)).cuda()
     y = x + 0.2 * torch.from_numpy(G.random_field(5, (1, 8, 16, 64, 64))).cuda()
     loss, g = s.loss_grad(x, y)
-    p = s.params.detach().cpu().to(torch.bfloat16).double().requires_grad_(True)
+    p = R.bf16_weights(s.params.detach().cpu().double()).requires_grad_(True)
     xr = x.cpu().to(torch.bfloat16).double()
-    lr = R.loss(p, xr, y.cpu().double())
+    # the reference rounds every buffer the library keeps in BF16, both ways;
+    # the loss target uses the unrounded state, as the library's does
+    lr = R.loss(p, xr, y.cpu().double(), bf16=True, x_target=x.cpu().double())
     lr.backward()
     gr = p.grad.numpy()
     gg = g.cpu().double().numpy()
-    assert abs(loss - lr.item()) <= 2e-2 * lr.item()
-    cos = float(np.dot(gg, gr) / (np.linalg.norm(gg) * np.linalg.norm(gr)))
-    assert cos > 0.99, cos
-    assert np.linalg.norm(gg - gr) <= 0.1 * np.linalg.norm(gr)
+    err, err_out = _grad_errors(gg, gr)
+    print(f"whole-network gradient: rel-L2 {err:.2e} (output layer {err_out:.2e}), "
+          f"loss rel {abs(loss - lr.item()) / lr.item():.2e}")
+    assert abs(loss - lr.item()) <= 5e-4 * lr.item()
+    assert err <= GRAD_REL and err_out <= GRAD_REL_OUT
 
 
 @pytest.mark.parametrize("hist", [1, 2])
@@ -133,19 +178,57 @@ def test_history_network_gradient_matches_torch_autograd_reference(hist):
     h = h.float().to(torch.bfloat16).double()  # the library rounds the network input to BF16
     for stiff in (0.0, 0.5):
         loss, g = s.loss_grad(x, y, stiff=stiff)
-        p = s.params.detach().cpu().to(torch.bfloat16).double().requires_grad_(True)
-        lr = R.loss_history(p, h, xd, y.cpu().double(), so, stiff)
+        p = R.bf16_weights(s.params.detach().cpu().double()).requires_grad_(True)
+        lr = R.loss_history(p, h, xd, y.cpu().double(), so, stiff, bf16=True)
         lr.backward()
         gr, gg = p.grad.numpy(), g.cpu().double().numpy()
-        assert abs(loss - lr.item()) <= 2e-2 * lr.item()
-        cos = float(np.dot(gg, gr) / (np.linalg.norm(gg) * np.linalg.norm(gr)))
-        assert cos > 0.99, (stiff, cos)
-        assert np.linalg.norm(gg - gr) <= 0.1 * np.linalg.norm(gr)
+        err, err_out = _grad_errors(gg, gr)
+        print(f"history {hist} stiff {stiff}: gradient rel-L2 {err:.2e} (output layer "
+              f"{err_out:.2e}), loss rel {abs(loss - lr.item()) / lr.item():.2e}")
+        assert abs(loss - lr.item()) <= 5e-4 * lr.item()
+        assert err <= (GRAD_REL_STIFF if stiff else GRAD_REL), (stiff, err)
+        assert err_out <= GRAD_REL_OUT, (stiff, err_out)
     # zero output layer: the guess is exactly the extrapolation
     s.init(seed=4, last_layer_scale=0.0)
     guess = s.predict(x)
     ref = R.extrapolate(xd).float().cuda()
     assert float((guess - ref).abs().max()) <= 2e-6
+
+
+@pytest.mark.parametrize("hist,stiff", [(0, 0.0), (2, 0.0), (2, 0.5)])
+def test_identity_network_gradient_matches_reference_elementwise(hist, stiff):
+    import paper_2601_06079_gb300 as pf
+    from tests import _torch_unet as R
+    s = pf.Surrogate(history=hist)
+    s.params.copy_(_identity_params().float().cuda())
+    u = torch.from_numpy(G.random_field(6, (2, 8, 16, 64, 64), 0.0, 1.0)).cuda()
+    du = torch.from_numpy(G.random_field(7, (2, 8, 16, 64, 64))).cuda()
+    x = torch.cat([u - 0.01 * k * du * (1.0 + 0.1 * k) for k in range(hist + 1)], dim=1).contiguous()
+    y = u + 0.012 * du + 0.002 * torch.from_numpy(G.random_field(8, (2, 8, 16, 64, 64))).cuda()
+    xd = x.cpu().double()
+    loss, g = s.loss_grad(x, y, stiff=stiff)
+    p = R.bf16_weights(s.params.detach().cpu().double()).requires_grad_(True)
+    if hist:
+        h, sc = R.history_input(xd)
+        so = R.output_scale(xd, sc)
+        h = h.float().to(torch.bfloat16).double()
+        lr = R.loss_history(p, h, xd, y.cpu().double(), so, stiff, bf16=True)
+    else:
+        lr = R.loss(p, x.cpu().to(torch.bfloat16).double(), y.cpu().double(), bf16=True,
+                    x_target=xd)
+    lr.backward()
+    gr, gg = p.grad.numpy(), g.cpu().double().numpy()
+    err = float(np.linalg.norm(gg - gr) / np.linalg.norm(gr))
+    print(f"identity network, history {hist}, stiff {stiff}: gradient rel-L2 {err:.2e}")
+    assert abs(loss - lr.item()) <= 1e-6 * lr.item()
+    assert err <= GRAD_REL_ID
+    # every layer's weight gradient is nonzero and checked, not just the output's
+    o = 0
+    for ci, co, _, _ in R.LAYERS:
+        n = 27 * co * ci
+        assert np.linalg.norm(gr[o:o + n]) > 0
+        assert np.linalg.norm(gg[o:o + n] - gr[o:o + n]) <= 1e-4 * np.linalg.norm(gr[o:o + n])
+        o += n + co
 
 
 def test_tcgen05_pipeline_timeout_is_reported_and_recoverable():
