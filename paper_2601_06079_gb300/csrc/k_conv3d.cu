@@ -321,13 +321,23 @@ __global__ void __launch_bounds__(256) k_bias_part(const __nv_bfloat16* __restri
   }
 }
 
-__global__ void k_bias_final(const float* __restrict__ part, int nblk, int C, float* db) {
-  const int c = threadIdx.x;
-  if (c >= C) return;
+// 8 threads per channel each sum every 8th block, then the 8 sums are added in
+// a fixed order (deterministic for a given block count).
+__global__ void __launch_bounds__(256) k_bias_final(const float* __restrict__ part, int nblk,
+                                                    int C, float* db) {
+  __shared__ float red[256];
+  const int c = threadIdx.x >> 3, k = threadIdx.x & 7;
   float t = 0.0f;
-#pragma unroll 8
-  for (int b = 0; b < nblk; ++b) t += part[(int64_t)b * C + c];
-  db[c] = t;
+  if (c < C)
+    for (int b = k; b < nblk; b += 8) t += part[(int64_t)b * C + c];
+  red[threadIdx.x] = t;
+  __syncthreads();
+  if (k == 0 && c < C) {
+    float s = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s += red[threadIdx.x + j];
+    db[c] = s;
+  }
 }
 
 }  // namespace
@@ -394,7 +404,7 @@ cudaError_t launch_bias_grad(const void* dy, int C, int64_t nvox, float* db, flo
     k_bias_part<32><<<(unsigned)nb, 256, 0, s>>>(DY, nvox, scratch);
   else
     return cudaErrorInvalidValue;
-  k_bias_final<<<1, 32, 0, s>>>(scratch, (int)nb, C, db);
+  k_bias_final<<<1, 256, 0, s>>>(scratch, (int)nb, C, db);  // C <= 32
   return cudaGetLastError();
 }
 

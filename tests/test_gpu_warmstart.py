@@ -1,8 +1,10 @@
 """The learned warm start (history-2 surrogate: a learned correction to
 quadratic extrapolation through the last three states), trained on the
-solver's own implicit trajectories from other seeds, against the plain U^n
-start on a held-out seed: Newton must start closer to the root, need fewer
-Newton iterations, and every start must converge to the same state within
+solver's own implicit trajectories from other seeds, on a held-out seed:
+against the plain U^n start (Newton must start closer to the root and need
+fewer Newton iterations) and against the same network with its output layer
+zero (pure quadratic extrapolation through the same path: what the trained
+correction adds on its own).  Every start converges to the same state within
 the Newton tolerance."""
 import numpy as np
 import pytest
@@ -23,12 +25,34 @@ def test_warm_start_beats_plain_start_at_same_accuracy():
     surr.init(seed=7, last_layer_scale=0.0)
     losses = WS.train(surr, data, iters=600, crop=64, batch=4, lr=1e-4, seed=1, stiff=0.5)
     assert np.isfinite(losses).all()
+    # training reduces the loss (the output layer starts at zero: the first
+    # losses are those of pure extrapolation)
+    first, last = float(np.mean(losses[:50])), float(np.mean(losses[-50:]))
+    print(f"training loss: first 50 {first:.4e}, last 50 {last:.4e}")
+    assert last < 0.9 * first
 
+    zero = pf.Surrogate(history=2)
+    zero.init(seed=7, last_layer_scale=0.0)
     U0 = torch.from_numpy(G.voronoi_grains(1, n=n, n_seeds=16, n_op=8)).cuda()
     Up, plain, r_plain = WS.run(solver, U0, 40, None, newton_rtol=1e-6)
     Uw, warm, r_warm = WS.run(solver, U0, 40, surr, newton_rtol=1e-6)
+    Uz, abl, r_abl = WS.run(solver, U0, 40, zero, newton_rtol=1e-6)
+    print("newton iterations plain / ablation / learned:", plain["newton_iters"],
+          abl["newton_iters"], warm["newton_iters"])
+    print("mean initial residual plain / ablation / learned:", np.mean(r_plain[2:]),
+          np.mean(r_abl[2:]), np.mean(r_warm[2:]))
     # from the third step on the surrogate has its full history
     assert np.median(r_warm[2:]) < 0.5 * np.median(r_plain[2:]), (r_warm[:6], r_plain[:6])
     assert warm["newton_iters"] < 0.75 * plain["newton_iters"], (warm, plain)
-    diff = float(torch.linalg.norm(Uw - Up) / torch.linalg.norm(Up))
-    assert diff <= 1e-5
+    # what the trained correction adds to the extrapolation it corrects: in
+    # the fast early coarsening it starts Newton much closer to the root (the
+    # mean initial residual, which those steps dominate, drops); in the slow
+    # late stage, where three states extrapolate almost exactly, it is a
+    # little worse (its median is a few per cent higher).  In Newton
+    # iterations the two are within one of each other: the saving against the
+    # plain start is the extrapolation's.
+    assert np.mean(r_warm[2:]) < 0.9 * np.mean(r_abl[2:]), (r_warm[:6], r_abl[:6])
+    assert warm["newton_iters"] <= abl["newton_iters"] + 1, (warm, abl)
+    for U in (Uw, Uz):
+        diff = float(torch.linalg.norm(U - Up) / torch.linalg.norm(Up))
+        assert diff <= 1e-5
