@@ -544,11 +544,18 @@ def forms_ensemble(dev, stream, flush, n_steps=1000):
     e.set_params([dict(W=p["W"], kappa=p["kappa"], L=p["L"], dt=0.01) for p in inst])
     fields = [G.ac_initial(1 + i, s) for i, s in enumerate(shapes)]
     st0 = e.pack(fields)
-    ty, _ = e.tune(reps=3)
+    ty, tune = e.tune(reps=10)
     nodes = int(st0.numel())
-    rows = {str(k): ty.count(k) for k in sorted(set(ty))}
+    per_class = {}
+    for (nx, ny), t in zip(shapes, ty):
+        per_class.setdefault(f"{nx}x{ny}", t)
+    best_uniform = min(tune["uniform_us"].values())
     out, res = {"instances": 256, "nodes": nodes, "steps": n_steps,
-                "tuned_band_rows_per_size_class": rows}, {}
+                "tuned_band_rows_per_size_class": dict(sorted(per_class.items())),
+                "autotuner": {"uniform_us_per_step": {str(k): v for k, v in
+                                                     tune["uniform_us"].items()},
+                              "tuned_us_per_step": tune["tuned_us"],
+                              "gain_over_best_uniform": best_uniform / tune["tuned_us"]}}, {}
     for mode in ("persistent", "per_step", "plain"):
         st = st0.clone()
         e.step(st, 8, mode)  # warm

@@ -251,11 +251,18 @@ pf_status pf_create_ensemble(pf_ctx** out, int count, const int64_t* nx, const i
  * per-instance arguments to the device and synchronises the stream. */
 pf_status pf_set_ensemble_params(pf_ctx* ctx, const pf_params* params);
 
-/* Autotuner: for each size class (equal nx, ny) times `reps` batched steps for
- * each band height in {6, 12, 24} rows and keeps the fastest.  ty_out (host,
- * count) receives the choice per instance, us_out (host, 3 per class in order
- * of first appearance) the timings; either may be NULL.  Overwrites the
- * working planes; synchronises the stream. */
+/* Autotuner of the band height per size class (no counterpart in the paper):
+ * every candidate is timed as the whole ensemble step (best of three rounds of
+ * `reps` per-step launches), the quantity the ensemble forms run.  First all
+ * classes at one height, for each of {6, 12, 24} rows; then, from the best of
+ * those, coordinate descent over the classes (most nodes first, at most two
+ * passes), where a class takes another height only if the whole step gets at
+ * least 1 % faster.  ty_out (host, count) receives the choice per instance;
+ * us_out (host, 3 * classes + 4 doubles, classes in order of first
+ * appearance) the microseconds per step: [3 ci + k] with class ci at height k
+ * during the descent (-1 where not tried), then the three uniform heights and
+ * the final choice.  Either may be NULL.  Overwrites the working planes;
+ * synchronises the stream. */
 pf_status pf_tune_ensemble(pf_ctx* ctx, int reps, int* ty_out, double* us_out);
 
 /* Advance every instance of the packed state (device, in/out) by n_steps

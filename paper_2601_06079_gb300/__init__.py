@@ -266,9 +266,17 @@ class Ensemble:
         self._check(pf_set_ensemble_params(self._ctx, ps))
 
     def tune(self, reps=10):
+        """Autotune the band height per size class on the whole ensemble step
+        (pf_tune_ensemble).  Returns (band height per instance, timings) with
+        timings = {"uniform_us": {6: .., 12: .., 24: ..}, "tuned_us": ..,
+        "trials_us": per class (order of first appearance) [us at 6, 12, 24]
+        (None where not tried)}."""
         st, ty, us = pf_tune_ensemble(self._ctx, reps, len(self.shapes), self.nclasses)
         self._check(st)
-        return ty, us
+        nc = self.nclasses
+        trials = [[u if u >= 0 else None for u in us[3 * c:3 * c + 3]] for c in range(nc)]
+        return ty, {"uniform_us": dict(zip((6, 12, 24), us[3 * nc:3 * nc + 3])),
+                    "tuned_us": us[3 * nc + 3], "trials_us": trials}
 
     def pack(self, fields):
         return torch.cat([torch.as_tensor(f, dtype=torch.float32).reshape(-1) for f in fields]

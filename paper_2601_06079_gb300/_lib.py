@@ -288,7 +288,7 @@ def pf_set_ensemble_params(ctx, params):
 
 def pf_tune_ensemble(ctx, reps, count, nclasses):
     ty = (C.c_int * count)()
-    us = (C.c_double * (3 * nclasses))()
+    us = (C.c_double * (3 * nclasses + 4))()
     s = lib().pf_tune_ensemble(ctx, reps, ty, us)
     return s, list(ty), list(us)
 

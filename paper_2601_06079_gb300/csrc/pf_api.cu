@@ -340,6 +340,8 @@ EnsLayout ens_layout(const pf_ctx* c) {
   return L;
 }
 
+// Task list: every instance's (column strip, band) tasks, the tallest bands
+// first so that the longest tasks start early (the order changes no result).
 std::vector<pf::EnsTask> ens_build_tasks(const pf_ctx* c, const std::vector<int>& which) {
   std::vector<pf::EnsTask> t;
   for (int i : which) {
@@ -348,6 +350,8 @@ std::vector<pf::EnsTask> ens_build_tasks(const pf_ctx* c, const std::vector<int>
     for (int y0 = 0; y0 < ny; y0 += ty)
       for (int bx = 0; bx < gx; ++bx) t.push_back(pf::EnsTask{i, bx, y0, ty});
   }
+  std::stable_sort(t.begin(), t.end(),
+                   [](const pf::EnsTask& a, const pf::EnsTask& b) { return a.ty > b.ty; });
   return t;
 }
 
@@ -1046,56 +1050,96 @@ pf_status pf_tune_ensemble(pf_ctx* c, int reps, int* ty_out, double* us_out) {
     PF_CUDA(cudaMemsetAsync(const_cast<float*>(x.in), 0, sizeof(float) * x.pitch * x.rows, c->stream));
     PF_CUDA(cudaMemsetAsync(x.out, 0, sizeof(float) * x.pitch * x.rows, c->stream));
   }
+  std::vector<std::pair<int64_t, int64_t>> classes;
+  std::vector<int> cls(c->ens_count);
+  for (int i = 0; i < c->ens_count; ++i) {
+    auto k = std::make_pair(c->ens_nx[i], c->ens_ny[i]);
+    auto it = std::find(classes.begin(), classes.end(), k);
+    cls[i] = (int)(it - classes.begin());
+    if (it == classes.end()) classes.push_back(k);
+  }
+  const int nc = (int)classes.size();
+  std::vector<int> all(c->ens_count);
+  for (int i = 0; i < c->ens_count; ++i) all[i] = i;
   cudaEvent_t e0, e1;
   PF_CUDA(cudaEventCreate(&e0));
   PF_CUDA(cudaEventCreate(&e1));
-  std::vector<std::pair<int64_t, int64_t>> classes;
-  for (int i = 0; i < c->ens_count; ++i) {
-    auto k = std::make_pair(c->ens_nx[i], c->ens_ny[i]);
-    if (std::find(classes.begin(), classes.end(), k) == classes.end()) classes.push_back(k);
-  }
-  pf_status st = PF_OK;
-  for (size_t ci = 0; ci < classes.size() && st == PF_OK; ++ci) {
-    std::vector<int> members;
-    for (int i = 0; i < c->ens_count; ++i)
-      if (c->ens_nx[i] == classes[ci].first && c->ens_ny[i] == classes[ci].second) members.push_back(i);
+  // whole-ensemble step time (us, best of three rounds of `reps` per-step
+  // launches) with band height assign[class] for every instance of a class
+  auto time_all = [&](const std::vector<int>& assign, double* us) -> pf_status {
+    for (int i = 0; i < c->ens_count; ++i) c->ens_ty[i] = assign[cls[i]];
+    pf_status s = ens_upload_tasks(c, ens_build_tasks(c, all));
+    if (s != PF_OK) return s;
+    const int grid = ens_step_grid(c->ens_ntasks);
     double best = 1e30;
-    int best_ty = 12;
-    for (int k = 0; k < 3 && st == PF_OK; ++k) {
-      for (int i : members) c->ens_ty[i] = cand[k];
-      st = ens_upload_tasks(c, ens_build_tasks(c, members));
-      if (st != PF_OK) break;
-      const int grid = ens_step_grid(c->ens_ntasks);
+    for (int round = 0; round < 3; ++round) {
       cudaError_t e = pf::launch_ensemble_step(c->ens_tasks, c->ens_ntasks, c->ens_dargs, 0,
                                                c->ens_iso, grid, c->stream);  // warm-up
       if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
       for (int r = 0; r < reps && e == cudaSuccess; ++r)
-        e = pf::launch_ensemble_step(c->ens_tasks, c->ens_ntasks, c->ens_dargs, r & 1, c->ens_iso,
-                                     grid, c->stream);
+        e = pf::launch_ensemble_step(c->ens_tasks, c->ens_ntasks, c->ens_dargs, r & 1,
+                                     c->ens_iso, grid, c->stream);
       if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
       float ms = 0.0f;
       if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-      if (e != cudaSuccess) {
-        st = cuda_fail(c, e, "ensemble tuning");
-        break;
-      }
-      const double us = 1e3 * ms / reps;
-      if (us_out) us_out[3 * ci + k] = us;
-      if (us < best) {
-        best = us;
-        best_ty = cand[k];
-      }
+      if (e != cudaSuccess) return cuda_fail(c, e, "ensemble tuning");
+      best = std::min(best, 1e3 * ms / reps);
     }
-    for (int i : members) c->ens_ty[i] = best_ty;
+    *us = best;
+    return PF_OK;
+  };
+  pf_status st = PF_OK;
+  // 1. every class at the same band height
+  double uni[3] = {0, 0, 0};
+  int bk = 0;
+  for (int k = 0; k < 3 && st == PF_OK; ++k) {
+    st = time_all(std::vector<int>(nc, cand[k]), &uni[k]);
+    if (uni[k] < uni[bk]) bk = k;
+  }
+  std::vector<int> assign(nc, cand[bk]);
+  double best = uni[bk];
+  if (us_out)
+    for (int ci = 0; ci < nc; ++ci)
+      for (int k = 0; k < 3; ++k) us_out[3 * ci + k] = k == bk ? best : -1.0;
+  // 2. coordinate descent over the classes, most nodes first: a class keeps
+  // another height only if the whole step gets at least 1 % faster
+  std::vector<int> order(nc);
+  for (int ci = 0; ci < nc; ++ci) order[ci] = ci;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    return classes[x].first * classes[x].second > classes[y].first * classes[y].second;
+  });
+  for (int pass = 0; pass < 2 && st == PF_OK; ++pass) {
+    bool changed = false;
+    for (int ci : order) {
+      for (int k = 0; k < 3 && st == PF_OK; ++k) {
+        if (cand[k] == assign[ci]) continue;
+        std::vector<int> trial = assign;
+        trial[ci] = cand[k];
+        double t = 0.0;
+        st = time_all(trial, &t);
+        if (st != PF_OK) break;
+        if (us_out) us_out[3 * ci + k] = t;
+        if (t < 0.99 * best) {
+          best = t;
+          assign = trial;
+          changed = true;
+        }
+      }
+      if (st != PF_OK) break;
+    }
+    if (!changed) break;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != PF_OK) return st;
+  if (us_out) {
+    for (int k = 0; k < 3; ++k) us_out[3 * nc + k] = uni[k];
+    us_out[3 * nc + 3] = best;
+  }
+  for (int i = 0; i < c->ens_count; ++i) c->ens_ty[i] = assign[cls[i]];
   if (ty_out)
     for (int i = 0; i < c->ens_count; ++i) ty_out[i] = c->ens_ty[i];
-  std::vector<int> all(c->ens_count);
-  for (int i = 0; i < c->ens_count; ++i) all[i] = i;
   destroy_graph(c);
   return ens_upload_tasks(c, ens_build_tasks(c, all));
 }

@@ -54,8 +54,12 @@ def test_modes_agree_bitwise_and_tuning_keeps_results():
         outs[mode] = st.clone()
     assert torch.equal(outs["plain"], outs["per_step"])
     assert torch.equal(outs["plain"], outs["persistent"])
-    ty, us = e.tune(reps=3)
-    assert set(ty) <= {6, 12, 24} and all(u > 0 for u in us)
+    ty, info = e.tune(reps=3)
+    assert set(ty) <= {6, 12, 24}
+    assert all(u > 0 for u in info["uniform_us"].values())
+    # the choice is never slower than the best single height by more than noise
+    assert info["tuned_us"] <= min(info["uniform_us"].values()) * 1.0001
+    assert all(u is None or u > 0 for row in info["trials_us"] for u in row)
     st = e.pack(fields)
     e.step(st, 17, "persistent")
     assert torch.equal(st, outs["plain"])
