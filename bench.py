@@ -738,7 +738,10 @@ def run_profile(args):
     ensemble  20 steps of the 256-instance AC ensemble, one launch per step (the
               persistent mode runs the same task body behind a grid barrier)
     coupled   20 coupled Allen-Cahn / Cahn-Hilliard steps on 2048^2
-    elastic   five Eshelby stiffness applications on 129^3 x 3 components"""
+    elastic   five Eshelby stiffness applications on 129^3 x 3 components
+    train     four surrogate training steps (history 2, 4 x 64^3 crops, stiffness
+              weight 0.5): forward, loss, backward with the tcgen05 weight gradient,
+              Adam"""
     import torch
 
     import paper_2601_06079_gb300 as pf
@@ -791,6 +794,14 @@ def run_profile(args):
             Ku = el.apply(u)
         torch.cuda.synchronize()
         print(f"profile run done: |Ku| {float(Ku.norm()):.6f}")
+    elif args.target == "train":
+        s = pf.Surrogate(history=2)
+        s.init(seed=1, last_layer_scale=0.1)
+        x = torch.from_numpy(G.random_field(6, (4, 24, 64, 64, 64), 0.0, 1.0)).cuda()
+        y = x[:, :8].clone() + 0.01 * torch.from_numpy(G.random_field(7, (4, 8, 64, 64, 64))).cuda()
+        losses = [s.train_step(x, y, lr=1e-4, stiff=0.5) for _ in range(4)]
+        torch.cuda.synchronize()
+        print(f"profile run done: losses {losses}")
     elif args.target == "coupled":
         s = pf.Solver((N_SIDE, N_SIDE), h=1.0, model="coupled")
         s.set_params(kappa=0.3, mobility=1.0, mobility2=150.0, dt=1e-3)
@@ -825,7 +836,7 @@ def main():
     ap.add_argument("--tsteps", type=int, default=N_TSTEPS)
     ap.add_argument("--target", default="ch",
                     choices=["ch", "surrogate", "jvp", "residual", "ensemble", "coupled",
-                             "elastic"],
+                             "elastic", "train"],
                     help="workload of --profile")
     args = ap.parse_args()
     if args.warmup < 3:

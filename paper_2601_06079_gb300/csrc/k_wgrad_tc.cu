@@ -12,14 +12,22 @@
 // (dz, dy) shifts of the output gradient fill the rows of 3 (c_out = 32) or 2
 // (c_out = 16) groups, the rows past the ninth combination are zero.
 //
-// A block owns tiles of 64 consecutive voxels (flattened (b, z, y, x) order;
-// W is a multiple of 8, so every 8-voxel run shares z and y).  Eight staging
-// warps load the shifted rows (8 voxels x 8 channels, 16-byte loads), transpose
-// them in registers and write the canonical no-swizzle K-major layout: core
-// matrices of 8 rows x 8 voxels, 8 rows (128 bytes) apart along M/N and the
-// operand's rows x 16 bytes apart along K.  Two stages alternate: while the
+// A block owns tiles of 8 y-rows x 8 x-voxels of one (b, z) plane (H and W are
+// multiples of 8); K chunk kb of a tile is its y-row kb.  Eight staging warps
+// load 8-voxel x 8-channel blocks (16-byte loads; each thread owns one such
+// block of every tile and loads the next tile's while it transposes and stores
+// the current one), transpose them in registers and write the
+// 128-byte-swizzled K-major layout: every operand row
+// holds the tile's 64 voxels in 128 bytes, its 16-byte chunk kb at position
+// kb XOR (row mod 8), in atoms of 8 rows (1 KB).  Lanes that store together
+// hold different chunks of rows with the same row mod 8, so the swizzle puts
+// their 16 bytes in different bank groups (the unswizzled layout put all of
+// them in the same one: 8-way conflicts on every store).  The output gradient is loaded once per source row
+// (z', y') of the tile's 3 x 10 neighbourhood and stored into every (dy, kb)
+// slot it feeds, up to three, rather than once per slot.  Two stages alternate: while the
 // staging warps fill one, one thread of warp 8 issues the 4 (K = 16) MMAs per
-// group on the other and commits them to the stage's barrier.  Every tile of
+// group on the other and commits them to the stage's barrier; the K = 16
+// steps advance the descriptors' start by 32 bytes within the rows.  Every tile of
 // the block accumulates into the same tensor-memory columns (g x 3 c_in + n);
 // at the end warps 0..3 (their tensor-memory lane quarters) write the block's
 // partial sums, which a second kernel adds over the blocks in a fixed order.
@@ -48,8 +56,8 @@ struct WCfg {
   static constexpr int kSPG = 128 / COUT;                  // (dz, dy) combinations per group
   static constexpr int kNG = (9 + kSPG - 1) / kSPG;        // groups
   static constexpr int kN = 3 * CIN;                       // GEMM N: (dx, c_in)
-  static constexpr uint32_t kABytes = kKB * 128 * 16;       // one group's A per stage
-  static constexpr uint32_t kBBytes = kKB * kN * 16;
+  static constexpr uint32_t kABytes = 128 * 128;            // one group's A: 128 rows x 128 bytes
+  static constexpr uint32_t kBBytes = kN * 128;
   static constexpr uint32_t kStage = kNG * kABytes + kBBytes;
   static constexpr uint32_t kCols = kNG * kN <= 128 ? 128 : kNG * kN <= 256 ? 256 : 512;
   static constexpr uint32_t kSmem = 1024 + kStages * kStage + 256;
@@ -64,6 +72,12 @@ struct __align__(8) WCtrl {
   uint32_t tmem;
   int abort;
 };
+
+// byte offset of 16-byte chunk kb (voxels 8 kb .. 8 kb + 7) of operand row r in
+// the 128-byte-swizzled K-major layout
+__device__ __forceinline__ uint32_t sw128(int r, int kb) {
+  return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((kb ^ (r & 7)) << 4));
+}
 
 // 8 x 8 BF16 transpose: in[i] = 8 channels of voxel i; out[j] = 8 voxels of channel j
 __device__ __forceinline__ void transpose8(const uint4 (&in)[8], uint4 (&out)[8]) {
@@ -92,8 +106,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   WCtrl* ctl = reinterpret_cast<WCtrl*>(base + kStages * C::kStage);
   volatile int* abort = &ctl->abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t nvox = (int64_t)B * D * H * W;
-  const int64_t ntiles = nvox / kTile;
+  const int tiles_x = W / 8, tiles_y = H / 8;
+  const int64_t ntiles = (int64_t)B * D * tiles_y * tiles_x;
 
   // zero both stages once: the rows of combinations past the ninth stay zero
   for (uint32_t i = threadIdx.x; i < kStages * C::kStage / 16; i += kThreads)
@@ -121,65 +135,80 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp < kStageWarps) {
     // ---- staging: 8 x 8 (voxel, channel) blocks of the shifted operands ----
-    const int st = threadIdx.x;
-    constexpr int kAItems = 9 * (COUT / 8) * kKB;  // (combination, c_out chunk, column)
-    constexpr int kBItems = 3 * (CIN / 8) * kKB;   // (dx, c_in chunk, column)
+    // Thread it owns one block per tile: a source row (dz, yr, c_out chunk) of
+    // the output gradient (it < kAItems) or a shifted input row (dx, c_in
+    // chunk, kb); source rows vary fastest across lanes, so that lanes storing
+    // together differ in kb.
+    constexpr int kAItems = 3 * 10 * (COUT / 8);
+    constexpr int kBItems = 3 * (CIN / 8) * kKB;
+    static_assert(kAItems + kBItems <= kStageWarps * 32, "one block per staging thread");
+    const int it = threadIdx.x;
+    const bool isA = it < kAItems, active = it < kAItems + kBItems;
+    const int yr = it % 10, ca = (it / 10) % (COUT / 8), dz = it / (10 * (COUT / 8));
+    const int jb = it - kAItems;
+    const int kbb = jb % kKB, cb = (jb / kKB) % (CIN / 8), dxb = jb / (kKB * (CIN / 8));
+    const uint4 zero = make_uint4(0, 0, 0, 0);
+    // the 8 loads of this thread's block of tile t
+    auto load = [&](int64_t t, uint4 (&v)[8]) {
+      const int x0 = (int)(t % tiles_x) * 8;
+      int64_t r = t / tiles_x;
+      const int y0 = (int)(r % tiles_y) * 8;
+      r /= tiles_y;
+      const int zz = (int)(r % D);
+      const int64_t b = r / D;
+      if (isA) {
+        const int z2 = zz - dz + 1, y2 = y0 - 1 + yr;
+        if (z2 >= 0 && z2 < D && y2 >= 0 && y2 < H) {
+          const __nv_bfloat16* src = dy + (((b * D + z2) * H + y2) * W + x0) * COUT + 8 * ca;
+#pragma unroll
+          for (int k = 0; k < 8; ++k) v[k] = __ldg(reinterpret_cast<const uint4*>(src + k * COUT));
+        } else {
+#pragma unroll
+          for (int k = 0; k < 8; ++k) v[k] = zero;
+        }
+      } else {
+        const int64_t row = (b * D + zz) * H + y0 + kbb;  // (b, z, y) row of the 8 voxels
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int x2 = x0 + k + dxb - 1;
+          v[k] = (x2 >= 0 && x2 < W)
+                     ? __ldg(reinterpret_cast<const uint4*>(x + (row * W + x2) * CIN + 8 * cb))
+                     : zero;
+        }
+      }
+    };
+    uint4 nxt[8];
+    if (active && blockIdx.x < ntiles) load(blockIdx.x, nxt);
     int i = 0;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
       const int s = i % kStages;
+      uint4 v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = nxt[k];
+      if (active && t + gridDim.x < ntiles) load(t + gridDim.x, nxt);  // in flight meanwhile
       if (i >= kStages && !bar_wait(&ctl->empty[s], ((i / kStages) - 1) & 1, abort, err)) break;
       unsigned char* stage = base + s * C::kStage;
-      const int64_t u0 = t * kTile;
-      for (int it = st; it < kAItems + kBItems; it += kStageWarps * 32) {
-        uint4 v[8];
-        const uint4 zero = make_uint4(0, 0, 0, 0);
-        unsigned char* dst;
-        uint32_t rows;
-        int row0;
-        if (it < kAItems) {
-          const int kb = it % kKB, c = (it / kKB) % (COUT / 8), combo = it / (kKB * (COUT / 8));
-          const int g = combo / C::kSPG, sl = combo % C::kSPG;
-          const int64_t u = u0 + kb * 8;
-          const int xx = (int)(u % W);
-          int64_t r = u / W;
-          const int yy = (int)(r % H);
-          r /= H;
-          const int zz = (int)(r % D);
-          const int64_t b = r / D;
-          const int z2 = zz - combo / 3 + 1, y2 = yy - combo % 3 + 1;
-          if (z2 >= 0 && z2 < D && y2 >= 0 && y2 < H) {
-            const __nv_bfloat16* src = dy + (((b * D + z2) * H + y2) * W + xx) * COUT + 8 * c;
-#pragma unroll
-            for (int k = 0; k < 8; ++k) v[k] = __ldg(reinterpret_cast<const uint4*>(src + k * COUT));
-          } else {
-#pragma unroll
-            for (int k = 0; k < 8; ++k) v[k] = zero;
-          }
-          dst = stage + g * C::kABytes + kb * (128 * 16);
-          rows = 128;
-          row0 = sl * COUT + 8 * c;
-        } else {
-          const int jb = it - kAItems;
-          const int kb = jb % kKB, c = (jb / kKB) % (CIN / 8), dx = jb / (kKB * (CIN / 8));
-          const int64_t u = u0 + kb * 8;
-          const int xx = (int)(u % W);
-          const int64_t row = u / W;  // (b, z, y) row of the 8 voxels
-#pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            const int x2 = xx + k + dx - 1;
-            v[k] = (x2 >= 0 && x2 < W)
-                       ? __ldg(reinterpret_cast<const uint4*>(x + (row * W + x2) * CIN + 8 * c))
-                       : zero;
-          }
-          dst = stage + C::kNG * C::kABytes + kb * (C::kN * 16);
-          rows = C::kN;
-          row0 = dx * CIN + 8 * c;
-        }
-        (void)rows;
+      if (active) {
         uint4 o[8];
         transpose8(v, o);
+        if (isA) {
+          // it feeds slot (dz, dy) at column kb = yr + dy - 2, for every dy with 0 <= kb < 8
 #pragma unroll
-        for (int j = 0; j < 8; ++j) *reinterpret_cast<uint4*>(dst + (row0 + j) * 16) = o[j];
+          for (int dyy = 0; dyy < 3; ++dyy) {
+            const int kb = yr + dyy - 2;
+            if (kb < 0 || kb >= kKB) continue;
+            const int combo = dz * 3 + dyy, g = combo / C::kSPG, sl = combo % C::kSPG;
+            unsigned char* dst = stage + g * C::kABytes;
+            const int r0 = sl * COUT + 8 * ca;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) *reinterpret_cast<uint4*>(dst + sw128(r0 + j, kb)) = o[j];
+          }
+        } else {
+          unsigned char* dst = stage + C::kNG * C::kABytes;
+          const int r0 = dxb * CIN + 8 * cb;
+#pragma unroll
+          for (int j = 0; j < 8; ++j) *reinterpret_cast<uint4*>(dst + sw128(r0 + j, kbb)) = o[j];
+        }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> MMA
       bar_arrive(&ctl->full[s]);
@@ -192,15 +221,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!bar_wait(&ctl->full[s], (i / kStages) & 1, abort, err)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t sa = su32(base + s * C::kStage);
-      const uint64_t b_desc = sdesc(sa + C::kNG * C::kABytes, C::kN * 16, 128);
+      // 128-byte swizzle (layout 2), 8-row atoms 1 KB apart (SBO); K = 16 steps
+      // are 32-byte advances of the start address inside the rows
+      const uint64_t b_desc = sdesc(sa + C::kNG * C::kABytes, 16, 1024, 2ull);
 #pragma unroll
       for (int g = 0; g < C::kNG; ++g) {
-        const uint64_t a_desc = sdesc(sa + g * C::kABytes, 128 * 16, 128);
+        const uint64_t a_desc = sdesc(sa + g * C::kABytes, 16, 1024, 2ull);
 #pragma unroll
         for (int kk = 0; kk < kTile / 16; ++kk)
-          mma_f16(tmem + g * C::kN, a_desc + (uint64_t)((2 * kk * 128 * 16) >> 4),
-                  b_desc + (uint64_t)((2 * kk * C::kN * 16) >> 4), C::kIdesc,
-                  (i > 0 || kk > 0) ? 1u : 0u);
+          mma_f16(tmem + g * C::kN, a_desc + (uint64_t)((32 * kk) >> 4),
+                  b_desc + (uint64_t)((32 * kk) >> 4), C::kIdesc, (i > 0 || kk > 0) ? 1u : 0u);
       }
       mma_commit(&ctl->empty[s]);
     }
@@ -266,7 +296,7 @@ cudaError_t wgrad_launch(const void* x, const void* dy, float* part, float* dw, 
   static std::atomic<unsigned long long> raised{0};
   cudaError_t e = raise_smem_limit(k_wgrad_tc<CIN, COUT>, C::kSmem, raised);
   if (e != cudaSuccess) return e;
-  const int64_t ntiles = (int64_t)B * D * H * W / kTile;
+  const int64_t ntiles = (int64_t)B * D * (H / 8) * (W / 8);
   const int grid = (int)(ntiles < wgrad_tc_blocks() ? ntiles : wgrad_tc_blocks());
   k_wgrad_tc<CIN, COUT><<<grid, kThreads, C::kSmem, s>>>(
       (const __nv_bfloat16*)x, (const __nv_bfloat16*)dy, part, B, D, H, W, err);
@@ -283,8 +313,7 @@ int wgrad_tc_blocks() { return device_sm_count(); }
 size_t wgrad_tc_part_floats() { return (size_t)wgrad_tc_blocks() * 3 * 128 * 96; }
 
 bool wgrad_tc_shape_ok(int B, int D, int H, int W) {
-  return B >= 1 && D >= 1 && H >= 1 && W >= 8 && W % 8 == 0 &&
-         ((int64_t)B * D * H * W) % kTile == 0;
+  return B >= 1 && D >= 1 && H >= 8 && W >= 8 && H % 8 == 0 && W % 8 == 0;
 }
 
 cudaError_t launch_wgrad_tc(int cin, int cout, const void* x, const void* dy, float* part,

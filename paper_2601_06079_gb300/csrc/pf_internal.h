@@ -275,9 +275,9 @@ cudaError_t launch_conv3d_tc(int cin, int cout, const void* x, const void* wt, c
                              int relu, void* y16, float* y32, int B, int D, int H, int W,
                              int* err, cudaStream_t s, int selftest = 0);
 int conv_wgrad_blocks(int B, int D, int H, int W, int max_blocks);
-// Weight gradient on tcgen05 (k_wgrad_tc.cu): needs W % 8 == 0 and a voxel
-// count that is a multiple of 64; part holds wgrad_tc_part_floats() floats of
-// per-block partial sums; err is the pipeline-timeout flag.
+// Weight gradient on tcgen05 (k_wgrad_tc.cu): needs H and W multiples of 8;
+// part holds wgrad_tc_part_floats() floats of per-block partial sums; err is
+// the pipeline-timeout flag.
 bool wgrad_tc_shape_ok(int B, int D, int H, int W);
 int wgrad_tc_blocks();
 size_t wgrad_tc_part_floats();
