@@ -547,15 +547,16 @@ def forms_ensemble(dev, stream, flush, n_steps=1000):
     ty, tune = e.tune(reps=10)
     nodes = int(st0.numel())
     per_class = {}
-    for (nx, ny), t in zip(shapes, ty):
-        per_class.setdefault(f"{nx}x{ny}", t)
-    best_uniform = min(tune["uniform_us"].values())
+    for (nx, ny), t, pol in zip(shapes, ty, tune["l2"]):
+        per_class.setdefault(f"{nx}x{ny}", {"band_rows": t, "l2": pol})
+    uni = {f"{t}/{pol}": v for (t, pol), v in tune["uniform_us"].items()}
+    best_uniform = min(uni, key=uni.get)
     out, res = {"instances": 256, "nodes": nodes, "steps": n_steps,
-                "tuned_band_rows_per_size_class": dict(sorted(per_class.items())),
-                "autotuner": {"uniform_us_per_step": {str(k): v for k, v in
-                                                     tune["uniform_us"].items()},
+                "tuned_schedule_per_size_class": dict(sorted(per_class.items())),
+                "autotuner": {"uniform_us_per_step": uni,
+                              "best_uniform": best_uniform,
                               "tuned_us_per_step": tune["tuned_us"],
-                              "gain_over_best_uniform": best_uniform / tune["tuned_us"]}}, {}
+                              "gain_over_best_uniform": uni[best_uniform] / tune["tuned_us"]}}, {}
     for mode in ("persistent", "per_step", "plain"):
         st = st0.clone()
         e.step(st, 8, mode)  # warm

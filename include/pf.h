@@ -251,19 +251,37 @@ pf_status pf_create_ensemble(pf_ctx** out, int count, const int64_t* nx, const i
  * per-instance arguments to the device and synchronises the stream. */
 pf_status pf_set_ensemble_params(pf_ctx* ctx, const pf_params* params);
 
-/* Autotuner of the band height per size class (no counterpart in the paper):
- * every candidate is timed as the whole ensemble step (best of three rounds of
- * `reps` per-step launches), the quantity the ensemble forms run.  First all
- * classes at one height, for each of {6, 12, 24} rows; then, from the best of
- * those, coordinate descent over the classes (most nodes first, at most two
- * passes), where a class takes another height only if the whole step gets at
- * least 1 % faster.  ty_out (host, count) receives the choice per instance;
- * us_out (host, 3 * classes + 4 doubles, classes in order of first
- * appearance) the microseconds per step: [3 ci + k] with class ci at height k
- * during the descent (-1 where not tried), then the three uniform heights and
- * the final choice.  Either may be NULL.  Overwrites the working planes;
- * synchronises the stream. */
-pf_status pf_tune_ensemble(pf_ctx* ctx, int reps, int* ty_out, double* us_out);
+/* L2 policies of an ensemble instance's working planes: the eviction priority
+ * its row loads and stores carry in the ensemble step.  Streaming a large
+ * instance lets the lines of the others stay in L2 from step to step.  The
+ * policy changes no result. */
+enum {
+  PF_L2_NORMAL = 0,      /* evict_normal */
+  PF_L2_STREAM = 1,      /* evict_first */
+  PF_L2_STREAM_HALF = 2  /* evict_first for half of the lines, the others unchanged */
+};
+
+/* Set the schedule of every instance: band height ty[i] (6, 12 or 24 rows per
+ * warp task) and L2 policy l2[i] (PF_L2_*).  Either may be NULL (kept).  The
+ * schedule changes no result.  Needs the workspace and parameters; uploads the
+ * task list and synchronises the stream.  Out-of-range values: PF_ERR_ARG. */
+pf_status pf_set_ensemble_schedule(pf_ctx* ctx, const int* ty, const int* l2);
+
+/* Autotuner of the schedule per size class (no counterpart in the paper).
+ * The candidates of a class are the 9 pairs (band height, L2 policy), index
+ * j = 3 * policy + k with heights {6, 12, 24}[k].  Every candidate is timed
+ * as the whole ensemble step (best of three back-to-back rounds of `reps`
+ * per-step launches), the quantity the ensemble forms run.  First all classes
+ * on one candidate, for each of the 9; then, from the best of those,
+ * coordinate descent over the classes (most nodes first, at most three
+ * passes), where a class takes another candidate only if the whole step gets
+ * at least 1 % faster.  ty_out and l2_out (host, count) receive the choice per
+ * instance; us_out (host, 9 * classes + 10 doubles, classes in order of first
+ * appearance) the microseconds per step: [9 ci + j] with class ci on
+ * candidate j during the descent (-1 where not tried), then the 9 uniform
+ * candidates and the final choice.  Any of them may be NULL.  Overwrites the
+ * working planes; synchronises the stream. */
+pf_status pf_tune_ensemble(pf_ctx* ctx, int reps, int* ty_out, int* l2_out, double* us_out);
 
 /* Advance every instance of the packed state (device, in/out) by n_steps
  * explicit steps (Eq. 12) in the given mode.  PF_ENS_PERSISTENT synchronises

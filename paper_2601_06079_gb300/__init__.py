@@ -21,7 +21,8 @@ from ._lib import (PF_ENS_PER_STEP, PF_ENS_PERSISTENT, PF_ENS_PLAIN,  # noqa: F4
                    pf_adjoint_workspace, pf_barrier_selftest, pf_bind_workspace,
                    pf_explicit_workspace,
                    pf_create_ensemble, pf_create_mesh, pf_destroy, pf_set_ensemble_params,
-                   pf_step_ensemble, pf_tune_ensemble, pf_surrogate_param_count,
+                   pf_step_ensemble, pf_tune_ensemble, pf_set_ensemble_schedule,
+                   pf_surrogate_param_count,
                    pf_surrogate_workspace, pf_surrogate_predict, pf_surrogate_train_step,
                    pf_conv3d_check, pf_surrogate_loss_grad,
                    pf_energy, pf_energy2d_static,
@@ -265,18 +266,32 @@ class Ensemble:
               for p in params]
         self._check(pf_set_ensemble_params(self._ctx, ps))
 
+    L2_POLICIES = ("normal", "stream", "stream_half")
+
+    def candidates(self):
+        """The tuner's schedule candidates in index order: (band rows, L2 policy)."""
+        return [(ty, pol) for pol in self.L2_POLICIES for ty in (6, 12, 24)]
+
+    def set_schedule(self, ty=None, l2=None):
+        """Band height (6, 12, 24) and L2 policy ("normal", "stream",
+        "stream_half") per instance (pf_set_ensemble_schedule); None keeps."""
+        codes = None if l2 is None else [self.L2_POLICIES.index(p) for p in l2]
+        self._check(pf_set_ensemble_schedule(self._ctx, ty, codes))
+
     def tune(self, reps=10):
-        """Autotune the band height per size class on the whole ensemble step
-        (pf_tune_ensemble).  Returns (band height per instance, timings) with
-        timings = {"uniform_us": {6: .., 12: .., 24: ..}, "tuned_us": ..,
-        "trials_us": per class (order of first appearance) [us at 6, 12, 24]
-        (None where not tried)}."""
-        st, ty, us = pf_tune_ensemble(self._ctx, reps, len(self.shapes), self.nclasses)
+        """Autotune (band height, L2 policy) per size class on the whole
+        ensemble step (pf_tune_ensemble).  Returns (band height per instance,
+        info) with info = {"l2": policy per instance, "uniform_us": {(ty,
+        policy): us}, "tuned_us": .., "trials_us": per class (order of first
+        appearance) {(ty, policy): us} of the candidates tried}."""
+        st, ty, l2, us = pf_tune_ensemble(self._ctx, reps, len(self.shapes), self.nclasses)
         self._check(st)
-        nc = self.nclasses
-        trials = [[u if u >= 0 else None for u in us[3 * c:3 * c + 3]] for c in range(nc)]
-        return ty, {"uniform_us": dict(zip((6, 12, 24), us[3 * nc:3 * nc + 3])),
-                    "tuned_us": us[3 * nc + 3], "trials_us": trials}
+        nc, cand = self.nclasses, self.candidates()
+        trials = [{cand[j]: us[9 * c + j] for j in range(9) if us[9 * c + j] >= 0}
+                  for c in range(nc)]
+        return ty, {"l2": [self.L2_POLICIES[p] for p in l2],
+                    "uniform_us": dict(zip(cand, us[9 * nc:9 * nc + 9])),
+                    "tuned_us": us[9 * nc + 9], "trials_us": trials}
 
     def pack(self, fields):
         return torch.cat([torch.as_tensor(f, dtype=torch.float32).reshape(-1) for f in fields]

@@ -109,8 +109,11 @@ def lib():
                                          C.POINTER(C.c_size_t), C.POINTER(C.c_int64)]
         L.pf_set_ensemble_params.restype = st
         L.pf_set_ensemble_params.argtypes = [ctx, C.POINTER(pf_params)]
+        L.pf_set_ensemble_schedule.restype = st
+        L.pf_set_ensemble_schedule.argtypes = [ctx, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.pf_tune_ensemble.restype = st
-        L.pf_tune_ensemble.argtypes = [ctx, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]
+        L.pf_tune_ensemble.argtypes = [ctx, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                       C.POINTER(C.c_double)]
         L.pf_step_ensemble.restype = st
         L.pf_step_ensemble.argtypes = [ctx, C.c_void_p, C.c_int64, C.c_int]
         L.pf_barrier_selftest.restype = st
@@ -185,7 +188,8 @@ def exported_symbols():
             "pf_set_form",
             "pf_step_implicit", "pf_jvp", "pf_implicit_residual", "pf_adjoint_workspace",
             "pf_adjoint", "pf_implicit_adjoint_workspace", "pf_implicit_adjoint",
-            "pf_create_ensemble", "pf_set_ensemble_params", "pf_tune_ensemble",
+            "pf_create_ensemble", "pf_set_ensemble_params", "pf_set_ensemble_schedule",
+            "pf_tune_ensemble",
             "pf_step_ensemble", "pf_barrier_selftest", "pf_surrogate_param_count",
             "pf_surrogate_workspace", "pf_surrogate_predict", "pf_surrogate_train_step",
             "pf_surrogate_loss_grad",
@@ -286,11 +290,18 @@ def pf_set_ensemble_params(ctx, params):
     return lib().pf_set_ensemble_params(ctx, arr)
 
 
+def pf_set_ensemble_schedule(ctx, ty=None, l2=None):
+    t = (C.c_int * len(ty))(*ty) if ty is not None else None
+    p = (C.c_int * len(l2))(*l2) if l2 is not None else None
+    return lib().pf_set_ensemble_schedule(ctx, t, p)
+
+
 def pf_tune_ensemble(ctx, reps, count, nclasses):
     ty = (C.c_int * count)()
-    us = (C.c_double * (3 * nclasses + 4))()
-    s = lib().pf_tune_ensemble(ctx, reps, ty, us)
-    return s, list(ty), list(us)
+    l2 = (C.c_int * count)()
+    us = (C.c_double * (9 * nclasses + 10))()
+    s = lib().pf_tune_ensemble(ctx, reps, ty, l2, us)
+    return s, list(ty), list(l2), list(us)
 
 
 def pf_step_ensemble(ctx, state_ptr, n_steps, mode):

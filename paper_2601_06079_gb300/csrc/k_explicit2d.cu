@@ -252,16 +252,47 @@ __device__ __forceinline__ void store_out(float* __restrict__ base0, int64_t pit
 
 // One warp task: the band of kTY output rows starting at y0, columns of
 // warp column bx.
-template <bool kCoherent>
-__device__ __forceinline__ u64 ld_row(const float* p) {
-  // coherent (L2) loads when the planes were written earlier in the same launch
-  return kCoherent ? __ldcg(reinterpret_cast<const u64*>(p))
-                   : __ldg(reinterpret_cast<const u64*>(p));
+template <bool kCoherent, bool kHint>
+__device__ __forceinline__ u64 ld_row(const float* p, u64 pol) {
+  // coherent (L2) loads when the planes were written earlier in the same launch;
+  // with kHint the load carries the L2 eviction policy `pol`
+  if constexpr (kHint) {
+    u64 v;
+    if constexpr (kCoherent)
+      asm volatile("ld.global.cg.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol));
+    else
+      asm volatile("ld.global.nc.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol));
+    return v;
+  } else {
+    return kCoherent ? __ldcg(reinterpret_cast<const u64*>(p))
+                     : __ldg(reinterpret_cast<const u64*>(p));
+  }
 }
 
-template <bool kCH, bool kIso, int kTY, bool kCoherent = false>
+template <bool kHint>
+__device__ __forceinline__ void st_row(float* p, u64 v, u64 pol) {
+  if constexpr (kHint)
+    asm volatile("st.global.L2::cache_hint.b64 [%0], %1, %2;" ::"l"(p), "l"(v), "l"(pol) : "memory");
+  else
+    *reinterpret_cast<u64*>(p) = v;
+}
+
+// L2 eviction policy of an ensemble instance's plane accesses
+__device__ __forceinline__ u64 l2_policy(int l2) {
+  u64 p;
+  if (l2 == kL2Stream)
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  else if (l2 == kL2StreamHalf)
+    asm volatile("createpolicy.fractional.L2::evict_first.L2::evict_unchanged.b64 %0, 0.5;"
+                 : "=l"(p));
+  else
+    asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+template <bool kCH, bool kIso, int kTY, bool kCoherent = false, bool kHint = false>
 __device__ __forceinline__ void sweep_task(const Explicit2DArgs& a, const float* in, float* out,
-                                           const Coef& K, int bx, int y0) {
+                                           const Coef& K, int bx, int y0, u64 pol = 0) {
   constexpr int kLag = kCH ? 2 : 1;
   constexpr int kWarm = 2 * kLag;  // rows consumed before the first finished row
   const int lane = threadIdx.x & 31;
@@ -281,7 +312,7 @@ __device__ __forceinline__ void sweep_task(const Explicit2DArgs& a, const float*
   u64 ahead[kAhead];  // rows k .. k+kAhead-1 in flight
 #pragma unroll
   for (int j = 0; j < kAhead; ++j) {
-    ahead[j] = ld_row<kCoherent>(src);
+    ahead[j] = ld_row<kCoherent, kHint>(src, pol);
     src += pitch;
   }
 #pragma unroll
@@ -289,7 +320,7 @@ __device__ __forceinline__ void sweep_task(const Explicit2DArgs& a, const float*
     const u64 P = ahead[0];
 #pragma unroll
     for (int j = 0; j + 1 < kAhead; ++j) ahead[j] = ahead[j + 1];
-    ahead[kAhead - 1] = ld_row<kCoherent>(src);
+    ahead[kAhead - 1] = ld_row<kCoherent, kHint>(src, pol);
     src += pitch;
     sweep_row<kCH, kIso>(P, w, K);
   }
@@ -298,12 +329,12 @@ __device__ __forceinline__ void sweep_task(const Explicit2DArgs& a, const float*
     const u64 P = ahead[0];
 #pragma unroll
     for (int j = 0; j + 1 < kAhead; ++j) ahead[j] = ahead[j + 1];
-    ahead[kAhead - 1] = ld_row<kCoherent>(src);
+    ahead[kAhead - 1] = ld_row<kCoherent, kHint>(src, pol);
     src += pitch;
     const u64 o = sweep_row<kCH, kIso>(P, w, K);
     const int y = y0 + it;
     if (plain)
-      *reinterpret_cast<u64*>(out0 + (int64_t)y * pitch + x) = o;
+      st_row<kHint>(out0 + (int64_t)y * pitch + x, o, pol);
     else if (writer && y < ny)
       store_out(out0, pitch, y, ny, x, nx, o);
   }
@@ -353,10 +384,11 @@ __device__ __forceinline__ void ensemble_task(const EnsTask& t, const Explicit2D
 #endif
   const float* in = parity ? a.out : a.in;
   float* out = parity ? const_cast<float*>(a.in) : a.out;
+  const u64 pol = l2_policy(a.l2);
   switch (t.ty) {
-    case 6: sweep_task<false, kIso, 6, kCoherent>(a, in, out, K, t.bx, t.y0); break;
-    case 12: sweep_task<false, kIso, 12, kCoherent>(a, in, out, K, t.bx, t.y0); break;
-    default: sweep_task<false, kIso, 24, kCoherent>(a, in, out, K, t.bx, t.y0); break;
+    case 6: sweep_task<false, kIso, 6, kCoherent, true>(a, in, out, K, t.bx, t.y0, pol); break;
+    case 12: sweep_task<false, kIso, 12, kCoherent, true>(a, in, out, K, t.bx, t.y0, pol); break;
+    default: sweep_task<false, kIso, 24, kCoherent, true>(a, in, out, K, t.bx, t.y0, pol); break;
   }
 }
 

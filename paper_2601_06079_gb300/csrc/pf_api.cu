@@ -1038,12 +1038,45 @@ pf_status pf_set_ensemble_params(pf_ctx* c, const pf_params* p) {
   return ens_upload_tasks(c, ens_build_tasks(c, all));
 }
 
-pf_status pf_tune_ensemble(pf_ctx* c, int reps, int* ty_out, double* us_out) {
+// Schedule candidates of an instance: band height kEnsTy[j % 3] and L2
+// policy j / 3 (pf::kL2Normal, kL2Stream, kL2StreamHalf).
+constexpr int kEnsTy[3] = {6, 12, 24};
+constexpr int kEnsCands = 9;
+
+// Upload the per-instance arguments and the task list for the current
+// schedule (synchronises the stream).
+pf_status ens_upload_schedule(pf_ctx* c) {
+  PF_CUDA(cudaMemcpyAsync(c->ens_dargs, c->ens_args.data(),
+                          sizeof(pf::Explicit2DArgs) * c->ens_count, cudaMemcpyHostToDevice,
+                          c->stream));
+  std::vector<int> all(c->ens_count);
+  for (int i = 0; i < c->ens_count; ++i) all[i] = i;
+  return ens_upload_tasks(c, ens_build_tasks(c, all));
+}
+
+pf_status pf_set_ensemble_schedule(pf_ctx* c, const int* ty, const int* l2) {
+  if (!c) return PF_ERR_ARG;
+  if (c->ens_count < 1) return fail(c, PF_ERR_ARG, "not an ensemble context");
+  if (!c->ws || !c->par_set) return fail(c, PF_ERR_STATE, "workspace or parameters missing");
+  for (int i = 0; i < c->ens_count; ++i) {
+    if (ty && ty[i] != 6 && ty[i] != 12 && ty[i] != 24)
+      return fail(c, PF_ERR_ARG, "band height of instance %d is not 6, 12 or 24", i);
+    if (l2 && (l2[i] < pf::kL2Normal || l2[i] > pf::kL2StreamHalf))
+      return fail(c, PF_ERR_ARG, "L2 policy of instance %d is not 0, 1 or 2", i);
+  }
+  for (int i = 0; i < c->ens_count; ++i) {
+    if (ty) c->ens_ty[i] = ty[i];
+    if (l2) c->ens_args[i].l2 = l2[i];
+  }
+  destroy_graph(c);
+  return ens_upload_schedule(c);
+}
+
+pf_status pf_tune_ensemble(pf_ctx* c, int reps, int* ty_out, int* l2_out, double* us_out) {
   if (!c) return PF_ERR_ARG;
   if (c->ens_count < 1) return fail(c, PF_ERR_ARG, "not an ensemble context");
   if (!c->ws || !c->par_set) return fail(c, PF_ERR_STATE, "workspace or parameters missing");
   if (reps < 1) return fail(c, PF_ERR_ARG, "reps must be >= 1");
-  const int cand[3] = {6, 12, 24};
   // planes hold defined values while timing (the step is data-independent in cost)
   for (int i = 0; i < c->ens_count; ++i) {
     const pf::Explicit2DArgs& x = c->ens_args[i];
@@ -1059,16 +1092,19 @@ pf_status pf_tune_ensemble(pf_ctx* c, int reps, int* ty_out, double* us_out) {
     if (it == classes.end()) classes.push_back(k);
   }
   const int nc = (int)classes.size();
-  std::vector<int> all(c->ens_count);
-  for (int i = 0; i < c->ens_count; ++i) all[i] = i;
   cudaEvent_t e0, e1;
   PF_CUDA(cudaEventCreate(&e0));
   PF_CUDA(cudaEventCreate(&e1));
   // whole-ensemble step time (us, best of three rounds of `reps` per-step
-  // launches) with band height assign[class] for every instance of a class
+  // launches) with candidate assign[class] for every instance of a class; the
+  // rounds run back to back, so the later ones see the L2 contents the
+  // schedule leaves from step to step
   auto time_all = [&](const std::vector<int>& assign, double* us) -> pf_status {
-    for (int i = 0; i < c->ens_count; ++i) c->ens_ty[i] = assign[cls[i]];
-    pf_status s = ens_upload_tasks(c, ens_build_tasks(c, all));
+    for (int i = 0; i < c->ens_count; ++i) {
+      c->ens_ty[i] = kEnsTy[assign[cls[i]] % 3];
+      c->ens_args[i].l2 = assign[cls[i]] / 3;
+    }
+    pf_status s = ens_upload_schedule(c);
     if (s != PF_OK) return s;
     const int grid = ens_step_grid(c->ens_ntasks);
     double best = 1e30;
@@ -1077,7 +1113,7 @@ pf_status pf_tune_ensemble(pf_ctx* c, int reps, int* ty_out, double* us_out) {
                                                c->ens_iso, grid, c->stream);  // warm-up
       if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
       for (int r = 0; r < reps && e == cudaSuccess; ++r)
-        e = pf::launch_ensemble_step(c->ens_tasks, c->ens_ntasks, c->ens_dargs, r & 1,
+        e = pf::launch_ensemble_step(c->ens_tasks, c->ens_ntasks, c->ens_dargs, (r + 1) & 1,
                                      c->ens_iso, grid, c->stream);
       if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -1090,36 +1126,37 @@ pf_status pf_tune_ensemble(pf_ctx* c, int reps, int* ty_out, double* us_out) {
     return PF_OK;
   };
   pf_status st = PF_OK;
-  // 1. every class at the same band height
-  double uni[3] = {0, 0, 0};
-  int bk = 0;
-  for (int k = 0; k < 3 && st == PF_OK; ++k) {
-    st = time_all(std::vector<int>(nc, cand[k]), &uni[k]);
-    if (uni[k] < uni[bk]) bk = k;
+  // 1. every class on the same candidate
+  double uni[kEnsCands];
+  int bj = 0;
+  for (int j = 0; j < kEnsCands && st == PF_OK; ++j) {
+    st = time_all(std::vector<int>(nc, j), &uni[j]);
+    if (st == PF_OK && uni[j] < uni[bj]) bj = j;
   }
-  std::vector<int> assign(nc, cand[bk]);
-  double best = uni[bk];
+  std::vector<int> assign(nc, bj);
+  double best = st == PF_OK ? uni[bj] : 0.0;
   if (us_out)
     for (int ci = 0; ci < nc; ++ci)
-      for (int k = 0; k < 3; ++k) us_out[3 * ci + k] = k == bk ? best : -1.0;
-  // 2. coordinate descent over the classes, most nodes first: a class keeps
-  // another height only if the whole step gets at least 1 % faster
+      for (int j = 0; j < kEnsCands; ++j) us_out[kEnsCands * ci + j] = j == bj ? best : -1.0;
+  // 2. coordinate descent over the classes, most nodes first (the classes
+  // that fill L2 the most are the first to try streaming): a class keeps
+  // another candidate only if the whole step gets at least 1 % faster
   std::vector<int> order(nc);
   for (int ci = 0; ci < nc; ++ci) order[ci] = ci;
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
     return classes[x].first * classes[x].second > classes[y].first * classes[y].second;
   });
-  for (int pass = 0; pass < 2 && st == PF_OK; ++pass) {
+  for (int pass = 0; pass < 3 && st == PF_OK; ++pass) {
     bool changed = false;
     for (int ci : order) {
-      for (int k = 0; k < 3 && st == PF_OK; ++k) {
-        if (cand[k] == assign[ci]) continue;
+      for (int j = 0; j < kEnsCands && st == PF_OK; ++j) {
+        if (j == assign[ci]) continue;
         std::vector<int> trial = assign;
-        trial[ci] = cand[k];
+        trial[ci] = j;
         double t = 0.0;
         st = time_all(trial, &t);
         if (st != PF_OK) break;
-        if (us_out) us_out[3 * ci + k] = t;
+        if (us_out) us_out[kEnsCands * ci + j] = t;
         if (t < 0.99 * best) {
           best = t;
           assign = trial;
@@ -1134,14 +1171,17 @@ pf_status pf_tune_ensemble(pf_ctx* c, int reps, int* ty_out, double* us_out) {
   cudaEventDestroy(e1);
   if (st != PF_OK) return st;
   if (us_out) {
-    for (int k = 0; k < 3; ++k) us_out[3 * nc + k] = uni[k];
-    us_out[3 * nc + 3] = best;
+    for (int j = 0; j < kEnsCands; ++j) us_out[kEnsCands * nc + j] = uni[j];
+    us_out[kEnsCands * nc + kEnsCands] = best;
   }
-  for (int i = 0; i < c->ens_count; ++i) c->ens_ty[i] = assign[cls[i]];
-  if (ty_out)
-    for (int i = 0; i < c->ens_count; ++i) ty_out[i] = c->ens_ty[i];
+  for (int i = 0; i < c->ens_count; ++i) {
+    c->ens_ty[i] = kEnsTy[assign[cls[i]] % 3];
+    c->ens_args[i].l2 = assign[cls[i]] / 3;
+    if (ty_out) ty_out[i] = c->ens_ty[i];
+    if (l2_out) l2_out[i] = c->ens_args[i].l2;
+  }
   destroy_graph(c);
-  return ens_upload_tasks(c, ens_build_tasks(c, all));
+  return ens_upload_schedule(c);
 }
 
 pf_status pf_step_ensemble(pf_ctx* c, float* packed, int64_t n_steps, int mode) {

@@ -87,8 +87,15 @@ struct Explicit2DArgs {
   // (filled by pack_explicit2d): g_lo, g_hi, -g_lo, p0..p3, then per stencil
   // a = c0 - cd, b = cd, c0, cx, cy, cd
   unsigned long long pair[7 + 12];
+  // L2 eviction priority of the working planes' row loads and stores in the
+  // ensemble sweep (kL2Normal, kL2Stream, kL2StreamHalf); single-mesh steps
+  // ignore it
+  int l2;
 };
 void pack_explicit2d(Explicit2DArgs& a);
+constexpr int kL2Normal = 0;      // evict_normal
+constexpr int kL2Stream = 1;      // evict_first: the lines go first when L2 needs room
+constexpr int kL2StreamHalf = 2;  // evict_first for half of the lines, the rest unchanged
 
 cudaError_t launch_ac2d(const Explicit2DArgs& a, cudaStream_t s);
 

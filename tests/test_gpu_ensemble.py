@@ -56,13 +56,35 @@ def test_modes_agree_bitwise_and_tuning_keeps_results():
     assert torch.equal(outs["plain"], outs["persistent"])
     ty, info = e.tune(reps=3)
     assert set(ty) <= {6, 12, 24}
-    assert all(u > 0 for u in info["uniform_us"].values())
-    # the choice is never slower than the best single height by more than noise
+    assert set(info["l2"]) <= set(e.L2_POLICIES)
+    assert len(info["uniform_us"]) == 9 and all(u > 0 for u in info["uniform_us"].values())
+    # the choice is never slower than the best single candidate by more than noise
     assert info["tuned_us"] <= min(info["uniform_us"].values()) * 1.0001
-    assert all(u is None or u > 0 for row in info["trials_us"] for u in row)
+    assert all(u > 0 for row in info["trials_us"] for u in row.values())
     st = e.pack(fields)
     e.step(st, 17, "persistent")
     assert torch.equal(st, outs["plain"])
+    # every schedule (band height x L2 policy, mixed across instances) is
+    # bitwise equal to the plain form in both batched modes
+    n = len(SHAPES)
+    cands = e.candidates()
+    for k in range(len(cands)):
+        sched = [cands[(k + i) % len(cands)] for i in range(n)]
+        e.set_schedule([c[0] for c in sched], [c[1] for c in sched])
+        for mode in ("per_step", "persistent"):
+            st = e.pack(fields)
+            e.step(st, 17, mode)
+            assert torch.equal(st, outs["plain"]), (k, mode)
+
+
+def test_schedule_setter_rejects_bad_values():
+    pf = _pf()
+    e, _, _ = make(SHAPES, seed=4)
+    with pytest.raises(pf.PFError):
+        e.set_schedule(ty=[7] * len(SHAPES))
+    with pytest.raises(ValueError):
+        e.set_schedule(l2=["keep"] * len(SHAPES))
+    assert pf._lib.pf_set_ensemble_schedule(e._ctx, None, [3] * len(SHAPES)) != 0
 
 
 def test_256_instance_ensemble_1000_steps():
