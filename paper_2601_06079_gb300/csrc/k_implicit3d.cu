@@ -375,6 +375,248 @@ __global__ void __launch_bounds__(TileCfg<kJVP>::kThreads) k_implicit3d(const Im
   }
 }
 
+// ---------------------------------------------------------------------------
+// J v on column tiles that sweep along z.  A block owns kSX x kSY output nodes
+// in x, y and a chunk of kCZ node planes in z.  It walks the element layers
+// of its column from the one below the chunk to the last one inside it:
+//   - node plane z+1 of U and v (fields in pairs, the kSNX x kSNY nodes
+//     around the tile, mirrored at the mesh boundary) enters a 3-plane ring
+//     in shared memory, pair index fastest, from registers loaded while the
+//     previous layer computed;
+//   - one thread per (element, field pair) interpolates U and v (with the
+//     gradient of v) at the 8 Gauss points from its 8 corners, and the G
+//     threads of an element (adjacent lanes, one per pair) sum S2 = sum_f U_f^2
+//     and T = sum_f U_f v_f by warp shuffles: every coupling of Eq. 14 is
+//     formed from one interpolation per field, with no second pass;
+//   - H v and the gradient term are weighted back to the corners: the 4 on
+//     the layer's lower face into one buffer, the 4 on its upper face into a
+//     2-layer ring;
+//   - node plane z gathers its 8 element contributions (lower faces of layer
+//     z, upper faces of layer z-1) in the fixed corner order, adds the mass
+//     term and writes J v.
+// Two block barriers per layer; no atomics, so results are bitwise repeatable.
+#ifndef PF_JVP_SX
+#define PF_JVP_SX 16
+#endif
+#ifndef PF_JVP_SY
+#define PF_JVP_SY 8
+#endif
+#ifndef PF_JVP_CZ
+#define PF_JVP_CZ 16
+#endif
+#ifndef PF_JVP_MINB
+#define PF_JVP_MINB 1
+#endif
+constexpr int kSX = PF_JVP_SX, kSY = PF_JVP_SY;  // output nodes per column tile in x, y
+constexpr int kSNX = kSX + 2, kSNY = kSY + 2;    // staged nodes per plane
+constexpr int kSEX = kSX + 1, kSEY = kSY + 1;    // elements per layer touching the tile
+constexpr int kSPlane = kSNX * kSNY;
+constexpr int kSElems = kSEX * kSEY;
+constexpr int kCZ = PF_JVP_CZ;                   // output node planes per block
+
+template <int NP>
+struct SweepCfg {
+  static constexpr int G = NP >= 3 ? 4 : NP;  // lanes per element, one per field pair
+  static constexpr int kThreads = (kSElems * G + 31) / 32 * 32;
+  static constexpr int kItems = (kSPlane * NP + kThreads - 1) / kThreads;  // staged pairs per thread
+  static constexpr size_t kSmem = sizeof(u64) * (size_t)NP * (2 * 3 * kSPlane + 4 * kSElems + 8 * kSElems);
+};
+
+template <int NF>
+__global__ void __launch_bounds__(SweepCfg<(NF + 1) / 2>::kThreads, PF_JVP_MINB)
+    k_jvp3d_sweep(const Implicit3DArgs a) {
+  constexpr int NP = (NF + 1) / 2;
+  constexpr int G = SweepCfg<NP>::G, kThreads = SweepCfg<NP>::kThreads;
+  constexpr int kItems = SweepCfg<NP>::kItems;
+  extern __shared__ u64 smem[];
+  u64* sU = smem;                        // [3 planes][kSPlane nodes][NP]
+  u64* sW = sU + 3 * kSPlane * NP;       // v, same layout
+  u64* sLow = sW + 3 * kSPlane * NP;     // [4 lower corners][kSElems][NP] of the current layer
+  u64* sUp = sLow + 4 * kSElems * NP;    // [2 layers][4 upper corners][kSElems][NP]
+
+  const int tiles_x = (a.nx + kSX - 1) / kSX, tiles_y = (a.ny + kSY - 1) / kSY;
+  const int b = blockIdx.x;
+  const int x0 = (b % tiles_x) * kSX, y0 = ((b / tiles_x) % tiles_y) * kSY;
+  const int z0 = (b / (tiles_x * tiles_y)) * kCZ;
+  const int cz = min(kCZ, a.nz - z0);    // output planes z0 .. z0 + cz - 1
+  const int64_t N = (int64_t)a.nx * a.ny * a.nz;
+  const int64_t plane = (int64_t)a.nx * a.ny;
+  const int tid = threadIdx.x;
+
+  // staged items of this thread: node (in the plane) and pair, as global
+  // offsets within a plane and field offsets
+  int64_t ioff[kItems];
+  int islot[kItems];
+#pragma unroll
+  for (int k = 0; k < kItems; ++k) {
+    const int it = tid + k * kThreads;
+    islot[k] = it < kSPlane * NP ? it : -1;
+    const int node = it / NP;
+    const int lx = node % kSNX, ly = node / kSNX;
+    const int gx = reflect(x0 - 1 + lx, a.nx), gy = reflect(y0 - 1 + ly, a.ny);
+    ioff[k] = (int64_t)gy * a.nx + gx;
+  }
+  u64 pu[kItems], pw[kItems];
+  auto fetch = [&](int z) {  // plane z (mirrored) of this thread's items into registers
+    const int64_t zo = (int64_t)reflect(z, a.nz) * plane;
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+      pu[k] = pw[k] = 0;
+      if (islot[k] >= 0) {
+        const int p = islot[k] % NP;
+        const int64_t g = zo + ioff[k];
+        const int64_t f0 = (int64_t)(2 * p) * N + g;
+        pu[k] = pk(__ldg(a.U + f0), 2 * p + 1 < NF ? __ldg(a.U + f0 + N) : 0.0f);
+        pw[k] = pk(__ldg(a.W + f0), 2 * p + 1 < NF ? __ldg(a.W + f0 + N) : 0.0f);
+      }
+    }
+  };
+  auto store_plane = [&](int slot) {
+#pragma unroll
+    for (int k = 0; k < kItems; ++k)
+      if (islot[k] >= 0) {
+        sU[slot * kSPlane * NP + islot[k]] = pu[k];
+        sW[slot * kSPlane * NP + islot[k]] = pw[k];
+      }
+  };
+
+  // element task of this thread
+  const int e_raw = tid / G, p_el = tid % G;
+  const bool el_ok = e_raw < kSElems && p_el < NP;
+  const int e = e_raw < kSElems ? e_raw : kSElems - 1;
+  const int pe = p_el < NP ? p_el : NP - 1;
+  const int node0 = (e / kSEX) * kSNX + e % kSEX;
+
+  // plane z0 - 1 -> slot 0, then plane z0 in flight
+  fetch(z0 - 1);
+  store_plane(0);
+  fetch(z0);
+
+  for (int i = 0; i <= cz; ++i) {  // element layer z0 - 1 + i between planes z0 - 1 + i, z0 + i
+    const int s0 = i % 3, s1 = (i + 1) % 3;
+    store_plane(s1);
+    if (i < cz) fetch(z0 + i + 1);
+    __syncthreads();
+
+    {
+      u64 c[8], uq[8], vq[8], hq[8], out[8], gx[4], gy[4], gz[4];
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        c[k] = sU[(((k >> 2) ? s1 : s0) * kSPlane + node0 + ((k >> 1) & 1) * kSNX + (k & 1)) * NP + pe];
+      interp3(c, uq);
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        c[k] = sW[(((k >> 2) ? s1 : s0) * kSPlane + node0 + ((k >> 1) & 1) * kSNX + (k & 1)) * NP + pe];
+      interp3_grad(c, vq, gx, gy, gz);
+      if (a.double_well) {
+        // f = W u^2 (1-u)^2:  f'' = 2W (1 - 6u + 6u^2)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const u64 u = uq[q];
+          const u64 f2 = fma2(bc(6.0f), sub2(mul2(u, u), u), bc(1.0f));
+          hq[q] = mul2(mul2(bc(a.dw2), f2), vq[q]);
+        }
+      } else {
+        // Fan-Chen: (H v)_f = (-a + 2g S2 + (3b - 6g) u_f^2) v_f + 4g u_f T
+        float s2[8], t[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const u64 uu = mul2(uq[q], uq[q]), uv = mul2(uq[q], vq[q]);
+          s2[q] = p_el < NP ? plo(uu) + phi(uu) : 0.0f;
+          t[q] = p_el < NP ? plo(uv) + phi(uv) : 0.0f;
+        }
+        if constexpr (G >= 2) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            s2[q] += __shfl_xor_sync(0xffffffffu, s2[q], 1);
+            t[q] += __shfl_xor_sync(0xffffffffu, t[q], 1);
+          }
+        }
+        if constexpr (G >= 4) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            s2[q] += __shfl_xor_sync(0xffffffffu, s2[q], 2);
+            t[q] += __shfl_xor_sync(0xffffffffu, t[q], 2);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const u64 u = uq[q];
+          hq[q] = fma2(fma2(bc(a.c3b6g), mul2(u, u), bc(fmaf(a.two_gamma, s2[q], -a.alpha))), vq[q],
+                       mul2(bc(a.four_gamma * t[q]), u));
+        }
+      }
+      project3_grad(hq, gx, gy, gz, a.kg, out);
+      if (el_ok) {
+        u64* up = sUp + (i & 1) * 4 * kSElems * NP;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          sLow[(k * kSElems + e) * NP + p_el] = out[k];
+          up[(k * kSElems + e) * NP + p_el] = out[4 + k];
+        }
+      }
+    }
+    __syncthreads();
+
+    if (i >= 1) {  // node plane z0 - 1 + i: lower faces of this layer, upper faces of the last
+      const int gz = z0 - 1 + i;
+      const u64* upp = sUp + ((i - 1) & 1) * 4 * kSElems * NP;
+      for (int t = tid; t < kSX * kSY * NP; t += kThreads) {
+        const int n = t / NP, p = t % NP;
+        const int lx = 1 + n % kSX, ly = 1 + n / kSX;
+        const int gx = x0 + lx - 1, gy = y0 + ly - 1;
+        if (gx >= a.nx || gy >= a.ny) continue;
+        u64 acc = sLow[(ly * kSEX + lx) * NP + p];  // corner 0 of the element above
+#pragma unroll
+        for (int k = 1; k < 8; ++k) {  // element with corner k at this node
+          const int ex = lx - (k & 1), ey = ly - ((k >> 1) & 1);
+          const u64* src = (k >> 2) ? upp : sLow;
+          acc = add2(acc, src[((k & 3) * kSElems + ey * kSEX + ex) * NP + p]);
+        }
+        const u64 own = sW[(s0 * kSPlane + ly * kSNX + lx) * NP + p];
+        u64 g = fma2(own, bc(a.inv_dt), mul2(bc(0.125f * a.mob), acc));
+        if (a.unscaled) {
+          const float wx = (gx == 0 || gx == a.nx - 1) ? 0.5f : 1.0f;
+          const float wy = (gy == 0 || gy == a.ny - 1) ? 0.5f : 1.0f;
+          const float wz = (gz == 0 || gz == a.nz - 1) ? 0.5f : 1.0f;
+          g = mul2(g, bc(a.cell * wx * wy * wz));
+        }
+        const int64_t o = (int64_t)gz * plane + (int64_t)gy * a.nx + gx;
+        a.out[(int64_t)(2 * p) * N + o] = plo(g);
+        if (2 * p + 1 < NF) a.out[(int64_t)(2 * p + 1) * N + o] = phi(g);
+      }
+    }
+  }
+}
+
+template <int NF>
+cudaError_t launch_sweep_nf(const Implicit3DArgs& a, cudaStream_t s) {
+  constexpr int NP = (NF + 1) / 2;
+  constexpr size_t smem = SweepCfg<NP>::kSmem;
+  static std::atomic<unsigned long long> raised{0};
+  const cudaError_t e = raise_smem_limit(k_jvp3d_sweep<NF>, (int)smem, raised);
+  if (e != cudaSuccess) return e;
+  const int64_t blocks = (int64_t)((a.nx + kSX - 1) / kSX) * ((a.ny + kSY - 1) / kSY) *
+                         ((a.nz + kCZ - 1) / kCZ);
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  k_jvp3d_sweep<NF><<<(unsigned)blocks, SweepCfg<NP>::kThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_any(const Implicit3DArgs& a, cudaStream_t s) {
+  switch (a.nf) {
+    case 1: return launch_sweep_nf<1>(a, s);
+    case 2: return launch_sweep_nf<2>(a, s);
+    case 3: return launch_sweep_nf<3>(a, s);
+    case 4: return launch_sweep_nf<4>(a, s);
+    case 5: return launch_sweep_nf<5>(a, s);
+    case 6: return launch_sweep_nf<6>(a, s);
+    case 7: return launch_sweep_nf<7>(a, s);
+    case 8: return launch_sweep_nf<8>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <int NF, bool kJVP>
 cudaError_t launch_nf(const Implicit3DArgs& a, cudaStream_t s) {
   constexpr int kTZ = TileCfg<kJVP>::kTZ, kThreads = TileCfg<kJVP>::kThreads;
@@ -412,6 +654,11 @@ cudaError_t launch_residual3d(const Implicit3DArgs& a, cudaStream_t s) {
   return launch_any<false>(a, s);
 }
 
-cudaError_t launch_jvp3d(const Implicit3DArgs& a, cudaStream_t s) { return launch_any<true>(a, s); }
+#ifndef PF_JVP_TILED
+#define PF_JVP_TILED 0
+#endif
+cudaError_t launch_jvp3d(const Implicit3DArgs& a, cudaStream_t s) {
+  return PF_JVP_TILED ? launch_any<true>(a, s) : launch_sweep_any(a, s);
+}
 
 }  // namespace pf
