@@ -8,18 +8,14 @@
 // halves, so every node uses the interior formula (an optional final
 // multiplication by m_i gives R and J v themselves).
 //
-// Work split: one block per 8 x 8 x kTZ node tile (kTZ = 8 for the JVP, 2 for
-// the residual; see TileCfg).  The block stages U (and v, or U^n) for the
-// nodes around it (one halo layer) in shared memory, mirrored at the mesh
-// boundary, then evaluates all elements touching the tile:
-//   phase 1: per element and Gauss point, S2 = sum_f U_f^2 (and T =
-//            sum_f U_f v_f for the JVP), the only couplings between fields
-//            (the JVP keeps the Hessian's factors 2 gamma S2 - alpha, 4 gamma T);
-//   phase 2: per field, the Gauss values (trilinear, sum-factorised), the
-//            pointwise f' or H v, and the gradient term kappa grad w . grad N_a
-//            (w = v for the JVP, U for the residual), all weighted back to the
-//            8 corners into a per-element buffer; then a node-centric gather
-//            of the 8 element contributions and the mass term.
+// Work split: a block owns a 16 x 8 node column in x, y and a chunk of 16
+// node planes in z, and sweeps its element layers along z (the kernel below
+// describes the steps).  One thread per (element, field pair) forms the
+// trilinear Gauss values (sum-factorised), the pointwise f' or H v, and the
+// gradient term kappa grad w . grad N_a (w = U for the residual, v for the
+// JVP), weighted back to the 8 corners; the lanes of an element sum the field
+// couplings S2 = sum_f U_f^2 and T = sum_f U_f v_f by warp shuffles; a
+// node-centric gather adds the 8 element contributions and the mass term.
 // The gradient term needs no extra loads: the three passes of the
 // sum-factorised interpolation already form the element's differences along
 // x, y and z, which (interpolated in the other directions) are the Gauss-point
@@ -29,40 +25,12 @@
 // Fields travel in pairs: shared memory holds (field 2p, field 2p+1) side by
 // side (a zero field pads an odd count), one 64-bit load fetches both, and
 // every interpolation, pointwise term, projection and stencil runs on packed
-// FP32 pairs with the f32x2 instructions of sm_100+, halving both the
-// shared-memory loads and the FP32 instructions of the per-field work.
+// FP32 pairs with the f32x2 instructions of sm_100+.
 // No atomics: the gather order is fixed, so results are bitwise repeatable.
 #include "pf_internal.h"
 
 namespace pf {
 namespace {
-
-#ifndef PF_IMP_TZ
-#define PF_IMP_TZ 8
-#endif
-#ifndef PF_IMP_THREADS
-#define PF_IMP_THREADS 768
-#endif
-#ifndef PF_RES_TZ
-#define PF_RES_TZ 2
-#endif
-#ifndef PF_RES_THREADS
-#define PF_RES_THREADS 256
-#endif
-constexpr int kTX = 8, kTY = 8;                // output nodes per tile edge in x, y
-constexpr int kNX = kTX + 2, kNY = kTY + 2;    // staged nodes (1 halo each side)
-constexpr int kEX = kTX + 1, kEY = kTY + 1;    // elements touching the tile
-
-// Tile depth and block size per operator.  The JVP keeps 8^3-node tiles, one
-// 157 KB block per SM.  The residual carries half the per-element state and
-// runs faster on flat 8 x 8 x 2 tiles, three blocks per SM.
-template <bool kJVP>
-struct TileCfg {
-  static constexpr int kTZ = kJVP ? PF_IMP_TZ : PF_RES_TZ;
-  static constexpr int kThreads = kJVP ? PF_IMP_THREADS : PF_RES_THREADS;
-  static constexpr int kNodes = kNX * kNY * (kTZ + 2);
-  static constexpr int kElems = kEX * kEY * (kTZ + 1);
-};
 
 typedef unsigned long long u64;  // packed FP32 pair: low half = the even field
 
@@ -217,202 +185,45 @@ __device__ __forceinline__ void project3_grad(const u64 q[8], const u64 gx[4], c
   }
 }
 
-__device__ __forceinline__ int nidx(int x, int y, int z) { return (z * kNY + y) * kNX + x; }
-
-// the 8 corners of element base (staged-node index of its lower corner)
-__device__ __forceinline__ void corners(const u64* P, int base, u64 c[8]) {
-#pragma unroll
-  for (int k = 0; k < 8; ++k) c[k] = P[base + ((k >> 2) * kNY + ((k >> 1) & 1)) * kNX + (k & 1)];
-}
-
-template <int NF, bool kJVP>
-__global__ void __launch_bounds__(TileCfg<kJVP>::kThreads) k_implicit3d(const Implicit3DArgs a) {
-  constexpr int kTZ = TileCfg<kJVP>::kTZ, kThreads = TileCfg<kJVP>::kThreads;
-  constexpr int kNodes = TileCfg<kJVP>::kNodes, kElems = TileCfg<kJVP>::kElems;
-  constexpr int NP = (NF + 1) / 2;  // field pairs
-  extern __shared__ u64 smem[];
-  u64* sU = smem;                                // [NP][kNodes] (field 2p, 2p+1)
-  u64* sW = sU + NP * kNodes;                    // v (JVP) or U^n (residual)
-  u64* sE = sW + NP * kNodes;                    // [8][kElems] corner contributions of a pair
-  // per-element values are stored [8][kElems] (Gauss point or corner major), so
-  // that consecutive threads (consecutive elements) hit consecutive banks.
-  // Residual: S2 at the Gauss points.  JVP: the pair (2 gamma S2 - alpha,
-  // 4 gamma T), the two coupling factors of H v, fetched by one 64-bit load.
-  float* sS = reinterpret_cast<float*>(sE + 8 * kElems);  // [8][kElems] (residual)
-  u64* sQ = sE + 8 * kElems;                               // [8][kElems] (JVP)
-
-  const int tiles_x = (a.nx + kTX - 1) / kTX, tiles_y = (a.ny + kTY - 1) / kTY;
-  const int tile = blockIdx.x;
-  const int x0 = (tile % tiles_x) * kTX, y0 = ((tile / tiles_x) % tiles_y) * kTY,
-            z0 = (tile / (tiles_x * tiles_y)) * kTZ;
-  const int64_t N = (int64_t)a.nx * a.ny * a.nz;
-
-  // stage U and v / U^n with mirror images beyond the mesh, fields in pairs
-  for (int i = threadIdx.x; i < kNodes; i += kThreads) {
-    const int lx = i % kNX, ly = (i / kNX) % kNY, lz = i / (kNX * kNY);
-    const int gx = reflect(x0 - 1 + lx, a.nx), gy = reflect(y0 - 1 + ly, a.ny),
-              gz = reflect(z0 - 1 + lz, a.nz);
-    const int64_t g = ((int64_t)gz * a.ny + gy) * a.nx + gx;
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-      const int f0 = 2 * p, f1 = 2 * p + 1;
-      sU[p * kNodes + i] = pk(a.U[f0 * N + g], f1 < NF ? a.U[f1 * N + g] : 0.0f);
-      sW[p * kNodes + i] = pk(a.W[f0 * N + g], f1 < NF ? a.W[f1 * N + g] : 0.0f);
-    }
-  }
-  __syncthreads();
-
-  // phase 1: field couplings at the Gauss points of every element
-  for (int e = threadIdx.x; e < kElems; e += kThreads) {
-    const int ex = e % kEX, ey = (e / kEX) % kEY, ez = e / (kEX * kEY);
-    const int base = nidx(ex, ey, ez);
-    u64 S2[8], T[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) S2[q] = T[q] = 0;
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-      u64 c[8], uq[8];
-      corners(sU + p * kNodes, base, c);
-      interp3(c, uq);
-      if (kJVP) {
-        u64 vq[8];
-        corners(sW + p * kNodes, base, c);
-        interp3(c, vq);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) T[q] = fma2(uq[q], vq[q], T[q]);
-      }
-#pragma unroll
-      for (int q = 0; q < 8; ++q) S2[q] = fma2(uq[q], uq[q], S2[q]);
-    }
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const float s2 = plo(S2[q]) + phi(S2[q]);
-      if (kJVP)
-        sQ[q * kElems + e] =
-            pk(fmaf(a.two_gamma, s2, -a.alpha), a.four_gamma * (plo(T[q]) + phi(T[q])));
-      else
-        sS[q * kElems + e] = s2;
-    }
-  }
-  // no barrier: phase 2 reads element e's coupling factors in the thread that
-  // wrote them (both loops give element e to the same thread), and writes only
-  // sE, which phase 1 does not touch
-
-  // phase 2: one field pair at a time
-  for (int p = 0; p < NP; ++p) {
-    const u64* Up = sU + p * kNodes;
-    const u64* Wp = sW + p * kNodes;
-    for (int e = threadIdx.x; e < kElems; e += kThreads) {
-      const int ex = e % kEX, ey = (e / kEX) % kEY, ez = e / (kEX * kEY);
-      const int base = nidx(ex, ey, ez);
-      u64 c[8], uq[8], vq[8], hq[8], out[8], gx[4], gy[4], gz[4];
-      corners(Up, base, c);
-      // the gradient term acts on v (JVP) or on U (residual)
-      if (kJVP) {
-        interp3(c, uq);
-        corners(Wp, base, c);
-        interp3_grad(c, vq, gx, gy, gz);
-      } else {
-        interp3_grad(c, uq, gx, gy, gz);
-      }
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const u64 u = uq[q], uu = mul2(u, u);
-        if (a.double_well) {
-          // f = W u^2 (1-u)^2:  f' = 2W u (1-u)(1-2u),  f'' = 2W (1 - 6u + 6u^2)
-          if (kJVP) {
-            const u64 f2 = fma2(bc(6.0f), sub2(uu, u), bc(1.0f));
-            hq[q] = mul2(mul2(bc(a.dw2), f2), vq[q]);
-          } else {
-            const u64 om = sub2(bc(1.0f), u);                  // 1 - u
-            const u64 o2 = fma2(bc(-2.0f), u, bc(1.0f));       // 1 - 2u
-            hq[q] = mul2(mul2(bc(a.dw2), u), mul2(om, o2));
-          }
-        } else {
-          // Fan-Chen: f'_f = u (-a + 2g S2 + (b - 2g) u^2)
-          //           (H v)_f = (-a + 2g S2 + (3b - 6g) u^2) v_f + 4g u T
-          if (kJVP) {
-            const u64 st = sQ[q * kElems + e];
-            hq[q] = fma2(fma2(bc(a.c3b6g), uu, bc(plo(st))), vq[q], mul2(bc(phi(st)), u));
-          } else {
-            const u64 base_c = bc(fmaf(a.two_gamma, sS[q * kElems + e], -a.alpha));
-            hq[q] = mul2(u, fma2(bc(a.cb2g), uu, base_c));
-          }
-        }
-      }
-      project3_grad(hq, gx, gy, gz, a.kg, out);
-#pragma unroll
-      for (int k = 0; k < 8; ++k) sE[k * kElems + e] = out[k];
-    }
-    __syncthreads();
-    // node gather: 8 elements around the node, mass term
-    for (int i = threadIdx.x; i < kTX * kTY * kTZ; i += kThreads) {
-      const int lx = 1 + i % kTX, ly = 1 + (i / kTX) % kTY, lz = 1 + i / (kTX * kTY);
-      const int gx = x0 + lx - 1, gy = y0 + ly - 1, gz = z0 + lz - 1;
-      if (gx >= a.nx || gy >= a.ny || gz >= a.nz) continue;
-      u64 acc = sE[(lz * kEY + ly) * kEX + lx];  // k = 0
-#pragma unroll
-      for (int k = 1; k < 8; ++k) {  // element with corner k at this node
-        const int ex = lx - (k & 1), ey = ly - ((k >> 1) & 1), ez = lz - (k >> 2);
-        acc = add2(acc, sE[k * kElems + (ez * kEY + ey) * kEX + ex]);
-      }
-      const int c0 = nidx(lx, ly, lz);
-      // G = (u - u^n)/dt + L (F + kappa K u) / m   or   v/dt + L (H v + kappa K v) / m,
-      // the element sums carrying weight |cell|/8 over the interior mass |cell|
-      const u64 own = kJVP ? Wp[c0] : sub2(Up[c0], Wp[c0]);
-      u64 g = fma2(own, bc(a.inv_dt), mul2(bc(0.125f * a.mob), acc));
-      if (a.unscaled) {
-        const float wx = (gx == 0 || gx == a.nx - 1) ? 0.5f : 1.0f;
-        const float wy = (gy == 0 || gy == a.ny - 1) ? 0.5f : 1.0f;
-        const float wz = (gz == 0 || gz == a.nz - 1) ? 0.5f : 1.0f;
-        g = mul2(g, bc(a.cell * wx * wy * wz));
-      }
-      const int64_t o = ((int64_t)gz * a.ny + gy) * a.nx + gx;
-      a.out[(2 * p) * N + o] = plo(g);
-      if (2 * p + 1 < NF) a.out[(2 * p + 1) * N + o] = phi(g);
-    }
-    __syncthreads();
-  }
-}
-
 // ---------------------------------------------------------------------------
-// J v on column tiles that sweep along z.  A block owns kSX x kSY output nodes
+// R and J v on column tiles that sweep along z.  A block owns kSX x kSY output nodes
 // in x, y and a chunk of kCZ node planes in z.  It walks the element layers
 // of its column from the one below the chunk to the last one inside it:
-//   - node plane z+1 of U and v (fields in pairs, the kSNX x kSNY nodes
+//   - node plane z+1 of U and v or U^n (fields in pairs, the kSNX x kSNY nodes
 //     around the tile, mirrored at the mesh boundary) enters a 3-plane ring
 //     in shared memory, pair index fastest, from registers loaded while the
 //     previous layer computed;
-//   - one thread per (element, field pair) interpolates U and v (with the
-//     gradient of v) at the 8 Gauss points from its 8 corners, and the G
-//     threads of an element (adjacent lanes, one per pair) sum S2 = sum_f U_f^2
-//     and T = sum_f U_f v_f by warp shuffles: every coupling of Eq. 14 is
-//     formed from one interpolation per field, with no second pass;
-//   - H v and the gradient term are weighted back to the corners: the 4 on
+//   - one thread per (element, field pair) interpolates U (and v for the JVP)
+//     at the 8 Gauss points from its 8 corners, with the gradient of the
+//     field the gradient term acts on, and the G threads of an element
+//     (adjacent lanes, one per pair) sum S2 = sum_f U_f^2 (and T =
+//     sum_f U_f v_f) by warp shuffles: every coupling of Eq. 13-14 is formed
+//     from one interpolation per field, with no second pass;
+//   - f' (or H v) and the gradient term are weighted back to the corners: the 4 on
 //     the layer's lower face into one buffer, the 4 on its upper face into a
 //     2-layer ring;
 //   - node plane z gathers its 8 element contributions (lower faces of layer
 //     z, upper faces of layer z-1) in the fixed corner order, adds the mass
-//     term and writes J v.
+//     term and writes R or J v.
 // Two block barriers per layer; no atomics, so results are bitwise repeatable.
-#ifndef PF_JVP_SX
-#define PF_JVP_SX 16
+#ifndef PF_SWEEP_SX
+#define PF_SWEEP_SX 16
 #endif
-#ifndef PF_JVP_SY
-#define PF_JVP_SY 8
+#ifndef PF_SWEEP_SY
+#define PF_SWEEP_SY 8
 #endif
-#ifndef PF_JVP_CZ
-#define PF_JVP_CZ 16
+#ifndef PF_SWEEP_CZ
+#define PF_SWEEP_CZ 16
 #endif
-#ifndef PF_JVP_MINB
-#define PF_JVP_MINB 1
+#ifndef PF_SWEEP_MINB
+#define PF_SWEEP_MINB 1
 #endif
-constexpr int kSX = PF_JVP_SX, kSY = PF_JVP_SY;  // output nodes per column tile in x, y
+constexpr int kSX = PF_SWEEP_SX, kSY = PF_SWEEP_SY;  // output nodes per column tile in x, y
 constexpr int kSNX = kSX + 2, kSNY = kSY + 2;    // staged nodes per plane
 constexpr int kSEX = kSX + 1, kSEY = kSY + 1;    // elements per layer touching the tile
 constexpr int kSPlane = kSNX * kSNY;
 constexpr int kSElems = kSEX * kSEY;
-constexpr int kCZ = PF_JVP_CZ;                   // output node planes per block
+constexpr int kCZ = PF_SWEEP_CZ;                   // output node planes per block
 
 template <int NP>
 struct SweepCfg {
@@ -422,15 +233,15 @@ struct SweepCfg {
   static constexpr size_t kSmem = sizeof(u64) * (size_t)NP * (2 * 3 * kSPlane + 4 * kSElems + 8 * kSElems);
 };
 
-template <int NF>
-__global__ void __launch_bounds__(SweepCfg<(NF + 1) / 2>::kThreads, PF_JVP_MINB)
-    k_jvp3d_sweep(const Implicit3DArgs a) {
+template <int NF, bool kJVP>
+__global__ void __launch_bounds__(SweepCfg<(NF + 1) / 2>::kThreads, PF_SWEEP_MINB)
+    k_implicit3d_sweep(const Implicit3DArgs a) {
   constexpr int NP = (NF + 1) / 2;
   constexpr int G = SweepCfg<NP>::G, kThreads = SweepCfg<NP>::kThreads;
   constexpr int kItems = SweepCfg<NP>::kItems;
   extern __shared__ u64 smem[];
   u64* sU = smem;                        // [3 planes][kSPlane nodes][NP]
-  u64* sW = sU + 3 * kSPlane * NP;       // v, same layout
+  u64* sW = sU + 3 * kSPlane * NP;       // v (JVP) or U^n (residual), same layout
   u64* sLow = sW + 3 * kSPlane * NP;     // [4 lower corners][kSElems][NP] of the current layer
   u64* sUp = sLow + 4 * kSElems * NP;    // [2 layers][4 upper corners][kSElems][NP]
 
@@ -499,51 +310,70 @@ __global__ void __launch_bounds__(SweepCfg<(NF + 1) / 2>::kThreads, PF_JVP_MINB)
     __syncthreads();
 
     {
+      // the gradient term acts on v (JVP) or on U (residual)
       u64 c[8], uq[8], vq[8], hq[8], out[8], gx[4], gy[4], gz[4];
 #pragma unroll
       for (int k = 0; k < 8; ++k)
         c[k] = sU[(((k >> 2) ? s1 : s0) * kSPlane + node0 + ((k >> 1) & 1) * kSNX + (k & 1)) * NP + pe];
-      interp3(c, uq);
+      if constexpr (kJVP) {
+        interp3(c, uq);
 #pragma unroll
-      for (int k = 0; k < 8; ++k)
-        c[k] = sW[(((k >> 2) ? s1 : s0) * kSPlane + node0 + ((k >> 1) & 1) * kSNX + (k & 1)) * NP + pe];
-      interp3_grad(c, vq, gx, gy, gz);
+        for (int k = 0; k < 8; ++k)
+          c[k] = sW[(((k >> 2) ? s1 : s0) * kSPlane + node0 + ((k >> 1) & 1) * kSNX + (k & 1)) * NP + pe];
+        interp3_grad(c, vq, gx, gy, gz);
+      } else {
+        interp3_grad(c, uq, gx, gy, gz);
+      }
       if (a.double_well) {
-        // f = W u^2 (1-u)^2:  f'' = 2W (1 - 6u + 6u^2)
+        // f = W u^2 (1-u)^2:  f' = 2W u (1-u)(1-2u),  f'' = 2W (1 - 6u + 6u^2)
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           const u64 u = uq[q];
-          const u64 f2 = fma2(bc(6.0f), sub2(mul2(u, u), u), bc(1.0f));
-          hq[q] = mul2(mul2(bc(a.dw2), f2), vq[q]);
+          if constexpr (kJVP) {
+            const u64 f2 = fma2(bc(6.0f), sub2(mul2(u, u), u), bc(1.0f));
+            hq[q] = mul2(mul2(bc(a.dw2), f2), vq[q]);
+          } else {
+            const u64 om = sub2(bc(1.0f), u);             // 1 - u
+            const u64 o2 = fma2(bc(-2.0f), u, bc(1.0f));  // 1 - 2u
+            hq[q] = mul2(mul2(bc(a.dw2), u), mul2(om, o2));
+          }
         }
       } else {
-        // Fan-Chen: (H v)_f = (-a + 2g S2 + (3b - 6g) u_f^2) v_f + 4g u_f T
+        // Fan-Chen: f'_f = u_f (-a + 2g S2 + (b - 2g) u_f^2)
+        //           (H v)_f = (-a + 2g S2 + (3b - 6g) u_f^2) v_f + 4g u_f T
         float s2[8], t[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          const u64 uu = mul2(uq[q], uq[q]), uv = mul2(uq[q], vq[q]);
+          const u64 uu = mul2(uq[q], uq[q]);
           s2[q] = p_el < NP ? plo(uu) + phi(uu) : 0.0f;
-          t[q] = p_el < NP ? plo(uv) + phi(uv) : 0.0f;
+          if constexpr (kJVP) {
+            const u64 uv = mul2(uq[q], vq[q]);
+            t[q] = p_el < NP ? plo(uv) + phi(uv) : 0.0f;
+          }
         }
         if constexpr (G >= 2) {
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
             s2[q] += __shfl_xor_sync(0xffffffffu, s2[q], 1);
-            t[q] += __shfl_xor_sync(0xffffffffu, t[q], 1);
+            if constexpr (kJVP) t[q] += __shfl_xor_sync(0xffffffffu, t[q], 1);
           }
         }
         if constexpr (G >= 4) {
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
             s2[q] += __shfl_xor_sync(0xffffffffu, s2[q], 2);
-            t[q] += __shfl_xor_sync(0xffffffffu, t[q], 2);
+            if constexpr (kJVP) t[q] += __shfl_xor_sync(0xffffffffu, t[q], 2);
           }
         }
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           const u64 u = uq[q];
-          hq[q] = fma2(fma2(bc(a.c3b6g), mul2(u, u), bc(fmaf(a.two_gamma, s2[q], -a.alpha))), vq[q],
-                       mul2(bc(a.four_gamma * t[q]), u));
+          const float base = fmaf(a.two_gamma, s2[q], -a.alpha);
+          if constexpr (kJVP)
+            hq[q] = fma2(fma2(bc(a.c3b6g), mul2(u, u), bc(base)), vq[q],
+                         mul2(bc(a.four_gamma * t[q]), u));
+          else
+            hq[q] = mul2(u, fma2(bc(a.cb2g), mul2(u, u), bc(base)));
         }
       }
       project3_grad(hq, gx, gy, gz, a.kg, out);
@@ -573,7 +403,10 @@ __global__ void __launch_bounds__(SweepCfg<(NF + 1) / 2>::kThreads, PF_JVP_MINB)
           const u64* src = (k >> 2) ? upp : sLow;
           acc = add2(acc, src[((k & 3) * kSElems + ey * kSEX + ex) * NP + p]);
         }
-        const u64 own = sW[(s0 * kSPlane + ly * kSNX + lx) * NP + p];
+        // G = (u - u^n)/dt + L (F + kappa K u) / m   or   v/dt + L (H v + kappa K v) / m,
+        // the element sums carrying weight |cell|/8 over the interior mass |cell|
+        const int c0 = (s0 * kSPlane + ly * kSNX + lx) * NP + p;
+        const u64 own = kJVP ? sW[c0] : sub2(sU[c0], sW[c0]);
         u64 g = fma2(own, bc(a.inv_dt), mul2(bc(0.125f * a.mob), acc));
         if (a.unscaled) {
           const float wx = (gx == 0 || gx == a.nx - 1) ? 0.5f : 1.0f;
@@ -589,61 +422,31 @@ __global__ void __launch_bounds__(SweepCfg<(NF + 1) / 2>::kThreads, PF_JVP_MINB)
   }
 }
 
-template <int NF>
+template <int NF, bool kJVP>
 cudaError_t launch_sweep_nf(const Implicit3DArgs& a, cudaStream_t s) {
   constexpr int NP = (NF + 1) / 2;
   constexpr size_t smem = SweepCfg<NP>::kSmem;
   static std::atomic<unsigned long long> raised{0};
-  const cudaError_t e = raise_smem_limit(k_jvp3d_sweep<NF>, (int)smem, raised);
+  const cudaError_t e = raise_smem_limit(k_implicit3d_sweep<NF, kJVP>, (int)smem, raised);
   if (e != cudaSuccess) return e;
   const int64_t blocks = (int64_t)((a.nx + kSX - 1) / kSX) * ((a.ny + kSY - 1) / kSY) *
                          ((a.nz + kCZ - 1) / kCZ);
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  k_jvp3d_sweep<NF><<<(unsigned)blocks, SweepCfg<NP>::kThreads, smem, s>>>(a);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_sweep_any(const Implicit3DArgs& a, cudaStream_t s) {
-  switch (a.nf) {
-    case 1: return launch_sweep_nf<1>(a, s);
-    case 2: return launch_sweep_nf<2>(a, s);
-    case 3: return launch_sweep_nf<3>(a, s);
-    case 4: return launch_sweep_nf<4>(a, s);
-    case 5: return launch_sweep_nf<5>(a, s);
-    case 6: return launch_sweep_nf<6>(a, s);
-    case 7: return launch_sweep_nf<7>(a, s);
-    case 8: return launch_sweep_nf<8>(a, s);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-template <int NF, bool kJVP>
-cudaError_t launch_nf(const Implicit3DArgs& a, cudaStream_t s) {
-  constexpr int kTZ = TileCfg<kJVP>::kTZ, kThreads = TileCfg<kJVP>::kThreads;
-  constexpr int kNodes = TileCfg<kJVP>::kNodes, kElems = TileCfg<kJVP>::kElems;
-  constexpr int NP = (NF + 1) / 2;
-  const size_t smem = sizeof(u64) * (2 * NP * kNodes + 8 * kElems) +
-                      sizeof(float) * kElems * 8 * (kJVP ? 2 : 1);
-  static std::atomic<unsigned long long> raised{0};
-  const cudaError_t e = raise_smem_limit(k_implicit3d<NF, kJVP>, (int)smem, raised);
-  if (e != cudaSuccess) return e;
-  const int tiles =
-      ((a.nx + kTX - 1) / kTX) * ((a.ny + kTY - 1) / kTY) * ((a.nz + kTZ - 1) / kTZ);
-  k_implicit3d<NF, kJVP><<<tiles, kThreads, smem, s>>>(a);
+  k_implicit3d_sweep<NF, kJVP><<<(unsigned)blocks, SweepCfg<NP>::kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 template <bool kJVP>
-cudaError_t launch_any(const Implicit3DArgs& a, cudaStream_t s) {
+cudaError_t launch_sweep_any(const Implicit3DArgs& a, cudaStream_t s) {
   switch (a.nf) {
-    case 1: return launch_nf<1, kJVP>(a, s);
-    case 2: return launch_nf<2, kJVP>(a, s);
-    case 3: return launch_nf<3, kJVP>(a, s);
-    case 4: return launch_nf<4, kJVP>(a, s);
-    case 5: return launch_nf<5, kJVP>(a, s);
-    case 6: return launch_nf<6, kJVP>(a, s);
-    case 7: return launch_nf<7, kJVP>(a, s);
-    case 8: return launch_nf<8, kJVP>(a, s);
+    case 1: return launch_sweep_nf<1, kJVP>(a, s);
+    case 2: return launch_sweep_nf<2, kJVP>(a, s);
+    case 3: return launch_sweep_nf<3, kJVP>(a, s);
+    case 4: return launch_sweep_nf<4, kJVP>(a, s);
+    case 5: return launch_sweep_nf<5, kJVP>(a, s);
+    case 6: return launch_sweep_nf<6, kJVP>(a, s);
+    case 7: return launch_sweep_nf<7, kJVP>(a, s);
+    case 8: return launch_sweep_nf<8, kJVP>(a, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -651,14 +454,9 @@ cudaError_t launch_any(const Implicit3DArgs& a, cudaStream_t s) {
 }  // namespace
 
 cudaError_t launch_residual3d(const Implicit3DArgs& a, cudaStream_t s) {
-  return launch_any<false>(a, s);
+  return launch_sweep_any<false>(a, s);
 }
 
-#ifndef PF_JVP_TILED
-#define PF_JVP_TILED 0
-#endif
-cudaError_t launch_jvp3d(const Implicit3DArgs& a, cudaStream_t s) {
-  return PF_JVP_TILED ? launch_any<true>(a, s) : launch_sweep_any(a, s);
-}
+cudaError_t launch_jvp3d(const Implicit3DArgs& a, cudaStream_t s) { return launch_sweep_any<true>(a, s); }
 
 }  // namespace pf
