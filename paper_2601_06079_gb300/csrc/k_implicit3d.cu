@@ -8,8 +8,8 @@
 // halves, so every node uses the interior formula (an optional final
 // multiplication by m_i gives R and J v themselves).
 //
-// Work split: a block owns a 16 x 8 node column in x, y and a chunk of 16
-// node planes in z, and sweeps its element layers along z (the kernel below
+// Work split: 16 x 8 node columns in x, y; one wave of resident blocks, each
+// sweeping an equal share of the column planes along z (the kernel below
 // describes the steps).  One thread per (element, field pair) forms the
 // trilinear Gauss values (sum-factorised), the pointwise f' or H v, and the
 // gradient term kappa grad w . grad N_a (w = U for the residual, v for the
@@ -27,6 +27,8 @@
 // every interpolation, pointwise term, projection and stencil runs on packed
 // FP32 pairs with the f32x2 instructions of sm_100+.
 // No atomics: the gather order is fixed, so results are bitwise repeatable.
+#include <algorithm>
+
 #include "pf_internal.h"
 
 namespace pf {
@@ -186,9 +188,11 @@ __device__ __forceinline__ void project3_grad(const u64 q[8], const u64 gx[4], c
 }
 
 // ---------------------------------------------------------------------------
-// R and J v on column tiles that sweep along z.  A block owns kSX x kSY output nodes
-// in x, y and a chunk of kCZ node planes in z.  It walks the element layers
-// of its column from the one below the chunk to the last one inside it:
+// R and J v on column tiles that sweep along z.  The column planes (kSX x kSY
+// output nodes of one node plane) are numbered column by column, and each
+// resident block takes an equal contiguous range of them: one or two
+// segments of a column.  Along a segment it walks the element layers from
+// the one below its first plane to the last one inside it:
 //   - node plane z+1 of U and v or U^n (fields in pairs, the kSNX x kSNY nodes
 //     around the tile, mirrored at the mesh boundary) enters a 3-plane ring
 //     in shared memory, pair index fastest, from registers loaded while the
@@ -212,9 +216,6 @@ __device__ __forceinline__ void project3_grad(const u64 q[8], const u64 gx[4], c
 #ifndef PF_SWEEP_SY
 #define PF_SWEEP_SY 8
 #endif
-#ifndef PF_SWEEP_CZ
-#define PF_SWEEP_CZ 16
-#endif
 #ifndef PF_SWEEP_MINB
 #define PF_SWEEP_MINB 1
 #endif
@@ -223,7 +224,6 @@ constexpr int kSNX = kSX + 2, kSNY = kSY + 2;    // staged nodes per plane
 constexpr int kSEX = kSX + 1, kSEY = kSY + 1;    // elements per layer touching the tile
 constexpr int kSPlane = kSNX * kSNY;
 constexpr int kSElems = kSEX * kSEY;
-constexpr int kCZ = PF_SWEEP_CZ;                   // output node planes per block
 
 template <int NP>
 struct SweepCfg {
@@ -246,18 +246,27 @@ __global__ void __launch_bounds__(SweepCfg<(NF + 1) / 2>::kThreads, PF_SWEEP_MIN
   u64* sUp = sLow + 4 * kSElems * NP;    // [2 layers][4 upper corners][kSElems][NP]
 
   const int tiles_x = (a.nx + kSX - 1) / kSX, tiles_y = (a.ny + kSY - 1) / kSY;
-  const int b = blockIdx.x;
-  const int x0 = (b % tiles_x) * kSX, y0 = ((b / tiles_x) % tiles_y) * kSY;
-  const int z0 = (b / (tiles_x * tiles_y)) * kCZ;
-  const int cz = min(kCZ, a.nz - z0);    // output planes z0 .. z0 + cz - 1
   const int64_t N = (int64_t)a.nx * a.ny * a.nz;
   const int64_t plane = (int64_t)a.nx * a.ny;
   const int tid = threadIdx.x;
+  // this block's share of the column planes (column-major: all planes of
+  // column 0, then column 1, ...), an equal contiguous range per block
+  const int64_t total = (int64_t)tiles_x * tiles_y * a.nz;
+  const int64_t g_end = total * (blockIdx.x + 1) / gridDim.x;
+  int64_t ioff[kItems];
+  int islot[kItems];
+  u64 pu[kItems], pw[kItems];
+  for (int64_t g = total * blockIdx.x / gridDim.x; g < g_end;) {
+  // one segment: column col, output planes z0 .. z0 + cz - 1
+  const int64_t col = g / a.nz;
+  const int z0 = (int)(g % a.nz);
+  const int cz = (int)min((int64_t)(a.nz - z0), g_end - g);
+  g += cz;
+  const int x0 = (int)(col % tiles_x) * kSX, y0 = (int)(col / tiles_x) * kSY;
+  __syncthreads();  // the last segment's gather has finished with the shared buffers
 
   // staged items of this thread: node (in the plane) and pair, as global
   // offsets within a plane and field offsets
-  int64_t ioff[kItems];
-  int islot[kItems];
 #pragma unroll
   for (int k = 0; k < kItems; ++k) {
     const int it = tid + k * kThreads;
@@ -267,7 +276,6 @@ __global__ void __launch_bounds__(SweepCfg<(NF + 1) / 2>::kThreads, PF_SWEEP_MIN
     const int gx = reflect(x0 - 1 + lx, a.nx), gy = reflect(y0 - 1 + ly, a.ny);
     ioff[k] = (int64_t)gy * a.nx + gx;
   }
-  u64 pu[kItems], pw[kItems];
   auto fetch = [&](int z) {  // plane z (mirrored) of this thread's items into registers
     const int64_t zo = (int64_t)reflect(z, a.nz) * plane;
 #pragma unroll
@@ -407,19 +415,20 @@ __global__ void __launch_bounds__(SweepCfg<(NF + 1) / 2>::kThreads, PF_SWEEP_MIN
         // the element sums carrying weight |cell|/8 over the interior mass |cell|
         const int c0 = (s0 * kSPlane + ly * kSNX + lx) * NP + p;
         const u64 own = kJVP ? sW[c0] : sub2(sU[c0], sW[c0]);
-        u64 g = fma2(own, bc(a.inv_dt), mul2(bc(0.125f * a.mob), acc));
+        u64 r = fma2(own, bc(a.inv_dt), mul2(bc(0.125f * a.mob), acc));
         if (a.unscaled) {
           const float wx = (gx == 0 || gx == a.nx - 1) ? 0.5f : 1.0f;
           const float wy = (gy == 0 || gy == a.ny - 1) ? 0.5f : 1.0f;
           const float wz = (gz == 0 || gz == a.nz - 1) ? 0.5f : 1.0f;
-          g = mul2(g, bc(a.cell * wx * wy * wz));
+          r = mul2(r, bc(a.cell * wx * wy * wz));
         }
         const int64_t o = (int64_t)gz * plane + (int64_t)gy * a.nx + gx;
-        a.out[(int64_t)(2 * p) * N + o] = plo(g);
-        if (2 * p + 1 < NF) a.out[(int64_t)(2 * p + 1) * N + o] = phi(g);
+        a.out[(int64_t)(2 * p) * N + o] = plo(r);
+        if (2 * p + 1 < NF) a.out[(int64_t)(2 * p + 1) * N + o] = phi(r);
       }
     }
   }
+  }  // segments
 }
 
 template <int NF, bool kJVP>
@@ -429,9 +438,18 @@ cudaError_t launch_sweep_nf(const Implicit3DArgs& a, cudaStream_t s) {
   static std::atomic<unsigned long long> raised{0};
   const cudaError_t e = raise_smem_limit(k_implicit3d_sweep<NF, kJVP>, (int)smem, raised);
   if (e != cudaSuccess) return e;
-  const int64_t blocks = (int64_t)((a.nx + kSX - 1) / kSX) * ((a.ny + kSY - 1) / kSY) *
-                         ((a.nz + kCZ - 1) / kCZ);
-  if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  // one wave of resident blocks, each sweeping an equal share of the column
+  // planes (no more blocks than column planes)
+  static std::atomic<int> per_sm{0};
+  if (per_sm.load() == 0) {
+    int n = 0;
+    const cudaError_t oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &n, k_implicit3d_sweep<NF, kJVP>, SweepCfg<NP>::kThreads, smem);
+    if (oe != cudaSuccess) return oe;
+    per_sm.store(n > 0 ? n : 1);
+  }
+  const int64_t planes = (int64_t)((a.nx + kSX - 1) / kSX) * ((a.ny + kSY - 1) / kSY) * a.nz;
+  const int64_t blocks = std::min<int64_t>(planes, (int64_t)per_sm.load() * device_sm_count());
   k_implicit3d_sweep<NF, kJVP><<<(unsigned)blocks, SweepCfg<NP>::kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
