@@ -30,42 +30,87 @@ __device__ double block_sum(double v, double* scratch) {
   return v;
 }
 
-// partials[b * k + j] = sum over block b's indices of V_j . w   (j < k <= kMaxBasis),
-// V_j = V + j * ldv; w is read once for all k products.  If w == nullptr the
-// squared norm of V_0 is taken (k must be 1).
-__global__ void __launch_bounds__(kThreads) k_dots(const float* __restrict__ V, int64_t ldv,
-                                                   int k, const float* __restrict__ w, int64_t n,
-                                                   double* __restrict__ partials) {
-  __shared__ double scratch[kThreads / 32];
-  const int64_t chunks = (n + kChunk - 1) / kChunk;
-  double acc[kMaxBasis];
+// Chunks of kChunk = 8 consecutive values: two 16-byte loads when the vectors
+// are 16-byte aligned (kVec) and the chunk is whole, elementwise otherwise
+// (values past n read as 0).  Each kernel below is instantiated for a bound
+// KMAX on the number of basis vectors (4, 8, 16, 32), so that its FP64
+// accumulators take registers only for the vectors a call can have.
+template <bool kVec>
+__device__ __forceinline__ void load8(const float* __restrict__ p, int64_t i0, int64_t n,
+                                      float v[kChunk]) {
+  if (kVec && i0 + kChunk <= n) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(p + i0));
+    const float4 b = __ldg(reinterpret_cast<const float4*>(p + i0 + 4));
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  } else {
 #pragma unroll
-  for (int j = 0; j < kMaxBasis; ++j) acc[j] = 0.0;
-  for (int64_t c = (int64_t)blockIdx.x * kThreads + threadIdx.x; c < chunks;
-       c += (int64_t)gridDim.x * kThreads) {
-    const int64_t i0 = c * kChunk;
-    float u[kChunk];
-#pragma unroll
-    for (int t = 0; t < kChunk; ++t) u[t] = (i0 + t < n) ? (w ? w[i0 + t] : V[i0 + t]) : 0.0f;
-#pragma unroll
-    for (int j = 0; j < kMaxBasis; ++j) {
-      if (j < k) {
-        const float* v = V + j * ldv + i0;
-        float s = 0.0f;
-#pragma unroll
-        for (int t = 0; t < kChunk; ++t)
-          if (i0 + t < n) s = fmaf(v[t], u[t], s);
-        acc[j] += (double)s;
-      }
-    }
+    for (int t = 0; t < kChunk; ++t) v[t] = (i0 + t < n) ? p[i0 + t] : 0.0f;
   }
+}
+
+template <bool kVec>
+__device__ __forceinline__ void store8(float* __restrict__ p, int64_t i0, int64_t n,
+                                       const float v[kChunk]) {
+  if (kVec && i0 + kChunk <= n) {
+    *reinterpret_cast<float4*>(p + i0) = make_float4(v[0], v[1], v[2], v[3]);
+    *reinterpret_cast<float4*>(p + i0 + 4) = make_float4(v[4], v[5], v[6], v[7]);
+  } else {
 #pragma unroll
-  for (int j = 0; j < kMaxBasis; ++j) {
+    for (int t = 0; t < kChunk; ++t)
+      if (i0 + t < n) p[i0 + t] = v[t];
+  }
+}
+
+// FP32 run of the chunk's products u[t] v[t], t in order (values past n skipped)
+__device__ __forceinline__ float chunk_dot(const float v[kChunk], const float u[kChunk],
+                                           int64_t i0, int64_t n) {
+  float s = 0.0f;
+#pragma unroll
+  for (int t = 0; t < kChunk; ++t)
+    if (i0 + t < n) s = fmaf(v[t], u[t], s);
+  return s;
+}
+
+template <int KMAX>
+__device__ __forceinline__ void write_partials(double (&acc)[KMAX], int k, double* scratch,
+                                               double* __restrict__ partials) {
+#pragma unroll
+  for (int j = 0; j < KMAX; ++j) {
     if (j < k) {
       const double r = block_sum(acc[j], scratch);
       if (threadIdx.x == 0) partials[blockIdx.x * k + j] = r;
     }
   }
+}
+
+// partials[b * k + j] = sum over block b's indices of V_j . w   (j < k <= KMAX),
+// V_j = V + j * ldv; w is read once for all k products.  If w == nullptr the
+// squared norm of V_0 is taken (k must be 1).
+template <int KMAX, bool kVec>
+__global__ void __launch_bounds__(kThreads) k_dots(const float* __restrict__ V, int64_t ldv,
+                                                   int k, const float* __restrict__ w, int64_t n,
+                                                   double* __restrict__ partials) {
+  __shared__ double scratch[kThreads / 32];
+  const int64_t chunks = (n + kChunk - 1) / kChunk;
+  double acc[KMAX];
+#pragma unroll
+  for (int j = 0; j < KMAX; ++j) acc[j] = 0.0;
+  for (int64_t c = (int64_t)blockIdx.x * kThreads + threadIdx.x; c < chunks;
+       c += (int64_t)gridDim.x * kThreads) {
+    const int64_t i0 = c * kChunk;
+    float u[kChunk];
+    load8<kVec>(w ? w : V, i0, n, u);
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j) {
+      if (j < k) {
+        float v[kChunk];
+        load8<kVec>(V + j * ldv, i0, n, v);
+        acc[j] += (double)chunk_dot(v, u, i0, n);
+      }
+    }
+  }
+  write_partials<KMAX>(acc, k, scratch, partials);
 }
 
 // out[j] = sum_b partials[b * k + j], fixed order
@@ -80,13 +125,30 @@ __global__ void k_sum_partials_cols(const double* __restrict__ partials, int nbl
   }
 }
 
+// x <- x - sum_j cf[j] V_j over one chunk, j in order for every element
+template <int KMAX, bool kVec>
+__device__ __forceinline__ void chunk_update(const float* __restrict__ V, int64_t ldv, int k,
+                                             const float* cf, int64_t i0, int64_t n,
+                                             float x[kChunk]) {
+#pragma unroll
+  for (int j = 0; j < KMAX; ++j) {
+    if (j < k) {
+      float v[kChunk];
+      load8<kVec>(V + j * ldv, i0, n, v);
+#pragma unroll
+      for (int t = 0; t < kChunk; ++t) x[t] = fmaf(-cf[j], v[t], x[t]);
+    }
+  }
+}
+
 // w <- w - sum_j coef[j] V_j (coef: device FP64);  optionally partials of |w|^2
+template <int KMAX, bool kVec>
 __global__ void __launch_bounds__(kThreads) k_update(const float* __restrict__ V, int64_t ldv,
                                                      int k, const double* __restrict__ coef,
                                                      float* __restrict__ w, int64_t n,
                                                      double* __restrict__ norm_partials) {
   __shared__ double scratch[kThreads / 32];
-  __shared__ float cf[kMaxBasis];
+  __shared__ float cf[KMAX];
   for (int j = threadIdx.x; j < k; j += kThreads) cf[j] = (float)coef[j];
   __syncthreads();
   const int64_t chunks = (n + kChunk - 1) / kChunk;
@@ -94,23 +156,54 @@ __global__ void __launch_bounds__(kThreads) k_update(const float* __restrict__ V
   for (int64_t c = (int64_t)blockIdx.x * kThreads + threadIdx.x; c < chunks;
        c += (int64_t)gridDim.x * kThreads) {
     const int64_t i0 = c * kChunk;
-    float s = 0.0f;
-#pragma unroll
-    for (int t = 0; t < kChunk; ++t) {
-      const int64_t i = i0 + t;
-      if (i < n) {
-        float x = w[i];
-        for (int j = 0; j < k; ++j) x = fmaf(-cf[j], V[j * ldv + i], x);
-        w[i] = x;
-        s = fmaf(x, x, s);
-      }
-    }
-    acc += (double)s;
+    float x[kChunk];
+    load8<kVec>(w, i0, n, x);
+    chunk_update<KMAX, kVec>(V, ldv, k, cf, i0, n, x);
+    store8<kVec>(w, i0, n, x);
+    acc += (double)chunk_dot(x, x, i0, n);
   }
   if (norm_partials) {
     acc = block_sum(acc, scratch);
     if (threadIdx.x == 0) norm_partials[blockIdx.x] = acc;
   }
+}
+
+// w <- w - sum_j coef[j] V_j, and partials[b * k + j] of V_j . w for the
+// updated w: the two halves of a CGS2 pass boundary (the first pass's update
+// and the second pass's inner products) in one pass over V and w.  Each
+// element's arithmetic and each thread's chunks are those of k_update
+// followed by k_dots, so the results are identical to the two kernels.
+template <int KMAX, bool kVec>
+__global__ void __launch_bounds__(kThreads) k_update_dots(const float* __restrict__ V,
+                                                          int64_t ldv, int k,
+                                                          const double* __restrict__ coef,
+                                                          float* __restrict__ w, int64_t n,
+                                                          double* __restrict__ partials) {
+  __shared__ double scratch[kThreads / 32];
+  __shared__ float cf[KMAX];
+  for (int j = threadIdx.x; j < k; j += kThreads) cf[j] = (float)coef[j];
+  __syncthreads();
+  const int64_t chunks = (n + kChunk - 1) / kChunk;
+  double acc[KMAX];
+#pragma unroll
+  for (int j = 0; j < KMAX; ++j) acc[j] = 0.0;
+  for (int64_t c = (int64_t)blockIdx.x * kThreads + threadIdx.x; c < chunks;
+       c += (int64_t)gridDim.x * kThreads) {
+    const int64_t i0 = c * kChunk;
+    float x[kChunk];
+    load8<kVec>(w, i0, n, x);
+    chunk_update<KMAX, kVec>(V, ldv, k, cf, i0, n, x);
+    store8<kVec>(w, i0, n, x);
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j) {
+      if (j < k) {
+        float v[kChunk];
+        load8<kVec>(V + j * ldv, i0, n, v);
+        acc[j] += (double)chunk_dot(v, x, i0, n);
+      }
+    }
+  }
+  write_partials<KMAX>(acc, k, scratch, partials);
 }
 
 // y <- a * x + b * y  (host scalars)
@@ -195,17 +288,71 @@ unsigned elementwise_blocks(int64_t n) {
 // never changes between calls on one device.
 int krylov_partial_blocks() { return 3 * device_sm_count(); }
 
+namespace {
+// 16-byte loads when every vector the call touches starts on a 16-byte boundary
+bool vec_ok(const void* a, const void* b, int64_t ldv) {
+  return ((uintptr_t)a % 16 == 0) && ((uintptr_t)b % 16 == 0) && (ldv % 4 == 0);
+}
+
+// calls K<KMAX, kVec> for the smallest KMAX in {4, 8, 16, 32} holding k
+template <template <int, bool> class K, typename... A>
+cudaError_t dispatch_k(int k, bool vec, cudaStream_t s, A... args) {
+  const dim3 g(krylov_partial_blocks()), b(kThreads);
+#define PF_KRYLOV_CASE(M)                                            \
+  if (k <= M) {                                                      \
+    if (vec) K<M, true>::launch(g, b, s, args...);                   \
+    else K<M, false>::launch(g, b, s, args...);                      \
+    return cudaGetLastError();                                       \
+  }
+  PF_KRYLOV_CASE(4)
+  PF_KRYLOV_CASE(8)
+  PF_KRYLOV_CASE(16)
+  PF_KRYLOV_CASE(kMaxBasis)
+#undef PF_KRYLOV_CASE
+  return cudaErrorInvalidValue;
+}
+
+template <int M, bool V>
+struct Dots {
+  template <typename... A>
+  static void launch(dim3 g, dim3 b, cudaStream_t s, A... a) { k_dots<M, V><<<g, b, 0, s>>>(a...); }
+};
+template <int M, bool V>
+struct Update {
+  template <typename... A>
+  static void launch(dim3 g, dim3 b, cudaStream_t s, A... a) { k_update<M, V><<<g, b, 0, s>>>(a...); }
+};
+template <int M, bool V>
+struct UpdateDots {
+  template <typename... A>
+  static void launch(dim3 g, dim3 b, cudaStream_t s, A... a) {
+    k_update_dots<M, V><<<g, b, 0, s>>>(a...);
+  }
+};
+}  // namespace
+
 cudaError_t launch_dots(const float* V, int64_t ldv, int k, const float* w, int64_t n,
                         double* partials, double* out, cudaStream_t s) {
-  k_dots<<<krylov_partial_blocks(), kThreads, 0, s>>>(V, ldv, k, w, n, partials);
+  cudaError_t e = dispatch_k<Dots>(k, vec_ok(V, w ? w : V, ldv), s, V, ldv, k, w, n, partials);
+  if (e != cudaSuccess) return e;
   k_sum_partials_cols<<<1, kThreads, 0, s>>>(partials, krylov_partial_blocks(), k, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_update(const float* V, int64_t ldv, int k, const double* coef, float* w,
                           int64_t n, double* partials, double* norm_out, cudaStream_t s) {
-  k_update<<<krylov_partial_blocks(), kThreads, 0, s>>>(V, ldv, k, coef, w, n, norm_out ? partials : nullptr);
+  cudaError_t e = dispatch_k<Update>(k, vec_ok(V, w, ldv), s, V, ldv, k, coef, w, n,
+                                     norm_out ? partials : (double*)nullptr);
+  if (e != cudaSuccess) return e;
   if (norm_out) k_sum_partials_cols<<<1, kThreads, 0, s>>>(partials, krylov_partial_blocks(), 1, norm_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_dots(const float* V, int64_t ldv, int k, const double* coef, float* w,
+                               int64_t n, double* partials, double* out, cudaStream_t s) {
+  cudaError_t e = dispatch_k<UpdateDots>(k, vec_ok(V, w, ldv), s, V, ldv, k, coef, w, n, partials);
+  if (e != cudaSuccess) return e;
+  k_sum_partials_cols<<<1, kThreads, 0, s>>>(partials, krylov_partial_blocks(), k, out);
   return cudaGetLastError();
 }
 

@@ -482,8 +482,7 @@ pf_status gmres3d(pf_ctx* c, int m, int maxit, double rtol, double atol, int* it
       float* vk1 = V + (int64_t)(k + 1) * ldv;
       PF_CUDA(jvp3d(c, c->u, V + (int64_t)k * ldv, vk1, 0));
       PF_CUDA(pf::launch_dots(V, ldv, k + 1, vk1, n, c->partials, dh1, c->stream));
-      PF_CUDA(pf::launch_update(V, ldv, k + 1, dh1, vk1, n, c->partials, nullptr, c->stream));
-      PF_CUDA(pf::launch_dots(V, ldv, k + 1, vk1, n, c->partials, dh2, c->stream));
+      PF_CUDA(pf::launch_update_dots(V, ldv, k + 1, dh1, vk1, n, c->partials, dh2, c->stream));
       PF_CUDA(pf::launch_update(V, ldv, k + 1, dh2, vk1, n, c->partials, dnrm, c->stream));
       PF_CUDA(cudaMemcpyAsync(host, c->small, sizeof(double) * (2 * pf::kMaxBasis + 1),
                               cudaMemcpyDeviceToHost, c->stream));

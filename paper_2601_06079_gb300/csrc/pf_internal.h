@@ -260,6 +260,10 @@ cudaError_t launch_dots(const float* V, int64_t ldv, int k, const float* w, int6
                         double* partials, double* out, cudaStream_t s);
 cudaError_t launch_update(const float* V, int64_t ldv, int k, const double* coef, float* w,
                           int64_t n, double* partials, double* norm_out, cudaStream_t s);
+// w <- w - sum_j coef[j] V_j, then out[j] = V_j . w (j < k) for the updated w,
+// in one pass (results identical to launch_update followed by launch_dots)
+cudaError_t launch_update_dots(const float* V, int64_t ldv, int k, const double* coef, float* w,
+                               int64_t n, double* partials, double* out, cudaStream_t s);
 cudaError_t launch_axpby(float a, const float* x, float b, float* y, int64_t n, cudaStream_t s);
 cudaError_t launch_mass_mul(const float* in, float* out, int nx, int ny, int nz, int nf,
                             double cell, float a, int inverse, cudaStream_t s);
