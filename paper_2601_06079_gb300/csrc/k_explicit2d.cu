@@ -476,23 +476,28 @@ __global__ void k_barrier_selftest(unsigned* bar, long long limit, int extra) {
 }
 
 // all instances' plain states (packed) <-> their padded working planes
-// (grid.y strides over the instances, so any count fits in one launch)
+// (grid.y strides over the instances, so any count fits in one launch; blocks
+// stride over rows and threads over columns, so no index is divided)
 __global__ void k_ens_to_work(const float* __restrict__ packed, const int64_t* __restrict__ off,
                               const Explicit2DArgs* inst, int count, float sub) {
   for (int k = blockIdx.y; k < count; k += gridDim.y) {
     const Explicit2DArgs& a = inst[k];
     const int nx = a.nx, ny = a.ny;
-    const int64_t pitch = a.pitch, n = pitch * (int64_t)a.rows;
+    const int64_t pitch = a.pitch;
     const float* in = packed + off[k];
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-      const int u = (int)(i % pitch), v = (int)(i / pitch);
-      const int x = u - kGhost, y = v - kGhost;
-      float val = 0.0f;
-      if (x >= -kGhost && x < nx + kGhost && y >= -kGhost && y < ny + kGhost)
-        val = in[(int64_t)reflect_row(y, ny) * nx + reflect_col(x, nx)] - sub;
-      const_cast<float*>(a.in)[i] = val;
-      a.out[i] = val;
+    for (int v = blockIdx.x; v < a.rows; v += gridDim.x) {
+      const int y = v - kGhost;
+      const bool row = y >= -kGhost && y < ny + kGhost;
+      const int64_t src = (int64_t)reflect_row(y, ny) * nx;
+      float* dA = const_cast<float*>(a.in) + v * pitch;
+      float* dB = a.out + v * pitch;
+      for (int u = threadIdx.x; u < pitch; u += blockDim.x) {
+        const int x = u - kGhost;
+        float val = 0.0f;
+        if (row && x >= -kGhost && x < nx + kGhost) val = in[src + reflect_col(x, nx)] - sub;
+        dA[u] = val;
+        dB[u] = val;
+      }
     }
   }
 }
@@ -502,41 +507,42 @@ __global__ void k_ens_from_work(float* __restrict__ packed, const int64_t* __res
   for (int k = blockIdx.y; k < count; k += gridDim.y) {
     const Explicit2DArgs& a = inst[k];
     const int nx = a.nx;
-    const int64_t n = (int64_t)nx * a.ny;
     const float* work = parity ? a.out : a.in;
     float* out = packed + off[k];
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-      const int x = (int)(i % nx), y = (int)(i / nx);
-      out[i] = work[(int64_t)(y + kGhost) * a.pitch + x + kGhost] + add;
+    for (int y = blockIdx.x; y < a.ny; y += gridDim.x) {
+      const float* src = work + (int64_t)(y + kGhost) * a.pitch + kGhost;
+      float* dst = out + (int64_t)y * nx;
+      for (int x = threadIdx.x; x < nx; x += blockDim.x) dst[x] = src[x] + add;
     }
   }
 }
 
 // Plain <-> padded working layout.  Working cell (u, v) holds real node
 // (reflect(u - kGhost), reflect(v - kGhost)) minus/plus the shift; padding
-// beyond the ghost frame is zero.
+// beyond the ghost frame is zero.  Blocks stride over rows, threads over
+// columns.
 __global__ void k_to_work(const float* __restrict__ in, float* __restrict__ work, int nx, int ny,
                           int64_t pitch, int rows, float sub) {
-  const int64_t n = pitch * rows;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const int u = (int)(i % pitch), v = (int)(i / pitch);
-    const int x = u - kGhost, y = v - kGhost;
-    float val = 0.0f;
-    if (x >= -kGhost && x < nx + kGhost && y >= -kGhost && y < ny + kGhost)
-      val = in[(int64_t)reflect_row(y, ny) * nx + reflect_col(x, nx)] - sub;
-    work[i] = val;
+  for (int v = blockIdx.x; v < rows; v += gridDim.x) {
+    const int y = v - kGhost;
+    const bool row = y >= -kGhost && y < ny + kGhost;
+    const int64_t src = (int64_t)reflect_row(y, ny) * nx;
+    float* dst = work + v * pitch;
+    for (int u = threadIdx.x; u < pitch; u += blockDim.x) {
+      const int x = u - kGhost;
+      float val = 0.0f;
+      if (row && x >= -kGhost && x < nx + kGhost) val = in[src + reflect_col(x, nx)] - sub;
+      dst[u] = val;
+    }
   }
 }
 
 __global__ void k_from_work(const float* __restrict__ work, float* __restrict__ out, int nx,
                             int ny, int64_t pitch, float add) {
-  const int64_t n = (int64_t)nx * ny;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const int x = (int)(i % nx), y = (int)(i / nx);
-    out[i] = work[(int64_t)(y + kGhost) * pitch + x + kGhost] + add;
+  for (int y = blockIdx.x; y < ny; y += gridDim.x) {
+    const float* src = work + (int64_t)(y + kGhost) * pitch + kGhost;
+    float* dst = out + (int64_t)y * nx;
+    for (int x = threadIdx.x; x < nx; x += blockDim.x) dst[x] = src[x] + add;
   }
 }
 
@@ -687,8 +693,7 @@ int work_rows(int ny) {
 
 cudaError_t launch_to_work(const float* in, float* work, int nx, int ny, float shift,
                            cudaStream_t s) {
-  const int64_t n = (int64_t)work_pitch(nx) * work_rows(ny);
-  int64_t blocks = (n + 255) / 256;
+  int64_t blocks = work_rows(ny);
   if (blocks > 16 * (int64_t)device_sm_count()) blocks = 16 * (int64_t)device_sm_count();
   k_to_work<<<(unsigned)blocks, 256, 0, s>>>(in, work, nx, ny, work_pitch(nx), work_rows(ny),
                                              shift);
@@ -697,8 +702,7 @@ cudaError_t launch_to_work(const float* in, float* work, int nx, int ny, float s
 
 cudaError_t launch_from_work(const float* work, float* out, int nx, int ny, float shift,
                              cudaStream_t s) {
-  const int64_t n = (int64_t)nx * ny;
-  int64_t blocks = (n + 255) / 256;
+  int64_t blocks = ny;
   if (blocks > 16 * (int64_t)device_sm_count()) blocks = 16 * (int64_t)device_sm_count();
   k_from_work<<<(unsigned)blocks, 256, 0, s>>>(work, out, nx, ny, work_pitch(nx), shift);
   return cudaGetLastError();

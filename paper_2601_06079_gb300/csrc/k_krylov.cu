@@ -11,6 +11,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kChunk = 8;      // products per FP32 partial sum
+constexpr int kMaxFields = 8;  // order parameters of a Newton vector (planes of the mass norm)
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -28,6 +29,28 @@ __device__ double block_sum(double v, double* scratch) {
   v = (threadIdx.x < kThreads / 32) ? scratch[threadIdx.x] : 0.0;
   if (w == 0) v = warp_sum(v);
   return v;
+}
+
+// The last block to finish sums all blocks' partials[b * k + j] into out[j]
+// in the fixed order of a separate single-block pass (b ascending per thread,
+// then the block sum), so one launch gives the final, repeatable values.
+// count: device counter, 0 before the launch and reset to 0 by the last block.
+__device__ void finish_sum(const double* partials, int k, double* __restrict__ out,
+                           unsigned* count, double* scratch) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(count, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int j = 0; j < k; ++j) {
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += kThreads) acc += __ldcg(partials + b * k + j);
+    acc = block_sum(acc, scratch);
+    if (threadIdx.x == 0) out[j] = acc;
+  }
+  if (threadIdx.x == 0) *count = 0;
 }
 
 // Chunks of kChunk = 8 consecutive values: two 16-byte loads when the vectors
@@ -74,7 +97,7 @@ __device__ __forceinline__ float chunk_dot(const float v[kChunk], const float u[
 
 template <int KMAX>
 __device__ __forceinline__ void write_partials(double (&acc)[KMAX], int k, double* scratch,
-                                               double* __restrict__ partials) {
+                                               double* partials, double* out, unsigned* count) {
 #pragma unroll
   for (int j = 0; j < KMAX; ++j) {
     if (j < k) {
@@ -82,15 +105,17 @@ __device__ __forceinline__ void write_partials(double (&acc)[KMAX], int k, doubl
       if (threadIdx.x == 0) partials[blockIdx.x * k + j] = r;
     }
   }
+  finish_sum(partials, k, out, count, scratch);
 }
 
-// partials[b * k + j] = sum over block b's indices of V_j . w   (j < k <= KMAX),
-// V_j = V + j * ldv; w is read once for all k products.  If w == nullptr the
-// squared norm of V_0 is taken (k must be 1).
+// out[j] = V_j . w (j < k <= KMAX), V_j = V + j * ldv; w is read once for all
+// k products (per-block partials in `partials`).  If w == nullptr the squared
+// norm of V_0 is taken (k must be 1).
 template <int KMAX, bool kVec>
 __global__ void __launch_bounds__(kThreads) k_dots(const float* __restrict__ V, int64_t ldv,
                                                    int k, const float* __restrict__ w, int64_t n,
-                                                   double* __restrict__ partials) {
+                                                   double* partials, double* out,
+                                                   unsigned* count) {
   __shared__ double scratch[kThreads / 32];
   const int64_t chunks = (n + kChunk - 1) / kChunk;
   double acc[KMAX];
@@ -110,19 +135,7 @@ __global__ void __launch_bounds__(kThreads) k_dots(const float* __restrict__ V, 
       }
     }
   }
-  write_partials<KMAX>(acc, k, scratch, partials);
-}
-
-// out[j] = sum_b partials[b * k + j], fixed order
-__global__ void k_sum_partials_cols(const double* __restrict__ partials, int nblocks, int k,
-                                    double* __restrict__ out) {
-  __shared__ double scratch[kThreads / 32];
-  for (int j = 0; j < k; ++j) {
-    double acc = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += kThreads) acc += partials[b * k + j];
-    acc = block_sum(acc, scratch);
-    if (threadIdx.x == 0) out[j] = acc;
-  }
+  write_partials<KMAX>(acc, k, scratch, partials, out, count);
 }
 
 // x <- x - sum_j cf[j] V_j over one chunk, j in order for every element
@@ -141,12 +154,13 @@ __device__ __forceinline__ void chunk_update(const float* __restrict__ V, int64_
   }
 }
 
-// w <- w - sum_j coef[j] V_j (coef: device FP64);  optionally partials of |w|^2
+// w <- w - sum_j coef[j] V_j (coef: device FP64);  optionally (norm_out) |w|^2
 template <int KMAX, bool kVec>
 __global__ void __launch_bounds__(kThreads) k_update(const float* __restrict__ V, int64_t ldv,
                                                      int k, const double* __restrict__ coef,
                                                      float* __restrict__ w, int64_t n,
-                                                     double* __restrict__ norm_partials) {
+                                                     double* partials, double* norm_out,
+                                                     unsigned* count) {
   __shared__ double scratch[kThreads / 32];
   __shared__ float cf[KMAX];
   for (int j = threadIdx.x; j < k; j += kThreads) cf[j] = (float)coef[j];
@@ -162,9 +176,10 @@ __global__ void __launch_bounds__(kThreads) k_update(const float* __restrict__ V
     store8<kVec>(w, i0, n, x);
     acc += (double)chunk_dot(x, x, i0, n);
   }
-  if (norm_partials) {
+  if (norm_out) {
     acc = block_sum(acc, scratch);
-    if (threadIdx.x == 0) norm_partials[blockIdx.x] = acc;
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+    finish_sum(partials, 1, norm_out, count, scratch);
   }
 }
 
@@ -178,7 +193,8 @@ __global__ void __launch_bounds__(kThreads) k_update_dots(const float* __restric
                                                           int64_t ldv, int k,
                                                           const double* __restrict__ coef,
                                                           float* __restrict__ w, int64_t n,
-                                                          double* __restrict__ partials) {
+                                                          double* partials, double* out,
+                                                          unsigned* count) {
   __shared__ double scratch[kThreads / 32];
   __shared__ float cf[KMAX];
   for (int j = threadIdx.x; j < k; j += kThreads) cf[j] = (float)coef[j];
@@ -203,32 +219,52 @@ __global__ void __launch_bounds__(kThreads) k_update_dots(const float* __restric
       }
     }
   }
-  write_partials<KMAX>(acc, k, scratch, partials);
+  write_partials<KMAX>(acc, k, scratch, partials, out, count);
 }
 
-// y <- a * x + b * y  (host scalars)
+// y <- a * x + b * y  (host scalars), chunks of 8
+template <bool kVec>
 __global__ void k_axpby(float a, const float* __restrict__ x, float b, float* __restrict__ y,
                         int64_t n) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    y[i] = fmaf(a, x[i], b * y[i]);
-}
-
-// x <- x + sum_j y_j V_j
-__global__ void k_lincomb(const float* __restrict__ V, int64_t ldv, int k, LinComb y,
-                          float* __restrict__ x, int64_t n) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    float s = x[i];
-    for (int j = 0; j < k; ++j) s = fmaf(y.c[j], V[j * ldv + i], s);
-    x[i] = s;
+  const int64_t chunks = (n + kChunk - 1) / kChunk;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < chunks;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i0 = c * kChunk;
+    float u[kChunk], v[kChunk];
+    load8<kVec>(x, i0, n, u);
+    load8<kVec>(y, i0, n, v);
+#pragma unroll
+    for (int t = 0; t < kChunk; ++t) v[t] = fmaf(a, u[t], b * v[t]);
+    store8<kVec>(y, i0, n, v);
   }
 }
 
-// lumped-mass boundary factor of a node: 1/2 per axis on which it is an end
-// node (nz = 1 is a 2-D mesh); node < 2^31 (the mesh limit)
-__device__ __forceinline__ float mass_factor(int node, int nx, int ny, int nz) {
-  const int x = node % nx, y = (node / nx) % ny, z = node / (nx * ny);
+// x <- x + sum_j y_j V_j, j in order for every element, chunks of 8
+template <int KMAX, bool kVec>
+__global__ void k_lincomb(const float* __restrict__ V, int64_t ldv, int k, LinComb y,
+                          float* __restrict__ x, int64_t n) {
+  const int64_t chunks = (n + kChunk - 1) / kChunk;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < chunks;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i0 = c * kChunk;
+    float s[kChunk];
+    load8<kVec>(x, i0, n, s);
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j) {
+      if (j < k) {
+        float v[kChunk];
+        load8<kVec>(V + j * ldv, i0, n, v);
+#pragma unroll
+        for (int t = 0; t < kChunk; ++t) s[t] = fmaf(y.c[j], v[t], s[t]);
+      }
+    }
+    store8<kVec>(x, i0, n, s);
+  }
+}
+
+// lumped-mass boundary factor: 1/2 per axis on which the node is an end node
+// (nz = 1 is a 2-D mesh)
+__device__ __forceinline__ float mass_factor(int x, int y, int z, int nx, int ny, int nz) {
   float m = 1.0f;
   if (x == 0 || x == nx - 1) m *= 0.5f;
   if (y == 0 || y == ny - 1) m *= 0.5f;
@@ -236,32 +272,79 @@ __device__ __forceinline__ float mass_factor(int node, int nx, int ny, int nz) {
   return m;
 }
 
-// partials of sum_i (m_i g_i)^2 over all fields: m_i = cell * boundary
-// factor.  Products in FP32 (GB300's FP64 rate is a small fraction of its
-// FP32 rate), runs of 16 squares in FP32, the runs and the block sum in FP64.
+// sum_i (m_i g_i)^2 over all fields into out[0]: m_i = cell * boundary factor.
+// Each thread takes chunks of 4 consecutive nodes (one index division per
+// chunk; kVec: one 16-byte load per field when the node count is a multiple
+// of 4).  Products in FP32 (GB300's FP64 rate is a small fraction of its FP32
+// rate), runs of 16 squares in FP32, the runs and the block sums in FP64.
+template <bool kVec>
 __global__ void __launch_bounds__(kThreads) k_mass_norm(const float* __restrict__ g, int nx,
                                                         int ny, int nz, int nf, float cell,
-                                                        double* __restrict__ partials) {
+                                                        double* partials, double* out,
+                                                        unsigned* count) {
   __shared__ double scratch[kThreads / 32];
-  const int N = nx * ny * nz;
+  const int64_t N = (int64_t)nx * ny * nz;
+  const int64_t chunks = (N + 3) / 4;
   double acc = 0.0;
   float run = 0.0f;
-  int k = 0;
-  for (int node = blockIdx.x * kThreads + threadIdx.x; node < N; node += gridDim.x * kThreads) {
-    const float m = cell * mass_factor(node, nx, ny, nz);
-    for (int f = 0; f < nf; ++f) {
-      const float v = m * g[(int64_t)f * N + node];
-      run = fmaf(v, v, run);
-      if (++k == 16) {
-        acc += (double)run;
-        run = 0.0f;
-        k = 0;
+  int kr = 0;
+  for (int64_t c = (int64_t)blockIdx.x * kThreads + threadIdx.x; c < chunks;
+       c += (int64_t)gridDim.x * kThreads) {
+    const int64_t i0 = 4 * c;
+    // node coordinates in 32-bit arithmetic (nodes < 2^31): a 64-bit integer
+    // division runs on the FP64 pipe, a small fraction of GB300's FP32 rate
+    const int node0 = (int)i0;
+    int x = node0 % nx;
+    const int r = node0 / nx;
+    int y = r % ny, z = r / ny;
+    float m[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      m[t] = (i0 + t < N) ? cell * mass_factor(x, y, z, nx, ny, nz) : 0.0f;
+      if (++x == nx) {
+        x = 0;
+        if (++y == ny) {
+          y = 0;
+          ++z;
+        }
+      }
+    }
+    // every field's chunk is loaded before any is used, so the loads of up
+    // to kMaxFields planes are in flight together
+    float v[kMaxFields][4];
+#pragma unroll
+    for (int f = 0; f < kMaxFields; ++f) {
+      if (f < nf) {
+        const float* p = g + (int64_t)f * N + i0;
+        if (kVec && i0 + 4 <= N) {
+          const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+          v[f][0] = q.x; v[f][1] = q.y; v[f][2] = q.z; v[f][3] = q.w;
+        } else {
+#pragma unroll
+          for (int t = 0; t < 4; ++t) v[f][t] = (i0 + t < N) ? p[t] : 0.0f;
+        }
+      }
+    }
+#pragma unroll
+    for (int f = 0; f < kMaxFields; ++f) {
+      if (f < nf) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const float u = m[t] * v[f][t];
+          run = fmaf(u, u, run);
+          if (++kr == 16) {
+            acc += (double)run;
+            run = 0.0f;
+            kr = 0;
+          }
+        }
       }
     }
   }
   acc += (double)run;
   acc = block_sum(acc, scratch);
   if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+  finish_sum(partials, 1, out, count, scratch);
 }
 
 // out = a * m_i^(+1 or -1) * in over nf planes of nx x ny x nz nodes, m the
@@ -271,7 +354,7 @@ __global__ void k_mass_mul(const float* __restrict__ in, float* __restrict__ out
                            int nz, int nf, float cell, float inv_cell, float a, int inverse) {
   const int N = nx * ny * nz;
   for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < N; node += gridDim.x * blockDim.x) {
-    const float fac = mass_factor(node, nx, ny, nz);
+    const float fac = mass_factor(node % nx, (node / nx) % ny, node / (nx * ny), nx, ny, nz);
     const float sc = a * (inverse ? inv_cell / fac : cell * fac);  // fac is a power of 2
     for (int f = 0; f < nf; ++f) out[(int64_t)f * N + node] = sc * in[(int64_t)f * N + node];
   }
@@ -332,39 +415,49 @@ struct UpdateDots {
 }  // namespace
 
 cudaError_t launch_dots(const float* V, int64_t ldv, int k, const float* w, int64_t n,
-                        double* partials, double* out, cudaStream_t s) {
-  cudaError_t e = dispatch_k<Dots>(k, vec_ok(V, w ? w : V, ldv), s, V, ldv, k, w, n, partials);
-  if (e != cudaSuccess) return e;
-  k_sum_partials_cols<<<1, kThreads, 0, s>>>(partials, krylov_partial_blocks(), k, out);
-  return cudaGetLastError();
+                        double* partials, double* out, unsigned* count, cudaStream_t s) {
+  return dispatch_k<Dots>(k, vec_ok(V, w ? w : V, ldv), s, V, ldv, k, w, n, partials, out, count);
 }
 
 cudaError_t launch_update(const float* V, int64_t ldv, int k, const double* coef, float* w,
-                          int64_t n, double* partials, double* norm_out, cudaStream_t s) {
-  cudaError_t e = dispatch_k<Update>(k, vec_ok(V, w, ldv), s, V, ldv, k, coef, w, n,
-                                     norm_out ? partials : (double*)nullptr);
-  if (e != cudaSuccess) return e;
-  if (norm_out) k_sum_partials_cols<<<1, kThreads, 0, s>>>(partials, krylov_partial_blocks(), 1, norm_out);
-  return cudaGetLastError();
+                          int64_t n, double* partials, double* norm_out, unsigned* count,
+                          cudaStream_t s) {
+  return dispatch_k<Update>(k, vec_ok(V, w, ldv), s, V, ldv, k, coef, w, n, partials, norm_out,
+                            count);
 }
 
 cudaError_t launch_update_dots(const float* V, int64_t ldv, int k, const double* coef, float* w,
-                               int64_t n, double* partials, double* out, cudaStream_t s) {
-  cudaError_t e = dispatch_k<UpdateDots>(k, vec_ok(V, w, ldv), s, V, ldv, k, coef, w, n, partials);
-  if (e != cudaSuccess) return e;
-  k_sum_partials_cols<<<1, kThreads, 0, s>>>(partials, krylov_partial_blocks(), k, out);
-  return cudaGetLastError();
+                               int64_t n, double* partials, double* out, unsigned* count,
+                               cudaStream_t s) {
+  return dispatch_k<UpdateDots>(k, vec_ok(V, w, ldv), s, V, ldv, k, coef, w, n, partials, out,
+                                count);
 }
 
 cudaError_t launch_axpby(float a, const float* x, float b, float* y, int64_t n, cudaStream_t s) {
-  k_axpby<<<elementwise_blocks(n), 256, 0, s>>>(a, x, b, y, n);
+  const unsigned g = elementwise_blocks((n + kChunk - 1) / kChunk);
+  if (vec_ok(x, y, 0))
+    k_axpby<true><<<g, 256, 0, s>>>(a, x, b, y, n);
+  else
+    k_axpby<false><<<g, 256, 0, s>>>(a, x, b, y, n);
   return cudaGetLastError();
 }
 
 cudaError_t launch_lincomb(const float* V, int64_t ldv, int k, const LinComb& y, float* x,
                            int64_t n, cudaStream_t s) {
-  k_lincomb<<<elementwise_blocks(n), 256, 0, s>>>(V, ldv, k, y, x, n);
-  return cudaGetLastError();
+  const dim3 g(elementwise_blocks((n + kChunk - 1) / kChunk)), b(256);
+  const bool vec = vec_ok(V, x, ldv);
+#define PF_LINCOMB_CASE(M)                                                  \
+  if (k <= M) {                                                             \
+    if (vec) k_lincomb<M, true><<<g, b, 0, s>>>(V, ldv, k, y, x, n);        \
+    else k_lincomb<M, false><<<g, b, 0, s>>>(V, ldv, k, y, x, n);           \
+    return cudaGetLastError();                                              \
+  }
+  PF_LINCOMB_CASE(4)
+  PF_LINCOMB_CASE(8)
+  PF_LINCOMB_CASE(16)
+  PF_LINCOMB_CASE(kMaxBasis)
+#undef PF_LINCOMB_CASE
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_mass_mul(const float* in, float* out, int nx, int ny, int nz, int nf,
@@ -375,9 +468,15 @@ cudaError_t launch_mass_mul(const float* in, float* out, int nx, int ny, int nz,
 }
 
 cudaError_t launch_mass_norm(const float* g, int nx, int ny, int nz, int nf, double cell,
-                             double* partials, double* out, cudaStream_t s) {
-  k_mass_norm<<<krylov_partial_blocks(), kThreads, 0, s>>>(g, nx, ny, nz, nf, (float)cell, partials);
-  k_sum_partials_cols<<<1, kThreads, 0, s>>>(partials, krylov_partial_blocks(), 1, out);
+                             double* partials, double* out, unsigned* count, cudaStream_t s) {
+  const int64_t N = (int64_t)nx * ny * nz;
+  if (nf < 1 || nf > kMaxFields) return cudaErrorInvalidValue;
+  if (N % 4 == 0 && (uintptr_t)g % 16 == 0)
+    k_mass_norm<true><<<krylov_partial_blocks(), kThreads, 0, s>>>(g, nx, ny, nz, nf, (float)cell,
+                                                                    partials, out, count);
+  else
+    k_mass_norm<false><<<krylov_partial_blocks(), kThreads, 0, s>>>(g, nx, ny, nz, nf, (float)cell,
+                                                                     partials, out, count);
   return cudaGetLastError();
 }
 

@@ -51,6 +51,8 @@ struct pf_ctx {
   float* basis = nullptr;  // kMaxBasis Krylov vectors
   int64_t ldv = 0;         // floats between consecutive Krylov vectors
   double* small = nullptr; // h1[32], h2[32], scalars
+  unsigned* count = nullptr;  // block counter of the single-launch reductions (0 between calls)
+  bool count_zeroed = false;  // set once the counter has been cleared after a bind
 
   // CUDA graph of kGraphSteps explicit steps buf_a -> ... -> buf_a
   cudaStream_t cap_stream = nullptr;
@@ -425,9 +427,21 @@ pf_status step_explicit3d(pf_ctx* c, float* state, int64_t n_steps) {
 }
 
 // ||M g||_2 in FP64 (weights = lumped mass), returned on the host
+// The single-launch reductions need their block counter at 0: cleared once
+// after every bind, then left at 0 by each reduction.
+pf_status clear_count(pf_ctx* c) {
+  if (!c->count_zeroed) {
+    PF_CUDA(cudaMemsetAsync(c->count, 0, sizeof(unsigned), c->stream));
+    c->count_zeroed = true;
+  }
+  return PF_OK;
+}
+
 pf_status mass_norm(pf_ctx* c, const float* g, double* out) {
+  if (pf_status st = clear_count(c)) return st;
   PF_CUDA(pf::launch_mass_norm(g, (int)c->n[0], (int)c->n[1], (int)c->n[2], imp_nf(c),
-                               c->h[0] * c->h[1] * c->h[2], c->partials, c->result, c->stream));
+                               c->h[0] * c->h[1] * c->h[2], c->partials, c->result, c->count,
+                               c->stream));
   double h;
   PF_CUDA(cudaMemcpyAsync(&h, c->result, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   PF_CUDA(cudaStreamSynchronize(c->stream));
@@ -442,6 +456,7 @@ pf_status mass_norm(pf_ctx* c, const float* g, double* out) {
 // 1986).
 pf_status gmres3d(pf_ctx* c, int m, int maxit, double rtol, double atol, int* iters,
                   double* rel_out) {
+  if (pf_status st = clear_count(c)) return st;
   const int64_t n = vec_len(c);
   const int64_t ldv = c->ldv;
   float* V = c->basis;
@@ -461,7 +476,7 @@ pf_status gmres3d(pf_ctx* c, int m, int maxit, double rtol, double atol, int* it
       PF_CUDA(jvp3d(c, c->u, c->d, V, 0));
       PF_CUDA(pf::launch_axpby(-1.0f, c->g, -1.0f, V, n, c->stream));
     }
-    PF_CUDA(pf::launch_dots(V, ldv, 1, nullptr, n, c->partials, dnrm, c->stream));
+    PF_CUDA(pf::launch_dots(V, ldv, 1, nullptr, n, c->partials, dnrm, c->count, c->stream));
     PF_CUDA(cudaMemcpyAsync(host, dnrm, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     PF_CUDA(cudaStreamSynchronize(c->stream));
     const double beta = std::sqrt(host[0]);
@@ -481,9 +496,10 @@ pf_status gmres3d(pf_ctx* c, int m, int maxit, double rtol, double atol, int* it
     for (; k < m && total < maxit; ++k) {
       float* vk1 = V + (int64_t)(k + 1) * ldv;
       PF_CUDA(jvp3d(c, c->u, V + (int64_t)k * ldv, vk1, 0));
-      PF_CUDA(pf::launch_dots(V, ldv, k + 1, vk1, n, c->partials, dh1, c->stream));
-      PF_CUDA(pf::launch_update_dots(V, ldv, k + 1, dh1, vk1, n, c->partials, dh2, c->stream));
-      PF_CUDA(pf::launch_update(V, ldv, k + 1, dh2, vk1, n, c->partials, dnrm, c->stream));
+      PF_CUDA(pf::launch_dots(V, ldv, k + 1, vk1, n, c->partials, dh1, c->count, c->stream));
+      PF_CUDA(pf::launch_update_dots(V, ldv, k + 1, dh1, vk1, n, c->partials, dh2, c->count,
+                                       c->stream));
+      PF_CUDA(pf::launch_update(V, ldv, k + 1, dh2, vk1, n, c->partials, dnrm, c->count, c->stream));
       PF_CUDA(cudaMemcpyAsync(host, c->small, sizeof(double) * (2 * pf::kMaxBasis + 1),
                               cudaMemcpyDeviceToHost, c->stream));
       PF_CUDA(cudaStreamSynchronize(c->stream));
@@ -615,6 +631,8 @@ pf_status pf_bind_workspace(pf_ctx* c, void* dev_ptr, size_t bytes) {
   c->ws = (char*)dev_ptr;
   c->partials = (double*)(c->ws + L.partials);
   c->result = (double*)(c->ws + L.result);
+  c->count = (unsigned*)(c->ws + L.result + 128);
+  c->count_zeroed = false;
   c->small = (double*)(c->ws + L.small);
   if (c->dim == 2) {
     c->buf_a = (float*)(c->ws + L.a);
@@ -1290,7 +1308,8 @@ cudaError_t stiff_only(pf_ctx* c, const float* U, float* out) {
 
 // FP64 dot product of two device vectors of the context's length, on the host
 pf_status dot_host(pf_ctx* c, const float* a, const float* b, double* scratch, double* out) {
-  PF_CUDA(pf::launch_dots(a, 0, 1, b, vec_len(c), c->partials, scratch, c->stream));
+  if (pf_status st = clear_count(c)) return st;
+  PF_CUDA(pf::launch_dots(a, 0, 1, b, vec_len(c), c->partials, scratch, c->count, c->stream));
   PF_CUDA(cudaMemcpyAsync(out, scratch, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   PF_CUDA(cudaStreamSynchronize(c->stream));
   return PF_OK;

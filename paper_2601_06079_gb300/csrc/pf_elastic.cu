@@ -127,7 +127,8 @@ void fill_load(const pf_elastic* e, int unit, double scale, int constrain, Elast
   a->a = (float)e->a;
 }
 
-// workspace: 7 vectors of 3N floats, then FP64 partials and scalars
+// workspace: 7 vectors of 3N floats, then FP64 partials, 32 FP64 scalars and
+// the block counter of the single-launch reductions
 struct Layout {
   size_t vec, off_part, off_sc, total;
 };
@@ -140,7 +141,7 @@ Layout layout(const pf_elastic* e) {
   np = std::max(np, (size_t)pf::cg_blocks());
   np = std::max(np, (size_t)pf::elastic_apply_blocks((int)e->n[0], (int)e->n[1], (int)e->n[2]));
   L.off_sc = L.off_part + (np * sizeof(double) + 255) / 256 * 256;
-  L.total = L.off_sc + 256;
+  L.total = L.off_sc + 512;
   return L;
 }
 
@@ -168,14 +169,14 @@ cudaError_t cg_iteration(const Elastic3DArgs& A, int64_t n, int napply, float* x
 // groups of kCheckEvery replayed from a CUDA graph (captured once per call on
 // a private stream), with a convergence check on the host after each group.
 pf_status cg(const pf_elastic* e, const Elastic3DArgs& base, const float* b, float* x, float* r,
-             float* p, float* Ap, double* part, double* sc, double rtol, int max_iter,
-             cudaStream_t s, pf_cg_stats* st) {
+             float* p, float* Ap, double* part, double* sc, unsigned* cnt, double rtol,
+             int max_iter, cudaStream_t s, pf_cg_stats* st) {
   const int64_t N = nodes(e), n = 3 * N;
   EL_CUDA(cudaMemsetAsync(x, 0, sizeof(float) * n, s));
   EL_CUDA(cudaMemcpyAsync(r, b, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
   EL_CUDA(pf::launch_elastic_constrain(r, base.nx, base.ny, base.nz, s));
   EL_CUDA(cudaMemcpyAsync(p, r, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
-  EL_CUDA(pf::launch_dots(r, 0, 1, r, n, part, sc, s));
+  EL_CUDA(pf::launch_dots(r, 0, 1, r, n, part, sc, cnt, s));
   double h_sc[2] = {0.0, 0.0};
   EL_CUDA(cudaMemcpyAsync(h_sc, sc, sizeof(double), cudaMemcpyDeviceToHost, s));
   EL_CUDA(cudaStreamSynchronize(s));
@@ -305,6 +306,8 @@ pf_status pf_elastic_solve(const pf_elastic* e, const float* b, float* u, double
         *f = (float*)(w + 3 * L.vec);
   double* part = (double*)(w + L.off_part);
   double* sc = (double*)(w + L.off_sc);
+  unsigned* cnt = (unsigned*)(w + L.off_sc + 256);
+  EL_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned), s));
   double lam, mu;
   lame(e->E, e->nu, &lam, &mu);
   if (!b) {
@@ -315,7 +318,7 @@ pf_status pf_elastic_solve(const pf_elastic* e, const float* b, float* u, double
   }
   Elastic3DArgs a;
   fill_apply(e, lam, mu, 1, &a);
-  return cg(e, a, b, u, r, p, Ap, part, sc, rtol, max_iter, s, stats);
+  return cg(e, a, b, u, r, p, Ap, part, sc, cnt, rtol, max_iter, s, stats);
 }
 
 pf_status pf_elastic_sensitivity(const pf_elastic* e, const float* g, float* u, double rtol,
@@ -334,6 +337,8 @@ pf_status pf_elastic_sensitivity(const pf_elastic* e, const float* g, float* u, 
         *la = (float*)(w + 5 * L.vec), *t = (float*)(w + 6 * L.vec);
   double* part = (double*)(w + L.off_part);
   double* sc = (double*)(w + L.off_sc);
+  unsigned* cnt = (unsigned*)(w + L.off_sc + 256);
+  EL_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned), s));
   double lam, mu;
   lame(e->E, e->nu, &lam, &mu);
   Elastic3DArgs a;
@@ -342,7 +347,7 @@ pf_status pf_elastic_sensitivity(const pf_elastic* e, const float* g, float* u, 
   fill_load(e, 0, (3.0 * lam + 2.0 * mu) * e->m, 1, &ld);
   EL_CUDA(pf::launch_elastic_load(ld, f, s));
   pf_cg_stats st_u = {}, st_l = {};
-  pf_status rs = cg(e, a, f, u, r, p, Ap, part, sc, rtol, max_iter, s, &st_u);
+  pf_status rs = cg(e, a, f, u, r, p, Ap, part, sc, cnt, rtol, max_iter, s, &st_u);
   if (rs != PF_OK) {
     if (stats) *stats = st_u;
     return rs;
@@ -360,8 +365,8 @@ pf_status pf_elastic_sensitivity(const pf_elastic* e, const float* g, float* u, 
          (double)(e->n[2] - 1) * e->h[2];
   }
   double h_d[3];
-  EL_CUDA(pf::launch_dots(gv, 0, 1, u, n, part, sc + 3, s));
-  rs = cg(e, a, gv, la, r, p, Ap, part, sc, rtol, max_iter, s, &st_l);
+  EL_CUDA(pf::launch_dots(gv, 0, 1, u, n, part, sc + 3, cnt, s));
+  rs = cg(e, a, gv, la, r, p, Ap, part, sc, cnt, rtol, max_iter, s, &st_l);
   if (rs != PF_OK) {
     if (stats) *stats = st_l;
     return rs;
@@ -378,7 +383,7 @@ pf_status pf_elastic_sensitivity(const pf_elastic* e, const float* g, float* u, 
     fill_load(e, 0, (3.0 * dl + 2.0 * dm) * e->m, 1, &lk);
     EL_CUDA(pf::launch_elastic_load(lk, Ap, s));
     EL_CUDA(pf::launch_axpby(1.0f, Ap, -1.0f, t, n, s));  // t = df - dK u
-    EL_CUDA(pf::launch_dots(la, 0, 1, t, n, part, sc + 4 + k, s));
+    EL_CUDA(pf::launch_dots(la, 0, 1, t, n, part, sc + 4 + k, cnt, s));
   }
   EL_CUDA(cudaMemcpyAsync(h_d, sc + 3, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
   EL_CUDA(cudaStreamSynchronize(s));

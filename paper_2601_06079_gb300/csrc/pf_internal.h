@@ -256,21 +256,26 @@ struct LinComb {
   float c[kMaxBasis];
 };
 int krylov_partial_blocks();
+// The reductions below finish in the same launch: the last block sums the
+// per-block partials (krylov_partial_blocks() x k doubles) in a fixed order.
+// count: a device counter that is 0 between calls (each call leaves it 0).
 cudaError_t launch_dots(const float* V, int64_t ldv, int k, const float* w, int64_t n,
-                        double* partials, double* out, cudaStream_t s);
+                        double* partials, double* out, unsigned* count, cudaStream_t s);
 cudaError_t launch_update(const float* V, int64_t ldv, int k, const double* coef, float* w,
-                          int64_t n, double* partials, double* norm_out, cudaStream_t s);
+                          int64_t n, double* partials, double* norm_out, unsigned* count,
+                          cudaStream_t s);
 // w <- w - sum_j coef[j] V_j, then out[j] = V_j . w (j < k) for the updated w,
 // in one pass (results identical to launch_update followed by launch_dots)
 cudaError_t launch_update_dots(const float* V, int64_t ldv, int k, const double* coef, float* w,
-                               int64_t n, double* partials, double* out, cudaStream_t s);
+                               int64_t n, double* partials, double* out, unsigned* count,
+                               cudaStream_t s);
 cudaError_t launch_axpby(float a, const float* x, float b, float* y, int64_t n, cudaStream_t s);
 cudaError_t launch_mass_mul(const float* in, float* out, int nx, int ny, int nz, int nf,
                             double cell, float a, int inverse, cudaStream_t s);
 cudaError_t launch_lincomb(const float* V, int64_t ldv, int k, const LinComb& y, float* x,
                            int64_t n, cudaStream_t s);
 cudaError_t launch_mass_norm(const float* g, int nx, int ny, int nz, int nf, double cell,
-                             double* partials, double* out, cudaStream_t s);
+                             double* partials, double* out, unsigned* count, cudaStream_t s);
 
 // Learned surrogate: 3x3x3 convolution kernels (BF16 tensor cores) and the
 // element-wise layers around them.  Activations NDHWC BF16.
