@@ -1,9 +1,11 @@
 // Vector kernels of the Newton-GMRES solver (JAX-PF Eq. 13-14).  The Krylov
-// basis is FP32; every inner product and norm is accumulated in FP64: each
-// thread forms FP32 partial sums over 8 consecutive products of its stride
-// and adds them into FP64 accumulators, blocks reduce in FP64 through shared
-// memory, and a single block sums the per-block partials in a fixed order,
-// so results are deterministic.
+// basis is FP32; every inner product and norm keeps about 48 bits per thread
+// and finishes in FP64: each thread forms FP32 sums over 8 consecutive
+// products and adds them into a compensated FP32 pair (hi + lo, Knuth's
+// two-sum), blocks reduce in FP64 through shared memory, and the last block
+// sums the per-block partials in a fixed order, so results are
+// deterministic.  No FP64 arithmetic runs per element: GB300 issues about 2
+// FP64 operations per clock per SM, 64 times fewer than FP32.
 #include "pf_internal.h"
 
 namespace pf {
@@ -12,6 +14,19 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kChunk = 8;      // products per FP32 partial sum
 constexpr int kMaxFields = 8;  // order parameters of a Newton vector (planes of the mass norm)
+
+// s added to the unevaluated sum hi + lo (Knuth's two-sum: the rounding error
+// of hi + s is exact in FP32 and collects in lo)
+struct Acc2 {
+  float hi = 0.0f, lo = 0.0f;
+  __device__ __forceinline__ void add(float s) {
+    const float t = hi + s;
+    const float bp = t - hi;
+    lo += (hi - (t - bp)) + (s - bp);
+    hi = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -96,12 +111,12 @@ __device__ __forceinline__ float chunk_dot(const float v[kChunk], const float u[
 }
 
 template <int KMAX>
-__device__ __forceinline__ void write_partials(double (&acc)[KMAX], int k, double* scratch,
+__device__ __forceinline__ void write_partials(Acc2 (&acc)[KMAX], int k, double* scratch,
                                                double* partials, double* out, unsigned* count) {
 #pragma unroll
   for (int j = 0; j < KMAX; ++j) {
     if (j < k) {
-      const double r = block_sum(acc[j], scratch);
+      const double r = block_sum(acc[j].value(), scratch);
       if (threadIdx.x == 0) partials[blockIdx.x * k + j] = r;
     }
   }
@@ -118,9 +133,7 @@ __global__ void __launch_bounds__(kThreads) k_dots(const float* __restrict__ V, 
                                                    unsigned* count) {
   __shared__ double scratch[kThreads / 32];
   const int64_t chunks = (n + kChunk - 1) / kChunk;
-  double acc[KMAX];
-#pragma unroll
-  for (int j = 0; j < KMAX; ++j) acc[j] = 0.0;
+  Acc2 acc[KMAX];
   for (int64_t c = (int64_t)blockIdx.x * kThreads + threadIdx.x; c < chunks;
        c += (int64_t)gridDim.x * kThreads) {
     const int64_t i0 = c * kChunk;
@@ -131,7 +144,7 @@ __global__ void __launch_bounds__(kThreads) k_dots(const float* __restrict__ V, 
       if (j < k) {
         float v[kChunk];
         load8<kVec>(V + j * ldv, i0, n, v);
-        acc[j] += (double)chunk_dot(v, u, i0, n);
+        acc[j].add(chunk_dot(v, u, i0, n));
       }
     }
   }
@@ -166,7 +179,7 @@ __global__ void __launch_bounds__(kThreads) k_update(const float* __restrict__ V
   for (int j = threadIdx.x; j < k; j += kThreads) cf[j] = (float)coef[j];
   __syncthreads();
   const int64_t chunks = (n + kChunk - 1) / kChunk;
-  double acc = 0.0;
+  Acc2 acc;
   for (int64_t c = (int64_t)blockIdx.x * kThreads + threadIdx.x; c < chunks;
        c += (int64_t)gridDim.x * kThreads) {
     const int64_t i0 = c * kChunk;
@@ -174,11 +187,11 @@ __global__ void __launch_bounds__(kThreads) k_update(const float* __restrict__ V
     load8<kVec>(w, i0, n, x);
     chunk_update<KMAX, kVec>(V, ldv, k, cf, i0, n, x);
     store8<kVec>(w, i0, n, x);
-    acc += (double)chunk_dot(x, x, i0, n);
+    if (norm_out) acc.add(chunk_dot(x, x, i0, n));
   }
   if (norm_out) {
-    acc = block_sum(acc, scratch);
-    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+    const double r = block_sum(acc.value(), scratch);
+    if (threadIdx.x == 0) partials[blockIdx.x] = r;
     finish_sum(partials, 1, norm_out, count, scratch);
   }
 }
@@ -200,9 +213,7 @@ __global__ void __launch_bounds__(kThreads) k_update_dots(const float* __restric
   for (int j = threadIdx.x; j < k; j += kThreads) cf[j] = (float)coef[j];
   __syncthreads();
   const int64_t chunks = (n + kChunk - 1) / kChunk;
-  double acc[KMAX];
-#pragma unroll
-  for (int j = 0; j < KMAX; ++j) acc[j] = 0.0;
+  Acc2 acc[KMAX];
   for (int64_t c = (int64_t)blockIdx.x * kThreads + threadIdx.x; c < chunks;
        c += (int64_t)gridDim.x * kThreads) {
     const int64_t i0 = c * kChunk;
@@ -215,7 +226,7 @@ __global__ void __launch_bounds__(kThreads) k_update_dots(const float* __restric
       if (j < k) {
         float v[kChunk];
         load8<kVec>(V + j * ldv, i0, n, v);
-        acc[j] += (double)chunk_dot(v, x, i0, n);
+        acc[j].add(chunk_dot(v, x, i0, n));
       }
     }
   }
@@ -276,7 +287,8 @@ __device__ __forceinline__ float mass_factor(int x, int y, int z, int nx, int ny
 // Each thread takes chunks of 4 consecutive nodes (one index division per
 // chunk; kVec: one 16-byte load per field when the node count is a multiple
 // of 4).  Products in FP32 (GB300's FP64 rate is a small fraction of its FP32
-// rate), runs of 16 squares in FP32, the runs and the block sums in FP64.
+// rate), a chunk's squares summed in FP32, the chunks in a compensated FP32
+// pair, the block sums in FP64.
 template <bool kVec>
 __global__ void __launch_bounds__(kThreads) k_mass_norm(const float* __restrict__ g, int nx,
                                                         int ny, int nz, int nf, float cell,
@@ -285,9 +297,7 @@ __global__ void __launch_bounds__(kThreads) k_mass_norm(const float* __restrict_
   __shared__ double scratch[kThreads / 32];
   const int64_t N = (int64_t)nx * ny * nz;
   const int64_t chunks = (N + 3) / 4;
-  double acc = 0.0;
-  float run = 0.0f;
-  int kr = 0;
+  Acc2 acc;
   for (int64_t c = (int64_t)blockIdx.x * kThreads + threadIdx.x; c < chunks;
        c += (int64_t)gridDim.x * kThreads) {
     const int64_t i0 = 4 * c;
@@ -325,6 +335,8 @@ __global__ void __launch_bounds__(kThreads) k_mass_norm(const float* __restrict_
         }
       }
     }
+    // the chunk's squares (at most 32) as one FP32 run, then one FP64 add
+    float run = 0.0f;
 #pragma unroll
     for (int f = 0; f < kMaxFields; ++f) {
       if (f < nf) {
@@ -332,18 +344,13 @@ __global__ void __launch_bounds__(kThreads) k_mass_norm(const float* __restrict_
         for (int t = 0; t < 4; ++t) {
           const float u = m[t] * v[f][t];
           run = fmaf(u, u, run);
-          if (++kr == 16) {
-            acc += (double)run;
-            run = 0.0f;
-            kr = 0;
-          }
         }
       }
     }
+    acc.add(run);
   }
-  acc += (double)run;
-  acc = block_sum(acc, scratch);
-  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+  const double r = block_sum(acc.value(), scratch);
+  if (threadIdx.x == 0) partials[blockIdx.x] = r;
   finish_sum(partials, 1, out, count, scratch);
 }
 
