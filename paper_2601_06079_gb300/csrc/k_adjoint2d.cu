@@ -279,13 +279,16 @@ __global__ void __launch_bounds__(kThreads) k_ch_adj_step(const ChMobArgs a, con
     dK = fmaf(mw, T.Kc[y - 1][x - 1], dK);
     dW = fmaf(mw, T.F[y - 1][x - 1], dW);
   }
-  // block sums (fixed order), accumulated across steps in this block's slot
-  double v[3] = {a.cell * (double)dK, a.cell * (double)dW, a.cell * (double)dM};
+  // block sums (fixed order), accumulated across steps in this block's slot:
+  // warp sums in FP32 (a shuffle tree per step in FP64 would cost about 20
+  // FP64 operations per thread, and GB300 issues 2 per clock per SM), the
+  // warps and the steps in FP64
+  float v[3] = {dK, dW, dM};
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_down_sync(0xffffffffu, v[j], o);
-    if ((threadIdx.x & 31) == 0) red[j][threadIdx.x >> 5] = v[j];
+    if ((threadIdx.x & 31) == 0) red[j][threadIdx.x >> 5] = a.cell * (double)v[j];
   }
   __syncthreads();
   if (threadIdx.x == 0) {

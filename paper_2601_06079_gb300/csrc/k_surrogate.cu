@@ -152,29 +152,46 @@ __global__ void k_incr_sumsq(const float* __restrict__ x, int nf, int nxc, int64
   if (threadIdx.x == 0) part[b * gridDim.x + blockIdx.x] = red[0];
 }
 
-__global__ void k_incr_scale(const double* __restrict__ part, int nblk, int B, double count,
-                             float a, int mode, float* __restrict__ sig) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= B) return;
+// Sum of p[0 .. n) by one block of kT threads in a fixed order (strided
+// per-thread sums, then a shared-memory tree), valid in thread 0.  Serial FP64
+// adds by one thread wait out the FP64 latency of every add on GB300.
+__device__ double block_sum_fixed(const double* __restrict__ p, int n) {
+  __shared__ double red[kT];
+  double s = 0.0;
+  for (int k = threadIdx.x; k < n; k += kT) s += p[k];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = kT / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  return red[0];
+}
+
+// one block per sample
+__global__ void __launch_bounds__(kT) k_incr_scale(const double* __restrict__ part, int nblk,
+                                                   double count, float a, int mode,
+                                                   float* __restrict__ sig) {
+  const int b = blockIdx.x;
   if (!mode) {
-    sig[b] = a;
+    if (threadIdx.x == 0) sig[b] = a;
     return;
   }
-  double ss = 0.0;
-  for (int k = 0; k < nblk; ++k) ss += part[b * nblk + k];
-  sig[b] = fmaxf(a * (float)sqrt(ss / count), 1e-30f);
+  const double ss = block_sum_fixed(part + (int64_t)b * nblk, nblk);
+  if (threadIdx.x == 0) sig[b] = fmaxf(a * (float)sqrt(ss / count), 1e-30f);
 }
 
 // output unit of the quadratic-extrapolation model: a * RMS of the second
 // difference, floored at 1e-3 of the increment unit sig[b] (a trajectory
-// with no curvature leaves a small correction rather than a vanishing unit)
-__global__ void k_curv_scale(const double* __restrict__ part, int nblk, int B, double count,
-                             float a, const float* __restrict__ sig, float* __restrict__ sigo) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= B) return;
-  double ss = 0.0;
-  for (int k = 0; k < nblk; ++k) ss += part[b * nblk + k];
-  sigo[b] = fmaxf(fmaxf(a * (float)sqrt(ss / count), 1e-3f * sig[b]), 1e-30f);
+// with no curvature leaves a small correction rather than a vanishing unit);
+// one block per sample
+__global__ void __launch_bounds__(kT) k_curv_scale(const double* __restrict__ part, int nblk,
+                                                   double count, float a,
+                                                   const float* __restrict__ sig,
+                                                   float* __restrict__ sigo) {
+  const int b = blockIdx.x;
+  const double ss = block_sum_fixed(part + (int64_t)b * nblk, nblk);
+  if (threadIdx.x == 0) sigo[b] = fmaxf(fmaxf(a * (float)sqrt(ss / count), 1e-3f * sig[b]), 1e-30f);
 }
 
 // Voxel index helpers for NDHWC: i = ((b * D + z) * H + y) * W + x
@@ -363,12 +380,10 @@ __global__ void k_grad_out(const float* __restrict__ g, int C, int nf, int B, in
   }
 }
 
-__global__ void k_sum_doubles(const double* __restrict__ p, int n, double scale, double* out) {
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int i = 0; i < n; ++i) s += p[i];
-    *out = s * scale;
-  }
+__global__ void __launch_bounds__(kT) k_sum_doubles(const double* __restrict__ p, int n,
+                                                    double scale, double* out) {
+  const double s = block_sum_fixed(p, n);
+  if (threadIdx.x == 0) *out = s * scale;
 }
 
 // master FP32 weights [27][co][ci] -> BF16 forward copy and the data-gradient
@@ -423,10 +438,10 @@ cudaError_t launch_incr_scale(const float* x, int nf, int B, int64_t V, float a,
     k_incr_sumsq<<<dim3(nblk, B), kT, 0, s>>>(x, nf, nf * (mode + 1), V, 0, part);
     if (cudaGetLastError() != cudaSuccess) return cudaErrorLaunchFailure;
   }
-  k_incr_scale<<<(B + 127) / 128, 128, 0, s>>>(part, nblk, B, (double)nf * V, a, mode, sig);
+  k_incr_scale<<<B, kT, 0, s>>>(part, nblk, (double)nf * V, a, mode, sig);
   if (mode == 2) {  // the partials are reused once the increment unit is formed
     k_incr_sumsq<<<dim3(nblk, B), kT, 0, s>>>(x, nf, 3 * nf, V, 1, part);
-    k_curv_scale<<<(B + 127) / 128, 128, 0, s>>>(part, nblk, B, (double)nf * V, a, sig, sigo);
+    k_curv_scale<<<B, kT, 0, s>>>(part, nblk, (double)nf * V, a, sig, sigo);
   } else {
     cudaMemcpyAsync(sigo, sig, sizeof(float) * B, cudaMemcpyDeviceToDevice, s);
   }
@@ -486,7 +501,7 @@ cudaError_t launch_mse(const float* pred, int C, int nf, int nxc, int B, int D, 
     qq = q;
   }
   k_sumsq<<<mse_blocks(), kT, 0, s>>>(qq, n, partials);
-  k_sum_doubles<<<1, 32, 0, s>>>(partials, mse_blocks(), (double)scale, loss);
+  k_sum_doubles<<<1, kT, 0, s>>>(partials, mse_blocks(), (double)scale, loss);
   const float* g = qq;
   if (c != 0.0f) {
     k_apply_stiff<<<blocks_for(n), kT, 0, s>>>(q, (int64_t)B * nf, D, H, W, c, 1, r);
