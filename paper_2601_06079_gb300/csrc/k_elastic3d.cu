@@ -26,8 +26,26 @@ namespace {
 
 constexpr int kThreads = 128;
 
-// FP64 sum over the block (any block shape up to 1024 threads), result in thread 0
-__device__ double block_sum(double v) {
+// Sum over the block (any block shape up to 1024 threads), result in thread
+// 0: warp sums in FP32 (GB300 issues about 2 FP64 operations per clock per
+// SM, 64 times fewer than FP32), the warp partials in FP64, fixed order
+__device__ double block_sum(float v) {
+  __shared__ double part[32];
+  const int t = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int nt = blockDim.x * blockDim.y * blockDim.z;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((t & 31) == 0) part[t >> 5] = (double)v;
+  __syncthreads();
+  double s = 0.0;
+  if (t == 0)
+    for (int w = 0; w < (nt + 31) / 32; ++w) s += part[w];
+  return s;
+}
+
+// the same for FP64 inputs (the single-block sum of the block partials)
+__device__ double block_sum_f64(double v) {
   __shared__ double part[32];
   const int t = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
   const int nt = blockDim.x * blockDim.y * blockDim.z;
@@ -266,7 +284,7 @@ __global__ void __launch_bounds__(kThreads, PF_EL_MINB) k_elastic_apply(const El
   else
     dot = boundary_block<kDot>(a, b - ni);
   if (kDot) {
-    const double s = block_sum((double)dot);
+    const double s = block_sum(dot);
     if (threadIdx.x == 0) a.dot[b] = s;
   }
 }
@@ -349,7 +367,7 @@ __global__ void k_cg_xr(float* __restrict__ x, float* __restrict__ r, const floa
     r[i] = ri;
     rr = fmaf(ri, ri, rr);
   }
-  const double s = block_sum((double)rr);
+  const double s = block_sum(rr);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
@@ -357,7 +375,7 @@ __global__ void k_cg_xr(float* __restrict__ x, float* __restrict__ r, const floa
 __global__ void k_sum_part(const double* __restrict__ part, int nb, double* __restrict__ out) {
   double v = 0.0;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) v += part[b];
-  const double s = block_sum(v);
+  const double s = block_sum_f64(v);
   if (threadIdx.x == 0) *out = s;
 }
 
