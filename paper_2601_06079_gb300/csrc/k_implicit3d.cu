@@ -194,7 +194,7 @@ __device__ __forceinline__ void project3_grad(const u64 q[8], const u64 gx[4], c
 // segments of a column.  Along a segment it walks the element layers from
 // the one below its first plane to the last one inside it:
 //   - node plane z+1 of U and v or U^n (fields in pairs, the kSNX x kSNY nodes
-//     around the tile, mirrored at the mesh boundary) enters a 3-plane ring
+//     around the tile, mirrored at the mesh boundary) enters a 4-plane ring
 //     in shared memory, pair index fastest, from registers loaded while the
 //     previous layer computed;
 //   - one thread per (element, field pair) interpolates U (and v for the JVP)
@@ -204,12 +204,15 @@ __device__ __forceinline__ void project3_grad(const u64 q[8], const u64 gx[4], c
 //     sum_f U_f v_f) by warp shuffles: every coupling of Eq. 13-14 is formed
 //     from one interpolation per field, with no second pass;
 //   - f' (or H v) and the gradient term are weighted back to the corners: the 4 on
-//     the layer's lower face into one buffer, the 4 on its upper face into a
-//     2-layer ring;
+//     the layer's lower face into a 2-layer ring, the 4 on its upper face into
+//     a 3-layer ring;
 //   - node plane z gathers its 8 element contributions (lower faces of layer
 //     z, upper faces of layer z-1) in the fixed corner order, adds the mass
 //     term and writes R or J v.
-// Two block barriers per layer; no atomics, so results are bitwise repeatable.
+// One block barrier per layer: the gather of a plane and the element work of
+// the next layer run in the same phase, the rings keeping what one writes
+// apart from what the other reads.  No atomics, so results are bitwise
+// repeatable.
 #ifndef PF_SWEEP_SX
 #define PF_SWEEP_SX 16
 #endif
@@ -230,7 +233,7 @@ struct SweepCfg {
   static constexpr int G = NP >= 3 ? 4 : NP;  // lanes per element, one per field pair
   static constexpr int kThreads = (kSElems * G + 31) / 32 * 32;
   static constexpr int kItems = (kSPlane * NP + kThreads - 1) / kThreads;  // staged pairs per thread
-  static constexpr size_t kSmem = sizeof(u64) * (size_t)NP * (2 * 3 * kSPlane + 4 * kSElems + 8 * kSElems);
+  static constexpr size_t kSmem = sizeof(u64) * (size_t)NP * (2 * 4 * kSPlane + 8 * kSElems + 12 * kSElems);
 };
 
 template <int NF, bool kJVP>
@@ -240,10 +243,10 @@ __global__ void __launch_bounds__(SweepCfg<(NF + 1) / 2>::kThreads, PF_SWEEP_MIN
   constexpr int G = SweepCfg<NP>::G, kThreads = SweepCfg<NP>::kThreads;
   constexpr int kItems = SweepCfg<NP>::kItems;
   extern __shared__ u64 smem[];
-  u64* sU = smem;                        // [3 planes][kSPlane nodes][NP]
-  u64* sW = sU + 3 * kSPlane * NP;       // v (JVP) or U^n (residual), same layout
-  u64* sLow = sW + 3 * kSPlane * NP;     // [4 lower corners][kSElems][NP] of the current layer
-  u64* sUp = sLow + 4 * kSElems * NP;    // [2 layers][4 upper corners][kSElems][NP]
+  u64* sU = smem;                        // [4 planes][kSPlane nodes][NP]
+  u64* sW = sU + 4 * kSPlane * NP;       // v (JVP) or U^n (residual), same layout
+  u64* sLowB = sW + 4 * kSPlane * NP;    // [2 layers][4 lower corners][kSElems][NP]
+  u64* sUpB = sLowB + 8 * kSElems * NP;  // [3 layers][4 upper corners][kSElems][NP]
 
   const int tiles_x = (a.nx + kSX - 1) / kSX, tiles_y = (a.ny + kSY - 1) / kSY;
   const int64_t N = (int64_t)a.nx * a.ny * a.nz;
@@ -311,12 +314,53 @@ __global__ void __launch_bounds__(SweepCfg<(NF + 1) / 2>::kThreads, PF_SWEEP_MIN
   store_plane(0);
   fetch(z0);
 
-  for (int i = 0; i <= cz; ++i) {  // element layer z0 - 1 + i between planes z0 - 1 + i, z0 + i
-    const int s0 = i % 3, s1 = (i + 1) % 3;
-    store_plane(s1);
-    if (i < cz) fetch(z0 + i + 1);
+  for (int i = 0; i <= cz + 1; ++i) {
+    // stage plane z0 + i; then gather node plane z0 - 2 + i and compute element
+    // layer z0 - 1 + i (between planes z0 - 1 + i and z0 + i) with one barrier:
+    // the rings (4 planes, 2 lower-face and 3 upper-face layers) keep what one
+    // phase writes apart from what the other reads
+    if (i <= cz) {
+      store_plane((i + 1) % 4);
+      if (i < cz) fetch(z0 + i + 1);
+    }
     __syncthreads();
 
+    if (i >= 2) {  // node plane z0 - 2 + i: lower faces of layer i - 1, upper faces of layer i - 2
+      const int gz = z0 - 2 + i;
+      const u64* sLow = sLowB + ((i - 1) & 1) * 4 * kSElems * NP;
+      const u64* upp = sUpB + ((i - 2) % 3) * 4 * kSElems * NP;
+      const int s0 = (i - 1) % 4;
+      for (int t = tid; t < kSX * kSY * NP; t += kThreads) {
+        const int n = t / NP, p = t % NP;
+        const int lx = 1 + n % kSX, ly = 1 + n / kSX;
+        const int gx = x0 + lx - 1, gy = y0 + ly - 1;
+        if (gx >= a.nx || gy >= a.ny) continue;
+        u64 acc = sLow[(ly * kSEX + lx) * NP + p];  // corner 0 of the element above
+#pragma unroll
+        for (int k = 1; k < 8; ++k) {  // element with corner k at this node
+          const int ex = lx - (k & 1), ey = ly - ((k >> 1) & 1);
+          const u64* src = (k >> 2) ? upp : sLow;
+          acc = add2(acc, src[((k & 3) * kSElems + ey * kSEX + ex) * NP + p]);
+        }
+        // G = (u - u^n)/dt + L (F + kappa K u) / m   or   v/dt + L (H v + kappa K v) / m,
+        // the element sums carrying weight |cell|/8 over the interior mass |cell|
+        const int c0 = (s0 * kSPlane + ly * kSNX + lx) * NP + p;
+        const u64 own = kJVP ? sW[c0] : sub2(sU[c0], sW[c0]);
+        u64 r = fma2(own, bc(a.inv_dt), mul2(bc(0.125f * a.mob), acc));
+        if (a.unscaled) {
+          const float wx = (gx == 0 || gx == a.nx - 1) ? 0.5f : 1.0f;
+          const float wy = (gy == 0 || gy == a.ny - 1) ? 0.5f : 1.0f;
+          const float wz = (gz == 0 || gz == a.nz - 1) ? 0.5f : 1.0f;
+          r = mul2(r, bc(a.cell * wx * wy * wz));
+        }
+        const int64_t o = (int64_t)gz * plane + (int64_t)gy * a.nx + gx;
+        a.out[(int64_t)(2 * p) * N + o] = plo(r);
+        if (2 * p + 1 < NF) a.out[(int64_t)(2 * p + 1) * N + o] = phi(r);
+      }
+    }
+
+    if (i <= cz) {
+      const int s0 = i % 4, s1 = (i + 1) % 4;
     {
       // the gradient term acts on v (JVP) or on U (residual)
       u64 c[8], uq[8], vq[8], hq[8], out[8], gx[4], gy[4], gz[4];
@@ -386,7 +430,8 @@ __global__ void __launch_bounds__(SweepCfg<(NF + 1) / 2>::kThreads, PF_SWEEP_MIN
       }
       project3_grad(hq, gx, gy, gz, a.kg, out);
       if (el_ok) {
-        u64* up = sUp + (i & 1) * 4 * kSElems * NP;
+        u64* sLow = sLowB + (i & 1) * 4 * kSElems * NP;
+        u64* up = sUpB + (i % 3) * 4 * kSElems * NP;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           sLow[(k * kSElems + e) * NP + p_el] = out[k];
@@ -394,38 +439,6 @@ __global__ void __launch_bounds__(SweepCfg<(NF + 1) / 2>::kThreads, PF_SWEEP_MIN
         }
       }
     }
-    __syncthreads();
-
-    if (i >= 1) {  // node plane z0 - 1 + i: lower faces of this layer, upper faces of the last
-      const int gz = z0 - 1 + i;
-      const u64* upp = sUp + ((i - 1) & 1) * 4 * kSElems * NP;
-      for (int t = tid; t < kSX * kSY * NP; t += kThreads) {
-        const int n = t / NP, p = t % NP;
-        const int lx = 1 + n % kSX, ly = 1 + n / kSX;
-        const int gx = x0 + lx - 1, gy = y0 + ly - 1;
-        if (gx >= a.nx || gy >= a.ny) continue;
-        u64 acc = sLow[(ly * kSEX + lx) * NP + p];  // corner 0 of the element above
-#pragma unroll
-        for (int k = 1; k < 8; ++k) {  // element with corner k at this node
-          const int ex = lx - (k & 1), ey = ly - ((k >> 1) & 1);
-          const u64* src = (k >> 2) ? upp : sLow;
-          acc = add2(acc, src[((k & 3) * kSElems + ey * kSEX + ex) * NP + p]);
-        }
-        // G = (u - u^n)/dt + L (F + kappa K u) / m   or   v/dt + L (H v + kappa K v) / m,
-        // the element sums carrying weight |cell|/8 over the interior mass |cell|
-        const int c0 = (s0 * kSPlane + ly * kSNX + lx) * NP + p;
-        const u64 own = kJVP ? sW[c0] : sub2(sU[c0], sW[c0]);
-        u64 r = fma2(own, bc(a.inv_dt), mul2(bc(0.125f * a.mob), acc));
-        if (a.unscaled) {
-          const float wx = (gx == 0 || gx == a.nx - 1) ? 0.5f : 1.0f;
-          const float wy = (gy == 0 || gy == a.ny - 1) ? 0.5f : 1.0f;
-          const float wz = (gz == 0 || gz == a.nz - 1) ? 0.5f : 1.0f;
-          r = mul2(r, bc(a.cell * wx * wy * wz));
-        }
-        const int64_t o = (int64_t)gz * plane + (int64_t)gy * a.nx + gx;
-        a.out[(int64_t)(2 * p) * N + o] = plo(r);
-        if (2 * p + 1 < NF) a.out[(int64_t)(2 * p + 1) * N + o] = phi(r);
-      }
     }
   }
   }  // segments
