@@ -446,8 +446,8 @@ def forms_implicit_adjoint(dev, stream, n=1024, n_steps=10):
             "forward_s": t_fwd, "forward_plus_adjoint_s": t_adj,
             "adjoint_over_forward": t_adj / t_fwd,
             "forward_gmres_iters": fwd["gmres_iters"], "total_gmres_iters": st["gmres_iters"],
-            "accuracy_gate": "<= 0.1 per mille (L) / 0.5 per mille (kappa) vs the FP64 oracle "
-                             "adjoint in the Table 1 setting (tests/test_gpu_implicit.py)"}
+            "accuracy_gate": "<= 0.1 per mille (L and kappa) vs the FP64 oracle adjoint in "
+                             "the Table 1 setting (tests/test_gpu_implicit.py)"}
 
 
 def forms_eshelby(dev, stream, flush, n=129):
