@@ -156,14 +156,14 @@ template <int KMAX, bool kVec>
 __device__ __forceinline__ void chunk_update(const float* __restrict__ V, int64_t ldv, int k,
                                              const float* cf, int64_t i0, int64_t n,
                                              float x[kChunk]) {
+  // up to 8 vectors fully unrolled; beyond, groups of 4 (a full unroll of 16
+  // or 32 hoists every vector's loads and takes up to 255 registers)
+#pragma unroll(KMAX <= 8 ? KMAX : 4)
+  for (int j = 0; j < k; ++j) {
+    float v[kChunk];
+    load8<kVec>(V + j * ldv, i0, n, v);
 #pragma unroll
-  for (int j = 0; j < KMAX; ++j) {
-    if (j < k) {
-      float v[kChunk];
-      load8<kVec>(V + j * ldv, i0, n, v);
-#pragma unroll
-      for (int t = 0; t < kChunk; ++t) x[t] = fmaf(-cf[j], v[t], x[t]);
-    }
+    for (int t = 0; t < kChunk; ++t) x[t] = fmaf(-cf[j], v[t], x[t]);
   }
 }
 
