@@ -3,6 +3,8 @@
 // pooling, nearest upsampling with an additive skip, ReLU masks, the
 // mean-squared loss, weight conversion and the Adam update, each with the
 // backward form the training step needs.
+#include <algorithm>
+
 #include "pf_internal.h"
 
 #include <cuda_bf16.h>
@@ -399,6 +401,22 @@ __global__ void k_convert_weights(const float* __restrict__ w, int ci, int co,
   }
 }
 
+// Every layer's conversion in one launch: blockIdx.y is the layer, blocks
+// stride over its weights (the per-element work of k_convert_weights)
+__global__ void k_convert_weights_all(const ConvertTable t) {
+  const int l = blockIdx.y;
+  const int ci = t.ci[l], co = t.co[l];
+  const int64_t n = (int64_t)27 * ci * co;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int c_in = (int)(i % ci), c_out = (int)((i / ci) % co), tap = (int)(i / (ci * co));
+    const __nv_bfloat16 v = __float2bfloat16(t.w[l][i]);
+    reinterpret_cast<__nv_bfloat16*>(t.fwd[l])[i] = v;
+    if (t.bwd[l])
+      reinterpret_cast<__nv_bfloat16*>(t.bwd[l])[((int64_t)(26 - tap) * ci + c_in) * co + c_out] = v;
+  }
+}
+
 // Adam (Kingma & Ba 2015) with bias correction; g holds the gradient
 __global__ void k_adam(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
                        const float* __restrict__ g, int64_t n, float lr, float b1, float b2,
@@ -516,6 +534,14 @@ cudaError_t launch_convert_weights(const float* w, int ci, int co, void* fwd, vo
                                    cudaStream_t s) {
   k_convert_weights<<<blocks_for((int64_t)27 * ci * co), kT, 0, s>>>(
       w, ci, co, (__nv_bfloat16*)fwd, (__nv_bfloat16*)bwd);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert_weights_all(const ConvertTable& t, cudaStream_t s) {
+  if (t.n < 1 || t.n > kMaxConvertLayers) return cudaErrorInvalidValue;
+  int64_t most = 0;
+  for (int l = 0; l < t.n; ++l) most = std::max<int64_t>(most, (int64_t)27 * t.ci[l] * t.co[l]);
+  k_convert_weights_all<<<dim3((unsigned)((most + kT - 1) / kT), t.n), kT, 0, s>>>(t);
   return cudaGetLastError();
 }
 

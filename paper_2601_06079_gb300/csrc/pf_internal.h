@@ -330,6 +330,17 @@ cudaError_t launch_mse(const float* pred, int C, int nf, int nxc, int B, int D, 
                        double* loss, cudaStream_t s);
 cudaError_t launch_convert_weights(const float* w, int ci, int co, void* fwd, void* bwd,
                                    cudaStream_t s);
+// All layers' conversions in one launch: layer l converts w[l] (27 x co x ci
+// FP32) into fwd[l] (and bwd[l] unless null), as launch_convert_weights does.
+constexpr int kMaxConvertLayers = 16;
+struct ConvertTable {
+  const float* w[kMaxConvertLayers];
+  void* fwd[kMaxConvertLayers];
+  void* bwd[kMaxConvertLayers];
+  int ci[kMaxConvertLayers], co[kMaxConvertLayers];
+  int n;
+};
+cudaError_t launch_convert_weights_all(const ConvertTable& t, cudaStream_t s);
 cudaError_t launch_adam(float* p, float* m, float* v, const float* g, int64_t n, float lr,
                         float b1, float b2, float eps, int step, cudaStream_t s);
 

@@ -135,10 +135,17 @@ struct Net {
 };
 
 pf_status convert_all(const Net& n, const float* params, bool with_bwd) {
-  for (int l = 0; l < kNL; ++l)
-    SG_CUDA(pf::launch_convert_weights(params + w_off(l), kLayers[l].cin, kLayers[l].cout,
-                                       n.at<void>(n.p.wf[l]),
-                                       with_bwd ? n.at<void>(n.p.wb[l]) : nullptr, n.s));
+  static_assert(kNL <= pf::kMaxConvertLayers, "layer table too small");
+  pf::ConvertTable t{};
+  for (int l = 0; l < kNL; ++l) {
+    t.w[l] = params + w_off(l);
+    t.fwd[l] = n.at<void>(n.p.wf[l]);
+    t.bwd[l] = with_bwd ? n.at<void>(n.p.wb[l]) : nullptr;
+    t.ci[l] = kLayers[l].cin;
+    t.co[l] = kLayers[l].cout;
+  }
+  t.n = kNL;
+  SG_CUDA(pf::launch_convert_weights_all(t, n.s));
   return PF_OK;
 }
 
