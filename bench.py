@@ -736,6 +736,9 @@ def run_profile(args):
     surrogate two warm-start predictions on 128^3 x 8 fields (tcgen05 convolutions)
     jvp       three Fan-Chen Jacobian-vector products on 128^3 x 8 fields
     residual  three Fan-Chen implicit residuals on 128^3 x 8 fields
+    newton    one implicit grain-growth step on 128^3 x 8 fields (after three
+              warm-up steps) inside a profiler range, for ncu
+              --profile-from-start off
     ensemble  20 steps of the 256-instance AC ensemble, one launch per step (the
               persistent mode runs the same task body behind a grid barrier)
     coupled   20 coupled Allen-Cahn / Cahn-Hilliard steps on 2048^2
@@ -787,6 +790,19 @@ def run_profile(args):
             r = solver.implicit_residual(Un, U)
         torch.cuda.synchronize()
         print(f"profile run done: |R| {float(r.norm()):.6f}")
+    elif args.target == "newton":
+        from paper_2601_06079_gb300 import warmstart as WS
+        n = 128
+        solver = WS.grain_solver(n)
+        U = torch.from_numpy(G.voronoi_grains(1, n=n, n_seeds=64, n_op=8)).cuda()
+        for _ in range(3):
+            solver.step_implicit(U, 1)
+        torch.cuda.synchronize()
+        torch.cuda.cudart().cudaProfilerStart()  # ncu --profile-from-start off: this step only
+        st = solver.step_implicit(U, 1)
+        torch.cuda.synchronize()
+        torch.cuda.cudart().cudaProfilerStop()
+        print(f"profile run done: {st['newton_iters']} Newton, {st['gmres_iters']} GMRES")
     elif args.target == "elastic":
         n = 129
         el = pf.Elastic((n, n, n), 100.0 / (n - 1))
@@ -836,7 +852,7 @@ def main():
                     help="run one workload untimed for ncu (see --target)")
     ap.add_argument("--tsteps", type=int, default=N_TSTEPS)
     ap.add_argument("--target", default="ch",
-                    choices=["ch", "surrogate", "jvp", "residual", "ensemble", "coupled",
+                    choices=["ch", "surrogate", "jvp", "residual", "newton", "ensemble", "coupled",
                              "elastic", "train"],
                     help="workload of --profile")
     args = ap.parse_args()
