@@ -736,6 +736,8 @@ def run_profile(args):
     surrogate two warm-start predictions on 128^3 x 8 fields (tcgen05 convolutions)
     jvp       three Fan-Chen Jacobian-vector products on 128^3 x 8 fields
     residual  three Fan-Chen implicit residuals on 128^3 x 8 fields
+    adjoint   the checkpointed CH adjoint with a mobility field on 512^2 (200 steps,
+              checkpoint every 100): forward, recompute and reverse launches
     newton    one implicit grain-growth step on 128^3 x 8 fields (after three
               warm-up steps) inside a profiler range, for ncu
               --profile-from-start off
@@ -790,6 +792,17 @@ def run_profile(args):
             r = solver.implicit_residual(Un, U)
         torch.cuda.synchronize()
         print(f"profile run done: |R| {float(r.norm()):.6f}")
+    elif args.target == "adjoint":
+        n = 512
+        mob = torch.from_numpy(G.gaussian_mobility(3, (n, n))).cuda()
+        c0 = torch.from_numpy(G.ch_initial(5, (n, n))).cuda()
+        s = pf.Solver((n, n), h=1.0, model="ch")
+        s.set_params(W=1.0, kappa=0.5, mobility=1.0, dt=1e-3, mobility_field=mob)
+        target = c0.clone()
+        s.step_explicit(target, 200)
+        loss, g = s.adjoint(c0, target, 200, 100)
+        torch.cuda.synchronize()
+        print(f"profile run done: loss {loss:.6e}")
     elif args.target == "newton":
         from paper_2601_06079_gb300 import warmstart as WS
         n = 128
@@ -852,7 +865,8 @@ def main():
                     help="run one workload untimed for ncu (see --target)")
     ap.add_argument("--tsteps", type=int, default=N_TSTEPS)
     ap.add_argument("--target", default="ch",
-                    choices=["ch", "surrogate", "jvp", "residual", "newton", "ensemble", "coupled",
+                    choices=["ch", "surrogate", "jvp", "residual", "newton", "adjoint", "ensemble",
+                             "coupled",
                              "elastic", "train"],
                     help="workload of --profile")
     args = ap.parse_args()

@@ -191,8 +191,8 @@ __global__ void __launch_bounds__(kThreads) k_ch_mob_step(const ChMobArgs a, flo
 }
 
 __global__ void __launch_bounds__(kThreads) k_ch_adj_step(const ChMobArgs a, const float* yin,
-                                                          float* yout, double* grad_m,
-                                                          double* acc) {
+                                                          float* yout, float* grad_hi,
+                                                          float* grad_lo, double* acc) {
   __shared__ Tile T;
   __shared__ double red[3][kThreads / 32];
   const int x0 = blockIdx.x * TX, y0 = block_row() * TY;
@@ -229,10 +229,12 @@ __global__ void __launch_bounds__(kThreads) k_ch_adj_step(const ChMobArgs a, con
   __syncthreads();
   // per-node products in FP32 (GB300's FP64 rate is a small fraction of its
   // FP32 rate); each thread's two or three nodes sum in FP32, the block sums
-  // and the running mobility gradient in FP64.  The lumped mass m_i is
-  // cell * frac, with cell applied once per thread.
+  // in FP64.  The running mobility gradient, summed over all steps, is a
+  // compensated FP32 pair per node (Knuth's two-sum: the rounding error of
+  // each addition is exact in FP32 and collects in lo).  The lumped mass m_i
+  // is cell * frac, with cell applied once per thread.
   float dM = 0.0f;
-  const float ngm = (float)(-(double)a.dt * a.M * a.cell);  // -dt M cell
+  const float ngm = a.ngm;  // -dt M cell
   for (int i = threadIdx.x; i < S1X * S1Y; i += kThreads) {
     const int x = 1 + i % S1X, y = 1 + i / S1X;
     const float w = gather4(T.E, y, x);
@@ -243,7 +245,13 @@ __global__ void __launch_bounds__(kThreads) k_ch_adj_step(const ChMobArgs a, con
       const float frac = ((gx == 0 || gx == a.nx - 1) ? 0.5f : 1.0f) *
                          ((gy == 0 || gy == a.ny - 1) ? 0.5f : 1.0f);
       dM = fmaf(frac * w, T.mu[y - 1][x - 1], dM);
-      if (grad_m) grad_m[(int64_t)gy * a.nx + gx] += (double)(ngm * frac * gather4(T.G, y, x));
+      if (grad_hi) {
+        const int64_t gi = (int64_t)gy * a.nx + gx;
+        const float v = ngm * frac * gather4(T.G, y, x);
+        const float hi = grad_hi[gi], t = hi + v, bp = t - hi;
+        grad_lo[gi] += (hi - (t - bp)) + (v - bp);
+        grad_hi[gi] = t;
+      }
     }
   }
   __syncthreads();
@@ -300,6 +308,14 @@ __global__ void __launch_bounds__(kThreads) k_ch_adj_step(const ChMobArgs a, con
     acc[3 * b + 1] += -(double)a.dt * s[1] / a.W;
     acc[3 * b + 2] += -(double)a.dt * s[2] / a.M;
   }
+}
+
+// out = hi + lo in FP64 (the compensated FP32 pair of the mobility gradient)
+__global__ void k_grad_to_double(const float* __restrict__ hi, const float* __restrict__ lo,
+                                 double* __restrict__ out, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (double)hi[i] + (double)lo[i];
 }
 
 // loss = 1/2 sum_i wt_i (c_i - t_i)^2 ; y = wt_i (c_i - t_i) / m_i
@@ -378,10 +394,19 @@ cudaError_t launch_ch_mob_step(const ChMobArgs& a, float* out, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_ch_adj_step(const ChMobArgs& a, const float* yin, float* yout, double* grad_m,
-                               double* acc, cudaStream_t s) {
+cudaError_t launch_ch_adj_step(const ChMobArgs& a, const float* yin, float* yout,
+                               float* grad_hi, float* grad_lo, double* acc, cudaStream_t s) {
+  if ((grad_hi == nullptr) != (grad_lo == nullptr)) return cudaErrorInvalidValue;
   const dim3 grid = row_grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY);
-  k_ch_adj_step<<<grid, kThreads, 0, s>>>(a, yin, yout, grad_m, acc);
+  k_ch_adj_step<<<grid, kThreads, 0, s>>>(a, yin, yout, grad_hi, grad_lo, acc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_to_double(const float* hi, const float* lo, double* out, int64_t n,
+                                  cudaStream_t s) {
+  int64_t blocks = (n + kThreads - 1) / kThreads;
+  if (blocks > 8 * (int64_t)device_sm_count()) blocks = 8 * (int64_t)device_sm_count();
+  k_grad_to_double<<<(unsigned)blocks, kThreads, 0, s>>>(hi, lo, out, n);
   return cudaGetLastError();
 }
 

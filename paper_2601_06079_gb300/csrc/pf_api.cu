@@ -278,7 +278,7 @@ pf_status step_explicit_mob(pf_ctx* c, float* state, int64_t n_steps) {
 }
 
 struct AdjLayout {
-  size_t ck, seg, y0, y1, ones, acc, small, total;
+  size_t ck, seg, y0, y1, ones, ghi, glo, acc, small, total;
   int64_t nck;
 };
 
@@ -296,6 +296,10 @@ AdjLayout adj_layout(const pf_ctx* c, int64_t n_steps, int ckpt) {
   L.y1 = off;
   off += field;
   L.ones = off;
+  off += field;
+  L.ghi = off;  // running mobility gradient, a compensated FP32 pair per node
+  off += field;
+  L.glo = off;
   off += field;
   L.acc = off;
   off += align_up(sizeof(double) * 3 * pf::ch_mob_blocks((int)c->n[0], (int)c->n[1]), 256);
@@ -1349,6 +1353,8 @@ pf_status pf_adjoint(pf_ctx* c, const float* state0, const float* target, int64_
   float* ones = (float*)(ws + L.ones);
   double* acc = (double*)(ws + L.acc);
   double* small = (double*)(ws + L.small);
+  float* ghi = grad_mobility ? (float*)(ws + L.ghi) : nullptr;
+  float* glo = grad_mobility ? (float*)(ws + L.glo) : nullptr;
   const int nb = pf::ch_mob_blocks(nx, ny);
   const float shift = (float)c->par.shift;
   const double cell = c->h[0] * c->h[1];
@@ -1359,6 +1365,7 @@ pf_status pf_adjoint(pf_ctx* c, const float* state0, const float* target, int64_
     c->mob.mfield = ones;
   }
   pf::ChMobArgs a = c->mob;
+  a.ngm = (float)(-(double)a.dt * a.M * a.cell);
   // forward with checkpoints: ck(j) = d^{j * ckpt_every}, ck(last) = d^N
   const int64_t last = (n_steps + ckpt_every - 1) / ckpt_every;
   PF_CUDA(pf::launch_add(state0, ck(0), N, -shift, c->stream));
@@ -1370,7 +1377,10 @@ pf_status pf_adjoint(pf_ctx* c, const float* state0, const float* target, int64_
     PF_CUDA(pf::launch_loss(ck(last), shift, target, nx, ny, cell, nodal_loss, y0, small + 8,
                             small, c->stream));
     PF_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * 3 * nb, c->stream));
-    if (grad_mobility) PF_CUDA(cudaMemsetAsync(grad_mobility, 0, sizeof(double) * N, c->stream));
+    if (grad_mobility) {
+      PF_CUDA(cudaMemsetAsync(ghi, 0, sizeof(float) * N, c->stream));
+      PF_CUDA(cudaMemsetAsync(glo, 0, sizeof(float) * N, c->stream));
+    }
     float* yin = y0;
     float* yout = y1;
     for (int64_t j = last - 1; j >= 0 && st == PF_OK; --j) {
@@ -1382,7 +1392,7 @@ pf_status pf_adjoint(pf_ctx* c, const float* state0, const float* target, int64_
       for (int64_t t = 1; t < len && st == PF_OK; ++t) st = mob_steps(c, seg(t - 1), seg(t), 1);
       for (int64_t t = len - 1; t >= 0 && st == PF_OK; --t) {
         a.d = seg(t);
-        cudaError_t e = pf::launch_ch_adj_step(a, yin, yout, grad_mobility, acc, c->stream);
+        cudaError_t e = pf::launch_ch_adj_step(a, yin, yout, ghi, glo, acc, c->stream);
         if (e != cudaSuccess) {
           c->mob.mfield = saved_field;
           return cuda_fail(c, e, "adjoint step");
@@ -1392,6 +1402,8 @@ pf_status pf_adjoint(pf_ctx* c, const float* state0, const float* target, int64_
     }
     if (st == PF_OK) {
       cudaError_t e = pf::launch_colsum(acc, nb, 3, 3, small + 1, c->stream);
+      if (e == cudaSuccess && grad_mobility)
+        e = pf::launch_grad_to_double(ghi, glo, grad_mobility, N, c->stream);
       if (e == cudaSuccess && grad_state0)
         e = pf::launch_mass_scale(yin, nx, ny, cell, grad_state0, c->stream);
       double host[4] = {0, 0, 0, 0};

@@ -169,11 +169,16 @@ struct ChMobArgs {
   Stencil2D k;           // Q1 stiffness stencil / cell
   float kappa, M, W, dt, ihx, ihy;
   double cell;
+  float ngm;  // -dt M cell, the factor of the mobility gradient (reverse step)
 };
 int ch_mob_blocks(int nx, int ny);
 cudaError_t launch_ch_mob_step(const ChMobArgs& a, float* out, cudaStream_t s);
+// grad_hi / grad_lo: the running mobility gradient as a compensated FP32 pair
+// per node (both null: not accumulated); grad_to_double writes hi + lo in FP64.
 cudaError_t launch_ch_adj_step(const ChMobArgs& a, const float* yin, float* yout,
-                               double* grad_m, double* acc, cudaStream_t s);
+                               float* grad_hi, float* grad_lo, double* acc, cudaStream_t s);
+cudaError_t launch_grad_to_double(const float* hi, const float* lo, double* out, int64_t n,
+                                  cudaStream_t s);
 cudaError_t launch_loss(const float* d, float shift, const float* target, int nx, int ny,
                         double cell, int nodal, float* y, double* partials, double* out,
                         cudaStream_t s);
