@@ -57,6 +57,9 @@ struct pf_ctx {
   // CUDA graph of kGraphSteps explicit steps buf_a -> ... -> buf_a
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
+  // the same for the mobility-field steps, with the field it was captured with
+  cudaGraphExec_t mob_graph = nullptr;
+  const float* mob_graph_field = nullptr;
 
   // batched ensemble (count > 0): instances' sizes, tuned band heights, device arrays
   int ens_count = 0;
@@ -204,7 +207,40 @@ void set_params3d(pf_ctx* c, const pf_params* p) {
 void destroy_graph(pf_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
   c->graph = nullptr;
+  if (c->mob_graph) cudaGraphExecDestroy(c->mob_graph);
+  c->mob_graph = nullptr;
 }
+
+// Captures the launches fn(stream) issues on the context's capture stream and
+// instantiates them into *out.
+template <class F>
+pf_status capture_graph(pf_ctx* c, F&& fn, cudaGraphExec_t* out, const char* what) {
+  if (!c->cap_stream) PF_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  PF_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+  const cudaError_t le = fn(c->cap_stream);
+  cudaGraph_t g = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(c->cap_stream, &g);
+  if (le != cudaSuccess || ee != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_fail(c, le != cudaSuccess ? le : ee, what);
+  }
+  const cudaError_t ie = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) {
+    *out = nullptr;
+    return cuda_fail(c, ie, what);
+  }
+  return PF_OK;
+}
+
+// Executable graphs that live for one call (freed when their launches are done)
+struct CallGraphs {
+  cudaGraphExec_t g[3] = {nullptr, nullptr, nullptr};
+  ~CallGraphs() {
+    for (cudaGraphExec_t x : g)
+      if (x) cudaGraphExecDestroy(x);
+  }
+};
 
 cudaError_t launch_step(pf_ctx* c, const float* in, float* out, cudaStream_t s) {
   pf::Explicit2DArgs a = c->ex;
@@ -242,7 +278,29 @@ pf_status ensure_graph(pf_ctx* c) {
 
 int64_t nodes2d(const pf_ctx* c) { return c->n[0] * c->n[1]; }
 
-// n steps from d_in into d_out (both plain planes) through the ping-pong planes
+// graph of kGraphSteps mobility-field steps buf_a -> buf_b -> ... -> buf_a
+pf_status ensure_mob_graph(pf_ctx* c) {
+  if (c->mob_graph && c->mob_graph_field == c->mob.mfield) return PF_OK;
+  if (c->mob_graph) cudaGraphExecDestroy(c->mob_graph);
+  c->mob_graph = nullptr;
+  pf::ChMobArgs a = c->mob;
+  const pf_status st = capture_graph(
+      c,
+      [&](cudaStream_t s) {
+        cudaError_t e = cudaSuccess;
+        for (int i = 0; i < kGraphSteps && e == cudaSuccess; ++i) {
+          a.d = (i % 2 == 0) ? c->buf_a : c->buf_b;
+          e = pf::launch_ch_mob_step(a, (i % 2 == 0) ? c->buf_b : c->buf_a, s);
+        }
+        return e;
+      },
+      &c->mob_graph, "capture mobility-field steps");
+  if (st == PF_OK) c->mob_graph_field = c->mob.mfield;
+  return st;
+}
+
+// n steps from d_in into d_out (both plain planes) through the ping-pong
+// planes; runs of kGraphSteps replay the mobility-field graph
 pf_status mob_steps(pf_ctx* c, const float* d_in, float* d_out, int64_t n) {
   const int64_t N = nodes2d(c);
   if (n == 0) {
@@ -250,13 +308,24 @@ pf_status mob_steps(pf_ctx* c, const float* d_in, float* d_out, int64_t n) {
       PF_CUDA(cudaMemcpyAsync(d_out, d_in, sizeof(float) * N, cudaMemcpyDeviceToDevice, c->stream));
     return PF_OK;
   }
-  pf::ChMobArgs a = c->mob;
   const float* cur = d_in;
+  if (n > kGraphSteps) {  // the last step still writes d_out directly
+    pf_status st = ensure_mob_graph(c);
+    if (st != PF_OK) return st;
+    PF_CUDA(cudaMemcpyAsync(c->buf_a, d_in, sizeof(float) * N, cudaMemcpyDeviceToDevice,
+                            c->stream));
+    for (; n > kGraphSteps; n -= kGraphSteps) PF_CUDA(cudaGraphLaunch(c->mob_graph, c->stream));
+    cur = c->buf_a;
+  }
+  pf::ChMobArgs a = c->mob;
+  float* pp[2] = {c->buf_a, c->buf_b};
+  int nxt = cur == c->buf_a ? 1 : 0;
   for (int64_t s = 0; s < n; ++s) {
-    float* dst = (s == n - 1) ? d_out : ((s % 2 == 0) ? c->buf_a : c->buf_b);
+    float* dst = (s == n - 1) ? d_out : pp[nxt];
     a.d = cur;
     PF_CUDA(pf::launch_ch_mob_step(a, dst, c->stream));
     cur = dst;
+    nxt ^= 1;
   }
   return PF_OK;
 }
@@ -267,8 +336,14 @@ pf_status step_explicit_mob(pf_ctx* c, float* state, int64_t n_steps) {
   float* cur = c->buf_a;
   float* oth = c->buf_b;
   PF_CUDA(pf::launch_add(state, cur, N, -shift, c->stream));
+  int64_t left = n_steps;
+  if (left >= kGraphSteps) {  // whole graphs leave the state in buf_a
+    pf_status st = ensure_mob_graph(c);
+    if (st != PF_OK) return st;
+    for (; left >= kGraphSteps; left -= kGraphSteps) PF_CUDA(cudaGraphLaunch(c->mob_graph, c->stream));
+  }
   pf::ChMobArgs a = c->mob;
-  for (int64_t s = 0; s < n_steps; ++s) {
+  for (; left > 0; --left) {
     a.d = cur;
     PF_CUDA(pf::launch_ch_mob_step(a, oth, c->stream));
     std::swap(cur, oth);
@@ -1383,21 +1458,58 @@ pf_status pf_adjoint(pf_ctx* c, const float* state0, const float* target, int64_
     }
     float* yin = y0;
     float* yout = y1;
+    // whole segments replay graphs captured here (while the forward pass runs):
+    // g[0] recomputes seg(1 .. ckpt-1) from seg(0), g[1 + p] reverses a segment
+    // starting from y0 (p = 0) or y1 (p = 1); a shorter last segment launches
+    // its steps one by one
+    CallGraphs cg;
+    const bool graphs = ckpt_every >= 8;
+    auto recompute = [&](cudaStream_t s, int64_t len) {
+      pf::ChMobArgs r = a;
+      cudaError_t e = cudaSuccess;
+      for (int64_t t = 1; t < len && e == cudaSuccess; ++t) {
+        r.d = seg(t - 1);
+        e = pf::launch_ch_mob_step(r, seg(t), s);
+      }
+      return e;
+    };
+    auto reverse = [&](cudaStream_t s, int64_t len, float* yi, float* yo) {
+      pf::ChMobArgs r = a;
+      cudaError_t e = cudaSuccess;
+      for (int64_t t = len - 1; t >= 0 && e == cudaSuccess; --t) {
+        r.d = seg(t);
+        e = pf::launch_ch_adj_step(r, yi, yo, ghi, glo, acc, s);
+        std::swap(yi, yo);
+      }
+      return e;
+    };
     for (int64_t j = last - 1; j >= 0 && st == PF_OK; --j) {
       const int64_t start = j * ckpt_every;
       const int64_t len = std::min<int64_t>(ckpt_every, n_steps - start);
+      const bool whole = graphs && len == ckpt_every;
       // recompute d^{start} .. d^{start+len-1} into the segment buffer
       PF_CUDA(cudaMemcpyAsync(seg(0), ck(j), sizeof(float) * N, cudaMemcpyDeviceToDevice,
                               c->stream));
-      for (int64_t t = 1; t < len && st == PF_OK; ++t) st = mob_steps(c, seg(t - 1), seg(t), 1);
-      for (int64_t t = len - 1; t >= 0 && st == PF_OK; --t) {
-        a.d = seg(t);
-        cudaError_t e = pf::launch_ch_adj_step(a, yin, yout, ghi, glo, acc, c->stream);
-        if (e != cudaSuccess) {
-          c->mob.mfield = saved_field;
-          return cuda_fail(c, e, "adjoint step");
-        }
-        std::swap(yin, yout);
+      cudaError_t e = cudaSuccess;
+      if (whole) {
+        if (!cg.g[0])
+          st = capture_graph(c, [&](cudaStream_t s) { return recompute(s, ckpt_every); }, &cg.g[0],
+                             "capture the recompute");
+        if (st == PF_OK) e = cudaGraphLaunch(cg.g[0], c->stream);
+        const int p = yin == y0 ? 0 : 1;
+        if (st == PF_OK && e == cudaSuccess && !cg.g[1 + p])
+          st = capture_graph(c, [&](cudaStream_t s) { return reverse(s, ckpt_every, yin, yout); },
+                             &cg.g[1 + p], "capture the reverse sweep");
+        if (st == PF_OK && e == cudaSuccess) e = cudaGraphLaunch(cg.g[1 + p], c->stream);
+        if (ckpt_every % 2) std::swap(yin, yout);
+      } else {
+        e = recompute(c->stream, len);
+        if (e == cudaSuccess) e = reverse(c->stream, len, yin, yout);
+        if (len % 2) std::swap(yin, yout);
+      }
+      if (st == PF_OK && e != cudaSuccess) {
+        c->mob.mfield = saved_field;
+        return cuda_fail(c, e, "adjoint step");
       }
     }
     if (st == PF_OK) {
