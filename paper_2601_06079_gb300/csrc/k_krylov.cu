@@ -2,9 +2,9 @@
 // basis is FP32; every inner product and norm keeps about 48 bits per thread
 // and finishes in FP64: each thread forms FP32 sums over 8 consecutive
 // products and adds them into a compensated FP32 pair (hi + lo, Knuth's
-// two-sum), blocks reduce in FP64 through shared memory, and the last block
-// sums the per-block partials in a fixed order, so results are
-// deterministic.  No FP64 arithmetic runs per element: GB300 issues about 2
+// two-sum), warps combine the pairs the same way and blocks add the warps'
+// values in FP64, and the last block sums the per-block partials in a fixed
+// order, so results are deterministic.  No FP64 arithmetic runs per element: GB300 issues about 2
 // FP64 operations per clock per SM, 64 times fewer than FP32.
 #include "pf_internal.h"
 
@@ -43,6 +43,30 @@ __device__ double block_sum(double v, double* scratch) {
   __syncthreads();
   v = (threadIdx.x < kThreads / 32) ? scratch[threadIdx.x] : 0.0;
   if (w == 0) v = warp_sum(v);
+  return v;
+}
+
+// Block-wide sum of the threads' compensated pairs, valid in thread 0: the
+// warp tree combines pairs in FP32 (two-sum, the low parts added), only the
+// warps' values are summed in FP64 (a tree in warp 0), in a fixed order.
+__device__ double block_sum2(Acc2 a, double* scratch) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h = __shfl_down_sync(0xffffffffu, a.hi, o);
+    const float l = __shfl_down_sync(0xffffffffu, a.lo, o);
+    a.add(h);
+    a.lo += l;
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) scratch[w] = a.value();
+  __syncthreads();
+  double v = 0.0;
+  if (w == 0) {
+    v = l < kThreads / 32 ? scratch[l] : 0.0;
+#pragma unroll
+    for (int o = kThreads / 64; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  }
   return v;
 }
 
@@ -116,7 +140,7 @@ __device__ __forceinline__ void write_partials(Acc2 (&acc)[KMAX], int k, double*
 #pragma unroll
   for (int j = 0; j < KMAX; ++j) {
     if (j < k) {
-      const double r = block_sum(acc[j].value(), scratch);
+      const double r = block_sum2(acc[j], scratch);
       if (threadIdx.x == 0) partials[blockIdx.x * k + j] = r;
     }
   }
@@ -190,7 +214,7 @@ __global__ void __launch_bounds__(kThreads) k_update(const float* __restrict__ V
     if (norm_out) acc.add(chunk_dot(x, x, i0, n));
   }
   if (norm_out) {
-    const double r = block_sum(acc.value(), scratch);
+    const double r = block_sum2(acc, scratch);
     if (threadIdx.x == 0) partials[blockIdx.x] = r;
     finish_sum(partials, 1, norm_out, count, scratch);
   }
@@ -349,7 +373,7 @@ __global__ void __launch_bounds__(kThreads) k_mass_norm(const float* __restrict_
     }
     acc.add(run);
   }
-  const double r = block_sum(acc.value(), scratch);
+  const double r = block_sum2(acc, scratch);
   if (threadIdx.x == 0) partials[blockIdx.x] = r;
   finish_sum(partials, 1, out, count, scratch);
 }
