@@ -331,6 +331,24 @@ pf_status pf_energy2d_static(const float* state, int64_t nx, int64_t ny, double 
                              double W, double kappa, double* out, void* stream,
                              const char** err);
 
+/* Squared distance sum_i (a_i - b_i)^2 of two FP32 device arrays, each
+ * difference formed in FP32 and the sum kept in FP64-equivalent precision in
+ * a fixed order, so repeated calls give the same bits.  The learned warm start
+ * takes sqrt(sum / n) over consecutive states U^{n+1} - U^n of its training
+ * trajectories (Eq. 13 steps) as the output unit of a surrogate without
+ * history.  No counterpart in the paper.
+ *   a, b         device, n FP32 values each (may be NULL when n == 0)
+ *   n            values, >= 0; n == 0 gives 0 and enqueues nothing
+ *   dev_scratch  device, PF_SQ_DISTANCE_SCRATCH doubles owned by the caller;
+ *                a call in flight on another stream must not share it
+ *   stream       cudaStream_t to enqueue on (NULL = legacy default stream)
+ *   out          host, 1 double
+ * PF_ERR_ARG for a NULL out, n < 0 or (n > 0 and a NULL pointer); PF_ERR_CUDA
+ * if a launch or the copy fails.  Synchronises the stream. */
+enum { PF_SQ_DISTANCE_SCRATCH = 2050 };
+pf_status pf_sq_distance(const float* a, const float* b, int64_t n, double* dev_scratch,
+                         void* stream, double* out);
+
 /* ---- Learned warm start for the implicit step (no counterpart in the paper) ----
  * A 3-D U-Net (4 levels, 32 channels, 3x3x3 convolutions, BF16 operands, FP32
  * accumulation; 15 layers) gives the first Newton iterate for U^{n+1}.

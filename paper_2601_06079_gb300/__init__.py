@@ -25,7 +25,7 @@ from ._lib import (PF_ENS_PER_STEP, PF_ENS_PERSISTENT, PF_ENS_PLAIN,  # noqa: F4
                    pf_surrogate_param_count,
                    pf_surrogate_workspace, pf_surrogate_predict, pf_surrogate_train_step,
                    pf_conv3d_check, pf_surrogate_loss_grad,
-                   pf_energy, pf_energy2d_static,
+                   pf_energy, pf_energy2d_static, pf_sq_distance, PF_SQ_DISTANCE_SCRATCH,
                    pf_implicit_residual, pf_jvp, pf_last_error, pf_set_params, pf_step_explicit,
                    pf_step_implicit)
 
@@ -528,6 +528,24 @@ class _CHMisfit(torch.autograd.Function):
         return (go * gm, (go * gk).to(torch.float64), (go * gw).to(torch.float64),
                 (go * gM).to(torch.float64), (go * g0).to(g0.dtype), None, None, None, None,
                 None, None)
+
+
+def sq_distance(a, b, stream=None):
+    """sum_i (a_i - b_i)^2 in FP64 for two contiguous float32 CUDA tensors of the
+    same size (pf_sq_distance), enqueued on `stream` (torch's current stream by
+    default)."""
+    if a.dtype != torch.float32 or b.dtype != torch.float32 or not (a.is_cuda and b.is_cuda):
+        raise ValueError("a and b must be float32 CUDA tensors")
+    if a.numel() != b.numel() or not (a.is_contiguous() and b.is_contiguous()):
+        raise ValueError("a and b must be contiguous and of the same size")
+    stream = stream if stream is not None else torch.cuda.current_stream(a.device)
+    scratch = _on_stream(stream, 0, a.device, dtype=torch.float64,
+                         shape=(PF_SQ_DISTANCE_SCRATCH,))
+    st, v = pf_sq_distance(a.data_ptr(), b.data_ptr(), a.numel(), scratch.data_ptr(),
+                           stream.cuda_stream)
+    if st != 0:
+        raise PFError(st, "pf_sq_distance")
+    return v
 
 
 def ch_misfit(mobility_field, kappa, W, M, c0, target, dt, n_steps, ckpt_every=100, h=1.0,

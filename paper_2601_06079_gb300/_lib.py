@@ -148,6 +148,9 @@ def lib():
         L.pf_energy2d_static.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_double,
                                          C.c_double, C.c_double, C.c_double, C.c_void_p,
                                          C.c_void_p, C.POINTER(C.c_char_p)]
+        L.pf_sq_distance.restype = st
+        L.pf_sq_distance.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
+                                     C.POINTER(C.c_double)]
         L.pf_implicit_adjoint_workspace.restype = st
         L.pf_implicit_adjoint_workspace.argtypes = [ctx, C.c_int64, C.POINTER(C.c_size_t)]
         L.pf_implicit_adjoint.restype = st
@@ -195,7 +198,8 @@ def exported_symbols():
             "pf_surrogate_loss_grad",
             "pf_conv3d_check", "pf_energy", "pf_elastic_workspace", "pf_elastic_apply",
             "pf_elastic_load", "pf_elastic_solve", "pf_elastic_sensitivity",
-            "pf_energy2d_static", "pf_fp32_peak", "pf_last_error", "pf_destroy"]
+            "pf_energy2d_static", "pf_sq_distance", "pf_fp32_peak", "pf_last_error",
+            "pf_destroy"]
 
 
 # --- thin same-name wrappers -------------------------------------------------
@@ -370,6 +374,17 @@ def pf_energy2d_static(state_ptr, nx, ny, hx, hy, W, kappa, out_ptr, stream):
     s = lib().pf_energy2d_static(C.c_void_p(state_ptr), nx, ny, hx, hy, W, kappa,
                                  C.c_void_p(out_ptr), C.c_void_p(stream), C.byref(msg))
     return s, (msg.value.decode() if msg.value else "")
+
+
+PF_SQ_DISTANCE_SCRATCH = 2050
+
+
+def pf_sq_distance(a_ptr, b_ptr, n, scratch_ptr, stream):
+    """sum_i (a_i - b_i)^2 of two device FP32 arrays; returns (status, value)."""
+    v = C.c_double(0.0)
+    s = lib().pf_sq_distance(C.c_void_p(a_ptr), C.c_void_p(b_ptr), n, C.c_void_p(scratch_ptr),
+                             C.c_void_p(stream), C.byref(v))
+    return s, v.value
 
 
 def pf_elastic_workspace(e):

@@ -195,3 +195,59 @@ extern "C" pf_status pf_energy2d_static(const float* state, int64_t nx, int64_t 
   if (err) *err = "";
   return PF_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Squared distance sum_i (a_i - b_i)^2 (pf_sq_distance).
+//
+// Each difference d is formed in FP32 and its square split exactly into
+// p = fl(d * d) and e = fma(d, d, -p).  A thread keeps a compensated FP32 pair
+// (Knuth's two-sum on the running value, rounding errors and e into the low
+// word), so no FP64 operation runs per element; the pair enters the FP64 block
+// sum once, and the block partials are summed by one block in a fixed order.
+// ---------------------------------------------------------------------------
+namespace pf {
+namespace {
+
+__global__ void __launch_bounds__(kThreads) k_sq_distance(const float* a, const float* b,
+                                                          int64_t n, double* partials) {
+  const int64_t stride = (int64_t)gridDim.x * kThreads;
+  float hi = 0.0f, lo = 0.0f;
+  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += stride) {
+    const float d = a[i] - b[i];
+    const float p = __fmul_rn(d, d);  // never contracted into the add below
+    const float e = fmaf(d, d, -p);
+    const float s = hi + p;
+    const float bp = s - hi;
+    lo += ((hi - (s - bp)) + (p - bp)) + e;
+    hi = s;
+  }
+  double v = (double)hi + (double)lo, unused = 0.0;
+  block_sum2(v, unused);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = v;
+    partials[2 * blockIdx.x + 1] = 0.0;
+  }
+}
+
+}  // namespace
+}  // namespace pf
+
+extern "C" pf_status pf_sq_distance(const float* a, const float* b, int64_t n,
+                                    double* dev_scratch, void* stream, double* out) {
+  if (!out || n < 0 || (n > 0 && (!a || !b || !dev_scratch))) return PF_ERR_ARG;
+  *out = 0.0;
+  if (n == 0) return PF_OK;
+  const cudaStream_t s = (cudaStream_t)stream;
+  const int64_t want = (n + pf::kThreads - 1) / pf::kThreads;
+  const int nb = (int)(want < pf::kMaxBlocks ? want : pf::kMaxBlocks);
+  double* result = dev_scratch + 2 * pf::kMaxBlocks;
+  pf::k_sq_distance<<<nb, pf::kThreads, 0, s>>>(a, b, n, dev_scratch);
+  pf::k_sum_partials<<<1, pf::kThreads, 0, s>>>(dev_scratch, nb, result);
+  double host = 0.0;
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(&host, result, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return PF_ERR_CUDA;
+  *out = host;
+  return PF_OK;
+}

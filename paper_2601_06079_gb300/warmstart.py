@@ -27,7 +27,7 @@ import torch
 
 import pf_inputs as G
 
-from . import Solver, Surrogate
+from . import Solver, Surrogate, sq_distance
 
 FANCHEN = dict(kappa=1.0, mobility=1.0, alpha=1.0, beta=1.0, gamma=1.5, shift=0.0)
 
@@ -54,12 +54,12 @@ def trajectories(solver, seeds, n_steps, n_grains=64):
 
 
 def increment_scale(trajs):
-    """RMS of U^{n+1} - U^n over the training pairs (output unit without history)."""
+    """RMS of U^{n+1} - U^n over the training pairs (output unit without history);
+    the squared increments are summed by the library (pf_sq_distance)."""
     s, n = 0.0, 0
     for t in trajs:
-        d = t[1:] - t[:-1]
-        s += float(d.double().pow(2).sum())
-        n += d.numel()
+        s += sq_distance(t[1:], t[:-1])
+        n += t[1:].numel()
     return (s / n) ** 0.5
 
 

@@ -93,3 +93,17 @@ def test_explicit_only_workspace_refuses_implicit_steps_on_host(libpf):
     st, ex = _lib.pf_explicit_workspace(ctx)
     assert st == 0 and ex == ws
     _lib.pf_destroy(ctx)
+
+
+def test_sq_distance_validates_on_host(libpf):
+    # argument errors and the empty sum return before any CUDA call
+    from paper_2601_06079_gb300 import _lib
+    _lib.lib()
+    assert _lib.pf_sq_distance(0, 0, 0, 0, 0) == (0, 0.0)
+    assert _lib.pf_sq_distance(0x1000, 0x1000, -1, 0x2000, 0)[0] == _lib.PF_ERR_ARG
+    for a, b, s in [(0, 0x1000, 0x2000), (0x1000, 0, 0x2000), (0x1000, 0x1000, 0)]:
+        assert _lib.pf_sq_distance(a, b, 5, s, 0)[0] == _lib.PF_ERR_ARG
+    v = _lib.C.c_double(1.0)
+    assert _lib.lib().pf_sq_distance(None, None, 0, None, None, None) == _lib.PF_ERR_ARG
+    assert _lib.lib().pf_sq_distance(None, None, 0, None, None, _lib.C.byref(v)) == 0
+    assert v.value == 0.0
