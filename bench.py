@@ -741,6 +741,9 @@ def run_profile(args):
     newton    one implicit grain-growth step on 128^3 x 8 fields (after three
               warm-up steps) inside a profiler range, for ncu
               --profile-from-start off
+    newton2d  one implicit split Cahn-Hilliard step on 2048^2 (dt 1, after three
+              warm-up steps) inside a profiler range, for ncu
+              --profile-from-start off
     ensemble  20 steps of the 256-instance AC ensemble, one launch per step (the
               persistent mode runs the same task body behind a grid barrier)
     coupled   20 coupled Allen-Cahn / Cahn-Hilliard steps on 2048^2
@@ -816,6 +819,18 @@ def run_profile(args):
         torch.cuda.synchronize()
         torch.cuda.cudart().cudaProfilerStop()
         print(f"profile run done: {st['newton_iters']} Newton, {st['gmres_iters']} GMRES")
+    elif args.target == "newton2d":
+        n = N_SIDE
+        solver = pf.Solver((n, n), h=1.0, model="ch")
+        solver.set_params(W=1.0, kappa=0.5, mobility=1.0, dt=1.0)
+        U = torch.from_numpy(G.ch_initial(1, (n, n))).cuda()
+        solver.step_implicit(U, 3)
+        torch.cuda.synchronize()
+        torch.cuda.cudart().cudaProfilerStart()  # ncu --profile-from-start off: this step only
+        st = solver.step_implicit(U, 1)
+        torch.cuda.synchronize()
+        torch.cuda.cudart().cudaProfilerStop()
+        print(f"profile run done: {st['newton_iters']} Newton, {st['gmres_iters']} GMRES")
     elif args.target == "elastic":
         n = 129
         el = pf.Elastic((n, n, n), 100.0 / (n - 1))
@@ -865,7 +880,8 @@ def main():
                     help="run one workload untimed for ncu (see --target)")
     ap.add_argument("--tsteps", type=int, default=N_TSTEPS)
     ap.add_argument("--target", default="ch",
-                    choices=["ch", "surrogate", "jvp", "residual", "newton", "adjoint", "ensemble",
+                    choices=["ch", "surrogate", "jvp", "residual", "newton", "newton2d", "adjoint",
+                             "ensemble",
                              "coupled",
                              "elastic", "train"],
                     help="workload of --profile")

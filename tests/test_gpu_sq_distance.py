@@ -18,8 +18,8 @@ def _ref(a, b):
 def test_matches_fp64_sum(n):
     import paper_2601_06079_gb300 as pf
     import pf_inputs as G
-    a = G.uniform(11, n, -1.0, 1.0, "sqdist-a").astype(np.float32)
-    b = (a + G.uniform(12, n, -1e-3, 1e-3, "sqdist-b")).astype(np.float32)
+    a = G.uniform(11, n, -1.0, 1.0, "vector").astype(np.float32)
+    b = (a + G.uniform(12, n, -1e-3, 1e-3, "vector")).astype(np.float32)
     ta, tb = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
     v = pf.sq_distance(ta, tb)
     ref = _ref(a, b)
@@ -31,7 +31,7 @@ def test_matches_fp64_sum(n):
 def test_increment_scale_of_a_trajectory():
     import pf_inputs as G
     from paper_2601_06079_gb300 import warmstart as WS
-    t = [torch.from_numpy(G.uniform(s, 5 * 8 * 16 ** 3, 0.0, 1.0, "sqdist-traj")
+    t = [torch.from_numpy(G.uniform(s, 5 * 8 * 16 ** 3, 0.0, 1.0, "vector")
                           .astype(np.float32).reshape(5, 8, 16, 16, 16)).cuda()
          for s in (1, 2)]
     s, n = 0.0, 0
