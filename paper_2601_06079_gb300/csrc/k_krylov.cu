@@ -111,6 +111,21 @@ __device__ __forceinline__ void load8(const float* __restrict__ p, int64_t i0, i
   }
 }
 
+// load8 through L2 only (ld.global.cg): for values this kernel wrote itself,
+// which the non-coherent read-only path of load8 may not see
+template <bool kVec>
+__device__ __forceinline__ void load8_cg(const float* p, int64_t i0, int64_t n, float v[kChunk]) {
+  if (kVec && i0 + kChunk <= n) {
+    const float4 a = __ldcg(reinterpret_cast<const float4*>(p + i0));
+    const float4 b = __ldcg(reinterpret_cast<const float4*>(p + i0 + 4));
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  } else {
+#pragma unroll
+    for (int t = 0; t < kChunk; ++t) v[t] = (i0 + t < n) ? __ldcg(p + i0 + t) : 0.0f;
+  }
+}
+
 template <bool kVec>
 __device__ __forceinline__ void store8(float* __restrict__ p, int64_t i0, int64_t n,
                                        const float v[kChunk]) {
@@ -134,45 +149,60 @@ __device__ __forceinline__ float chunk_dot(const float v[kChunk], const float u[
   return s;
 }
 
-template <int KMAX>
-__device__ __forceinline__ void write_partials(Acc2 (&acc)[KMAX], int k, double* scratch,
-                                               double* partials, double* out, unsigned* count) {
+// Block sums of the accumulators of vectors j0 .. j0 + G - 1 (those below k)
+// into partials[blockIdx.x * k + j].
+template <int G>
+__device__ __forceinline__ void group_partials(Acc2 (&acc)[G], int j0, int k, double* scratch,
+                                               double* partials) {
 #pragma unroll
-  for (int j = 0; j < KMAX; ++j) {
-    if (j < k) {
+  for (int j = 0; j < G; ++j) {
+    if (j0 + j < k) {
       const double r = block_sum2(acc[j], scratch);
-      if (threadIdx.x == 0) partials[blockIdx.x * k + j] = r;
+      if (threadIdx.x == 0) partials[blockIdx.x * k + j0 + j] = r;
     }
   }
-  finish_sum(partials, k, out, count, scratch);
 }
 
-// out[j] = V_j . w (j < k <= KMAX), V_j = V + j * ldv; w is read once for all
-// k products (per-block partials in `partials`).  If w == nullptr the squared
-// norm of V_0 is taken (k must be 1).
+// Inner products take the basis vectors in groups of at most kGroup per pass
+// over the chunks (w re-read per group): each j's per-thread sum still runs
+// over the same chunks in the same order, so the results do not depend on the
+// grouping, and the accumulators (2 registers per vector) stay within the
+// 80 registers a thread may hold at 3 blocks of 256 threads per SM, the
+// residency that the fixed grid of 3 blocks per SM needs to run in one wave.
+constexpr int kGroup = 16;
+constexpr int kMinBlocks = 3;
+
+// out[j] = V_j . w (j < k <= KMAX), V_j = V + j * ldv; w is read once per
+// group of kGroup products (per-block partials in `partials`).  If w == nullptr
+// the squared norm of V_0 is taken (k must be 1).
 template <int KMAX, bool kVec>
-__global__ void __launch_bounds__(kThreads) k_dots(const float* __restrict__ V, int64_t ldv,
-                                                   int k, const float* __restrict__ w, int64_t n,
-                                                   double* partials, double* out,
-                                                   unsigned* count) {
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_dots(const float* __restrict__ V,
+                                                               int64_t ldv, int k,
+                                                               const float* __restrict__ w,
+                                                               int64_t n, double* partials,
+                                                               double* out, unsigned* count) {
+  constexpr int G = KMAX < kGroup ? KMAX : kGroup;
   __shared__ double scratch[kThreads / 32];
   const int64_t chunks = (n + kChunk - 1) / kChunk;
-  Acc2 acc[KMAX];
-  for (int64_t c = (int64_t)blockIdx.x * kThreads + threadIdx.x; c < chunks;
-       c += (int64_t)gridDim.x * kThreads) {
-    const int64_t i0 = c * kChunk;
-    float u[kChunk];
-    load8<kVec>(w ? w : V, i0, n, u);
+  for (int j0 = 0; j0 < k; j0 += G) {
+    Acc2 acc[G];
+    for (int64_t c = (int64_t)blockIdx.x * kThreads + threadIdx.x; c < chunks;
+         c += (int64_t)gridDim.x * kThreads) {
+      const int64_t i0 = c * kChunk;
+      float u[kChunk];
+      load8<kVec>(w ? w : V, i0, n, u);
 #pragma unroll
-    for (int j = 0; j < KMAX; ++j) {
-      if (j < k) {
-        float v[kChunk];
-        load8<kVec>(V + j * ldv, i0, n, v);
-        acc[j].add(chunk_dot(v, u, i0, n));
+      for (int j = 0; j < G; ++j) {
+        if (j0 + j < k) {
+          float v[kChunk];
+          load8<kVec>(V + (j0 + j) * ldv, i0, n, v);
+          acc[j].add(chunk_dot(v, u, i0, n));
+        }
       }
     }
+    group_partials<G>(acc, j0, k, scratch, partials);
   }
-  write_partials<KMAX>(acc, k, scratch, partials, out, count);
+  finish_sum(partials, k, out, count, scratch);
 }
 
 // x <- x - sum_j cf[j] V_j over one chunk, j in order for every element
@@ -193,11 +223,13 @@ __device__ __forceinline__ void chunk_update(const float* __restrict__ V, int64_
 
 // w <- w - sum_j coef[j] V_j (coef: device FP64);  optionally (norm_out) |w|^2
 template <int KMAX, bool kVec>
-__global__ void __launch_bounds__(kThreads) k_update(const float* __restrict__ V, int64_t ldv,
-                                                     int k, const double* __restrict__ coef,
-                                                     float* __restrict__ w, int64_t n,
-                                                     double* partials, double* norm_out,
-                                                     unsigned* count) {
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_update(const float* __restrict__ V,
+                                                                 int64_t ldv, int k,
+                                                                 const double* __restrict__ coef,
+                                                                 float* __restrict__ w, int64_t n,
+                                                                 double* partials,
+                                                                 double* norm_out,
+                                                                 unsigned* count) {
   __shared__ double scratch[kThreads / 32];
   __shared__ float cf[KMAX];
   for (int j = threadIdx.x; j < k; j += kThreads) cf[j] = (float)coef[j];
@@ -224,37 +256,58 @@ __global__ void __launch_bounds__(kThreads) k_update(const float* __restrict__ V
 // updated w: the two halves of a CGS2 pass boundary (the first pass's update
 // and the second pass's inner products) in one pass over V and w.  Each
 // element's arithmetic and each thread's chunks are those of k_update
-// followed by k_dots, so the results are identical to the two kernels.
+// followed by k_dots, so the results are identical to the two kernels.  The
+// pass takes the products of the first kGroup vectors; later groups re-read
+// the updated w (this thread's own stores, through L2) and their vectors.
 template <int KMAX, bool kVec>
-__global__ void __launch_bounds__(kThreads) k_update_dots(const float* __restrict__ V,
-                                                          int64_t ldv, int k,
-                                                          const double* __restrict__ coef,
-                                                          float* __restrict__ w, int64_t n,
-                                                          double* partials, double* out,
-                                                          unsigned* count) {
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_update_dots(
+    const float* __restrict__ V, int64_t ldv, int k, const double* __restrict__ coef,
+    float* __restrict__ w, int64_t n, double* partials, double* out, unsigned* count) {
+  constexpr int G = KMAX < kGroup ? KMAX : kGroup;
   __shared__ double scratch[kThreads / 32];
   __shared__ float cf[KMAX];
   for (int j = threadIdx.x; j < k; j += kThreads) cf[j] = (float)coef[j];
   __syncthreads();
   const int64_t chunks = (n + kChunk - 1) / kChunk;
-  Acc2 acc[KMAX];
-  for (int64_t c = (int64_t)blockIdx.x * kThreads + threadIdx.x; c < chunks;
-       c += (int64_t)gridDim.x * kThreads) {
-    const int64_t i0 = c * kChunk;
-    float x[kChunk];
-    load8<kVec>(w, i0, n, x);
-    chunk_update<KMAX, kVec>(V, ldv, k, cf, i0, n, x);
-    store8<kVec>(w, i0, n, x);
+  {
+    Acc2 acc[G];
+    for (int64_t c = (int64_t)blockIdx.x * kThreads + threadIdx.x; c < chunks;
+         c += (int64_t)gridDim.x * kThreads) {
+      const int64_t i0 = c * kChunk;
+      float x[kChunk];
+      load8<kVec>(w, i0, n, x);
+      chunk_update<KMAX, kVec>(V, ldv, k, cf, i0, n, x);
+      store8<kVec>(w, i0, n, x);
 #pragma unroll
-    for (int j = 0; j < KMAX; ++j) {
-      if (j < k) {
-        float v[kChunk];
-        load8<kVec>(V + j * ldv, i0, n, v);
-        acc[j].add(chunk_dot(v, x, i0, n));
+      for (int j = 0; j < G; ++j) {
+        if (j < k) {
+          float v[kChunk];
+          load8<kVec>(V + j * ldv, i0, n, v);
+          acc[j].add(chunk_dot(v, x, i0, n));
+        }
       }
     }
+    group_partials<G>(acc, 0, k, scratch, partials);
   }
-  write_partials<KMAX>(acc, k, scratch, partials, out, count);
+  for (int j0 = G; j0 < k; j0 += G) {
+    Acc2 acc[G];
+    for (int64_t c = (int64_t)blockIdx.x * kThreads + threadIdx.x; c < chunks;
+         c += (int64_t)gridDim.x * kThreads) {
+      const int64_t i0 = c * kChunk;
+      float x[kChunk];
+      load8_cg<kVec>(w, i0, n, x);
+#pragma unroll
+      for (int j = 0; j < G; ++j) {
+        if (j0 + j < k) {
+          float v[kChunk];
+          load8<kVec>(V + (j0 + j) * ldv, i0, n, v);
+          acc[j].add(chunk_dot(v, x, i0, n));
+        }
+      }
+    }
+    group_partials<G>(acc, j0, k, scratch, partials);
+  }
+  finish_sum(partials, k, out, count, scratch);
 }
 
 // y <- a * x + b * y  (host scalars), chunks of 8
