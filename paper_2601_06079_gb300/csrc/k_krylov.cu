@@ -170,6 +170,7 @@ __device__ __forceinline__ void group_partials(Acc2 (&acc)[G], int j0, int k, do
 // 80 registers a thread may hold at 3 blocks of 256 threads per SM, the
 // residency that the fixed grid of 3 blocks per SM needs to run in one wave.
 constexpr int kGroup = 16;
+constexpr int kGroupDots = 8;  // k_dots holds two chunks per vector in flight
 constexpr int kMinBlocks = 3;
 
 // out[j] = V_j . w (j < k <= KMAX), V_j = V + j * ldv; w is read once per
@@ -181,22 +182,29 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_dots(const float* __re
                                                                const float* __restrict__ w,
                                                                int64_t n, double* partials,
                                                                double* out, unsigned* count) {
-  constexpr int G = KMAX < kGroup ? KMAX : kGroup;
+  constexpr int G = KMAX < kGroupDots ? KMAX : kGroupDots;
   __shared__ double scratch[kThreads / 32];
   const int64_t chunks = (n + kChunk - 1) / kChunk;
+  const int64_t stride = (int64_t)gridDim.x * kThreads;
+  const float* x = w ? w : V;
   for (int j0 = 0; j0 < k; j0 += G) {
     Acc2 acc[G];
-    for (int64_t c = (int64_t)blockIdx.x * kThreads + threadIdx.x; c < chunks;
-         c += (int64_t)gridDim.x * kThreads) {
-      const int64_t i0 = c * kChunk;
-      float u[kChunk];
-      load8<kVec>(w ? w : V, i0, n, u);
+    // two of the thread's chunks per iteration (twice the loads in flight),
+    // added in chunk order
+    for (int64_t c = (int64_t)blockIdx.x * kThreads + threadIdx.x; c < chunks; c += 2 * stride) {
+      const int64_t i0 = c * kChunk, i1 = (c + stride) * kChunk;
+      const bool second = c + stride < chunks;
+      float u0[kChunk], u1[kChunk];
+      load8<kVec>(x, i0, n, u0);
+      if (second) load8<kVec>(x, i1, n, u1);
 #pragma unroll
       for (int j = 0; j < G; ++j) {
         if (j0 + j < k) {
-          float v[kChunk];
-          load8<kVec>(V + (j0 + j) * ldv, i0, n, v);
-          acc[j].add(chunk_dot(v, u, i0, n));
+          float v0[kChunk], v1[kChunk];
+          load8<kVec>(V + (j0 + j) * ldv, i0, n, v0);
+          if (second) load8<kVec>(V + (j0 + j) * ldv, i1, n, v1);
+          acc[j].add(chunk_dot(v0, u0, i0, n));
+          if (second) acc[j].add(chunk_dot(v1, u1, i1, n));
         }
       }
     }
