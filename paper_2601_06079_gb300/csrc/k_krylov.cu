@@ -243,15 +243,33 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_update(const float* __
   for (int j = threadIdx.x; j < k; j += kThreads) cf[j] = (float)coef[j];
   __syncthreads();
   const int64_t chunks = (n + kChunk - 1) / kChunk;
+  const int64_t stride = (int64_t)gridDim.x * kThreads;
   Acc2 acc;
-  for (int64_t c = (int64_t)blockIdx.x * kThreads + threadIdx.x; c < chunks;
-       c += (int64_t)gridDim.x * kThreads) {
-    const int64_t i0 = c * kChunk;
-    float x[kChunk];
-    load8<kVec>(w, i0, n, x);
-    chunk_update<KMAX, kVec>(V, ldv, k, cf, i0, n, x);
-    store8<kVec>(w, i0, n, x);
-    if (norm_out) acc.add(chunk_dot(x, x, i0, n));
+  // two of the thread's chunks per iteration (twice the loads in flight); each
+  // element's update and the norm's chunk order are those of one at a time
+  for (int64_t c = (int64_t)blockIdx.x * kThreads + threadIdx.x; c < chunks; c += 2 * stride) {
+    const int64_t i0 = c * kChunk, i1 = (c + stride) * kChunk;
+    const bool second = c + stride < chunks;
+    float x0[kChunk], x1[kChunk];
+    load8<kVec>(w, i0, n, x0);
+    if (second) load8<kVec>(w, i1, n, x1);
+#pragma unroll(KMAX <= 4 ? KMAX : 2)
+    for (int j = 0; j < k; ++j) {
+      float v0[kChunk], v1[kChunk];
+      load8<kVec>(V + j * ldv, i0, n, v0);
+      if (second) load8<kVec>(V + j * ldv, i1, n, v1);
+#pragma unroll
+      for (int t = 0; t < kChunk; ++t) {
+        x0[t] = fmaf(-cf[j], v0[t], x0[t]);
+        if (second) x1[t] = fmaf(-cf[j], v1[t], x1[t]);
+      }
+    }
+    store8<kVec>(w, i0, n, x0);
+    if (second) store8<kVec>(w, i1, n, x1);
+    if (norm_out) {
+      acc.add(chunk_dot(x0, x0, i0, n));
+      if (second) acc.add(chunk_dot(x1, x1, i1, n));
+    }
   }
   if (norm_out) {
     const double r = block_sum2(acc, scratch);
