@@ -28,8 +28,12 @@ constexpr int S2X = TX + 4, S2Y = TY + 4;  // nodes with a 2-node halo
 constexpr int S1X = TX + 2, S1Y = TY + 2;  // nodes with a 1-node halo
 constexpr int EX = TX + 3, EY = TY + 3;    // elements touching the 1-halo nodes
 
+// Mirror image of node index k on an axis of n nodes (period 2(n-1)).  Halo
+// indices lie within one period of the axis, where a reflection at each end
+// gives the image without the integer division.
 __device__ __forceinline__ int mirror(int k, int n) {
   const int p = 2 * (n - 1);
+  if (k >= 1 - n && k <= p) return k < 0 ? -k : (k < n ? k : p - k);
   k %= p;
   if (k < 0) k += p;
   return k < n ? k : p - k;

@@ -25,8 +25,12 @@ constexpr int kThreads = 256;
 constexpr int SX = TX + 2, SY = TY + 2;    // nodes with a 1-node halo
 constexpr int EX = TX + 1, EY = TY + 1;    // elements touching the tile nodes
 
+// Mirror image of node index k on an axis of n nodes (period 2(n-1)).  Halo
+// indices lie within one period of the axis, where a reflection at each end
+// gives the image without the integer division.
 __device__ __forceinline__ int mirror(int k, int n) {
   const int p = 2 * (n - 1);
+  if (k >= 1 - n && k <= p) return k < 0 ? -k : (k < n ? k : p - k);
   k %= p;
   if (k < 0) k += p;
   return k < n ? k : p - k;
