@@ -107,3 +107,11 @@ def test_sq_distance_validates_on_host(libpf):
     assert _lib.lib().pf_sq_distance(None, None, 0, None, None, None) == _lib.PF_ERR_ARG
     assert _lib.lib().pf_sq_distance(None, None, 0, None, None, _lib.C.byref(v)) == 0
     assert v.value == 0.0
+
+
+def test_sq_distance_wrapper_rejects_host_tensors(libpf):
+    import torch
+
+    import paper_2601_06079_gb300 as pf
+    with pytest.raises(ValueError):
+        pf.sq_distance(torch.zeros(4), torch.zeros(4))
