@@ -115,3 +115,33 @@ def test_sq_distance_wrapper_rejects_host_tensors(libpf):
     import paper_2601_06079_gb300 as pf
     with pytest.raises(ValueError):
         pf.sq_distance(torch.zeros(4), torch.zeros(4))
+
+
+def test_ensemble_calls_validate_on_host(libpf):
+    # call order and parameter checks of the ensemble entry points return
+    # before any CUDA call (a fake, never dereferenced workspace address)
+    from paper_2601_06079_gb300 import _lib
+    _lib.lib()
+    st, ctx, ws, _ = _lib.pf_create_ensemble([16, 24], [16, 12], None, 0)
+    assert st == 0
+    good = _lib.pf_params(1.0, 0.5, 1.0, 1e-3, 0.0, 0.0, 0.0, 0.5, None, 0.0)
+    # no workspace yet
+    assert _lib.pf_set_ensemble_params(ctx, [good, good]) == _lib.PF_ERR_STATE
+    assert _lib.pf_set_ensemble_schedule(ctx, [6, 6], None) == _lib.PF_ERR_STATE
+    assert _lib.pf_tune_ensemble(ctx, 1, 2, 2)[0] == _lib.PF_ERR_STATE
+    assert _lib.pf_bind_workspace(ctx, 0x100000, ws) == 0
+    # parameters not set yet
+    assert _lib.pf_set_ensemble_schedule(ctx, [6, 6], None) == _lib.PF_ERR_STATE
+    assert _lib.pf_tune_ensemble(ctx, 1, 2, 2)[0] == _lib.PF_ERR_STATE
+    bad_dt = _lib.pf_params(1.0, 0.5, 1.0, 0.0, 0.0, 0.0, 0.0, 0.5, None, 0.0)
+    other_shift = _lib.pf_params(1.0, 0.5, 1.0, 1e-3, 0.0, 0.0, 0.0, 0.0, None, 0.0)
+    with_field = _lib.pf_params(1.0, 0.5, 1.0, 1e-3, 0.0, 0.0, 0.0, 0.5, 0x2000, 0.0)
+    for p in ([good, bad_dt], [good, other_shift], [with_field, good]):
+        assert _lib.pf_set_ensemble_params(ctx, p) == _lib.PF_ERR_ARG
+    _lib.pf_destroy(ctx)
+    # a mesh context is not an ensemble
+    st, ctx, ws = _lib.pf_create_mesh(2, [64, 64], [1.0, 1.0], _lib.PF_MODEL_AC, 1, 0)
+    assert st == 0
+    assert _lib.pf_set_ensemble_schedule(ctx, [6], None) == _lib.PF_ERR_ARG
+    assert _lib.pf_tune_ensemble(ctx, 1, 1, 1)[0] == _lib.PF_ERR_ARG
+    _lib.pf_destroy(ctx)
