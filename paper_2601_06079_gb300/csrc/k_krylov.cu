@@ -95,8 +95,8 @@ __device__ void finish_sum(const double* partials, int k, double* __restrict__ o
 // Chunks of kChunk = 8 consecutive values: two 16-byte loads when the vectors
 // are 16-byte aligned (kVec) and the chunk is whole, elementwise otherwise
 // (values past n read as 0).  Each kernel below is instantiated for a bound
-// KMAX on the number of basis vectors (4, 8, 16, 32), so that its FP64
-// accumulators take registers only for the vectors a call can have.
+// KMAX on the number of basis vectors (4, 8, 16, 32), so that its accumulators
+// (compensated FP32 pairs) take registers only for the vectors a call can have.
 template <bool kVec>
 __device__ __forceinline__ void load8(const float* __restrict__ p, int64_t i0, int64_t n,
                                       float v[kChunk]) {
@@ -163,19 +163,21 @@ __device__ __forceinline__ void group_partials(Acc2 (&acc)[G], int j0, int k, do
   }
 }
 
-// Inner products take the basis vectors in groups of at most kGroup per pass
-// over the chunks (w re-read per group): each j's per-thread sum still runs
-// over the same chunks in the same order, so the results do not depend on the
-// grouping, and the accumulators (2 registers per vector) stay within the
-// 80 registers a thread may hold at 3 blocks of 256 threads per SM, the
-// residency that the fixed grid of 3 blocks per SM needs to run in one wave.
+// Inner products take the basis vectors in groups per pass over the chunks
+// (w re-read per group; kGroupDots in k_dots, which holds two chunks per
+// vector in flight, kGroup in the fused k_update_dots): each j's per-thread
+// sum still runs over the same chunks in the same order, so the results do
+// not depend on the grouping, and the accumulators (2 registers per vector)
+// stay within the 80 registers a thread may hold at 3 blocks of 256 threads
+// per SM, the residency that the fixed grid of 3 blocks per SM needs to run
+// in one wave.
 constexpr int kGroup = 16;
-constexpr int kGroupDots = 8;  // k_dots holds two chunks per vector in flight
+constexpr int kGroupDots = 8;
 constexpr int kMinBlocks = 3;
 
 // out[j] = V_j . w (j < k <= KMAX), V_j = V + j * ldv; w is read once per
-// group of kGroup products (per-block partials in `partials`).  If w == nullptr
-// the squared norm of V_0 is taken (k must be 1).
+// group of kGroupDots products (per-block partials in `partials`).  If
+// w == nullptr the squared norm of V_0 is taken (k must be 1).
 template <int KMAX, bool kVec>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) k_dots(const float* __restrict__ V,
                                                                int64_t ldv, int k,
