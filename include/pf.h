@@ -331,9 +331,11 @@ pf_status pf_energy2d_static(const float* state, int64_t nx, int64_t ny, double 
                              double W, double kappa, double* out, void* stream,
                              const char** err);
 
-/* Squared distance sum_i (a_i - b_i)^2 of two FP32 device arrays, each
- * difference formed in FP32 and the sum kept in FP64-equivalent precision in
- * a fixed order, so repeated calls give the same bits.  The learned warm start
+/* Squared distance sum_i (a_i - b_i)^2 of two FP32 device arrays: each
+ * difference is formed in FP32 and its square split exactly into two FP32
+ * terms; each thread sums them in a compensated FP32 pair (about 48 bits),
+ * and the block and final sums run in FP64 in a fixed order, so repeated
+ * calls give the same bits.  The learned warm start
  * takes sqrt(sum / n) over consecutive states U^{n+1} - U^n of its training
  * trajectories (Eq. 13 steps) as the output unit of a surrogate without
  * history.  No counterpart in the paper.
